@@ -1,0 +1,453 @@
+#!/usr/bin/env python
+"""Exact-simulation benchmark: node-pattern evaluations per second.
+
+One step = one full exact simulation (every one of the 2^32 input patterns)
+of the 16x16 unsigned multiplier miter: array multiplier vs radix-4
+Booth/Dadda multiplier, 32 PIs, outputs XORed and ORed (synthetic, seeded,
+equivalent, so the whole space is enumerated).  The unit of work is one AIG
+AND node evaluated for one input pattern: cone ANDs x 2^32 per step.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+
+Prints one JSON line.  With --impl reference the CPU oracle is timed on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "16x16 array vs radix-4 Booth/Dadda multiplier miter, 32 PIs, 2^32 patterns, equivalent"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--tier", choices=["auto", "interp", "jit", "spill"], default="auto")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-pairs", type=int, default=4096)
+    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-rate", type=float, default=6.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; replicas, no data-path collective)
+# ---------------------------------------------------------------------------
+
+def dist_setup(n_gpus: int):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clock sampling during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.th:
+            self.th.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# ---------------------------------------------------------------------------
+
+def cpu_oracle_rate(aig, seconds: float):
+    """Time the oracle as it stands on the host cores over a bounded word
+    sample of the workload; returns (evals/s, cores, sample description)."""
+    import oracle as O
+    out = aig.outputs[0]
+    _, cone = O.support(aig.num_pis, aig.fanins, out)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    probe = 4096
+    O.check(aig.num_pis, aig.fanins, out, 0, probe)
+    per_word = (time.perf_counter() - t0) / probe
+    words = max(cores * 256, int(seconds * cores / max(per_word, 1e-9)))
+    words = min(words, 1 << 26)
+    t0 = time.perf_counter()
+    cex, _ = O.check_parallel(aig.num_pis, aig.fanins, out, cores, 0, words)
+    dt = time.perf_counter() - t0
+    assert cex is None
+    rate = cone * 64.0 * words / dt
+    return rate, cores, f"oracle over words [0, {words}) of 2^26 ({words * 64} of 2^32 patterns), {dt:.1f} s"
+
+
+# ---------------------------------------------------------------------------
+# batched and served sub-measurements
+# ---------------------------------------------------------------------------
+
+def measure_batch(ctx, args):
+    """4096 node-pair miters: one persistent launch (CUDA-graph replay) vs one
+    launch per miter (back to back on one stream, one sync; and with a sync
+    after every miter), same interpreter kernel family, identical results."""
+    import numpy as np
+    import torch
+    from paper_2512_06627_b300 import circuits as C
+    from paper_2512_06627_b300 import lec_es as L
+    pb = C.config4_pairs(num_pairs=args.batch_pairs)
+    f = pb.aig.flat_fanins()
+    ms = [L.Miter(pb.aig.num_pis, f, o) for o in pb.aig.outputs]
+    k = len(ms)
+    t0 = time.perf_counter()
+    b = L.lec_es_batch_prepare(ctx, ms)
+    prep = time.perf_counter() - t0
+    L.lec_es_batch_run_async(ctx, b)
+    ref = [r.cex for r in L.lec_es_batch_results(ctx, b, k)]
+    infos = [L.lec_es_compile(m)[0] for m in ms]
+    work = np.array([float(i.num_records) * float(max(1, 1 << max(0, i.n - 5))) for i in infos])
+    ts = []
+    for _ in range(args.batch_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L.lec_es_batch_run_async(ctx, b)
+        got = [r.cex for r in L.lec_es_batch_results(ctx, b, k)]
+        ts.append(time.perf_counter() - t0)
+        assert got == ref
+    L.lec_es_batch_free(ctx, b)
+    batched = k / statistics.median(ts)
+    plans = [L.lec_es_prepare(ctx, m, L.options(tier=L.TIER_INTERP)) for m in ms]
+    # (i) back to back on one stream, one sync at the end
+    t0 = time.perf_counter()
+    for p in plans:
+        L.lec_es_run_async(ctx, p)
+    torch.cuda.synchronize()
+    one_async_s = time.perf_counter() - t0
+    # the plan results come from each plan's own read-back
+    got = [L.lec_es_plan_result(ctx, p).cex for p in plans]
+    assert got == ref
+    # (ii) a sync after every miter
+    t0 = time.perf_counter()
+    for p in plans:
+        L.lec_es_run_async(ctx, p)
+        L.lec_es_plan_result(ctx, p)
+    one_sync_s = time.perf_counter() - t0
+    for p in plans:
+        L.lec_es_plan_free(ctx, p)
+    big = work >= np.sort(work)[-max(1, k // 100)]
+    return {
+        "pairs": k, "nonequivalent": int(sum(1 for x in ref if x != L.NO_CEX)),
+        "support_pis": {"min": int(min(i.n for i in infos)), "max": int(max(i.n for i in infos))},
+        "cone_ands": {"min": int(min(i.cone_ands for i in infos)), "max": int(max(i.cone_ands for i in infos))},
+        "batched_miters_per_s": batched,
+        "one_launch_per_miter_async_miters_per_s": k / one_async_s,
+        "one_launch_per_miter_sync_miters_per_s": k / one_sync_s,
+        "speedup_vs_async": batched / (k / one_async_s),
+        "speedup_vs_sync": batched / (k / one_sync_s),
+        "work_share_top_1pct": float(work[big].sum() / work.sum()),
+        "prepare_s": prep,
+    }
+
+
+def measure_serve(ctx, args):
+    """A seeded Poisson stream of product-bit miter requests (w x w array vs
+    Booth, w in 8..18): submitted at their arrival times through the
+    continuous-batching server; p50/p99 latency and miters/s, against the
+    same requests one launch each."""
+    import numpy as np
+    from paper_2512_06627_b300 import circuits as C
+    from paper_2512_06627_b300 import lec_es as L
+    reqs = C.config5_stream(num_requests=max(1, args.serve_requests), rate_per_s=args.serve_rate)
+    pm = C.ProductBitMiters(seed=5)
+    ms = []
+    for i, r in enumerate(reqs):
+        aig, out = pm.miter(r.w, r.bit, r.mutant, mutant_seed=i)
+        ms.append(L.Miter(aig.num_pis, aig.flat_fanins(), out))
+    # warm the specialised-kernel cache for every distinct program (reported)
+    t0 = time.perf_counter()
+    seen = set()
+    for m in ms:
+        info, _ = L.lec_es_compile(m)
+        if info.hash in seen:
+            continue
+        seen.add(info.hash)
+        p = L.lec_es_prepare(ctx, m)
+        L.lec_es_plan_free(ctx, p)
+    warm_s = time.perf_counter() - t0
+    # one launch per request, sequential
+    t0 = time.perf_counter()
+    alone = [L.lec_es_check(ctx, m).cex for m in ms]
+    one_s = time.perf_counter() - t0
+    # served
+    start = time.perf_counter()
+    tickets = []
+    for r, m in zip(reqs, ms):
+        dt = r.arrival_s - (time.perf_counter() - start)
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(L.lec_es_submit(ctx, m))
+    res = [L.lec_es_wait(ctx, t, 3600.0) for t in tickets]
+    span = time.perf_counter() - start
+    assert [r.cex for r in res] == alone
+    lat = np.array([r.latency_ms for r in res])
+    return {
+        "requests": len(ms), "rate_per_s": args.serve_rate, "distinct_programs": len(seen),
+        "widths": sorted(set(r.w for r in reqs)), "mutants": int(sum(r.mutant for r in reqs)),
+        "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
+        "served_miters_per_s": len(ms) / span, "one_launch_each_miters_per_s": len(ms) / one_s,
+        "offered_span_s": reqs[-1].arrival_s, "jit_warmup_s": warm_s,
+        "results_equal_alone": True,
+    }
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2512_06627_b300 import build as B
+    from paper_2512_06627_b300 import circuits as C
+    from paper_2512_06627_b300 import lec_es as L
+
+    B.build()
+    dev = local
+    torch.cuda.set_device(dev)
+    tier = {"auto": L.TIER_AUTO, "interp": L.TIER_INTERP, "jit": L.TIER_JIT, "spill": L.TIER_SPILL}[args.tier]
+    ctx = L.lec_es_create(dev, arena_bytes=2 << 30, jit_cache_dir=os.path.join(ROOT, ".jit_cache"))
+    aig = C.config3_mult16()
+    m = L.miter_of(aig)
+    opt = L.options(tier=tier)
+    t0 = time.perf_counter()
+    plan = L.lec_es_prepare(ctx, m, opt)
+    prep_s = time.perf_counter() - t0
+    info = L.lec_es_plan_info(plan)
+    n = info.n
+    units = float(info.cone_ands) * float(1 << n)  # node-pattern evaluations per step
+    per_clk, sms, khz, lop3_rate = L.lec_es_lop3_peak(ctx)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")  # > 126 MB L2
+    st = ctx.stream
+    tier_ran = None
+    for _ in range(args.warmup):
+        L.lec_es_run_async(ctx, plan)
+        r = L.lec_es_plan_result(ctx, plan)
+        assert r.verdict == L.EQUIVALENT
+        tier_ran = r.tier
+    barrier(ws)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev)
+    sampler.start()
+    time.sleep(0.3)
+    step_ms, kern_ms = [], []
+    for _ in range(args.steps):
+        with torch.cuda.stream(st):
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        L.lec_es_run_async(ctx, plan)
+        e1.record(st)
+        r = L.lec_es_plan_result(ctx, plan)
+        assert r.verdict == L.EQUIVALENT and r.cex == L.NO_CEX
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(r.device_ms)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    barrier(ws)
+    total_ms = max_over_ranks(sum(step_ms), ws)
+    value = ws * args.steps * units / (total_ms / 1e3)
+
+    # end to end through the public call with host buffers (front end, upload,
+    # kernel, result read-back all inside the timed region)
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        r = L.lec_es_check_ex(ctx, m, opt)
+        assert r.verdict == L.EQUIVALENT
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
+    e2e_value = ws * e2e_steps * units / e2e_s
+
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    lop3_per_launch = units / 32.0  # one 32-bit LOP3 per AND per 32 patterns
+    kern_s = statistics.mean(kern_ms) / 1e3
+    achieved = lop3_per_launch / kern_s
+    peak = sms * per_clk * sm_max * 1e6
+    line = {
+        "metric": "node-pattern evals/s",
+        "value": value,
+        "unit": "node-pattern evals/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic (seeded generated netlists)",
+        "config": {"workload": WORKLOAD, "cone_ands": info.cone_ands, "support_pis": n,
+                   "patterns_per_step": 1 << n, "value_slots": info.num_slots, "tier": int(tier_ran),
+                   "l2": "flushed between steps (256 MB write); program is 40 KB",
+                   "parallelism": "replicas" if ws > 1 else "1 GPU"},
+        "e2e": {"value": e2e_value, "unit": "node-pattern evals/s",
+                "h2d_bytes_per_step": int(info.num_records) * 8 + 32, "d2h_bytes_per_step": 32},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "LOP3/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_basis": f"{sms} SMs x {per_clk:.1f} LOP3/clk/SM (measured) x {sm_max:.0f} MHz max"},
+        "lop3_measured": {"per_clk_per_sm": per_clk, "sm_clock_mhz_during": khz / 1e3, "lop3_per_s": lop3_rate},
+        "kernel_ms_mean": statistics.mean(kern_ms),
+        "prepare_s": prep_s,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_batch:
+        line["batched"] = measure_batch(ctx, args)
+    if rank == 0 and args.serve_requests > 0:
+        line["served"] = measure_serve(ctx, args)
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, cores, sample = cpu_oracle_rate(aig, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": "node-pattern evals/s", "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    L.lec_es_plan_free(ctx, plan)
+    L.lec_es_destroy(ctx)
+    return line
+
+
+def run_reference(args, ws, rank):
+    """The oracle as it stands on the host cores, one bounded sample per step."""
+    from paper_2512_06627_b300 import circuits as C
+    aig = C.config3_mult16()
+    if rank != 0:
+        return None
+    import oracle as O
+    _, cone = O.support(aig.num_pis, aig.fanins, aig.outputs[0])
+    per = max(2.0, min(20.0, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(aig, per / 4)
+    rates, samples = [], []
+    for _ in range(args.steps):
+        r, cores, s = cpu_oracle_rate(aig, per)
+        rates.append(r)
+        samples.append(s)
+    value = statistics.mean(rates)
+    units = cone * float(1 << 32)
+    return {
+        "impl": "reference",
+        "metric": "node-pattern evals/s", "value": value, "unit": "node-pattern evals/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": units / value * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded generated netlists)",
+        "config": {"workload": WORKLOAD, "cone_ands": cone, "support_pis": 32},
+        "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count() or 1, "sample": samples[-1], "value": value,
+                         "unit": "node-pattern evals/s"},
+        "e2e": {"value": value, "unit": "node-pattern evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        line = run_reference(args, ws, rank)
+    else:
+        line = run_ours(args, ws, rank, local)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

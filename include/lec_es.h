@@ -1,0 +1,234 @@
+/*
+ * lec_es.h -- C ABI of the B300 exact-simulation (ES) engine.
+ *
+ * Problem (paper §2.1): given a miter AIG -- two combinational circuits with
+ * corresponding outputs XORed and the XORs ORed into one output -- prove the
+ * output constant 0 (EQUIVALENT) or return an input pattern that sets it
+ * (NONEQUIVALENT).  ES (paper §2.2, "Exact Simulation") decides this by
+ * evaluating the output's cone under every assignment of its primary-input
+ * support.  The cone is compiled into a branch-free instruction stream whose
+ * value registers are reused under reference-count guidance (paper §3.3,
+ * "Instructionalized ES").
+ *
+ * Conventions for every entry point:
+ *   - returns lec_es_status (0 = LEC_ES_OK); nothing aborts, throws or exits;
+ *   - input arrays are caller-owned and only read during the call; the
+ *     library copies what it keeps (submit included);
+ *   - result structs are caller-allocated and written only on LEC_ES_OK;
+ *   - device pointers are marked "device"; everything else is host memory;
+ *   - one lec_es_ctx per host thread, except lec_es_submit / poll / wait /
+ *     cancel, which are thread-safe on one ctx.
+ *
+ * Pattern numbering: the support S of the output is the set of PIs in its
+ * transitive fan-in cone (§2.1) sorted by PI index, n = |S|.  Pattern p gives
+ * bit k of p to PI S[k].  A 64-pattern word w holds patterns 64w..64w+63:
+ * PI S[k] is the constant mask with bit b = bit k of b for k < 6, and all ones
+ * iff bit (k-6) of w is set for k >= 6.  There are max(1, 2^(n-6)) words.
+ * The counterexample reported is the lowest failing p.
+ */
+#ifndef LEC_ES_H
+#define LEC_ES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lec_es_ctx lec_es_ctx;   /* opaque: device state, arena, JIT cache */
+typedef struct lec_es_plan lec_es_plan; /* opaque: one compiled, device-resident miter */
+typedef struct lec_es_batch_plan lec_es_batch_plan; /* opaque: many miters, one launch */
+
+typedef enum {
+  LEC_ES_OK = 0,
+  LEC_ES_EINVAL = 1,        /* malformed graph or argument */
+  LEC_ES_ETOOBIG = 2,       /* n > max_pis (<= 63) or more than 65535 value slots */
+  LEC_ES_ENOMEM = 3,        /* host allocation or device arena exhausted */
+  LEC_ES_ECUDA = 4,         /* a CUDA runtime call failed */
+  LEC_ES_ETIMEOUT = 5,      /* wait deadline passed */
+  LEC_ES_EBUSY = 6,         /* poll: request not finished yet */
+  LEC_ES_ECANCELLED = 7,    /* request was cancelled */
+  LEC_ES_EDEVICE_WAIT = 8,  /* a bounded device-side wait gave up (kernel returned early) */
+  LEC_ES_EJIT = 9,          /* run-time compilation of a specialised kernel failed */
+  LEC_ES_ENOTFOUND = 10     /* unknown ticket */
+} lec_es_status;
+
+typedef enum {
+  LEC_ES_EQUIVALENT = 0,
+  LEC_ES_NONEQUIVALENT = 1,
+  LEC_ES_UNDECIDED = 2      /* only a word sub-range was checked and it passed */
+} lec_es_verdict;
+
+/* Kernel tiers. */
+enum {
+  LEC_ES_TIER_AUTO = 0,
+  LEC_ES_TIER_INTERP = 1,   /* generic interpreter, value slots in shared memory */
+  LEC_ES_TIER_JIT = 2,      /* cone compiled to straight-line register code (NVRTC) */
+  LEC_ES_TIER_SPILL = 3     /* generic interpreter, value slots in global memory */
+};
+
+/* Evaluation orders for the slot compiler (all give identical results). */
+enum {
+  LEC_ES_ORDER_AUTO = 0,    /* the one with the fewest value slots */
+  LEC_ES_ORDER_DFS = 1,     /* post-order from the output, deeper fanin first */
+  LEC_ES_ORDER_VAR = 2,     /* ascending variable index */
+  LEC_ES_ORDER_LEVEL = 3    /* by logic level, then variable */
+};
+
+/* A miter: AIGER numbering.  Variable 0 is FALSE, 1..num_pis are PIs, AND
+ * variable num_pis+1+i has fanins fanins[2i], fanins[2i+1] (literals 2*var +
+ * complement, each fanin variable below the AND's own).  Only the cone of
+ * out_lit is read, so many miters may share one fanins array. */
+typedef struct {
+  uint32_t num_pis;
+  uint32_t num_ands;
+  const uint32_t *fanins;   /* host, 2*num_ands literals */
+  uint32_t out_lit;
+} lec_es_miter;
+
+typedef struct {
+  lec_es_verdict verdict;
+  uint32_t support_n;       /* n */
+  uint64_t cex;             /* lowest failing pattern (UINT64_MAX if none) */
+  uint32_t support[64];     /* S[0..n-1]: original PI indices, 0-based */
+  uint32_t cone_ands;       /* AND nodes in the cone (the evaluation count unit) */
+  uint32_t num_slots;       /* value slots after reference-count reuse */
+  uint32_t tier;            /* LEC_ES_TIER_* that ran */
+  uint32_t order;           /* LEC_ES_ORDER_* used */
+  uint64_t words_checked;   /* 64-pattern words in the requested range */
+  double device_ms;         /* kernel time (CUDA events) */
+  double host_ms;           /* front end: cone, order, slots, upload */
+  double jit_ms;            /* run-time compilation (0 if cached) */
+  double latency_ms;        /* served requests: completion minus submission */
+} lec_es_result;
+
+typedef struct {
+  uint64_t word_begin;      /* first 64-pattern word checked (default 0) */
+  uint64_t word_end;        /* one past the last; UINT64_MAX = all words */
+  uint32_t tier;            /* LEC_ES_TIER_* (default AUTO) */
+  uint32_t order;           /* LEC_ES_ORDER_* (default AUTO) */
+  uint32_t block_threads;   /* 0 = library choice */
+  uint32_t grid_blocks;     /* 0 = library choice */
+} lec_es_options;
+
+typedef struct {
+  int device;               /* CUDA device ordinal */
+  void *arena;              /* device memory the ctx sub-allocates from, e.g. a
+                               torch tensor; NULL = the ctx allocates
+                               arena_bytes itself with cudaMalloc */
+  size_t arena_bytes;
+  void *stream;             /* cudaStream_t for all work; NULL = ctx creates one */
+  uint32_t max_pis;         /* <= 63; default 63 when 0 */
+  double timeout_s;         /* bound on any host wait; 0 = 600 s */
+  const char *jit_cache_dir;/* directory for compiled JIT kernels; NULL = memory only */
+} lec_es_config;
+
+/* Host-only view of a compiled slot program (no GPU needed).  Records are
+ * 8 bytes: {u16 dst, u16 a, u16 b, u8 op, u8 pad}; op 0..3 = AND of slots a
+ * and b, operand a complemented if op&1, b if op&2; op 4 = load support PI a;
+ * op 5 = load constant 0.  Caller provides records[cap]. */
+typedef struct {
+  uint32_t n;
+  uint32_t support[64];
+  uint32_t cone_ands;
+  uint32_t num_slots;
+  uint32_t out_slot;
+  uint32_t out_compl;
+  uint32_t order;
+  uint64_t num_records;     /* written even when cap is too small */
+  uint64_t hash;            /* structural hash of the program */
+} lec_es_program_info;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Creates a context on cfg->device.  Errors: EINVAL (NULL args, max_pis >
+ * 63), ECUDA (device not usable), ENOMEM. */
+int lec_es_create(lec_es_ctx **out, const lec_es_config *cfg);
+/* Frees everything the ctx owns (not a caller-provided arena or stream).
+ * Outstanding submitted requests are cancelled first. */
+void lec_es_destroy(lec_es_ctx *c);
+const char *lec_es_strerror(int status);
+
+/* ---- front end (host only) ------------------------------------------- */
+
+/* Cone extraction, support, evaluation order and reference-count slot
+ * assignment (§3.3) without touching a GPU.  Writes min(cap, needed)
+ * records; info->num_records is the needed count.  Errors: EINVAL
+ * (malformed cone), ETOOBIG (n > 63 or > 65535 slots). */
+int lec_es_compile(const lec_es_miter *m, uint32_t order, lec_es_program_info *info,
+                   uint64_t *records, uint64_t cap);
+
+/* ---- single miter ----------------------------------------------------- */
+
+/* Full ES of one miter, synchronous on the ctx stream.  Equivalent to
+ * prepare + run + plan_free with default options. */
+int lec_es_check(lec_es_ctx *c, const lec_es_miter *m, lec_es_result *out);
+/* As lec_es_check over a word sub-range and with explicit options; a
+ * passing proper sub-range gives LEC_ES_UNDECIDED. */
+int lec_es_check_ex(lec_es_ctx *c, const lec_es_miter *m, const lec_es_options *opt,
+                    lec_es_result *out);
+
+/* Compile a miter and keep its program resident on the device (the host
+ * copy of m may be freed afterwards).  opt may be NULL. */
+int lec_es_prepare(lec_es_ctx *c, const lec_es_miter *m, const lec_es_options *opt,
+                   lec_es_plan **out);
+/* Enqueue one ES pass of a prepared plan on the ctx stream and return at
+ * once (result reset, kernel, 8-byte result copy).  opt may be NULL. */
+int lec_es_run_async(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt);
+/* Wait for the last run of the plan and fill *out. */
+int lec_es_plan_result(lec_es_ctx *c, lec_es_plan *p, lec_es_result *out);
+/* Program description of a prepared plan (host memory only). */
+int lec_es_plan_info(const lec_es_plan *p, lec_es_program_info *info);
+void lec_es_plan_free(lec_es_ctx *c, lec_es_plan *p);
+
+/* Per-node values for small cones: row j of host_out (words_per_row words)
+ * holds the value of the j-th cone AND in ascending variable order, over words
+ * [word_begin, word_end); vars_out[j] (host, cone_ands entries) receives that
+ * variable.  Uses the interpreter kernel with an extra store per AND.
+ * Errors: EINVAL if the range is empty or outside the cone's words. */
+int lec_es_truth_tables(lec_es_ctx *c, const lec_es_miter *m, uint64_t word_begin,
+                        uint64_t word_end, uint32_t *vars_out, uint64_t *host_out);
+
+/* ---- batch: many miters, one persistent launch ------------------------- */
+
+/* ES of k miters in one persistent launch over a queue of (miter, word
+ * range) tiles; out[i] is identical to lec_es_check on m[i]. */
+int lec_es_batch(lec_es_ctx *c, const lec_es_miter *m, size_t k, lec_es_result *out);
+/* Prepared form: compile and upload k miters once, then run repeatedly
+ * (the launch sequence is captured in a CUDA graph and replayed). */
+int lec_es_batch_prepare(lec_es_ctx *c, const lec_es_miter *m, size_t k,
+                         const lec_es_options *opt, lec_es_batch_plan **out);
+int lec_es_batch_run_async(lec_es_ctx *c, lec_es_batch_plan *b);
+int lec_es_batch_results(lec_es_ctx *c, lec_es_batch_plan *b, lec_es_result *out, size_t k);
+void lec_es_batch_free(lec_es_ctx *c, lec_es_batch_plan *b);
+
+/* ---- serving: asynchronous requests, continuous batching ----------------- */
+
+/* Admit a request; returns a ticket at once.  The miter is copied.
+ * Errors: EINVAL, ETOOBIG, ENOMEM (queue full). */
+int lec_es_submit(lec_es_ctx *c, const lec_es_miter *m, uint64_t *ticket);
+/* EBUSY while the request runs; OK and *out once done (the ticket is then
+ * released); ECANCELLED if cancelled; ENOTFOUND for an unknown ticket. */
+int lec_es_poll(lec_es_ctx *c, uint64_t ticket, lec_es_result *out);
+/* Blocks until done or timeout_s passes (ETIMEOUT). */
+int lec_es_wait(lec_es_ctx *c, uint64_t ticket, double timeout_s, lec_es_result *out);
+/* Cancels a queued or running request (a running one stops at its next tile). */
+int lec_es_cancel(lec_es_ctx *c, uint64_t ticket);
+/* Serving limits: bytes of device memory the admitted requests may hold
+ * (value slots x resident words x 8 B, plus programs) and the number of
+ * requests in flight.  Call before the first submit. */
+int lec_es_server_config(lec_es_ctx *c, size_t slot_budget_bytes, uint32_t max_inflight);
+
+/* ---- device facts ----------------------------------------------------- */
+
+/* Measured 32-bit LOP3 throughput: results per clock per SM, from a
+ * dependent-chain-free microbenchmark timed with CUDA events; also SM count
+ * and the SM clock (kHz) read during the run. */
+int lec_es_lop3_peak(lec_es_ctx *c, double *lop3_per_clk_per_sm, int *sm_count,
+                     int *clock_khz, double *lop3_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LEC_ES_H */

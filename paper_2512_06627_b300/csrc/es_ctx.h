@@ -1,0 +1,120 @@
+// es_ctx.h -- definitions of the opaque C-ABI handles and the internal
+// interfaces between the C ABI, the JIT tier, the batch engine and the server.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+
+#include "../../include/lec_es.h"
+#include "es_internal.h"
+
+namespace lec {
+
+// First-fit sub-allocator over one device allocation (256-byte blocks).
+struct Arena {
+  uint8_t *base = nullptr;
+  size_t bytes = 0;
+  size_t in_use = 0;
+  std::mutex mu;
+  std::map<size_t, size_t> free_list;  // offset -> size
+  std::map<size_t, size_t> used;
+  int init(void *base, size_t bytes);
+  void *alloc(size_t n);
+  void free(void *p);
+};
+
+struct PlanGeom {
+  int block = 0;
+  int grid = 0;
+  size_t smem = 0;
+  uint32_t ring_recs = 0;
+  uint32_t resident = 0;
+  uint32_t nrec_padded = 0;
+  bool spill = false;
+};
+
+struct JitKernel {
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t kern = nullptr;
+  int regs = 0;
+  size_t local_bytes = 0;
+  int block = 128;
+  int blocks_per_sm = 1;
+  double compile_ms = 0;
+};
+struct JitState;
+struct Server;
+
+double now_ms();
+int wait_event(cudaEvent_t ev, double timeout_s);
+int choose_interp_geometry(lec_es_ctx *c, const Program &prog, uint64_t chunks, const lec_es_options *opt,
+                           PlanGeom &g);
+
+// JIT tier (jit.cpp)
+uint32_t jit_auto_tier(lec_es_ctx *c, const Program &g, uint64_t chunks);
+int jit_prepare(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt);
+int jit_launch(lec_es_ctx *c, lec_es_plan *p, uint64_t chunk_begin, uint64_t chunk_end, int grid);
+// Non-blocking lookup for the server: the compiled kernel if ready, else
+// schedules a background compile (once per program) and returns nullptr.
+lec::JitKernel *jit_lookup_or_schedule(lec_es_ctx *c, const Program &g);
+int jit_attach(lec_es_ctx *c, lec_es_plan *p, JitKernel *k, const lec_es_options *opt);
+void jit_release_all(lec_es_ctx *c);
+
+// single-miter plans (api.cpp)
+int plan_prepare(lec_es_ctx *c, const lec_es_miter *m, const lec_es_options *opt, lec_es_plan **out);
+int plan_prepare_program(lec_es_ctx *c, Program &&prog, const lec_es_options *opt, lec_es_plan **out);
+int plan_run_async(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt);
+int plan_run_async_grid(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt, int grid_override);
+int plan_finish_device(lec_es_ctx *c, lec_es_plan *p);
+int plan_result(lec_es_ctx *c, lec_es_plan *p, lec_es_result *out);
+void plan_release(lec_es_ctx *c, lec_es_plan *p);
+void fill_result(const lec_es_plan *p, lec_es_result *out);
+
+// server (server.cpp)
+void server_shutdown(lec_es_ctx *c);
+
+}  // namespace lec
+
+struct lec_es_ctx {
+  int device = 0;
+  int sm_count = 0;
+  int smem_optin = 0;
+  int cc_major = 0, cc_minor = 0;
+  uint32_t max_pis = 63;
+  double timeout_s = 600.0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void *arena_base = nullptr;
+  bool own_arena = false;
+  lec::Arena arena;
+  unsigned long long *h_init = nullptr;  // pinned {~0, 0, 0, ~0}
+  std::string jit_dir;
+  lec::JitState *jit = nullptr;
+  lec::Server *server = nullptr;
+  std::mutex server_mu;
+  size_t slot_budget = (size_t)32 << 30;
+  uint32_t max_inflight = 64;
+};
+
+struct lec_es_plan {
+  lec::Program prog;
+  lec::PlanGeom geom;
+  uint32_t tier = 0;
+  void *d_recs = nullptr;
+  void *d_spill = nullptr;
+  size_t spill_bytes = 0;
+  unsigned long long *d_res = nullptr;  // [cex, evaluated, status, spare]
+  unsigned long long *h_res = nullptr;  // pinned copy
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  bool pending = false;
+  uint64_t last_wb = 0, last_we = 0;
+  double host_ms = 0, jit_ms = 0;
+  lec::JitKernel *jit = nullptr;
+  int jit_block = 0, jit_grid = 0;
+  cudaStream_t stream = nullptr;         // where runs are enqueued (ctx stream by default)
+};

@@ -1,0 +1,129 @@
+// es_internal.h -- types shared by the front end, the kernels and the C ABI.
+#pragma once
+
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace lec {
+
+// One instruction of the slot program (8 bytes, 16-byte aligned pairs for TMA).
+//   op 0..3 : slot[dst] = (slot[a] ^ (op&1 ? ~0 : 0)) & (slot[b] ^ (op&2 ? ~0 : 0))
+//   op 4    : slot[dst] = value of support PI a for the current patterns
+//   op 5    : slot[dst] = 0
+struct Rec {
+  uint16_t dst, a, b;
+  uint8_t op, pad;
+};
+static_assert(sizeof(Rec) == 8, "record is 8 bytes");
+
+enum : uint8_t { OP_AND = 0, OP_PI = 4, OP_CONST0 = 5 };
+
+// Compiled cone (paper §3.3 "Instructionalized ES"): branch-free instruction
+// stream over value slots reused by reference count.
+struct Program {
+  uint32_t n = 0;                   // support size
+  std::vector<uint32_t> support;    // original PI indices (0-based), ascending
+  std::vector<uint32_t> order_vars; // cone AND variables in evaluation order
+  std::vector<Rec> recs;
+  uint32_t num_slots = 0;
+  uint32_t out_slot = 0;
+  uint32_t out_compl = 0;
+  uint32_t cone_ands = 0;
+  uint32_t order = 0;
+  uint64_t hash = 0;
+};
+
+struct MiterView {
+  uint32_t num_pis, num_ands;
+  const uint32_t *fanins;
+  uint32_t out_lit;
+};
+
+// Front end.  Returns an lec_es_status code.
+int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Program &out);
+
+// Words of 64 patterns for a support of n PIs.
+inline uint64_t num_words(uint32_t n) { return n <= 6 ? 1ull : (1ull << (n - 6)); }
+// 32-pattern chunks (the kernels' unit: one 32-bit lane per thread).
+inline uint64_t num_chunks(uint32_t n) { return n <= 5 ? 1ull : (1ull << (n - 5)); }
+
+// ---- kernel parameter blocks (passed by value) --------------------------------
+
+struct InterpParams {
+  const Rec *recs;          // device, padded to an even count, 16-byte aligned
+  uint32_t nrec;            // records to execute
+  uint32_t nrec_padded;     // even
+  uint32_t nslots;
+  uint32_t out_slot;
+  uint32_t out_compl;
+  uint32_t n;               // support size
+  uint32_t ring_recs;       // records per staging stage (multiple of 2)
+  uint32_t resident;        // 1: whole program staged once
+  uint64_t chunk_begin;     // 32-pattern chunks [begin, end)
+  uint64_t chunk_end;
+  unsigned long long *cex;  // device, initialised to ~0
+  unsigned long long *evaluated; // device: patterns evaluated
+  uint32_t *status;         // device error word (0 = ok)
+  uint32_t *spill;          // global value slots for the spill tier
+  uint64_t *tt_out;         // truth-table dump: [cone AND][word] (optional)
+  const uint32_t *tt_row;   // record index -> dump row (or 0xffffffff)
+  uint64_t tt_words;        // words per dump row
+  uint64_t tt_word_begin;
+};
+
+// Batched tiles: miter table + tile queue.
+struct BatchMiter {
+  uint32_t rec_off;         // into the shared record arena (records)
+  uint32_t nrec;
+  uint32_t nrec_padded;
+  uint32_t nslots;
+  uint32_t out_slot;
+  uint32_t out_compl;
+  uint32_t n;
+  uint32_t pad;
+};
+
+struct BatchTile {
+  uint32_t miter;
+  uint32_t pad;
+  uint64_t chunk_begin;
+  uint64_t chunk_end;
+};
+
+struct BatchParams {
+  const Rec *recs;
+  const BatchMiter *miters;
+  const BatchTile *tiles;
+  uint32_t num_tiles;
+  uint32_t max_slots;       // smem is sized for this
+  uint32_t ring_recs;
+  uint32_t pad;
+  unsigned long long *cex;  // per miter
+  unsigned int *head;       // tile queue head (scratch, zeroed before launch)
+  uint32_t *status;
+  const volatile uint32_t *cancel; // per miter cancel flags (optional)
+};
+
+// Status bits written by kernels.
+enum : uint32_t {
+  DEV_OK = 0,
+  DEV_WAIT_TIMEOUT = 1u,    // an mbarrier wait exceeded its iteration bound
+  DEV_BAD_PROGRAM = 2u,     // slot index out of range (host bug guard)
+};
+
+// Kernel launchers (kernels.cu).  Return cudaError_t as int.
+int launch_interp(const InterpParams &p, int block, int grid, size_t smem, bool spill, void *stream);
+int interp_smem_bytes(uint32_t nslots, uint32_t nrec_padded, int block, uint32_t *ring_recs,
+                      uint32_t *resident, size_t *bytes);
+int configure_batch(int block, size_t smem);
+int batch_blocks_per_sm(int block, size_t smem);
+int launch_batch(const BatchParams &p, int block, int grid, size_t smem, void *stream);
+size_t batch_smem_bytes(uint32_t max_slots, int block, uint32_t ring_recs);
+int launch_lop3_bench(uint32_t *out, unsigned long long *cycles, int grid, int block, int iters,
+                      void *stream);
+int max_smem_optin(int device);
+int set_kernel_smem_limits(size_t bytes);
+
+}  // namespace lec

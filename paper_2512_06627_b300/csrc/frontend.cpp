@@ -1,0 +1,287 @@
+// frontend.cpp -- host front end of the ES engine.
+//
+// Steps (paper §2.1 and §3.3):
+//   cone     transitive fan-in of the miter output; support = PIs reached,
+//            sorted by PI index (support PI k <-> pattern bit k);
+//   order    a topological order of the cone's ANDs (DFS post-order with the
+//            deeper fanin first, ascending variable, or by level);
+//   slots    "registers aggressively reused under reference-count guidance":
+//            every value's reference count is its number of fanout edges in
+//            the cone (+1 for the output); walking the order, each AND reads
+//            its operands, drops their counts, frees operands that reach zero
+//            (lowest free slot first), then takes a slot for its result, which
+//            may be an operand's just-freed slot.  PIs and the constant are
+//            loaded lazily into a slot right before their first reader.
+// The peak slot count is the live-set size the kernels must hold per lane.
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <functional>
+#include <queue>
+#include <vector>
+
+#include "../../include/lec_es.h"
+#include "es_internal.h"
+
+namespace lec {
+
+namespace {
+
+struct Cone {
+  std::vector<uint32_t> ands;   // cone AND vars, ascending
+  std::vector<uint32_t> pis;    // support PI vars (1-based), ascending
+  bool uses_const = false;
+};
+
+inline const uint32_t *fanin_of(const MiterView &m, uint32_t v) {
+  return m.fanins + 2ull * (v - m.num_pis - 1);
+}
+
+int extract_cone(const MiterView &m, std::vector<uint8_t> &mark, Cone &c) {
+  const uint64_t maxvar = (uint64_t)m.num_pis + m.num_ands;
+  const uint32_t root = m.out_lit >> 1;
+  if (root > maxvar) return LEC_ES_EINVAL;
+  if (m.num_ands && !m.fanins) return LEC_ES_EINVAL;
+  // sparse marking: only visited variables are touched, so many miters can
+  // share one large graph
+  std::vector<uint32_t> stack{root};
+  std::vector<uint32_t> visited;
+  mark.resize(maxvar + 1, 0);
+  int rc = LEC_ES_OK;
+  while (!stack.empty()) {
+    uint32_t v = stack.back();
+    stack.pop_back();
+    if (mark[v]) continue;
+    mark[v] = 1;
+    visited.push_back(v);
+    if (v == 0) {
+      c.uses_const = true;
+    } else if (v <= m.num_pis) {
+      c.pis.push_back(v);
+    } else {
+      c.ands.push_back(v);
+      const uint32_t *f = fanin_of(m, v);
+      for (int e = 0; e < 2; e++) {
+        uint32_t u = f[e] >> 1;
+        if (u >= v) { rc = LEC_ES_EINVAL; break; }
+        if (!mark[u]) stack.push_back(u);
+      }
+      if (rc) break;
+    }
+  }
+  for (uint32_t v : visited) mark[v] = 0;
+  if (rc) return rc;
+  std::sort(c.ands.begin(), c.ands.end());
+  std::sort(c.pis.begin(), c.pis.end());
+  return LEC_ES_OK;
+}
+
+// Dense index of a cone variable: position in ands (ANDs) via binary search.
+struct ConeIndex {
+  const Cone &c;
+  explicit ConeIndex(const Cone &cc) : c(cc) {}
+  int64_t and_pos(uint32_t v) const {
+    auto it = std::lower_bound(c.ands.begin(), c.ands.end(), v);
+    if (it == c.ands.end() || *it != v) return -1;
+    return it - c.ands.begin();
+  }
+};
+
+void order_levels(const MiterView &m, const Cone &c, const ConeIndex &ix, std::vector<uint32_t> &level) {
+  level.assign(c.ands.size(), 0);
+  for (size_t i = 0; i < c.ands.size(); i++) {
+    const uint32_t *f = fanin_of(m, c.ands[i]);
+    uint32_t l = 0;
+    for (int e = 0; e < 2; e++) {
+      int64_t p = ix.and_pos(f[e] >> 1);
+      if (p >= 0) l = std::max(l, level[p] + 1);
+    }
+    level[i] = l;
+  }
+}
+
+// Evaluation orders; each returns positions into c.ands.
+void order_var(const Cone &c, std::vector<uint32_t> &ord) {
+  ord.resize(c.ands.size());
+  for (size_t i = 0; i < ord.size(); i++) ord[i] = (uint32_t)i;
+}
+
+void order_level(const std::vector<uint32_t> &level, std::vector<uint32_t> &ord) {
+  ord.resize(level.size());
+  for (size_t i = 0; i < ord.size(); i++) ord[i] = (uint32_t)i;
+  std::stable_sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) { return level[x] < level[y]; });
+}
+
+void order_dfs(const MiterView &m, const Cone &c, const ConeIndex &ix, const std::vector<uint32_t> &level,
+               uint32_t root_var, std::vector<uint32_t> &ord) {
+  ord.clear();
+  ord.reserve(c.ands.size());
+  std::vector<uint8_t> state(c.ands.size(), 0);  // 0 new, 1 open, 2 done
+  int64_t rp = ix.and_pos(root_var);
+  if (rp < 0) return;
+  std::vector<std::pair<uint32_t, uint8_t>> stack;
+  stack.push_back({(uint32_t)rp, 0});
+  while (!stack.empty()) {
+    auto &top = stack.back();
+    uint32_t i = top.first;
+    if (top.second == 0) {
+      if (state[i]) { stack.pop_back(); continue; }
+      state[i] = 1;
+      top.second = 1;
+      const uint32_t *f = fanin_of(m, c.ands[i]);
+      int64_t p0 = ix.and_pos(f[0] >> 1), p1 = ix.and_pos(f[1] >> 1);
+      // push so that the deeper fanin is visited (and finished) first
+      int64_t first = p0, second = p1;
+      uint32_t l0 = p0 >= 0 ? level[p0] + 1 : 0, l1 = p1 >= 0 ? level[p1] + 1 : 0;
+      if (l1 > l0) std::swap(first, second);
+      if (second >= 0 && !state[second]) stack.push_back({(uint32_t)second, 0});
+      if (first >= 0 && !state[first]) stack.push_back({(uint32_t)first, 0});
+    } else {
+      stack.pop_back();
+      if (state[i] == 1) {
+        state[i] = 2;
+        ord.push_back(i);
+      }
+    }
+  }
+}
+
+// Reference-count slot assignment over a given order.
+int assign_slots(const MiterView &m, const Cone &c, const ConeIndex &ix, const std::vector<uint32_t> &ord,
+                 uint32_t root_var, Program &p) {
+  const size_t NA = c.ands.size(), NP = c.pis.size();
+  // value ids: [0, NA) ANDs, [NA, NA+NP) PIs, NA+NP the constant
+  const size_t NV = NA + NP + 1;
+  auto vid = [&](uint32_t var) -> int64_t {
+    if (var == 0) return (int64_t)(NA + NP);
+    if (var <= m.num_pis) {
+      auto it = std::lower_bound(c.pis.begin(), c.pis.end(), var);
+      return (int64_t)(NA + (it - c.pis.begin()));
+    }
+    return ix.and_pos(var);
+  };
+  std::vector<uint32_t> refs(NV, 0);
+  std::vector<int64_t> f0v(NA), f1v(NA);
+  for (size_t i = 0; i < NA; i++) {
+    const uint32_t *f = fanin_of(m, c.ands[i]);
+    f0v[i] = vid(f[0] >> 1);
+    f1v[i] = vid(f[1] >> 1);
+    refs[f0v[i]]++;
+    refs[f1v[i]]++;
+  }
+  int64_t root = vid(root_var);
+  refs[root]++;
+  std::vector<int32_t> slot(NV, -1);
+  std::priority_queue<uint32_t, std::vector<uint32_t>, std::greater<uint32_t>> freel;
+  uint32_t high = 0;
+  auto alloc = [&]() -> uint32_t {
+    if (!freel.empty()) {
+      uint32_t s = freel.top();
+      freel.pop();
+      return s;
+    }
+    return high++;
+  };
+  auto load = [&](int64_t v) {
+    if (slot[v] >= 0) return;
+    uint32_t s = alloc();
+    slot[v] = (int32_t)s;
+    Rec r{};
+    r.dst = (uint16_t)s;
+    if (v == (int64_t)(NA + NP)) {
+      r.op = OP_CONST0;
+    } else {
+      r.op = OP_PI;
+      r.a = (uint16_t)(v - NA);   // support index k
+    }
+    p.recs.push_back(r);
+  };
+  p.recs.clear();
+  p.order_vars.clear();
+  for (uint32_t i : ord) {
+    int64_t a = f0v[i], b = f1v[i];
+    if (a >= (int64_t)NA) load(a);
+    if (b >= (int64_t)NA) load(b);
+    if (slot[a] < 0 || slot[b] < 0) return LEC_ES_EINVAL;  // order not topological
+    Rec r{};
+    r.a = (uint16_t)slot[a];
+    r.b = (uint16_t)slot[b];
+    const uint32_t *f = fanin_of(m, c.ands[i]);
+    r.op = (uint8_t)(OP_AND | (f[0] & 1) | ((f[1] & 1) << 1));
+    // when a == b both edges count, so the count reaches zero at most once
+    if (--refs[a] == 0) freel.push((uint32_t)slot[a]);
+    if (--refs[b] == 0) freel.push((uint32_t)slot[b]);
+    uint32_t d = alloc();
+    r.dst = (uint16_t)d;
+    slot[i] = (int32_t)d;
+    p.recs.push_back(r);
+    p.order_vars.push_back(c.ands[i]);
+    if (high > 65535) return LEC_ES_ETOOBIG;
+  }
+  if (root >= (int64_t)NA) load(root);  // output is a PI or the constant
+  p.num_slots = high;
+  p.out_slot = (uint32_t)slot[root];
+  return LEC_ES_OK;
+}
+
+uint64_t fnv1a(const void *data, size_t len, uint64_t h) {
+  const uint8_t *b = (const uint8_t *)data;
+  for (size_t i = 0; i < len; i++) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+}  // namespace
+
+int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Program &out) {
+  thread_local std::vector<uint8_t> mark;
+  Cone c;
+  int rc = extract_cone(m, mark, c);
+  if (rc) return rc;
+  if (c.pis.size() > max_pis || c.pis.size() > 63) return LEC_ES_ETOOBIG;
+  ConeIndex ix(c);
+  const uint32_t root_var = m.out_lit >> 1;
+  std::vector<uint32_t> level;
+  order_levels(m, c, ix, level);
+
+  const uint32_t cands_auto[3] = {LEC_ES_ORDER_DFS, LEC_ES_ORDER_VAR, LEC_ES_ORDER_LEVEL};
+  std::vector<uint32_t> tried;
+  if (order == LEC_ES_ORDER_AUTO) tried.assign(cands_auto, cands_auto + 3);
+  else if (order <= LEC_ES_ORDER_LEVEL) tried.push_back(order);
+  else return LEC_ES_EINVAL;
+
+  bool have = false;
+  Program best;
+  for (uint32_t o : tried) {
+    std::vector<uint32_t> ord;
+    if (o == LEC_ES_ORDER_DFS) order_dfs(m, c, ix, level, root_var, ord);
+    else if (o == LEC_ES_ORDER_VAR) order_var(c, ord);
+    else order_level(level, ord);
+    if (ord.size() != c.ands.size()) return LEC_ES_EINVAL;
+    Program p;
+    rc = assign_slots(m, c, ix, ord, root_var, p);
+    if (rc) return rc;
+    p.order = o;
+    if (!have || p.num_slots < best.num_slots) {
+      best = std::move(p);
+      have = true;
+    }
+  }
+  best.n = (uint32_t)c.pis.size();
+  best.support.resize(c.pis.size());
+  for (size_t k = 0; k < c.pis.size(); k++) best.support[k] = c.pis[k] - 1;
+  best.cone_ands = (uint32_t)c.ands.size();
+  best.out_compl = m.out_lit & 1;
+  if (best.num_slots == 0) best.num_slots = 1;
+  uint64_t h = 1469598103934665603ull;
+  h = fnv1a(best.recs.data(), best.recs.size() * sizeof(Rec), h);
+  uint32_t tail[3] = {best.n, best.out_slot, best.out_compl};
+  best.hash = fnv1a(tail, sizeof(tail), h);
+  out = std::move(best);
+  return LEC_ES_OK;
+}
+
+}  // namespace lec

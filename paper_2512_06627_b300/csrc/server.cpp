@@ -1,0 +1,479 @@
+// server.cpp -- served exact simulation: continuous batching of ES requests.
+//
+// A request is one miter.  lec_es_submit runs the host front end in the
+// caller's thread (cone, support, order, reference-count slots), keeps only
+// the compiled program and returns a ticket.  A dispatcher thread
+//   * admits queued requests in arrival order while the requests on the GPU
+//     hold less than the slot budget (value slots x resident 64-pattern words
+//     x 8 bytes: the live set a request keeps per word in flight) and fewer
+//     than max_inflight run;
+//   * launches each admitted request on one of several CUDA streams, so work
+//     of requests that arrive while others run overlaps on the device; small
+//     requests go to high-priority streams and every grid is sized so blocks
+//     retire after a few passes, letting the block scheduler interleave them;
+//   * keeps programs resident: interpreter records are uploaded once per
+//     distinct program, and specialised (JIT) kernels are compiled in the
+//     background on first sight and used once ready (the interpreter runs a
+//     program until then);
+//   * retires requests whose completion event has fired, releasing their
+//     budget.  Counterexamples end a request early through the same minimum
+//     that drives early exit; cancellation writes 0 into that word, which
+//     stops the kernel at its next pass.
+// Results are identical to lec_es_check: the same kernels over the same
+// pattern space, with the exact lowest-counterexample rule.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/lec_es.h"
+#include "es_ctx.h"
+#include "es_internal.h"
+
+namespace lec {
+
+namespace {
+
+constexpr int kStreams = 8;                    // half high priority, half low
+constexpr uint64_t kSmallWork = 1ull << 33;    // record x chunk products below this are "small"
+
+struct Slot {
+  unsigned long long *d_res = nullptr;  // [cex, evaluated, status, spare]
+  unsigned long long *h_res = nullptr;  // pinned
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  bool busy = false;
+};
+
+struct Resident {  // device copy of one program's records
+  void *d_recs = nullptr;
+  PlanGeom geom;
+};
+
+struct Request {
+  enum State { QUEUED, RUNNING, DONE, CANCELLED, FAILED };
+  uint64_t ticket = 0;
+  Program prog;
+  State state = QUEUED;
+  int slot = -1;
+  int stream = -1;
+  size_t reserve = 0;
+  double t_submit = 0, t_done = 0;
+  bool cancel = false, cancel_sent = false;
+  int err = 0;
+  uint32_t tier = 0;
+  lec_es_result res{};
+};
+
+}  // namespace
+
+struct Server {
+  lec_es_ctx *c = nullptr;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<uint64_t> queue;
+  std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
+  std::vector<uint64_t> running;
+  std::vector<Slot> slots;
+  std::vector<cudaStream_t> streams;
+  std::vector<int> stream_load;
+  cudaStream_t ctl = nullptr;
+  unsigned long long *h_zero = nullptr;
+  std::unordered_map<uint64_t, Resident> resident;
+  size_t used = 0;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  std::thread th;
+};
+
+namespace {
+
+size_t reserve_bytes(lec_es_ctx *c, const Program &g) {
+  const uint64_t words = num_words(g.n);
+  const uint64_t in_flight_words = (uint64_t)c->sm_count * 2048 / 2;  // 2048 lanes per SM, 2 lanes a word
+  const uint64_t rw = std::min(words, in_flight_words);
+  return (size_t)g.num_slots * rw * 8 + g.recs.size() * sizeof(Rec);
+}
+
+void finish(Server *s, Request *r, Request::State st) {
+  r->state = st;
+  r->t_done = now_ms();
+  s->cv_done.notify_all();
+}
+
+// Launch one admitted request.  Called with s->mu held.
+int launch(Server *s, Request *r) {
+  lec_es_ctx *c = s->c;
+  const Program &g = r->prog;
+  const uint64_t C = num_chunks(g.n);
+  const uint64_t work = (uint64_t)g.recs.size() * C;
+  // stream: least loaded within the request's priority class
+  const int half = kStreams / 2;
+  const int lo = work < kSmallWork ? 0 : half;
+  int best = lo;
+  for (int i = lo; i < lo + half; i++)
+    if (s->stream_load[i] < s->stream_load[best]) best = i;
+  cudaStream_t st = s->streams[best];
+  // result slot
+  int si = -1;
+  for (size_t i = 0; i < s->slots.size(); i++)
+    if (!s->slots[i].busy) {
+      si = (int)i;
+      break;
+    }
+  if (si < 0) return LEC_ES_EBUSY;
+  Slot &sl = s->slots[si];
+
+  JitKernel *k = nullptr;
+  if (jit_auto_tier(c, g, C) == LEC_ES_TIER_JIT) k = jit_lookup_or_schedule(c, g);
+  Resident *res = nullptr;
+  if (!k) {
+    auto it = s->resident.find(g.hash);
+    if (it == s->resident.end()) {
+      Resident rr;
+      if (choose_interp_geometry(c, g, C, nullptr, rr.geom)) return LEC_ES_EINVAL;
+      if (rr.geom.spill) return LEC_ES_ETOOBIG;  // served requests keep slots on chip
+      const size_t rb = (size_t)rr.geom.nrec_padded * sizeof(Rec);
+      rr.d_recs = c->arena.alloc(rb);
+      if (!rr.d_recs) return LEC_ES_ENOMEM;
+      std::vector<Rec> padded(rr.geom.nrec_padded);
+      memcpy(padded.data(), g.recs.data(), g.recs.size() * sizeof(Rec));
+      if (cudaMemcpyAsync(rr.d_recs, padded.data(), rb, cudaMemcpyHostToDevice, s->ctl) != cudaSuccess ||
+          cudaStreamSynchronize(s->ctl) != cudaSuccess) {
+        c->arena.free(rr.d_recs);
+        return LEC_ES_ECUDA;
+      }
+      it = s->resident.emplace(g.hash, rr).first;
+    }
+    res = &it->second;
+  }
+  if (cudaMemcpyAsync(sl.d_res, c->h_init, 32, cudaMemcpyHostToDevice, st) != cudaSuccess) return LEC_ES_ECUDA;
+  cudaEventRecord(sl.e0, st);
+  int err;
+  if (k) {
+    // a few chunks per thread, so blocks retire and other requests interleave
+    uint64_t cb = 0, ce = C;
+    unsigned long long *cex = sl.d_res, *ev = sl.d_res + 1;
+    void *args[] = {&cb, &ce, &cex, &ev};
+    const uint64_t per_block = (uint64_t)k->block * 8;
+    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>((C + per_block - 1) / per_block, 1u << 30));
+    err = cudaLaunchKernel((const void *)k->kern, dim3((unsigned)grid), dim3(k->block), args, 0, st) ==
+                  cudaSuccess
+              ? 0
+              : 1;
+    r->tier = LEC_ES_TIER_JIT;
+  } else {
+    InterpParams ip{};
+    ip.recs = (const Rec *)res->d_recs;
+    ip.nrec = (uint32_t)g.recs.size();
+    ip.nrec_padded = res->geom.nrec_padded;
+    ip.nslots = g.num_slots;
+    ip.out_slot = g.out_slot;
+    ip.out_compl = g.out_compl;
+    ip.n = g.n;
+    ip.ring_recs = res->geom.ring_recs;
+    ip.resident = res->geom.resident;
+    ip.chunk_begin = 0;
+    ip.chunk_end = C;
+    ip.cex = sl.d_res;
+    ip.evaluated = sl.d_res + 1;
+    ip.status = (uint32_t *)(sl.d_res + 2);
+    const uint64_t passes = (C + res->geom.block - 1) / res->geom.block;
+    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>((passes + 3) / 4, 1u << 30));
+    err = launch_interp(ip, res->geom.block, (int)grid, res->geom.smem, false, st);
+    r->tier = LEC_ES_TIER_INTERP;
+  }
+  if (err) return LEC_ES_ECUDA;
+  cudaEventRecord(sl.e1, st);
+  cudaMemcpyAsync(sl.h_res, sl.d_res, 32, cudaMemcpyDeviceToHost, st);
+  cudaEventRecord(sl.e2, st);
+  sl.busy = true;
+  r->slot = si;
+  r->stream = best;
+  s->stream_load[best]++;
+  return LEC_ES_OK;
+}
+
+void retire(Server *s, Request *r) {
+  Slot &sl = s->slots[r->slot];
+  const Program &g = r->prog;
+  lec_es_result &o = r->res;
+  memset(&o, 0, sizeof(o));
+  o.support_n = g.n;
+  for (uint32_t q = 0; q < g.n; q++) o.support[q] = g.support[q];
+  o.cone_ands = g.cone_ands;
+  o.num_slots = g.num_slots;
+  o.tier = r->tier;
+  o.order = g.order;
+  o.words_checked = num_words(g.n);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, sl.e0, sl.e1);
+  o.device_ms = ms;
+  o.cex = sl.h_res[0];
+  o.verdict = o.cex == UINT64_MAX ? LEC_ES_EQUIVALENT : LEC_ES_NONEQUIVALENT;
+  const uint32_t status = (uint32_t)sl.h_res[2];
+  sl.busy = false;
+  s->stream_load[r->stream]--;
+  s->used -= r->reserve;
+  r->t_done = now_ms();
+  o.latency_ms = r->t_done - r->t_submit;
+  if (r->cancel) {
+    finish(s, r, Request::CANCELLED);
+  } else if (status) {
+    r->err = (status & DEV_WAIT_TIMEOUT) ? LEC_ES_EDEVICE_WAIT : LEC_ES_ECUDA;
+    finish(s, r, Request::FAILED);
+  } else {
+    finish(s, r, Request::DONE);
+  }
+}
+
+void dispatcher(Server *s) {
+  lec_es_ctx *c = s->c;
+  cudaSetDevice(c->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (!s->stop) {
+    // completions
+    for (size_t i = 0; i < s->running.size();) {
+      Request *r = s->reqs[s->running[i]].get();
+      Slot &sl = s->slots[r->slot];
+      if (r->cancel && !r->cancel_sent && cudaEventQuery(sl.e0) == cudaSuccess) {
+        // the request's reset copy has run: zero its counterexample word so
+        // every later pass of its kernel sees "nothing lower to find"
+        cudaMemcpyAsync(sl.d_res, s->h_zero, 8, cudaMemcpyHostToDevice, s->ctl);
+        r->cancel_sent = true;
+      }
+      cudaError_t q = cudaEventQuery(sl.e2);
+      if (q == cudaSuccess) {
+        retire(s, r);
+        s->running[i] = s->running.back();
+        s->running.pop_back();
+      } else {
+        if (q != cudaErrorNotReady) {
+          r->err = LEC_ES_ECUDA;
+          sl.busy = false;
+          s->stream_load[r->stream]--;
+          s->used -= r->reserve;
+          finish(s, r, Request::FAILED);
+          s->running[i] = s->running.back();
+          s->running.pop_back();
+          continue;
+        }
+        i++;
+      }
+    }
+    // admission in arrival order
+    while (!s->queue.empty() && s->running.size() < c->max_inflight) {
+      Request *r = s->reqs[s->queue.front()].get();
+      if (r->state == Request::CANCELLED) {
+        s->queue.pop_front();
+        continue;
+      }
+      r->reserve = reserve_bytes(c, r->prog);
+      if (s->used + r->reserve > c->slot_budget && !s->running.empty()) break;
+      int rc = launch(s, r);
+      if (rc == LEC_ES_ENOMEM || rc == LEC_ES_EBUSY) {
+        if (s->running.empty()) {
+          r->err = rc;
+          s->queue.pop_front();
+          finish(s, r, Request::FAILED);
+          continue;
+        }
+        break;
+      }
+      s->queue.pop_front();
+      if (rc) {
+        r->err = rc;
+        finish(s, r, Request::FAILED);
+        continue;
+      }
+      s->used += r->reserve;
+      r->state = Request::RUNNING;
+      s->running.push_back(r->ticket);
+    }
+    if (s->running.empty()) {
+      s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+    } else {
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(50));
+      lk.lock();
+    }
+  }
+}
+
+int ensure_server(lec_es_ctx *c) {
+  std::lock_guard<std::mutex> g(c->server_mu);
+  if (c->server) return LEC_ES_OK;
+  cudaSetDevice(c->device);
+  std::unique_ptr<Server> s(new (std::nothrow) Server());
+  if (!s) return LEC_ES_ENOMEM;
+  s->c = c;
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  s->streams.resize(kStreams);
+  s->stream_load.assign(kStreams, 0);
+  for (int i = 0; i < kStreams; i++) {
+    const int prio = i < kStreams / 2 ? greatest : least;
+    if (cudaStreamCreateWithPriority(&s->streams[i], cudaStreamNonBlocking, prio) != cudaSuccess)
+      return LEC_ES_ECUDA;
+  }
+  if (cudaStreamCreateWithFlags(&s->ctl, cudaStreamNonBlocking) != cudaSuccess) return LEC_ES_ECUDA;
+  if (cudaMallocHost((void **)&s->h_zero, 8) != cudaSuccess) return LEC_ES_ENOMEM;
+  *s->h_zero = 0;
+  s->slots.resize(c->max_inflight);
+  for (Slot &sl : s->slots) {
+    sl.d_res = (unsigned long long *)c->arena.alloc(32);
+    if (!sl.d_res) return LEC_ES_ENOMEM;
+    if (cudaMallocHost((void **)&sl.h_res, 32) != cudaSuccess) return LEC_ES_ENOMEM;
+    if (cudaEventCreate(&sl.e0) != cudaSuccess || cudaEventCreate(&sl.e1) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.e2, cudaEventDisableTiming) != cudaSuccess)
+      return LEC_ES_ECUDA;
+  }
+  Server *raw = s.get();
+  raw->th = std::thread(dispatcher, raw);
+  c->server = s.release();
+  return LEC_ES_OK;
+}
+
+}  // namespace
+
+void server_shutdown(lec_es_ctx *c) {
+  Server *s = nullptr;
+  {
+    std::lock_guard<std::mutex> g(c->server_mu);
+    s = c->server;
+    c->server = nullptr;
+  }
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    for (uint64_t t : s->running) {
+      Request *r = s->reqs[t].get();
+      cudaMemcpyAsync(s->slots[r->slot].d_res, s->h_zero, 8, cudaMemcpyHostToDevice, s->ctl);
+    }
+  }
+  s->cv_work.notify_all();
+  if (s->th.joinable()) s->th.join();
+  cudaSetDevice(c->device);
+  for (cudaStream_t st : s->streams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  cudaStreamSynchronize(s->ctl);
+  cudaStreamDestroy(s->ctl);
+  for (Slot &sl : s->slots) {
+    c->arena.free(sl.d_res);
+    if (sl.h_res) cudaFreeHost(sl.h_res);
+    if (sl.e0) cudaEventDestroy(sl.e0);
+    if (sl.e1) cudaEventDestroy(sl.e1);
+    if (sl.e2) cudaEventDestroy(sl.e2);
+  }
+  for (auto &kv : s->resident) c->arena.free(kv.second.d_recs);
+  if (s->h_zero) cudaFreeHost(s->h_zero);
+  s->cv_done.notify_all();
+  delete s;
+}
+
+}  // namespace lec
+
+using namespace lec;
+
+extern "C" int lec_es_server_config(lec_es_ctx *c, size_t slot_budget_bytes, uint32_t max_inflight) {
+  if (!c || max_inflight == 0 || max_inflight > 4096) return LEC_ES_EINVAL;
+  std::lock_guard<std::mutex> g(c->server_mu);
+  if (c->server) return LEC_ES_EBUSY;
+  c->slot_budget = slot_budget_bytes;
+  c->max_inflight = max_inflight;
+  return LEC_ES_OK;
+}
+
+extern "C" int lec_es_submit(lec_es_ctx *c, const lec_es_miter *m, uint64_t *ticket) {
+  if (!c || !m || !ticket) return LEC_ES_EINVAL;
+  const double t0 = now_ms();
+  std::unique_ptr<Request> r(new (std::nothrow) Request());
+  if (!r) return LEC_ES_ENOMEM;
+  MiterView v{m->num_pis, m->num_ands, m->fanins, m->out_lit};
+  int rc;
+  try {
+    rc = compile_program(v, LEC_ES_ORDER_AUTO, c->max_pis, r->prog);
+  } catch (const std::bad_alloc &) {
+    return LEC_ES_ENOMEM;
+  }
+  if (rc) return rc;
+  rc = ensure_server(c);
+  if (rc) return rc;
+  Server *s = c->server;
+  r->t_submit = t0;
+  r->res.host_ms = now_ms() - t0;
+  std::lock_guard<std::mutex> lk(s->mu);
+  r->ticket = s->next_ticket++;
+  *ticket = r->ticket;
+  s->queue.push_back(r->ticket);
+  s->reqs[r->ticket] = std::move(r);
+  s->cv_work.notify_one();
+  return LEC_ES_OK;
+}
+
+namespace {
+// Called with s->mu held: result of a finished request (and release).
+int collect(Server *s, uint64_t ticket, lec_es_result *out) {
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return LEC_ES_ENOTFOUND;
+  Request *r = it->second.get();
+  if (r->state == Request::QUEUED || r->state == Request::RUNNING) return LEC_ES_EBUSY;
+  int rc = LEC_ES_OK;
+  if (r->state == Request::CANCELLED) rc = LEC_ES_ECANCELLED;
+  else if (r->state == Request::FAILED) rc = r->err ? r->err : LEC_ES_ECUDA;
+  else if (out) *out = r->res;
+  s->reqs.erase(it);
+  return rc;
+}
+}  // namespace
+
+extern "C" int lec_es_poll(lec_es_ctx *c, uint64_t ticket, lec_es_result *out) {
+  if (!c || !out) return LEC_ES_EINVAL;
+  Server *s = c->server;
+  if (!s) return LEC_ES_ENOTFOUND;
+  std::lock_guard<std::mutex> lk(s->mu);
+  return collect(s, ticket, out);
+}
+
+extern "C" int lec_es_wait(lec_es_ctx *c, uint64_t ticket, double timeout_s, lec_es_result *out) {
+  if (!c || !out) return LEC_ES_EINVAL;
+  Server *s = c->server;
+  if (!s) return LEC_ES_ENOTFOUND;
+  std::unique_lock<std::mutex> lk(s->mu);
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+  for (;;) {
+    int rc = collect(s, ticket, out);
+    if (rc != LEC_ES_EBUSY) return rc;
+    if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
+      rc = collect(s, ticket, out);
+      return rc == LEC_ES_EBUSY ? LEC_ES_ETIMEOUT : rc;
+    }
+  }
+}
+
+extern "C" int lec_es_cancel(lec_es_ctx *c, uint64_t ticket) {
+  if (!c) return LEC_ES_EINVAL;
+  Server *s = c->server;
+  if (!s) return LEC_ES_ENOTFOUND;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return LEC_ES_ENOTFOUND;
+  Request *r = it->second.get();
+  if (r->state == Request::QUEUED) {
+    finish(s, r, Request::CANCELLED);
+  } else if (r->state == Request::RUNNING) {
+    r->cancel = true;
+  }
+  return LEC_ES_OK;
+}

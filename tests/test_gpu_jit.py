@@ -1,0 +1,86 @@
+"""GPU parity of the specialised (run-time compiled, register-resident) tier."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2512_06627_b300 import circuits as C
+from paper_2512_06627_b300 import lec_es as L
+from tests.gpu_common import make_ctx, oracle_cex
+from tests.reference_eval import random_aig
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = make_ctx()
+    yield c
+    L.lec_es_destroy(c)
+
+
+def jit(ctx, aig, out, wb=0, we=L.NO_CEX):
+    r = L.lec_es_check_ex(ctx, L.Miter(aig.num_pis, aig.flat_fanins(), out), L.options(wb, we, L.TIER_JIT))
+    assert r.tier == L.TIER_JIT
+    return r
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_graphs(ctx, seed):
+    rng = np.random.default_rng(9100 + seed)
+    aig = random_aig(rng, int(rng.integers(1, 14)), int(rng.integers(1, 120)))
+    out = aig.outputs[0]
+    assert jit(ctx, aig, out).cex_or_none == oracle_cex(aig, out)
+
+
+def test_small_supports(ctx):
+    for n in range(0, 9):
+        g = C.AigBuilder(10)
+        x = g.and_tree([g.pi(i + 1) for i in range(n)]) if n else 0
+        for neg in (0, 1):
+            aig = g.finish([x ^ neg])
+            assert jit(ctx, aig, x ^ neg).cex_or_none == oracle_cex(aig, x ^ neg), (n, neg)
+
+
+def test_configs_1_2(ctx):
+    for aig in [C.config1_adders()] + [C.config1_adders(s) for s in (1, 2, 3)] + [C.config2_mult12()] + \
+               [C.config2_mult12(s) for s in (1, 2, 3)]:
+        out = aig.outputs[0]
+        r = jit(ctx, aig, out)
+        assert r.cex_or_none == oracle_cex(aig, out)
+
+
+def test_word_ranges(ctx):
+    mm = C.config2_mult12(mutant_seed=1)
+    out = mm.outputs[0]
+    rng = np.random.default_rng(12)
+    for _ in range(8):
+        wb, we = sorted(int(x) for x in rng.integers(0, 1 << 18, size=2))
+        if wb == we:
+            continue
+        assert jit(ctx, mm, out, wb, we).cex_or_none == oracle_cex(mm, out, wb, we)
+
+
+def test_config3_full_and_closed_form_cex(ctx):
+    m = C.config3_mult16()
+    r = jit(ctx, m, m.outputs[0])
+    assert r.verdict == L.EQUIVALENT
+    mm = C.config3_mult16(mutant=True)
+    r = jit(ctx, mm, mm.outputs[0])
+    assert r.verdict == L.NONEQUIVALENT and r.cex == (1 << 32) - 1
+
+
+def test_auto_picks_jit_for_big_work(ctx):
+    m = C.config3_mult16()
+    r = L.lec_es_check(ctx, L.miter_of(m))
+    assert r.tier == L.TIER_JIT and r.verdict == L.EQUIVALENT
+
+
+def test_disk_cache_roundtrip(tmp_path):
+    aig = C.config2_mult12(mutant_seed=2)
+    out = aig.outputs[0]
+    for _ in range(2):
+        c = make_ctx(arena_bytes=64 << 20, jit_cache_dir=str(tmp_path))
+        r = L.lec_es_check_ex(c, L.miter_of(aig), L.options(tier=L.TIER_JIT))
+        assert r.cex_or_none == oracle_cex(aig, out)
+        L.lec_es_destroy(c)
+    assert any(p.suffix == ".cubin" for p in tmp_path.iterdir())

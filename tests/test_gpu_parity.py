@@ -1,0 +1,161 @@
+"""GPU parity: the CUDA path against the CPU oracle, bit-exact.
+
+Everything is integer and exact, so the bar is equality of the verdict, the
+counterexample index and (for small cones) every node's truth table.  All
+calls go through the C ABI (ctypes binding).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2512_06627_b300 import circuits as C
+from paper_2512_06627_b300 import lec_es as L
+from tests.reference_eval import random_aig
+
+pytestmark = pytest.mark.gpu
+
+TIERS = [L.TIER_INTERP, L.TIER_SPILL]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2512_06627_b300 import build
+    build.build()
+    c = L.lec_es_create(0, arena_bytes=4 << 30)
+    yield c
+    L.lec_es_destroy(c)
+
+
+def _oracle(aig, out, wb=0, we=None):
+    cex, _, n = O.check(aig.num_pis, aig.fanins, out, wb, O.NONE if we is None else we)
+    return cex, n
+
+
+def _gpu(ctx, aig, out, tier=L.TIER_AUTO, wb=0, we=L.NO_CEX, order=L.ORDER_AUTO, block=0):
+    m = L.Miter(aig.num_pis, aig.flat_fanins(), out)
+    return L.lec_es_check_ex(ctx, m, L.options(wb, we, tier, order, block))
+
+
+@pytest.mark.parametrize("tier", TIERS)
+@pytest.mark.parametrize("seed", range(25))
+def test_random_graphs(ctx, tier, seed):
+    rng = np.random.default_rng(7000 + seed)
+    aig = random_aig(rng, int(rng.integers(1, 14)), int(rng.integers(1, 120)))
+    out = aig.outputs[0]
+    cex, n = _oracle(aig, out)
+    r = _gpu(ctx, aig, out, tier)
+    assert r.support_n == n
+    assert r.cex_or_none == cex
+    assert r.verdict == (L.EQUIVALENT if cex is None else L.NONEQUIVALENT)
+
+
+@pytest.mark.parametrize("n", range(0, 9))
+def test_small_supports(ctx, n):
+    """n < 6: masks of the single word; PI k >= 5 from the chunk index."""
+    for neg in (0, 1):
+        g = C.AigBuilder(10)
+        lits = [g.pi(i + 1) for i in range(n)]
+        x = g.and_tree(lits) if n else 0
+        out = x ^ neg
+        aig = g.finish([out])
+        for tier in TIERS:
+            r = _gpu(ctx, aig, out, tier)
+            assert r.cex_or_none == _oracle(aig, out)[0], (n, neg, tier)
+
+
+@pytest.mark.parametrize("tier", TIERS)
+def test_config1_adders(ctx, tier):
+    m = C.config1_adders()
+    r = _gpu(ctx, m, m.outputs[0], tier)
+    assert r.verdict == L.EQUIVALENT and r.cex == L.NO_CEX and r.support_n == 16
+    for seed in (1, 2, 3, 4, 5):
+        mm = C.config1_adders(mutant_seed=seed)
+        r = _gpu(ctx, mm, mm.outputs[0], tier)
+        assert r.cex_or_none == _oracle(mm, mm.outputs[0])[0]
+
+
+@pytest.mark.parametrize("tier", TIERS)
+def test_config2_mult12(ctx, tier):
+    m = C.config2_mult12()
+    r = _gpu(ctx, m, m.outputs[0], tier)
+    assert r.verdict == L.EQUIVALENT and r.support_n == 24
+    for seed in (1, 2, 3):
+        mm = C.config2_mult12(mutant_seed=seed)
+        r = _gpu(ctx, mm, mm.outputs[0], tier)
+        assert r.verdict == L.NONEQUIVALENT
+        assert r.cex_or_none == _oracle(mm, mm.outputs[0])[0]
+
+
+@pytest.mark.parametrize("order", [L.ORDER_DFS, L.ORDER_VAR, L.ORDER_LEVEL])
+@pytest.mark.parametrize("block", [32, 64, 128, 256])
+def test_orders_and_blocks_agree(ctx, order, block):
+    mm = C.config1_adders(mutant_seed=1)
+    r = _gpu(ctx, mm, mm.outputs[0], L.TIER_INTERP, order=order, block=block)
+    assert r.cex_or_none == _oracle(mm, mm.outputs[0])[0]
+
+
+def test_word_ranges_ragged(ctx):
+    """Sub-ranges that start and end mid-pass give the oracle's first failure
+    in that range (and UNDECIDED when it passes)."""
+    mm = C.config2_mult12(mutant_seed=1)
+    out = mm.outputs[0]
+    rng = np.random.default_rng(11)
+    W = 1 << 18
+    ranges = [(0, 1), (0, 129), (127, 300), (W - 77, W)] + [
+        tuple(sorted(rng.integers(0, W, size=2))) for _ in range(10)]
+    for wb, we in ranges:
+        if wb == we:
+            continue
+        for tier in TIERS:
+            r = _gpu(ctx, mm, out, tier, int(wb), int(we))
+            cex, _ = _oracle(mm, out, int(wb), int(we))
+            assert r.cex_or_none == cex, (wb, we, tier)
+            if cex is None:
+                assert r.verdict == L.UNDECIDED
+
+
+@pytest.mark.parametrize("tier", TIERS)
+def test_truth_tables_every_node(ctx, tier):
+    """Per-node values of small cones equal the oracle's truth tables."""
+    for aig in (C.config1_adders(), C.config1_adders(3), C.build_multiplier_pair(5, "dadda"),
+                random_aig(np.random.default_rng(3), 4, 40)):
+        out = aig.outputs[0]
+        m = L.Miter(aig.num_pis, aig.flat_fanins(), out)
+        W = O.num_words(L.lec_es_compile(m)[0].n)
+        for wb, we in ((0, W), (W // 3, W)):
+            if wb >= we:
+                continue
+            vars_, tt = L.lec_es_truth_tables(ctx, m, wb, we)
+            exp = O.truth_tables(aig.num_pis, aig.fanins, out, [int(v) for v in vars_], wb, we)
+            n = L.lec_es_compile(m)[0].n
+            vm = np.uint64((1 << (1 << n)) - 1) if n < 6 else np.uint64((1 << 64) - 1)
+            assert np.array_equal(tt & vm, exp & vm)
+
+
+def test_config3_full_enumeration(ctx):
+    """16x16 array vs Booth/Dadda: all 2^32 patterns, EQUIVALENT; the mutant's
+    only failing pattern is the closed-form 2^32 - 1."""
+    m = C.config3_mult16()
+    r = _gpu(ctx, m, m.outputs[0], L.TIER_INTERP)
+    assert r.verdict == L.EQUIVALENT and r.support_n == 32
+    mm = C.config3_mult16(mutant=True)
+    r = _gpu(ctx, mm, mm.outputs[0], L.TIER_INTERP)
+    assert r.verdict == L.NONEQUIVALENT and r.cex == (1 << 32) - 1
+
+
+def test_config3_sampled_ranges_vs_oracle(ctx):
+    mm = C.config3_mult16(mutant=True)
+    out = mm.outputs[0]
+    W = 1 << 26
+    rng = np.random.default_rng(5)
+    for wb in list(rng.integers(0, W - 40, size=6)) + [W - 40]:
+        wb = int(wb)
+        r = _gpu(ctx, mm, out, L.TIER_INTERP, wb, wb + 40)
+        assert r.cex_or_none == _oracle(mm, out, wb, wb + 40)[0]
+
+
+def test_lop3_peak_measures(ctx):
+    per_clk, sms, khz, rate = L.lec_es_lop3_peak(ctx)
+    assert sms >= 100 and 16 <= per_clk <= 300 and 500_000 < khz < 3_000_000
