@@ -73,7 +73,8 @@ enum {
   LEC_ES_ORDER_AUTO = 0,    /* the one with the fewest value slots */
   LEC_ES_ORDER_DFS = 1,     /* post-order from the output, deeper fanin first */
   LEC_ES_ORDER_VAR = 2,     /* ascending variable index */
-  LEC_ES_ORDER_LEVEL = 3    /* by logic level, then variable */
+  LEC_ES_ORDER_LEVEL = 3,   /* by logic level, then variable */
+  LEC_ES_ORDER_GREEDY = 4   /* list scheduling that keeps the live set small */
 };
 
 /* A miter: AIGER numbering.  Variable 0 is FALSE, 1..num_pis are PIs, AND
@@ -158,6 +159,14 @@ const char *lec_es_strerror(int status);
  * (malformed cone), ETOOBIG (n > 63 or > 65535 slots). */
 int lec_es_compile(const lec_es_miter *m, uint32_t order, lec_es_program_info *info,
                    uint64_t *records, uint64_t cap);
+
+/* Generate the specialised straight-line kernel for m and compile it with
+ * NVRTC for compute capability cc_major.cc_minor ("a" target), without
+ * loading it (no GPU needed).  log receives NVRTC's log, including ptxas'
+ * register and spill counts; *cubin_bytes the image size.  Errors: EINVAL,
+ * ETOOBIG, EJIT. */
+int lec_es_jit_compile(const lec_es_miter *m, int cc_major, int cc_minor, char *log, size_t log_cap,
+                       uint64_t *cubin_bytes);
 
 /* ---- single miter ----------------------------------------------------- */
 

@@ -14,6 +14,7 @@
 //            loaded lazily into a slot right before their first reader.
 // The peak slot count is the live-set size the kernels must hold per lane.
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -147,6 +148,93 @@ void order_dfs(const MiterView &m, const Cone &c, const ConeIndex &ix, const std
   }
 }
 
+// Greedy list scheduling for a small live set: among the ANDs whose fanins
+// are computed, take the one whose evaluation changes the number of live
+// values least (+1 for its result, +1 per PI or constant it loads first,
+// -1 per operand it reads for the last time); ties go to the most recently
+// readied node, which keeps chains together.
+void order_greedy(const MiterView &m, const Cone &c, const ConeIndex &ix, uint32_t root_var,
+                  std::vector<uint32_t> &ord) {
+  const size_t NA = c.ands.size(), NP = c.pis.size();
+  const size_t NV = NA + NP + 1;
+  auto vid = [&](uint32_t var) -> int64_t {
+    if (var == 0) return (int64_t)(NA + NP);
+    if (var <= m.num_pis) {
+      auto it = std::lower_bound(c.pis.begin(), c.pis.end(), var);
+      return (int64_t)(NA + (it - c.pis.begin()));
+    }
+    return ix.and_pos(var);
+  };
+  std::vector<int64_t> f0(NA), f1(NA);
+  std::vector<uint32_t> refs(NV, 0), pending(NA, 0);
+  std::vector<std::vector<uint32_t>> users(NV);
+  for (size_t i = 0; i < NA; i++) {
+    const uint32_t *f = fanin_of(m, c.ands[i]);
+    f0[i] = vid(f[0] >> 1);
+    f1[i] = vid(f[1] >> 1);
+    refs[f0[i]]++;
+    refs[f1[i]]++;
+    users[f0[i]].push_back((uint32_t)i);
+    if (f1[i] != f0[i]) users[f1[i]].push_back((uint32_t)i);
+    pending[i] = (f0[i] < (int64_t)NA ? 1u : 0u) + (f1[i] < (int64_t)NA && f1[i] != f0[i] ? 1u : 0u);
+  }
+  refs[vid(root_var)]++;
+  std::vector<uint8_t> loaded(NV, 0), done(NA, 0);
+  auto delta = [&](uint32_t i) -> int {
+    int d = 1;
+    const int64_t a = f0[i], b = f1[i];
+    if (a >= (int64_t)NA && !loaded[a]) d++;
+    if (b != a && b >= (int64_t)NA && !loaded[b]) d++;
+    if (a == b) {
+      if (refs[a] == 2) d--;
+    } else {
+      if (refs[a] == 1) d--;
+      if (refs[b] == 1) d--;
+    }
+    return d;
+  };
+  typedef std::pair<int, int64_t> Key;  // (delta, -stamp)
+  std::priority_queue<std::pair<Key, uint32_t>, std::vector<std::pair<Key, uint32_t>>,
+                      std::greater<std::pair<Key, uint32_t>>>
+      pq;
+  int64_t stamp = 0;
+  auto push = [&](uint32_t i) { pq.push({{delta(i), -(stamp++)}, i}); };
+  for (size_t i = 0; i < NA; i++)
+    if (pending[i] == 0) push((uint32_t)i);
+  ord.clear();
+  ord.reserve(NA);
+  while (!pq.empty()) {
+    auto top = pq.top();
+    pq.pop();
+    const uint32_t i = top.second;
+    if (done[i]) continue;
+    if (top.first.first != delta(i)) {  // stale key
+      push(i);
+      continue;
+    }
+    done[i] = 1;
+    ord.push_back(i);
+    for (int64_t v : {f0[i], f1[i]}) {
+      if (v >= (int64_t)NA && !loaded[v]) {
+        loaded[v] = 1;
+        for (uint32_t u : users[v])
+          if (!done[u] && pending[u] == 0) push(u);
+      }
+    }
+    refs[f0[i]]--;
+    refs[f1[i]]--;
+    for (int64_t v : {f0[i], f1[i]}) {
+      if (refs[v] == 1)
+        for (uint32_t u : users[v])
+          if (!done[u] && pending[u] == 0) push(u);
+    }
+    loaded[i] = 1;
+    for (uint32_t u : users[i]) {
+      if (--pending[u] == 0) push(u);
+    }
+  }
+}
+
 // Reference-count slot assignment over a given order.
 int assign_slots(const MiterView &m, const Cone &c, const ConeIndex &ix, const std::vector<uint32_t> &ord,
                  uint32_t root_var, Program &p) {
@@ -247,10 +335,10 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
   std::vector<uint32_t> level;
   order_levels(m, c, ix, level);
 
-  const uint32_t cands_auto[3] = {LEC_ES_ORDER_DFS, LEC_ES_ORDER_VAR, LEC_ES_ORDER_LEVEL};
+  const uint32_t cands_auto[4] = {LEC_ES_ORDER_DFS, LEC_ES_ORDER_VAR, LEC_ES_ORDER_LEVEL, LEC_ES_ORDER_GREEDY};
   std::vector<uint32_t> tried;
-  if (order == LEC_ES_ORDER_AUTO) tried.assign(cands_auto, cands_auto + 3);
-  else if (order <= LEC_ES_ORDER_LEVEL) tried.push_back(order);
+  if (order == LEC_ES_ORDER_AUTO) tried.assign(cands_auto, cands_auto + 4);
+  else if (order <= LEC_ES_ORDER_GREEDY) tried.push_back(order);
   else return LEC_ES_EINVAL;
 
   bool have = false;
@@ -259,6 +347,7 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
     std::vector<uint32_t> ord;
     if (o == LEC_ES_ORDER_DFS) order_dfs(m, c, ix, level, root_var, ord);
     else if (o == LEC_ES_ORDER_VAR) order_var(c, ord);
+    else if (o == LEC_ES_ORDER_GREEDY) order_greedy(m, c, ix, root_var, ord);
     else order_level(level, ord);
     if (ord.size() != c.ands.size()) return LEC_ES_EINVAL;
     Program p;

@@ -21,6 +21,7 @@
 #include <nvrtc.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 #include <sys/stat.h>
 
@@ -145,8 +146,9 @@ int compile_cubin(const std::string &src, int major, int minor, std::vector<char
     return LEC_ES_EJIT;
   // sm_103a on B300; the "a" suffix targets this exact architecture
   std::string arch = "-arch=sm_" + std::to_string(major) + std::to_string(minor) + "a";
-  const char *opts[] = {arch.c_str(), "-O3", "--std=c++17", "-lineinfo"};
-  nvrtcResult rc = nvrtcCompileProgram(prog, 4, opts);
+  // NVRTC optimises by default; -Xptxas -v puts register and spill counts in the log
+  const char *opts[] = {arch.c_str(), "--std=c++17", "-lineinfo", "-diag-suppress=177", "-Xptxas", "-v"};
+  nvrtcResult rc = nvrtcCompileProgram(prog, 6, opts);
   size_t lsz = 0;
   nvrtcGetProgramLogSize(prog, &lsz);
   if (lsz > 1) {
@@ -194,7 +196,10 @@ int build_kernel(lec_es_ctx *c, const Program &g, JitKernel **out) {
   if (path.empty() || !read_file(path, cubin)) {
     std::string log;
     int rc = compile_cubin(gen_source(g), c->cc_major, c->cc_minor, cubin, log);
-    if (rc) return rc;
+    if (rc) {
+      if (getenv("LEC_ES_JIT_LOG")) fprintf(stderr, "lec_es JIT failed:\n%s\n", log.c_str());
+      return rc;
+    }
     if (!path.empty()) write_file(path, cubin);
   }
   cudaSetDevice(c->device);
@@ -327,7 +332,26 @@ void jit_release_all(lec_es_ctx *c) {
   c->jit = nullptr;
 }
 
-// Source of the specialised kernel (test hook; no GPU needed).
+// Source of the specialised kernel (no GPU needed).
 std::string jit_source_for(const Program &g) { return gen_source(g); }
 
 }  // namespace lec
+
+extern "C" int lec_es_jit_compile(const lec_es_miter *m, int cc_major, int cc_minor, char *log, size_t log_cap,
+                                  uint64_t *cubin_bytes) {
+  if (!m) return LEC_ES_EINVAL;
+  lec::Program g;
+  lec::MiterView v{m->num_pis, m->num_ands, m->fanins, m->out_lit};
+  int rc = lec::compile_program(v, LEC_ES_ORDER_AUTO, 63, g);
+  if (rc) return rc;
+  std::vector<char> cubin;
+  std::string lg;
+  rc = lec::compile_cubin(lec::gen_source(g), cc_major, cc_minor, cubin, lg);
+  if (log && log_cap) {
+    const size_t n = std::min(log_cap - 1, lg.size());
+    memcpy(log, lg.data(), n);
+    log[n] = 0;
+  }
+  if (cubin_bytes) *cubin_bytes = cubin.size();
+  return rc;
+}

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "liblec_es.so")
 OK, EINVAL, ETOOBIG, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ECANCELLED, EDEVICE_WAIT, EJIT, ENOTFOUND = range(11)
 EQUIVALENT, NONEQUIVALENT, UNDECIDED = 0, 1, 2
 TIER_AUTO, TIER_INTERP, TIER_JIT, TIER_SPILL = 0, 1, 2, 3
-ORDER_AUTO, ORDER_DFS, ORDER_VAR, ORDER_LEVEL = 0, 1, 2, 3
+ORDER_AUTO, ORDER_DFS, ORDER_VAR, ORDER_LEVEL, ORDER_GREEDY = 0, 1, 2, 3, 4
 NO_CEX = (1 << 64) - 1
 
 # every entry point declared in include/lec_es.h
@@ -32,7 +32,7 @@ EXPORTS = [
     "lec_es_check_ex", "lec_es_prepare", "lec_es_run_async", "lec_es_plan_result", "lec_es_plan_info",
     "lec_es_plan_free", "lec_es_truth_tables", "lec_es_batch", "lec_es_batch_prepare",
     "lec_es_batch_run_async", "lec_es_batch_results", "lec_es_batch_free", "lec_es_submit", "lec_es_poll",
-    "lec_es_wait", "lec_es_cancel", "lec_es_server_config", "lec_es_lop3_peak",
+    "lec_es_wait", "lec_es_cancel", "lec_es_server_config", "lec_es_lop3_peak", "lec_es_jit_compile",
 ]
 
 
@@ -125,6 +125,8 @@ def load() -> ctypes.CDLL:
         "lec_es_wait": ([_P, ctypes.c_uint64, ctypes.c_double, R], ctypes.c_int),
         "lec_es_cancel": ([_P, ctypes.c_uint64], ctypes.c_int),
         "lec_es_server_config": ([_P, ctypes.c_size_t, ctypes.c_uint32], ctypes.c_int),
+        "lec_es_jit_compile": ([M, ctypes.c_int, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t, _u64p],
+                               ctypes.c_int),
         "lec_es_lop3_peak": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     }
@@ -331,6 +333,15 @@ def lec_es_wait(ctx: Context, ticket: int, timeout_s: float = 600.0) -> lec_es_r
 
 def lec_es_cancel(ctx: Context, ticket: int) -> None:
     _ok(load().lec_es_cancel(ctx.handle, ticket), "lec_es_cancel")
+
+
+def lec_es_jit_compile(m: Miter, cc_major: int = 10, cc_minor: int = 3):
+    """Host-only NVRTC compile of the specialised kernel: (log, cubin bytes)."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    n = ctypes.c_uint64()
+    _ok(load().lec_es_jit_compile(ctypes.byref(m.c), cc_major, cc_minor, buf, len(buf), ctypes.byref(n)),
+        "lec_es_jit_compile")
+    return buf.value.decode(errors="replace"), int(n.value)
 
 
 def lec_es_lop3_peak(ctx: Context):

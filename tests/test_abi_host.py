@@ -227,3 +227,15 @@ def test_shared_graph_cones_are_independent():
         info, _ = L.lec_es_compile(L.Miter(pb.aig.num_pis, f, out))
         sup, na = O.support(pb.aig.num_pis, pb.aig.fanins, out)
         assert info.cone_ands == na and info.n == len(sup)
+
+
+def test_jit_compiles_for_sm103a_without_spills():
+    """The specialised kernel of the 12x12 and 16x16 miters compiles with
+    NVRTC for sm_103a and keeps every value in registers."""
+    import re as _re
+    for aig in (C.config2_mult12(), C.config3_mult16(), C.config1_adders(1)):
+        log, nbytes = L.lec_es_jit_compile(L.miter_of(aig), 10, 3)
+        assert nbytes > 0
+        regs = int(_re.search(r"Used (\d+) registers", log).group(1))
+        assert regs <= 255
+        assert "0 bytes spill stores" in log, log
