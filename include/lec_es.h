@@ -199,6 +199,31 @@ void lec_es_plan_free(lec_es_ctx *c, lec_es_plan *p);
 int lec_es_truth_tables(lec_es_ctx *c, const lec_es_miter *m, uint64_t word_begin,
                         uint64_t word_end, uint32_t *vars_out, uint64_t *host_out);
 
+/* For callers that cannot allocate device memory (a framework's caching
+ * allocator owns it all, or a service may not allocate after start-up).
+ * The paper has no counterpart: it is a deployment variant of the
+ * global-memory interpreter.  ES of one program compiled by lec_es_compile
+ * whose records the caller has copied to device memory:
+ *   d_records         device, 16-byte aligned, records_capacity >= num_records
+ *                     rounded up to even (the copy engine moves 16-byte pairs);
+ *   prog              the lec_es_program_info lec_es_compile returned;
+ *   word_begin/end    64-pattern word range (word_end clipped to the cone's);
+ *   d_result          device, 4 x u64 written by the call: [0] lowest failing
+ *                     pattern or UINT64_MAX, [1] patterns evaluated,
+ *                     [2] status (0 ok, 1 a bounded device wait gave up), [3] unused;
+ *   stream            cudaStream_t; the call enqueues and returns at once.
+ * The value slots live in a fixed 16 MiB device array that every GPU using
+ * the library holds until exit; live sets with num_slots * 32 * 4 bytes above
+ * that are rejected with LEC_ES_ETOOBIG.  The first call on a device looks up
+ * the array's address (make it before any stream capture).  No cudaMalloc,
+ * cudaFree or other allocating call is made.  All calls share the array:
+ * calls whose kernels overlap on the GPU race and must be serialised.
+ * Errors: EINVAL (NULL, misaligned or short buffers, bad program info,
+ * empty range), ETOOBIG, ECUDA. */
+int lec_es_check_noalloc(const uint64_t *d_records, uint64_t records_capacity,
+                         const lec_es_program_info *prog, uint64_t word_begin, uint64_t word_end,
+                         unsigned long long *d_result, void *stream);
+
 /* ---- batch: many miters, one persistent launch ------------------------- */
 
 /* ES of k miters in one persistent launch over a queue of (miter, word

@@ -33,6 +33,7 @@ EXPORTS = [
     "lec_es_plan_free", "lec_es_truth_tables", "lec_es_batch", "lec_es_batch_prepare",
     "lec_es_batch_run_async", "lec_es_batch_results", "lec_es_batch_free", "lec_es_submit", "lec_es_poll",
     "lec_es_wait", "lec_es_cancel", "lec_es_server_config", "lec_es_lop3_peak", "lec_es_jit_compile",
+    "lec_es_check_noalloc",
 ]
 
 
@@ -127,6 +128,8 @@ def load() -> ctypes.CDLL:
         "lec_es_server_config": ([_P, ctypes.c_size_t, ctypes.c_uint32], ctypes.c_int),
         "lec_es_jit_compile": ([M, ctypes.c_int, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t, _u64p],
                                ctypes.c_int),
+        "lec_es_check_noalloc": ([_P, ctypes.c_uint64, ctypes.POINTER(lec_es_program_info), ctypes.c_uint64,
+                                  ctypes.c_uint64, _P, _P], ctypes.c_int),
         "lec_es_lop3_peak": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     }
@@ -342,6 +345,15 @@ def lec_es_jit_compile(m: Miter, cc_major: int = 10, cc_minor: int = 3):
     _ok(load().lec_es_jit_compile(ctypes.byref(m.c), cc_major, cc_minor, buf, len(buf), ctypes.byref(n)),
         "lec_es_jit_compile")
     return buf.value.decode(errors="replace"), int(n.value)
+
+
+def lec_es_check_noalloc(d_records: int, records_capacity: int, info: lec_es_program_info, word_begin: int,
+                         word_end: int, d_result: int, stream: int) -> None:
+    """Enqueue the allocation-free check: device pointers and a stream handle
+    are passed as integers; the call allocates nothing."""
+    _ok(load().lec_es_check_noalloc(ctypes.c_void_p(d_records), records_capacity, ctypes.byref(info),
+                                    word_begin, word_end, ctypes.c_void_p(d_result), ctypes.c_void_p(stream)),
+        "lec_es_check_noalloc")
 
 
 def lec_es_lop3_peak(ctx: Context):
