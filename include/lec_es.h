@@ -111,7 +111,18 @@ typedef struct {
   uint32_t order;           /* LEC_ES_ORDER_* (default AUTO) */
   uint32_t block_threads;   /* 0 = library choice */
   uint32_t grid_blocks;     /* 0 = library choice */
+  uint32_t flags;           /* LEC_ES_FLAG_* */
 } lec_es_options;
+
+/* Option flags. */
+enum {
+  LEC_ES_FLAG_JIT_AND_FORM = 1u,     /* JIT tier: one C expression per AND, fused by the
+                                        compiler, instead of the 3-input table cover */
+  LEC_ES_FLAG_TEST_WAIT_TIMEOUT = 2u /* test hook (interpreter tier): the kernel waits for
+                                        16 bytes more than its record copy delivers, so
+                                        its bounded wait must give up and the call must
+                                        return LEC_ES_EDEVICE_WAIT */
+};
 
 typedef struct {
   int device;               /* CUDA device ordinal */
@@ -139,6 +150,8 @@ typedef struct {
   uint32_t order;
   uint64_t num_records;     /* written even when cap is too small */
   uint64_t hash;            /* structural hash of the program */
+  uint32_t num_luts;        /* 3-input tables covering the cone (JIT instructions) */
+  uint32_t lut_live;        /* peak live values when evaluating the tables */
 } lec_es_program_info;
 
 /* ---- context ---------------------------------------------------------- */

@@ -193,11 +193,11 @@ extern "C" int lec_es_create(lec_es_ctx **out, const lec_es_config *cfg) {
   }
   c->arena_base = base;
   if (c->arena.init(base, bytes) != LEC_ES_OK) return LEC_ES_ENOMEM;
-  if (cudaMallocHost((void **)&c->h_init, 4 * sizeof(unsigned long long)) != cudaSuccess) return LEC_ES_ENOMEM;
+  if (cudaMallocHost((void **)&c->h_init, kResWords * sizeof(unsigned long long)) != cudaSuccess)
+    return LEC_ES_ENOMEM;
+  for (int i = 0; i < kResWords; i++) c->h_init[i] = 0;
   c->h_init[0] = ~0ull;
-  c->h_init[1] = 0;
-  c->h_init[2] = 0;
-  c->h_init[3] = ~0ull;
+  c->h_init[4] = ~0ull;
   *out = c.release();
   return LEC_ES_OK;
 }
@@ -238,6 +238,8 @@ extern "C" int lec_es_compile(const lec_es_miter *m, uint32_t order, lec_es_prog
   info->order = p.order;
   info->num_records = p.recs.size();
   info->hash = p.hash;
+  info->num_luts = (uint32_t)p.lut.order.size();
+  info->lut_live = p.lut.live;
   if (records && cap) memcpy(records, p.recs.data(), sizeof(Rec) * std::min<uint64_t>(cap, p.recs.size()));
   return LEC_ES_OK;
 }
@@ -298,6 +300,8 @@ int plan_prepare_program(lec_es_ctx *c, Program &&prog, const lec_es_options *op
   if (!p) return LEC_ES_ENOMEM;
   p->prog = std::move(prog);
   p->stream = c->stream;
+  p->flags = opt ? opt->flags : 0;
+  p->jit_lut = !(p->flags & LEC_ES_FLAG_JIT_AND_FORM);
   int rc;
   if (cudaSetDevice(c->device) != cudaSuccess) return LEC_ES_ECUDA;
   const Program &g = p->prog;
@@ -343,9 +347,10 @@ int plan_finish_device(lec_es_ctx *c, lec_es_plan *p) {
       if (!p->d_spill) return LEC_ES_ENOMEM;
     }
   }
-  p->d_res = (unsigned long long *)c->arena.alloc(4 * sizeof(unsigned long long));
+  p->d_res = (unsigned long long *)c->arena.alloc(kResWords * sizeof(unsigned long long));
   if (!p->d_res) return LEC_ES_ENOMEM;
-  if (cudaMallocHost((void **)&p->h_res, 4 * sizeof(unsigned long long)) != cudaSuccess) return LEC_ES_ENOMEM;
+  if (cudaMallocHost((void **)&p->h_res, kResWords * sizeof(unsigned long long)) != cudaSuccess)
+    return LEC_ES_ENOMEM;
   if (cudaEventCreate(&p->e0) != cudaSuccess || cudaEventCreate(&p->e1) != cudaSuccess ||
       cudaEventCreateWithFlags(&p->e2, cudaEventDisableTiming) != cudaSuccess)
     return LEC_ES_ECUDA;
@@ -370,13 +375,13 @@ int plan_run_async_grid(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt
   const uint64_t C = num_chunks(g.n);
   const uint64_t cb = std::min<uint64_t>(2 * wb, C), ce = std::min<uint64_t>(2 * we, C);
   cudaStream_t st = p->stream;
-  if (cudaMemcpyAsync(p->d_res, c->h_init, 4 * sizeof(unsigned long long), cudaMemcpyHostToDevice, st) !=
-      cudaSuccess)
+  if (cudaMemcpyAsync(p->d_res, c->h_init, kResWords * sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                      st) != cudaSuccess)
     return LEC_ES_ECUDA;
   cudaEventRecord(p->e0, st);
   int err;
   if (p->tier == LEC_ES_TIER_JIT) {
-    err = jit_launch(c, p, cb, ce, grid_override);
+    err = jit_launch(c, p, cb, ce, grid_override, ~0ull);
   } else {
     InterpParams ip{};
     ip.recs = (const Rec *)p->d_recs;
@@ -394,13 +399,14 @@ int plan_run_async_grid(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt
     ip.evaluated = p->d_res + 1;
     ip.status = (uint32_t *)(p->d_res + 2);
     ip.spill = (uint32_t *)p->d_spill;
+    ip.extra_tx = (p->flags & LEC_ES_FLAG_TEST_WAIT_TIMEOUT) ? 16u : 0u;
     int grid = p->geom.grid;
     if (grid_override > 0 && !p->geom.spill) grid = grid_override;
     err = launch_interp(ip, p->geom.block, grid, p->geom.smem, p->geom.spill, st);
   }
   if (err) return LEC_ES_ECUDA;
   cudaEventRecord(p->e1, st);
-  if (cudaMemcpyAsync(p->h_res, p->d_res, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st) !=
+  if (cudaMemcpyAsync(p->h_res, p->d_res, kResWords * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st) !=
       cudaSuccess)
     return LEC_ES_ECUDA;
   if (cudaEventRecord(p->e2, st) != cudaSuccess) return LEC_ES_ECUDA;
@@ -466,6 +472,8 @@ extern "C" int lec_es_plan_info(const lec_es_plan *p, lec_es_program_info *info)
   info->order = g.order;
   info->num_records = g.recs.size();
   info->hash = g.hash;
+  info->num_luts = (uint32_t)g.lut.order.size();
+  info->lut_live = g.lut.live;
   return LEC_ES_OK;
 }
 
@@ -528,7 +536,7 @@ extern "C" int lec_es_truth_tables(lec_es_ctx *c, const lec_es_miter *m, uint64_
   void *d_recs = c->arena.alloc((size_t)geom.nrec_padded * sizeof(Rec));
   void *d_row = c->arena.alloc(row.size() * 4);
   void *d_out = c->arena.alloc(std::max<size_t>(out_bytes, 8));
-  void *d_res = c->arena.alloc(32);
+  void *d_res = c->arena.alloc(kResWords * 8);
   void *d_spill = geom.spill ? c->arena.alloc((size_t)g.num_slots * geom.grid * geom.block * 4u) : nullptr;
   auto cleanup = [&]() {
     c->arena.free(d_recs);
@@ -547,7 +555,7 @@ extern "C" int lec_es_truth_tables(lec_es_ctx *c, const lec_es_miter *m, uint64_
   cudaError_t e = cudaMemcpyAsync(d_recs, padded.data(), padded.size() * sizeof(Rec), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_row, row.data(), row.size() * 4, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_out, 0, std::max<size_t>(out_bytes, 8), st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_res, c->h_init, 32, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_res, c->h_init, kResWords * 8, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) {
     cudaStreamSynchronize(st);
     cleanup();
@@ -566,7 +574,7 @@ extern "C" int lec_es_truth_tables(lec_es_ctx *c, const lec_es_miter *m, uint64_
   ip.chunk_begin = std::min<uint64_t>(2 * word_begin, num_chunks(g.n));
   ip.chunk_end = std::min<uint64_t>(2 * word_end, num_chunks(g.n));
   unsigned long long *res = (unsigned long long *)d_res;
-  ip.cex = res + 3;  // a private counterexample slot: the dump never exits early
+  ip.cex = res + 4;  // a counterexample word nothing lowers: the dump never exits early
   ip.evaluated = res + 1;
   ip.status = (uint32_t *)(res + 2);
   ip.spill = (uint32_t *)d_spill;

@@ -58,7 +58,8 @@ int choose_interp_geometry(lec_es_ctx *c, const Program &prog, uint64_t chunks, 
 // JIT tier (jit.cpp)
 uint32_t jit_auto_tier(lec_es_ctx *c, const Program &g, uint64_t chunks);
 int jit_prepare(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt);
-int jit_launch(lec_es_ctx *c, lec_es_plan *p, uint64_t chunk_begin, uint64_t chunk_end, int grid);
+int jit_launch(lec_es_ctx *c, lec_es_plan *p, uint64_t chunk_begin, uint64_t chunk_end, int grid,
+               uint64_t max_grabs);
 // Non-blocking lookup for the server: the compiled kernel if ready, else
 // schedules a background compile (once per program) and returns nullptr.
 lec::JitKernel *jit_lookup_or_schedule(lec_es_ctx *c, const Program &g);
@@ -92,7 +93,7 @@ struct lec_es_ctx {
   void *arena_base = nullptr;
   bool own_arena = false;
   lec::Arena arena;
-  unsigned long long *h_init = nullptr;  // pinned {~0, 0, 0, ~0}
+  unsigned long long *h_init = nullptr;  // pinned result-word initialiser, kResWords words
   std::string jit_dir;
   lec::JitState *jit = nullptr;
   lec::Server *server = nullptr;
@@ -101,6 +102,11 @@ struct lec_es_ctx {
   uint32_t max_inflight = 64;
 };
 
+// Result words of a run: [0] lowest failing pattern (init ~0), [1] patterns
+// evaluated, [2] status, [3] JIT chunk-grab counter, [4] a second
+// counterexample word (init ~0) for runs that must not exit early.
+constexpr int kResWords = 8;
+
 struct lec_es_plan {
   lec::Program prog;
   lec::PlanGeom geom;
@@ -108,7 +114,7 @@ struct lec_es_plan {
   void *d_recs = nullptr;
   void *d_spill = nullptr;
   size_t spill_bytes = 0;
-  unsigned long long *d_res = nullptr;  // [cex, evaluated, status, spare]
+  unsigned long long *d_res = nullptr;  // kResWords result words
   unsigned long long *h_res = nullptr;  // pinned copy
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   bool pending = false;
@@ -116,5 +122,7 @@ struct lec_es_plan {
   double host_ms = 0, jit_ms = 0;
   lec::JitKernel *jit = nullptr;
   int jit_block = 0, jit_grid = 0;
+  bool jit_lut = true;                   // table form (else AND form)
+  uint32_t flags = 0;                    // LEC_ES_FLAG_* the plan was prepared with
   cudaStream_t stream = nullptr;         // where runs are enqueued (ctx stream by default)
 };

@@ -20,6 +20,31 @@ static_assert(sizeof(Rec) == 8, "record is 8 bytes");
 
 enum : uint8_t { OP_AND = 0, OP_PI = 4, OP_CONST0 = 5 };
 
+// Cover of a cone by 3-input lookup tables (lutmap.cpp).  Value ids: ANDs
+// 0..NA-1 (ascending variable), support PIs NA..NA+n-1, the constant NA+n.
+struct LutCover {
+  struct Lut {
+    int32_t node;      // the AND whose function the table computes
+    uint8_t n;         // leaves used (0..3)
+    int32_t leaf[3];   // value ids, ascending; -1 if unused
+    uint8_t tt;        // truth table, leaf i = x_i with x0 = 0xAA, x1 = 0xCC, x2 = 0xF0
+  };
+  std::vector<Lut> luts;       // ascending node order
+  std::vector<int32_t> index;  // AND id -> position in luts, or -1
+};
+
+void lut_map(size_t NA, size_t NP, const std::vector<int64_t> &f0, const std::vector<int64_t> &f1,
+             const std::vector<uint8_t> &c0, const std::vector<uint8_t> &c1, int64_t root, LutCover &out);
+
+// LUT program: tables in evaluation order over value ids (see LutCover).
+struct LutProgram {
+  uint32_t na = 0;                       // ANDs of the cone (value ids below this are ANDs)
+  uint32_t np = 0;                       // support PIs
+  std::vector<LutCover::Lut> order;      // evaluation order (topological)
+  int64_t root = -1;                     // value id of the output's node
+  uint32_t live = 0;                     // peak number of live values in this order
+};
+
 // Compiled cone (paper §3.3 "Instructionalized ES"): branch-free instruction
 // stream over value slots reused by reference count.
 struct Program {
@@ -33,6 +58,7 @@ struct Program {
   uint32_t cone_ands = 0;
   uint32_t order = 0;
   uint64_t hash = 0;
+  LutProgram lut;                   // 3-input table cover (the JIT tier's instructions)
 };
 
 struct MiterView {
@@ -71,6 +97,7 @@ struct InterpParams {
   const uint32_t *tt_row;   // record index -> dump row (or 0xffffffff)
   uint64_t tt_words;        // words per dump row
   uint64_t tt_word_begin;
+  uint32_t extra_tx;        // test hook: bytes expected beyond the record copy (0 normally)
 };
 
 // Batched tiles: miter table + tile queue.

@@ -313,6 +313,117 @@ int assign_slots(const MiterView &m, const Cone &c, const ConeIndex &ix, const s
   return LEC_ES_OK;
 }
 
+// 3-input table cover of the cone and its evaluation order: post-order from
+// the output, deeper leaf first; the live count is the peak number of table
+// outputs and PIs alive at once (each value dies after its last reader).
+void build_lut_program(const MiterView &m, const Cone &c, const ConeIndex &ix, uint32_t root_var,
+                       const std::vector<uint32_t> &and_order, LutProgram &lp) {
+  const size_t NA = c.ands.size(), NP = c.pis.size();
+  auto vid = [&](uint32_t var) -> int64_t {
+    if (var == 0) return (int64_t)(NA + NP);
+    if (var <= m.num_pis) {
+      auto it = std::lower_bound(c.pis.begin(), c.pis.end(), var);
+      return (int64_t)(NA + (it - c.pis.begin()));
+    }
+    return ix.and_pos(var);
+  };
+  std::vector<int64_t> f0(NA), f1(NA);
+  std::vector<uint8_t> c0(NA), c1(NA);
+  for (size_t i = 0; i < NA; i++) {
+    const uint32_t *f = fanin_of(m, c.ands[i]);
+    f0[i] = vid(f[0] >> 1);
+    f1[i] = vid(f[1] >> 1);
+    c0[i] = (uint8_t)(f[0] & 1);
+    c1[i] = (uint8_t)(f[1] & 1);
+  }
+  lp.na = (uint32_t)NA;
+  lp.np = (uint32_t)NP;
+  lp.root = vid(root_var);
+  lp.order.clear();
+  lp.live = 0;
+  if (lp.root >= (int64_t)NA) return;  // output is a PI or the constant
+  LutCover cov;
+  lut_map(NA, NP, f0, f1, c0, c1, lp.root, cov);
+  // level of each table (leaves at 0)
+  std::vector<uint32_t> lev(cov.luts.size(), 0);
+  for (size_t i = 0; i < cov.luts.size(); i++) {
+    uint32_t l = 0;
+    for (int k = 0; k < cov.luts[i].n; k++) {
+      const int32_t x = cov.luts[i].leaf[k];
+      if (x < (int32_t)NA) l = std::max(l, lev[cov.index[x]] + 1);
+    }
+    lev[i] = l;
+  }
+  const size_t NV = NA + NP + 1;
+  auto live_of = [&](const std::vector<LutCover::Lut> &ord) -> uint32_t {
+    std::vector<uint32_t> uses(NV, 0);
+    for (const auto &l : ord)
+      for (int k = 0; k < l.n; k++) uses[l.leaf[k]]++;
+    uses[lp.root]++;
+    std::vector<uint8_t> alive(NV, 0);
+    uint32_t live = 0, peak = 0;
+    for (const auto &l : ord) {
+      for (int k = 0; k < l.n; k++)
+        if (!alive[l.leaf[k]]) { alive[l.leaf[k]] = 1; live++; }  // PI / constant first read
+      peak = std::max(peak, live + 1);
+      for (int k = 0; k < l.n; k++)
+        if (--uses[l.leaf[k]] == 0) { alive[l.leaf[k]] = 0; live--; }
+      alive[l.node] = 1;
+      live++;
+      peak = std::max(peak, live);
+    }
+    return peak;
+  };
+  std::vector<std::vector<LutCover::Lut>> cands;
+  // (1) post-order from the root, deeper leaf first
+  {
+    std::vector<LutCover::Lut> ord;
+    std::vector<uint8_t> st(cov.luts.size(), 0);
+    std::vector<std::pair<int32_t, uint8_t>> stack{{cov.index[lp.root], 0}};
+    while (!stack.empty()) {
+      auto &top = stack.back();
+      const int32_t i = top.first;
+      if (top.second == 0) {
+        if (st[i]) { stack.pop_back(); continue; }
+        st[i] = 1;
+        top.second = 1;
+        std::vector<int32_t> kids;
+        for (int k = 0; k < cov.luts[i].n; k++) {
+          const int32_t x = cov.luts[i].leaf[k];
+          if (x < (int32_t)NA && !st[cov.index[x]]) kids.push_back(cov.index[x]);
+        }
+        // the deepest child is finished first, so it is pushed last
+        std::sort(kids.begin(), kids.end(), [&](int32_t a, int32_t b) { return lev[a] < lev[b]; });
+        for (int32_t k : kids) stack.push_back({k, 0});
+      } else {
+        stack.pop_back();
+        if (st[i] == 1) {
+          st[i] = 2;
+          ord.push_back(cov.luts[i]);
+        }
+      }
+    }
+    cands.push_back(std::move(ord));
+  }
+  // (2) ascending variable order (the AIG's own topological order)
+  cands.push_back(cov.luts);
+  // (3) the order of the cone's slot program (the AIG order with the fewest slots)
+  if (!and_order.empty()) {
+    std::vector<LutCover::Lut> ord;
+    for (uint32_t i : and_order)
+      if (cov.index[i] >= 0) ord.push_back(cov.luts[cov.index[i]]);
+    cands.push_back(std::move(ord));
+  }
+  size_t bi = 0;
+  uint32_t bl = UINT32_MAX;
+  for (size_t i = 0; i < cands.size(); i++) {
+    const uint32_t l = live_of(cands[i]);
+    if (l < bl) { bl = l; bi = i; }
+  }
+  lp.order = std::move(cands[bi]);
+  lp.live = bl;
+}
+
 uint64_t fnv1a(const void *data, size_t len, uint64_t h) {
   const uint8_t *b = (const uint8_t *)data;
   for (size_t i = 0; i < len; i++) {
@@ -364,6 +475,13 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
   for (size_t k = 0; k < c.pis.size(); k++) best.support[k] = c.pis[k] - 1;
   best.cone_ands = (uint32_t)c.ands.size();
   best.out_compl = m.out_lit & 1;
+  {
+    // the AND positions (into the ascending cone list) of the chosen slot order
+    std::vector<uint32_t> and_order;
+    and_order.reserve(best.order_vars.size());
+    for (uint32_t var : best.order_vars) and_order.push_back((uint32_t)ix.and_pos(var));
+    build_lut_program(m, c, ix, root_var, and_order, best.lut);
+  }
   if (best.num_slots == 0) best.num_slots = 1;
   uint64_t h = 1469598103934665603ull;
   h = fnv1a(best.recs.data(), best.recs.size() * sizeof(Rec), h);

@@ -60,55 +60,34 @@ constexpr uint64_t kJitMinWork = 1ull << 34;  // AND-chunk evaluations that repa
 
 const char *kMask32[5] = {"0xAAAAAAAAu", "0xCCCCCCCCu", "0xF0F0F0F0u", "0xFF00FF00u", "0xFFFF0000u"};
 
-std::string gen_source(const Program &g) {
-  std::ostringstream s;
+// Kernel prologue / epilogue shared by both code forms.  Chunks are handed
+// out 32 at a time per warp from a counter (one grab ahead), so warps that
+// run faster take more and all finish together; a warp stops at the end of
+// the range, when its next chunk is not below the current counterexample, or
+// after max_grabs grabs (the server bounds block lifetimes this way).
+void emit_prologue(std::ostringstream &s) {
   s << "typedef unsigned int u32; typedef unsigned long long u64;\n"
        "extern \"C\" __global__ void __launch_bounds__("
     << kJitBlock
-    << ") es_jit(const u64 cb, const u64 ce, u64 *cex, u64 *evaluated) {\n"
-       "  const u64 T = (u64)gridDim.x * "
-    << kJitBlock
-    << ";\n"
+    << ") es_jit(const u64 cb, const u64 ce, u64 *cex, u64 *evaluated, u64 *next, const u64 max_grabs) {\n"
        "  const unsigned lane = threadIdx.x & 31u;\n"
        "  u64 done = 0;\n"
+       "  u64 mine = __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(next, 32ull) : 0ull, 0);\n"
        "  u64 cur = __shfl_sync(0xffffffffu, lane == 0 ? *(volatile u64 *)cex : 0ull, 0);\n"
-       "  for (u64 base = cb + (u64)blockIdx.x * "
-    << kJitBlock
-    << "; base < ce; base += T) {\n"
-       "    const u64 wfirst = base + (threadIdx.x & ~31u);\n"
-       "    if (wfirst * 32ull >= cur) break;\n"
+       "  for (u64 g = 1; ; g++) {\n"
+       "    const u64 wfirst = cb + mine;\n"
+       "    if (wfirst >= ce || wfirst * 32ull >= cur) break;\n"
+       "    const bool more = g < max_grabs;\n"
+       "    const u64 ahead = (lane == 0 && more) ? atomicAdd(next, 32ull) : ~0ull;\n"
        "    const u64 nxt = lane == 0 ? *(volatile u64 *)cex : 0ull;\n"
-       "    const u64 c = base + threadIdx.x;\n"
-       "    const u32 clo = (u32)c, chi = (u32)(c >> 32);\n";
-  // value names per slot, rebound as records execute
-  std::vector<std::string> slot(g.num_slots);
-  auto opnd = [&](uint32_t sl, bool neg) { return neg ? "~" + slot[sl] : slot[sl]; };
-  size_t i = 0;
-  for (const Rec &r : g.recs) {
-    if (r.op == OP_PI) {
-      const uint32_t k = r.a;
-      std::string nm = "p" + std::to_string(k);
-      if (k < 5) {
-        s << "    const u32 " << nm << " = " << kMask32[k] << ";\n";
-      } else if (k - 5 < 32) {
-        s << "    const u32 " << nm << " = 0u - ((clo >> " << (k - 5) << ") & 1u);\n";
-      } else {
-        s << "    const u32 " << nm << " = 0u - ((chi >> " << (k - 37) << ") & 1u);\n";
-      }
-      slot[r.dst] = nm;
-    } else if (r.op == OP_CONST0) {
-      slot[r.dst] = "0u";
-    } else {
-      std::string nm = "v" + std::to_string(i);
-      s << "    const u32 " << nm << " = " << opnd(r.a, r.op & 1) << " & " << opnd(r.b, (r.op >> 1) & 1)
-        << ";\n";
-      slot[r.dst] = nm;
-    }
-    i++;
-  }
-  const uint32_t vmask = g.n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << g.n)) - 1u);
-  s << "    u32 out = (" << (g.out_compl ? "~" : "") << slot[g.out_slot] << ") & 0x" << std::hex << vmask
-    << std::dec
+       "    const u64 c = wfirst + lane;\n"
+       "    const u32 clo = (u32)c, chi = (u32)(c >> 32);\n"
+       "    (void)chi;\n";
+}
+
+void emit_epilogue(std::ostringstream &s, const std::string &outv, bool compl_, uint32_t n) {
+  const uint32_t vmask = n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << n)) - 1u);
+  s << "    u32 out = (" << (compl_ ? "~" : "") << outv << ") & 0x" << std::hex << vmask << std::dec
     << "u;\n"
        "    if (c >= ce) out = 0u;\n"
        "    const unsigned bal = __ballot_sync(0xffffffffu, out != 0u);\n"
@@ -116,12 +95,121 @@ std::string gen_source(const Program &g) {
        "      if ((int)lane == __ffs(bal) - 1) atomicMin(cex, c * 32ull + (u64)(__ffs(out) - 1));\n"
        "    }\n"
        "    done += (c < ce) ? 1ull : 0ull;\n"
+       "    mine = __shfl_sync(0xffffffffu, ahead, 0);\n"
        "    cur = __shfl_sync(0xffffffffu, nxt, 0);\n"
+       "    if (!more) break;\n"
        "  }\n"
        "  for (int o = 16; o > 0; o >>= 1) done += __shfl_down_sync(0xffffffffu, done, o);\n"
        "  if (lane == 0 && done) atomicAdd(evaluated, done * 32ull);\n"
        "}\n";
+}
+
+std::string pi_expr(uint32_t k) {
+  if (k < 5) return kMask32[k];
+  if (k - 5 < 32) return "(0u - ((clo >> " + std::to_string(k - 5) + ") & 1u))";
+  return "(0u - ((chi >> " + std::to_string(k - 37) + ") & 1u))";
+}
+
+// AND form: one C expression per AND of the slot program; the compiler forms
+// its own 3-input LOP3s.
+std::string gen_source_and(const Program &g) {
+  std::ostringstream s;
+  emit_prologue(s);
+  std::vector<std::string> slot(g.num_slots);
+  auto opnd = [&](uint32_t sl, bool neg) { return neg ? "~" + slot[sl] : slot[sl]; };
+  size_t i = 0;
+  for (const Rec &r : g.recs) {
+    if (r.op == OP_PI) {
+      const std::string nm = "p" + std::to_string(r.a);
+      s << "    const u32 " << nm << " = " << pi_expr(r.a) << ";\n";
+      slot[r.dst] = nm;
+    } else if (r.op == OP_CONST0) {
+      slot[r.dst] = "0u";
+    } else {
+      const std::string nm = "v" + std::to_string(i);
+      s << "    const u32 " << nm << " = " << opnd(r.a, r.op & 1) << " & " << opnd(r.b, (r.op >> 1) & 1)
+        << ";\n";
+      slot[r.dst] = nm;
+    }
+    i++;
+  }
+  emit_epilogue(s, slot[g.out_slot], g.out_compl, g.n);
   return s.str();
+}
+
+// Table form: one lop3 per 3-input table of the cover, in the cover's
+// evaluation order; tables whose leaves are all constants (the constant and
+// PI masks 0..4) are folded here.
+std::string gen_source_lut(const Program &g) {
+  const LutProgram &lp = g.lut;
+  std::ostringstream s;
+  emit_prologue(s);
+  const uint32_t NA = lp.na, NP = lp.np;
+  const size_t NV = NA + NP + 1;
+  std::vector<std::string> name(NV);
+  std::vector<int8_t> isconst(NV, 0);
+  std::vector<uint32_t> cval(NV, 0);
+  std::vector<uint8_t> emitted(NV, 0);
+  static const uint32_t mask[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
+  for (uint32_t k = 0; k < NP; k++) {
+    name[NA + k] = "p" + std::to_string(k);
+    if (k < 5) {
+      isconst[NA + k] = 1;
+      cval[NA + k] = mask[k];
+    }
+  }
+  isconst[NA + NP] = 1;
+  cval[NA + NP] = 0;
+  auto operand = [&](int32_t id) -> std::string {
+    if (id < 0) return "0u";
+    if (isconst[id]) {
+      char b[16];
+      snprintf(b, sizeof(b), "0x%08xu", cval[id]);
+      return b;
+    }
+    if (id >= (int32_t)NA && !emitted[id]) {  // PI from the chunk index, at first use
+      s << "    const u32 " << name[id] << " = " << pi_expr((uint32_t)(id - NA)) << ";\n";
+      emitted[id] = 1;
+    }
+    return name[id];
+  };
+  for (const auto &l : lp.order) {
+    const int32_t v = l.node;
+    name[v] = "v" + std::to_string(v);
+    bool allc = true;
+    for (int k = 0; k < l.n; k++) allc = allc && isconst[l.leaf[k]];
+    if (allc) {
+      uint32_t x[3] = {0, 0, 0};
+      for (int k = 0; k < l.n; k++) x[k] = cval[l.leaf[k]];
+      uint32_t r = 0;
+      for (int b = 0; b < 32; b++) {
+        const int m = (int)((x[0] >> b) & 1) | (int)(((x[1] >> b) & 1) << 1) | (int)(((x[2] >> b) & 1) << 2);
+        r |= (uint32_t)((l.tt >> m) & 1) << b;
+      }
+      isconst[v] = 1;
+      cval[v] = r;
+      continue;
+    }
+    const std::string x0 = operand(l.leaf[0]), x1 = operand(l.n > 1 ? l.leaf[1] : -1),
+                      x2 = operand(l.n > 2 ? l.leaf[2] : -1);
+    char lut[8];
+    snprintf(lut, sizeof(lut), "0x%02x", l.tt);
+    // lop3 operands a, b, c carry the patterns 0xF0, 0xCC, 0xAA: (x2, x1, x0)
+    s << "    u32 " << name[v] << "; asm(\"lop3.b32 %0, %1, %2, %3, " << lut << ";\" : \"=r\"(" << name[v]
+      << ") : \"r\"(" << x2 << "), \"r\"(" << x1 << "), \"r\"(" << x0 << "));\n";
+  }
+  std::string outv;
+  if (lp.root < 0) {
+    outv = "0u";
+  } else {
+    outv = operand((int32_t)lp.root);
+  }
+  emit_epilogue(s, outv, g.out_compl, g.n);
+  return s.str();
+}
+
+std::string gen_source(const Program &g, bool lut_form) {
+  return lut_form && !g.lut.order.empty() ? gen_source_lut(g) : gen_source_and(g);
 }
 
 bool read_file(const std::string &path, std::vector<char> &out) {
@@ -182,20 +270,20 @@ uint32_t jit_auto_tier(lec_es_ctx *c, const Program &g, uint64_t chunks) {
 namespace {
 
 // Compile (or read from the disk cache) and load one program's kernel.
-int build_kernel(lec_es_ctx *c, const Program &g, JitKernel **out) {
+int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out) {
   const double t0 = now_ms();
   std::vector<char> cubin;
   std::string path;
   if (!c->jit_dir.empty()) {
     mkdir(c->jit_dir.c_str(), 0755);
     char name[64];
-    snprintf(name, sizeof(name), "/es_%016llx_sm%d%d.cubin", (unsigned long long)g.hash, c->cc_major,
-             c->cc_minor);
+    snprintf(name, sizeof(name), "/es_%016llx_%s_sm%d%d.cubin", (unsigned long long)g.hash,
+             lut_form ? "lut" : "and", c->cc_major, c->cc_minor);
     path = c->jit_dir + name;
   }
   if (path.empty() || !read_file(path, cubin)) {
     std::string log;
-    int rc = compile_cubin(gen_source(g), c->cc_major, c->cc_minor, cubin, log);
+    int rc = compile_cubin(gen_source(g, lut_form), c->cc_major, c->cc_minor, cubin, log);
     if (rc) {
       if (getenv("LEC_ES_JIT_LOG")) fprintf(stderr, "lec_es JIT failed:\n%s\n", log.c_str());
       return rc;
@@ -224,6 +312,8 @@ int build_kernel(lec_es_ctx *c, const Program &g, JitKernel **out) {
   return LEC_ES_OK;
 }
 
+uint64_t cache_key(const Program &g, bool lut_form) { return g.hash ^ (lut_form ? 0x9E3779B97F4A7C15ull : 0ull); }
+
 void worker_loop(lec_es_ctx *c) {
   JitState *js = c->jit;
   for (;;) {
@@ -236,9 +326,9 @@ void worker_loop(lec_es_ctx *c) {
       js->todo.pop_front();
     }
     JitKernel *k = nullptr;
-    int rc = build_kernel(c, g, &k);
+    int rc = build_kernel(c, g, true, &k);
     std::lock_guard<std::mutex> lk(js->mu);
-    if (rc == LEC_ES_OK) js->cache[g.hash] = k;
+    if (rc == LEC_ES_OK) js->cache[cache_key(g, true)] = k;
   }
 }
 
@@ -265,25 +355,26 @@ int jit_prepare(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt) {
   const Program &g = p->prog;
   JitState *js = state(c);
   JitKernel *k = nullptr;
+  const uint64_t key = cache_key(g, p->jit_lut);
   {
     std::lock_guard<std::mutex> lk(js->mu);
-    auto it = js->cache.find(g.hash);
+    auto it = js->cache.find(key);
     if (it != js->cache.end()) k = it->second;
   }
   if (k) {
     p->jit_ms = 0;
   } else {
-    int rc = build_kernel(c, g, &k);
+    int rc = build_kernel(c, g, p->jit_lut, &k);
     if (rc) return rc;
     p->jit_ms = k->compile_ms;
     std::lock_guard<std::mutex> lk(js->mu);
-    auto it = js->cache.find(g.hash);
+    auto it = js->cache.find(key);
     if (it != js->cache.end()) {  // raced with a background compile
       cudaLibraryUnload(k->lib);
       delete k;
       k = it->second;
     } else {
-      js->cache[g.hash] = k;
+      js->cache[key] = k;
     }
   }
   return jit_attach(c, p, k, opt);
@@ -292,10 +383,11 @@ int jit_prepare(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt) {
 JitKernel *jit_lookup_or_schedule(lec_es_ctx *c, const Program &g) {
   JitState *js = state(c);
   std::lock_guard<std::mutex> lk(js->mu);
-  auto it = js->cache.find(g.hash);
+  const uint64_t key = cache_key(g, true);
+  auto it = js->cache.find(key);
   if (it != js->cache.end()) return it->second;
-  if (!js->scheduled[g.hash]) {
-    js->scheduled[g.hash] = true;
+  if (!js->scheduled[key]) {
+    js->scheduled[key] = true;
     js->todo.push_back(g);
     if (js->workers.empty()) {
       const unsigned nw = std::max(1u, std::min(4u, std::thread::hardware_concurrency() / 2));
@@ -306,10 +398,11 @@ JitKernel *jit_lookup_or_schedule(lec_es_ctx *c, const Program &g) {
   return nullptr;
 }
 
-int jit_launch(lec_es_ctx *c, lec_es_plan *p, uint64_t chunk_begin, uint64_t chunk_end, int grid) {
+int jit_launch(lec_es_ctx *c, lec_es_plan *p, uint64_t chunk_begin, uint64_t chunk_end, int grid,
+               uint64_t max_grabs) {
   (void)c;
-  unsigned long long *cex = p->d_res, *evaluated = p->d_res + 1;
-  void *args[] = {&chunk_begin, &chunk_end, &cex, &evaluated};
+  unsigned long long *cex = p->d_res, *evaluated = p->d_res + 1, *next = p->d_res + 3;
+  void *args[] = {&chunk_begin, &chunk_end, &cex, &evaluated, &next, &max_grabs};
   const int g = grid > 0 ? grid : p->jit_grid;
   cudaError_t e = cudaLaunchKernel((const void *)p->jit->kern, dim3(g), dim3(p->jit_block), args, 0, p->stream);
   return e == cudaSuccess ? 0 : (int)e;
@@ -333,7 +426,7 @@ void jit_release_all(lec_es_ctx *c) {
 }
 
 // Source of the specialised kernel (no GPU needed).
-std::string jit_source_for(const Program &g) { return gen_source(g); }
+std::string jit_source_for(const Program &g) { return gen_source(g, true); }
 
 }  // namespace lec
 
@@ -346,7 +439,7 @@ extern "C" int lec_es_jit_compile(const lec_es_miter *m, int cc_major, int cc_mi
   if (rc) return rc;
   std::vector<char> cubin;
   std::string lg;
-  rc = lec::compile_cubin(lec::gen_source(g), cc_major, cc_minor, cubin, lg);
+  rc = lec::compile_cubin(lec::gen_source(g, true), cc_major, cc_minor, cubin, lg);
   if (log && log_cap) {
     const size_t n = std::min(log_cap - 1, lg.size());
     memcpy(log, lg.data(), n);

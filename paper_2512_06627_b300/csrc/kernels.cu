@@ -37,7 +37,8 @@ namespace lec {
 namespace {
 
 constexpr int NSTAGE = 4;
-constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr uint32_t kWaitLimit = 1u << 24;           // poll backstop
+constexpr uint64_t kWaitNs = 1000000000ull;         // a wait gives up after 1 s
 
 __constant__ uint32_t kMask32[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
 
@@ -81,10 +82,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: false after kWaitLimit unsuccessful polls.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait: false once 1 s of global time has passed (or after
+// kWaitLimit polls, whichever comes first).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
   for (uint32_t i = 0; i < kWaitLimit; i++) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 15u) == 15u && global_ns() - t0 > kWaitNs) return false;
     if (i > 64) __nanosleep(128);
   }
   return false;
@@ -166,7 +177,7 @@ __global__ void __launch_bounds__(T) es_interp(const InterpParams p) {
   const uint32_t nch = p.resident ? 1u : (p.nrec + p.ring_recs - 1) / p.ring_recs;
   if (p.resident) {
     if (t == 0) {
-      mbar_arrive_expect_tx(bar, p.nrec_padded * 8u);
+      mbar_arrive_expect_tx(bar, p.nrec_padded * 8u + p.extra_tx);
       bulk_g2s(ring, p.recs, p.nrec_padded * 8u, bar);
     }
     const bool ok = mbar_wait(bar, 0);
@@ -197,7 +208,7 @@ __global__ void __launch_bounds__(T) es_interp(const InterpParams p) {
         if (t == 0) {
           const uint32_t off = k * p.ring_recs;
           const uint32_t cnt = min(p.ring_recs, p.nrec_padded - off);
-          mbar_arrive_expect_tx(bar + k, cnt * 8u);
+          mbar_arrive_expect_tx(bar + k, cnt * 8u + (k == 0 ? p.extra_tx : 0u));
           bulk_g2s(ring + (size_t)k * p.ring_recs, p.recs + off, cnt * 8u, bar + k);
         }
         inflight |= 1u << k;

@@ -1,0 +1,230 @@
+// lutmap.cpp -- cover a cone with 3-input lookup tables (one LOP3 each).
+//
+// A 32-bit LOP3 computes any Boolean function of three 32-bit operands, so an
+// AND-inverter cone can be evaluated with fewer instructions than ANDs by
+// covering it with 3-input cuts: a full adder's sum and carry (nine ANDs in
+// an AIG) become two LOP3s.  This is the XOR/majority compaction the paper
+// obtains by converting the AIG to an XAG before instructionalising it (§2.1,
+// §3.3), generalised to every 3-feasible cut.  Results are the same Boolean
+// functions, so verdicts and counterexamples are unchanged.
+//
+// Method (standard cut-based technology mapping):
+//   cuts      every node gets its trivial cut {v} plus the merges of its
+//             fanins' cuts with at most three leaves (PIs, the constant or
+//             ANDs), each with its 8-bit truth table over the sorted leaves;
+//   selection area flow AF(v) = (1 + sum of AF(leaf) over the cut's AND
+//             leaves) / fanout(v), best cut per node, then two rounds of
+//             exact-area recovery against the current cover's references;
+//   cover     the output's node and, recursively, the AND leaves of every
+//             chosen cut.
+// Truth-table convention: leaf i of a cut is variable x_i with the patterns
+// x0 = 0xAA, x1 = 0xCC, x2 = 0xF0, so a table is also LOP3's immediate when
+// the operands are passed as (x2, x1, x0).
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "es_internal.h"
+
+namespace lec {
+
+namespace {
+
+struct Cut {
+  uint8_t n = 0;
+  int32_t leaf[3] = {-1, -1, -1};  // value ids, ascending
+  uint8_t tt = 0;
+};
+
+// Truth table of a function over cut `from`, re-expressed over the leaves of
+// `to` (from's leaves are a subset of to's).
+uint8_t expand(uint8_t tt, const Cut &from, const Cut &to) {
+  int pos[3] = {0, 0, 0};
+  for (int i = 0; i < from.n; i++)
+    for (int j = 0; j < to.n; j++)
+      if (to.leaf[j] == from.leaf[i]) pos[i] = j;
+  uint8_t out = 0;
+  for (int m = 0; m < 8; m++) {
+    int mm = 0;
+    for (int i = 0; i < from.n; i++) mm |= ((m >> pos[i]) & 1) << i;
+    out |= (uint8_t)(((tt >> mm) & 1) << m);
+  }
+  return out;
+}
+
+bool merge(const Cut &a, const Cut &b, Cut &out) {
+  int32_t l[6];
+  int n = 0, i = 0, j = 0;
+  while (i < a.n || j < b.n) {
+    int32_t x;
+    if (j >= b.n || (i < a.n && a.leaf[i] < b.leaf[j])) x = a.leaf[i++];
+    else if (i >= a.n || b.leaf[j] < a.leaf[i]) x = b.leaf[j++];
+    else { x = a.leaf[i++]; j++; }
+    if (n == 3) return false;
+    l[n++] = x;
+  }
+  out.n = (uint8_t)n;
+  for (int k = 0; k < 3; k++) out.leaf[k] = k < n ? l[k] : -1;
+  return true;
+}
+
+// Drop leaves the table does not depend on (keeps cuts minimal).
+void minimise(Cut &c) {
+  static const uint8_t var[3] = {0xAA, 0xCC, 0xF0};
+  for (int i = c.n - 1; i >= 0; i--) {
+    const int sh = 1 << i;
+    const uint8_t hi = c.tt & var[i], lo = (uint8_t)(c.tt & (uint8_t)~var[i]);
+    if ((uint8_t)(hi >> sh) == lo) {  // independent of x_i: remove it
+      Cut d;
+      d.n = (uint8_t)(c.n - 1);
+      int k = 0;
+      for (int q = 0; q < c.n; q++)
+        if (q != i) d.leaf[k++] = c.leaf[q];
+      uint8_t t = 0;
+      for (int m = 0; m < 8; m++) {
+        // minterm m over d -> insert a 0 bit at position i
+        const int low = m & ((1 << i) - 1), high = (m >> i) << (i + 1);
+        t |= (uint8_t)(((c.tt >> (low | high)) & 1) << m);
+      }
+      // tables over fewer leaves repeat; normalise to the 3-variable form
+      for (int m = 0; m < 8; m++) {
+        const int mm = m & ((1 << d.n) - 1);
+        t = (uint8_t)((t & ~(1 << m)) | (((t >> mm) & 1) << m));
+      }
+      d.tt = t;
+      c = d;
+    }
+  }
+}
+
+}  // namespace
+
+// values: ids 0..NA-1 are the cone's ANDs (ascending variable), NA..NA+NP-1
+// the support PIs, NA+NP the constant.  fanin value ids and complement bits
+// per AND come in f0/f1/c0/c1.
+void lut_map(size_t NA, size_t NP, const std::vector<int64_t> &f0, const std::vector<int64_t> &f1,
+             const std::vector<uint8_t> &c0, const std::vector<uint8_t> &c1, int64_t root, LutCover &out) {
+  const size_t NV = NA + NP + 1;
+  const int32_t CONST = (int32_t)(NA + NP);
+  std::vector<std::vector<Cut>> cuts(NV);
+  for (size_t v = NA; v < NV; v++) {
+    Cut t;
+    if ((int32_t)v == CONST) {
+      t.n = 0;
+      t.tt = 0x00;
+    } else {
+      t.n = 1;
+      t.leaf[0] = (int32_t)v;
+      t.tt = 0xAA;
+    }
+    cuts[v].push_back(t);
+  }
+  std::vector<uint32_t> fanout(NV, 0);
+  for (size_t i = 0; i < NA; i++) {
+    fanout[f0[i]]++;
+    fanout[f1[i]]++;
+  }
+  fanout[root]++;
+  std::vector<double> af(NV, 0.0);
+  std::vector<int> best(NV, -1);
+  const size_t kMaxCuts = 24;
+  for (size_t v = 0; v < NA; v++) {
+    std::vector<Cut> &cv = cuts[v];
+    for (const Cut &a : cuts[f0[v]]) {
+      for (const Cut &b : cuts[f1[v]]) {
+        Cut m;
+        if (!merge(a, b, m)) continue;
+        const uint8_t ta = (uint8_t)(expand(a.tt, a, m) ^ (c0[v] ? 0xFF : 0x00));
+        const uint8_t tb = (uint8_t)(expand(b.tt, b, m) ^ (c1[v] ? 0xFF : 0x00));
+        m.tt = ta & tb;
+        minimise(m);
+        bool dup = false;
+        for (const Cut &e : cv)
+          if (e.n == m.n && e.leaf[0] == m.leaf[0] && e.leaf[1] == m.leaf[1] && e.leaf[2] == m.leaf[2]) {
+            dup = true;
+            break;
+          }
+        if (!dup) cv.push_back(m);
+      }
+    }
+    // area flow of each cut; keep the best kMaxCuts (the trivial cut is added last)
+    auto flow = [&](const Cut &c) {
+      double s = 1.0;
+      for (int k = 0; k < c.n; k++)
+        if (c.leaf[k] < (int32_t)NA) s += af[c.leaf[k]];
+      return s;
+    };
+    std::stable_sort(cv.begin(), cv.end(), [&](const Cut &x, const Cut &y) {
+      const double fx = flow(x), fy = flow(y);
+      return fx < fy || (fx == fy && x.n < y.n);
+    });
+    if (cv.size() > kMaxCuts) cv.resize(kMaxCuts);
+    best[v] = 0;
+    af[v] = cv.empty() ? 1.0 : flow(cv[0]) / std::max<uint32_t>(1, fanout[v]);
+    Cut t;
+    t.n = 1;
+    t.leaf[0] = (int32_t)v;
+    t.tt = 0xAA;
+    cv.push_back(t);  // trivial cut: used only when v is a leaf of a parent's cut
+  }
+
+  // cover with reference counting, then exact-area recovery
+  std::vector<uint32_t> refs(NV, 0);
+  std::vector<uint8_t> used(NA, 0);
+  auto deref = [&](auto &&self, int32_t v) -> uint32_t {  // returns LUTs freed
+    if (v >= (int32_t)NA) return 0;
+    uint32_t freed = 1;
+    const Cut &c = cuts[v][best[v]];
+    for (int k = 0; k < c.n; k++)
+      if (c.leaf[k] < (int32_t)NA && --refs[c.leaf[k]] == 0) freed += self(self, c.leaf[k]);
+    return freed;
+  };
+  auto ref = [&](auto &&self, int32_t v) -> uint32_t {  // returns LUTs added
+    if (v >= (int32_t)NA) return 0;
+    uint32_t added = 1;
+    const Cut &c = cuts[v][best[v]];
+    for (int k = 0; k < c.n; k++)
+      if (c.leaf[k] < (int32_t)NA && refs[c.leaf[k]]++ == 0) added += self(self, c.leaf[k]);
+    return added;
+  };
+  if (root < (int64_t)NA) {
+    refs[root] = 1;
+    ref(ref, (int32_t)root);
+  }
+  for (int round = 0; round < 2; round++) {
+    for (size_t v = 0; v < NA; v++) {
+      if (refs[v] == 0) continue;
+      deref(deref, (int32_t)v);
+      uint32_t best_area = UINT32_MAX;
+      int best_i = best[v];
+      const int ncut = (int)cuts[v].size() - 1;  // skip the trivial cut
+      for (int i = 0; i < ncut; i++) {
+        best[v] = i;
+        const uint32_t a = ref(ref, (int32_t)v);
+        deref(deref, (int32_t)v);
+        if (a < best_area) {
+          best_area = a;
+          best_i = i;
+        }
+      }
+      best[v] = best_i;
+      ref(ref, (int32_t)v);
+    }
+  }
+  out.luts.clear();
+  out.index.assign(NA, -1);
+  for (size_t v = 0; v < NA; v++) {
+    if (refs[v] == 0) continue;
+    const Cut &c = cuts[v][best[v]];
+    LutCover::Lut l;
+    l.node = (int32_t)v;
+    l.n = c.n;
+    for (int k = 0; k < 3; k++) l.leaf[k] = c.leaf[k];
+    l.tt = c.tt;
+    out.index[v] = (int32_t)out.luts.size();
+    out.luts.push_back(l);
+  }
+}
+
+}  // namespace lec

@@ -47,7 +47,7 @@ constexpr int kStreams = 8;                    // half high priority, half low
 constexpr uint64_t kSmallWork = 1ull << 33;    // record x chunk products below this are "small"
 
 struct Slot {
-  unsigned long long *d_res = nullptr;  // [cex, evaluated, status, spare]
+  unsigned long long *d_res = nullptr;  // kResWords result words
   unsigned long long *h_res = nullptr;  // pinned
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   bool busy = false;
@@ -155,15 +155,17 @@ int launch(Server *s, Request *r) {
     }
     res = &it->second;
   }
-  if (cudaMemcpyAsync(sl.d_res, c->h_init, 32, cudaMemcpyHostToDevice, st) != cudaSuccess) return LEC_ES_ECUDA;
+  if (cudaMemcpyAsync(sl.d_res, c->h_init, kResWords * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return LEC_ES_ECUDA;
   cudaEventRecord(sl.e0, st);
   int err;
   if (k) {
-    // a few chunks per thread, so blocks retire and other requests interleave
-    uint64_t cb = 0, ce = C;
-    unsigned long long *cex = sl.d_res, *ev = sl.d_res + 1;
-    void *args[] = {&cb, &ce, &cex, &ev};
-    const uint64_t per_block = (uint64_t)k->block * 8;
+    // each warp grabs at most 8 times, so blocks retire and other requests
+    // interleave; enough blocks that the grabs cover every chunk
+    uint64_t cb = 0, ce = C, grabs = 8;
+    unsigned long long *cex = sl.d_res, *ev = sl.d_res + 1, *next = sl.d_res + 3;
+    void *args[] = {&cb, &ce, &cex, &ev, &next, &grabs};
+    const uint64_t per_block = (uint64_t)(k->block / 32) * 32 * grabs;
     const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>((C + per_block - 1) / per_block, 1u << 30));
     err = cudaLaunchKernel((const void *)k->kern, dim3((unsigned)grid), dim3(k->block), args, 0, st) ==
                   cudaSuccess
@@ -193,7 +195,7 @@ int launch(Server *s, Request *r) {
   }
   if (err) return LEC_ES_ECUDA;
   cudaEventRecord(sl.e1, st);
-  cudaMemcpyAsync(sl.h_res, sl.d_res, 32, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(sl.h_res, sl.d_res, kResWords * 8, cudaMemcpyDeviceToHost, st);
   cudaEventRecord(sl.e2, st);
   sl.busy = true;
   r->slot = si;
@@ -329,9 +331,9 @@ int ensure_server(lec_es_ctx *c) {
   *s->h_zero = 0;
   s->slots.resize(c->max_inflight);
   for (Slot &sl : s->slots) {
-    sl.d_res = (unsigned long long *)c->arena.alloc(32);
+    sl.d_res = (unsigned long long *)c->arena.alloc(kResWords * 8);
     if (!sl.d_res) return LEC_ES_ENOMEM;
-    if (cudaMallocHost((void **)&sl.h_res, 32) != cudaSuccess) return LEC_ES_ENOMEM;
+    if (cudaMallocHost((void **)&sl.h_res, kResWords * 8) != cudaSuccess) return LEC_ES_ENOMEM;
     if (cudaEventCreate(&sl.e0) != cudaSuccess || cudaEventCreate(&sl.e1) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.e2, cudaEventDisableTiming) != cudaSuccess)
       return LEC_ES_ECUDA;

@@ -67,7 +67,7 @@ class lec_es_result(ctypes.Structure):
 class lec_es_options(ctypes.Structure):
     _fields_ = [("word_begin", ctypes.c_uint64), ("word_end", ctypes.c_uint64), ("tier", ctypes.c_uint32),
                 ("order", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
-                ("grid_blocks", ctypes.c_uint32)]
+                ("grid_blocks", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
 
 
 class lec_es_config(ctypes.Structure):
@@ -79,7 +79,8 @@ class lec_es_config(ctypes.Structure):
 class lec_es_program_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint32), ("support", ctypes.c_uint32 * 64), ("cone_ands", ctypes.c_uint32),
                 ("num_slots", ctypes.c_uint32), ("out_slot", ctypes.c_uint32), ("out_compl", ctypes.c_uint32),
-                ("order", ctypes.c_uint32), ("num_records", ctypes.c_uint64), ("hash", ctypes.c_uint64)]
+                ("order", ctypes.c_uint32), ("num_records", ctypes.c_uint64), ("hash", ctypes.c_uint64),
+                ("num_luts", ctypes.c_uint32), ("lut_live", ctypes.c_uint32)]
 
 
 _lib: Optional[ctypes.CDLL] = None
@@ -166,9 +167,12 @@ def miter_of(aig, out_lit: Optional[int] = None) -> Miter:
     return Miter(aig.num_pis, aig.flat_fanins(), aig.outputs[0] if out_lit is None else out_lit)
 
 
+FLAG_JIT_AND_FORM, FLAG_TEST_WAIT_TIMEOUT = 1, 2
+
+
 def options(word_begin: int = 0, word_end: int = NO_CEX, tier: int = TIER_AUTO, order: int = ORDER_AUTO,
-            block_threads: int = 0, grid_blocks: int = 0) -> lec_es_options:
-    return lec_es_options(word_begin, word_end, tier, order, block_threads, grid_blocks)
+            block_threads: int = 0, grid_blocks: int = 0, flags: int = 0) -> lec_es_options:
+    return lec_es_options(word_begin, word_end, tier, order, block_threads, grid_blocks, flags)
 
 
 # ---- entry points (same names as the C ABI) -------------------------------------

@@ -84,3 +84,25 @@ def test_disk_cache_roundtrip(tmp_path):
         assert r.cex_or_none == oracle_cex(aig, out)
         L.lec_es_destroy(c)
     assert any(p.suffix == ".cubin" for p in tmp_path.iterdir())
+
+
+def test_and_form_and_table_form_agree(ctx):
+    for aig in (C.config2_mult12(1), C.config2_mult12(), C.config1_adders(2)):
+        m = L.miter_of(aig)
+        a = L.lec_es_check_ex(ctx, m, L.options(tier=L.TIER_JIT, flags=L.FLAG_JIT_AND_FORM))
+        b = L.lec_es_check_ex(ctx, m, L.options(tier=L.TIER_JIT))
+        assert a.cex == b.cex == (oracle_cex(aig, aig.outputs[0]) if oracle_cex(aig, aig.outputs[0]) is not None
+                                  else L.NO_CEX)
+
+
+def test_grid_sizes_and_grab_balance(ctx):
+    """Tiny grids (a few warps grab everything) and the default grid agree."""
+    mm = C.config2_mult12(mutant_seed=3)
+    m = L.miter_of(mm)
+    ref = oracle_cex(mm, mm.outputs[0])
+    for grid in (1, 3, 0):
+        r = L.lec_es_check_ex(ctx, m, L.options(tier=L.TIER_JIT, grid_blocks=grid))
+        assert r.cex_or_none == ref
+    eq = C.config2_mult12()
+    r = L.lec_es_check_ex(ctx, L.miter_of(eq), L.options(tier=L.TIER_JIT, grid_blocks=2))
+    assert r.verdict == L.EQUIVALENT

@@ -159,3 +159,20 @@ def test_config3_sampled_ranges_vs_oracle(ctx):
 def test_lop3_peak_measures(ctx):
     per_clk, sms, khz, rate = L.lec_es_lop3_peak(ctx)
     assert sms >= 100 and 16 <= per_clk <= 300 and 500_000 < khz < 3_000_000
+
+
+def test_bounded_wait_gives_up_and_context_survives(ctx):
+    """Test hook: the interpreter waits for 16 bytes its record copy never
+    delivers; the bounded wait must give up (about a second), the call must
+    return EDEVICE_WAIT, and the context must keep working."""
+    import time
+    mm = C.config1_adders(mutant_seed=1)
+    m = L.miter_of(mm)
+    t0 = time.time()
+    with pytest.raises(L.LecEsError) as e:
+        L.lec_es_check_ex(ctx, m, L.options(tier=L.TIER_INTERP, grid_blocks=1,
+                                            flags=L.FLAG_TEST_WAIT_TIMEOUT))
+    assert e.value.status == L.EDEVICE_WAIT
+    assert time.time() - t0 < 15
+    r = L.lec_es_check_ex(ctx, m, L.options(tier=L.TIER_INTERP))
+    assert r.cex_or_none == _oracle(mm, mm.outputs[0])[0]
