@@ -47,8 +47,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-pairs", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=3)
-    ap.add_argument("--serve-requests", type=int, default=48)
-    ap.add_argument("--serve-rate", type=float, default=6.0)
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-load", type=float, default=0.7)
     return ap.parse_args()
 
 
@@ -183,9 +183,11 @@ def cpu_oracle_rate(aig, seconds: float):
 # ---------------------------------------------------------------------------
 
 def measure_batch(ctx, args):
-    """4096 node-pair miters: one persistent launch (CUDA-graph replay) vs one
-    launch per miter (back to back on one stream, one sync; and with a sync
-    after every miter), same interpreter kernel family, identical results."""
+    """4096 node-pair miters: one prepared batch (CUDA-graph replay: the heavy
+    miters' specialised kernels, then the persistent tile-queue kernel for the
+    rest) vs one launch per miter with the same kernel for each miter (back to
+    back on one stream with one sync at the end; and with a sync after every
+    miter).  Identical results are asserted."""
     import numpy as np
     import torch
     from paper_2512_06627_b300 import circuits as C
@@ -198,7 +200,9 @@ def measure_batch(ctx, args):
     b = L.lec_es_batch_prepare(ctx, ms)
     prep = time.perf_counter() - t0
     L.lec_es_batch_run_async(ctx, b)
-    ref = [r.cex for r in L.lec_es_batch_results(ctx, b, k)]
+    first = L.lec_es_batch_results(ctx, b, k)
+    ref = [r.cex for r in first]
+    tiers = [int(r.tier) for r in first]
     infos = [L.lec_es_compile(m)[0] for m in ms]
     work = np.array([float(i.num_records) * float(max(1, 1 << max(0, i.n - 5))) for i in infos])
     ts = []
@@ -211,87 +215,107 @@ def measure_batch(ctx, args):
         assert got == ref
     L.lec_es_batch_free(ctx, b)
     batched = k / statistics.median(ts)
-    plans = [L.lec_es_prepare(ctx, m, L.options(tier=L.TIER_INTERP)) for m in ms]
-    # (i) back to back on one stream, one sync at the end
-    t0 = time.perf_counter()
-    for p in plans:
-        L.lec_es_run_async(ctx, p)
-    torch.cuda.synchronize()
-    one_async_s = time.perf_counter() - t0
-    # the plan results come from each plan's own read-back
-    got = [L.lec_es_plan_result(ctx, p).cex for p in plans]
-    assert got == ref
-    # (ii) a sync after every miter
-    t0 = time.perf_counter()
-    for p in plans:
-        L.lec_es_run_async(ctx, p)
-        L.lec_es_plan_result(ctx, p)
-    one_sync_s = time.perf_counter() - t0
+    plans = [L.lec_es_prepare(ctx, m, L.options(tier=t)) for m, t in zip(ms, tiers)]
+    one_async, one_sync = [], []
+    for _ in range(2):
+        # (i) back to back on one stream, one sync at the end
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for p in plans:
+            L.lec_es_run_async(ctx, p)
+        torch.cuda.synchronize()
+        one_async.append(time.perf_counter() - t0)
+        got = [L.lec_es_plan_result(ctx, p).cex for p in plans]
+        assert got == ref
+        # (ii) a sync after every miter
+        t0 = time.perf_counter()
+        for p in plans:
+            L.lec_es_run_async(ctx, p)
+            L.lec_es_plan_result(ctx, p)
+        one_sync.append(time.perf_counter() - t0)
     for p in plans:
         L.lec_es_plan_free(ctx, p)
+    a_s, s_s = min(one_async), min(one_sync)
     big = work >= np.sort(work)[-max(1, k // 100)]
     return {
         "pairs": k, "nonequivalent": int(sum(1 for x in ref if x != L.NO_CEX)),
         "support_pis": {"min": int(min(i.n for i in infos)), "max": int(max(i.n for i in infos))},
         "cone_ands": {"min": int(min(i.cone_ands for i in infos)), "max": int(max(i.cone_ands for i in infos))},
-        "batched_miters_per_s": batched,
-        "one_launch_per_miter_async_miters_per_s": k / one_async_s,
-        "one_launch_per_miter_sync_miters_per_s": k / one_sync_s,
-        "speedup_vs_async": batched / (k / one_async_s),
-        "speedup_vs_sync": batched / (k / one_sync_s),
+        "jit_miters": int(sum(1 for t in tiers if t == L.TIER_JIT)),
+        "batched_miters_per_s": batched, "batched_ms": statistics.median(ts) * 1e3,
+        "one_launch_per_miter_async_miters_per_s": k / a_s,
+        "one_launch_per_miter_sync_miters_per_s": k / s_s,
+        "speedup_vs_async": batched / (k / a_s),
+        "speedup_vs_sync": batched / (k / s_s),
         "work_share_top_1pct": float(work[big].sum() / work.sum()),
         "prepare_s": prep,
     }
 
 
 def measure_serve(ctx, args):
-    """A seeded Poisson stream of product-bit miter requests (w x w array vs
-    Booth, w in 8..18): submitted at their arrival times through the
-    continuous-batching server; p50/p99 latency and miters/s, against the
-    same requests one launch each."""
+    """Seeded product-bit miter requests (w x w array vs Booth, w in 8..18,
+    bit in [w-1, 2w-1], 1% mutants) through the continuous-batching server:
+    capacity with every request queued at once, then a Poisson stream at
+    --serve-load of that capacity for p50/p99 latency; against the same
+    requests one lec_es_check each.  Every result equals the request alone."""
     import numpy as np
     from paper_2512_06627_b300 import circuits as C
     from paper_2512_06627_b300 import lec_es as L
-    reqs = C.config5_stream(num_requests=max(1, args.serve_requests), rate_per_s=args.serve_rate)
+    R = max(1, args.serve_requests)
+    base = C.config5_stream(num_requests=R, rate_per_s=1.0)
     pm = C.ProductBitMiters(seed=5)
     ms = []
-    for i, r in enumerate(reqs):
+    for i, r in enumerate(base):
         aig, out = pm.miter(r.w, r.bit, r.mutant, mutant_seed=i)
         ms.append(L.Miter(aig.num_pis, aig.flat_fanins(), out))
-    # warm the specialised-kernel cache for every distinct program (reported)
+    # compile the specialised kernels of the distinct programs (parallel, reported)
     t0 = time.perf_counter()
-    seen = set()
+    seen, uniq = set(), []
     for m in ms:
-        info, _ = L.lec_es_compile(m)
-        if info.hash in seen:
-            continue
-        seen.add(info.hash)
-        p = L.lec_es_prepare(ctx, m)
-        L.lec_es_plan_free(ctx, p)
+        h = L.lec_es_compile(m)[0].hash
+        if h not in seen:
+            seen.add(h)
+            uniq.append(m)
+    b = L.lec_es_batch_prepare(ctx, uniq)
+    L.lec_es_batch_free(ctx, b)
     warm_s = time.perf_counter() - t0
     # one launch per request, sequential
+    for m in ms[:4]:
+        L.lec_es_check(ctx, m)
     t0 = time.perf_counter()
     alone = [L.lec_es_check(ctx, m).cex for m in ms]
     one_s = time.perf_counter() - t0
-    # served
+    # capacity: every request submitted at once
+    t0 = time.perf_counter()
+    tk = [L.lec_es_submit(ctx, m) for m in ms]
+    res = [L.lec_es_wait(ctx, t, 3600.0) for t in tk]
+    cap_s = time.perf_counter() - t0
+    assert [r.cex for r in res] == alone
+    capacity = R / cap_s
+    # Poisson arrivals at a fraction of capacity
+    rate = args.serve_load * capacity
+    reqs = C.config5_stream(num_requests=R, rate_per_s=rate)
     start = time.perf_counter()
-    tickets = []
+    tk = []
     for r, m in zip(reqs, ms):
         dt = r.arrival_s - (time.perf_counter() - start)
         if dt > 0:
             time.sleep(dt)
-        tickets.append(L.lec_es_submit(ctx, m))
-    res = [L.lec_es_wait(ctx, t, 3600.0) for t in tickets]
+        tk.append(L.lec_es_submit(ctx, m))
+    res = [L.lec_es_wait(ctx, t, 3600.0) for t in tk]
     span = time.perf_counter() - start
     assert [r.cex for r in res] == alone
     lat = np.array([r.latency_ms for r in res])
     return {
-        "requests": len(ms), "rate_per_s": args.serve_rate, "distinct_programs": len(seen),
-        "widths": sorted(set(r.w for r in reqs)), "mutants": int(sum(r.mutant for r in reqs)),
+        "requests": R, "distinct_programs": len(uniq), "widths": sorted(set(r.w for r in base)),
+        "mutants": int(sum(r.mutant for r in base)),
+        "served_capacity_miters_per_s": capacity,
+        "one_launch_each_miters_per_s": R / one_s,
+        "speedup_vs_one_launch_each": capacity / (R / one_s),
+        "poisson_rate_per_s": rate, "poisson_load": args.serve_load,
         "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
-        "served_miters_per_s": len(ms) / span, "one_launch_each_miters_per_s": len(ms) / one_s,
-        "offered_span_s": reqs[-1].arrival_s, "jit_warmup_s": warm_s,
-        "results_equal_alone": True,
+        "poisson_miters_per_s": R / span,
+        "jit_warmup_s": warm_s, "results_equal_alone": True,
     }
 
 

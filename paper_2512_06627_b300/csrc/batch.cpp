@@ -29,9 +29,19 @@
 
 using namespace lec;
 
+namespace {
+constexpr double kBatchJitWork = 5e7;   // records x chunks: about 50 us in the interpreter
+constexpr uint32_t kBatchJitLive = 230; // table live set that still fits the register file
+}  // namespace
+
 struct lec_es_batch_plan {
   size_t k = 0;
   std::vector<Program> progs;
+  std::vector<int> jit_of;                // miter -> index into jit_miters, or -1
+  std::vector<uint32_t> jit_miters;       // miters run by their own specialised kernel
+  std::vector<JitKernel *> jit_kernels;
+  unsigned long long *d_aux = nullptr;    // per JIT miter: {patterns evaluated, chunk-grab counter}
+  double jit_ms = 0;
   std::vector<int> fallback_of;           // miter -> index into fallbacks, or -1
   std::vector<lec_es_plan *> fallbacks;   // miters whose live set exceeds the batch kernel's slots
   int block = 0, grid = 0;
@@ -67,6 +77,7 @@ void batch_release(lec_es_ctx *c, lec_es_batch_plan *b) {
   c->arena.free(b->d_tiles);
   c->arena.free(b->d_cex);
   c->arena.free(b->d_head);
+  c->arena.free(b->d_aux);
   for (lec_es_plan *p : b->fallbacks) plan_release(c, p);
   delete b;
 }
@@ -134,6 +145,37 @@ extern "C" int lec_es_batch_prepare(lec_es_ctx *c, const lec_es_miter *m, size_t
   b->grid = c->sm_count * bps;
   if (opt && opt->grid_blocks) b->grid = (int)opt->grid_blocks;
 
+  // heavy miters (interpreter cost above ~50 us) get their own specialised
+  // kernel, compiled in parallel here and launched inside the same graph
+  b->jit_of.assign(k, -1);
+  const bool allow_jit = !(opt && (opt->tier == LEC_ES_TIER_INTERP || opt->tier == LEC_ES_TIER_SPILL));
+  if (allow_jit) {
+    for (size_t i = 0; i < k; i++) {
+      const Program &g = b->progs[i];
+      const double work = (double)g.recs.size() * (double)num_chunks(g.n);
+      if (work >= kBatchJitWork && !g.lut.order.empty() && g.lut.live <= kBatchJitLive) {
+        b->jit_of[i] = (int)b->jit_miters.size();
+        b->jit_miters.push_back((uint32_t)i);
+      }
+    }
+    b->jit_kernels.assign(b->jit_miters.size(), nullptr);
+    std::vector<int> jrc(b->jit_miters.size(), LEC_ES_OK);
+    const double tj = now_ms();
+    const unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), 16u));
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; t++) {
+      th.emplace_back([&, t]() {
+        cudaSetDevice(c->device);
+        for (size_t j = t; j < b->jit_miters.size(); j += nt)
+          jrc[j] = jit_get_kernel(c, b->progs[b->jit_miters[j]], true, &b->jit_kernels[j], nullptr);
+      });
+    }
+    for (auto &x : th) x.join();
+    b->jit_ms = now_ms() - tj;
+    for (int r : jrc)
+      if (r) return r;
+  }
+
   // pack programs
   std::vector<BatchMiter> mt(k);
   size_t total_recs = 0;
@@ -158,7 +200,7 @@ extern "C" int lec_es_batch_prepare(lec_es_ctx *c, const lec_es_miter *m, size_t
   double total_cost = 0;
   std::vector<size_t> idx;
   for (size_t i = 0; i < k; i++) {
-    if (slots[i] > ms) continue;
+    if (slots[i] > ms || b->jit_of[i] >= 0) continue;
     idx.push_back(i);
     total_cost += (double)mt[i].nrec * (double)num_chunks(mt[i].n);
   }
@@ -185,7 +227,7 @@ extern "C" int lec_es_batch_prepare(lec_es_ctx *c, const lec_es_miter *m, size_t
 
   // miters too wide for the batch kernel: their own spill-tier plans
   for (size_t i = 0; i < k; i++) {
-    if (slots[i] <= ms) continue;
+    if (slots[i] <= ms || b->jit_of[i] >= 0) continue;
     lec_es_options o{};
     o.word_end = UINT64_MAX;
     o.tier = LEC_ES_TIER_SPILL;
@@ -204,7 +246,8 @@ extern "C" int lec_es_batch_prepare(lec_es_ctx *c, const lec_es_miter *m, size_t
   b->d_tiles = c->arena.alloc(std::max<size_t>(16, tiles.size() * sizeof(BatchTile)));
   b->d_cex = (unsigned long long *)c->arena.alloc(k * 8);
   b->d_head = (uint32_t *)c->arena.alloc(16);
-  if (!b->d_recs || !b->d_miters || !b->d_tiles || !b->d_cex || !b->d_head) {
+  b->d_aux = (unsigned long long *)c->arena.alloc(std::max<size_t>(16, b->jit_miters.size() * 16));
+  if (!b->d_recs || !b->d_miters || !b->d_tiles || !b->d_cex || !b->d_head || !b->d_aux) {
     batch_release(c, b.release());
     return LEC_ES_ENOMEM;
   }
@@ -247,7 +290,22 @@ extern "C" int lec_es_batch_prepare(lec_es_ctx *c, const lec_es_miter *m, size_t
   if (e == cudaSuccess) {
     cudaMemsetAsync(b->d_cex, 0xFF, k * 8, st);
     cudaMemsetAsync(b->d_head, 0, 16, st);
-    if (b->num_tiles) lerr = launch_batch(bp, b->block, b->grid, b->smem, st);
+    if (!b->jit_miters.empty()) cudaMemsetAsync(b->d_aux, 0, b->jit_miters.size() * 16, st);
+    // heavy miters first, each over the whole GPU, then the tile queue
+    for (size_t j = 0; j < b->jit_miters.size() && !lerr; j++) {
+      const uint32_t i = b->jit_miters[j];
+      JitKernel *kk = b->jit_kernels[j];
+      uint64_t cb = 0, ce = num_chunks(b->progs[i].n), grabs = ~0ull;
+      unsigned long long *cex = b->d_cex + i, *ev = b->d_aux + 2 * j, *next = b->d_aux + 2 * j + 1;
+      void *args[] = {&cb, &ce, &cex, &ev, &next, &grabs};
+      const uint64_t warps_needed = (ce + 31) / 32;
+      const uint64_t grid = std::max<uint64_t>(
+          1, std::min<uint64_t>((uint64_t)c->sm_count * kk->blocks_per_sm, (warps_needed * 32 + kk->block - 1) / kk->block));
+      if (cudaLaunchKernel((const void *)kk->kern, dim3((unsigned)grid), dim3(kk->block), args, 0, st) !=
+          cudaSuccess)
+        lerr = 1;
+    }
+    if (b->num_tiles && !lerr) lerr = launch_batch(bp, b->block, b->grid, b->smem, st);
     cudaMemcpyAsync(b->h_cex, b->d_cex, k * 8, cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(b->h_status, b->d_head, 16, cudaMemcpyDeviceToHost, st);
     e = cudaStreamEndCapture(st, &b->graph);
@@ -297,11 +355,12 @@ extern "C" int lec_es_batch_results(lec_es_ctx *c, lec_es_batch_plan *b, lec_es_
     for (uint32_t q = 0; q < g.n; q++) r.support[q] = g.support[q];
     r.cone_ands = g.cone_ands;
     r.num_slots = g.num_slots;
-    r.tier = LEC_ES_TIER_INTERP;
+    r.tier = b->jit_of[i] >= 0 ? LEC_ES_TIER_JIT : LEC_ES_TIER_INTERP;
     r.order = g.order;
     r.words_checked = num_words(g.n);
     r.device_ms = ms;
     r.host_ms = b->host_ms / (double)k;
+    r.jit_ms = b->jit_ms / (double)k;
     r.cex = b->h_cex[i];
     r.verdict = r.cex == UINT64_MAX ? LEC_ES_EQUIVALENT : LEC_ES_NONEQUIVALENT;
   }

@@ -64,6 +64,8 @@ int jit_launch(lec_es_ctx *c, lec_es_plan *p, uint64_t chunk_begin, uint64_t chu
 // schedules a background compile (once per program) and returns nullptr.
 lec::JitKernel *jit_lookup_or_schedule(lec_es_ctx *c, const Program &g);
 int jit_attach(lec_es_ctx *c, lec_es_plan *p, JitKernel *k, const lec_es_options *opt);
+// Cached kernel for a program (compiled on a miss; thread-safe).
+int jit_get_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out, double *compile_ms);
 void jit_release_all(lec_es_ctx *c);
 
 // single-miter plans (api.cpp)

@@ -55,8 +55,9 @@ struct JitState {
 namespace {
 
 constexpr int kJitBlock = 128;
-constexpr uint32_t kMaxJitSlots = 240;   // beyond this the register file spills
-constexpr uint64_t kJitMinWork = 1ull << 34;  // AND-chunk evaluations that repay a compile
+constexpr uint32_t kMaxJitLive = 230;        // table live set that still fits the register file
+constexpr double kJitCachedWork = 5e7;       // records x chunks: ~50 us in the interpreter
+constexpr double kJitColdWork = 1e11;        // ~0.1 s in the interpreter: repays a compile
 
 const char *kMask32[5] = {"0xAAAAAAAAu", "0xCCCCCCCCu", "0xF0F0F0F0u", "0xFF00FF00u", "0xFFFF0000u"};
 
@@ -260,11 +261,19 @@ int compile_cubin(const std::string &src, int major, int minor, std::vector<char
 
 }  // namespace
 
+uint64_t cache_key(const Program &g, bool lut_form);
+JitState *state(lec_es_ctx *c);
+
+// The specialised kernel once it is compiled (in memory or on disk) wins above
+// a few tens of microseconds of interpreter time; a cold compile (0.1-1 s)
+// pays off only for large work.
 uint32_t jit_auto_tier(lec_es_ctx *c, const Program &g, uint64_t chunks) {
-  (void)c;
-  const uint64_t work = (uint64_t)g.recs.size() * chunks;
-  if (g.num_slots <= kMaxJitSlots && work >= kJitMinWork) return LEC_ES_TIER_JIT;
-  return LEC_ES_TIER_INTERP;
+  const double work = (double)g.recs.size() * (double)chunks;
+  if (g.lut.order.empty() || g.lut.live > kMaxJitLive || work < kJitCachedWork) return LEC_ES_TIER_INTERP;
+  if (work >= kJitColdWork) return LEC_ES_TIER_JIT;
+  JitState *js = state(c);
+  std::lock_guard<std::mutex> lk(js->mu);
+  return js->cache.count(cache_key(g, true)) ? LEC_ES_TIER_JIT : LEC_ES_TIER_INTERP;
 }
 
 namespace {
@@ -312,8 +321,6 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   return LEC_ES_OK;
 }
 
-uint64_t cache_key(const Program &g, bool lut_form) { return g.hash ^ (lut_form ? 0x9E3779B97F4A7C15ull : 0ull); }
-
 void worker_loop(lec_es_ctx *c) {
   JitState *js = c->jit;
   for (;;) {
@@ -332,12 +339,45 @@ void worker_loop(lec_es_ctx *c) {
   }
 }
 
+}  // namespace
+
+uint64_t cache_key(const Program &g, bool lut_form) { return g.hash ^ (lut_form ? 0x9E3779B97F4A7C15ull : 0ull); }
+
 JitState *state(lec_es_ctx *c) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> g(mu);
   if (!c->jit) c->jit = new JitState();
   return c->jit;
 }
 
-}  // namespace
+int jit_get_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out, double *compile_ms) {
+  JitState *js = state(c);
+  const uint64_t key = cache_key(g, lut_form);
+  {
+    std::lock_guard<std::mutex> lk(js->mu);
+    auto it = js->cache.find(key);
+    if (it != js->cache.end()) {
+      *out = it->second;
+      if (compile_ms) *compile_ms = 0;
+      return LEC_ES_OK;
+    }
+  }
+  JitKernel *k = nullptr;
+  int rc = build_kernel(c, g, lut_form, &k);
+  if (rc) return rc;
+  if (compile_ms) *compile_ms = k->compile_ms;
+  std::lock_guard<std::mutex> lk(js->mu);
+  auto it = js->cache.find(key);
+  if (it != js->cache.end()) {  // another thread built it first
+    cudaLibraryUnload(k->lib);
+    delete k;
+    k = it->second;
+  } else {
+    js->cache[key] = k;
+  }
+  *out = k;
+  return LEC_ES_OK;
+}
 
 int jit_attach(lec_es_ctx *c, lec_es_plan *p, JitKernel *k, const lec_es_options *opt) {
   const Program &g = p->prog;
@@ -354,29 +394,10 @@ int jit_attach(lec_es_ctx *c, lec_es_plan *p, JitKernel *k, const lec_es_options
 int jit_prepare(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt) {
   const Program &g = p->prog;
   JitState *js = state(c);
+  (void)js;
   JitKernel *k = nullptr;
-  const uint64_t key = cache_key(g, p->jit_lut);
-  {
-    std::lock_guard<std::mutex> lk(js->mu);
-    auto it = js->cache.find(key);
-    if (it != js->cache.end()) k = it->second;
-  }
-  if (k) {
-    p->jit_ms = 0;
-  } else {
-    int rc = build_kernel(c, g, p->jit_lut, &k);
-    if (rc) return rc;
-    p->jit_ms = k->compile_ms;
-    std::lock_guard<std::mutex> lk(js->mu);
-    auto it = js->cache.find(key);
-    if (it != js->cache.end()) {  // raced with a background compile
-      cudaLibraryUnload(k->lib);
-      delete k;
-      k = it->second;
-    } else {
-      js->cache[key] = k;
-    }
-  }
+  int rc = jit_get_kernel(c, g, p->jit_lut, &k, &p->jit_ms);
+  if (rc) return rc;
   return jit_attach(c, p, k, opt);
 }
 
