@@ -70,7 +70,7 @@ enum {
 
 /* Evaluation orders for the slot compiler (all give identical results). */
 enum {
-  LEC_ES_ORDER_AUTO = 0,    /* the one with the fewest value slots */
+  LEC_ES_ORDER_AUTO = 0,    /* the fewer value slots of DFS and VAR */
   LEC_ES_ORDER_DFS = 1,     /* post-order from the output, deeper fanin first */
   LEC_ES_ORDER_VAR = 2,     /* ascending variable index */
   LEC_ES_ORDER_LEVEL = 3,   /* by logic level, then variable */

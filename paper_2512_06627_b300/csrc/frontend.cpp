@@ -78,15 +78,30 @@ int extract_cone(const MiterView &m, std::vector<uint8_t> &mark, Cone &c) {
   return LEC_ES_OK;
 }
 
-// Dense index of a cone variable: position in ands (ANDs) via binary search.
+// Dense index of the cone's variables: value id of every cone variable
+// (ANDs 0..NA-1 in ascending order, PIs NA.., the constant last), in a
+// per-thread array over the whole graph that is reset when the cone is done,
+// so many cones of one large graph cost only their own size.
 struct ConeIndex {
   const Cone &c;
-  explicit ConeIndex(const Cone &cc) : c(cc) {}
-  int64_t and_pos(uint32_t v) const {
-    auto it = std::lower_bound(c.ands.begin(), c.ands.end(), v);
-    if (it == c.ands.end() || *it != v) return -1;
-    return it - c.ands.begin();
+  std::vector<int32_t> &id;  // variable -> value id, -1 outside the cone
+  ConeIndex(const Cone &cc, std::vector<int32_t> &map, uint64_t maxvar) : c(cc), id(map) {
+    if (id.size() < maxvar + 1) id.resize(maxvar + 1, -1);
+    const size_t NA = c.ands.size(), NP = c.pis.size();
+    for (size_t i = 0; i < NA; i++) id[c.ands[i]] = (int32_t)i;
+    for (size_t k = 0; k < NP; k++) id[c.pis[k]] = (int32_t)(NA + k);
+    id[0] = (int32_t)(NA + NP);
   }
+  ~ConeIndex() {
+    for (uint32_t v : c.ands) id[v] = -1;
+    for (uint32_t v : c.pis) id[v] = -1;
+    id[0] = -1;
+  }
+  int64_t and_pos(uint32_t v) const {
+    const int32_t x = id[v];
+    return x >= 0 && (size_t)x < c.ands.size() ? x : -1;
+  }
+  int64_t vid(uint32_t v) const { return id[v]; }
 };
 
 void order_levels(const MiterView &m, const Cone &c, const ConeIndex &ix, std::vector<uint32_t> &level) {
@@ -157,14 +172,7 @@ void order_greedy(const MiterView &m, const Cone &c, const ConeIndex &ix, uint32
                   std::vector<uint32_t> &ord) {
   const size_t NA = c.ands.size(), NP = c.pis.size();
   const size_t NV = NA + NP + 1;
-  auto vid = [&](uint32_t var) -> int64_t {
-    if (var == 0) return (int64_t)(NA + NP);
-    if (var <= m.num_pis) {
-      auto it = std::lower_bound(c.pis.begin(), c.pis.end(), var);
-      return (int64_t)(NA + (it - c.pis.begin()));
-    }
-    return ix.and_pos(var);
-  };
+  auto vid = [&](uint32_t var) -> int64_t { return ix.vid(var); };
   std::vector<int64_t> f0(NA), f1(NA);
   std::vector<uint32_t> refs(NV, 0), pending(NA, 0);
   std::vector<std::vector<uint32_t>> users(NV);
@@ -241,14 +249,7 @@ int assign_slots(const MiterView &m, const Cone &c, const ConeIndex &ix, const s
   const size_t NA = c.ands.size(), NP = c.pis.size();
   // value ids: [0, NA) ANDs, [NA, NA+NP) PIs, NA+NP the constant
   const size_t NV = NA + NP + 1;
-  auto vid = [&](uint32_t var) -> int64_t {
-    if (var == 0) return (int64_t)(NA + NP);
-    if (var <= m.num_pis) {
-      auto it = std::lower_bound(c.pis.begin(), c.pis.end(), var);
-      return (int64_t)(NA + (it - c.pis.begin()));
-    }
-    return ix.and_pos(var);
-  };
+  auto vid = [&](uint32_t var) -> int64_t { return ix.vid(var); };
   std::vector<uint32_t> refs(NV, 0);
   std::vector<int64_t> f0v(NA), f1v(NA);
   for (size_t i = 0; i < NA; i++) {
@@ -319,14 +320,7 @@ int assign_slots(const MiterView &m, const Cone &c, const ConeIndex &ix, const s
 void build_lut_program(const MiterView &m, const Cone &c, const ConeIndex &ix, uint32_t root_var,
                        const std::vector<uint32_t> &and_order, LutProgram &lp) {
   const size_t NA = c.ands.size(), NP = c.pis.size();
-  auto vid = [&](uint32_t var) -> int64_t {
-    if (var == 0) return (int64_t)(NA + NP);
-    if (var <= m.num_pis) {
-      auto it = std::lower_bound(c.pis.begin(), c.pis.end(), var);
-      return (int64_t)(NA + (it - c.pis.begin()));
-    }
-    return ix.and_pos(var);
-  };
+  auto vid = [&](uint32_t var) -> int64_t { return ix.vid(var); };
   std::vector<int64_t> f0(NA), f1(NA);
   std::vector<uint8_t> c0(NA), c1(NA);
   for (size_t i = 0; i < NA; i++) {
@@ -437,18 +431,21 @@ uint64_t fnv1a(const void *data, size_t len, uint64_t h) {
 
 int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Program &out) {
   thread_local std::vector<uint8_t> mark;
+  thread_local std::vector<int32_t> dense;
   Cone c;
   int rc = extract_cone(m, mark, c);
   if (rc) return rc;
   if (c.pis.size() > max_pis || c.pis.size() > 63) return LEC_ES_ETOOBIG;
-  ConeIndex ix(c);
+  ConeIndex ix(c, dense, (uint64_t)m.num_pis + m.num_ands);
   const uint32_t root_var = m.out_lit >> 1;
   std::vector<uint32_t> level;
   order_levels(m, c, ix, level);
 
-  const uint32_t cands_auto[4] = {LEC_ES_ORDER_DFS, LEC_ES_ORDER_VAR, LEC_ES_ORDER_LEVEL, LEC_ES_ORDER_GREEDY};
+  // level and greedy orders never beat these two on datapath cones; they stay
+  // available on request
+  const uint32_t cands_auto[2] = {LEC_ES_ORDER_DFS, LEC_ES_ORDER_VAR};
   std::vector<uint32_t> tried;
-  if (order == LEC_ES_ORDER_AUTO) tried.assign(cands_auto, cands_auto + 4);
+  if (order == LEC_ES_ORDER_AUTO) tried.assign(cands_auto, cands_auto + 2);
   else if (order <= LEC_ES_ORDER_GREEDY) tried.push_back(order);
   else return LEC_ES_EINVAL;
 

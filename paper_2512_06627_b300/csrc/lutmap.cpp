@@ -37,20 +37,39 @@ struct Cut {
   uint8_t tt = 0;
 };
 
+// Re-expressing a table over a superset of its leaves depends only on where
+// each old leaf lands (3 positions of 0..2 and the old leaf count): 108
+// placements x 256 tables, computed once.
+struct ExpandTable {
+  uint8_t t[4 * 27][256];
+  ExpandTable() {
+    for (int n = 0; n <= 3; n++)
+      for (int code = 0; code < 27; code++) {
+        const int pos[3] = {code % 3, (code / 3) % 3, code / 9};
+        for (int tt = 0; tt < 256; tt++) {
+          uint8_t out = 0;
+          for (int m = 0; m < 8; m++) {
+            int mm = 0;
+            for (int i = 0; i < n; i++) mm |= ((m >> pos[i]) & 1) << i;
+            out |= (uint8_t)(((tt >> mm) & 1) << m);
+          }
+          t[n * 27 + code][tt] = out;
+        }
+      }
+  }
+};
+const ExpandTable kExpand;
+
 // Truth table of a function over cut `from`, re-expressed over the leaves of
 // `to` (from's leaves are a subset of to's).
-uint8_t expand(uint8_t tt, const Cut &from, const Cut &to) {
-  int pos[3] = {0, 0, 0};
-  for (int i = 0; i < from.n; i++)
-    for (int j = 0; j < to.n; j++)
-      if (to.leaf[j] == from.leaf[i]) pos[i] = j;
-  uint8_t out = 0;
-  for (int m = 0; m < 8; m++) {
-    int mm = 0;
-    for (int i = 0; i < from.n; i++) mm |= ((m >> pos[i]) & 1) << i;
-    out |= (uint8_t)(((tt >> mm) & 1) << m);
+inline uint8_t expand(uint8_t tt, const Cut &from, const Cut &to) {
+  int code = 0, mul = 1;
+  for (int i = 0; i < from.n; i++, mul *= 3) {
+    int j = 0;
+    while (to.leaf[j] != from.leaf[i]) j++;
+    code += j * mul;
   }
-  return out;
+  return kExpand.t[from.n * 27 + code][tt];
 }
 
 bool merge(const Cut &a, const Cut &b, Cut &out) {
@@ -128,7 +147,7 @@ void lut_map(size_t NA, size_t NP, const std::vector<int64_t> &f0, const std::ve
   fanout[root]++;
   std::vector<double> af(NV, 0.0);
   std::vector<int> best(NV, -1);
-  const size_t kMaxCuts = 24;
+  const size_t kMaxCuts = 8;
   for (size_t v = 0; v < NA; v++) {
     std::vector<Cut> &cv = cuts[v];
     for (const Cut &a : cuts[f0[v]]) {
