@@ -197,8 +197,9 @@ def measure_batch(ctx, args):
     ms = [L.Miter(pb.aig.num_pis, f, o) for o in pb.aig.outputs]
     k = len(ms)
     t0 = time.perf_counter()
-    b = L.lec_es_batch_prepare(ctx, ms)
+    b = L.lec_es_batch_prepare(ctx, ms, L.options(flags=L.FLAG_AUTOTUNE))
     prep = time.perf_counter() - t0
+    layout = L.lec_es_batch_info(b)
     L.lec_es_batch_run_async(ctx, b)
     first = L.lec_es_batch_results(ctx, b, k)
     ref = [r.cex for r in first]
@@ -248,7 +249,10 @@ def measure_batch(ctx, args):
         "speedup_vs_async": batched / (k / a_s),
         "speedup_vs_sync": batched / (k / s_s),
         "work_share_top_1pct": float(work[big].sum() / work.sum()),
-        "prepare_s": prep,
+        "prepare_s": prep, "jit_compile_s": layout.jit_ms / 1e3, "autotune_s": layout.tune_ms / 1e3,
+        "layout": {"tile_miters": layout.tile_miters, "tiles": layout.tiles,
+                   "threads_per_tile_pass": layout.block_threads, "tiles_per_block_slot": layout.tile_granularity,
+                   "stage_records": layout.stage_records, "grid_blocks": layout.grid_blocks},
     }
 
 

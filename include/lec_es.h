@@ -112,16 +112,22 @@ typedef struct {
   uint32_t block_threads;   /* 0 = library choice */
   uint32_t grid_blocks;     /* 0 = library choice */
   uint32_t flags;           /* LEC_ES_FLAG_* */
+  uint32_t tile_granularity;/* batch: tiles per resident block slot (0 = 16) */
+  uint32_t stage_records;   /* batch: records per staging stage, even, <= 4096 (0 = 512) */
 } lec_es_options;
 
 /* Option flags. */
 enum {
   LEC_ES_FLAG_JIT_AND_FORM = 1u,     /* JIT tier: one C expression per AND, fused by the
                                         compiler, instead of the 3-input table cover */
-  LEC_ES_FLAG_TEST_WAIT_TIMEOUT = 2u /* test hook (interpreter tier): the kernel waits for
+  LEC_ES_FLAG_TEST_WAIT_TIMEOUT = 2u,/* test hook (interpreter tier): the kernel waits for
                                         16 bytes more than its record copy delivers, so
                                         its bounded wait must give up and the call must
                                         return LEC_ES_EDEVICE_WAIT */
+  LEC_ES_FLAG_AUTOTUNE = 4u          /* batch: time candidate layouts (threads per tile
+                                        pass x tiles per block slot x staging depth) on
+                                        the tile queue and keep the fastest; cached per
+                                        batch shape (and in jit_cache_dir) */
 };
 
 typedef struct {
@@ -246,6 +252,22 @@ int lec_es_batch(lec_es_ctx *c, const lec_es_miter *m, size_t k, lec_es_result *
  * (the launch sequence is captured in a CUDA graph and replayed). */
 int lec_es_batch_prepare(lec_es_ctx *c, const lec_es_miter *m, size_t k,
                          const lec_es_options *opt, lec_es_batch_plan **out);
+/* Layout a prepared batch ended up with. */
+typedef struct {
+  uint32_t miters;          /* k */
+  uint32_t jit_miters;      /* run by their own specialised kernel */
+  uint32_t tile_miters;     /* run by the persistent tile-queue kernel */
+  uint32_t fallback_miters; /* live set beyond shared memory: global-memory plans */
+  uint32_t tiles;           /* (miter, chunk range) tiles in the queue */
+  uint32_t block_threads;   /* threads per tile pass */
+  uint32_t stage_records;   /* records per staging stage */
+  uint32_t tile_granularity;/* tiles per resident block slot */
+  uint32_t grid_blocks;     /* persistent blocks */
+  double prepare_ms;        /* whole preparation */
+  double jit_ms;            /* of which compiling specialised kernels */
+  double tune_ms;           /* of which timing candidate layouts */
+} lec_es_batch_layout;
+int lec_es_batch_info(const lec_es_batch_plan *b, lec_es_batch_layout *info);
 int lec_es_batch_run_async(lec_es_ctx *c, lec_es_batch_plan *b);
 int lec_es_batch_results(lec_es_ctx *c, lec_es_batch_plan *b, lec_es_result *out, size_t k);
 void lec_es_batch_free(lec_es_ctx *c, lec_es_batch_plan *b);

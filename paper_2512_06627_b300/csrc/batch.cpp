@@ -1,25 +1,40 @@
-// batch.cpp -- many miters in one persistent launch.
+// batch.cpp -- many miters in one launch sequence, replayed as a CUDA graph.
 //
 // Sub-miters of the kind a sweeping scheduler hands to exact simulation
 // (paper §3.2: one sub-miter per signal pair; ES cost grows with 2^PIs and
 // linearly with gates) are uneven: a few PIs and tens of ANDs up to ~30 PIs
 // and thousands of ANDs.  One launch per miter leaves the GPU idle on the
-// small ones.  Here every miter's slot program is packed into one record
-// arena, its pattern space is cut into (miter, chunk range) tiles whose sizes
-// follow cost_ES = ANDs x 2^PIs, and a persistent kernel with one block per
-// resident slot pulls tiles from a global queue head with atomicAdd.  Tiles of
-// a miter are queued in ascending pattern order, so a counterexample found
-// early lets the remaining tiles of that miter skip (the minimum is kept
-// exact: a tile is skipped only when its first pattern is not below it).
-// The reset-launch-readback sequence is captured once in a CUDA graph and
-// replayed by every run.
+// small ones.  Preparation has two stages:
+//   programs  every miter is compiled (front end, 16 host threads); miters
+//             whose interpreter cost exceeds ~50 us get their specialised
+//             kernel (compiled in parallel); the others' slot programs are
+//             packed into one record arena;
+//   layout    the light miters' pattern spaces are cut into (miter, chunk
+//             range) tiles sized by cost_ES = records x chunks; a persistent
+//             kernel pulls tiles from a queue head with atomicAdd; the graph
+//             forks into branches so the specialised kernels overlap each
+//             other and the tile queue.
+// Tiles of a miter are queued in ascending pattern order, so a counterexample
+// found early lets the remaining tiles skip (a tile is skipped only when its
+// first pattern is not below the current minimum, so the minimum is exact).
+// The layout's tunables -- threads per tile pass, tiles per resident block
+// (how many 32-pattern words a thread takes per tile) and records per staging
+// stage -- can be chosen by timing candidate layouts of the tile queue
+// (LEC_ES_FLAG_AUTOTUNE); choices are cached per batch shape in memory and in
+// the context's cache directory.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
+#include <fstream>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <new>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -30,8 +45,15 @@
 using namespace lec;
 
 namespace {
-constexpr double kBatchJitWork = 5e7;   // records x chunks: about 50 us in the interpreter
-constexpr uint32_t kBatchJitLive = 230; // table live set that still fits the register file
+constexpr double kBatchJitWork = 5e7;    // records x chunks: about 50 us in the interpreter
+constexpr uint32_t kBatchJitLive = 230;  // table live set that still fits the register file
+constexpr int kBranches = 4;             // parallel graph branches
+
+struct Layout {
+  int block = 256;            // threads per tile pass
+  uint32_t ring_recs = 512;   // records per staging stage (4 stages)
+  uint32_t granularity = 16;  // tiles per resident block slot
+};
 }  // namespace
 
 struct lec_es_batch_plan {
@@ -40,36 +62,54 @@ struct lec_es_batch_plan {
   std::vector<int> jit_of;                // miter -> index into jit_miters, or -1
   std::vector<uint32_t> jit_miters;       // miters run by their own specialised kernel
   std::vector<JitKernel *> jit_kernels;
-  unsigned long long *d_aux = nullptr;    // per JIT miter: {patterns evaluated, chunk-grab counter}
-  double jit_ms = 0;
   std::vector<int> fallback_of;           // miter -> index into fallbacks, or -1
-  std::vector<lec_es_plan *> fallbacks;   // miters whose live set exceeds the batch kernel's slots
-  int block = 0, grid = 0;
+  std::vector<lec_es_plan *> fallbacks;   // live sets beyond the tile kernel's shared memory
+  std::vector<BatchMiter> mt;
+  std::vector<size_t> light;              // miters of the tile queue
+  uint32_t max_slots = 1;
+  Layout layout;
+  int grid = 0;
   size_t smem = 0;
-  uint32_t ring_recs = 512;
-  uint32_t max_slots = 0;
   uint32_t num_tiles = 0;
   void *d_recs = nullptr, *d_miters = nullptr, *d_tiles = nullptr;
+  size_t tiles_cap = 0;
   unsigned long long *d_cex = nullptr;
   uint32_t *d_head = nullptr;             // [head, status]
+  unsigned long long *d_aux = nullptr;    // per specialised miter: {patterns evaluated, grab counter}
   unsigned long long *h_cex = nullptr;    // pinned
   uint32_t *h_status = nullptr;           // pinned
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaStream_t side[kBranches] = {};
+  cudaEvent_t fork = nullptr, join[kBranches] = {};
   bool pending = false;
-  double host_ms = 0;
+  double host_ms = 0, jit_ms = 0, tune_ms = 0;
   BatchParams params{};
 };
 
 namespace {
 
-void batch_release(lec_es_ctx *c, lec_es_batch_plan *b) {
-  if (!b) return;
+std::mutex g_tune_mu;
+std::map<std::string, std::map<uint64_t, Layout>> g_tuned;  // cache file -> shape -> layout
+
+void release_graph(lec_es_batch_plan *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+void batch_release(lec_es_ctx *c, lec_es_batch_plan *b) {
+  if (!b) return;
+  release_graph(b);
   if (b->e0) cudaEventDestroy(b->e0);
   if (b->e1) cudaEventDestroy(b->e1);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (int i = 0; i < kBranches; i++) {
+    if (b->join[i]) cudaEventDestroy(b->join[i]);
+    if (b->side[i]) cudaStreamDestroy(b->side[i]);
+  }
   if (b->h_cex) cudaFreeHost(b->h_cex);
   if (b->h_status) cudaFreeHost(b->h_status);
   c->arena.free(b->d_recs);
@@ -105,129 +145,50 @@ int compile_all(lec_es_ctx *c, const lec_es_miter *m, size_t k, uint32_t order, 
   return LEC_ES_OK;
 }
 
-}  // namespace
-
-extern "C" int lec_es_batch_prepare(lec_es_ctx *c, const lec_es_miter *m, size_t k, const lec_es_options *opt,
-                                    lec_es_batch_plan **out) {
-  if (!c || !m || !out || k == 0 || k > 0xFFFFFFFFull) return LEC_ES_EINVAL;
-  *out = nullptr;
-  const double t0 = now_ms();
-  std::unique_ptr<lec_es_batch_plan> b(new (std::nothrow) lec_es_batch_plan());
-  if (!b) return LEC_ES_ENOMEM;
-  b->k = k;
+// Stage 1: programs, specialised kernels, fallbacks, packed records, buffers.
+int stage_programs(lec_es_ctx *c, lec_es_batch_plan *b, const lec_es_miter *m, size_t k,
+                   const lec_es_options *opt) {
   int rc = compile_all(c, m, k, opt ? opt->order : LEC_ES_ORDER_AUTO, b->progs);
   if (rc) return rc;
   if (cudaSetDevice(c->device) != cudaSuccess) return LEC_ES_ECUDA;
-
-  // block size: the largest that holds the batch's largest live set in shared
-  // memory; miters beyond what a 64-thread block holds run on their own
-  std::vector<uint32_t> slots(k);
-  for (size_t i = 0; i < k; i++) slots[i] = b->progs[i].num_slots;
-  const int pref = opt && opt->block_threads ? (int)opt->block_threads : 256;
-  uint32_t max_fit64 = (uint32_t)((c->smem_optin - 64 - 4 * 512 * 8) / (64 * 4));
-  b->fallback_of.assign(k, -1);
-  uint32_t ms = 1;
-  for (size_t i = 0; i < k; i++)
-    if (slots[i] <= max_fit64) ms = std::max(ms, slots[i]);
-  b->max_slots = ms;
-  b->block = 0;
-  for (int blk : {256, 128, 64}) {
-    if (blk > pref) continue;
-    if (batch_smem_bytes(ms, blk, b->ring_recs) <= (size_t)c->smem_optin) {
-      b->block = blk;
-      break;
-    }
-  }
-  if (!b->block) b->block = 64;
-  b->smem = batch_smem_bytes(ms, b->block, b->ring_recs);
-  if (configure_batch(b->block, b->smem) != 0) return LEC_ES_ECUDA;
-  const int bps = std::max(1, batch_blocks_per_sm(b->block, b->smem));
-  b->grid = c->sm_count * bps;
-  if (opt && opt->grid_blocks) b->grid = (int)opt->grid_blocks;
-
-  // heavy miters (interpreter cost above ~50 us) get their own specialised
-  // kernel, compiled in parallel here and launched inside the same graph
+  // live sets the tile kernel holds in shared memory at 64 threads per block
+  const uint32_t max_fit64 = (uint32_t)((c->smem_optin - 64 - 4 * 1024 * 8) / (64 * 4));
   b->jit_of.assign(k, -1);
+  b->fallback_of.assign(k, -1);
   const bool allow_jit = !(opt && (opt->tier == LEC_ES_TIER_INTERP || opt->tier == LEC_ES_TIER_SPILL));
-  if (allow_jit) {
-    for (size_t i = 0; i < k; i++) {
-      const Program &g = b->progs[i];
-      const double work = (double)g.recs.size() * (double)num_chunks(g.n);
-      if (work >= kBatchJitWork && !g.lut.order.empty() && g.lut.live <= kBatchJitLive) {
-        b->jit_of[i] = (int)b->jit_miters.size();
-        b->jit_miters.push_back((uint32_t)i);
-      }
-    }
-    b->jit_kernels.assign(b->jit_miters.size(), nullptr);
-    std::vector<int> jrc(b->jit_miters.size(), LEC_ES_OK);
-    const double tj = now_ms();
-    const unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), 16u));
-    std::vector<std::thread> th;
-    for (unsigned t = 0; t < nt; t++) {
-      th.emplace_back([&, t]() {
-        cudaSetDevice(c->device);
-        for (size_t j = t; j < b->jit_miters.size(); j += nt)
-          jrc[j] = jit_get_kernel(c, b->progs[b->jit_miters[j]], true, &b->jit_kernels[j], nullptr);
-      });
-    }
-    for (auto &x : th) x.join();
-    b->jit_ms = now_ms() - tj;
-    for (int r : jrc)
-      if (r) return r;
-  }
-
-  // pack programs
-  std::vector<BatchMiter> mt(k);
-  size_t total_recs = 0;
   for (size_t i = 0; i < k; i++) {
-    const size_t np = std::max<size_t>(2, (b->progs[i].recs.size() + 1) & ~(size_t)1);
-    mt[i].rec_off = (uint32_t)total_recs;
-    mt[i].nrec = (uint32_t)b->progs[i].recs.size();
-    mt[i].nrec_padded = (uint32_t)np;
-    mt[i].nslots = b->progs[i].num_slots;
-    mt[i].out_slot = b->progs[i].out_slot;
-    mt[i].out_compl = b->progs[i].out_compl;
-    mt[i].n = b->progs[i].n;
-    total_recs += np;
-  }
-  if (total_recs > 0xFFFFFFFFull) return LEC_ES_ETOOBIG;
-  std::vector<Rec> arena_recs(total_recs);
-  for (size_t i = 0; i < k; i++)
-    memcpy(&arena_recs[mt[i].rec_off], b->progs[i].recs.data(), b->progs[i].recs.size() * sizeof(Rec));
-
-  // tiles sized by cost_ES (records x chunks), big miters first, each miter's
-  // tiles in ascending pattern order
-  double total_cost = 0;
-  std::vector<size_t> idx;
-  for (size_t i = 0; i < k; i++) {
-    if (slots[i] > ms || b->jit_of[i] >= 0) continue;
-    idx.push_back(i);
-    total_cost += (double)mt[i].nrec * (double)num_chunks(mt[i].n);
-  }
-  std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
-    return (double)mt[x].nrec * num_chunks(mt[x].n) > (double)mt[y].nrec * num_chunks(mt[y].n);
-  });
-  const double target = std::max(1.0, total_cost / ((double)b->grid * 16.0));
-  std::vector<BatchTile> tiles;
-  for (size_t i : idx) {
-    const uint64_t C = num_chunks(mt[i].n);
-    uint64_t tc = (uint64_t)(target / std::max<uint32_t>(1, mt[i].nrec));
-    tc = ((tc + b->block - 1) / b->block) * b->block;
-    tc = std::max<uint64_t>(tc, (uint64_t)b->block);
-    for (uint64_t c0 = 0; c0 < C; c0 += tc) {
-      BatchTile t{};
-      t.miter = (uint32_t)i;
-      t.chunk_begin = c0;
-      t.chunk_end = std::min(C, c0 + tc);
-      tiles.push_back(t);
+    const Program &g = b->progs[i];
+    const double work = (double)g.recs.size() * (double)num_chunks(g.n);
+    if (allow_jit && work >= kBatchJitWork && !g.lut.order.empty() && g.lut.live <= kBatchJitLive) {
+      b->jit_of[i] = (int)b->jit_miters.size();
+      b->jit_miters.push_back((uint32_t)i);
+    } else if (g.num_slots > max_fit64) {
+      b->fallback_of[i] = 0;  // index assigned below
+    } else {
+      b->light.push_back(i);
+      b->max_slots = std::max(b->max_slots, g.num_slots);
     }
   }
-  if (tiles.size() > 0xFFFFFFF0ull) return LEC_ES_ETOOBIG;
-  b->num_tiles = (uint32_t)tiles.size();
-
-  // miters too wide for the batch kernel: their own spill-tier plans
+  // specialised kernels, compiled in parallel
+  b->jit_kernels.assign(b->jit_miters.size(), nullptr);
+  std::vector<int> jrc(b->jit_miters.size(), LEC_ES_OK);
+  const double tj = now_ms();
+  const unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), 16u));
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt && !b->jit_miters.empty(); t++) {
+    th.emplace_back([&, t]() {
+      cudaSetDevice(c->device);
+      for (size_t j = t; j < b->jit_miters.size(); j += nt)
+        jrc[j] = jit_get_kernel(c, b->progs[b->jit_miters[j]], true, &b->jit_kernels[j], nullptr);
+    });
+  }
+  for (auto &x : th) x.join();
+  b->jit_ms = now_ms() - tj;
+  for (int r : jrc)
+    if (r) return r;
+  // fallbacks: their own global-memory plans
   for (size_t i = 0; i < k; i++) {
-    if (slots[i] <= ms || b->jit_of[i] >= 0) continue;
+    if (b->fallback_of[i] < 0) continue;
     lec_es_options o{};
     o.word_end = UINT64_MAX;
     o.tier = LEC_ES_TIER_SPILL;
@@ -238,84 +199,285 @@ extern "C" int lec_es_batch_prepare(lec_es_ctx *c, const lec_es_miter *m, size_t
     b->fallback_of[i] = (int)b->fallbacks.size();
     b->fallbacks.push_back(p);
   }
-
-  // device buffers
-  const size_t rb = std::max<size_t>(16, arena_recs.size() * sizeof(Rec));
-  b->d_recs = c->arena.alloc(rb);
+  // pack the light programs
+  b->mt.assign(k, BatchMiter{});
+  size_t total = 0;
+  for (size_t i : b->light) {
+    const Program &g = b->progs[i];
+    const size_t np = std::max<size_t>(2, (g.recs.size() + 1) & ~(size_t)1);
+    BatchMiter &x = b->mt[i];
+    x.rec_off = (uint32_t)total;
+    x.nrec = (uint32_t)g.recs.size();
+    x.nrec_padded = (uint32_t)np;
+    x.nslots = g.num_slots;
+    x.out_slot = g.out_slot;
+    x.out_compl = g.out_compl;
+    x.n = g.n;
+    total += np;
+  }
+  if (total > 0xFFFFFFFFull) return LEC_ES_ETOOBIG;
+  std::vector<Rec> arena(std::max<size_t>(2, total));
+  for (size_t i : b->light)
+    memcpy(&arena[b->mt[i].rec_off], b->progs[i].recs.data(), b->progs[i].recs.size() * sizeof(Rec));
+  b->d_recs = c->arena.alloc(arena.size() * sizeof(Rec));
   b->d_miters = c->arena.alloc(std::max<size_t>(16, k * sizeof(BatchMiter)));
-  b->d_tiles = c->arena.alloc(std::max<size_t>(16, tiles.size() * sizeof(BatchTile)));
   b->d_cex = (unsigned long long *)c->arena.alloc(k * 8);
   b->d_head = (uint32_t *)c->arena.alloc(16);
   b->d_aux = (unsigned long long *)c->arena.alloc(std::max<size_t>(16, b->jit_miters.size() * 16));
-  if (!b->d_recs || !b->d_miters || !b->d_tiles || !b->d_cex || !b->d_head || !b->d_aux) {
-    batch_release(c, b.release());
-    return LEC_ES_ENOMEM;
-  }
+  if (!b->d_recs || !b->d_miters || !b->d_cex || !b->d_head || !b->d_aux) return LEC_ES_ENOMEM;
   if (cudaMallocHost((void **)&b->h_cex, k * 8) != cudaSuccess ||
-      cudaMallocHost((void **)&b->h_status, 16) != cudaSuccess) {
-    batch_release(c, b.release());
+      cudaMallocHost((void **)&b->h_status, 16) != cudaSuccess)
     return LEC_ES_ENOMEM;
+  cudaStream_t st = c->stream;
+  cudaError_t e = cudaMemcpyAsync(b->d_recs, arena.data(), arena.size() * sizeof(Rec), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_miters, b->mt.data(), k * sizeof(BatchMiter), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return LEC_ES_ECUDA;
+  if (cudaEventCreate(&b->e0) != cudaSuccess || cudaEventCreate(&b->e1) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+    return LEC_ES_ECUDA;
+  for (int i = 0; i < kBranches; i++)
+    if (cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess)
+      return LEC_ES_ECUDA;
+  return LEC_ES_OK;
+}
+
+// Stage 2: tiles, kernel geometry and the captured graph for one layout.
+// With light_only the graph holds just the tile queue (for timing layouts).
+int stage_layout(lec_es_ctx *c, lec_es_batch_plan *b, const Layout &L, int grid_override, bool light_only) {
+  release_graph(b);
+  b->layout = L;
+  b->smem = batch_smem_bytes(b->max_slots, L.block, L.ring_recs);
+  if (b->smem > (size_t)c->smem_optin) return LEC_ES_ETOOBIG;
+  if (configure_batch(L.block, b->smem) != 0) return LEC_ES_ECUDA;
+  const int bps = std::max(1, batch_blocks_per_sm(L.block, b->smem));
+  b->grid = grid_override > 0 ? grid_override : c->sm_count * bps;
+  // tiles sized by cost (records x chunks), big miters first, each miter's
+  // tiles in ascending pattern order
+  double total = 0;
+  std::vector<size_t> idx(b->light);
+  for (size_t i : idx) total += (double)b->mt[i].nrec * (double)num_chunks(b->mt[i].n);
+  std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
+    return (double)b->mt[x].nrec * num_chunks(b->mt[x].n) > (double)b->mt[y].nrec * num_chunks(b->mt[y].n);
+  });
+  const double target = std::max(1.0, total / ((double)b->grid * (double)L.granularity));
+  std::vector<BatchTile> tiles;
+  for (size_t i : idx) {
+    const uint64_t C = num_chunks(b->mt[i].n);
+    uint64_t tc = (uint64_t)(target / std::max<uint32_t>(1, b->mt[i].nrec));
+    tc = ((tc + L.block - 1) / L.block) * L.block;
+    tc = std::max<uint64_t>(tc, (uint64_t)L.block);
+    for (uint64_t c0 = 0; c0 < C; c0 += tc) {
+      BatchTile t{};
+      t.miter = (uint32_t)i;
+      t.chunk_begin = c0;
+      t.chunk_end = std::min(C, c0 + tc);
+      tiles.push_back(t);
+    }
+  }
+  if (tiles.size() > 0xFFFFFFF0ull) return LEC_ES_ETOOBIG;
+  b->num_tiles = (uint32_t)tiles.size();
+  if (tiles.size() > b->tiles_cap) {
+    c->arena.free(b->d_tiles);
+    b->tiles_cap = std::max<size_t>(tiles.size(), 16);
+    b->d_tiles = c->arena.alloc(b->tiles_cap * sizeof(BatchTile));
+    if (!b->d_tiles) return LEC_ES_ENOMEM;
   }
   cudaStream_t st = c->stream;
-  cudaError_t e = cudaMemcpyAsync(b->d_recs, arena_recs.data(), arena_recs.size() * sizeof(Rec),
-                                  cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->d_miters, mt.data(), k * sizeof(BatchMiter), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && !tiles.empty())
-    e = cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) {
-    batch_release(c, b.release());
+  if (!tiles.empty() &&
+      (cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, st) !=
+           cudaSuccess ||
+       cudaStreamSynchronize(st) != cudaSuccess))
     return LEC_ES_ECUDA;
-  }
   BatchParams &bp = b->params;
   bp.recs = (const Rec *)b->d_recs;
   bp.miters = (const BatchMiter *)b->d_miters;
   bp.tiles = (const BatchTile *)b->d_tiles;
   bp.num_tiles = b->num_tiles;
-  bp.max_slots = ms;
-  bp.ring_recs = b->ring_recs;
+  bp.max_slots = b->max_slots;
+  bp.ring_recs = L.ring_recs;
   bp.cex = b->d_cex;
   bp.head = b->d_head;
   bp.status = b->d_head + 1;
   bp.cancel = nullptr;
-
-  // capture reset + kernel + read-back once
-  if (cudaEventCreate(&b->e0) != cudaSuccess || cudaEventCreate(&b->e1) != cudaSuccess) {
-    batch_release(c, b.release());
-    return LEC_ES_ECUDA;
-  }
+  // specialised kernels by descending work, dealt round robin to the branches
+  std::vector<size_t> jorder(light_only ? 0 : b->jit_miters.size());
+  for (size_t j = 0; j < jorder.size(); j++) jorder[j] = j;
+  std::stable_sort(jorder.begin(), jorder.end(), [&](size_t x, size_t y) {
+    const Program &gx = b->progs[b->jit_miters[x]], &gy = b->progs[b->jit_miters[y]];
+    return (double)gx.lut.order.size() * num_chunks(gx.n) > (double)gy.lut.order.size() * num_chunks(gy.n);
+  });
   int lerr = 0;
-  e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    cudaMemsetAsync(b->d_cex, 0xFF, k * 8, st);
-    cudaMemsetAsync(b->d_head, 0, 16, st);
-    if (!b->jit_miters.empty()) cudaMemsetAsync(b->d_aux, 0, b->jit_miters.size() * 16, st);
-    // heavy miters first, each over the whole GPU, then the tile queue
-    for (size_t j = 0; j < b->jit_miters.size() && !lerr; j++) {
-      const uint32_t i = b->jit_miters[j];
-      JitKernel *kk = b->jit_kernels[j];
-      uint64_t cb = 0, ce = num_chunks(b->progs[i].n), grabs = ~0ull;
-      unsigned long long *cex = b->d_cex + i, *ev = b->d_aux + 2 * j, *next = b->d_aux + 2 * j + 1;
-      void *args[] = {&cb, &ce, &cex, &ev, &next, &grabs};
-      const uint64_t warps_needed = (ce + 31) / 32;
-      const uint64_t grid = std::max<uint64_t>(
-          1, std::min<uint64_t>((uint64_t)c->sm_count * kk->blocks_per_sm, (warps_needed * 32 + kk->block - 1) / kk->block));
-      if (cudaLaunchKernel((const void *)kk->kern, dim3((unsigned)grid), dim3(kk->block), args, 0, st) !=
-          cudaSuccess)
-        lerr = 1;
-    }
-    if (b->num_tiles && !lerr) lerr = launch_batch(bp, b->block, b->grid, b->smem, st);
-    cudaMemcpyAsync(b->h_cex, b->d_cex, k * 8, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(b->h_status, b->d_head, 16, cudaMemcpyDeviceToHost, st);
-    e = cudaStreamEndCapture(st, &b->graph);
+  const size_t k = b->k;
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return LEC_ES_ECUDA;
+  cudaMemsetAsync(b->d_cex, 0xFF, k * 8, st);
+  cudaMemsetAsync(b->d_head, 0, 16, st);
+  if (!b->jit_miters.empty()) cudaMemsetAsync(b->d_aux, 0, b->jit_miters.size() * 16, st);
+  // fork: branch 0 runs the tile queue; the specialised kernels are dealt to
+  // branches 1, 2, 3, 0, ... so small kernels overlap instead of queueing
+  cudaEventRecord(b->fork, st);
+  for (int i = 0; i < kBranches; i++) cudaStreamWaitEvent(b->side[i], b->fork, 0);
+  if (b->num_tiles) lerr = launch_batch(bp, L.block, b->grid, b->smem, b->side[0]);
+  for (size_t q = 0; q < jorder.size() && !lerr; q++) {
+    const size_t j = jorder[q];
+    const uint32_t i = b->jit_miters[j];
+    JitKernel *kk = b->jit_kernels[j];
+    uint64_t cb = 0, ce = num_chunks(b->progs[i].n), grabs = ~0ull;
+    unsigned long long *cex = b->d_cex + i, *ev = b->d_aux + 2 * j, *next = b->d_aux + 2 * j + 1;
+    void *args[] = {&cb, &ce, &cex, &ev, &next, &grabs};
+    const uint64_t warps = (ce + 31) / 32;
+    const uint64_t grid = std::max<uint64_t>(
+        1, std::min<uint64_t>((uint64_t)c->sm_count * kk->blocks_per_sm, (warps * 32 + kk->block - 1) / kk->block));
+    if (cudaLaunchKernel((const void *)kk->kern, dim3((unsigned)grid), dim3(kk->block), args, 0,
+                         b->side[(q + 1) % kBranches]) != cudaSuccess)
+      lerr = 1;
   }
-  if (e != cudaSuccess || lerr || cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) {
-    batch_release(c, b.release());
-    return LEC_ES_ECUDA;
+  for (int i = 0; i < kBranches; i++) {
+    cudaEventRecord(b->join[i], b->side[i]);
+    cudaStreamWaitEvent(st, b->join[i], 0);
+  }
+  cudaMemcpyAsync(b->h_cex, b->d_cex, k * 8, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(b->h_status, b->d_head, 16, cudaMemcpyDeviceToHost, st);
+  e = cudaStreamEndCapture(st, &b->graph);
+  if (e != cudaSuccess || lerr) return LEC_ES_ECUDA;
+  if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) return LEC_ES_ECUDA;
+  return LEC_ES_OK;
+}
+
+// Batch shape for the tuning cache: log2 of light miters and light work,
+// largest live set in steps of 16, SM count.
+uint64_t shape_key(lec_es_ctx *c, const lec_es_batch_plan *b) {
+  double work = 0;
+  for (size_t i : b->light) work += (double)b->mt[i].nrec * (double)num_chunks(b->mt[i].n);
+  const uint64_t lk = (uint64_t)std::log2((double)b->light.size() + 1.0);
+  const uint64_t lw = (uint64_t)std::log2(work + 1.0);
+  return (lk << 48) | (lw << 32) | ((uint64_t)(b->max_slots / 16) << 16) | (uint64_t)c->sm_count;
+}
+
+std::string tune_file(lec_es_ctx *c) { return c->jit_dir.empty() ? std::string() : c->jit_dir + "/batch_layouts.txt"; }
+
+bool tuned_lookup(lec_es_ctx *c, uint64_t key, Layout &L) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  const std::string f = tune_file(c);
+  auto &m = g_tuned[f];
+  if (m.empty() && !f.empty()) {
+    std::ifstream in(f);
+    unsigned long long kk;
+    int blk;
+    unsigned ring, gran;
+    while (in >> std::hex >> kk >> std::dec >> blk >> ring >> gran) m[kk] = Layout{blk, ring, gran};
+  }
+  auto it = m.find(key);
+  if (it == m.end()) return false;
+  L = it->second;
+  return true;
+}
+
+void tuned_store(lec_es_ctx *c, uint64_t key, const Layout &L) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  const std::string f = tune_file(c);
+  g_tuned[f][key] = L;
+  if (!f.empty()) {
+    std::ofstream out(f, std::ios::app);
+    out << std::hex << (unsigned long long)key << std::dec << " " << L.block << " " << L.ring_recs << " "
+        << L.granularity << "\n";
+  }
+}
+
+// Time each candidate layout on the tile queue alone (graph replays: one
+// warm-up, then the median of three) and keep the fastest.
+int autotune(lec_es_ctx *c, lec_es_batch_plan *b, int grid_override, Layout &best) {
+  const double t0 = now_ms();
+  const uint64_t key = shape_key(c, b);
+  if (tuned_lookup(c, key, best)) return LEC_ES_OK;
+  float best_ms = 1e30f;
+  bool have = false;
+  cudaStream_t st = c->stream;
+  for (int blk : {256, 128, 64})
+    for (uint32_t ring : {256u, 512u, 1024u})
+      for (uint32_t gran : {4u, 16u, 64u}) {
+        Layout L{blk, ring, gran};
+        if (batch_smem_bytes(b->max_slots, blk, ring) > (size_t)c->smem_optin) continue;
+        if (stage_layout(c, b, L, grid_override, true) != LEC_ES_OK) continue;
+        float t[3] = {0, 0, 0};
+        bool ok = true;
+        for (int r = 0; r < 4 && ok; r++) {
+          cudaEventRecord(b->e0, st);
+          ok = cudaGraphLaunch(b->exec, st) == cudaSuccess;
+          cudaEventRecord(b->e1, st);
+          ok = ok && wait_event(b->e1, c->timeout_s) == LEC_ES_OK;
+          if (ok && r > 0) cudaEventElapsedTime(&t[r - 1], b->e0, b->e1);
+        }
+        if (!ok || cudaStreamSynchronize(st) != cudaSuccess || b->h_status[1]) return LEC_ES_ECUDA;
+        std::sort(t, t + 3);
+        if (!have || t[1] < best_ms) {
+          best_ms = t[1];
+          best = L;
+          have = true;
+        }
+      }
+  if (!have) return LEC_ES_ETOOBIG;
+  tuned_store(c, key, best);
+  b->tune_ms = now_ms() - t0;
+  return LEC_ES_OK;
+}
+
+}  // namespace
+
+extern "C" int lec_es_batch_prepare(lec_es_ctx *c, const lec_es_miter *m, size_t k, const lec_es_options *opt,
+                                    lec_es_batch_plan **out) {
+  if (!c || !m || !out || k == 0 || k > 0xFFFFFFFFull) return LEC_ES_EINVAL;
+  *out = nullptr;
+  const double t0 = now_ms();
+  lec_es_batch_plan *b = new (std::nothrow) lec_es_batch_plan();
+  if (!b) return LEC_ES_ENOMEM;
+  b->k = k;
+  int rc = stage_programs(c, b, m, k, opt);
+  const int grid_override = opt && opt->grid_blocks ? (int)opt->grid_blocks : 0;
+  Layout L;
+  if (!rc) {
+    if (opt && (opt->flags & LEC_ES_FLAG_AUTOTUNE) && !b->light.empty()) {
+      rc = autotune(c, b, grid_override, L);
+    } else {
+      if (opt && opt->block_threads) L.block = (int)opt->block_threads;
+      if (opt && opt->stage_records) L.ring_recs = opt->stage_records;
+      if (opt && opt->tile_granularity) L.granularity = opt->tile_granularity;
+      if (L.block != 64 && L.block != 128 && L.block != 256) rc = LEC_ES_EINVAL;
+      if (L.ring_recs < 2 || (L.ring_recs & 1) || L.ring_recs > 4096) rc = LEC_ES_EINVAL;
+      // a layout that does not fit shared memory falls back to smaller blocks
+      while (!rc && L.block > 64 && batch_smem_bytes(b->max_slots, L.block, L.ring_recs) > (size_t)c->smem_optin)
+        L.block /= 2;
+    }
+  }
+  if (!rc) rc = stage_layout(c, b, L, grid_override, false);
+  if (rc) {
+    cudaStreamSynchronize(c->stream);
+    batch_release(c, b);
+    return rc;
   }
   b->host_ms = now_ms() - t0;
-  *out = b.release();
+  *out = b;
+  return LEC_ES_OK;
+}
+
+extern "C" int lec_es_batch_info(const lec_es_batch_plan *b, lec_es_batch_layout *info) {
+  if (!b || !info) return LEC_ES_EINVAL;
+  memset(info, 0, sizeof(*info));
+  info->miters = (uint32_t)b->k;
+  info->jit_miters = (uint32_t)b->jit_miters.size();
+  info->fallback_miters = (uint32_t)b->fallbacks.size();
+  info->tile_miters = (uint32_t)b->light.size();
+  info->tiles = b->num_tiles;
+  info->block_threads = (uint32_t)b->layout.block;
+  info->stage_records = b->layout.ring_recs;
+  info->tile_granularity = b->layout.granularity;
+  info->grid_blocks = (uint32_t)b->grid;
+  info->prepare_ms = b->host_ms;
+  info->jit_ms = b->jit_ms;
+  info->tune_ms = b->tune_ms;
   return LEC_ES_OK;
 }
 

@@ -45,7 +45,9 @@ struct JitKernel {
   size_t local_bytes = 0;
   int block = 128;
   int blocks_per_sm = 1;
-  double compile_ms = 0;
+  double compile_ms = 0;   // whole build
+  double nvrtc_ms = 0;     // of which NVRTC (0 on a disk-cache hit)
+  double load_ms = 0;      // of which loading the cubin and querying the kernel
 };
 struct JitState;
 struct Server;

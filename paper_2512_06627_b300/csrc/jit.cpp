@@ -290,9 +290,12 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
              lut_form ? "lut" : "and", c->cc_major, c->cc_minor);
     path = c->jit_dir + name;
   }
+  double nvrtc_ms = 0;
   if (path.empty() || !read_file(path, cubin)) {
     std::string log;
+    const double tn = now_ms();
     int rc = compile_cubin(gen_source(g, lut_form), c->cc_major, c->cc_minor, cubin, log);
+    nvrtc_ms = now_ms() - tn;
     if (rc) {
       if (getenv("LEC_ES_JIT_LOG")) fprintf(stderr, "lec_es JIT failed:\n%s\n", log.c_str());
       return rc;
@@ -300,6 +303,7 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
     if (!path.empty()) write_file(path, cubin);
   }
   cudaSetDevice(c->device);
+  const double tl = now_ms();
   JitKernel *k = new JitKernel();
   if (cudaLibraryLoadData(&k->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess ||
       cudaLibraryGetKernel(&k->kern, k->lib, "es_jit") != cudaSuccess) {
@@ -316,7 +320,12 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void *)k->kern, kJitBlock, 0);
   k->blocks_per_sm = std::max(1, bps);
   k->block = kJitBlock;
+  k->load_ms = now_ms() - tl;
+  k->nvrtc_ms = nvrtc_ms;
   k->compile_ms = now_ms() - t0;
+  if (getenv("LEC_ES_JIT_LOG"))
+    fprintf(stderr, "lec_es JIT %016llx: nvrtc %.1f ms, load %.1f ms, %d regs\n", (unsigned long long)g.hash,
+            nvrtc_ms, k->load_ms, k->regs);
   *out = k;
   return LEC_ES_OK;
 }

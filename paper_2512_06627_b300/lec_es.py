@@ -33,7 +33,7 @@ EXPORTS = [
     "lec_es_plan_free", "lec_es_truth_tables", "lec_es_batch", "lec_es_batch_prepare",
     "lec_es_batch_run_async", "lec_es_batch_results", "lec_es_batch_free", "lec_es_submit", "lec_es_poll",
     "lec_es_wait", "lec_es_cancel", "lec_es_server_config", "lec_es_lop3_peak", "lec_es_jit_compile",
-    "lec_es_check_noalloc",
+    "lec_es_check_noalloc", "lec_es_batch_info",
 ]
 
 
@@ -67,7 +67,8 @@ class lec_es_result(ctypes.Structure):
 class lec_es_options(ctypes.Structure):
     _fields_ = [("word_begin", ctypes.c_uint64), ("word_end", ctypes.c_uint64), ("tier", ctypes.c_uint32),
                 ("order", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
-                ("grid_blocks", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+                ("grid_blocks", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("tile_granularity", ctypes.c_uint32), ("stage_records", ctypes.c_uint32)]
 
 
 class lec_es_config(ctypes.Structure):
@@ -120,6 +121,7 @@ def load() -> ctypes.CDLL:
         "lec_es_batch": ([_P, M, ctypes.c_size_t, R], ctypes.c_int),
         "lec_es_batch_prepare": ([_P, M, ctypes.c_size_t, O, ctypes.POINTER(_P)], ctypes.c_int),
         "lec_es_batch_run_async": ([_P, _P], ctypes.c_int),
+        "lec_es_batch_info": ([_P, ctypes.POINTER(lec_es_batch_layout)], ctypes.c_int),
         "lec_es_batch_results": ([_P, _P, R, ctypes.c_size_t], ctypes.c_int),
         "lec_es_batch_free": ([_P, _P], None),
         "lec_es_submit": ([_P, M, _u64p], ctypes.c_int),
@@ -167,12 +169,22 @@ def miter_of(aig, out_lit: Optional[int] = None) -> Miter:
     return Miter(aig.num_pis, aig.flat_fanins(), aig.outputs[0] if out_lit is None else out_lit)
 
 
-FLAG_JIT_AND_FORM, FLAG_TEST_WAIT_TIMEOUT = 1, 2
+FLAG_JIT_AND_FORM, FLAG_TEST_WAIT_TIMEOUT, FLAG_AUTOTUNE = 1, 2, 4
+
+
+class lec_es_batch_layout(ctypes.Structure):
+    _fields_ = [("miters", ctypes.c_uint32), ("jit_miters", ctypes.c_uint32), ("tile_miters", ctypes.c_uint32),
+                ("fallback_miters", ctypes.c_uint32), ("tiles", ctypes.c_uint32),
+                ("block_threads", ctypes.c_uint32), ("stage_records", ctypes.c_uint32),
+                ("tile_granularity", ctypes.c_uint32), ("grid_blocks", ctypes.c_uint32),
+                ("prepare_ms", ctypes.c_double), ("jit_ms", ctypes.c_double), ("tune_ms", ctypes.c_double)]
 
 
 def options(word_begin: int = 0, word_end: int = NO_CEX, tier: int = TIER_AUTO, order: int = ORDER_AUTO,
-            block_threads: int = 0, grid_blocks: int = 0, flags: int = 0) -> lec_es_options:
-    return lec_es_options(word_begin, word_end, tier, order, block_threads, grid_blocks, flags)
+            block_threads: int = 0, grid_blocks: int = 0, flags: int = 0, tile_granularity: int = 0,
+            stage_records: int = 0) -> lec_es_options:
+    return lec_es_options(word_begin, word_end, tier, order, block_threads, grid_blocks, flags,
+                          tile_granularity, stage_records)
 
 
 # ---- entry points (same names as the C ABI) -------------------------------------
@@ -296,6 +308,12 @@ def lec_es_batch_prepare(ctx: Context, ms: Sequence[Miter], opt: Optional[lec_es
     _ok(load().lec_es_batch_prepare(ctx.handle, arr, len(ms), ctypes.byref(opt) if opt else None,
                                     ctypes.byref(b)), "lec_es_batch_prepare")
     return b
+
+
+def lec_es_batch_info(b) -> lec_es_batch_layout:
+    info = lec_es_batch_layout()
+    _ok(load().lec_es_batch_info(b, ctypes.byref(info)), "lec_es_batch_info")
+    return info
 
 
 def lec_es_batch_run_async(ctx: Context, b) -> None:

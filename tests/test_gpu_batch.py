@@ -63,3 +63,31 @@ def test_full_4096_pairs_batch_equals_single(ctx, pairs):
     assert outs[0] == single
     nonequiv = sum(1 for x in single if x != L.NO_CEX)
     assert nonequiv >= sum(pairs.mutated) // 2
+
+
+def test_layouts_and_autotune_give_identical_results(ctx, pairs, tmp_path):
+    """Every tile layout (threads per pass, tiles per block slot, staging
+    depth) and the autotuned one give the same result for every miter."""
+    f = pairs.aig.flat_fanins()
+    sel = list(range(0, 4096, 5))
+    ms = [L.Miter(pairs.aig.num_pis, f, pairs.aig.outputs[i]) for i in sel]
+    ref = None
+    for blk, gran, ring in [(256, 16, 512), (128, 4, 256), (64, 64, 1024), (256, 1, 2)]:
+        b = L.lec_es_batch_prepare(ctx, ms, L.options(tier=L.TIER_INTERP, block_threads=blk,
+                                                       tile_granularity=gran, stage_records=ring))
+        info = L.lec_es_batch_info(b)
+        assert info.block_threads == blk and info.stage_records == ring and info.tile_granularity == gran
+        L.lec_es_batch_run_async(ctx, b)
+        got = [r.cex for r in L.lec_es_batch_results(ctx, b, len(ms))]
+        L.lec_es_batch_free(ctx, b)
+        ref = got if ref is None else ref
+        assert got == ref
+    tuned = L.lec_es_create(0, arena_bytes=1 << 30, jit_cache_dir=str(tmp_path))
+    b = L.lec_es_batch_prepare(tuned, ms, L.options(flags=L.FLAG_AUTOTUNE))
+    info = L.lec_es_batch_info(b)
+    assert info.block_threads in (64, 128, 256) and info.tile_granularity in (4, 16, 64)
+    L.lec_es_batch_run_async(tuned, b)
+    assert [r.cex for r in L.lec_es_batch_results(tuned, b, len(ms))] == ref
+    L.lec_es_batch_free(tuned, b)
+    assert (tmp_path / "batch_layouts.txt").exists()
+    L.lec_es_destroy(tuned)
