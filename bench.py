@@ -192,6 +192,14 @@ def measure_batch(ctx, args):
     import torch
     from paper_2512_06627_b300 import circuits as C
     from paper_2512_06627_b300 import lec_es as L
+    # sweeping step (1) on the GPU: signatures and candidate pairs of the
+    # 32x32 graph the node pairs come from (the same words the generator draws)
+    base = C.build_golden_revised_multipliers(32)
+    pw = C.signature_words(base, 64, 4)
+    L.lec_es_match_pairs(ctx, base.num_pis, base.flat_fanins(), pw, 28)
+    t0 = time.perf_counter()
+    cand = L.lec_es_match_pairs(ctx, base.num_pis, base.flat_fanins(), pw, 28)
+    sweep_ms = (time.perf_counter() - t0) * 1e3
     pb = C.config4_pairs(num_pairs=args.batch_pairs)
     f = pb.aig.flat_fanins()
     ms = [L.Miter(pb.aig.num_pis, f, o) for o in pb.aig.outputs]
@@ -250,6 +258,8 @@ def measure_batch(ctx, args):
         "speedup_vs_sync": batched / (k / s_s),
         "work_share_top_1pct": float(work[big].sum() / work.sum()),
         "prepare_s": prep, "jit_compile_s": layout.jit_ms / 1e3, "autotune_s": layout.tune_ms / 1e3,
+        "sweep_step1": {"graph_ands": int(base.num_ands), "signature_words": 64, "candidate_pairs": len(cand),
+                        "ms": sweep_ms},
         "layout": {"tile_miters": layout.tile_miters, "tiles": layout.tiles,
                    "threads_per_tile_pass": layout.block_threads, "tiles_per_block_slot": layout.tile_granularity,
                    "stage_records": layout.stage_records, "grid_blocks": layout.grid_blocks},

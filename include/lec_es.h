@@ -289,6 +289,26 @@ int lec_es_cancel(lec_es_ctx *c, uint64_t ticket);
  * requests in flight.  Call before the first submit. */
 int lec_es_server_config(lec_es_ctx *c, size_t slot_budget_bytes, uint32_t max_inflight);
 
+/* ---- sweeping step (1): random simulation and candidate pairs ------------ */
+
+/* Simulate the whole graph on caller-drawn random words (sweeping flow step
+ * (1), §2.3) on the device.  pi_words: host, num_pis x nwords words (row k =
+ * PI k).  hash_out: host, num_pis+num_ands+1 words, a 64-bit hash of every
+ * variable's signature (equal signatures give equal hashes).  sigs_out: host,
+ * (num_pis+num_ands+1) x nwords words, or NULL.  Errors: EINVAL (a fanin not
+ * below its AND, NULL arrays), ENOMEM (arena), ECUDA. */
+int lec_es_signatures(lec_es_ctx *c, uint32_t num_pis, uint32_t num_ands, const uint32_t *fanins,
+                      const uint64_t *pi_words, uint32_t nwords, uint64_t *sigs_out, uint64_t *hash_out);
+/* Potentially-equivalent node pairs from those signatures: AND nodes with
+ * identical (not complemented) signatures form classes, constant signatures
+ * are dropped, every member is paired with its class's lowest variable, and a
+ * pair is kept if the union of the two PI supports has at most max_support
+ * PIs (num_pis <= 64).  pairs (host, 2*cap): (representative, member)
+ * variables, ascending; *npairs = total found (may exceed cap). */
+int lec_es_match_pairs(lec_es_ctx *c, uint32_t num_pis, uint32_t num_ands, const uint32_t *fanins,
+                       const uint64_t *pi_words, uint32_t nwords, uint32_t max_support, uint32_t *pairs,
+                       uint64_t cap, uint64_t *npairs);
+
 /* ---- device facts ----------------------------------------------------- */
 
 /* Measured 32-bit LOP3 throughput: results per clock per SM, from a

@@ -635,6 +635,42 @@ def support_masks(aig: Aig) -> List[int]:
     return m
 
 
+def signature_words(aig: Aig, nwords: int, seed: int) -> np.ndarray:
+    """The (num_pis, nwords) random PI words random_signatures draws."""
+    rng = Xoshiro256ss(seed)
+    return np.stack([rng.words(nwords) for _ in range(aig.num_pis)]) if aig.num_pis else \
+        np.zeros((0, nwords), dtype=np.uint64)
+
+
+def candidate_pairs(base: Aig, sig_words: int, seed: int, max_support: int):
+    """Node pairs with equal random-simulation signatures (input selection):
+    classes of identical non-constant signatures over the AND nodes, each
+    member paired with the class's lowest variable, kept if the joint PI
+    support has at most max_support PIs.  Returns (sorted pairs, masks)."""
+    sig = random_signatures(base, sig_words, seed)
+    masks = support_masks(base)
+    V = base.max_var + 1
+    first = base.num_pis + 1
+    classes: Dict[bytes, List[int]] = {}
+    zero = np.zeros(sig_words, dtype=np.uint64)
+    ones = zero ^ np.uint64(MASK64)
+    for v in range(first, V):
+        s = sig[v]
+        if np.array_equal(s, zero) or np.array_equal(s, ones):
+            continue
+        classes.setdefault(s.tobytes(), []).append(v)
+    cands: List[Tuple[int, int]] = []
+    for members in classes.values():
+        if len(members) < 2:
+            continue
+        rep = members[0]
+        for v in members[1:]:
+            if bin(masks[rep] | masks[v]).count("1") <= max_support:
+                cands.append((rep, v))
+    cands.sort()
+    return cands, masks
+
+
 @dataclasses.dataclass
 class PairBatch:
     """Node-pair miters sharing one AIG: miter j is (aig, outputs[j])."""
@@ -665,27 +701,9 @@ def config4_pairs(num_pairs: int = 4096, w: int = 32, max_support: int = 28, see
     x XOR y'.
     """
     base = build_golden_revised_multipliers(w)
-    sig = random_signatures(base, sig_words, seed)
-    masks = support_masks(base)
+    cands, masks = candidate_pairs(base, sig_words, seed, max_support)
     V = base.max_var + 1
     first = base.num_pis + 1
-    classes: Dict[bytes, List[int]] = {}
-    zero = np.zeros(sig_words, dtype=np.uint64)
-    ones = zero ^ np.uint64(MASK64)
-    for v in range(first, V):
-        s = sig[v]
-        if np.array_equal(s, zero) or np.array_equal(s, ones):
-            continue
-        classes.setdefault(s.tobytes(), []).append(v)
-    cands: List[Tuple[int, int]] = []
-    for members in classes.values():
-        if len(members) < 2:
-            continue
-        rep = members[0]
-        for v in members[1:]:
-            if bin(masks[rep] | masks[v]).count("1") <= max_support:
-                cands.append((rep, v))
-    cands.sort()
     rng = Xoshiro256ss(seed ^ 0xBA7C4)
     if len(cands) > num_pairs:
         idx = list(range(len(cands)))

@@ -33,7 +33,7 @@ EXPORTS = [
     "lec_es_plan_free", "lec_es_truth_tables", "lec_es_batch", "lec_es_batch_prepare",
     "lec_es_batch_run_async", "lec_es_batch_results", "lec_es_batch_free", "lec_es_submit", "lec_es_poll",
     "lec_es_wait", "lec_es_cancel", "lec_es_server_config", "lec_es_lop3_peak", "lec_es_jit_compile",
-    "lec_es_check_noalloc", "lec_es_batch_info",
+    "lec_es_check_noalloc", "lec_es_batch_info", "lec_es_signatures", "lec_es_match_pairs",
 ]
 
 
@@ -122,6 +122,10 @@ def load() -> ctypes.CDLL:
         "lec_es_batch_prepare": ([_P, M, ctypes.c_size_t, O, ctypes.POINTER(_P)], ctypes.c_int),
         "lec_es_batch_run_async": ([_P, _P], ctypes.c_int),
         "lec_es_batch_info": ([_P, ctypes.POINTER(lec_es_batch_layout)], ctypes.c_int),
+        "lec_es_signatures": ([_P, ctypes.c_uint32, ctypes.c_uint32, _u32p, _u64p, ctypes.c_uint32, _u64p, _u64p],
+                              ctypes.c_int),
+        "lec_es_match_pairs": ([_P, ctypes.c_uint32, ctypes.c_uint32, _u32p, _u64p, ctypes.c_uint32,
+                                ctypes.c_uint32, _u32p, ctypes.c_uint64, _u64p], ctypes.c_int),
         "lec_es_batch_results": ([_P, _P, R, ctypes.c_size_t], ctypes.c_int),
         "lec_es_batch_free": ([_P, _P], None),
         "lec_es_submit": ([_P, M, _u64p], ctypes.c_int),
@@ -376,6 +380,35 @@ def lec_es_check_noalloc(d_records: int, records_capacity: int, info: lec_es_pro
     _ok(load().lec_es_check_noalloc(ctypes.c_void_p(d_records), records_capacity, ctypes.byref(info),
                                     word_begin, word_end, ctypes.c_void_p(d_result), ctypes.c_void_p(stream)),
         "lec_es_check_noalloc")
+
+
+def lec_es_signatures(ctx: Context, num_pis: int, fanins, pi_words, want_sigs: bool = True):
+    """(signatures (V, nwords) uint64 or None, hashes (V,) uint64) of every
+    variable; pi_words is a (num_pis, nwords) uint64 array."""
+    f = np.ascontiguousarray(np.asarray(fanins, dtype=np.uint32).reshape(-1))
+    pw = np.ascontiguousarray(np.asarray(pi_words, dtype=np.uint64).reshape(num_pis, -1))
+    nw = pw.shape[1] if num_pis else 1
+    V = num_pis + len(f) // 2 + 1
+    h = np.zeros(V, dtype=np.uint64)
+    sg = np.zeros((V, nw), dtype=np.uint64) if want_sigs else None
+    _ok(load().lec_es_signatures(ctx.handle, num_pis, len(f) // 2, f.ctypes.data_as(_u32p),
+                                 pw.ctypes.data_as(_u64p), nw, sg.ctypes.data_as(_u64p) if want_sigs else None,
+                                 h.ctypes.data_as(_u64p)), "lec_es_signatures")
+    return sg, h
+
+
+def lec_es_match_pairs(ctx: Context, num_pis: int, fanins, pi_words, max_support: int):
+    """List of (representative var, member var) candidate pairs."""
+    f = np.ascontiguousarray(np.asarray(fanins, dtype=np.uint32).reshape(-1))
+    pw = np.ascontiguousarray(np.asarray(pi_words, dtype=np.uint64).reshape(num_pis, -1))
+    n = ctypes.c_uint64()
+    lib = load()
+    args = (ctx.handle, num_pis, len(f) // 2, f.ctypes.data_as(_u32p), pw.ctypes.data_as(_u64p), pw.shape[1],
+            max_support)
+    _ok(lib.lec_es_match_pairs(*args, None, 0, ctypes.byref(n)), "lec_es_match_pairs")
+    out = np.zeros(max(1, 2 * n.value), dtype=np.uint32)
+    _ok(lib.lec_es_match_pairs(*args, out.ctypes.data_as(_u32p), n.value, ctypes.byref(n)), "lec_es_match_pairs")
+    return [(int(out[2 * i]), int(out[2 * i + 1])) for i in range(n.value)]
 
 
 def lec_es_lop3_peak(ctx: Context):
