@@ -18,6 +18,7 @@
 // Before every chunk a warp compares its first pattern with the current
 // counterexample (loaded one iteration ahead) and stops if it is not lower.
 #include <cuda_runtime.h>
+#include <nvPTXCompiler.h>
 #include <nvrtc.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -55,6 +56,7 @@ struct JitState {
 namespace {
 
 constexpr int kJitBlock = 128;
+constexpr int kCodegenVersion = 4;  // part of cached cubin names: bump when the kernel's interface changes
 constexpr uint32_t kMaxJitLive = 230;        // table live set that still fits the register file
 constexpr double kJitCachedWork = 5e7;       // records x chunks: ~50 us in the interpreter
 constexpr double kJitColdWork = 1e11;        // ~0.1 s in the interpreter: repays a compile
@@ -213,6 +215,179 @@ std::string gen_source(const Program &g, bool lut_form) {
   return lut_form && !g.lut.order.empty() ? gen_source_lut(g) : gen_source_and(g);
 }
 
+// PTX of the table form, written directly (no C++ front end): the same
+// kernel as gen_source_lut -- per-warp chunk grabs one ahead, PI words from
+// the chunk index, one lop3 per table, warp ballot and atomicMin -- with
+// virtual registers left to ptxas.  Constants (PI masks 0..4, folded tables)
+// are immediate operands.
+std::string gen_ptx_lut(const Program &g, int major, int minor) {
+  const LutProgram &lp = g.lut;
+  const uint32_t NA = lp.na, NP = lp.np;
+  const size_t NV = NA + NP + 1;
+  std::vector<int8_t> isconst(NV, 0);
+  std::vector<uint32_t> cval(NV, 0);
+  static const uint32_t mask[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
+  for (uint32_t k = 0; k < NP && k < 5; k++) {
+    isconst[NA + k] = 1;
+    cval[NA + k] = mask[k];
+  }
+  isconst[NA + NP] = 1;
+  // fold tables whose leaves are all constant
+  for (const auto &l : lp.order) {
+    bool allc = true;
+    for (int k = 0; k < l.n; k++) allc = allc && isconst[l.leaf[k]];
+    if (!allc) continue;
+    uint32_t x[3] = {0, 0, 0};
+    for (int k = 0; k < l.n; k++) x[k] = cval[l.leaf[k]];
+    uint32_t r = 0;
+    for (int b = 0; b < 32; b++) {
+      const int m = (int)((x[0] >> b) & 1) | (int)(((x[1] >> b) & 1) << 1) | (int)(((x[2] >> b) & 1) << 2);
+      r |= (uint32_t)((l.tt >> m) & 1) << b;
+    }
+    isconst[l.node] = 1;
+    cval[l.node] = r;
+  }
+  std::ostringstream s;
+  char buf[160];
+  s << ".version 9.0\n.target sm_" << major << minor << "a\n.address_size 64\n\n"
+    << ".visible .entry es_jit(.param .u64 p_cb, .param .u64 p_ce, .param .u64 p_cex, .param .u64 p_ev,\n"
+    << "    .param .u64 p_next, .param .u64 p_maxg)\n.maxntid " << kJitBlock << ", 1, 1\n{\n"
+    << "  .reg .pred %p<10>;\n  .reg .b32 %t<24>;\n  .reg .b64 %d<32>;\n"
+    << "  .reg .b32 %v<" << (NA + 1) << ">;\n  .reg .b32 %q<" << (NP + 1) << ">;\n";
+  // parameters, lane, first grab, first counterexample poll
+  s << "  ld.param.u64 %d1, [p_cb];\n  ld.param.u64 %d2, [p_ce];\n  ld.param.u64 %d3, [p_cex];\n"
+       "  ld.param.u64 %d4, [p_ev];\n  ld.param.u64 %d5, [p_next];\n  ld.param.u64 %d6, [p_maxg];\n"
+       "  cvta.to.global.u64 %d3, %d3;\n  cvta.to.global.u64 %d4, %d4;\n  cvta.to.global.u64 %d5, %d5;\n"
+       "  mov.u32 %t1, %tid.x;\n  and.b32 %t2, %t1, 31;\n  setp.eq.u32 %p1, %t2, 0;\n"
+       "  mov.u64 %d10, 0;\n  mov.u64 %d11, 0;\n  @%p1 atom.global.add.u64 %d11, [%d5], 32;\n"
+       "  mov.b64 {%t3, %t4}, %d11;\n  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n"
+       "  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n  mov.b64 %d11, {%t3, %t4};\n"
+       "  mov.u64 %d12, 0;\n  @%p1 ld.volatile.global.u64 %d12, [%d3];\n  mov.b64 {%t3, %t4}, %d12;\n"
+       "  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n"
+       "  mov.b64 %d12, {%t3, %t4};\n  mov.u64 %d13, 1;\n  cvt.u64.u32 %d18, %t2;\n";
+  // constants (PI masks, the constant, folded tables) are lop3 immediates
+  std::vector<std::string> name(NV);
+  for (size_t v = 0; v < NV; v++) {
+    if (!isconst[v]) continue;
+    snprintf(buf, sizeof(buf), "0x%08x", cval[v]);
+    name[v] = buf;
+  }
+  for (uint32_t k = 5; k < NP; k++) name[NA + k] = "%q" + std::to_string(k);
+  s << "$LOOP:\n"
+       "  add.u64 %d14, %d1, %d11;\n  setp.ge.u64 %p2, %d14, %d2;\n  @%p2 bra $DONE;\n"
+       "  shl.b64 %d15, %d14, 5;\n  setp.ge.u64 %p2, %d15, %d12;\n  @%p2 bra $DONE;\n"
+       "  setp.lt.u64 %p3, %d13, %d6;\n  and.pred %p4, %p1, %p3;\n  mov.u64 %d16, -1;\n"
+       "  @%p4 atom.global.add.u64 %d16, [%d5], 32;\n  mov.u64 %d17, 0;\n"
+       "  @%p1 ld.volatile.global.u64 %d17, [%d3];\n  add.u64 %d19, %d14, %d18;\n"
+       "  cvt.u32.u64 %t5, %d19;\n  shr.u64 %d20, %d19, 32;\n  cvt.u32.u64 %t6, %d20;\n";
+  std::vector<uint8_t> pi_done(NP, 0);
+  auto operand = [&](int32_t id) -> std::string {
+    if (id < 0) return "0";
+    if (isconst[id]) return name[id];
+    if (id >= (int32_t)NA && id < (int32_t)(NA + NP)) {
+      const uint32_t k = (uint32_t)(id - NA);
+      if (!pi_done[k]) {  // all ones iff bit (k-5) of the chunk index is set
+        const uint32_t j = k - 5;
+        snprintf(buf, sizeof(buf), "  bfe.u32 %%q%u, %%t%d, %u, 1;\n  neg.s32 %%q%u, %%q%u;\n", k, j < 32 ? 5 : 6,
+                 j < 32 ? j : j - 32, k, k);
+        s << buf;
+        pi_done[k] = 1;
+      }
+    }
+    return name[id];
+  };
+  for (const auto &l : lp.order) {
+    if (isconst[l.node]) continue;
+    name[l.node] = "%v" + std::to_string(l.node);
+    const std::string x0 = operand(l.leaf[0]), x1 = operand(l.n > 1 ? l.leaf[1] : -1),
+                      x2 = operand(l.n > 2 ? l.leaf[2] : -1);
+    // lop3 operands a, b, c carry the patterns 0xF0, 0xCC, 0xAA: (x2, x1, x0)
+    snprintf(buf, sizeof(buf), "  lop3.b32 %s, %s, %s, %s, 0x%02x;\n", name[l.node].c_str(), x2.c_str(), x1.c_str(),
+             x0.c_str(), l.tt);
+    s << buf;
+  }
+  const uint32_t vmask = g.n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << g.n)) - 1u);
+  const std::string root = lp.root < 0 ? std::string("0") : operand((int32_t)lp.root);
+  snprintf(buf, sizeof(buf), "  xor.b32 %%t7, %s, 0x%08x;\n  and.b32 %%t7, %%t7, 0x%08x;\n", root.c_str(),
+           g.out_compl ? 0xFFFFFFFFu : 0u, vmask);
+  s << buf;
+  s << "  setp.ge.u64 %p5, %d19, %d2;\n  @%p5 mov.b32 %t7, 0;\n  setp.ne.u32 %p6, %t7, 0;\n"
+       "  vote.sync.ballot.b32 %t8, %p6, -1;\n  setp.eq.u32 %p7, %t8, 0;\n  @%p7 bra $NOFAIL;\n"
+       "  neg.s32 %t9, %t8;\n  and.b32 %t9, %t9, %t8;\n  bfind.u32 %t10, %t9;\n"
+       "  setp.ne.u32 %p7, %t10, %t2;\n  @%p7 bra $NOFAIL;\n"
+       "  neg.s32 %t11, %t7;\n  and.b32 %t11, %t11, %t7;\n  bfind.u32 %t12, %t11;\n"
+       "  cvt.u64.u32 %d21, %t12;\n  shl.b64 %d22, %d19, 5;\n  add.u64 %d22, %d22, %d21;\n"
+       "  atom.global.min.u64 %d23, [%d3], %d22;\n"
+       "$NOFAIL:\n"
+       "  setp.lt.u64 %p5, %d19, %d2;\n  selp.u64 %d24, 1, 0, %p5;\n  add.u64 %d10, %d10, %d24;\n"
+       "  mov.b64 {%t3, %t4}, %d16;\n  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n"
+       "  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n  mov.b64 %d11, {%t3, %t4};\n"
+       "  mov.b64 {%t3, %t4}, %d17;\n  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n"
+       "  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n  mov.b64 %d12, {%t3, %t4};\n"
+       "  add.u64 %d13, %d13, 1;\n  @!%p3 bra $DONE;\n  bra $LOOP;\n"
+       "$DONE:\n";
+  // warp sum of chunks done, then one reduction per warp
+  for (int o = 16; o > 0; o >>= 1) {
+    const std::string os = std::to_string(o);
+    s << "  mov.b64 {%t13, %t14}, %d10;\n  shfl.sync.down.b32 %t15, %t13, " << os << ", 31, -1;\n"
+      << "  shfl.sync.down.b32 %t16, %t14, " << os << ", 31, -1;\n  mov.b64 %d25, {%t15, %t16};\n"
+      << "  add.u64 %d10, %d10, %d25;\n";
+  }
+  s << "  setp.ne.u64 %p8, %d10, 0;\n  and.pred %p8, %p8, %p1;\n  shl.b64 %d26, %d10, 5;\n"
+       "  @%p8 red.global.add.u64 [%d4], %d26;\n  ret;\n}\n";
+  return s.str();
+}
+
+int compile_ptx(const std::string &ptx, int major, int minor, std::vector<char> &cubin, std::string &log) {
+  if (const char *dump = getenv("LEC_ES_DUMP_PTX")) {  // debugging aid: keep the generated PTX
+    std::ofstream f(dump);
+    f << ptx;
+  }
+  nvPTXCompilerHandle h = nullptr;
+  if (nvPTXCompilerCreate(&h, ptx.size(), ptx.c_str()) != NVPTXCOMPILE_SUCCESS) return LEC_ES_EJIT;
+  const std::string gpu = "--gpu-name=sm_" + std::to_string(major) + std::to_string(minor) + "a";
+  const char *opts[] = {gpu.c_str(), "--verbose"};
+  const nvPTXCompileResult rc = nvPTXCompilerCompile(h, 2, opts);
+  size_t n = 0;
+  if (nvPTXCompilerGetInfoLogSize(h, &n) == NVPTXCOMPILE_SUCCESS && n > 1) {
+    std::string info(n, 0);
+    nvPTXCompilerGetInfoLog(h, &info[0]);
+    log += info;
+  }
+  if (rc != NVPTXCOMPILE_SUCCESS) {
+    if (nvPTXCompilerGetErrorLogSize(h, &n) == NVPTXCOMPILE_SUCCESS && n > 1) {
+      std::string err(n, 0);
+      nvPTXCompilerGetErrorLog(h, &err[0]);
+      log += err;
+    }
+    nvPTXCompilerDestroy(&h);
+    return LEC_ES_EJIT;
+  }
+  n = 0;
+  if (nvPTXCompilerGetCompiledProgramSize(h, &n) != NVPTXCOMPILE_SUCCESS || n == 0) {
+    nvPTXCompilerDestroy(&h);
+    return LEC_ES_EJIT;
+  }
+  cubin.resize(n);
+  nvPTXCompilerGetCompiledProgram(h, cubin.data());
+  nvPTXCompilerDestroy(&h);
+  return LEC_ES_OK;
+}
+
+int compile_cubin(const std::string &src, int major, int minor, std::vector<char> &cubin, std::string &log);
+
+// The table form goes straight to PTX and the PTX compiler; the AND form
+// goes through NVRTC.
+int compile_program_kernel(const Program &g, bool lut_form, int major, int minor, std::vector<char> &cubin,
+                           std::string &log) {
+  // LEC_ES_JIT_NVRTC=1 compiles the table form from CUDA C++ through NVRTC
+  // instead (same tables, for comparing the two compilation paths)
+  static const bool via_nvrtc = getenv("LEC_ES_JIT_NVRTC") != nullptr;
+  if (lut_form && !g.lut.order.empty() && !via_nvrtc)
+    return compile_ptx(gen_ptx_lut(g, major, minor), major, minor, cubin, log);
+  return compile_cubin(gen_source(g, lut_form), major, minor, cubin, log);
+}
+
 bool read_file(const std::string &path, std::vector<char> &out) {
   std::ifstream f(path, std::ios::binary);
   if (!f) return false;
@@ -286,15 +461,16 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   if (!c->jit_dir.empty()) {
     mkdir(c->jit_dir.c_str(), 0755);
     char name[64];
-    snprintf(name, sizeof(name), "/es_%016llx_%s_sm%d%d.cubin", (unsigned long long)g.hash,
-             lut_form ? "lut" : "and", c->cc_major, c->cc_minor);
+    snprintf(name, sizeof(name), "/es_v%d_%016llx_%s%s_sm%d%d.cubin", kCodegenVersion,
+             (unsigned long long)g.hash, lut_form ? "lut" : "and", getenv("LEC_ES_JIT_NVRTC") ? "_nvrtc" : "",
+             c->cc_major, c->cc_minor);
     path = c->jit_dir + name;
   }
   double nvrtc_ms = 0;
   if (path.empty() || !read_file(path, cubin)) {
     std::string log;
     const double tn = now_ms();
-    int rc = compile_cubin(gen_source(g, lut_form), c->cc_major, c->cc_minor, cubin, log);
+    int rc = compile_program_kernel(g, lut_form, c->cc_major, c->cc_minor, cubin, log);
     nvrtc_ms = now_ms() - tn;
     if (rc) {
       if (getenv("LEC_ES_JIT_LOG")) fprintf(stderr, "lec_es JIT failed:\n%s\n", log.c_str());
@@ -469,7 +645,7 @@ extern "C" int lec_es_jit_compile(const lec_es_miter *m, int cc_major, int cc_mi
   if (rc) return rc;
   std::vector<char> cubin;
   std::string lg;
-  rc = lec::compile_cubin(lec::gen_source(g, true), cc_major, cc_minor, cubin, lg);
+  rc = lec::compile_program_kernel(g, true, cc_major, cc_minor, cubin, lg);
   if (log && log_cap) {
     const size_t n = std::min(log_cap - 1, lg.size());
     memcpy(log, lg.data(), n);
