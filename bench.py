@@ -29,10 +29,10 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "16x16 array vs radix-4 Booth/Dadda multiplier miter, 32 PIs, 2^32 patterns, equivalent"
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture (profiles/es_jit_mult16.md), keyed by (tier, program hash, number
-# of 3-input tables); reported only while the program and its kernel form
-# are the ones that were captured.
-NCU_TRAFFIC = {}
+# capture (profiles/es_jit_mult16.md, code-generator version 5), keyed by
+# (tier, program hash, number of 3-input tables); reported only while the
+# program is the one that was captured.
+NCU_TRAFFIC = {("jit", 0x27b56cd32749aac7, 1714): 33024}
 
 
 def parse():

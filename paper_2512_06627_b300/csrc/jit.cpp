@@ -56,7 +56,7 @@ struct JitState {
 namespace {
 
 constexpr int kJitBlock = 128;
-constexpr int kCodegenVersion = 4;  // part of cached cubin names: bump when the kernel's interface changes
+constexpr int kCodegenVersion = 5;  // part of cached cubin names: bump when the kernel's interface changes
 constexpr uint32_t kMaxJitLive = 230;        // table live set that still fits the register file
 constexpr double kJitCachedWork = 5e7;       // records x chunks: ~50 us in the interpreter
 constexpr double kJitColdWork = 1e11;        // ~0.1 s in the interpreter: repays a compile
@@ -273,6 +273,15 @@ std::string gen_ptx_lut(const Program &g, int major, int minor) {
     name[v] = buf;
   }
   for (uint32_t k = 5; k < NP; k++) name[NA + k] = "%q" + std::to_string(k);
+  // grabs are multiples of 32 chunks, so the low five bits of a lane's chunk
+  // index are those of cb + lane: PIs 5..9 are fixed per lane, computed here
+  s << "  cvt.u32.u64 %t17, %d1;\n  add.u32 %t17, %t17, %t2;\n";
+  std::vector<uint8_t> pi_done(NP, 0);
+  for (uint32_t k = 5; k < NP && k < 10; k++) {
+    snprintf(buf, sizeof(buf), "  bfe.s32 %%q%u, %%t17, %u, 1;\n", k, k - 5);
+    s << buf;
+    pi_done[k] = 1;
+  }
   s << "$LOOP:\n"
        "  add.u64 %d14, %d1, %d11;\n  setp.ge.u64 %p2, %d14, %d2;\n  @%p2 bra $DONE;\n"
        "  shl.b64 %d15, %d14, 5;\n  setp.ge.u64 %p2, %d15, %d12;\n  @%p2 bra $DONE;\n"
@@ -280,18 +289,17 @@ std::string gen_ptx_lut(const Program &g, int major, int minor) {
        "  @%p4 atom.global.add.u64 %d16, [%d5], 32;\n  mov.u64 %d17, 0;\n"
        "  @%p1 ld.volatile.global.u64 %d17, [%d3];\n  add.u64 %d19, %d14, %d18;\n"
        "  cvt.u32.u64 %t5, %d19;\n  shr.u64 %d20, %d19, 32;\n  cvt.u32.u64 %t6, %d20;\n";
-  std::vector<uint8_t> pi_done(NP, 0);
+  std::vector<uint8_t> pi_loop(NP, 0);
   auto operand = [&](int32_t id) -> std::string {
     if (id < 0) return "0";
     if (isconst[id]) return name[id];
     if (id >= (int32_t)NA && id < (int32_t)(NA + NP)) {
       const uint32_t k = (uint32_t)(id - NA);
-      if (!pi_done[k]) {  // all ones iff bit (k-5) of the chunk index is set
+      if (!pi_done[k] && !pi_loop[k]) {  // all ones iff bit (k-5) of the chunk index is set
         const uint32_t j = k - 5;
-        snprintf(buf, sizeof(buf), "  bfe.u32 %%q%u, %%t%d, %u, 1;\n  neg.s32 %%q%u, %%q%u;\n", k, j < 32 ? 5 : 6,
-                 j < 32 ? j : j - 32, k, k);
+        snprintf(buf, sizeof(buf), "  bfe.s32 %%q%u, %%t%d, %u, 1;\n", k, j < 32 ? 5 : 6, j < 32 ? j : j - 32);
         s << buf;
-        pi_done[k] = 1;
+        pi_loop[k] = 1;
       }
     }
     return name[id];
