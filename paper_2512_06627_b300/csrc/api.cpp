@@ -81,6 +81,49 @@ double now_ms() {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? LEC_ES_OK : LEC_ES_ECUDA; }
 
+// Per-run pinned words and events come from a pool: pinned allocation and
+// its release are slow (and the release can wait for the device), so a
+// check-per-call user would otherwise pay them every time.
+int run_res_acquire(lec_es_ctx *c, RunRes *out) {
+  std::lock_guard<std::mutex> g(c->res_mu);
+  if (c->res_free.empty()) {
+    const int kSlab = 64;
+    void *slab = nullptr;
+    if (cudaMallocHost(&slab, (size_t)kSlab * kResWords * sizeof(unsigned long long)) != cudaSuccess)
+      return LEC_ES_ENOMEM;
+    c->res_slabs.push_back(slab);
+    for (int i = 0; i < kSlab; i++) {
+      RunRes r;
+      r.h_res = (unsigned long long *)slab + (size_t)i * kResWords;
+      if (cudaEventCreate(&r.e0) != cudaSuccess || cudaEventCreate(&r.e1) != cudaSuccess ||
+          cudaEventCreateWithFlags(&r.e2, cudaEventDisableTiming) != cudaSuccess)
+        return LEC_ES_ECUDA;
+      c->res_events.push_back(r.e0);
+      c->res_events.push_back(r.e1);
+      c->res_events.push_back(r.e2);
+      c->res_free.push_back(r);
+    }
+  }
+  *out = c->res_free.back();
+  c->res_free.pop_back();
+  return LEC_ES_OK;
+}
+
+void run_res_release(lec_es_ctx *c, const RunRes &r) {
+  if (!r.h_res) return;
+  std::lock_guard<std::mutex> g(c->res_mu);
+  c->res_free.push_back(r);
+}
+
+void run_res_destroy_all(lec_es_ctx *c) {
+  std::lock_guard<std::mutex> g(c->res_mu);
+  for (cudaEvent_t e : c->res_events) cudaEventDestroy(e);
+  for (void *s : c->res_slabs) cudaFreeHost(s);
+  c->res_events.clear();
+  c->res_slabs.clear();
+  c->res_free.clear();
+}
+
 // Wait for an event with a host-side deadline (no unbounded synchronize).
 int wait_event(cudaEvent_t ev, double timeout_s) {
   const double t0 = now_ms();
@@ -208,6 +251,7 @@ extern "C" void lec_es_destroy(lec_es_ctx *c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   lec::jit_release_all(c);
+  lec::run_res_destroy_all(c);
   if (c->h_init) cudaFreeHost(c->h_init);
   if (c->own_arena && c->arena_base) cudaFree(c->arena_base);
   if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -263,10 +307,7 @@ void fill_result(const lec_es_plan *p, lec_es_result *out) {
 
 void plan_release(lec_es_ctx *c, lec_es_plan *p) {
   if (!p) return;
-  if (p->e0) cudaEventDestroy(p->e0);
-  if (p->e1) cudaEventDestroy(p->e1);
-  if (p->e2) cudaEventDestroy(p->e2);
-  if (p->h_res) cudaFreeHost(p->h_res);
+  run_res_release(c, p->res);
   c->arena.free(p->d_recs);
   c->arena.free(p->d_res);
   c->arena.free(p->d_spill);
@@ -349,12 +390,14 @@ int plan_finish_device(lec_es_ctx *c, lec_es_plan *p) {
   }
   p->d_res = (unsigned long long *)c->arena.alloc(kResWords * sizeof(unsigned long long));
   if (!p->d_res) return LEC_ES_ENOMEM;
-  if (cudaMallocHost((void **)&p->h_res, kResWords * sizeof(unsigned long long)) != cudaSuccess)
-    return LEC_ES_ENOMEM;
-  if (cudaEventCreate(&p->e0) != cudaSuccess || cudaEventCreate(&p->e1) != cudaSuccess ||
-      cudaEventCreateWithFlags(&p->e2, cudaEventDisableTiming) != cudaSuccess)
-    return LEC_ES_ECUDA;
-  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return LEC_ES_ECUDA;
+  int rc = run_res_acquire(c, &p->res);
+  if (rc) return rc;
+  p->h_res = p->res.h_res;
+  p->e0 = p->res.e0;
+  p->e1 = p->res.e1;
+  p->e2 = p->res.e2;
+  // the record upload reads a host vector that dies with this call
+  if (p->tier != LEC_ES_TIER_JIT && cudaStreamSynchronize(p->stream) != cudaSuccess) return LEC_ES_ECUDA;
   return LEC_ES_OK;
 }
 

@@ -9,6 +9,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/lec_es.h"
 #include "es_internal.h"
@@ -36,6 +37,12 @@ struct PlanGeom {
   uint32_t resident = 0;
   uint32_t nrec_padded = 0;
   bool spill = false;
+};
+
+// Pinned result words and events of one run, recycled by the context.
+struct RunRes {
+  unsigned long long *h_res = nullptr;  // kResWords pinned words
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
 };
 
 struct JitKernel {
@@ -76,6 +83,9 @@ int plan_prepare_program(lec_es_ctx *c, Program &&prog, const lec_es_options *op
 int plan_run_async(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt);
 int plan_run_async_grid(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt, int grid_override);
 int plan_finish_device(lec_es_ctx *c, lec_es_plan *p);
+int run_res_acquire(lec_es_ctx *c, RunRes *out);
+void run_res_release(lec_es_ctx *c, const RunRes &r);
+void run_res_destroy_all(lec_es_ctx *c);
 int plan_result(lec_es_ctx *c, lec_es_plan *p, lec_es_result *out);
 void plan_release(lec_es_ctx *c, lec_es_plan *p);
 void fill_result(const lec_es_plan *p, lec_es_result *out);
@@ -104,6 +114,11 @@ struct lec_es_ctx {
   std::mutex server_mu;
   size_t slot_budget = (size_t)32 << 30;
   uint32_t max_inflight = 64;
+  // recycled per-run resources (pinned host words are allocated in slabs)
+  std::mutex res_mu;
+  std::vector<lec::RunRes> res_free;
+  std::vector<void *> res_slabs;
+  std::vector<cudaEvent_t> res_events;
 };
 
 // Result words of a run: [0] lowest failing pattern (init ~0), [1] patterns
@@ -113,6 +128,7 @@ constexpr int kResWords = 8;
 
 struct lec_es_plan {
   lec::Program prog;
+  lec::RunRes res;                       // from the context's pool
   lec::PlanGeom geom;
   uint32_t tier = 0;
   void *d_recs = nullptr;

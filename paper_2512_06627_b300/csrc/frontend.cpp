@@ -317,8 +317,9 @@ int assign_slots(const MiterView &m, const Cone &c, const ConeIndex &ix, const s
 // 3-input table cover of the cone and its evaluation order: post-order from
 // the output, deeper leaf first; the live count is the peak number of table
 // outputs and PIs alive at once (each value dies after its last reader).
-void build_lut_program(const MiterView &m, const Cone &c, const ConeIndex &ix, uint32_t root_var,
-                       const std::vector<uint32_t> &and_order, LutProgram &lp) {
+// The cone's 3-input table cover (independent of the evaluation order).
+void cover_cone(const MiterView &m, const Cone &c, const ConeIndex &ix, uint32_t root_var, LutProgram &lp,
+                LutCover &cov) {
   const size_t NA = c.ands.size(), NP = c.pis.size();
   auto vid = [&](uint32_t var) -> int64_t { return ix.vid(var); };
   std::vector<int64_t> f0(NA), f1(NA);
@@ -336,8 +337,13 @@ void build_lut_program(const MiterView &m, const Cone &c, const ConeIndex &ix, u
   lp.order.clear();
   lp.live = 0;
   if (lp.root >= (int64_t)NA) return;  // output is a PI or the constant
-  LutCover cov;
   lut_map(NA, NP, f0, f1, c0, c1, lp.root, cov);
+}
+
+// Evaluation order of the tables and its live count.
+void order_luts(const Cone &c, const std::vector<uint32_t> &and_order, const LutCover &cov, LutProgram &lp) {
+  const size_t NA = c.ands.size(), NP = c.pis.size();
+  if (lp.root >= (int64_t)NA || cov.luts.empty()) return;
   // level of each table (leaves at 0)
   std::vector<uint32_t> lev(cov.luts.size(), 0);
   for (size_t i = 0; i < cov.luts.size(); i++) {
@@ -449,24 +455,33 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
   else if (order <= LEC_ES_ORDER_GREEDY) tried.push_back(order);
   else return LEC_ES_EINVAL;
 
-  bool have = false;
-  Program best;
-  for (uint32_t o : tried) {
+  // the table cover does not depend on the order
+  LutProgram lp;
+  LutCover cov;
+  cover_cone(m, c, ix, root_var, lp, cov);
+  std::vector<Program> cand(tried.size());
+  std::vector<int> crc(tried.size(), LEC_ES_OK);
+  auto run_order = [&](size_t t) {
+    const uint32_t o = tried[t];
     std::vector<uint32_t> ord;
     if (o == LEC_ES_ORDER_DFS) order_dfs(m, c, ix, level, root_var, ord);
     else if (o == LEC_ES_ORDER_VAR) order_var(c, ord);
     else if (o == LEC_ES_ORDER_GREEDY) order_greedy(m, c, ix, root_var, ord);
     else order_level(level, ord);
-    if (ord.size() != c.ands.size()) return LEC_ES_EINVAL;
-    Program p;
-    rc = assign_slots(m, c, ix, ord, root_var, p);
-    if (rc) return rc;
-    p.order = o;
-    if (!have || p.num_slots < best.num_slots) {
-      best = std::move(p);
-      have = true;
+    if (ord.size() != c.ands.size()) {
+      crc[t] = LEC_ES_EINVAL;
+      return;
     }
+    crc[t] = assign_slots(m, c, ix, ord, root_var, cand[t]);
+    cand[t].order = o;
+  };
+  for (size_t t = 0; t < tried.size(); t++) run_order(t);
+  size_t bi = tried.size();
+  for (size_t t = 0; t < tried.size(); t++) {
+    if (crc[t]) return crc[t];
+    if (bi == tried.size() || cand[t].num_slots < cand[bi].num_slots) bi = t;
   }
+  Program best = std::move(cand[bi]);
   best.n = (uint32_t)c.pis.size();
   best.support.resize(c.pis.size());
   for (size_t k = 0; k < c.pis.size(); k++) best.support[k] = c.pis[k] - 1;
@@ -477,7 +492,8 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
     std::vector<uint32_t> and_order;
     and_order.reserve(best.order_vars.size());
     for (uint32_t var : best.order_vars) and_order.push_back((uint32_t)ix.and_pos(var));
-    build_lut_program(m, c, ix, root_var, and_order, best.lut);
+    order_luts(c, and_order, cov, lp);
+    best.lut = std::move(lp);
   }
   if (best.num_slots == 0) best.num_slots = 1;
   uint64_t h = 1469598103934665603ull;

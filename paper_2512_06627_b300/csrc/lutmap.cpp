@@ -126,7 +126,15 @@ void lut_map(size_t NA, size_t NP, const std::vector<int64_t> &f0, const std::ve
              const std::vector<uint8_t> &c0, const std::vector<uint8_t> &c1, int64_t root, LutCover &out) {
   const size_t NV = NA + NP + 1;
   const int32_t CONST = (int32_t)(NA + NP);
-  std::vector<std::vector<Cut>> cuts(NV);
+  const size_t kMaxCuts = 8;           // non-trivial cuts kept per node
+  const size_t kStride = kMaxCuts + 1;  // + the trivial cut
+  // flat per-thread storage, reused across calls (no per-node allocations)
+  thread_local std::vector<Cut> store;
+  thread_local std::vector<uint8_t> ncut;
+  thread_local std::vector<Cut> scratch;
+  store.resize(NV * kStride);
+  ncut.assign(NV, 0);
+  auto cut_at = [&](size_t v, size_t i) -> Cut & { return store[v * kStride + i]; };
   for (size_t v = NA; v < NV; v++) {
     Cut t;
     if ((int32_t)v == CONST) {
@@ -137,7 +145,8 @@ void lut_map(size_t NA, size_t NP, const std::vector<int64_t> &f0, const std::ve
       t.leaf[0] = (int32_t)v;
       t.tt = 0xAA;
     }
-    cuts[v].push_back(t);
+    cut_at(v, 0) = t;
+    ncut[v] = 1;
   }
   std::vector<uint32_t> fanout(NV, 0);
   for (size_t i = 0; i < NA; i++) {
@@ -147,11 +156,12 @@ void lut_map(size_t NA, size_t NP, const std::vector<int64_t> &f0, const std::ve
   fanout[root]++;
   std::vector<double> af(NV, 0.0);
   std::vector<int> best(NV, -1);
-  const size_t kMaxCuts = 8;
   for (size_t v = 0; v < NA; v++) {
-    std::vector<Cut> &cv = cuts[v];
-    for (const Cut &a : cuts[f0[v]]) {
-      for (const Cut &b : cuts[f1[v]]) {
+    scratch.clear();
+    for (size_t ia = 0; ia < ncut[f0[v]]; ia++) {
+      const Cut &a = cut_at(f0[v], ia);
+      for (size_t ib = 0; ib < ncut[f1[v]]; ib++) {
+        const Cut &b = cut_at(f1[v], ib);
         Cut m;
         if (!merge(a, b, m)) continue;
         const uint8_t ta = (uint8_t)(expand(a.tt, a, m) ^ (c0[v] ? 0xFF : 0x00));
@@ -159,33 +169,35 @@ void lut_map(size_t NA, size_t NP, const std::vector<int64_t> &f0, const std::ve
         m.tt = ta & tb;
         minimise(m);
         bool dup = false;
-        for (const Cut &e : cv)
+        for (const Cut &e : scratch)
           if (e.n == m.n && e.leaf[0] == m.leaf[0] && e.leaf[1] == m.leaf[1] && e.leaf[2] == m.leaf[2]) {
             dup = true;
             break;
           }
-        if (!dup) cv.push_back(m);
+        if (!dup) scratch.push_back(m);
       }
     }
-    // area flow of each cut; keep the best kMaxCuts (the trivial cut is added last)
+    // area flow of each cut; keep the best kMaxCuts, then the trivial cut
     auto flow = [&](const Cut &c) {
       double s = 1.0;
       for (int k = 0; k < c.n; k++)
         if (c.leaf[k] < (int32_t)NA) s += af[c.leaf[k]];
       return s;
     };
-    std::stable_sort(cv.begin(), cv.end(), [&](const Cut &x, const Cut &y) {
+    std::stable_sort(scratch.begin(), scratch.end(), [&](const Cut &x, const Cut &y) {
       const double fx = flow(x), fy = flow(y);
       return fx < fy || (fx == fy && x.n < y.n);
     });
-    if (cv.size() > kMaxCuts) cv.resize(kMaxCuts);
+    const size_t keep = std::min(scratch.size(), kMaxCuts);
+    for (size_t i = 0; i < keep; i++) cut_at(v, i) = scratch[i];
     best[v] = 0;
-    af[v] = cv.empty() ? 1.0 : flow(cv[0]) / std::max<uint32_t>(1, fanout[v]);
+    af[v] = keep == 0 ? 1.0 : flow(scratch[0]) / std::max<uint32_t>(1, fanout[v]);
     Cut t;
     t.n = 1;
     t.leaf[0] = (int32_t)v;
     t.tt = 0xAA;
-    cv.push_back(t);  // trivial cut: used only when v is a leaf of a parent's cut
+    cut_at(v, keep) = t;  // trivial cut: used only when v is a leaf of a parent's cut
+    ncut[v] = (uint8_t)(keep + 1);
   }
 
   // cover with reference counting, then exact-area recovery
@@ -194,7 +206,7 @@ void lut_map(size_t NA, size_t NP, const std::vector<int64_t> &f0, const std::ve
   auto deref = [&](auto &&self, int32_t v) -> uint32_t {  // returns LUTs freed
     if (v >= (int32_t)NA) return 0;
     uint32_t freed = 1;
-    const Cut &c = cuts[v][best[v]];
+    const Cut &c = cut_at(v, best[v]);
     for (int k = 0; k < c.n; k++)
       if (c.leaf[k] < (int32_t)NA && --refs[c.leaf[k]] == 0) freed += self(self, c.leaf[k]);
     return freed;
@@ -202,7 +214,7 @@ void lut_map(size_t NA, size_t NP, const std::vector<int64_t> &f0, const std::ve
   auto ref = [&](auto &&self, int32_t v) -> uint32_t {  // returns LUTs added
     if (v >= (int32_t)NA) return 0;
     uint32_t added = 1;
-    const Cut &c = cuts[v][best[v]];
+    const Cut &c = cut_at(v, best[v]);
     for (int k = 0; k < c.n; k++)
       if (c.leaf[k] < (int32_t)NA && refs[c.leaf[k]]++ == 0) added += self(self, c.leaf[k]);
     return added;
@@ -217,8 +229,8 @@ void lut_map(size_t NA, size_t NP, const std::vector<int64_t> &f0, const std::ve
       deref(deref, (int32_t)v);
       uint32_t best_area = UINT32_MAX;
       int best_i = best[v];
-      const int ncut = (int)cuts[v].size() - 1;  // skip the trivial cut
-      for (int i = 0; i < ncut; i++) {
+      const int nc = (int)ncut[v] - 1;  // skip the trivial cut
+      for (int i = 0; i < nc; i++) {
         best[v] = i;
         const uint32_t a = ref(ref, (int32_t)v);
         deref(deref, (int32_t)v);
@@ -235,7 +247,7 @@ void lut_map(size_t NA, size_t NP, const std::vector<int64_t> &f0, const std::ve
   out.index.assign(NA, -1);
   for (size_t v = 0; v < NA; v++) {
     if (refs[v] == 0) continue;
-    const Cut &c = cuts[v][best[v]];
+    const Cut &c = cut_at(v, best[v]);
     LutCover::Lut l;
     l.node = (int32_t)v;
     l.n = c.n;
