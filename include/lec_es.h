@@ -113,7 +113,7 @@ typedef struct {
   uint32_t grid_blocks;     /* 0 = library choice */
   uint32_t flags;           /* LEC_ES_FLAG_* */
   uint32_t tile_granularity;/* batch: tiles per resident block slot (0 = 16) */
-  uint32_t stage_records;   /* batch: records per staging stage, even, <= 4096 (0 = 512) */
+  uint32_t stage_records;   /* batch: 16-byte records per staging stage, even, <= 2048 (0 = 256) */
 } lec_es_options;
 
 /* Option flags. */

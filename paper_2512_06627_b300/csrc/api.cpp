@@ -184,6 +184,36 @@ int choose_interp_geometry(lec_es_ctx *c, const Program &prog, uint64_t chunks, 
   return LEC_ES_OK;
 }
 
+bool choose_word_geometry(lec_es_ctx *c, const Program &prog, const lec_es_options *opt, PlanGeom &g) {
+  const uint32_t nand = (uint32_t)std::count_if(prog.recs.begin(), prog.recs.end(), [](const Rec &r) { return r.op < 4; });
+  const int pref = opt && opt->block_threads ? (int)opt->block_threads : 256;
+  g = PlanGeom{};
+  for (int b = 256; b >= 32; b /= 2) {
+    if (b > pref) continue;
+    uint32_t ring, res;
+    const size_t bytes = interp_w_smem_bytes(prog.num_slots, nand, b, &ring, &res);
+    if (bytes <= (size_t)c->smem_optin) {
+      g.block = b;
+      g.ring_recs = ring;
+      g.resident = res;
+      g.smem = bytes;
+      g.word = true;
+      g.nrec_padded = nand;
+      break;
+    }
+  }
+  if (!g.word) return false;
+  const uint64_t words = num_words(prog.n);
+  const size_t per_sm = 228u * 1024u;
+  int bps = (int)std::max<size_t>(1, per_sm / (g.smem + 1024));
+  bps = std::min(bps, 2048 / g.block);
+  const uint64_t passes = (words + g.block - 1) / g.block;
+  uint64_t grid = (uint64_t)c->sm_count * bps;
+  if (opt && opt->grid_blocks) grid = opt->grid_blocks;
+  g.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(grid, passes));
+  return true;
+}
+
 }  // namespace lec
 
 // ---- context -------------------------------------------------------------------
@@ -309,6 +339,7 @@ void plan_release(lec_es_ctx *c, lec_es_plan *p) {
   if (!p) return;
   run_res_release(c, p->res);
   c->arena.free(p->d_recs);
+  c->arena.free(p->d_loads);
   c->arena.free(p->d_res);
   c->arena.free(p->d_spill);
   delete p;
@@ -357,9 +388,14 @@ int plan_prepare_program(lec_es_ctx *c, Program &&prog, const lec_es_options *op
     }
     p->tier = LEC_ES_TIER_JIT;
   } else {
-    rc = choose_interp_geometry(c, g, chunks, opt, p->geom);
-    if (rc) return rc;
-    p->tier = p->geom.spill ? LEC_ES_TIER_SPILL : LEC_ES_TIER_INTERP;
+    const bool want_spill = want == LEC_ES_TIER_SPILL;
+    if (!want_spill && choose_word_geometry(c, g, opt, p->geom)) {
+      p->tier = LEC_ES_TIER_INTERP;
+    } else {
+      rc = choose_interp_geometry(c, g, chunks, opt, p->geom);
+      if (rc) return rc;
+      p->tier = p->geom.spill ? LEC_ES_TIER_SPILL : LEC_ES_TIER_INTERP;
+    }
   }
   rc = plan_finish_device(c, p.get());
   if (rc) {
@@ -374,7 +410,22 @@ int plan_prepare_program(lec_es_ctx *c, Program &&prog, const lec_es_options *op
 // Records upload (interpreter tiers), spill scratch, result words, events.
 int plan_finish_device(lec_es_ctx *c, lec_es_plan *p) {
   const Program &g = p->prog;
-  if (p->tier != LEC_ES_TIER_JIT) {
+  if (p->geom.word) {
+    std::vector<XRec> xr;
+    std::vector<XLoad> xl;
+    encode_w(g, p->geom.block, xr, xl, p->out_off);
+    p->nload = (uint32_t)xl.size();
+    p->d_recs = c->arena.alloc(std::max<size_t>(16, xr.size() * sizeof(XRec)));
+    p->d_loads = c->arena.alloc(std::max<size_t>(16, xl.size() * sizeof(XLoad)));
+    if (!p->d_recs || !p->d_loads) return LEC_ES_ENOMEM;
+    if ((!xr.empty() &&
+         cudaMemcpyAsync(p->d_recs, xr.data(), xr.size() * sizeof(XRec), cudaMemcpyHostToDevice, p->stream) !=
+             cudaSuccess) ||
+        (!xl.empty() &&
+         cudaMemcpyAsync(p->d_loads, xl.data(), xl.size() * sizeof(XLoad), cudaMemcpyHostToDevice, p->stream) !=
+             cudaSuccess))
+      return LEC_ES_ECUDA;
+  } else if (p->tier != LEC_ES_TIER_JIT) {
     const size_t rb = (size_t)p->geom.nrec_padded * sizeof(Rec);
     p->d_recs = c->arena.alloc(rb);
     if (!p->d_recs) return LEC_ES_ENOMEM;
@@ -425,6 +476,25 @@ int plan_run_async_grid(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt
   int err;
   if (p->tier == LEC_ES_TIER_JIT) {
     err = jit_launch(c, p, cb, ce, grid_override, ~0ull);
+  } else if (p->geom.word) {
+    XParams xp{};
+    xp.recs = (const XRec *)p->d_recs;
+    xp.loads = (const XLoad *)p->d_loads;
+    xp.nrec = p->geom.nrec_padded;
+    xp.nload = p->nload;
+    xp.out_off = p->out_off;
+    xp.out_compl = g.out_compl;
+    xp.n = g.n;
+    xp.ring_recs = p->geom.ring_recs;
+    xp.resident = p->geom.resident;
+    xp.extra_tx = (p->flags & LEC_ES_FLAG_TEST_WAIT_TIMEOUT) ? 16u : 0u;
+    xp.word_begin = wb;
+    xp.word_end = we;
+    xp.cex = p->d_res;
+    xp.evaluated = p->d_res + 1;
+    xp.status = (uint32_t *)(p->d_res + 2);
+    const int grid = grid_override > 0 ? grid_override : p->geom.grid;
+    err = launch_interp_w(xp, p->geom.block, grid, p->geom.smem, st);
   } else {
     InterpParams ip{};
     ip.recs = (const Rec *)p->d_recs;

@@ -50,8 +50,8 @@ constexpr uint32_t kBatchJitLive = 230;  // table live set that still fits the r
 constexpr int kBranches = 4;             // parallel graph branches
 
 struct Layout {
-  int block = 256;            // threads per tile pass
-  uint32_t ring_recs = 512;   // records per staging stage (4 stages)
+  int block = 256;            // threads (64-pattern words) per tile pass
+  uint32_t ring_recs = 256;   // 16-byte records per staging stage (4 stages)
   uint32_t granularity = 16;  // tiles per resident block slot
 };
 }  // namespace
@@ -64,9 +64,11 @@ struct lec_es_batch_plan {
   std::vector<JitKernel *> jit_kernels;
   std::vector<int> fallback_of;           // miter -> index into fallbacks, or -1
   std::vector<lec_es_plan *> fallbacks;   // live sets beyond the tile kernel's shared memory
-  std::vector<BatchMiter> mt;
   std::vector<size_t> light;              // miters of the tile queue
   uint32_t max_slots = 1;
+  int packed_block = 0;                   // block size the device records are encoded for
+  size_t recs_cap = 0, loads_cap = 0;
+  void *d_loads = nullptr;
   Layout layout;
   int grid = 0;
   size_t smem = 0;
@@ -85,7 +87,7 @@ struct lec_es_batch_plan {
   cudaEvent_t fork = nullptr, join[kBranches] = {};
   bool pending = false;
   double host_ms = 0, jit_ms = 0, tune_ms = 0;
-  BatchParams params{};
+  XBatchParams params{};
 };
 
 namespace {
@@ -113,6 +115,7 @@ void batch_release(lec_es_ctx *c, lec_es_batch_plan *b) {
   if (b->h_cex) cudaFreeHost(b->h_cex);
   if (b->h_status) cudaFreeHost(b->h_status);
   c->arena.free(b->d_recs);
+  c->arena.free(b->d_loads);
   c->arena.free(b->d_miters);
   c->arena.free(b->d_tiles);
   c->arena.free(b->d_cex);
@@ -152,7 +155,8 @@ int stage_programs(lec_es_ctx *c, lec_es_batch_plan *b, const lec_es_miter *m, s
   if (rc) return rc;
   if (cudaSetDevice(c->device) != cudaSuccess) return LEC_ES_ECUDA;
   // live sets the tile kernel holds in shared memory at 64 threads per block
-  const uint32_t max_fit64 = (uint32_t)((c->smem_optin - 64 - 4 * 1024 * 8) / (64 * 4));
+  // (8 bytes per slot per thread, a 4 x 512-record ring)
+  const uint32_t max_fit64 = (uint32_t)((c->smem_optin - 64 - 4 * 512 * 16) / (64 * 8));
   b->jit_of.assign(k, -1);
   b->fallback_of.assign(k, -1);
   const bool allow_jit = !(opt && (opt->tier == LEC_ES_TIER_INTERP || opt->tier == LEC_ES_TIER_SPILL));
@@ -199,41 +203,14 @@ int stage_programs(lec_es_ctx *c, lec_es_batch_plan *b, const lec_es_miter *m, s
     b->fallback_of[i] = (int)b->fallbacks.size();
     b->fallbacks.push_back(p);
   }
-  // pack the light programs
-  b->mt.assign(k, BatchMiter{});
-  size_t total = 0;
-  for (size_t i : b->light) {
-    const Program &g = b->progs[i];
-    const size_t np = std::max<size_t>(2, (g.recs.size() + 1) & ~(size_t)1);
-    BatchMiter &x = b->mt[i];
-    x.rec_off = (uint32_t)total;
-    x.nrec = (uint32_t)g.recs.size();
-    x.nrec_padded = (uint32_t)np;
-    x.nslots = g.num_slots;
-    x.out_slot = g.out_slot;
-    x.out_compl = g.out_compl;
-    x.n = g.n;
-    total += np;
-  }
-  if (total > 0xFFFFFFFFull) return LEC_ES_ETOOBIG;
-  std::vector<Rec> arena(std::max<size_t>(2, total));
-  for (size_t i : b->light)
-    memcpy(&arena[b->mt[i].rec_off], b->progs[i].recs.data(), b->progs[i].recs.size() * sizeof(Rec));
-  b->d_recs = c->arena.alloc(arena.size() * sizeof(Rec));
-  b->d_miters = c->arena.alloc(std::max<size_t>(16, k * sizeof(BatchMiter)));
+  b->d_miters = c->arena.alloc(std::max<size_t>(16, k * sizeof(XMiter)));
   b->d_cex = (unsigned long long *)c->arena.alloc(k * 8);
   b->d_head = (uint32_t *)c->arena.alloc(16);
   b->d_aux = (unsigned long long *)c->arena.alloc(std::max<size_t>(16, b->jit_miters.size() * 16));
-  if (!b->d_recs || !b->d_miters || !b->d_cex || !b->d_head || !b->d_aux) return LEC_ES_ENOMEM;
+  if (!b->d_miters || !b->d_cex || !b->d_head || !b->d_aux) return LEC_ES_ENOMEM;
   if (cudaMallocHost((void **)&b->h_cex, k * 8) != cudaSuccess ||
       cudaMallocHost((void **)&b->h_status, 16) != cudaSuccess)
     return LEC_ES_ENOMEM;
-  cudaStream_t st = c->stream;
-  cudaError_t e = cudaMemcpyAsync(b->d_recs, arena.data(), arena.size() * sizeof(Rec), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->d_miters, b->mt.data(), k * sizeof(BatchMiter), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return LEC_ES_ECUDA;
   if (cudaEventCreate(&b->e0) != cudaSuccess || cudaEventCreate(&b->e1) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
     return LEC_ES_ECUDA;
@@ -249,31 +226,82 @@ int stage_programs(lec_es_ctx *c, lec_es_batch_plan *b, const lec_es_miter *m, s
 int stage_layout(lec_es_ctx *c, lec_es_batch_plan *b, const Layout &L, int grid_override, bool light_only) {
   release_graph(b);
   b->layout = L;
-  b->smem = batch_smem_bytes(b->max_slots, L.block, L.ring_recs);
+  b->smem = batch_w_smem_bytes(b->max_slots, L.block, L.ring_recs);
   if (b->smem > (size_t)c->smem_optin) return LEC_ES_ETOOBIG;
-  if (configure_batch(L.block, b->smem) != 0) return LEC_ES_ECUDA;
-  const int bps = std::max(1, batch_blocks_per_sm(L.block, b->smem));
+  if (configure_batch_w(L.block, b->smem) != 0) return LEC_ES_ECUDA;
+  const int bps = std::max(1, batch_w_blocks_per_sm(L.block, b->smem));
   b->grid = grid_override > 0 ? grid_override : c->sm_count * bps;
-  // tiles sized by cost (records x chunks), big miters first, each miter's
+  cudaStream_t st = c->stream;
+  const size_t k = b->k;
+  // records encoded for this block size (byte offsets depend on it)
+  if (b->packed_block != L.block) {
+    std::vector<XMiter> mt(k, XMiter{});
+    std::vector<XRec> arec;
+    std::vector<XLoad> aload;
+    std::vector<XRec> xr;
+    std::vector<XLoad> xl;
+    for (size_t i : b->light) {
+      XMiter &x = mt[i];
+      encode_w(b->progs[i], L.block, xr, xl, x.out_off);
+      x.rec_off = (uint32_t)arec.size();
+      x.nrec = (uint32_t)xr.size();
+      x.load_off = (uint32_t)aload.size();
+      x.nload = (uint32_t)xl.size();
+      x.out_compl = b->progs[i].out_compl;
+      x.n = b->progs[i].n;
+      arec.insert(arec.end(), xr.begin(), xr.end());
+      aload.insert(aload.end(), xl.begin(), xl.end());
+    }
+    if (arec.size() > 0xFFFFFFF0ull || aload.size() > 0xFFFFFFF0ull) return LEC_ES_ETOOBIG;
+    if (arec.size() > b->recs_cap) {
+      c->arena.free(b->d_recs);
+      b->recs_cap = std::max<size_t>(arec.size(), 16);
+      b->d_recs = c->arena.alloc(b->recs_cap * sizeof(XRec));
+      if (!b->d_recs) return LEC_ES_ENOMEM;
+    }
+    if (aload.size() > b->loads_cap) {
+      c->arena.free(b->d_loads);
+      b->loads_cap = std::max<size_t>(aload.size(), 16);
+      b->d_loads = c->arena.alloc(b->loads_cap * sizeof(XLoad));
+      if (!b->d_loads) return LEC_ES_ENOMEM;
+    }
+    if (!b->d_recs) {
+      b->recs_cap = 16;
+      b->d_recs = c->arena.alloc(16 * sizeof(XRec));
+    }
+    if (!b->d_loads) {
+      b->loads_cap = 16;
+      b->d_loads = c->arena.alloc(16 * sizeof(XLoad));
+    }
+    if (!b->d_recs || !b->d_loads) return LEC_ES_ENOMEM;
+    cudaError_t e = cudaSuccess;
+    if (!arec.empty()) e = cudaMemcpyAsync(b->d_recs, arec.data(), arec.size() * sizeof(XRec), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !aload.empty())
+      e = cudaMemcpyAsync(b->d_loads, aload.data(), aload.size() * sizeof(XLoad), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_miters, mt.data(), k * sizeof(XMiter), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return LEC_ES_ECUDA;
+    b->packed_block = L.block;
+  }
+  // tiles sized by cost (records x words), big miters first, each miter's
   // tiles in ascending pattern order
+  auto cost = [&](size_t i) { return (double)b->progs[i].recs.size() * (double)num_words(b->progs[i].n); };
   double total = 0;
   std::vector<size_t> idx(b->light);
-  for (size_t i : idx) total += (double)b->mt[i].nrec * (double)num_chunks(b->mt[i].n);
-  std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
-    return (double)b->mt[x].nrec * num_chunks(b->mt[x].n) > (double)b->mt[y].nrec * num_chunks(b->mt[y].n);
-  });
+  for (size_t i : idx) total += cost(i);
+  std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) { return cost(x) > cost(y); });
   const double target = std::max(1.0, total / ((double)b->grid * (double)L.granularity));
-  std::vector<BatchTile> tiles;
+  std::vector<XTile> tiles;
   for (size_t i : idx) {
-    const uint64_t C = num_chunks(b->mt[i].n);
-    uint64_t tc = (uint64_t)(target / std::max<uint32_t>(1, b->mt[i].nrec));
-    tc = ((tc + L.block - 1) / L.block) * L.block;
-    tc = std::max<uint64_t>(tc, (uint64_t)L.block);
-    for (uint64_t c0 = 0; c0 < C; c0 += tc) {
-      BatchTile t{};
+    const uint64_t W = num_words(b->progs[i].n);
+    uint64_t tw = (uint64_t)(target / std::max<size_t>(1, b->progs[i].recs.size()));
+    tw = ((tw + L.block - 1) / L.block) * L.block;
+    tw = std::max<uint64_t>(tw, (uint64_t)L.block);
+    for (uint64_t w0 = 0; w0 < W; w0 += tw) {
+      XTile t{};
       t.miter = (uint32_t)i;
-      t.chunk_begin = c0;
-      t.chunk_end = std::min(C, c0 + tc);
+      t.word_begin = w0;
+      t.word_end = std::min(W, w0 + tw);
       tiles.push_back(t);
     }
   }
@@ -282,21 +310,20 @@ int stage_layout(lec_es_ctx *c, lec_es_batch_plan *b, const Layout &L, int grid_
   if (tiles.size() > b->tiles_cap) {
     c->arena.free(b->d_tiles);
     b->tiles_cap = std::max<size_t>(tiles.size(), 16);
-    b->d_tiles = c->arena.alloc(b->tiles_cap * sizeof(BatchTile));
+    b->d_tiles = c->arena.alloc(b->tiles_cap * sizeof(XTile));
     if (!b->d_tiles) return LEC_ES_ENOMEM;
   }
-  cudaStream_t st = c->stream;
   if (!tiles.empty() &&
-      (cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, st) !=
+      (cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(XTile), cudaMemcpyHostToDevice, st) !=
            cudaSuccess ||
        cudaStreamSynchronize(st) != cudaSuccess))
     return LEC_ES_ECUDA;
-  BatchParams &bp = b->params;
-  bp.recs = (const Rec *)b->d_recs;
-  bp.miters = (const BatchMiter *)b->d_miters;
-  bp.tiles = (const BatchTile *)b->d_tiles;
+  XBatchParams &bp = b->params;
+  bp.recs = (const XRec *)b->d_recs;
+  bp.loads = (const XLoad *)b->d_loads;
+  bp.miters = (const XMiter *)b->d_miters;
+  bp.tiles = (const XTile *)b->d_tiles;
   bp.num_tiles = b->num_tiles;
-  bp.max_slots = b->max_slots;
   bp.ring_recs = L.ring_recs;
   bp.cex = b->d_cex;
   bp.head = b->d_head;
@@ -310,7 +337,6 @@ int stage_layout(lec_es_ctx *c, lec_es_batch_plan *b, const Layout &L, int grid_
     return (double)gx.lut.order.size() * num_chunks(gx.n) > (double)gy.lut.order.size() * num_chunks(gy.n);
   });
   int lerr = 0;
-  const size_t k = b->k;
   cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return LEC_ES_ECUDA;
   cudaMemsetAsync(b->d_cex, 0xFF, k * 8, st);
@@ -320,7 +346,7 @@ int stage_layout(lec_es_ctx *c, lec_es_batch_plan *b, const Layout &L, int grid_
   // branches 1, 2, 3, 0, ... so small kernels overlap instead of queueing
   cudaEventRecord(b->fork, st);
   for (int i = 0; i < kBranches; i++) cudaStreamWaitEvent(b->side[i], b->fork, 0);
-  if (b->num_tiles) lerr = launch_batch(bp, L.block, b->grid, b->smem, b->side[0]);
+  if (b->num_tiles) lerr = launch_batch_w(bp, L.block, b->grid, b->smem, b->side[0]);
   for (size_t q = 0; q < jorder.size() && !lerr; q++) {
     const size_t j = jorder[q];
     const uint32_t i = b->jit_miters[j];
@@ -351,7 +377,7 @@ int stage_layout(lec_es_ctx *c, lec_es_batch_plan *b, const Layout &L, int grid_
 // largest live set in steps of 16, SM count.
 uint64_t shape_key(lec_es_ctx *c, const lec_es_batch_plan *b) {
   double work = 0;
-  for (size_t i : b->light) work += (double)b->mt[i].nrec * (double)num_chunks(b->mt[i].n);
+  for (size_t i : b->light) work += (double)b->progs[i].recs.size() * (double)num_words(b->progs[i].n);
   const uint64_t lk = (uint64_t)std::log2((double)b->light.size() + 1.0);
   const uint64_t lw = (uint64_t)std::log2(work + 1.0);
   return (lk << 48) | (lw << 32) | ((uint64_t)(b->max_slots / 16) << 16) | (uint64_t)c->sm_count;
@@ -397,10 +423,10 @@ int autotune(lec_es_ctx *c, lec_es_batch_plan *b, int grid_override, Layout &bes
   bool have = false;
   cudaStream_t st = c->stream;
   for (int blk : {256, 128, 64})
-    for (uint32_t ring : {256u, 512u, 1024u})
+    for (uint32_t ring : {128u, 256u, 512u})
       for (uint32_t gran : {4u, 16u, 64u}) {
         Layout L{blk, ring, gran};
-        if (batch_smem_bytes(b->max_slots, blk, ring) > (size_t)c->smem_optin) continue;
+        if (batch_w_smem_bytes(b->max_slots, blk, ring) > (size_t)c->smem_optin) continue;
         if (stage_layout(c, b, L, grid_override, true) != LEC_ES_OK) continue;
         float t[3] = {0, 0, 0};
         bool ok = true;
@@ -446,9 +472,9 @@ extern "C" int lec_es_batch_prepare(lec_es_ctx *c, const lec_es_miter *m, size_t
       if (opt && opt->stage_records) L.ring_recs = opt->stage_records;
       if (opt && opt->tile_granularity) L.granularity = opt->tile_granularity;
       if (L.block != 64 && L.block != 128 && L.block != 256) rc = LEC_ES_EINVAL;
-      if (L.ring_recs < 2 || (L.ring_recs & 1) || L.ring_recs > 4096) rc = LEC_ES_EINVAL;
+      if (L.ring_recs < 2 || (L.ring_recs & 1) || L.ring_recs > 2048) rc = LEC_ES_EINVAL;
       // a layout that does not fit shared memory falls back to smaller blocks
-      while (!rc && L.block > 64 && batch_smem_bytes(b->max_slots, L.block, L.ring_recs) > (size_t)c->smem_optin)
+      while (!rc && L.block > 64 && batch_w_smem_bytes(b->max_slots, L.block, L.ring_recs) > (size_t)c->smem_optin)
         L.block /= 2;
     }
   }

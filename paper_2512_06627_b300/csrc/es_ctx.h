@@ -37,6 +37,7 @@ struct PlanGeom {
   uint32_t resident = 0;
   uint32_t nrec_padded = 0;
   bool spill = false;
+  bool word = false;  // word-wide shared-memory kernel (else the chunk kernel)
 };
 
 // Pinned result words and events of one run, recycled by the context.
@@ -63,6 +64,9 @@ double now_ms();
 int wait_event(cudaEvent_t ev, double timeout_s);
 int choose_interp_geometry(lec_es_ctx *c, const Program &prog, uint64_t chunks, const lec_es_options *opt,
                            PlanGeom &g);
+// Geometry of the word-wide kernel; false if the live set does not fit
+// shared memory even at 32 threads per block.
+bool choose_word_geometry(lec_es_ctx *c, const Program &prog, const lec_es_options *opt, PlanGeom &g);
 
 // JIT tier (jit.cpp)
 uint32_t jit_auto_tier(lec_es_ctx *c, const Program &g, uint64_t chunks);
@@ -132,6 +136,8 @@ struct lec_es_plan {
   lec::PlanGeom geom;
   uint32_t tier = 0;
   void *d_recs = nullptr;
+  void *d_loads = nullptr;               // word-wide kernel: PI/constant loads
+  uint32_t nload = 0, out_off = 0;
   void *d_spill = nullptr;
   size_t spill_bytes = 0;
   unsigned long long *d_res = nullptr;  // kResWords result words

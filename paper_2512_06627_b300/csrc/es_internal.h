@@ -100,38 +100,54 @@ struct InterpParams {
   uint32_t extra_tx;        // test hook: bytes expected beyond the record copy (0 normally)
 };
 
-// Batched tiles: miter table + tile queue.
-struct BatchMiter {
-  uint32_t rec_off;         // into the shared record arena (records)
-  uint32_t nrec;
-  uint32_t nrec_padded;
-  uint32_t nslots;
-  uint32_t out_slot;
-  uint32_t out_compl;
-  uint32_t n;
-  uint32_t pad;
+// ---- word-wide interpreter (interp_w.cu) -------------------------------------
+// Records pre-decoded for one block size T: byte offsets slot * T * 8 of the
+// two operand slots and the result slot; ctl bit 0/1 complement operand a/b.
+struct XRec {
+  uint32_t a_off, b_off, d_off, ctl;
 };
-
-struct BatchTile {
-  uint32_t miter;
-  uint32_t pad;
-  uint64_t chunk_begin;
-  uint64_t chunk_end;
+// A PI (k < 63) or constant (k = 63) load into d_off before AND record `at`.
+struct XLoad {
+  uint32_t at, d_off, k, pad;
 };
-
-struct BatchParams {
-  const Rec *recs;
-  const BatchMiter *miters;
-  const BatchTile *tiles;
-  uint32_t num_tiles;
-  uint32_t max_slots;       // smem is sized for this
-  uint32_t ring_recs;
-  uint32_t pad;
-  unsigned long long *cex;  // per miter
-  unsigned int *head;       // tile queue head (scratch, zeroed before launch)
+struct XParams {
+  const XRec *recs;
+  const XLoad *loads;
+  uint32_t nrec, nload;
+  uint32_t out_off, out_compl, n;
+  uint32_t ring_recs, resident, extra_tx;
+  uint64_t word_begin, word_end;  // 64-pattern words
+  unsigned long long *cex;
+  unsigned long long *evaluated;
   uint32_t *status;
-  const volatile uint32_t *cancel; // per miter cancel flags (optional)
 };
+struct XMiter {
+  uint32_t rec_off, nrec, load_off, nload, out_off, out_compl, n, pad;
+};
+struct XTile {
+  uint32_t miter, pad;
+  uint64_t word_begin, word_end;
+};
+struct XBatchParams {
+  const XRec *recs;
+  const XLoad *loads;
+  const XMiter *miters;
+  const XTile *tiles;
+  uint32_t num_tiles, ring_recs;
+  unsigned long long *cex;
+  unsigned int *head;
+  uint32_t *status;
+  const volatile uint32_t *cancel;
+};
+
+// Encode a slot program for the word-wide kernels at block size `block`.
+void encode_w(const Program &g, int block, std::vector<XRec> &recs, std::vector<XLoad> &loads, uint32_t &out_off);
+size_t interp_w_smem_bytes(uint32_t nslots, uint32_t nrec, int block, uint32_t *ring_recs, uint32_t *resident);
+size_t batch_w_smem_bytes(uint32_t max_slots, int block, uint32_t ring_recs);
+int launch_interp_w(const XParams &p, int block, int grid, size_t smem, void *stream);
+int configure_batch_w(int block, size_t smem);
+int batch_w_blocks_per_sm(int block, size_t smem);
+int launch_batch_w(const XBatchParams &p, int block, int grid, size_t smem, void *stream);
 
 // Status bits written by kernels.
 enum : uint32_t {
@@ -144,10 +160,6 @@ enum : uint32_t {
 int launch_interp(const InterpParams &p, int block, int grid, size_t smem, bool spill, void *stream);
 int interp_smem_bytes(uint32_t nslots, uint32_t nrec_padded, int block, uint32_t *ring_recs,
                       uint32_t *resident, size_t *bytes);
-int configure_batch(int block, size_t smem);
-int batch_blocks_per_sm(int block, size_t smem);
-int launch_batch(const BatchParams &p, int block, int grid, size_t smem, void *stream);
-size_t batch_smem_bytes(uint32_t max_slots, int block, uint32_t ring_recs);
 int launch_lop3_bench(uint32_t *out, unsigned long long *cycles, int grid, int block, int iters,
                       void *stream);
 int max_smem_optin(int device);

@@ -504,4 +504,19 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
   return LEC_ES_OK;
 }
 
+void encode_w(const Program &g, int block, std::vector<XRec> &recs, std::vector<XLoad> &loads, uint32_t &out_off) {
+  const uint32_t unit = (uint32_t)block * 8u;  // bytes between consecutive slots of one thread
+  recs.clear();
+  loads.clear();
+  recs.reserve(g.recs.size());
+  for (const Rec &r : g.recs) {
+    if (r.op < 4) {
+      recs.push_back(XRec{r.a * unit, r.b * unit, r.dst * unit, (uint32_t)(r.op & 3u)});
+    } else {
+      loads.push_back(XLoad{(uint32_t)recs.size(), r.dst * unit, r.op == OP_PI ? (uint32_t)r.a : 63u, 0u});
+    }
+  }
+  out_off = g.out_slot * unit;
+}
+
 }  // namespace lec

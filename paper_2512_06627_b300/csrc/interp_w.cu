@@ -1,0 +1,439 @@
+// interp_w.cu -- word-wide interpreter: one 64-bit word (two 32-bit halves)
+// per thread, pre-decoded records.
+//
+// The generic tier for cones without a specialised kernel.  Each thread holds
+// the value slots of one 64-pattern word as two 32-bit halves (uint2, so a
+// slot access is one 8-byte shared-memory operation) and evaluates each AND
+// as one LOP3 per half.  The record stream is prepared on the host for the
+// launch's block size:
+//   record  {a_off, b_off, d_off, ctl}: byte offsets of the two operand slots
+//           and the result slot from the thread's slot base, complement bits
+//           in ctl (bit 0: a, bit 1: b), turned into all-zero/all-one masks
+//           with one bit-field extract each -- no branch, no address math;
+//   loads   PI and constant loads live in a separate list {before record i,
+//           d_off, k}, consumed between runs of AND records, so the record
+//           loop has no kind test.
+// Records are staged global->shared by the bulk-copy engine (whole program
+// when it fits, else a 4-stage ring) and read warp-uniformly.  Both the
+// single-miter kernel and the tile-queue batch kernel use this scheme.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "es_internal.h"
+
+namespace lec {
+namespace {
+
+constexpr int NSTAGE = 4;
+constexpr uint32_t kWaitLimit = 1u << 24;
+constexpr uint64_t kWaitNs = 1000000000ull;
+
+__constant__ uint32_t kMaskW[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void expect_and_copy(uint64_t *bar, void *dst, const void *src, uint32_t bytes,
+                                                uint32_t extra) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes + extra)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: gives up after 1 s of global time (or kWaitLimit polls).
+__device__ __forceinline__ bool wait(uint64_t *bar, uint32_t parity) {
+  if (try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0; i < kWaitLimit; i++) {
+    if (try_wait(bar, parity)) return true;
+    if ((i & 15u) == 15u && global_ns() - t0 > kWaitNs) return false;
+    if (i > 64) __nanosleep(128);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void drain(uint64_t *bar, uint32_t inflight, uint32_t parity) {
+  if (threadIdx.x != 0) return;
+  for (int s = 0; s < NSTAGE; s++)
+    if ((inflight >> s) & 1u) (void)wait(bar + s, (parity >> s) & 1u);
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long *p) {
+  return *(const volatile unsigned long long *)p;
+}
+
+// Support PI k for 64-pattern word w, as (low half, high half).
+__device__ __forceinline__ uint2 pi_pair(uint32_t k, uint64_t w) {
+  if (k < 5) return make_uint2(kMaskW[k], kMaskW[k]);
+  if (k == 5) return make_uint2(0u, 0xFFFFFFFFu);
+  if (k == 63) return make_uint2(0u, 0u);  // the constant
+  const uint32_t v = 0u - (uint32_t)((w >> (k - 6)) & 1ull);
+  return make_uint2(v, v);
+}
+
+// Run AND records [0, cnt) of a staged block.  S is this thread's slot base
+// (a byte address in shared memory); record offsets are added to it.
+__device__ __forceinline__ void run_ands(const XRec *rr, uint32_t cnt, uint8_t *S) {
+  const uint4 *r4 = reinterpret_cast<const uint4 *>(rr);
+#pragma unroll 4
+  for (uint32_t i = 0; i < cnt; i++) {
+    const uint4 r = r4[i];  // same address in every lane: broadcast
+    const uint2 x = *reinterpret_cast<const uint2 *>(S + r.x);
+    const uint2 y = *reinterpret_cast<const uint2 *>(S + r.y);
+    int ma, mb;  // all ones when the operand is complemented
+    asm("bfe.s32 %0, %1, 0, 1;" : "=r"(ma) : "r"(r.w));
+    asm("bfe.s32 %0, %1, 1, 1;" : "=r"(mb) : "r"(r.w));
+    uint2 v;
+    v.x = (x.x ^ (uint32_t)ma) & (y.x ^ (uint32_t)mb);
+    v.y = (x.y ^ (uint32_t)ma) & (y.y ^ (uint32_t)mb);
+    *reinterpret_cast<uint2 *>(S + r.z) = v;
+  }
+}
+
+// Execute one staged block of records [base, base + cnt) of the program,
+// applying each load exactly before the record it precedes (a PI may take a
+// slot an earlier record has just freed).  li is the next load (updated).
+__device__ __forceinline__ void run_block(const XRec *rr, uint32_t base, uint32_t cnt, const XLoad *loads,
+                                          uint32_t nload, uint32_t &li, uint8_t *S, uint64_t w) {
+  uint32_t i = 0;
+  for (;;) {
+    while (li < nload && loads[li].at <= base + i) {
+      const XLoad l = loads[li];
+      *reinterpret_cast<uint2 *>(S + l.d_off) = pi_pair(l.k, w);
+      li++;
+    }
+    if (i >= cnt) break;
+    uint32_t stop = cnt;
+    if (li < nload && loads[li].at < base + cnt) stop = loads[li].at - base;
+    run_ands(rr + i, stop - i, S);
+    i = stop;
+  }
+}
+
+__device__ __forceinline__ uint2 valid_pair(uint32_t n) {
+  if (n >= 6) return make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+  if (n == 5) return make_uint2(0xFFFFFFFFu, 0u);
+  return make_uint2((1u << (1u << n)) - 1u, 0u);
+}
+
+// Lowest failing pattern of the warp's words (lane order = word order).
+__device__ __forceinline__ void report(uint2 out, uint64_t w, bool valid, unsigned long long *cex) {
+  const unsigned long long o = valid ? ((unsigned long long)out.y << 32 | out.x) : 0ull;
+  const unsigned bal = __ballot_sync(0xFFFFFFFFu, o != 0ull);
+  if (bal && (int)(threadIdx.x & 31) == __ffs(bal) - 1)
+    atomicMin(cex, (unsigned long long)(w * 64ull + (uint64_t)(__ffsll((long long)o) - 1)));
+}
+
+template <int T>
+__global__ void __launch_bounds__(T) es_interp_w(const XParams p) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  volatile unsigned long long *bcast = reinterpret_cast<unsigned long long *>(smem + 48);
+  XRec *ring = reinterpret_cast<XRec *>(smem + 64);
+  const uint32_t ring_bytes = p.resident ? p.nrec * 16u : NSTAGE * p.ring_recs * 16u;
+  uint8_t *S = smem + 64 + ((ring_bytes + 15u) & ~15u) + threadIdx.x * 8u;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    for (int s = 0; s < NSTAGE; s++) mbar_init(bar + s);
+    fence_init();
+  }
+  __syncthreads();
+  const uint32_t nch = p.resident ? 1u : (p.nrec + p.ring_recs - 1) / p.ring_recs;
+  if (p.resident && p.nrec) {
+    if (t == 0) expect_and_copy(bar, ring, p.recs, p.nrec * 16u, p.extra_tx);
+    const bool ok = wait(bar, 0);
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) atomicOr(p.status, DEV_WAIT_TIMEOUT);
+      drain(bar, 1u, 0u);
+      return;
+    }
+  }
+  uint32_t parity = 0, inflight = 0;
+  const uint64_t total = p.word_end - p.word_begin;
+  const uint64_t passes = (total + T - 1) / T;
+  const uint2 vm = valid_pair(p.n);
+  const uint32_t oc = p.out_compl ? 0xFFFFFFFFu : 0u;
+  unsigned long long done = 0;
+  for (uint64_t pass = blockIdx.x; pass < passes; pass += gridDim.x) {
+    const uint64_t w0 = p.word_begin + pass * T;
+    if (t == 0) *bcast = ld_volatile(p.cex);
+    __syncthreads();
+    if (w0 * 64ull >= *bcast) break;  // block-uniform early exit
+    const uint64_t w = w0 + t;
+    uint32_t li = 0;
+    if (p.resident) {
+      run_block(ring, 0, p.nrec, p.loads, p.nload, li, S, w);
+    } else {
+      for (uint32_t k = 0; k < nch && k < (uint32_t)NSTAGE; k++) {
+        if (t == 0) {
+          const uint32_t off = k * p.ring_recs;
+          expect_and_copy(bar + k, ring + (size_t)k * p.ring_recs, p.recs + off,
+                          min(p.ring_recs, p.nrec - off) * 16u, k == 0 ? p.extra_tx : 0u);
+        }
+        inflight |= 1u << k;
+      }
+      bool bad = false;
+      for (uint32_t k = 0; k < nch; k++) {
+        const uint32_t s = k % NSTAGE;
+        const bool ok = wait(bar + s, (parity >> s) & 1u);
+        if (__syncthreads_or(!ok)) {
+          bad = true;
+          break;
+        }
+        parity ^= 1u << s;
+        inflight &= ~(1u << s);
+        const uint32_t off = k * p.ring_recs;
+        run_block(ring + (size_t)s * p.ring_recs, off, min(p.ring_recs, p.nrec - off), p.loads, p.nload, li, S, w);
+        __syncthreads();
+        if (k + NSTAGE < nch) {
+          if (t == 0) {
+            const uint32_t off2 = (k + NSTAGE) * p.ring_recs;
+            expect_and_copy(bar + s, ring + (size_t)s * p.ring_recs, p.recs + off2,
+                            min(p.ring_recs, p.nrec - off2) * 16u, 0u);
+          }
+          inflight |= 1u << s;
+        }
+      }
+      if (bad) {
+        if (t == 0) atomicOr(p.status, DEV_WAIT_TIMEOUT);
+        drain(bar, inflight, parity);
+        return;
+      }
+    }
+    // loads after the last record (an output that is a PI or the constant)
+    while (li < p.nload) {
+      *reinterpret_cast<uint2 *>(S + p.loads[li].d_off) = pi_pair(p.loads[li].k, w);
+      li++;
+    }
+    uint2 out = *reinterpret_cast<const uint2 *>(S + p.out_off);
+    out.x = (out.x ^ oc) & vm.x;
+    out.y = (out.y ^ oc) & vm.y;
+    report(out, w, w < p.word_end, p.cex);
+    done += (unsigned long long)min((uint64_t)T, p.word_end - w0);
+    __syncthreads();
+  }
+  if (t == 0 && done) atomicAdd(p.evaluated, done * 64ull);
+}
+
+// Tile-queue form: blocks pull (miter, word range) tiles.
+template <int T>
+__global__ void __launch_bounds__(T) es_batch_w(const XBatchParams p) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  volatile unsigned long long *bcast = reinterpret_cast<unsigned long long *>(smem + 40);
+  volatile uint32_t *btile = reinterpret_cast<uint32_t *>(smem + 56);
+  XRec *ring = reinterpret_cast<XRec *>(smem + 64);
+  uint8_t *S = smem + 64 + NSTAGE * p.ring_recs * 16u + threadIdx.x * 8u;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    for (int s = 0; s < NSTAGE; s++) mbar_init(bar + s);
+    fence_init();
+  }
+  __syncthreads();
+  uint32_t parity = 0;
+  for (;;) {
+    if (t == 0) *btile = atomicAdd(p.head, 1u);
+    __syncthreads();
+    const uint32_t tile = *btile;
+    __syncthreads();
+    if (tile >= p.num_tiles) break;
+    const XTile bt = p.tiles[tile];
+    const XMiter bm = p.miters[bt.miter];
+    const XRec *recs = p.recs + bm.rec_off;
+    const XLoad *loads = p.loads + bm.load_off;
+    const uint32_t nch = (bm.nrec + p.ring_recs - 1) / p.ring_recs;
+    const uint2 vm = valid_pair(bm.n);
+    const uint32_t oc = bm.out_compl ? 0xFFFFFFFFu : 0u;
+    const bool resident = nch <= (uint32_t)NSTAGE;  // the whole program fits the ring
+    if (resident && bm.nrec) {
+      uint32_t inflight = 0;
+      for (uint32_t k = 0; k < nch; k++) {
+        if (t == 0) {
+          const uint32_t off = k * p.ring_recs;
+          expect_and_copy(bar + k, ring + (size_t)k * p.ring_recs, recs + off,
+                          min(p.ring_recs, bm.nrec - off) * 16u, 0u);
+        }
+        inflight |= 1u << k;
+      }
+      bool ok = true;
+      for (uint32_t k = 0; k < nch && ok; k++) {
+        ok = wait(bar + k, (parity >> k) & 1u);
+        if (ok) {
+          parity ^= 1u << k;
+          inflight &= ~(1u << k);
+        }
+      }
+      if (__syncthreads_or(!ok)) {
+        if (t == 0) atomicOr(p.status, DEV_WAIT_TIMEOUT);
+        drain(bar, inflight, parity);
+        return;
+      }
+    }
+    for (uint64_t w0 = bt.word_begin; w0 < bt.word_end; w0 += T) {
+      if (t == 0) {
+        unsigned long long cur = ld_volatile(p.cex + bt.miter);
+        if (p.cancel && p.cancel[bt.miter]) cur = 0;
+        *bcast = cur;
+      }
+      __syncthreads();
+      const unsigned long long cur = *bcast;
+      __syncthreads();
+      if (w0 * 64ull >= cur) break;
+      const uint64_t w = w0 + t;
+      uint32_t li = 0;
+      if (resident) {
+        run_block(ring, 0, bm.nrec, loads, bm.nload, li, S, w);
+      } else {
+        uint32_t inflight = 0;
+        for (uint32_t k = 0; k < (uint32_t)NSTAGE; k++) {
+          if (t == 0) {
+            const uint32_t off = k * p.ring_recs;
+            expect_and_copy(bar + k, ring + (size_t)k * p.ring_recs, recs + off,
+                            min(p.ring_recs, bm.nrec - off) * 16u, 0u);
+          }
+          inflight |= 1u << k;
+        }
+        bool bad = false;
+        for (uint32_t k = 0; k < nch; k++) {
+          const uint32_t s = k % NSTAGE;
+          const bool ok = wait(bar + s, (parity >> s) & 1u);
+          if (__syncthreads_or(!ok)) {
+            bad = true;
+            break;
+          }
+          parity ^= 1u << s;
+          inflight &= ~(1u << s);
+          const uint32_t off = k * p.ring_recs;
+          run_block(ring + (size_t)s * p.ring_recs, off, min(p.ring_recs, bm.nrec - off), loads, bm.nload, li, S,
+                    w);
+          __syncthreads();
+          if (k + NSTAGE < nch) {
+            if (t == 0) {
+              const uint32_t off2 = (k + NSTAGE) * p.ring_recs;
+              expect_and_copy(bar + s, ring + (size_t)s * p.ring_recs, recs + off2,
+                              min(p.ring_recs, bm.nrec - off2) * 16u, 0u);
+            }
+            inflight |= 1u << s;
+          }
+        }
+        if (bad) {
+          if (t == 0) atomicOr(p.status, DEV_WAIT_TIMEOUT);
+          drain(bar, inflight, parity);
+          return;
+        }
+      }
+      while (li < bm.nload) {
+        *reinterpret_cast<uint2 *>(S + loads[li].d_off) = pi_pair(loads[li].k, w);
+        li++;
+      }
+      uint2 out = *reinterpret_cast<const uint2 *>(S + bm.out_off);
+      out.x = (out.x ^ oc) & vm.x;
+      out.y = (out.y ^ oc) & vm.y;
+      report(out, w, w < bt.word_end, p.cex + bt.miter);
+      __syncthreads();
+    }
+    __syncthreads();  // ring reuse by the next tile
+  }
+}
+
+template <int T>
+int launch_w(const XParams &p, int grid, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(es_interp_w<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  es_interp_w<T><<<grid, T, smem, st>>>(p);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+size_t interp_w_smem_bytes(uint32_t nslots, uint32_t nrec, int block, uint32_t *ring_recs, uint32_t *resident) {
+  const size_t limit = 227u * 1024u;
+  const size_t slots = (size_t)nslots * block * 8u;
+  const size_t whole = 64 + (size_t)nrec * 16u + slots;
+  if (whole <= limit) {
+    *resident = 1;
+    *ring_recs = nrec;
+    return whole;
+  }
+  *resident = 0;
+  *ring_recs = 256;
+  return 64 + (size_t)NSTAGE * 256u * 16u + slots;
+}
+
+size_t batch_w_smem_bytes(uint32_t max_slots, int block, uint32_t ring_recs) {
+  return 64 + (size_t)NSTAGE * ring_recs * 16u + (size_t)max_slots * block * 8u;
+}
+
+int launch_interp_w(const XParams &p, int block, int grid, size_t smem, void *stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (block) {
+    case 32: return launch_w<32>(p, grid, smem, st);
+    case 64: return launch_w<64>(p, grid, smem, st);
+    case 128: return launch_w<128>(p, grid, smem, st);
+    case 256: return launch_w<256>(p, grid, smem, st);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
+
+int configure_batch_w(int block, size_t smem) {
+  cudaError_t e;
+  switch (block) {
+    case 64: e = cudaFuncSetAttribute(es_batch_w<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+    case 128: e = cudaFuncSetAttribute(es_batch_w<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+    case 256: e = cudaFuncSetAttribute(es_batch_w<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+    default: return (int)cudaErrorInvalidValue;
+  }
+  return (int)e;
+}
+
+int batch_w_blocks_per_sm(int block, size_t smem) {
+  int n = 0;
+  cudaError_t e;
+  switch (block) {
+    case 64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, es_batch_w<64>, 64, smem); break;
+    case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, es_batch_w<128>, 128, smem); break;
+    case 256: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, es_batch_w<256>, 256, smem); break;
+    default: return 0;
+  }
+  return e == cudaSuccess ? n : 0;
+}
+
+int launch_batch_w(const XBatchParams &p, int block, int grid, size_t smem, void *stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (block) {
+    case 64: es_batch_w<64><<<grid, 64, smem, st>>>(p); break;
+    case 128: es_batch_w<128><<<grid, 128, smem, st>>>(p); break;
+    case 256: es_batch_w<256><<<grid, 256, smem, st>>>(p); break;
+    default: return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
+}
+
+}  // namespace lec

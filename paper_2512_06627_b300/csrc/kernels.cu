@@ -14,8 +14,9 @@
 //               once (it fits) or through a 4-stage ring; value slots live in
 //               shared memory (slot-major, lane-minor: conflict-free) or, for
 //               live sets too large for shared memory, in global memory.
-//   es_batch    persistent kernel over a queue of (miter, chunk range) tiles
-//               pulled with atomicAdd; per-miter counterexample.
+//               The single-miter interpreter tier itself runs the word-wide
+//               kernel (interp_w.cu); this one serves the spill tier, the
+//               truth-table dump and the allocation-free entry point.
 //   lop3_bench  throughput microbenchmark of 32-bit LOP3.
 //
 // Every AND is one LOP3 per 32-bit lane: (x ^ ca) & (y ^ cb) with warp-uniform
@@ -256,134 +257,6 @@ __global__ void __launch_bounds__(T) es_interp(const InterpParams p) {
 }
 
 // ---------------------------------------------------------------------------
-// Persistent batch kernel: blocks pull (miter, chunk range) tiles.
-// ---------------------------------------------------------------------------
-template <int T>
-__global__ void __launch_bounds__(T) es_batch(const BatchParams p) {
-  extern __shared__ __align__(128) uint8_t smem[];
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-  volatile unsigned long long *bcast = reinterpret_cast<unsigned long long *>(smem + 40);
-  volatile uint32_t *btile = reinterpret_cast<uint32_t *>(smem + 56);
-  Rec *ring = reinterpret_cast<Rec *>(smem + 64);
-  uint32_t *S = reinterpret_cast<uint32_t *>(smem + 64 + NSTAGE * p.ring_recs * 8u) + threadIdx.x;
-  const int t = threadIdx.x;
-  if (t == 0) {
-    for (int s = 0; s < NSTAGE; s++) mbar_init(bar + s, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  uint32_t parity = 0;
-  for (;;) {
-    if (t == 0) *btile = atomicAdd(p.head, 1u);
-    __syncthreads();
-    const uint32_t tile = *btile;
-    __syncthreads();
-    if (tile >= p.num_tiles) break;
-    const BatchTile bt = p.tiles[tile];
-    const BatchMiter bm = p.miters[bt.miter];
-    const Rec *recs = p.recs + bm.rec_off;
-    const uint32_t nch = (bm.nrec + p.ring_recs - 1) / p.ring_recs;
-    const uint32_t vmask = valid_mask(bm.n);
-    const uint32_t ocompl = bm.out_compl ? 0xFFFFFFFFu : 0u;
-    const bool resident = nch <= (uint32_t)NSTAGE;  // program fits the ring: stage once per tile
-    if (resident && t == 0) {
-      for (uint32_t k = 0; k < nch; k++) {
-        const uint32_t off = k * p.ring_recs;
-        const uint32_t cnt = min(p.ring_recs, bm.nrec_padded - off);
-        mbar_arrive_expect_tx(bar + k, cnt * 8u);
-        bulk_g2s(ring + (size_t)k * p.ring_recs, recs + off, cnt * 8u, bar + k);
-      }
-    }
-    if (resident) {
-      uint32_t inflight = (1u << nch) - 1u;
-      bool ok = true;
-      for (uint32_t k = 0; k < nch && ok; k++) {
-        ok = mbar_wait(bar + k, (parity >> k) & 1u);
-        if (ok) {
-          parity ^= 1u << k;
-          inflight &= ~(1u << k);
-        }
-      }
-      if (__syncthreads_or(!ok)) {
-        if (t == 0) atomicOr(p.status, DEV_WAIT_TIMEOUT);
-        drain_inflight(bar, inflight, parity);
-        return;
-      }
-    }
-    for (uint64_t c0 = bt.chunk_begin; c0 < bt.chunk_end; c0 += T) {
-      if (t == 0) {
-        unsigned long long cur = ld_volatile_u64(p.cex + bt.miter);
-        if (p.cancel && p.cancel[bt.miter]) cur = 0;
-        *bcast = cur;
-      }
-      __syncthreads();
-      const unsigned long long cur = *bcast;
-      __syncthreads();
-      if (c0 * 32ull >= cur) break;
-      const uint64_t c = c0 + t;
-      InterpParams dummy;
-      if (resident) {
-        for (uint32_t k = 0; k < nch; k++) {
-          const uint32_t off = k * p.ring_recs;
-          run_records<false>(ring + (size_t)k * p.ring_recs, min(p.ring_recs, bm.nrec - off), S, T, c, 0,
-                             dummy);
-        }
-      } else {
-        uint32_t inflight = 0;
-        for (uint32_t k = 0; k < (uint32_t)NSTAGE; k++) {
-          if (t == 0) {
-            const uint32_t off = k * p.ring_recs;
-            const uint32_t cnt = min(p.ring_recs, bm.nrec_padded - off);
-            mbar_arrive_expect_tx(bar + k, cnt * 8u);
-            bulk_g2s(ring + (size_t)k * p.ring_recs, recs + off, cnt * 8u, bar + k);
-          }
-          inflight |= 1u << k;
-        }
-        bool bad = false;
-        for (uint32_t k = 0; k < nch; k++) {
-          const uint32_t s = k % NSTAGE;
-          const bool ok = mbar_wait(bar + s, (parity >> s) & 1u);
-          if (__syncthreads_or(!ok)) {
-            bad = true;
-            break;
-          }
-          parity ^= 1u << s;
-          inflight &= ~(1u << s);
-          const uint32_t off = k * p.ring_recs;
-          run_records<false>(ring + (size_t)s * p.ring_recs, min(p.ring_recs, bm.nrec - off), S, T, c, 0,
-                             dummy);
-          __syncthreads();
-          if (k + NSTAGE < nch) {
-            if (t == 0) {
-              const uint32_t off2 = (k + NSTAGE) * p.ring_recs;
-              const uint32_t cnt = min(p.ring_recs, bm.nrec_padded - off2);
-              mbar_arrive_expect_tx(bar + s, cnt * 8u);
-              bulk_g2s(ring + (size_t)s * p.ring_recs, recs + off2, cnt * 8u, bar + s);
-            }
-            inflight |= 1u << s;
-          }
-        }
-        if (bad) {
-          if (t == 0) atomicOr(p.status, DEV_WAIT_TIMEOUT);
-          drain_inflight(bar, inflight, parity);
-          return;
-        }
-      }
-      uint32_t out = (S[bm.out_slot * T] ^ ocompl) & vmask;
-      if (c >= bt.chunk_end) out = 0;
-      const unsigned bal = __ballot_sync(0xFFFFFFFFu, out != 0u);
-      if (bal) {
-        const int lane = __ffs(bal) - 1;
-        if ((t & 31) == lane)
-          atomicMin(p.cex + bt.miter, (unsigned long long)(c * 32ull + (uint64_t)(__ffs(out) - 1)));
-      }
-      __syncthreads();
-    }
-    __syncthreads();  // ring reuse by the next tile
-  }
-}
-
-// ---------------------------------------------------------------------------
 // LOP3 throughput microbenchmark: 8 independent chains per thread.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) lop3_bench(uint32_t *out, unsigned long long *cycles, int iters) {
@@ -456,51 +329,12 @@ int interp_smem_bytes(uint32_t nslots, uint32_t nrec_padded, int block, uint32_t
   return *bytes <= limit ? 0 : 1;
 }
 
-size_t batch_smem_bytes(uint32_t max_slots, int block, uint32_t ring_recs) {
-  return 64 + (size_t)NSTAGE * ring_recs * 8u + (size_t)max_slots * block * 4u;
-}
-
 int launch_interp(const InterpParams &p, int block, int grid, size_t smem, bool spill, void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const bool tt = p.tt_out != nullptr;
   if (spill) return tt ? launch_block<true, true>(p, block, grid, smem, st)
                        : launch_block<true, false>(p, block, grid, smem, st);
   return tt ? launch_block<false, true>(p, block, grid, smem, st) : launch_block<false, false>(p, block, grid, smem, st);
-}
-
-int configure_batch(int block, size_t smem) {
-  cudaError_t e;
-  switch (block) {
-    case 64: e = cudaFuncSetAttribute(es_batch<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-    case 128: e = cudaFuncSetAttribute(es_batch<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-    case 256: e = cudaFuncSetAttribute(es_batch<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-    default: return (int)cudaErrorInvalidValue;
-  }
-  return (int)e;
-}
-
-int batch_blocks_per_sm(int block, size_t smem) {
-  int n = 0;
-  cudaError_t e;
-  switch (block) {
-    case 64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, es_batch<64>, 64, smem); break;
-    case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, es_batch<128>, 128, smem); break;
-    case 256: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, es_batch<256>, 256, smem); break;
-    default: return 0;
-  }
-  return e == cudaSuccess ? n : 0;
-}
-
-// Launch only (configure_batch first): safe inside stream capture.
-int launch_batch(const BatchParams &p, int block, int grid, size_t smem, void *stream) {
-  cudaStream_t st = (cudaStream_t)stream;
-  switch (block) {
-    case 64: es_batch<64><<<grid, 64, smem, st>>>(p); break;
-    case 128: es_batch<128><<<grid, 128, smem, st>>>(p); break;
-    case 256: es_batch<256><<<grid, 256, smem, st>>>(p); break;
-    default: return (int)cudaErrorInvalidValue;
-  }
-  return (int)cudaGetLastError();
 }
 
 int launch_lop3_bench(uint32_t *out, unsigned long long *cycles, int grid, int block, int iters, void *stream) {

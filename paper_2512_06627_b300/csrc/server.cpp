@@ -53,8 +53,10 @@ struct Slot {
   bool busy = false;
 };
 
-struct Resident {  // device copy of one program's records
+struct Resident {  // device copy of one program's records (word-wide kernel)
   void *d_recs = nullptr;
+  void *d_loads = nullptr;
+  uint32_t nload = 0, out_off = 0;
   PlanGeom geom;
 };
 
@@ -139,16 +141,26 @@ int launch(Server *s, Request *r) {
     auto it = s->resident.find(g.hash);
     if (it == s->resident.end()) {
       Resident rr;
-      if (choose_interp_geometry(c, g, C, nullptr, rr.geom)) return LEC_ES_EINVAL;
-      if (rr.geom.spill) return LEC_ES_ETOOBIG;  // served requests keep slots on chip
-      const size_t rb = (size_t)rr.geom.nrec_padded * sizeof(Rec);
-      rr.d_recs = c->arena.alloc(rb);
-      if (!rr.d_recs) return LEC_ES_ENOMEM;
-      std::vector<Rec> padded(rr.geom.nrec_padded);
-      memcpy(padded.data(), g.recs.data(), g.recs.size() * sizeof(Rec));
-      if (cudaMemcpyAsync(rr.d_recs, padded.data(), rb, cudaMemcpyHostToDevice, s->ctl) != cudaSuccess ||
-          cudaStreamSynchronize(s->ctl) != cudaSuccess) {
+      if (!choose_word_geometry(c, g, nullptr, rr.geom)) return LEC_ES_ETOOBIG;  // slots stay on chip
+      std::vector<XRec> xr;
+      std::vector<XLoad> xl;
+      encode_w(g, rr.geom.block, xr, xl, rr.out_off);
+      rr.nload = (uint32_t)xl.size();
+      rr.d_recs = c->arena.alloc(std::max<size_t>(16, xr.size() * sizeof(XRec)));
+      rr.d_loads = c->arena.alloc(std::max<size_t>(16, xl.size() * sizeof(XLoad)));
+      if (!rr.d_recs || !rr.d_loads) {
         c->arena.free(rr.d_recs);
+        c->arena.free(rr.d_loads);
+        return LEC_ES_ENOMEM;
+      }
+      cudaError_t e = cudaSuccess;
+      if (!xr.empty()) e = cudaMemcpyAsync(rr.d_recs, xr.data(), xr.size() * sizeof(XRec), cudaMemcpyHostToDevice, s->ctl);
+      if (e == cudaSuccess && !xl.empty())
+        e = cudaMemcpyAsync(rr.d_loads, xl.data(), xl.size() * sizeof(XLoad), cudaMemcpyHostToDevice, s->ctl);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s->ctl);
+      if (e != cudaSuccess) {
+        c->arena.free(rr.d_recs);
+        c->arena.free(rr.d_loads);
         return LEC_ES_ECUDA;
       }
       it = s->resident.emplace(g.hash, rr).first;
@@ -173,24 +185,25 @@ int launch(Server *s, Request *r) {
               : 1;
     r->tier = LEC_ES_TIER_JIT;
   } else {
-    InterpParams ip{};
-    ip.recs = (const Rec *)res->d_recs;
-    ip.nrec = (uint32_t)g.recs.size();
-    ip.nrec_padded = res->geom.nrec_padded;
-    ip.nslots = g.num_slots;
-    ip.out_slot = g.out_slot;
-    ip.out_compl = g.out_compl;
-    ip.n = g.n;
-    ip.ring_recs = res->geom.ring_recs;
-    ip.resident = res->geom.resident;
-    ip.chunk_begin = 0;
-    ip.chunk_end = C;
-    ip.cex = sl.d_res;
-    ip.evaluated = sl.d_res + 1;
-    ip.status = (uint32_t *)(sl.d_res + 2);
-    const uint64_t passes = (C + res->geom.block - 1) / res->geom.block;
+    XParams xp{};
+    xp.recs = (const XRec *)res->d_recs;
+    xp.loads = (const XLoad *)res->d_loads;
+    xp.nrec = res->geom.nrec_padded;
+    xp.nload = res->nload;
+    xp.out_off = res->out_off;
+    xp.out_compl = g.out_compl;
+    xp.n = g.n;
+    xp.ring_recs = res->geom.ring_recs;
+    xp.resident = res->geom.resident;
+    xp.word_begin = 0;
+    xp.word_end = num_words(g.n);
+    xp.cex = sl.d_res;
+    xp.evaluated = sl.d_res + 1;
+    xp.status = (uint32_t *)(sl.d_res + 2);
+    // a few passes per block, so blocks retire and other requests interleave
+    const uint64_t passes = (xp.word_end + res->geom.block - 1) / res->geom.block;
     const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>((passes + 3) / 4, 1u << 30));
-    err = launch_interp(ip, res->geom.block, (int)grid, res->geom.smem, false, st);
+    err = launch_interp_w(xp, res->geom.block, (int)grid, res->geom.smem, st);
     r->tier = LEC_ES_TIER_INTERP;
   }
   if (err) return LEC_ES_ECUDA;
@@ -378,7 +391,10 @@ void server_shutdown(lec_es_ctx *c) {
     if (sl.e1) cudaEventDestroy(sl.e1);
     if (sl.e2) cudaEventDestroy(sl.e2);
   }
-  for (auto &kv : s->resident) c->arena.free(kv.second.d_recs);
+  for (auto &kv : s->resident) {
+    c->arena.free(kv.second.d_recs);
+    c->arena.free(kv.second.d_loads);
+  }
   if (s->h_zero) cudaFreeHost(s->h_zero);
   s->cv_done.notify_all();
   delete s;

@@ -72,7 +72,7 @@ def test_layouts_and_autotune_give_identical_results(ctx, pairs, tmp_path):
     sel = list(range(0, 4096, 5))
     ms = [L.Miter(pairs.aig.num_pis, f, pairs.aig.outputs[i]) for i in sel]
     ref = None
-    for blk, gran, ring in [(256, 16, 512), (128, 4, 256), (64, 64, 1024), (256, 1, 2)]:
+    for blk, gran, ring in [(256, 16, 256), (128, 4, 128), (64, 64, 1024), (256, 1, 2)]:
         b = L.lec_es_batch_prepare(ctx, ms, L.options(tier=L.TIER_INTERP, block_threads=blk,
                                                        tile_granularity=gran, stage_records=ring))
         info = L.lec_es_batch_info(b)
