@@ -312,7 +312,7 @@ extern "C" int lec_es_compile(const lec_es_miter *m, uint32_t order, lec_es_prog
   info->order = p.order;
   info->num_records = p.recs.size();
   info->hash = p.hash;
-  info->num_luts = (uint32_t)p.lut.order.size();
+  info->num_luts = p.lut.count;
   info->lut_live = p.lut.live;
   if (records && cap) memcpy(records, p.recs.data(), sizeof(Rec) * std::min<uint64_t>(cap, p.recs.size()));
   return LEC_ES_OK;
@@ -353,7 +353,8 @@ int plan_prepare(lec_es_ctx *c, const lec_es_miter *m, const lec_es_options *opt
   MiterView v{m->num_pis, m->num_ands, m->fanins, m->out_lit};
   int rc;
   try {
-    rc = compile_program(v, opt ? opt->order : LEC_ES_ORDER_AUTO, c->max_pis, prog);
+    const KernelProbe probe{jit_have_kernel, c};
+    rc = compile_program(v, opt ? opt->order : LEC_ES_ORDER_AUTO, c->max_pis, prog, &probe);
   } catch (const std::bad_alloc &) {
     return LEC_ES_ENOMEM;
   }
@@ -585,7 +586,7 @@ extern "C" int lec_es_plan_info(const lec_es_plan *p, lec_es_program_info *info)
   info->order = g.order;
   info->num_records = g.recs.size();
   info->hash = g.hash;
-  info->num_luts = (uint32_t)g.lut.order.size();
+  info->num_luts = g.lut.count;
   info->lut_live = g.lut.live;
   return LEC_ES_OK;
 }

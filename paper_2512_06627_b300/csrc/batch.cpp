@@ -135,7 +135,8 @@ int compile_all(lec_es_ctx *c, const lec_es_miter *m, size_t k, uint32_t order, 
       for (size_t i = t; i < k; i += nt) {
         MiterView v{m[i].num_pis, m[i].num_ands, m[i].fanins, m[i].out_lit};
         try {
-          rcs[i] = compile_program(v, order, c->max_pis, progs[i]);
+          const KernelProbe probe{jit_have_kernel, c};
+          rcs[i] = compile_program(v, order, c->max_pis, progs[i], &probe);
         } catch (const std::bad_alloc &) {
           rcs[i] = LEC_ES_ENOMEM;
         }
@@ -163,7 +164,7 @@ int stage_programs(lec_es_ctx *c, lec_es_batch_plan *b, const lec_es_miter *m, s
   for (size_t i = 0; i < k; i++) {
     const Program &g = b->progs[i];
     const double work = (double)g.recs.size() * (double)num_chunks(g.n);
-    if (allow_jit && work >= kBatchJitWork && !g.lut.order.empty() && g.lut.live <= kBatchJitLive) {
+    if (allow_jit && work >= kBatchJitWork && g.lut.count && g.lut.live <= kBatchJitLive) {
       b->jit_of[i] = (int)b->jit_miters.size();
       b->jit_miters.push_back((uint32_t)i);
     } else if (g.num_slots > max_fit64) {
@@ -334,7 +335,7 @@ int stage_layout(lec_es_ctx *c, lec_es_batch_plan *b, const Layout &L, int grid_
   for (size_t j = 0; j < jorder.size(); j++) jorder[j] = j;
   std::stable_sort(jorder.begin(), jorder.end(), [&](size_t x, size_t y) {
     const Program &gx = b->progs[b->jit_miters[x]], &gy = b->progs[b->jit_miters[y]];
-    return (double)gx.lut.order.size() * num_chunks(gx.n) > (double)gy.lut.order.size() * num_chunks(gy.n);
+    return (double)gx.lut.count * num_chunks(gx.n) > (double)gy.lut.count * num_chunks(gy.n);
   });
   int lerr = 0;
   cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);

@@ -56,6 +56,8 @@ struct JitKernel {
   double compile_ms = 0;   // whole build
   double nvrtc_ms = 0;     // of which NVRTC (0 on a disk-cache hit)
   double load_ms = 0;      // of which loading the cubin and querying the kernel
+  uint32_t num_luts = 0;   // the program's table count and live count when built
+  uint32_t lut_live = 0;
 };
 struct JitState;
 struct Server;
@@ -79,6 +81,9 @@ lec::JitKernel *jit_lookup_or_schedule(lec_es_ctx *c, const Program &g);
 int jit_attach(lec_es_ctx *c, lec_es_plan *p, JitKernel *k, const lec_es_options *opt);
 // Cached kernel for a program (compiled on a miss; thread-safe).
 int jit_get_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out, double *compile_ms);
+// KernelProbe callback (arg = the context): the compiled table-form kernel
+// for a program hash, if this context holds one.
+bool jit_have_kernel(void *arg, uint64_t hash, uint32_t *luts, uint32_t *live);
 void jit_release_all(lec_es_ctx *c);
 
 // single-miter plans (api.cpp)

@@ -43,6 +43,8 @@ struct LutProgram {
   std::vector<LutCover::Lut> order;      // evaluation order (topological)
   int64_t root = -1;                     // value id of the output's node
   uint32_t live = 0;                     // peak number of live values in this order
+  uint32_t count = 0;                    // tables in the cover (order.size() unless elided)
+  bool elided = false;                   // cover not built: the specialised kernel exists
 };
 
 // Compiled cone (paper §3.3 "Instructionalized ES"): branch-free instruction
@@ -68,7 +70,17 @@ struct MiterView {
 };
 
 // Front end.  Returns an lec_es_status code.
-int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Program &out);
+// The table cover only feeds code generation for the specialised kernel.  A
+// caller that already holds that kernel (looked up by the program hash) can
+// pass `have_kernel`: when it returns true with the kernel's table count and
+// live count, the cover is not rebuilt and the LutProgram is marked elided.
+struct KernelProbe {
+  bool (*have_kernel)(void *arg, uint64_t hash, uint32_t *luts, uint32_t *live);
+  void *arg;
+};
+
+int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Program &out,
+                    const KernelProbe *probe = nullptr);
 
 // Words of 64 patterns for a support of n PIs.
 inline uint64_t num_words(uint32_t n) { return n <= 6 ? 1ull : (1ull << (n - 6)); }

@@ -435,7 +435,7 @@ uint64_t fnv1a(const void *data, size_t len, uint64_t h) {
 
 }  // namespace
 
-int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Program &out) {
+int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Program &out, const KernelProbe *probe) {
   thread_local std::vector<uint8_t> mark;
   thread_local std::vector<int32_t> dense;
   Cone c;
@@ -455,10 +455,6 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
   else if (order <= LEC_ES_ORDER_GREEDY) tried.push_back(order);
   else return LEC_ES_EINVAL;
 
-  // the table cover does not depend on the order
-  LutProgram lp;
-  LutCover cov;
-  cover_cone(m, c, ix, root_var, lp, cov);
   std::vector<Program> cand(tried.size());
   std::vector<int> crc(tried.size(), LEC_ES_OK);
   auto run_order = [&](size_t t) {
@@ -487,19 +483,32 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
   for (size_t k = 0; k < c.pis.size(); k++) best.support[k] = c.pis[k] - 1;
   best.cone_ands = (uint32_t)c.ands.size();
   best.out_compl = m.out_lit & 1;
-  {
-    // the AND positions (into the ascending cone list) of the chosen slot order
-    std::vector<uint32_t> and_order;
-    and_order.reserve(best.order_vars.size());
-    for (uint32_t var : best.order_vars) and_order.push_back((uint32_t)ix.and_pos(var));
-    order_luts(c, and_order, cov, lp);
-    best.lut = std::move(lp);
-  }
   if (best.num_slots == 0) best.num_slots = 1;
   uint64_t h = 1469598103934665603ull;
   h = fnv1a(best.recs.data(), best.recs.size() * sizeof(Rec), h);
   uint32_t tail[3] = {best.n, best.out_slot, best.out_compl};
   best.hash = fnv1a(tail, sizeof(tail), h);
+  uint32_t luts = 0, live = 0;
+  if (probe && probe->have_kernel(probe->arg, best.hash, &luts, &live)) {
+    best.lut.na = (uint32_t)c.ands.size();
+    best.lut.np = (uint32_t)c.pis.size();
+    best.lut.root = ix.vid(root_var);
+    best.lut.count = luts;
+    best.lut.live = live;
+    best.lut.elided = true;
+  } else {
+    // the table cover (independent of the slot order), then its evaluation
+    // order, one candidate of which follows the chosen slot order
+    LutProgram lp;
+    LutCover cov;
+    cover_cone(m, c, ix, root_var, lp, cov);
+    std::vector<uint32_t> and_order;
+    and_order.reserve(best.order_vars.size());
+    for (uint32_t var : best.order_vars) and_order.push_back((uint32_t)ix.and_pos(var));
+    order_luts(c, and_order, cov, lp);
+    lp.count = (uint32_t)lp.order.size();
+    best.lut = std::move(lp);
+  }
   out = std::move(best);
   return LEC_ES_OK;
 }

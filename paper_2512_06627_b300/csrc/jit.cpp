@@ -452,7 +452,7 @@ JitState *state(lec_es_ctx *c);
 // pays off only for large work.
 uint32_t jit_auto_tier(lec_es_ctx *c, const Program &g, uint64_t chunks) {
   const double work = (double)g.recs.size() * (double)chunks;
-  if (g.lut.order.empty() || g.lut.live > kMaxJitLive || work < kJitCachedWork) return LEC_ES_TIER_INTERP;
+  if (g.lut.count == 0 || g.lut.live > kMaxJitLive || work < kJitCachedWork) return LEC_ES_TIER_INTERP;
   if (work >= kJitColdWork) return LEC_ES_TIER_JIT;
   JitState *js = state(c);
   std::lock_guard<std::mutex> lk(js->mu);
@@ -463,6 +463,9 @@ namespace {
 
 // Compile (or read from the disk cache) and load one program's kernel.
 int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out) {
+  // an elided cover means the kernel was found by hash; generating code from
+  // it would drop the tables
+  if (lut_form && g.lut.elided) return LEC_ES_EINVAL;
   const double t0 = now_ms();
   std::vector<char> cubin;
   std::string path;
@@ -504,6 +507,8 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void *)k->kern, kJitBlock, 0);
   k->blocks_per_sm = std::max(1, bps);
   k->block = kJitBlock;
+  k->num_luts = g.lut.count;
+  k->lut_live = g.lut.live;
   k->load_ms = now_ms() - tl;
   k->nvrtc_ms = nvrtc_ms;
   k->compile_ms = now_ms() - t0;
@@ -535,6 +540,18 @@ void worker_loop(lec_es_ctx *c) {
 }  // namespace
 
 uint64_t cache_key(const Program &g, bool lut_form) { return g.hash ^ (lut_form ? 0x9E3779B97F4A7C15ull : 0ull); }
+
+bool jit_have_kernel(void *arg, uint64_t hash, uint32_t *luts, uint32_t *live) {
+  lec_es_ctx *c = (lec_es_ctx *)arg;
+  if (!c->jit) return false;
+  JitState *js = c->jit;
+  std::lock_guard<std::mutex> lk(js->mu);
+  auto it = js->cache.find(hash ^ 0x9E3779B97F4A7C15ull);
+  if (it == js->cache.end() || it->second->num_luts == 0) return false;
+  *luts = it->second->num_luts;
+  *live = it->second->lut_live;
+  return true;
+}
 
 JitState *state(lec_es_ctx *c) {
   static std::mutex mu;

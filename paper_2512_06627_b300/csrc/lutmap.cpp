@@ -33,9 +33,17 @@ namespace {
 
 struct Cut {
   uint8_t n = 0;
-  int32_t leaf[3] = {-1, -1, -1};  // value ids, ascending
   uint8_t tt = 0;
+  int32_t leaf[3] = {-1, -1, -1};  // value ids, ascending
 };
+
+// One bit per leaf (id mod 64): a merge whose union has more than three bits
+// set has more than three leaves, so it is rejected without merging.
+inline uint64_t sig_of(const Cut &c) {
+  uint64_t s = 0;
+  for (int k = 0; k < c.n; k++) s |= 1ull << (c.leaf[k] & 63);
+  return s;
+}
 
 // Re-expressing a table over a superset of its leaves depends only on where
 // each old leaf lands (3 positions of 0..2 and the old leaf count): 108
@@ -156,11 +164,19 @@ void lut_map(size_t NA, size_t NP, const std::vector<int64_t> &f0, const std::ve
   fanout[root]++;
   std::vector<double> af(NV, 0.0);
   std::vector<int> best(NV, -1);
+  thread_local std::vector<uint64_t> sig;
+  sig.resize(NV * kStride);
+  for (size_t v = NA; v < NV; v++) sig[v * kStride] = sig_of(cut_at(v, 0));
+  thread_local std::vector<double> flows;
+  thread_local std::vector<uint32_t> rank;
   for (size_t v = 0; v < NA; v++) {
     scratch.clear();
-    for (size_t ia = 0; ia < ncut[f0[v]]; ia++) {
+    const size_t na_ = ncut[f0[v]], nb_ = ncut[f1[v]];
+    const uint64_t *sa = &sig[f0[v] * kStride], *sb = &sig[f1[v] * kStride];
+    for (size_t ia = 0; ia < na_; ia++) {
       const Cut &a = cut_at(f0[v], ia);
-      for (size_t ib = 0; ib < ncut[f1[v]]; ib++) {
+      for (size_t ib = 0; ib < nb_; ib++) {
+        if (__builtin_popcountll(sa[ia] | sb[ib]) > 3) continue;
         const Cut &b = cut_at(f1[v], ib);
         Cut m;
         if (!merge(a, b, m)) continue;
@@ -184,19 +200,34 @@ void lut_map(size_t NA, size_t NP, const std::vector<int64_t> &f0, const std::ve
         if (c.leaf[k] < (int32_t)NA) s += af[c.leaf[k]];
       return s;
     };
-    std::stable_sort(scratch.begin(), scratch.end(), [&](const Cut &x, const Cut &y) {
-      const double fx = flow(x), fy = flow(y);
-      return fx < fy || (fx == fy && x.n < y.n);
-    });
-    const size_t keep = std::min(scratch.size(), kMaxCuts);
-    for (size_t i = 0; i < keep; i++) cut_at(v, i) = scratch[i];
+    // the kMaxCuts best by (flow, leaves), ties in generation order: a
+    // stable insertion into a short ranked list
+    flows.resize(scratch.size());
+    rank.clear();
+    for (size_t i = 0; i < scratch.size(); i++) {
+      flows[i] = flow(scratch[i]);
+      auto before = [&](uint32_t x, uint32_t y) {
+        return flows[x] < flows[y] || (flows[x] == flows[y] && scratch[x].n < scratch[y].n);
+      };
+      if (rank.size() == kMaxCuts && !before((uint32_t)i, rank.back())) continue;
+      size_t pos = rank.size();
+      while (pos > 0 && before((uint32_t)i, rank[pos - 1])) pos--;
+      rank.insert(rank.begin() + pos, (uint32_t)i);
+      if (rank.size() > kMaxCuts) rank.pop_back();
+    }
+    const size_t keep = rank.size();
+    for (size_t i = 0; i < keep; i++) {
+      cut_at(v, i) = scratch[rank[i]];
+      sig[v * kStride + i] = sig_of(scratch[rank[i]]);
+    }
     best[v] = 0;
-    af[v] = keep == 0 ? 1.0 : flow(scratch[0]) / std::max<uint32_t>(1, fanout[v]);
+    af[v] = keep == 0 ? 1.0 : flows[rank[0]] / std::max<uint32_t>(1, fanout[v]);
     Cut t;
     t.n = 1;
     t.leaf[0] = (int32_t)v;
     t.tt = 0xAA;
     cut_at(v, keep) = t;  // trivial cut: used only when v is a leaf of a parent's cut
+    sig[v * kStride + keep] = sig_of(t);
     ncut[v] = (uint8_t)(keep + 1);
   }
 
@@ -219,6 +250,22 @@ void lut_map(size_t NA, size_t NP, const std::vector<int64_t> &f0, const std::ve
       if (c.leaf[k] < (int32_t)NA && refs[c.leaf[k]]++ == 0) added += self(self, c.leaf[k]);
     return added;
   };
+  // LUTs that referencing cut `c` would add: the same count as ref(), taken
+  // without touching the reference counts (a node joins once, when its count
+  // is zero; the stamp marks the ones already counted)
+  std::vector<uint32_t> stamp(NA, 0);
+  uint32_t cur = 0;
+  auto added = [&](auto &&self, const Cut &c) -> uint32_t {
+    uint32_t a = 1;
+    for (int k = 0; k < c.n; k++) {
+      const int32_t l = c.leaf[k];
+      if (l < (int32_t)NA && refs[l] == 0 && stamp[l] != cur) {
+        stamp[l] = cur;
+        a += self(self, cut_at(l, best[l]));
+      }
+    }
+    return a;
+  };
   if (root < (int64_t)NA) {
     refs[root] = 1;
     ref(ref, (int32_t)root);
@@ -226,14 +273,14 @@ void lut_map(size_t NA, size_t NP, const std::vector<int64_t> &f0, const std::ve
   for (int round = 0; round < 2; round++) {
     for (size_t v = 0; v < NA; v++) {
       if (refs[v] == 0) continue;
+      const int nc = (int)ncut[v] - 1;  // skip the trivial cut
+      if (nc <= 1) continue;
       deref(deref, (int32_t)v);
       uint32_t best_area = UINT32_MAX;
       int best_i = best[v];
-      const int nc = (int)ncut[v] - 1;  // skip the trivial cut
       for (int i = 0; i < nc; i++) {
-        best[v] = i;
-        const uint32_t a = ref(ref, (int32_t)v);
-        deref(deref, (int32_t)v);
+        cur++;
+        const uint32_t a = added(added, cut_at(v, i));
         if (a < best_area) {
           best_area = a;
           best_i = i;

@@ -421,7 +421,8 @@ extern "C" int lec_es_submit(lec_es_ctx *c, const lec_es_miter *m, uint64_t *tic
   MiterView v{m->num_pis, m->num_ands, m->fanins, m->out_lit};
   int rc;
   try {
-    rc = compile_program(v, LEC_ES_ORDER_AUTO, c->max_pis, r->prog);
+    const KernelProbe probe{jit_have_kernel, c};
+    rc = compile_program(v, LEC_ES_ORDER_AUTO, c->max_pis, r->prog, &probe);
   } catch (const std::bad_alloc &) {
     return LEC_ES_ENOMEM;
   }

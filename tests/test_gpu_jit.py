@@ -106,3 +106,35 @@ def test_grid_sizes_and_grab_balance(ctx):
     eq = C.config2_mult12()
     r = L.lec_es_check_ex(ctx, L.miter_of(eq), L.options(tier=L.TIER_JIT, grid_blocks=2))
     assert r.verdict == L.EQUIVALENT
+
+
+def test_cached_kernel_skips_table_cover():
+    """A second check of a cone whose kernel this context holds reuses it (the
+    cover is not rebuilt) and reports the kernel's table counts; a mutant
+    (different program hash) is mapped and compiled afresh."""
+    c = make_ctx(arena_bytes=64 << 20)
+    try:
+        aig = C.config2_mult12(mutant_seed=5)
+        out = aig.outputs[0]
+        want = oracle_cex(aig, out)
+        info0, _ = L.lec_es_compile(L.miter_of(aig))
+        opt = L.options(tier=L.TIER_JIT)
+        plans = []
+        for _ in range(3):
+            p = L.lec_es_prepare(c, L.miter_of(aig), opt)
+            L.lec_es_run_async(c, p)
+            r = L.lec_es_plan_result(c, p)
+            assert r.tier == L.TIER_JIT and r.cex_or_none == want
+            i = L.lec_es_plan_info(p)
+            assert (i.num_luts, i.lut_live, i.hash) == (info0.num_luts, info0.lut_live, info0.hash)
+            plans.append(p)
+        for p in plans:
+            L.lec_es_plan_free(c, p)
+        other = C.config2_mult12(mutant_seed=6)
+        r = L.lec_es_check_ex(c, L.miter_of(other), opt)
+        assert r.cex_or_none == oracle_cex(other, other.outputs[0])
+        good = C.config2_mult12()
+        r = L.lec_es_check(c, L.miter_of(good))
+        assert r.verdict == L.EQUIVALENT
+    finally:
+        L.lec_es_destroy(c)
