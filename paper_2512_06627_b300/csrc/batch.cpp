@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -47,7 +48,8 @@ using namespace lec;
 namespace {
 constexpr double kBatchJitWork = 5e7;    // records x chunks: about 50 us in the interpreter
 constexpr uint32_t kBatchJitLive = 230;  // table live set that still fits the register file
-constexpr int kBranches = 4;             // parallel graph branches
+constexpr int kMaxBranches = 16;         // parallel graph branches (at most)
+constexpr int kDefaultBranches = 4;
 
 struct Layout {
   int block = 256;            // threads (64-pattern words) per tile pass
@@ -83,8 +85,9 @@ struct lec_es_batch_plan {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaStream_t side[kBranches] = {};
-  cudaEvent_t fork = nullptr, join[kBranches] = {};
+  int branches = kDefaultBranches;
+  cudaStream_t side[kMaxBranches] = {};
+  cudaEvent_t fork = nullptr, join[kMaxBranches] = {};
   bool pending = false;
   double host_ms = 0, jit_ms = 0, tune_ms = 0;
   XBatchParams params{};
@@ -108,7 +111,7 @@ void batch_release(lec_es_ctx *c, lec_es_batch_plan *b) {
   if (b->e0) cudaEventDestroy(b->e0);
   if (b->e1) cudaEventDestroy(b->e1);
   if (b->fork) cudaEventDestroy(b->fork);
-  for (int i = 0; i < kBranches; i++) {
+  for (int i = 0; i < kMaxBranches; i++) {
     if (b->join[i]) cudaEventDestroy(b->join[i]);
     if (b->side[i]) cudaStreamDestroy(b->side[i]);
   }
@@ -215,7 +218,8 @@ int stage_programs(lec_es_ctx *c, lec_es_batch_plan *b, const lec_es_miter *m, s
   if (cudaEventCreate(&b->e0) != cudaSuccess || cudaEventCreate(&b->e1) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
     return LEC_ES_ECUDA;
-  for (int i = 0; i < kBranches; i++)
+  if (const char *e = getenv("LEC_ES_BATCH_BRANCHES")) b->branches = std::max(1, std::min(kMaxBranches, atoi(e)));
+  for (int i = 0; i < b->branches; i++)
     if (cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess)
       return LEC_ES_ECUDA;
@@ -346,7 +350,7 @@ int stage_layout(lec_es_ctx *c, lec_es_batch_plan *b, const Layout &L, int grid_
   // fork: branch 0 runs the tile queue; the specialised kernels are dealt to
   // branches 1, 2, 3, 0, ... so small kernels overlap instead of queueing
   cudaEventRecord(b->fork, st);
-  for (int i = 0; i < kBranches; i++) cudaStreamWaitEvent(b->side[i], b->fork, 0);
+  for (int i = 0; i < b->branches; i++) cudaStreamWaitEvent(b->side[i], b->fork, 0);
   if (b->num_tiles) lerr = launch_batch_w(bp, L.block, b->grid, b->smem, b->side[0]);
   for (size_t q = 0; q < jorder.size() && !lerr; q++) {
     const size_t j = jorder[q];
@@ -354,15 +358,14 @@ int stage_layout(lec_es_ctx *c, lec_es_batch_plan *b, const Layout &L, int grid_
     JitKernel *kk = b->jit_kernels[j];
     uint64_t cb = 0, ce = num_chunks(b->progs[i].n), grabs = ~0ull;
     unsigned long long *cex = b->d_cex + i, *ev = b->d_aux + 2 * j, *next = b->d_aux + 2 * j + 1;
-    void *args[] = {&cb, &ce, &cex, &ev, &next, &grabs};
-    const uint64_t warps = (ce + 31) / 32;
-    const uint64_t grid = std::max<uint64_t>(
-        1, std::min<uint64_t>((uint64_t)c->sm_count * kk->blocks_per_sm, (warps * 32 + kk->block - 1) / kk->block));
+    uint64_t grid = 1, rep = 1;
+    jit_geometry(kk, ce - cb, c->sm_count, &grid, &rep);
+    void *args[] = {&cb, &ce, &cex, &ev, &next, &grabs, &rep};
     if (cudaLaunchKernel((const void *)kk->kern, dim3((unsigned)grid), dim3(kk->block), args, 0,
-                         b->side[(q + 1) % kBranches]) != cudaSuccess)
+                         b->side[(q + 1) % b->branches]) != cudaSuccess)
       lerr = 1;
   }
-  for (int i = 0; i < kBranches; i++) {
+  for (int i = 0; i < b->branches; i++) {
     cudaEventRecord(b->join[i], b->side[i]);
     cudaStreamWaitEvent(st, b->join[i], 0);
   }

@@ -58,6 +58,7 @@ struct JitKernel {
   double load_ms = 0;      // of which loading the cubin and querying the kernel
   uint32_t num_luts = 0;   // the program's table count and live count when built
   uint32_t lut_live = 0;
+  uint32_t work_per_chunk = 0;  // straight-line instructions per 32-pattern chunk (about)
 };
 struct JitState;
 struct Server;
@@ -73,6 +74,10 @@ bool choose_word_geometry(lec_es_ctx *c, const Program &prog, const lec_es_optio
 // JIT tier (jit.cpp)
 uint32_t jit_auto_tier(lec_es_ctx *c, const Program &g, uint64_t chunks);
 int jit_prepare(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt);
+// Passes of 32 chunks per grab for a launch of `grid` blocks over `chunks`.
+uint64_t jit_reps(const JitKernel *k, uint64_t chunks, uint64_t grid);
+// Grid and passes per grab for a launch over `chunks` chunks.
+void jit_geometry(const JitKernel *k, uint64_t chunks, int sm_count, uint64_t *grid, uint64_t *rep);
 int jit_launch(lec_es_ctx *c, lec_es_plan *p, uint64_t chunk_begin, uint64_t chunk_end, int grid,
                uint64_t max_grabs);
 // Non-blocking lookup for the server: the compiled kernel if ready, else

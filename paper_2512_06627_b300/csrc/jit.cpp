@@ -56,7 +56,7 @@ struct JitState {
 namespace {
 
 constexpr int kJitBlock = 128;
-constexpr int kCodegenVersion = 5;  // part of cached cubin names: bump when the kernel's interface changes
+constexpr int kCodegenVersion = 6;  // part of cached cubin names: bump when the kernel's interface changes
 constexpr uint32_t kMaxJitLive = 230;        // table live set that still fits the register file
 constexpr double kJitCachedWork = 5e7;       // records x chunks: ~50 us in the interpreter
 constexpr double kJitColdWork = 1e11;        // ~0.1 s in the interpreter: repays a compile
@@ -64,26 +64,33 @@ constexpr double kJitColdWork = 1e11;        // ~0.1 s in the interpreter: repay
 const char *kMask32[5] = {"0xAAAAAAAAu", "0xCCCCCCCCu", "0xF0F0F0F0u", "0xFF00FF00u", "0xFFFF0000u"};
 
 // Kernel prologue / epilogue shared by both code forms.  Chunks are handed
-// out 32 at a time per warp from a counter (one grab ahead), so warps that
-// run faster take more and all finish together; a warp stops at the end of
-// the range, when its next chunk is not below the current counterexample, or
-// after max_grabs grabs (the server bounds block lifetimes this way).
+// out 32 x rep at a time per warp from a counter (one grab ahead), so warps
+// that run faster take more and all finish together; a grab is rep passes of
+// 32 chunks, enough work to hide the counter's latency and keep its
+// contention low on small cones.  A warp stops at the end of the range, when
+// its next grab does not start below the current counterexample, or after
+// max_grabs grabs (the server bounds block lifetimes this way).
 void emit_prologue(std::ostringstream &s) {
   s << "typedef unsigned int u32; typedef unsigned long long u64;\n"
        "extern \"C\" __global__ void __launch_bounds__("
     << kJitBlock
-    << ") es_jit(const u64 cb, const u64 ce, u64 *cex, u64 *evaluated, u64 *next, const u64 max_grabs) {\n"
+    << ") es_jit(const u64 cb, const u64 ce, u64 *cex, u64 *evaluated, u64 *next, const u64 max_grabs,\n"
+       "    const u64 rep) {\n"
        "  const unsigned lane = threadIdx.x & 31u;\n"
+       "  const u64 step = 32ull * rep;\n"
        "  u64 done = 0;\n"
-       "  u64 mine = __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(next, 32ull) : 0ull, 0);\n"
+       "  u64 mine = __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(next, step) : 0ull, 0);\n"
        "  u64 cur = __shfl_sync(0xffffffffu, lane == 0 ? *(volatile u64 *)cex : 0ull, 0);\n"
        "  for (u64 g = 1; ; g++) {\n"
        "    const u64 wfirst = cb + mine;\n"
        "    if (wfirst >= ce || wfirst * 32ull >= cur) break;\n"
        "    const bool more = g < max_grabs;\n"
-       "    const u64 ahead = (lane == 0 && more) ? atomicAdd(next, 32ull) : ~0ull;\n"
+       "    const u64 ahead = (lane == 0 && more) ? atomicAdd(next, step) : ~0ull;\n"
        "    const u64 nxt = lane == 0 ? *(volatile u64 *)cex : 0ull;\n"
-       "    const u64 c = wfirst + lane;\n"
+       "    for (u64 r = 0; r < rep; r++) {\n"
+       "    const u64 base = wfirst + 32ull * r;\n"
+       "    if (base >= ce) break;\n"
+       "    const u64 c = base + lane;\n"
        "    const u32 clo = (u32)c, chi = (u32)(c >> 32);\n"
        "    (void)chi;\n";
 }
@@ -98,6 +105,7 @@ void emit_epilogue(std::ostringstream &s, const std::string &outv, bool compl_, 
        "      if ((int)lane == __ffs(bal) - 1) atomicMin(cex, c * 32ull + (u64)(__ffs(out) - 1));\n"
        "    }\n"
        "    done += (c < ce) ? 1ull : 0ull;\n"
+       "    }\n"
        "    mine = __shfl_sync(0xffffffffu, ahead, 0);\n"
        "    cur = __shfl_sync(0xffffffffu, nxt, 0);\n"
        "    if (!more) break;\n"
@@ -251,15 +259,16 @@ std::string gen_ptx_lut(const Program &g, int major, int minor) {
   char buf[160];
   s << ".version 9.0\n.target sm_" << major << minor << "a\n.address_size 64\n\n"
     << ".visible .entry es_jit(.param .u64 p_cb, .param .u64 p_ce, .param .u64 p_cex, .param .u64 p_ev,\n"
-    << "    .param .u64 p_next, .param .u64 p_maxg)\n.maxntid " << kJitBlock << ", 1, 1\n{\n"
+    << "    .param .u64 p_next, .param .u64 p_maxg, .param .u64 p_rep)\n.maxntid " << kJitBlock << ", 1, 1\n{\n"
     << "  .reg .pred %p<10>;\n  .reg .b32 %t<24>;\n  .reg .b64 %d<32>;\n"
     << "  .reg .b32 %v<" << (NA + 1) << ">;\n  .reg .b32 %q<" << (NP + 1) << ">;\n";
   // parameters, lane, first grab, first counterexample poll
   s << "  ld.param.u64 %d1, [p_cb];\n  ld.param.u64 %d2, [p_ce];\n  ld.param.u64 %d3, [p_cex];\n"
        "  ld.param.u64 %d4, [p_ev];\n  ld.param.u64 %d5, [p_next];\n  ld.param.u64 %d6, [p_maxg];\n"
+       "  ld.param.u64 %d7, [p_rep];\n  shl.b64 %d7, %d7, 5;\n"
        "  cvta.to.global.u64 %d3, %d3;\n  cvta.to.global.u64 %d4, %d4;\n  cvta.to.global.u64 %d5, %d5;\n"
        "  mov.u32 %t1, %tid.x;\n  and.b32 %t2, %t1, 31;\n  setp.eq.u32 %p1, %t2, 0;\n"
-       "  mov.u64 %d10, 0;\n  mov.u64 %d11, 0;\n  @%p1 atom.global.add.u64 %d11, [%d5], 32;\n"
+       "  mov.u64 %d10, 0;\n  mov.u64 %d11, 0;\n  @%p1 atom.global.add.u64 %d11, [%d5], %d7;\n"
        "  mov.b64 {%t3, %t4}, %d11;\n  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n"
        "  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n  mov.b64 %d11, {%t3, %t4};\n"
        "  mov.u64 %d12, 0;\n  @%p1 ld.volatile.global.u64 %d12, [%d3];\n  mov.b64 {%t3, %t4}, %d12;\n"
@@ -273,8 +282,9 @@ std::string gen_ptx_lut(const Program &g, int major, int minor) {
     name[v] = buf;
   }
   for (uint32_t k = 5; k < NP; k++) name[NA + k] = "%q" + std::to_string(k);
-  // grabs are multiples of 32 chunks, so the low five bits of a lane's chunk
-  // index are those of cb + lane: PIs 5..9 are fixed per lane, computed here
+  // grabs and passes are multiples of 32 chunks, so the low five bits of a
+  // lane's chunk index are those of cb + lane: PIs 5..9 are fixed per lane,
+  // computed here
   s << "  cvt.u32.u64 %t17, %d1;\n  add.u32 %t17, %t17, %t2;\n";
   std::vector<uint8_t> pi_done(NP, 0);
   for (uint32_t k = 5; k < NP && k < 10; k++) {
@@ -286,8 +296,11 @@ std::string gen_ptx_lut(const Program &g, int major, int minor) {
        "  add.u64 %d14, %d1, %d11;\n  setp.ge.u64 %p2, %d14, %d2;\n  @%p2 bra $DONE;\n"
        "  shl.b64 %d15, %d14, 5;\n  setp.ge.u64 %p2, %d15, %d12;\n  @%p2 bra $DONE;\n"
        "  setp.lt.u64 %p3, %d13, %d6;\n  and.pred %p4, %p1, %p3;\n  mov.u64 %d16, -1;\n"
-       "  @%p4 atom.global.add.u64 %d16, [%d5], 32;\n  mov.u64 %d17, 0;\n"
-       "  @%p1 ld.volatile.global.u64 %d17, [%d3];\n  add.u64 %d19, %d14, %d18;\n"
+       "  @%p4 atom.global.add.u64 %d16, [%d5], %d7;\n  mov.u64 %d17, 0;\n"
+       "  @%p1 ld.volatile.global.u64 %d17, [%d3];\n"
+       // passes of 32 chunks from d27 up to the grab's end d28
+       "  mov.u64 %d27, %d14;\n  add.u64 %d28, %d14, %d7;\n"
+       "$PASS:\n  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra $GRABEND;\n  add.u64 %d19, %d27, %d18;\n"
        "  cvt.u32.u64 %t5, %d19;\n  shr.u64 %d20, %d19, 32;\n  cvt.u32.u64 %t6, %d20;\n";
   std::vector<uint8_t> pi_loop(NP, 0);
   auto operand = [&](int32_t id) -> std::string {
@@ -328,6 +341,8 @@ std::string gen_ptx_lut(const Program &g, int major, int minor) {
        "  atom.global.min.u64 %d23, [%d3], %d22;\n"
        "$NOFAIL:\n"
        "  setp.lt.u64 %p5, %d19, %d2;\n  selp.u64 %d24, 1, 0, %p5;\n  add.u64 %d10, %d10, %d24;\n"
+       "  add.u64 %d27, %d27, 32;\n  setp.lt.u64 %p9, %d27, %d28;\n  @%p9 bra $PASS;\n"
+       "$GRABEND:\n"
        "  mov.b64 {%t3, %t4}, %d16;\n  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n"
        "  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n  mov.b64 %d11, {%t3, %t4};\n"
        "  mov.b64 {%t3, %t4}, %d17;\n  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n"
@@ -509,6 +524,7 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   k->block = kJitBlock;
   k->num_luts = g.lut.count;
   k->lut_live = g.lut.live;
+  k->work_per_chunk = lut_form ? g.lut.count : (uint32_t)g.recs.size();
   k->load_ms = now_ms() - tl;
   k->nvrtc_ms = nvrtc_ms;
   k->compile_ms = now_ms() - t0;
@@ -594,10 +610,11 @@ int jit_attach(lec_es_ctx *c, lec_es_plan *p, JitKernel *k, const lec_es_options
   p->jit = k;
   p->jit_block = k->block;
   const uint64_t chunks = num_chunks(g.n);
-  uint64_t grid = (uint64_t)c->sm_count * k->blocks_per_sm;
-  if (opt && opt->grid_blocks) grid = opt->grid_blocks;
-  grid = std::min<uint64_t>(grid, (chunks + k->block - 1) / k->block);
-  p->jit_grid = (int)std::max<uint64_t>(1, grid);
+  // a caller's grid is kept; otherwise each launch sizes its own (jit_geometry)
+  p->jit_grid = 0;
+  if (opt && opt->grid_blocks)
+    p->jit_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(opt->grid_blocks, (chunks + k->block - 1) / k->block));
+  (void)c;
   return LEC_ES_OK;
 }
 
@@ -629,12 +646,47 @@ JitKernel *jit_lookup_or_schedule(lec_es_ctx *c, const Program &g) {
   return nullptr;
 }
 
+uint64_t jit_reps(const JitKernel *k, uint64_t chunks, uint64_t grid) {
+  // ~4k instructions per warp per grab, but at least four grabs per warp of
+  // the grid so the counter still balances the load
+  const uint64_t per_chunk = std::max<uint64_t>(1, k->work_per_chunk) + 40;
+  uint64_t rep = (4096 + per_chunk - 1) / per_chunk;
+  const uint64_t warps = std::max<uint64_t>(1, grid * (uint64_t)(k->block / 32));
+  rep = std::min<uint64_t>(rep, chunks / (32ull * 4ull * warps));
+  return std::max<uint64_t>(1, std::min<uint64_t>(rep, 32));
+}
+
+void jit_geometry(const JitKernel *k, uint64_t chunks, int sm_count, uint64_t *grid, uint64_t *rep) {
+  // Every warp grab costs one atomic on a single counter, so a small cone
+  // needs both long grabs (rep passes of 32 chunks, ~4k instructions) and a
+  // grid no larger than its grabs can keep busy (four grabs per warp); the
+  // grid keeps at least 8 warps per SM, shortening grabs if it has to, and
+  // at most what is resident at once.
+  const uint64_t wpb = (uint64_t)std::max(1, k->block / 32);
+  const uint64_t w_full = (uint64_t)sm_count * (uint64_t)k->blocks_per_sm * wpb;
+  const uint64_t w_min = std::min<uint64_t>(w_full, (uint64_t)sm_count * 8ull);
+  const uint64_t per_chunk = std::max<uint64_t>(1, k->work_per_chunk) + 40;
+  uint64_t r = std::min<uint64_t>(32, (4096 + per_chunk - 1) / per_chunk);
+  uint64_t grabs = chunks / (32ull * r);
+  uint64_t w = std::min<uint64_t>(w_full, grabs / 4);
+  if (w < w_min) {
+    r = std::max<uint64_t>(1, std::min<uint64_t>(r, chunks / (32ull * 4ull * w_min)));
+    grabs = (chunks + 32ull * r - 1) / (32ull * r);
+    w = std::min<uint64_t>(w_full, std::max<uint64_t>(1, grabs / 4));
+  }
+  *rep = r;
+  *grid = std::max<uint64_t>(1, (w + wpb - 1) / wpb);
+}
+
 int jit_launch(lec_es_ctx *c, lec_es_plan *p, uint64_t chunk_begin, uint64_t chunk_end, int grid,
                uint64_t max_grabs) {
-  (void)c;
   unsigned long long *cex = p->d_res, *evaluated = p->d_res + 1, *next = p->d_res + 3;
-  void *args[] = {&chunk_begin, &chunk_end, &cex, &evaluated, &next, &max_grabs};
-  const int g = grid > 0 ? grid : p->jit_grid;
+  uint64_t geo_grid = 1, rep = 1;
+  jit_geometry(p->jit, chunk_end - chunk_begin, c->sm_count, &geo_grid, &rep);
+  const int fixed = grid > 0 ? grid : p->jit_grid;
+  const int g = fixed > 0 ? fixed : (int)geo_grid;
+  if (fixed > 0) rep = jit_reps(p->jit, chunk_end - chunk_begin, (uint64_t)g);
+  void *args[] = {&chunk_begin, &chunk_end, &cex, &evaluated, &next, &max_grabs, &rep};
   cudaError_t e = cudaLaunchKernel((const void *)p->jit->kern, dim3(g), dim3(p->jit_block), args, 0, p->stream);
   return e == cudaSuccess ? 0 : (int)e;
 }

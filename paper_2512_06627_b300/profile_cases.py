@@ -8,6 +8,7 @@ Cases:
   mult12-interp   the 12x12 miter on the interpreter (short launches)
   pairs-light     the node-pair miters light enough for the tile queue, one batch
   pairs-all       all 4,096 node-pair miters, one prepared batch
+  pair-jit        one node-pair miter of support --n on the specialised kernel
   sweep-32x32     random-simulation signatures of the 32x32 four-multiplier graph
 
 Each case prepares its work first and then runs it N times (default 2), so a
@@ -20,8 +21,9 @@ import sys
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["mult16-jit", "mult16-interp", "mult12-interp", "pairs-light", "pairs-all",
-                                     "sweep-32x32"])
+                                     "pair-jit", "sweep-32x32"])
     ap.add_argument("--runs", type=int, default=2)
+    ap.add_argument("--n", type=int, default=24, help="support size for pair-jit")
     a = ap.parse_args(argv)
     from paper_2512_06627_b300 import circuits as C
     from paper_2512_06627_b300 import lec_es as L
@@ -40,6 +42,24 @@ def main(argv=None):
             L.lec_es_run_async(ctx, p)
             r = L.lec_es_plan_result(ctx, p)
             print(f"verdict {r.verdict} tier {r.tier} device_ms {r.device_ms:.3f}")
+        L.lec_es_plan_free(ctx, p)
+    elif a.case == "pair-jit":
+        pb = C.config4_pairs()
+        f = pb.aig.flat_fanins()
+        m = None
+        for o in pb.aig.outputs:
+            cand = L.Miter(pb.aig.num_pis, f, o)
+            info = L.lec_es_compile(cand)[0]
+            if info.n == a.n and info.num_luts >= 64:
+                m = cand
+                break
+        if m is None:
+            sys.exit(f"no node-pair miter with support {a.n}")
+        p = L.lec_es_prepare(ctx, m, L.options(tier=L.TIER_JIT))
+        for _ in range(a.runs):
+            L.lec_es_run_async(ctx, p)
+            r = L.lec_es_plan_result(ctx, p)
+            print(f"n {info.n} tables {info.num_luts} verdict {r.verdict} device_ms {r.device_ms:.4f}")
         L.lec_es_plan_free(ctx, p)
     else:
         pb = C.config4_pairs()
