@@ -29,10 +29,10 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "16x16 array vs radix-4 Booth/Dadda multiplier miter, 32 PIs, 2^32 patterns, equivalent"
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture (profiles/es_jit_mult16.md, code-generator version 5), keyed by
-# (tier, program hash, number of 3-input tables); reported only while the
-# program is the one that was captured.
-NCU_TRAFFIC = {("jit", 0x27b56cd32749aac7, 1714): 33024}
+# capture (profiles/es_jit_mult16.md), keyed by (tier, program hash, number of
+# 3-input tables, code-generator version); reported only while the program and
+# the generated kernel are the ones that were captured.
+NCU_TRAFFIC = {("jit", 0x27b56cd32749aac7, 1714, 6): 33536}
 
 
 def parse():
@@ -418,7 +418,7 @@ def run_ours(args, ws, rank, local):
     achieved = lop3_per_launch / kern_s
     peak = sms * per_clk * sm_max * 1e6
     tier_name = {L.TIER_JIT: "jit", L.TIER_INTERP: "interp", L.TIER_SPILL: "spill"}.get(int(tier_ran), "?")
-    traffic = NCU_TRAFFIC.get((tier_name, int(info.hash), int(info.num_luts)))
+    traffic = NCU_TRAFFIC.get((tier_name, int(info.hash), int(info.num_luts), L.lec_es_codegen_version()))
     line = {
         "metric": "node-pattern evals/s",
         "value": value,

@@ -317,6 +317,13 @@ int lec_es_match_pairs(lec_es_ctx *c, uint32_t num_pis, uint32_t num_ands, const
 int lec_es_lop3_peak(lec_es_ctx *c, double *lop3_per_clk_per_sm, int *sm_count,
                      int *clock_khz, double *lop3_per_s);
 
+/* Version of the specialised-kernel code generator (no counterpart in the
+ * paper).  It changes whenever the generated kernel's code or interface
+ * does, is part of the on-disk kernel cache names, and lets a caller tell
+ * whether a profile of a kernel still describes the one this library emits.
+ * Never fails. */
+uint32_t lec_es_codegen_version(void);
+
 #ifdef __cplusplus
 }
 #endif

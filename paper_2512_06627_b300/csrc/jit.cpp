@@ -713,6 +713,8 @@ std::string jit_source_for(const Program &g) { return gen_source(g, true); }
 
 }  // namespace lec
 
+extern "C" uint32_t lec_es_codegen_version(void) { return (uint32_t)lec::kCodegenVersion; }
+
 extern "C" int lec_es_jit_compile(const lec_es_miter *m, int cc_major, int cc_minor, char *log, size_t log_cap,
                                   uint64_t *cubin_bytes) {
   if (!m) return LEC_ES_EINVAL;

@@ -34,6 +34,7 @@ EXPORTS = [
     "lec_es_batch_run_async", "lec_es_batch_results", "lec_es_batch_free", "lec_es_submit", "lec_es_poll",
     "lec_es_wait", "lec_es_cancel", "lec_es_server_config", "lec_es_lop3_peak", "lec_es_jit_compile",
     "lec_es_check_noalloc", "lec_es_batch_info", "lec_es_signatures", "lec_es_match_pairs",
+    "lec_es_codegen_version",
 ]
 
 
@@ -137,6 +138,7 @@ def load() -> ctypes.CDLL:
                                ctypes.c_int),
         "lec_es_check_noalloc": ([_P, ctypes.c_uint64, ctypes.POINTER(lec_es_program_info), ctypes.c_uint64,
                                   ctypes.c_uint64, _P, _P], ctypes.c_int),
+        "lec_es_codegen_version": ([], ctypes.c_uint32),
         "lec_es_lop3_peak": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     }
@@ -417,3 +419,8 @@ def lec_es_lop3_peak(ctx: Context):
     _ok(load().lec_es_lop3_peak(ctx.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                                 ctypes.byref(d)), "lec_es_lop3_peak")
     return a.value, b.value, c.value, d.value
+
+
+def lec_es_codegen_version() -> int:
+    """Version of the specialised-kernel code generator."""
+    return int(load().lec_es_codegen_version())

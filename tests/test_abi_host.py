@@ -30,7 +30,7 @@ def _built():
 
 def test_exports_every_declared_symbol():
     hdr = open(os.path.join(ROOT, "include", "lec_es.h")).read()
-    declared = set(re.findall(r"^(?:int|void|const char \*)\s*(lec_es_[a-z0-9_]+)\s*\(", hdr, re.M))
+    declared = set(re.findall(r"^(?:int|void|uint32_t|const char \*)\s*(lec_es_[a-z0-9_]+)\s*\(", hdr, re.M))
     assert declared == set(L.EXPORTS)
     lib = L.load()
     for name in declared:
