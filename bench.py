@@ -298,9 +298,23 @@ def measure_serve(ctx, args):
     # one launch per request, sequential
     for m in ms[:4]:
         L.lec_es_check(ctx, m)
+    # the ES time model's predictions for these requests, made before they run
+    preds = [L.lec_es_cost_predict(ctx, m, os.cpu_count() or 1) for m in ms]
     t0 = time.perf_counter()
-    alone = [L.lec_es_check(ctx, m).cex for m in ms]
+    one = [L.lec_es_check(ctx, m) for m in ms]
     one_s = time.perf_counter() - t0
+    alone = [r.cex for r in one]
+    cost = {}
+    for tier, name in ((L.TIER_INTERP, "interp"), (L.TIER_JIT, "jit")):
+        errs = [abs((p.jit_ms if tier == L.TIER_JIT else p.interp_ms) / r.device_ms - 1.0)
+                for p, r in zip(preds, one) if r.tier == tier and r.verdict == L.EQUIVALENT and r.device_ms > 0]
+        co = L.lec_es_cost_model(ctx, tier)
+        cost[name] = {"a_ms": co.a_ms, "c_ms": co.c_ms, "alpha_ms": co.alpha_ms, "samples": int(co.samples),
+                      "requests": len(errs),
+                      "median_rel_err": float(np.median(errs)) if errs else None,
+                      "p90_rel_err": float(np.percentile(errs, 90)) if errs else None}
+    cost["paper_cpu_alpha_ms"] = 0.3
+    cost["beta"] = 23
     # capacity: every request submitted at once
     t0 = time.perf_counter()
     tk = [L.lec_es_submit(ctx, m) for m in ms]
@@ -332,6 +346,7 @@ def measure_serve(ctx, args):
         "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
         "poisson_miters_per_s": R / span,
         "jit_warmup_s": warm_s, "results_equal_alone": True,
+        "cost_model": cost,
     }
 
 

@@ -317,6 +317,49 @@ int lec_es_match_pairs(lec_es_ctx *c, uint32_t num_pis, uint32_t num_ands, const
 int lec_es_lop3_peak(lec_es_ctx *c, double *lop3_per_clk_per_sm, int *sm_count,
                      int *clock_khz, double *lop3_per_s);
 
+/* ---- ES time model (§3.2, refit for this GPU) --------------------------- */
+
+/* The paper models ES time as alpha * gates * 2^(n - beta).  alpha * 2^-beta
+ * is one factor, so beta stays at the paper's 23 and each tier gets its own
+ * alpha, plus a fixed launch cost a and a cost c per gate for one pass over
+ * the program (the floor of a small support on a GPU):
+ *   t_ms = a_ms + c_ms * gates + alpha_ms * gates * 2^(n - 23),
+ * gates = cone ANDs, n = support PIs.  Build time of a specialised kernel:
+ * a_ms + c_ms * tables (alpha_ms = 0). */
+typedef struct {
+  double a_ms;              /* fixed cost per run (ms) */
+  double c_ms;              /* ms per gate, independent of n */
+  double alpha_ms;          /* ms per gate at 2^23 patterns (the paper's alpha, in ms) */
+  uint64_t samples;         /* measurements folded in (0: built-in B300 values) */
+} lec_es_cost_coeffs;
+
+typedef struct {
+  double interp_ms;         /* predicted device time on the interpreter tier */
+  double jit_ms;            /* predicted device time of the specialised kernel */
+  double jit_compile_ms;    /* predicted build time (0 if the context holds the kernel) */
+  double paper_cpu_s;       /* the paper's one-core CPU model: 0.0003 s * gates * 2^(n-23) */
+  uint32_t gates, n, num_luts;
+  uint32_t tier;            /* tier an AUTO run picks (LEC_ES_TIER_*) */
+  uint32_t gpu_offload;     /* the paper's rule: 1 if paper_cpu_s / cpu_threads > 0.1 s */
+  uint32_t pad;
+} lec_es_cost;
+
+/* Weighted least-squares fit (relative error; a_ms, c_ms, alpha_ms >= 0) of
+ * k measurements (gates[i], n[i], ms[i]) to the model above.  Host only.
+ * EINVAL on k = 0, n > 63 or a time <= 0. */
+int lec_es_cost_fit(const uint32_t *gates, const uint32_t *n, const double *ms, size_t k,
+                    lec_es_cost_coeffs *out);
+/* The context's current coefficients for tier (LEC_ES_TIER_INTERP, _JIT,
+ * _SPILL) or 4 for kernel builds.  Each context starts from built-in B300
+ * values and folds in its own full, equivalent runs (single checks and
+ * served requests) and kernel builds.  c may be NULL: built-in values. */
+int lec_es_cost_model(lec_es_ctx *c, uint32_t tier, lec_es_cost_coeffs *out);
+/* Predicted times of miter m (front end on the host; nothing runs on the
+ * GPU) and the tier an AUTO check would take.  c may be NULL: built-in
+ * values, no kernel cache.  cpu_threads is the thread count for the paper's
+ * GPU-offload rule. */
+int lec_es_cost_predict(lec_es_ctx *c, const lec_es_miter *m, uint32_t cpu_threads, lec_es_cost *out);
+
 /* Version of the specialised-kernel code generator (no counterpart in the
  * paper).  It changes whenever the generated kernel's code or interface
  * does, is part of the on-disk kernel cache names, and lets a caller tell

@@ -374,6 +374,7 @@ int plan_prepare_program(lec_es_ctx *c, Program &&prog, const lec_es_options *op
   p->prog = std::move(prog);
   p->stream = c->stream;
   p->flags = opt ? opt->flags : 0;
+  p->user_grid = opt && opt->grid_blocks;
   p->jit_lut = !(p->flags & LEC_ES_FLAG_JIT_AND_FORM);
   int rc;
   if (cudaSetDevice(c->device) != cudaSuccess) return LEC_ES_ECUDA;
@@ -467,6 +468,8 @@ int plan_run_async_grid(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt
   if (wb >= we) return LEC_ES_EINVAL;
   p->last_wb = wb;
   p->last_we = we;
+  p->last_default_grid = grid_override <= 0 && !(opt && opt->grid_blocks) && !p->user_grid &&
+                         !(p->flags & LEC_ES_FLAG_TEST_WAIT_TIMEOUT);
   const uint64_t C = num_chunks(g.n);
   const uint64_t cb = std::min<uint64_t>(2 * wb, C), ce = std::min<uint64_t>(2 * we, C);
   cudaStream_t st = p->stream;
@@ -548,6 +551,9 @@ int plan_result(lec_es_ctx *c, lec_es_plan *p, lec_es_result *out) {
   if (cex != UINT64_MAX) out->verdict = LEC_ES_NONEQUIVALENT;
   else if (p->last_wb == 0 && p->last_we >= W) out->verdict = LEC_ES_EQUIVALENT;
   else out->verdict = LEC_ES_UNDECIDED;
+  // a full enumeration on the library's own geometry refines the time model
+  if (out->verdict == LEC_ES_EQUIVALENT && p->last_default_grid)
+    cost_add_run(c, p->tier, p->prog.cone_ands, p->prog.n, ms);
   return LEC_ES_OK;
 }
 

@@ -46,7 +46,7 @@
 using namespace lec;
 
 namespace {
-constexpr double kBatchJitWork = 5e7;    // records x chunks: about 50 us in the interpreter
+constexpr double kBatchJitMs = 0.05;     // predicted interpreter time above which a miter gets its own kernel
 constexpr uint32_t kBatchJitLive = 230;  // table live set that still fits the register file
 constexpr int kMaxBranches = 16;         // parallel graph branches (at most)
 constexpr int kDefaultBranches = 4;
@@ -166,8 +166,8 @@ int stage_programs(lec_es_ctx *c, lec_es_batch_plan *b, const lec_es_miter *m, s
   const bool allow_jit = !(opt && (opt->tier == LEC_ES_TIER_INTERP || opt->tier == LEC_ES_TIER_SPILL));
   for (size_t i = 0; i < k; i++) {
     const Program &g = b->progs[i];
-    const double work = (double)g.recs.size() * (double)num_chunks(g.n);
-    if (allow_jit && work >= kBatchJitWork && g.lut.count && g.lut.live <= kBatchJitLive) {
+    const double t_int = cost_run_ms(c, LEC_ES_TIER_INTERP, g.cone_ands, g.n);
+    if (allow_jit && t_int >= kBatchJitMs && g.lut.count && g.lut.live <= kBatchJitLive) {
       b->jit_of[i] = (int)b->jit_miters.size();
       b->jit_miters.push_back((uint32_t)i);
     } else if (g.num_slots > max_fit64) {

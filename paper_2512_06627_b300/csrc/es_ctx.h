@@ -63,7 +63,43 @@ struct JitKernel {
 struct JitState;
 struct Server;
 
+// ES time model of §3.2 refit per tier: t = a + c * gates + alpha * gates *
+// 2^(n - 23) (beta fixed at the paper's 23, so alpha is in the paper's
+// units; c * gates is one pass over the program, the floor for small
+// supports), fitted in relative error from weighted normal-equation sums that
+// start from built-in B300 values.
+struct CostSums {
+  double S[3][3] = {};         // sum of f f^T / t^2 over features f = (1, gates, x)
+  double b[3] = {};            // sum of f / t
+  uint64_t count = 0;
+};
+struct CostFit {
+  double coef[3] = {0, 0, 0};  // a_ms, c_ms, alpha_ms
+  double S[3][3] = {};         // prior (built-in values) sums
+  double b[3] = {};
+  // measured runs, binned by (n, log2 gates); a bin counts as at most a few
+  // samples, so thousands of runs of one size cannot outweigh the others
+  std::map<uint32_t, CostSums> bins;
+  uint64_t samples = 0;        // measurements added on this context
+};
+struct CostModel {
+  std::mutex mu;
+  CostFit tier[4];       // indexed by LEC_ES_TIER_*
+  CostFit compile;       // specialised-kernel build: a + c * tables (coef[0], coef[1])
+  bool ready = false;
+};
+
 double now_ms();
+
+// ES time model (cost.cpp).  c may be null (built-in values only).
+double cost_x(uint32_t gates, uint32_t n);
+double cost_run_ms(lec_es_ctx *c, uint32_t tier, uint32_t gates, uint32_t n);
+double cost_compile_ms(lec_es_ctx *c, uint32_t tables);
+void cost_add_run(lec_es_ctx *c, uint32_t tier, uint32_t gates, uint32_t n, double ms);
+void cost_add_compile(lec_es_ctx *c, uint32_t tables, double ms);
+// Weighted (relative-error) least squares of t = a + c g + alpha x with all
+// three coefficients >= 0; coef = (a, c, alpha).
+bool cost_fit(const double *g, const double *x, const double *t, size_t k, double coef[3]);
 int wait_event(cudaEvent_t ev, double timeout_s);
 int choose_interp_geometry(lec_es_ctx *c, const Program &prog, uint64_t chunks, const lec_es_options *opt,
                            PlanGeom &g);
@@ -133,6 +169,7 @@ struct lec_es_ctx {
   std::vector<lec::RunRes> res_free;
   std::vector<void *> res_slabs;
   std::vector<cudaEvent_t> res_events;
+  lec::CostModel cost;  // ES time model, refined by this context's runs
 };
 
 // Result words of a run: [0] lowest failing pattern (init ~0), [1] patterns
@@ -155,6 +192,8 @@ struct lec_es_plan {
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   bool pending = false;
   uint64_t last_wb = 0, last_we = 0;
+  bool last_default_grid = false;        // the last run used the library's own launch geometry
+  bool user_grid = false;                // prepared with a caller's grid_blocks
   double host_ms = 0, jit_ms = 0;
   lec::JitKernel *jit = nullptr;
   int jit_block = 0, jit_grid = 0;

@@ -58,8 +58,6 @@ namespace {
 constexpr int kJitBlock = 128;
 constexpr int kCodegenVersion = 6;  // part of cached cubin names: bump when the kernel's interface changes
 constexpr uint32_t kMaxJitLive = 230;        // table live set that still fits the register file
-constexpr double kJitCachedWork = 5e7;       // records x chunks: ~50 us in the interpreter
-constexpr double kJitColdWork = 1e11;        // ~0.1 s in the interpreter: repays a compile
 
 const char *kMask32[5] = {"0xAAAAAAAAu", "0xCCCCCCCCu", "0xF0F0F0F0u", "0xFF00FF00u", "0xFFFF0000u"};
 
@@ -462,16 +460,22 @@ int compile_cubin(const std::string &src, int major, int minor, std::vector<char
 uint64_t cache_key(const Program &g, bool lut_form);
 JitState *state(lec_es_ctx *c);
 
-// The specialised kernel once it is compiled (in memory or on disk) wins above
-// a few tens of microseconds of interpreter time; a cold compile (0.1-1 s)
-// pays off only for large work.
+// The ES time model (cost.cpp) decides: the specialised kernel when its
+// predicted time, plus the predicted build time unless this context already
+// holds the kernel, is below the interpreter's.  Cones whose table live set
+// does not fit the register file stay on the interpreter.
 uint32_t jit_auto_tier(lec_es_ctx *c, const Program &g, uint64_t chunks) {
-  const double work = (double)g.recs.size() * (double)chunks;
-  if (g.lut.count == 0 || g.lut.live > kMaxJitLive || work < kJitCachedWork) return LEC_ES_TIER_INTERP;
-  if (work >= kJitColdWork) return LEC_ES_TIER_JIT;
-  JitState *js = state(c);
-  std::lock_guard<std::mutex> lk(js->mu);
-  return js->cache.count(cache_key(g, true)) ? LEC_ES_TIER_JIT : LEC_ES_TIER_INTERP;
+  (void)chunks;
+  if (g.lut.count == 0 || g.lut.live > kMaxJitLive) return LEC_ES_TIER_INTERP;
+  bool cached = g.lut.elided;
+  if (!cached && c) {
+    JitState *js = state(c);
+    std::lock_guard<std::mutex> lk(js->mu);
+    cached = js->cache.count(cache_key(g, true)) != 0;
+  }
+  const double t_int = cost_run_ms(c, LEC_ES_TIER_INTERP, g.cone_ands, g.n);
+  const double t_jit = cost_run_ms(c, LEC_ES_TIER_JIT, g.cone_ands, g.n) + (cached ? 0.0 : cost_compile_ms(c, g.lut.count));
+  return t_jit < t_int ? LEC_ES_TIER_JIT : LEC_ES_TIER_INTERP;
 }
 
 namespace {
@@ -528,6 +532,7 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   k->load_ms = now_ms() - tl;
   k->nvrtc_ms = nvrtc_ms;
   k->compile_ms = now_ms() - t0;
+  if (nvrtc_ms > 0) cost_add_compile(c, g.lut.count, k->compile_ms);  // a build, not a disk-cache read
   if (getenv("LEC_ES_JIT_LOG"))
     fprintf(stderr, "lec_es JIT %016llx: nvrtc %.1f ms, load %.1f ms, %d regs\n", (unsigned long long)g.hash,
             nvrtc_ms, k->load_ms, k->regs);

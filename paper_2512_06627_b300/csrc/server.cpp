@@ -44,7 +44,7 @@ namespace lec {
 namespace {
 
 constexpr int kStreams = 8;                    // half high priority, half low
-constexpr uint64_t kSmallWork = 1ull << 33;    // record x chunk products below this are "small"
+constexpr double kSmallMs = 5.0;               // predicted device time below this is "small"
 
 struct Slot {
   unsigned long long *d_res = nullptr;  // kResWords result words
@@ -116,10 +116,13 @@ int launch(Server *s, Request *r) {
   lec_es_ctx *c = s->c;
   const Program &g = r->prog;
   const uint64_t C = num_chunks(g.n);
-  const uint64_t work = (uint64_t)g.recs.size() * C;
-  // stream: least loaded within the request's priority class
+  JitKernel *k = nullptr;
+  if (jit_auto_tier(c, g, C) == LEC_ES_TIER_JIT) k = jit_lookup_or_schedule(c, g);
+  // stream: least loaded within the request's priority class, from the ES
+  // time model on the tier it will run
+  const double predicted = cost_run_ms(c, k ? LEC_ES_TIER_JIT : LEC_ES_TIER_INTERP, g.cone_ands, g.n);
   const int half = kStreams / 2;
-  const int lo = work < kSmallWork ? 0 : half;
+  const int lo = predicted < kSmallMs ? 0 : half;
   int best = lo;
   for (int i = lo; i < lo + half; i++)
     if (s->stream_load[i] < s->stream_load[best]) best = i;
@@ -134,8 +137,6 @@ int launch(Server *s, Request *r) {
   if (si < 0) return LEC_ES_EBUSY;
   Slot &sl = s->slots[si];
 
-  JitKernel *k = nullptr;
-  if (jit_auto_tier(c, g, C) == LEC_ES_TIER_JIT) k = jit_lookup_or_schedule(c, g);
   Resident *res = nullptr;
   if (!k) {
     auto it = s->resident.find(g.hash);

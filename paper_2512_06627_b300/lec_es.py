@@ -34,7 +34,7 @@ EXPORTS = [
     "lec_es_batch_run_async", "lec_es_batch_results", "lec_es_batch_free", "lec_es_submit", "lec_es_poll",
     "lec_es_wait", "lec_es_cancel", "lec_es_server_config", "lec_es_lop3_peak", "lec_es_jit_compile",
     "lec_es_check_noalloc", "lec_es_batch_info", "lec_es_signatures", "lec_es_match_pairs",
-    "lec_es_codegen_version",
+    "lec_es_codegen_version", "lec_es_cost_fit", "lec_es_cost_model", "lec_es_cost_predict",
 ]
 
 
@@ -83,6 +83,18 @@ class lec_es_program_info(ctypes.Structure):
                 ("num_slots", ctypes.c_uint32), ("out_slot", ctypes.c_uint32), ("out_compl", ctypes.c_uint32),
                 ("order", ctypes.c_uint32), ("num_records", ctypes.c_uint64), ("hash", ctypes.c_uint64),
                 ("num_luts", ctypes.c_uint32), ("lut_live", ctypes.c_uint32)]
+
+
+class lec_es_cost_coeffs(ctypes.Structure):
+    _fields_ = [("a_ms", ctypes.c_double), ("c_ms", ctypes.c_double), ("alpha_ms", ctypes.c_double),
+                ("samples", ctypes.c_uint64)]
+
+
+class lec_es_cost(ctypes.Structure):
+    _fields_ = [("interp_ms", ctypes.c_double), ("jit_ms", ctypes.c_double), ("jit_compile_ms", ctypes.c_double),
+                ("paper_cpu_s", ctypes.c_double), ("gates", ctypes.c_uint32), ("n", ctypes.c_uint32),
+                ("num_luts", ctypes.c_uint32), ("tier", ctypes.c_uint32), ("gpu_offload", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32)]
 
 
 _lib: Optional[ctypes.CDLL] = None
@@ -139,6 +151,10 @@ def load() -> ctypes.CDLL:
         "lec_es_check_noalloc": ([_P, ctypes.c_uint64, ctypes.POINTER(lec_es_program_info), ctypes.c_uint64,
                                   ctypes.c_uint64, _P, _P], ctypes.c_int),
         "lec_es_codegen_version": ([], ctypes.c_uint32),
+        "lec_es_cost_fit": ([_u32p, _u32p, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t,
+                             ctypes.POINTER(lec_es_cost_coeffs)], ctypes.c_int),
+        "lec_es_cost_model": ([_P, ctypes.c_uint32, ctypes.POINTER(lec_es_cost_coeffs)], ctypes.c_int),
+        "lec_es_cost_predict": ([_P, M, ctypes.c_uint32, ctypes.POINTER(lec_es_cost)], ctypes.c_int),
         "lec_es_lop3_peak": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     }
@@ -424,3 +440,31 @@ def lec_es_lop3_peak(ctx: Context):
 def lec_es_codegen_version() -> int:
     """Version of the specialised-kernel code generator."""
     return int(load().lec_es_codegen_version())
+
+
+TIER_COMPILE = 4  # lec_es_cost_model: the kernel-build model
+
+
+def lec_es_cost_fit(gates, n, ms) -> lec_es_cost_coeffs:
+    """Fit t = a + c * gates + alpha * gates * 2^(n-23) (relative error, all >= 0)."""
+    g = np.ascontiguousarray(np.asarray(gates, dtype=np.uint32))
+    nn = np.ascontiguousarray(np.asarray(n, dtype=np.uint32))
+    t = np.ascontiguousarray(np.asarray(ms, dtype=np.float64))
+    out = lec_es_cost_coeffs()
+    _ok(load().lec_es_cost_fit(g.ctypes.data_as(_u32p), nn.ctypes.data_as(_u32p),
+                               t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(t), ctypes.byref(out)),
+        "lec_es_cost_fit")
+    return out
+
+
+def lec_es_cost_model(ctx: Optional[Context], tier: int) -> lec_es_cost_coeffs:
+    out = lec_es_cost_coeffs()
+    _ok(load().lec_es_cost_model(ctx.handle if ctx else None, tier, ctypes.byref(out)), "lec_es_cost_model")
+    return out
+
+
+def lec_es_cost_predict(ctx: Optional[Context], m: Miter, cpu_threads: int = 1) -> lec_es_cost:
+    out = lec_es_cost()
+    _ok(load().lec_es_cost_predict(ctx.handle if ctx else None, ctypes.byref(m.c), cpu_threads, ctypes.byref(out)),
+        "lec_es_cost_predict")
+    return out
