@@ -317,6 +317,52 @@ int lec_es_match_pairs(lec_es_ctx *c, uint32_t num_pis, uint32_t num_ands, const
 int lec_es_lop3_peak(lec_es_ctx *c, double *lop3_per_clk_per_sm, int *sm_count,
                      int *clock_khz, double *lop3_per_s);
 
+/* ---- sweeping with ES as the engine (§2.3, §3.2) ------------------------ */
+
+typedef struct {
+  uint32_t sim_words;       /* 64-pattern random-simulation words per round (0 = 64) */
+  uint32_t max_rounds;      /* (0 = 512) */
+  uint32_t max_leaves;      /* free inputs of a local sub-miter (0 = 16, at most 40) */
+  uint32_t max_nodes;       /* ANDs of a local sub-miter (0 = 128) */
+  uint32_t final_max_pis;   /* run the output's own ES check if its support is at most this (0 = 36, <= 63) */
+  uint32_t pad;
+  uint64_t seed;            /* random simulation seed */
+} lec_es_sweep_options;
+
+typedef struct {
+  lec_es_verdict verdict;   /* UNDECIDED if neither merging, simulation nor the final check decides */
+  uint32_t rounds;
+  uint64_t pairs_checked;   /* local sub-miters checked by ES */
+  uint64_t pairs_proven;    /* of which EQUIVALENT (merged) */
+  uint64_t pairs_refuted;   /* of which a counterexample with free cut inputs (left unmerged) */
+  uint64_t pairs_skipped;   /* candidate pairs over the leaf or node limit */
+  uint32_t ands_initial, ands_final;   /* ANDs of the output's cone before and after */
+  uint32_t final_support;   /* PIs of the output's remaining cone */
+  uint32_t decided_by;      /* 0 the output became a constant, 1 random simulation, 2 the final ES check, 3 undecided */
+  double sim_ms, es_ms, host_ms, total_ms;
+} lec_es_sweep_result;
+
+/* Sweep a miter (no counterpart entry point in the paper; its flow, §2.3,
+ * with ES as the checking engine and local sub-miters as in §3.2): rounds of
+ * GPU random simulation, candidate pairs (equal signatures up to
+ * complement), local sub-miters whose inputs are the points where the two
+ * cones meet (an EQUIVALENT result is a proof; a counterexample with free
+ * inputs only leaves the pair unmerged), one batched ES launch per round,
+ * and merging with structural hashing.  The miter may have any number of
+ * PIs; the output's own ES check (final_max_pis) runs when merging stops
+ * short of a constant.
+ * cex_bits (optional, (num_pis + 63) / 64 words): for NONEQUIVALENT, a
+ *   failing input assignment, bit i = PI i (0-based); not necessarily the
+ *   lowest one unless decided_by = 2.
+ * merges (optional, 3 * merges_cap words): (member, representative, phase)
+ *   variables of the input AIG proven equal (member == representative XOR
+ *   phase) by the local checks, in the order proven; *nmerges = total (may
+ *   exceed merges_cap).
+ * Errors: EINVAL (malformed AIG), ENOMEM, ECUDA. */
+int lec_es_sweep(lec_es_ctx *c, const lec_es_miter *m, const lec_es_sweep_options *opt,
+                 lec_es_sweep_result *out, uint64_t *cex_bits, uint32_t *merges, uint64_t merges_cap,
+                 uint64_t *nmerges);
+
 /* ---- ES time model (§3.2, refit for this GPU) --------------------------- */
 
 /* The paper models ES time as alpha * gates * 2^(n - beta).  alpha * 2^-beta

@@ -575,6 +575,31 @@ def build_golden_revised_multipliers(w: int) -> Aig:
     return g.finish(outs["A"] + outs["B"], side_ranges=ranges, side_outputs=outs)
 
 
+def build_revised_pair(w: int, kind: str = "array", mutant_seed: Optional[int] = None) -> Aig:
+    """w x w multiplier (side A, plain XOR/majority forms) against its locally
+    re-synthesized copy (side B, the alternative forms), as one miter over
+    all 2w product bits: the golden-vs-revised setting of equivalence
+    checking, where internal nodes correspond one to one.  ``kind`` is
+    "array" or "booth"; an optional seeded edge inversion goes into side B."""
+    g, a, b = _two_operand_builder(w)
+    build = array_multiplier if kind == "array" else booth_multiplier
+    g.new_scope()
+    sa = g.next_var
+    oa = build(g, a, b)
+    g.new_scope()
+    g.style = "alt"
+    sb = g.next_var
+    ob = build(g, a, b)
+    eb = g.next_var
+    g.style = "plain"
+    g.new_scope()
+    m = g.finish([miter_outputs(g, oa, ob)], side_ranges={"A": (sa, sb), "B": (sb, eb)},
+                 side_outputs={"A": oa, "B": ob})
+    if mutant_seed is not None:
+        m, _ = inject_edge_inversion(m, "B", mutant_seed)
+    return m
+
+
 def _copy_path_with_flip(g_f0: List[int], g_f1: List[int], num_pis: int, root: int,
                          flip_var: int, flip_edge: int) -> int:
     """Append to (g_f0, g_f1) a copy of every AND on a path from ``flip_var`` to

@@ -91,6 +91,12 @@ struct CostModel {
 
 double now_ms();
 
+// Random simulation of a whole AIG on the GPU (sweep.cu): signatures (host
+// rows, may be null), hashes (phase-normalised with norm), PI-support masks
+// (num_pis <= 64; may be null).
+int simulate(lec_es_ctx *c, uint32_t num_pis, uint32_t num_ands, const uint32_t *fanins, const uint64_t *pi_words,
+             uint32_t nwords, uint64_t *h_sigs, uint64_t *h_hash, uint64_t *h_sup, bool norm);
+
 // ES time model (cost.cpp).  c may be null (built-in values only).
 double cost_x(uint32_t gates, uint32_t n);
 double cost_run_ms(lec_es_ctx *c, uint32_t tier, uint32_t gates, uint32_t n);

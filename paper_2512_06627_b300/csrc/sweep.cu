@@ -39,9 +39,11 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x, uint64_t w) {
   return z ^ (z >> 31);
 }
 
+// With norm set the hash is of the node's signature complemented when its
+// first pattern is 1, so a node and its complement hash alike.
 __global__ void __launch_bounds__(256) sim_level(const uint32_t *__restrict__ fanins, const uint32_t *__restrict__ nodes,
                                                  uint32_t count, uint32_t num_pis, uint32_t nwords, uint64_t *sig,
-                                                 uint64_t *sup, uint64_t *hash) {
+                                                 uint64_t *sup, uint64_t *hash, int norm) {
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t lane = threadIdx.x & 31u;
   if (warp >= count) return;  // whole warps exit together
@@ -52,11 +54,13 @@ __global__ void __launch_bounds__(256) sim_level(const uint32_t *__restrict__ fa
   const uint64_t *s0 = sig + (size_t)(l0 >> 1) * nwords;
   const uint64_t *s1 = sig + (size_t)(l1 >> 1) * nwords;
   uint64_t *d = sig + (size_t)v * nwords;
+  // the phase: first pattern of the node (word 0, bit 0), known to every lane
+  const uint64_t flip = norm && (((s0[0] ^ m0) & (s1[0] ^ m1)) & 1ull) ? ~0ull : 0ull;
   uint64_t h = 0;
   for (uint32_t w = lane; w < nwords; w += 32) {
     const uint64_t x = (s0[w] ^ m0) & (s1[w] ^ m1);
     d[w] = x;
-    h ^= mix64(x, w);
+    h ^= mix64(x ^ flip, w);
   }
   for (int o = 16; o > 0; o >>= 1) h ^= __shfl_xor_sync(0xFFFFFFFFu, h, o);
   if (lane == 0) {
@@ -67,13 +71,14 @@ __global__ void __launch_bounds__(256) sim_level(const uint32_t *__restrict__ fa
 
 // Hashes (and support masks) of the constant and the PIs.
 __global__ void __launch_bounds__(256) sim_leaves(uint32_t num_pis, uint32_t nwords, const uint64_t *sig, uint64_t *sup,
-                                                  uint64_t *hash) {
+                                                  uint64_t *hash, int norm) {
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t lane = threadIdx.x & 31u;
   if (warp > num_pis) return;
   const uint64_t *s = sig + (size_t)warp * nwords;
+  const uint64_t flip = norm && (s[0] & 1ull) ? ~0ull : 0ull;
   uint64_t h = 0;
-  for (uint32_t w = lane; w < nwords; w += 32) h ^= mix64(s[w], w);
+  for (uint32_t w = lane; w < nwords; w += 32) h ^= mix64(s[w] ^ flip, w);
   for (int o = 16; o > 0; o >>= 1) h ^= __shfl_xor_sync(0xFFFFFFFFu, h, o);
   if (lane == 0) {
     hash[warp] = h;
@@ -93,9 +98,13 @@ struct SimBuffers {
   }
 };
 
-// Simulate every variable; fills host arrays (sigs may be null).
+}  // namespace
+
+// Simulate every variable; fills host arrays (sigs may be null).  With norm
+// the hashes are of phase-normalised signatures (complemented when the first
+// pattern is 1).
 int simulate(lec_es_ctx *c, uint32_t num_pis, uint32_t num_ands, const uint32_t *fanins, const uint64_t *pi_words,
-             uint32_t nwords, uint64_t *h_sigs, uint64_t *h_hash, uint64_t *h_sup) {
+             uint32_t nwords, uint64_t *h_sigs, uint64_t *h_hash, uint64_t *h_sup, bool norm) {
   if (!c || (num_ands && !fanins) || (num_pis && !pi_words) || nwords == 0 || !h_hash) return LEC_ES_EINVAL;
   const uint64_t V = (uint64_t)num_pis + num_ands + 1;
   // levels (every fanin variable is below its AND: one forward pass)
@@ -140,14 +149,15 @@ int simulate(lec_es_ctx *c, uint32_t num_pis, uint32_t num_ands, const uint32_t 
     e = cudaMemcpyAsync(b.sig + nwords, pi_words, (uint64_t)num_pis * nwords * 8, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
     const uint32_t warps = num_pis + 1;
-    sim_leaves<<<(warps * 32 + 255) / 256, 256, 0, st>>>(num_pis, nwords, b.sig, b.sup, b.hash);
+    sim_leaves<<<(warps * 32 + 255) / 256, 256, 0, st>>>(num_pis, nwords, b.sig, b.sup, b.hash, norm ? 1 : 0);
     e = cudaGetLastError();
   }
   for (uint32_t l = 1; l <= maxl && e == cudaSuccess; l++) {
     const uint32_t cnt = off[l + 1] - off[l];
     if (!cnt) continue;
     sim_level<<<(uint32_t)(((uint64_t)cnt * 32 + 255) / 256), 256, 0, st>>>(
-        (const uint32_t *)b.fan, (const uint32_t *)b.nodes + off[l], cnt, num_pis, nwords, b.sig, b.sup, b.hash);
+        (const uint32_t *)b.fan, (const uint32_t *)b.nodes + off[l], cnt, num_pis, nwords, b.sig, b.sup, b.hash,
+        norm ? 1 : 0);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_hash, b.hash, V * 8, cudaMemcpyDeviceToHost, st);
@@ -158,7 +168,6 @@ int simulate(lec_es_ctx *c, uint32_t num_pis, uint32_t num_ands, const uint32_t 
   return (e == cudaSuccess && se == cudaSuccess) ? LEC_ES_OK : LEC_ES_ECUDA;
 }
 
-}  // namespace
 }  // namespace lec
 
 using namespace lec;
@@ -166,7 +175,7 @@ using namespace lec;
 extern "C" int lec_es_signatures(lec_es_ctx *c, uint32_t num_pis, uint32_t num_ands, const uint32_t *fanins,
                                  const uint64_t *pi_words, uint32_t nwords, uint64_t *sigs_out, uint64_t *hash_out) {
   if (!hash_out) return LEC_ES_EINVAL;
-  return simulate(c, num_pis, num_ands, fanins, pi_words, nwords, sigs_out, hash_out, nullptr);
+  return simulate(c, num_pis, num_ands, fanins, pi_words, nwords, sigs_out, hash_out, nullptr, false);
 }
 
 extern "C" int lec_es_match_pairs(lec_es_ctx *c, uint32_t num_pis, uint32_t num_ands, const uint32_t *fanins,
@@ -180,7 +189,7 @@ extern "C" int lec_es_match_pairs(lec_es_ctx *c, uint32_t num_pis, uint32_t num_
   } catch (const std::bad_alloc &) {
     return LEC_ES_ENOMEM;
   }
-  int rc = simulate(c, num_pis, num_ands, fanins, pi_words, nwords, sigs.data(), hash.data(), sup.data());
+  int rc = simulate(c, num_pis, num_ands, fanins, pi_words, nwords, sigs.data(), hash.data(), sup.data(), false);
   if (rc) return rc;
   auto row = [&](uint64_t v) { return &sigs[v * nwords]; };
   auto constant = [&](uint64_t v) {

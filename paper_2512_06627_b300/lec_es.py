@@ -34,7 +34,7 @@ EXPORTS = [
     "lec_es_batch_run_async", "lec_es_batch_results", "lec_es_batch_free", "lec_es_submit", "lec_es_poll",
     "lec_es_wait", "lec_es_cancel", "lec_es_server_config", "lec_es_lop3_peak", "lec_es_jit_compile",
     "lec_es_check_noalloc", "lec_es_batch_info", "lec_es_signatures", "lec_es_match_pairs",
-    "lec_es_codegen_version", "lec_es_cost_fit", "lec_es_cost_model", "lec_es_cost_predict",
+    "lec_es_codegen_version", "lec_es_cost_fit", "lec_es_cost_model", "lec_es_cost_predict", "lec_es_sweep",
 ]
 
 
@@ -97,6 +97,21 @@ class lec_es_cost(ctypes.Structure):
                 ("pad", ctypes.c_uint32)]
 
 
+class lec_es_sweep_options(ctypes.Structure):
+    _fields_ = [("sim_words", ctypes.c_uint32), ("max_rounds", ctypes.c_uint32), ("max_leaves", ctypes.c_uint32),
+                ("max_nodes", ctypes.c_uint32), ("final_max_pis", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64)]
+
+
+class lec_es_sweep_result(ctypes.Structure):
+    _fields_ = [("verdict", ctypes.c_int), ("rounds", ctypes.c_uint32), ("pairs_checked", ctypes.c_uint64),
+                ("pairs_proven", ctypes.c_uint64), ("pairs_refuted", ctypes.c_uint64),
+                ("pairs_skipped", ctypes.c_uint64), ("ands_initial", ctypes.c_uint32),
+                ("ands_final", ctypes.c_uint32), ("final_support", ctypes.c_uint32), ("decided_by", ctypes.c_uint32),
+                ("sim_ms", ctypes.c_double), ("es_ms", ctypes.c_double), ("host_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double)]
+
+
 _lib: Optional[ctypes.CDLL] = None
 _P = ctypes.c_void_p
 _u32p = ctypes.POINTER(ctypes.c_uint32)
@@ -151,6 +166,8 @@ def load() -> ctypes.CDLL:
         "lec_es_check_noalloc": ([_P, ctypes.c_uint64, ctypes.POINTER(lec_es_program_info), ctypes.c_uint64,
                                   ctypes.c_uint64, _P, _P], ctypes.c_int),
         "lec_es_codegen_version": ([], ctypes.c_uint32),
+        "lec_es_sweep": ([_P, M, ctypes.POINTER(lec_es_sweep_options), ctypes.POINTER(lec_es_sweep_result), _u64p,
+                          _u32p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
         "lec_es_cost_fit": ([_u32p, _u32p, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t,
                              ctypes.POINTER(lec_es_cost_coeffs)], ctypes.c_int),
         "lec_es_cost_model": ([_P, ctypes.c_uint32, ctypes.POINTER(lec_es_cost_coeffs)], ctypes.c_int),
@@ -468,3 +485,22 @@ def lec_es_cost_predict(ctx: Optional[Context], m: Miter, cpu_threads: int = 1) 
     _ok(load().lec_es_cost_predict(ctx.handle if ctx else None, ctypes.byref(m.c), cpu_threads, ctypes.byref(out)),
         "lec_es_cost_predict")
     return out
+
+
+def lec_es_sweep(ctx: Context, m: Miter, sim_words: int = 0, max_rounds: int = 0, max_leaves: int = 0,
+                 max_nodes: int = 0, final_max_pis: int = 0, seed: int = 0, merges_cap: int = 0):
+    """Sweep a miter: (result, cex as a list of PI values or None, merges as
+    (member, representative, phase) triples of the input AIG)."""
+    num_pis = int(m.c.num_pis)
+    o = lec_es_sweep_options(sim_words, max_rounds, max_leaves, max_nodes, final_max_pis, 0, seed)
+    r = lec_es_sweep_result()
+    cex = np.zeros(max(1, (num_pis + 63) // 64), dtype=np.uint64)
+    mg = np.zeros(max(1, 3 * merges_cap), dtype=np.uint32)
+    n = ctypes.c_uint64()
+    _ok(load().lec_es_sweep(ctx.handle, ctypes.byref(m.c), ctypes.byref(o), ctypes.byref(r), cex.ctypes.data_as(_u64p),
+                            mg.ctypes.data_as(_u32p), merges_cap, ctypes.byref(n)), "lec_es_sweep")
+    bits = None
+    if r.verdict == NONEQUIVALENT:
+        bits = [int((int(cex[k // 64]) >> (k % 64)) & 1) for k in range(num_pis)]
+    trip = [(int(mg[3 * i]), int(mg[3 * i + 1]), int(mg[3 * i + 2])) for i in range(min(merges_cap, n.value))]
+    return r, bits, trip
