@@ -350,6 +350,29 @@ def measure_serve(ctx, args):
     }
 
 
+def measure_sweep(ctx):
+    """The sweeping loop with ES as its engine on 64-PI miters that ES alone
+    cannot enumerate: 32x32 array and Booth multipliers against their
+    re-synthesized copies, and a seeded mutant of the first."""
+    from paper_2512_06627_b300 import circuits as C
+    from paper_2512_06627_b300 import lec_es as L
+    out = {}
+    for name, aig in (("array32_vs_resynthesized", C.build_revised_pair(32)),
+                      ("booth32_vs_resynthesized", C.build_revised_pair(32, "booth")),
+                      ("array32_vs_resynthesized_mutant", C.build_revised_pair(32, mutant_seed=4))):
+        m = L.Miter(aig.num_pis, aig.flat_fanins(), aig.outputs[0])
+        L.lec_es_sweep(ctx, m, seed=1)  # warm (kernel modules, buffers)
+        t0 = time.perf_counter()
+        r, _, _ = L.lec_es_sweep(ctx, m, seed=1)
+        wall = (time.perf_counter() - t0) * 1e3
+        out[name] = {"pis": aig.num_pis, "verdict": {0: "equivalent", 1: "nonequivalent", 2: "undecided"}[r.verdict],
+                     "decided_by": ["constant output", "simulation", "final ES", "undecided"][r.decided_by],
+                     "rounds": r.rounds, "pairs_checked": r.pairs_checked, "pairs_proven": r.pairs_proven,
+                     "ands_initial": r.ands_initial, "ands_final": r.ands_final, "ms": wall,
+                     "sim_ms": r.sim_ms, "es_ms": r.es_ms, "host_ms": r.host_ms}
+    return out
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -476,6 +499,8 @@ def run_ours(args, ws, rank, local):
         line["batched"] = measure_batch(ctx, args)
     if rank == 0 and args.serve_requests > 0:
         line["served"] = measure_serve(ctx, args)
+    if rank == 0 and not args.no_batch:
+        line["sweep"] = measure_sweep(ctx)
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, sample = cpu_oracle_rate(aig, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "node-pattern evals/s", "cores": cores, "kind": "oracle",

@@ -46,6 +46,7 @@ namespace lec {
 namespace {
 
 constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kMissRun = 1024;  // consecutive too-wide regions that end a round's cutting
 
 struct Graph {
   uint32_t P = 0;              // PIs are variables 1..P, the constant is 0
@@ -359,10 +360,26 @@ extern "C" int lec_es_sweep(lec_es_ctx *c, const lec_es_miter *m, const lec_es_s
         }
         i = j;
       }
+      // lowest pairs first; a long run of pairs whose regions are too wide
+      // means the merged frontier is below them, so the rest wait for the
+      // next round
+      std::stable_sort(cands.begin(), cands.end(), [&](const Region &x, const Region &y) {
+        return std::max(level[x.rep], level[x.mem]) < std::max(level[y.rep], level[y.mem]);
+      });
       std::vector<Region> regions;
+      uint32_t misses = 0;
       for (Region &r : cands) {
-        if (cut_region(g, level, mask, touched, r, max_nodes, max_leaves)) regions.push_back(std::move(r));
-        else out->pairs_skipped++;
+        if (misses >= kMissRun) {
+          out->pairs_skipped++;
+          continue;
+        }
+        if (cut_region(g, level, mask, touched, r, max_nodes, max_leaves)) {
+          regions.push_back(std::move(r));
+          misses = 0;
+        } else {
+          out->pairs_skipped++;
+          misses++;
+        }
       }
       if (regions.empty()) {
         out->host_ms += ms_since(t0);
