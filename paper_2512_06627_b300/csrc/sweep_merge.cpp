@@ -29,6 +29,8 @@
 // its support is small enough, else the verdict is UNDECIDED (SAT and BDD
 // engines are not part of this library).
 #include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -166,14 +168,28 @@ struct Region {
 // the region, or one of them is, becomes internal), so a leaf is not a free
 // copy of logic over other leaves -- the main source of spurious
 // counterexamples.  False if the region exceeds the limits.
+typedef std::vector<std::pair<uint32_t, uint32_t>> Heap;  // (level, var) max-heaps, reused across calls
+
 bool cut_region(const Graph &g, const std::vector<uint32_t> &level, std::vector<uint8_t> &mask,
-                std::vector<uint32_t> &touched, Region &r, uint32_t max_nodes, uint32_t max_leaves) {
+                std::vector<uint32_t> &touched, Heap &pq, Heap &leafq, Region &r, uint32_t max_nodes,
+                uint32_t max_leaves) {
   constexpr uint8_t kIn = 4, kLeaf = 8;  // mask bits beside the two sides
-  std::priority_queue<std::pair<uint32_t, uint32_t>> pq;  // (level, var), highest first
+  pq.clear();
+  leafq.clear();
+  auto push = [](Heap &h, uint32_t l, uint32_t v) {
+    h.push_back({l, v});
+    std::push_heap(h.begin(), h.end());
+  };
+  auto pop = [](Heap &h) {
+    std::pop_heap(h.begin(), h.end());
+    const uint32_t v = h.back().second;
+    h.pop_back();
+    return v;
+  };
   auto reach = [&](uint32_t v, uint8_t side) {
     if (!mask[v]) {
       touched.push_back(v);
-      pq.push({level[v], v});
+      push(pq, level[v], v);
     }
     mask[v] |= side;
   };
@@ -182,16 +198,14 @@ bool cut_region(const Graph &g, const std::vector<uint32_t> &level, std::vector<
   reach(r.mem, 2);
   bool ok = true;
   uint32_t nand = 0, nleaf = 0;
-  std::priority_queue<std::pair<uint32_t, uint32_t>> leafq;
   while (!pq.empty() && ok) {
-    const uint32_t v = pq.top().second;
-    pq.pop();
+    const uint32_t v = pop(pq);
     if (v == 0) continue;  // the constant stays a constant
     if (v <= g.P || (mask[v] & 3) == 3) {
       mask[v] |= kLeaf;
       // opening leaves rarely removes many: give up early on wide cones
       if (++nleaf > 2 * max_leaves + 4) ok = false;
-      if (v > g.P) leafq.push({level[v], v});
+      if (v > g.P) push(leafq, level[v], v);
       continue;
     }
     mask[v] |= kIn;
@@ -201,8 +215,7 @@ bool cut_region(const Graph &g, const std::vector<uint32_t> &level, std::vector<
   }
   // open leaves that cost no new leaf
   while (ok && !leafq.empty()) {
-    const uint32_t v = leafq.top().second;
-    leafq.pop();
+    const uint32_t v = pop(leafq);
     const uint32_t a = fanin(v, 0), b = fanin(v, 1);
     const int fresh = (a != 0 && !(mask[a] & (kIn | kLeaf))) + (b != 0 && a != b && !(mask[b] & (kIn | kLeaf)));
     if (fresh > 1) continue;
@@ -214,7 +227,7 @@ bool cut_region(const Graph &g, const std::vector<uint32_t> &level, std::vector<
       if (!mask[u]) touched.push_back(u);
       mask[u] |= kLeaf;
       nleaf++;
-      if (u > g.P) leafq.push({level[u], u});
+      if (u > g.P) push(leafq, level[u], u);
     }
   }
   if (ok && nleaf <= max_leaves) {
@@ -257,6 +270,7 @@ extern "C" int lec_es_sweep(lec_es_ctx *c, const lec_es_miter *m, const lec_es_s
   const uint32_t max_nodes = opt && opt->max_nodes ? opt->max_nodes : 128;
   const uint32_t final_pis = std::min<uint32_t>(opt && opt->final_max_pis ? opt->final_max_pis : 36, 63);
   const uint64_t seed = opt ? opt->seed : 0;
+  const bool log = getenv("LEC_ES_SWEEP_LOG") != nullptr;  // per-round counts and host times
   const auto t_start = std::chrono::steady_clock::now();
   memset(out, 0, sizeof(*out));
   out->verdict = LEC_ES_UNDECIDED;
@@ -284,6 +298,7 @@ extern "C" int lec_es_sweep(lec_es_ctx *c, const lec_es_miter *m, const lec_es_s
     std::vector<uint32_t> level;
     std::vector<uint8_t> mask;
     std::vector<uint32_t> touched;
+    Heap heap, heap2;
     uint32_t idle = 0;
     for (uint32_t round = 0; round < max_rounds; round++) {
       if ((g.out >> 1) == 0) break;  // the output is a constant
@@ -363,28 +378,31 @@ extern "C" int lec_es_sweep(lec_es_ctx *c, const lec_es_miter *m, const lec_es_s
       // lowest pairs first; a long run of pairs whose regions are too wide
       // means the merged frontier is below them, so the rest wait for the
       // next round
+      const double t_class = ms_since(t0);
       std::stable_sort(cands.begin(), cands.end(), [&](const Region &x, const Region &y) {
         return std::max(level[x.rep], level[x.mem]) < std::max(level[y.rep], level[y.mem]);
       });
+      // lowest first; a long run of too-wide regions ends the round's cutting
+      // (the merged frontier is below them; threads did not pay here: the
+      // cuts are allocation-bound)
+      std::vector<uint8_t> cut_ok(cands.size(), 0);
+      {
+        uint32_t misses = 0;
+        for (size_t i = 0; i < cands.size() && misses < kMissRun; i++) {
+          cut_ok[i] = cut_region(g, level, mask, touched, heap, heap2, cands[i], max_nodes, max_leaves) ? 1 : 0;
+          misses = cut_ok[i] ? 0 : misses + 1;
+        }
+      }
       std::vector<Region> regions;
-      uint32_t misses = 0;
-      for (Region &r : cands) {
-        if (misses >= kMissRun) {
-          out->pairs_skipped++;
-          continue;
-        }
-        if (cut_region(g, level, mask, touched, r, max_nodes, max_leaves)) {
-          regions.push_back(std::move(r));
-          misses = 0;
-        } else {
-          out->pairs_skipped++;
-          misses++;
-        }
+      for (size_t i = 0; i < cands.size(); i++) {
+        if (cut_ok[i]) regions.push_back(std::move(cands[i]));
+        else out->pairs_skipped++;
       }
       if (regions.empty()) {
         out->host_ms += ms_since(t0);
         break;
       }
+      const double t_cut = ms_since(t0) - t_class;
       // (3) one AIG holding every local sub-miter: leaf i of a region is PI
       // i + 1, region ANDs are copied, the pair's XOR is the output
       uint32_t L = 0;
@@ -440,7 +458,11 @@ extern "C" int lec_es_sweep(lec_es_ctx *c, const lec_es_miter *m, const lec_es_s
       }
       out->pairs_proven += proven;
       if (proven) g = rebuild(g, subst);
-      out->host_ms += ms_since(t0);
+      const double t_merge = ms_since(t0);
+      out->host_ms += t_merge;
+      if (log)
+        fprintf(stderr, "sweep round %u: vars %u candidates %zu regions %zu proven %u | class %.2f cut %.2f merge %.2f ms\n",
+                round, V, cands.size(), regions.size(), proven, t_class, t_cut, t_merge);
       idle = proven ? 0 : idle + 1;
       if (idle >= 2) break;  // two rounds (two sets of random words) without a merge
     }
