@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-load", type=float, default=0.7)
+    ap.add_argument("--serve-full", action="store_true",
+                    help="the served workload at full size: a Poisson stream over all --serve-requests "
+                         "(e.g. 20000) at --serve-load of a capacity measured on the first 400, verdicts "
+                         "checked against the generator, a seeded sample of 200 re-run alone")
     return ap.parse_args()
 
 
@@ -373,6 +377,71 @@ def measure_sweep(ctx):
     return out
 
 
+def measure_serve_full(ctx, args):
+    """The served workload at its full size: every request of the seeded
+    Poisson stream (array-vs-Booth product-bit miters, w in 8..18, 1%
+    mutants) through the continuous-batching server.  The arrival rate is
+    --serve-load of the capacity measured with the first 400 requests queued
+    at once.  Each verdict must match the generator (mutants differ, the rest
+    are equivalent), and a seeded sample of 200 requests is re-run alone."""
+    import numpy as np
+    from paper_2512_06627_b300 import circuits as C
+    from paper_2512_06627_b300 import lec_es as L
+    R = max(1, args.serve_requests)
+    base = C.config5_stream(num_requests=R, rate_per_s=1.0)
+    pm = C.ProductBitMiters(seed=5)
+    flat, first = {}, {}
+    ms = []
+    for i, r in enumerate(base):
+        aig, out = pm.miter(r.w, r.bit, r.mutant, mutant_seed=i)
+        f = flat.get(id(aig))
+        if f is None:
+            f = flat[id(aig)] = (aig, aig.flat_fanins())  # one fanin array per distinct netlist (kept alive)
+        ms.append(L.Miter(aig.num_pis, f[1], out))
+        first.setdefault((id(aig), out), ms[-1])
+    t0 = time.perf_counter()
+    seen, uniq = set(), []
+    for m in first.values():
+        h = L.lec_es_compile(m)[0].hash
+        if h not in seen:
+            seen.add(h)
+            uniq.append(m)
+    b = L.lec_es_batch_prepare(ctx, uniq)
+    L.lec_es_batch_free(ctx, b)
+    warm_s = time.perf_counter() - t0
+    K = min(R, 400)
+    t0 = time.perf_counter()
+    tk = [L.lec_es_submit(ctx, m) for m in ms[:K]]
+    [L.lec_es_wait(ctx, t, 3600.0) for t in tk]
+    capacity = K / (time.perf_counter() - t0)
+    rate = args.serve_load * capacity
+    reqs = C.config5_stream(num_requests=R, rate_per_s=rate)
+    start = time.perf_counter()
+    tk = []
+    for r, m in zip(reqs, ms):
+        dt = r.arrival_s - (time.perf_counter() - start)
+        if dt > 0:
+            time.sleep(dt)
+        tk.append(L.lec_es_submit(ctx, m))
+    res = [L.lec_es_wait(ctx, t, 3600.0) for t in tk]
+    span = time.perf_counter() - start
+    want = [L.NONEQUIVALENT if r.mutant else L.EQUIVALENT for r in base]
+    assert [r.verdict for r in res] == want
+    rng = np.random.default_rng(11)
+    sample = sorted(rng.choice(R, size=min(R, 200), replace=False).tolist())
+    for i in sample:
+        assert L.lec_es_check(ctx, ms[i]).cex == res[i].cex
+    lat = np.array([r.latency_ms for r in res])
+    return {
+        "requests": R, "distinct_programs": len(uniq), "mutants": int(sum(r.mutant for r in base)),
+        "capacity_miters_per_s_first_400": capacity, "poisson_rate_per_s": rate, "poisson_load": args.serve_load,
+        "poisson_miters_per_s": R / span, "span_s": span,
+        "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
+        "p999_latency_ms": float(np.percentile(lat, 99.9)),
+        "verdicts_match_generator": True, "sample_equal_alone": len(sample), "jit_warmup_s": warm_s,
+    }
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -498,7 +567,7 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and not args.no_batch:
         line["batched"] = measure_batch(ctx, args)
     if rank == 0 and args.serve_requests > 0:
-        line["served"] = measure_serve(ctx, args)
+        line["served"] = measure_serve_full(ctx, args) if args.serve_full else measure_serve(ctx, args)
     if rank == 0 and not args.no_batch:
         line["sweep"] = measure_sweep(ctx)
     if rank == 0 and not args.no_cpu_baseline:
