@@ -49,6 +49,7 @@ namespace {
 
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kMissRun = 1024;  // consecutive too-wide regions that end a round's cutting
+constexpr uint32_t kNoMeet = 48;     // region ANDs walked before the two cones must have met
 
 struct Graph {
   uint32_t P = 0;              // PIs are variables 1..P, the constant is 0
@@ -198,10 +199,12 @@ bool cut_region(const Graph &g, const std::vector<uint32_t> &level, std::vector<
   reach(r.mem, 2);
   bool ok = true;
   uint32_t nand = 0, nleaf = 0;
+  bool met = r.rep == 0;  // a constant pair has no meeting point to wait for
   while (!pq.empty() && ok) {
     const uint32_t v = pop(pq);
     if (v == 0) continue;  // the constant stays a constant
     if (v <= g.P || (mask[v] & 3) == 3) {
+      met = met || (mask[v] & 3) == 3;
       mask[v] |= kLeaf;
       // opening leaves rarely removes many: give up early on wide cones
       if (++nleaf > 2 * max_leaves + 4) ok = false;
@@ -210,6 +213,9 @@ bool cut_region(const Graph &g, const std::vector<uint32_t> &level, std::vector<
     }
     mask[v] |= kIn;
     if (++nand > max_nodes) ok = false;
+    // cones that have not met after a few dozen nodes lie above the merged
+    // frontier: their region would run to the node limit
+    if (!met && nand > kNoMeet) ok = false;
     reach(fanin(v, 0), mask[v] & 3);
     reach(fanin(v, 1), mask[v] & 3);
   }
