@@ -59,6 +59,7 @@ struct JitKernel {
   uint32_t num_luts = 0;   // the program's table count and live count when built
   uint32_t lut_live = 0;
   uint32_t work_per_chunk = 0;  // straight-line instructions per 32-pattern chunk (about)
+  uint32_t rep_fixed = 0;       // passes per grab compiled into the kernel (0: a launch parameter)
 };
 struct JitState;
 struct Server;

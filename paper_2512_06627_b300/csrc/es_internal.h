@@ -82,6 +82,12 @@ struct KernelProbe {
 int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Program &out,
                     const KernelProbe *probe = nullptr);
 
+// Tables of the specialised kernel evaluated once per grab (hoist.cpp):
+// hoisted[i] for lp.order[i]; support PIs [vary_lo, vary_hi) change from pass
+// to pass; at most `budget` hoisted values are read by per-pass code.
+void plan_hoist(const LutProgram &lp, uint32_t vary_lo, uint32_t vary_hi, uint32_t budget,
+                std::vector<uint8_t> &hoisted, uint32_t *roots);
+
 // Words of 64 patterns for a support of n PIs.
 inline uint64_t num_words(uint32_t n) { return n <= 6 ? 1ull : (1ull << (n - 6)); }
 // 32-pattern chunks (the kernels' unit: one 32-bit lane per thread).

@@ -1,0 +1,128 @@
+// hoist.cpp -- tables of the specialised kernel evaluated once per grab.
+//
+// A warp takes grabs of rep passes; grab q covers the chunks [q*G, (q+1)*G),
+// G = 32 * rep (a power of two), so within a grab a chunk index differs only
+// in its low log2(G) bits: bits 0..4 are the lane (support PIs 5..9, fixed
+// per thread), bits 5..log2(G)-1 are the pass (the only PIs that change from
+// pass to pass), and every higher bit is the grab's.  A table none of whose
+// inputs depends on the pass PIs has the same value in every pass of a grab,
+// so it can be evaluated once per grab -- the same Boolean function of the
+// same inputs, fewer instructions.  Keeping such a value across the passes
+// costs a register, so only a few hoisted values may be read by the
+// per-pass code; a hoisted table whose every reader is hoisted costs
+// nothing.  The hoisted set is grown by whole fanin cones of invariant
+// tables at the edge of the invariant region, greedily by tables removed per
+// register, up to a register budget.
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "es_internal.h"
+
+namespace lec {
+
+void plan_hoist(const LutProgram &lp, uint32_t vary_lo, uint32_t vary_hi, uint32_t budget,
+                std::vector<uint8_t> &hoisted, uint32_t *roots_out) {
+  const uint32_t NA = lp.na, NP = lp.np;
+  const size_t NL = lp.order.size();
+  hoisted.assign(NL, 0);
+  if (roots_out) *roots_out = 0;
+  if (NL == 0 || lp.root < 0 || lp.root >= (int64_t)NA) return;
+  std::vector<int32_t> pos(NA, -1);  // AND value id -> table index
+  for (size_t i = 0; i < NL; i++) pos[lp.order[i].node] = (int32_t)i;
+  // invariant over the passes of a grab: constants, PIs outside the pass
+  // range, tables of invariant inputs
+  std::vector<uint8_t> inv(NL, 0);
+  auto leaf_inv = [&](int32_t v) -> bool {
+    if (v < 0) return true;
+    if ((uint32_t)v >= NA) {
+      const uint32_t k = (uint32_t)v - NA;
+      return k >= NP || k < vary_lo || k >= vary_hi;  // k == NP is the constant
+    }
+    return pos[v] >= 0 && inv[pos[v]];
+  };
+  for (size_t i = 0; i < NL; i++) {
+    bool ok = true;
+    for (int k = 0; k < lp.order[i].n; k++) ok = ok && leaf_inv(lp.order[i].leaf[k]);
+    inv[i] = ok;
+  }
+  // readers of each table (table indices; the output counts as a reader
+  // that is never hoisted)
+  std::vector<std::vector<int32_t>> readers(NL);
+  for (size_t i = 0; i < NL; i++)
+    for (int k = 0; k < lp.order[i].n; k++) {
+      const int32_t v = lp.order[i].leaf[k];
+      if (v >= 0 && (uint32_t)v < NA && pos[v] >= 0) readers[pos[v]].push_back((int32_t)i);
+    }
+  const int32_t out_t = pos[lp.root];
+  // A hoisted set is the fanin cone of its roots (every table a hoisted
+  // table reads is hoisted too); its cost is the number of hoisted values
+  // the per-pass code reads (a table outside the set, or the output).
+  std::vector<uint8_t> in(NL, 0), trial(NL, 0);
+  auto grow = [&](std::vector<uint8_t> &h, int32_t r) -> uint32_t {  // add r's cone, return tables added
+    uint32_t added = 0;
+    std::vector<int32_t> st{r};
+    while (!st.empty()) {
+      const int32_t i = st.back();
+      st.pop_back();
+      if (h[i]) continue;
+      h[i] = 1;
+      added++;
+      for (int k = 0; k < lp.order[i].n; k++) {
+        const int32_t v = lp.order[i].leaf[k];
+        if (v >= 0 && (uint32_t)v < NA && pos[v] >= 0 && !h[pos[v]]) st.push_back(pos[v]);
+      }
+    }
+    return added;
+  };
+  auto cost = [&](const std::vector<uint8_t> &h) -> uint32_t {
+    uint32_t c = 0;
+    for (size_t i = 0; i < NL; i++) {
+      if (!h[i]) continue;
+      bool read = (int32_t)i == out_t;
+      for (int32_t r : readers[i]) read = read || !h[r];
+      c += read;
+    }
+    return c;
+  };
+  // candidate roots: invariant tables read by a table that is not
+  // invariant, or the output itself when it is invariant
+  std::vector<int32_t> cand;
+  for (size_t i = 0; i < NL; i++) {
+    if (!inv[i]) continue;
+    bool edge = (int32_t)i == out_t;
+    for (int32_t r : readers[i]) edge = edge || !inv[r];
+    if (edge) cand.push_back((int32_t)i);
+  }
+  uint32_t have_cost = 0, roots = 0;
+  std::vector<uint8_t> used(cand.size(), 0);
+  for (;;) {
+    int best = -1;
+    uint32_t best_gain = 0, best_cost = 0;
+    for (size_t c = 0; c < cand.size(); c++) {
+      if (used[c] || in[cand[c]]) continue;
+      trial = in;
+      const uint32_t gain = grow(trial, cand[c]);
+      const uint32_t cc = cost(trial);
+      if (cc > budget) continue;
+      // tables removed from every pass per extra register read per pass
+      const uint32_t dc = cc > have_cost ? cc - have_cost : 0;
+      if (gain < 2 * std::max<uint32_t>(1, dc)) continue;
+      if (best < 0 || gain * std::max<uint32_t>(1, best_cost) > best_gain * std::max<uint32_t>(1, dc)) {
+        best = (int)c;
+        best_gain = gain;
+        best_cost = dc;
+      }
+    }
+    if (best < 0) break;
+    used[best] = 1;
+    grow(in, cand[best]);
+    have_cost = cost(in);
+    roots++;
+  }
+  hoisted = in;
+  if (roots_out) *roots_out = have_cost;
+}
+
+}  // namespace lec

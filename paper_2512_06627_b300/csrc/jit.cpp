@@ -56,18 +56,21 @@ struct JitState {
 namespace {
 
 constexpr int kJitBlock = 128;
-constexpr int kCodegenVersion = 6;  // part of cached cubin names: bump when the kernel's interface changes
+constexpr int kCodegenVersion = 7;  // part of cached cubin names: bump when the kernel's interface changes
+constexpr uint32_t kHoistBudget = 128;  // hoisted values read per pass (registers); see jit_shape
+constexpr uint64_t kGrabsWanted = 4 * 148 * 8;  // four grabs per warp at 8 warps on each of 148 SMs
 constexpr uint32_t kMaxJitLive = 230;        // table live set that still fits the register file
 
 const char *kMask32[5] = {"0xAAAAAAAAu", "0xCCCCCCCCu", "0xF0F0F0F0u", "0xFF00FF00u", "0xFFFF0000u"};
 
-// Kernel prologue / epilogue shared by both code forms.  Chunks are handed
-// out 32 x rep at a time per warp from a counter (one grab ahead), so warps
-// that run faster take more and all finish together; a grab is rep passes of
-// 32 chunks, enough work to hide the counter's latency and keep its
-// contention low on small cones.  A warp stops at the end of the range, when
-// its next grab does not start below the current counterexample, or after
-// max_grabs grabs (the server bounds block lifetimes this way).
+// Kernel prologue / epilogue shared by the C++ code forms; the launch
+// contract is the PTX form's: a counter hands out grab numbers, grab q is
+// chunks [q*G, (q+1)*G) of the whole pattern space (G = 32 * rep, rep a power
+// of two) intersected with [cb, ce), taken one ahead, so warps that run
+// faster take more and all finish together.  A warp stops at the end of the
+// range, when its grab's first pattern is not below the current
+// counterexample, or after max_grabs grabs (the server bounds block lifetimes
+// this way).
 void emit_prologue(std::ostringstream &s) {
   s << "typedef unsigned int u32; typedef unsigned long long u64;\n"
        "extern \"C\" __global__ void __launch_bounds__("
@@ -75,19 +78,22 @@ void emit_prologue(std::ostringstream &s) {
     << ") es_jit(const u64 cb, const u64 ce, u64 *cex, u64 *evaluated, u64 *next, const u64 max_grabs,\n"
        "    const u64 rep) {\n"
        "  const unsigned lane = threadIdx.x & 31u;\n"
-       "  const u64 step = 32ull * rep;\n"
+       "  const u64 G = 32ull * rep, q0 = cb / G, qend = (ce + G - 1) / G;\n"
        "  u64 done = 0;\n"
-       "  u64 mine = __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(next, step) : 0ull, 0);\n"
+       "  u64 mine = __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(next, 1ull) : 0ull, 0);\n"
        "  u64 cur = __shfl_sync(0xffffffffu, lane == 0 ? *(volatile u64 *)cex : 0ull, 0);\n"
        "  for (u64 g = 1; ; g++) {\n"
-       "    const u64 wfirst = cb + mine;\n"
-       "    if (wfirst >= ce || wfirst * 32ull >= cur) break;\n"
+       "    const u64 q = q0 + mine;\n"
+       "    if (q >= qend) break;\n"
+       "    const u64 gfirst = q * G;\n"
+       "    if ((gfirst > cb ? gfirst : cb) * 32ull >= cur) break;\n"
        "    const bool more = g < max_grabs;\n"
-       "    const u64 ahead = (lane == 0 && more) ? atomicAdd(next, step) : ~0ull;\n"
+       "    const u64 ahead = (lane == 0 && more) ? atomicAdd(next, 1ull) : ~0ull;\n"
        "    const u64 nxt = lane == 0 ? *(volatile u64 *)cex : 0ull;\n"
        "    for (u64 r = 0; r < rep; r++) {\n"
-       "    const u64 base = wfirst + 32ull * r;\n"
+       "    const u64 base = gfirst + 32ull * r;\n"
        "    if (base >= ce) break;\n"
+       "    if (base + 32ull <= cb) continue;\n"
        "    const u64 c = base + lane;\n"
        "    const u32 clo = (u32)c, chi = (u32)(c >> 32);\n"
        "    (void)chi;\n";
@@ -97,12 +103,13 @@ void emit_epilogue(std::ostringstream &s, const std::string &outv, bool compl_, 
   const uint32_t vmask = n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << n)) - 1u);
   s << "    u32 out = (" << (compl_ ? "~" : "") << outv << ") & 0x" << std::hex << vmask << std::dec
     << "u;\n"
-       "    if (c >= ce) out = 0u;\n"
+       "    const bool inside = c >= cb && c < ce;\n"
+       "    if (!inside) out = 0u;\n"
        "    const unsigned bal = __ballot_sync(0xffffffffu, out != 0u);\n"
        "    if (bal) {\n"
        "      if ((int)lane == __ffs(bal) - 1) atomicMin(cex, c * 32ull + (u64)(__ffs(out) - 1));\n"
        "    }\n"
-       "    done += (c < ce) ? 1ull : 0ull;\n"
+       "    done += inside ? 1ull : 0ull;\n"
        "    }\n"
        "    mine = __shfl_sync(0xffffffffu, ahead, 0);\n"
        "    cur = __shfl_sync(0xffffffffu, nxt, 0);\n"
@@ -221,15 +228,49 @@ std::string gen_source(const Program &g, bool lut_form) {
   return lut_form && !g.lut.order.empty() ? gen_source_lut(g) : gen_source_and(g);
 }
 
-// PTX of the table form, written directly (no C++ front end): the same
-// kernel as gen_source_lut -- per-warp chunk grabs one ahead, PI words from
-// the chunk index, one lop3 per table, warp ballot and atomicMin -- with
-// virtual registers left to ptxas.  Constants (PI masks 0..4, folded tables)
-// are immediate operands.
-std::string gen_ptx_lut(const Program &g, int major, int minor) {
+// Passes per grab (a power of two) and the hoisting budget of a table-form
+// kernel.  Long grabs amortise hoisted tables (and the counter's atomic):
+// 16 to 32 passes, at least ~4k instructions per grab; but a small pattern
+// space keeps enough grabs to fill the GPU, which wins over both.
+// LEC_ES_JIT_REP / LEC_ES_JIT_HOIST override them (for measurements).
+void jit_shape(const Program &g, uint32_t *rep, uint32_t *budget) {
+  const uint32_t per = g.lut.count + 40;
+  uint32_t r = 16;
+  while (r < 32 && r * per < 4096) r <<= 1;
+  const uint64_t chunks = num_chunks(g.n);
+  while (r > 1 && chunks / (32ull * r) < kGrabsWanted) r >>= 1;
+  uint32_t h = kHoistBudget;
+  if (const char *e = getenv("LEC_ES_JIT_REP")) r = (uint32_t)std::max(1, atoi(e));
+  if (const char *e = getenv("LEC_ES_JIT_HOIST")) h = (uint32_t)std::max(0, atoi(e));
+  uint32_t p2 = 1;
+  while (p2 < r && p2 < 1024) p2 <<= 1;
+  *rep = p2;
+  *budget = h;
+}
+
+// PTX of the table form, written directly (no C++ front end), with virtual
+// registers left to ptxas; constants (PI masks 0..4, folded tables) are
+// immediate operands.
+//
+// Grabs: the counter hands out grab numbers; grab q is chunks [q*G, (q+1)*G)
+// of the whole pattern space, G = 32 * REP, intersected with [cb, ce).  In a
+// chunk index, bits 0..4 are the lane (support PIs 5..9, fixed per thread),
+// bits 5..log2(G)-1 the pass (PIs that change from pass to pass) and the
+// rest the grab's.  Tables chosen by plan_hoist (no pass PI among their
+// inputs) are evaluated once per grab, the others once per pass.  A warp
+// takes its next grab one ahead, stops at the end of the range, when its
+// grab's first pattern is not below the current counterexample, or after
+// max_grabs grabs.
+std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, uint32_t budget) {
   const LutProgram &lp = g.lut;
   const uint32_t NA = lp.na, NP = lp.np;
   const size_t NV = NA + NP + 1;
+  uint32_t lgG = 5;
+  while ((1u << (lgG - 5)) < REP) lgG++;
+  const uint32_t vary_lo = 10, vary_hi = std::min<uint32_t>(NP, 5 + lgG);  // pass PIs [vary_lo, vary_hi)
+  std::vector<uint8_t> hoisted;
+  uint32_t roots = 0;
+  plan_hoist(lp, vary_lo, std::max(vary_lo, vary_hi), budget, hoisted, &roots);
   std::vector<int8_t> isconst(NV, 0);
   std::vector<uint32_t> cval(NV, 0);
   static const uint32_t mask[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
@@ -258,15 +299,18 @@ std::string gen_ptx_lut(const Program &g, int major, int minor) {
   s << ".version 9.0\n.target sm_" << major << minor << "a\n.address_size 64\n\n"
     << ".visible .entry es_jit(.param .u64 p_cb, .param .u64 p_ce, .param .u64 p_cex, .param .u64 p_ev,\n"
     << "    .param .u64 p_next, .param .u64 p_maxg, .param .u64 p_rep)\n.maxntid " << kJitBlock << ", 1, 1\n{\n"
-    << "  .reg .pred %p<10>;\n  .reg .b32 %t<24>;\n  .reg .b64 %d<32>;\n"
+    << "  .reg .pred %p<12>;\n  .reg .b32 %t<24>;\n  .reg .b64 %d<40>;\n"
     << "  .reg .b32 %v<" << (NA + 1) << ">;\n  .reg .b32 %q<" << (NP + 1) << ">;\n";
-  // parameters, lane, first grab, first counterexample poll
+  // parameters; grab range [d8, d9) of grab numbers; lane; first grab; first
+  // counterexample poll
+  snprintf(buf, sizeof(buf), "  shr.u64 %%d8, %%d1, %u;\n  add.u64 %%d9, %%d2, %u;\n  shr.u64 %%d9, %%d9, %u;\n", lgG,
+           (1u << lgG) - 1u, lgG);
   s << "  ld.param.u64 %d1, [p_cb];\n  ld.param.u64 %d2, [p_ce];\n  ld.param.u64 %d3, [p_cex];\n"
        "  ld.param.u64 %d4, [p_ev];\n  ld.param.u64 %d5, [p_next];\n  ld.param.u64 %d6, [p_maxg];\n"
-       "  ld.param.u64 %d7, [p_rep];\n  shl.b64 %d7, %d7, 5;\n"
        "  cvta.to.global.u64 %d3, %d3;\n  cvta.to.global.u64 %d4, %d4;\n  cvta.to.global.u64 %d5, %d5;\n"
-       "  mov.u32 %t1, %tid.x;\n  and.b32 %t2, %t1, 31;\n  setp.eq.u32 %p1, %t2, 0;\n"
-       "  mov.u64 %d10, 0;\n  mov.u64 %d11, 0;\n  @%p1 atom.global.add.u64 %d11, [%d5], %d7;\n"
+    << buf
+    << "  mov.u32 %t1, %tid.x;\n  and.b32 %t2, %t1, 31;\n  setp.eq.u32 %p1, %t2, 0;\n"
+       "  mov.u64 %d10, 0;\n  mov.u64 %d11, 0;\n  @%p1 atom.global.add.u64 %d11, [%d5], 1;\n"
        "  mov.b64 {%t3, %t4}, %d11;\n  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n"
        "  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n  mov.b64 %d11, {%t3, %t4};\n"
        "  mov.u64 %d12, 0;\n  @%p1 ld.volatile.global.u64 %d12, [%d3];\n  mov.b64 {%t3, %t4}, %d12;\n"
@@ -280,57 +324,68 @@ std::string gen_ptx_lut(const Program &g, int major, int minor) {
     name[v] = buf;
   }
   for (uint32_t k = 5; k < NP; k++) name[NA + k] = "%q" + std::to_string(k);
-  // grabs and passes are multiples of 32 chunks, so the low five bits of a
-  // lane's chunk index are those of cb + lane: PIs 5..9 are fixed per lane,
-  // computed here
-  s << "  cvt.u32.u64 %t17, %d1;\n  add.u32 %t17, %t17, %t2;\n";
-  std::vector<uint8_t> pi_done(NP, 0);
-  for (uint32_t k = 5; k < NP && k < 10; k++) {
-    snprintf(buf, sizeof(buf), "  bfe.s32 %%q%u, %%t17, %u, 1;\n", k, k - 5);
-    s << buf;
-    pi_done[k] = 1;
-  }
-  s << "$LOOP:\n"
-       "  add.u64 %d14, %d1, %d11;\n  setp.ge.u64 %p2, %d14, %d2;\n  @%p2 bra $DONE;\n"
-       "  shl.b64 %d15, %d14, 5;\n  setp.ge.u64 %p2, %d15, %d12;\n  @%p2 bra $DONE;\n"
-       "  setp.lt.u64 %p3, %d13, %d6;\n  and.pred %p4, %p1, %p3;\n  mov.u64 %d16, -1;\n"
-       "  @%p4 atom.global.add.u64 %d16, [%d5], %d7;\n  mov.u64 %d17, 0;\n"
-       "  @%p1 ld.volatile.global.u64 %d17, [%d3];\n"
-       // passes of 32 chunks from d27 up to the grab's end d28
-       "  mov.u64 %d27, %d14;\n  add.u64 %d28, %d14, %d7;\n"
-       "$PASS:\n  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra $GRABEND;\n  add.u64 %d19, %d27, %d18;\n"
-       "  cvt.u32.u64 %t5, %d19;\n  shr.u64 %d20, %d19, 32;\n  cvt.u32.u64 %t6, %d20;\n";
-  std::vector<uint8_t> pi_loop(NP, 0);
-  auto operand = [&](int32_t id) -> std::string {
-    if (id < 0) return "0";
-    if (isconst[id]) return name[id];
-    if (id >= (int32_t)NA && id < (int32_t)(NA + NP)) {
-      const uint32_t k = (uint32_t)(id - NA);
-      if (!pi_done[k] && !pi_loop[k]) {  // all ones iff bit (k-5) of the chunk index is set
-        const uint32_t j = k - 5;
-        snprintf(buf, sizeof(buf), "  bfe.s32 %%q%u, %%t%d, %u, 1;\n", k, j < 32 ? 5 : 6, j < 32 ? j : j - 32);
-        s << buf;
-        pi_loop[k] = 1;
-      }
-    }
-    return name[id];
-  };
+  // which PIs are read at all
+  std::vector<uint8_t> pi_used(NP, 0);
   for (const auto &l : lp.order) {
     if (isconst[l.node]) continue;
+    for (int k = 0; k < l.n; k++)
+      if (l.leaf[k] >= (int32_t)NA && l.leaf[k] < (int32_t)(NA + NP)) pi_used[l.leaf[k] - NA] = 1;
+  }
+  if (lp.root >= (int64_t)NA && lp.root < (int64_t)(NA + NP)) pi_used[lp.root - NA] = 1;
+  // PIs 5..9: bits 0..4 of the chunk index are the lane
+  for (uint32_t k = 5; k < NP && k < 10; k++) {
+    snprintf(buf, sizeof(buf), "  bfe.s32 %%q%u, %%t2, %u, 1;\n", k, k - 5);
+    if (pi_used[k]) s << buf;
+  }
+  // PI k >= 5 from bit (k - 5) of the chunk index in (t5: low, t6: high word)
+  auto emit_pi = [&](uint32_t k) {
+    const uint32_t j = k - 5;
+    snprintf(buf, sizeof(buf), "  bfe.s32 %%q%u, %%t%d, %u, 1;\n", k, j < 32 ? 5 : 6, j < 32 ? j : j - 32);
+    s << buf;
+  };
+  auto emit_table = [&](const LutCover::Lut &l) {
     name[l.node] = "%v" + std::to_string(l.node);
-    const std::string x0 = operand(l.leaf[0]), x1 = operand(l.n > 1 ? l.leaf[1] : -1),
-                      x2 = operand(l.n > 2 ? l.leaf[2] : -1);
+    auto op = [&](int32_t id) -> std::string { return id < 0 ? std::string("0") : name[id]; };
+    const std::string x0 = op(l.leaf[0]), x1 = op(l.n > 1 ? l.leaf[1] : -1), x2 = op(l.n > 2 ? l.leaf[2] : -1);
     // lop3 operands a, b, c carry the patterns 0xF0, 0xCC, 0xAA: (x2, x1, x0)
     snprintf(buf, sizeof(buf), "  lop3.b32 %s, %s, %s, %s, 0x%02x;\n", name[l.node].c_str(), x2.c_str(), x1.c_str(),
              x0.c_str(), l.tt);
     s << buf;
-  }
+  };
+  // grab loop: d14 grab number, d15 its first chunk
+  s << "$LOOP:\n"
+       "  add.u64 %d14, %d8, %d11;\n  setp.ge.u64 %p2, %d14, %d9;\n  @%p2 bra $DONE;\n";
+  snprintf(buf, sizeof(buf), "  shl.b64 %%d15, %%d14, %u;\n", lgG);
+  s << buf
+    << "  max.u64 %d20, %d15, %d1;\n  shl.b64 %d21, %d20, 5;\n  setp.ge.u64 %p2, %d21, %d12;\n  @%p2 bra $DONE;\n"
+       "  setp.lt.u64 %p3, %d13, %d6;\n  and.pred %p4, %p1, %p3;\n  mov.u64 %d16, -1;\n"
+       "  @%p4 atom.global.add.u64 %d16, [%d5], 1;\n  mov.u64 %d17, 0;\n"
+       "  @%p1 ld.volatile.global.u64 %d17, [%d3];\n"
+       "  cvt.u32.u64 %t5, %d15;\n  shr.u64 %d20, %d15, 32;\n  cvt.u32.u64 %t6, %d20;\n";
+  // the grab's PIs, then the hoisted tables
+  for (uint32_t k = std::max(10u, vary_hi); k < NP; k++)
+    if (pi_used[k]) emit_pi(k);
+  for (size_t i = 0; i < lp.order.size(); i++)
+    if (hoisted[i] && !isconst[lp.order[i].node]) emit_table(lp.order[i]);
+  // passes of 32 chunks from d27 up to the grab's end d28
+  snprintf(buf, sizeof(buf), "  mov.u64 %%d27, %%d15;\n  add.u64 %%d28, %%d15, %u;\n", 1u << lgG);
+  s << buf
+    << "$PASS:\n  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra $GRABEND;\n"
+       "  add.u64 %d22, %d27, 32;\n  setp.le.u64 %p10, %d22, %d1;\n  @%p10 bra $NEXTPASS;\n"
+       "  add.u64 %d19, %d27, %d18;\n"
+       "  cvt.u32.u64 %t5, %d19;\n  shr.u64 %d20, %d19, 32;\n  cvt.u32.u64 %t6, %d20;\n";
+  for (uint32_t k = vary_lo; k < vary_hi; k++)
+    if (pi_used[k]) emit_pi(k);
+  for (size_t i = 0; i < lp.order.size(); i++)
+    if (!hoisted[i] && !isconst[lp.order[i].node]) emit_table(lp.order[i]);
   const uint32_t vmask = g.n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << g.n)) - 1u);
-  const std::string root = lp.root < 0 ? std::string("0") : operand((int32_t)lp.root);
+  const std::string root = lp.root < 0 ? std::string("0") : name[lp.root];
   snprintf(buf, sizeof(buf), "  xor.b32 %%t7, %s, 0x%08x;\n  and.b32 %%t7, %%t7, 0x%08x;\n", root.c_str(),
            g.out_compl ? 0xFFFFFFFFu : 0u, vmask);
   s << buf;
-  s << "  setp.ge.u64 %p5, %d19, %d2;\n  @%p5 mov.b32 %t7, 0;\n  setp.ne.u32 %p6, %t7, 0;\n"
+  // chunks outside [cb, ce) neither fail nor count
+  s << "  setp.ge.u64 %p5, %d19, %d2;\n  setp.lt.u64 %p11, %d19, %d1;\n  or.pred %p5, %p5, %p11;\n"
+       "  @%p5 mov.b32 %t7, 0;\n  setp.ne.u32 %p6, %t7, 0;\n"
        "  vote.sync.ballot.b32 %t8, %p6, -1;\n  setp.eq.u32 %p7, %t8, 0;\n  @%p7 bra $NOFAIL;\n"
        "  neg.s32 %t9, %t8;\n  and.b32 %t9, %t9, %t8;\n  bfind.u32 %t10, %t9;\n"
        "  setp.ne.u32 %p7, %t10, %t2;\n  @%p7 bra $NOFAIL;\n"
@@ -338,7 +393,8 @@ std::string gen_ptx_lut(const Program &g, int major, int minor) {
        "  cvt.u64.u32 %d21, %t12;\n  shl.b64 %d22, %d19, 5;\n  add.u64 %d22, %d22, %d21;\n"
        "  atom.global.min.u64 %d23, [%d3], %d22;\n"
        "$NOFAIL:\n"
-       "  setp.lt.u64 %p5, %d19, %d2;\n  selp.u64 %d24, 1, 0, %p5;\n  add.u64 %d10, %d10, %d24;\n"
+       "  selp.u64 %d24, 0, 1, %p5;\n  add.u64 %d10, %d10, %d24;\n"
+       "$NEXTPASS:\n"
        "  add.u64 %d27, %d27, 32;\n  setp.lt.u64 %p9, %d27, %d28;\n  @%p9 bra $PASS;\n"
        "$GRABEND:\n"
        "  mov.b64 {%t3, %t4}, %d16;\n  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n"
@@ -356,6 +412,9 @@ std::string gen_ptx_lut(const Program &g, int major, int minor) {
   }
   s << "  setp.ne.u64 %p8, %d10, 0;\n  and.pred %p8, %p8, %p1;\n  shl.b64 %d26, %d10, 5;\n"
        "  @%p8 red.global.add.u64 [%d4], %d26;\n  ret;\n}\n";
+  if (getenv("LEC_ES_JIT_LOG"))
+    fprintf(stderr, "lec_es JIT %016llx: %u tables, rep %u, %zu hoisted (%u roots)\n", (unsigned long long)g.hash,
+            lp.count, REP, (size_t)std::count(hoisted.begin(), hoisted.end(), (uint8_t)1), roots);
   return s.str();
 }
 
@@ -404,8 +463,23 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
   // LEC_ES_JIT_NVRTC=1 compiles the table form from CUDA C++ through NVRTC
   // instead (same tables, for comparing the two compilation paths)
   static const bool via_nvrtc = getenv("LEC_ES_JIT_NVRTC") != nullptr;
-  if (lut_form && !g.lut.order.empty() && !via_nvrtc)
-    return compile_ptx(gen_ptx_lut(g, major, minor), major, minor, cubin, log);
+  if (lut_form && !g.lut.order.empty() && !via_nvrtc) {
+    // hoisted values live in registers across the passes: if ptxas has to
+    // spill, halve the budget and build again
+    uint32_t rep = 0, budget = 0;
+    jit_shape(g, &rep, &budget);
+    for (;;) {
+      std::string lg;
+      const int rc = compile_ptx(gen_ptx_lut(g, major, minor, rep, budget), major, minor, cubin, lg);
+      const bool spills = rc == LEC_ES_OK && lg.find(" 0 bytes spill stores") == std::string::npos &&
+                          lg.find("spill stores") != std::string::npos;
+      if (rc != LEC_ES_OK || !spills || budget == 0) {
+        log += lg;
+        return rc;
+      }
+      budget /= 2;
+    }
+  }
   return compile_cubin(gen_source(g, lut_form), major, minor, cubin, log);
 }
 
@@ -490,10 +564,12 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   std::string path;
   if (!c->jit_dir.empty()) {
     mkdir(c->jit_dir.c_str(), 0755);
-    char name[64];
-    snprintf(name, sizeof(name), "/es_v%d_%016llx_%s%s_sm%d%d.cubin", kCodegenVersion,
-             (unsigned long long)g.hash, lut_form ? "lut" : "and", getenv("LEC_ES_JIT_NVRTC") ? "_nvrtc" : "",
-             c->cc_major, c->cc_minor);
+    char name[96];
+    uint32_t rep = 0, budget = 0;
+    jit_shape(g, &rep, &budget);
+    snprintf(name, sizeof(name), "/es_v%d_%016llx_%s%s_r%u_h%u_sm%d%d.cubin", kCodegenVersion,
+             (unsigned long long)g.hash, lut_form ? "lut" : "and", getenv("LEC_ES_JIT_NVRTC") ? "_nvrtc" : "", rep,
+             budget, c->cc_major, c->cc_minor);
     path = c->jit_dir + name;
   }
   double nvrtc_ms = 0;
@@ -529,6 +605,11 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   k->num_luts = g.lut.count;
   k->lut_live = g.lut.live;
   k->work_per_chunk = lut_form ? g.lut.count : (uint32_t)g.recs.size();
+  if (lut_form && !g.lut.order.empty() && !getenv("LEC_ES_JIT_NVRTC")) {  // the PTX form: passes per grab compiled in
+    uint32_t rep = 0, budget = 0;
+    jit_shape(g, &rep, &budget);
+    k->rep_fixed = rep;
+  }
   k->load_ms = now_ms() - tl;
   k->nvrtc_ms = nvrtc_ms;
   k->compile_ms = now_ms() - t0;
@@ -651,14 +732,19 @@ JitKernel *jit_lookup_or_schedule(lec_es_ctx *c, const Program &g) {
   return nullptr;
 }
 
+// Passes per grab: a power of two, compiled into the PTX form; otherwise
+// ~4k instructions per warp per grab, but at least four grabs per warp of
+// the grid so the counter still balances the load.
 uint64_t jit_reps(const JitKernel *k, uint64_t chunks, uint64_t grid) {
-  // ~4k instructions per warp per grab, but at least four grabs per warp of
-  // the grid so the counter still balances the load
+  if (k->rep_fixed) return k->rep_fixed;
   const uint64_t per_chunk = std::max<uint64_t>(1, k->work_per_chunk) + 40;
   uint64_t rep = (4096 + per_chunk - 1) / per_chunk;
   const uint64_t warps = std::max<uint64_t>(1, grid * (uint64_t)(k->block / 32));
   rep = std::min<uint64_t>(rep, chunks / (32ull * 4ull * warps));
-  return std::max<uint64_t>(1, std::min<uint64_t>(rep, 32));
+  rep = std::max<uint64_t>(1, std::min<uint64_t>(rep, 32));
+  uint64_t p2 = 1;
+  while (p2 * 2 <= rep) p2 <<= 1;
+  return p2;
 }
 
 void jit_geometry(const JitKernel *k, uint64_t chunks, int sm_count, uint64_t *grid, uint64_t *rep) {
@@ -670,6 +756,14 @@ void jit_geometry(const JitKernel *k, uint64_t chunks, int sm_count, uint64_t *g
   const uint64_t wpb = (uint64_t)std::max(1, k->block / 32);
   const uint64_t w_full = (uint64_t)sm_count * (uint64_t)k->blocks_per_sm * wpb;
   const uint64_t w_min = std::min<uint64_t>(w_full, (uint64_t)sm_count * 8ull);
+  if (k->rep_fixed) {
+    const uint64_t r = k->rep_fixed;
+    const uint64_t grabs = std::max<uint64_t>(1, (chunks + 32ull * r - 1) / (32ull * r)) + 1;  // + an unaligned end
+    const uint64_t w = std::min<uint64_t>(w_full, std::max(std::min(w_min, grabs), grabs / 4));
+    *rep = r;
+    *grid = std::max<uint64_t>(1, (w + wpb - 1) / wpb);
+    return;
+  }
   const uint64_t per_chunk = std::max<uint64_t>(1, k->work_per_chunk) + 40;
   uint64_t r = std::min<uint64_t>(32, (4096 + per_chunk - 1) / per_chunk);
   uint64_t grabs = chunks / (32ull * r);
@@ -679,7 +773,9 @@ void jit_geometry(const JitKernel *k, uint64_t chunks, int sm_count, uint64_t *g
     grabs = (chunks + 32ull * r - 1) / (32ull * r);
     w = std::min<uint64_t>(w_full, std::max<uint64_t>(1, grabs / 4));
   }
-  *rep = r;
+  uint64_t p2 = 1;  // grabs are aligned to 32 * rep chunks: a power of two
+  while (p2 * 2 <= r) p2 <<= 1;
+  *rep = p2;
   *grid = std::max<uint64_t>(1, (w + wpb - 1) / wpb);
 }
 

@@ -239,3 +239,18 @@ def test_jit_compiles_for_sm103a_without_spills():
         regs = int(_re.search(r"Used (\d+) registers", log).group(1))
         assert regs <= 255
         assert "0 bytes spill stores" in log, log
+
+
+@pytest.mark.parametrize("rep,hoist", [("4", "0"), ("16", "64"), ("32", "128")])
+def test_jit_grab_shapes_and_hoisting_compile_without_spills(rep, hoist, monkeypatch):
+    """Passes per grab and hoisted tables (values kept across the passes of
+    a grab) change the register demand; every shape still compiles for
+    sm_103a with all values in registers."""
+    import re as _re
+    monkeypatch.setenv("LEC_ES_JIT_REP", rep)
+    monkeypatch.setenv("LEC_ES_JIT_HOIST", hoist)
+    for aig in (C.config2_mult12(), C.config3_mult16()):
+        log, nbytes = L.lec_es_jit_compile(L.miter_of(aig), 10, 3)
+        assert nbytes > 0
+        assert int(_re.search(r"Used (\d+) registers", log).group(1)) <= 255
+        assert "0 bytes spill stores" in log, log

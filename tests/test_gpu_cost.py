@@ -47,8 +47,9 @@ def test_model_learns_from_full_equivalent_runs_only():
 
 def test_predictions_track_measured_times():
     """Learn from a few product-bit miters, predict others (different widths
-    and bits) within 40% on both tiers; the model is the paper's form plus a
-    launch and a one-pass term, fitted in relative error."""
+    and bits) within 40% on both tiers, or 20 us for launch-sized runs; the
+    model is the paper's form plus a launch and a one-pass term, fitted in
+    relative error."""
     c = make_ctx(arena_bytes=512 << 20)
     try:
         pm = C.ProductBitMiters(seed=5)
@@ -58,14 +59,14 @@ def test_predictions_track_measured_times():
         for w, bit in ((10, 15), (12, 12), (14, 20)):
             for tier in (L.TIER_INTERP, L.TIER_JIT):
                 _run(c, miter(w, bit), tier)
-        held = [(11, 16), (13, 19), (14, 27)]
+        held = [(11, 16), (13, 19), (14, 27), (15, 22)]
         for w, bit in held:
             m = miter(w, bit)
             p = L.lec_es_cost_predict(c, m, 16)
             for tier, pred in ((L.TIER_INTERP, p.interp_ms), (L.TIER_JIT, p.jit_ms)):
                 r = _run(c, m, tier)
                 assert r.verdict == L.EQUIVALENT
-                assert pred == pytest.approx(r.device_ms, rel=0.4), (w, bit, tier, pred, r.device_ms)
+                assert pred == pytest.approx(r.device_ms, rel=0.4, abs=0.02), (w, bit, tier, pred, r.device_ms)
     finally:
         L.lec_es_destroy(c)
 

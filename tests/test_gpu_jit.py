@@ -138,3 +138,33 @@ def test_cached_kernel_skips_table_cover():
         assert r.verdict == L.EQUIVALENT
     finally:
         L.lec_es_destroy(c)
+
+
+@pytest.mark.parametrize("rep,hoist", [("4", "0"), ("16", "64"), ("32", "128"), ("8", "16")])
+def test_passes_per_grab_and_hoisted_tables_keep_results(rep, hoist, monkeypatch):
+    """Every grab shape and hoisting budget gives the oracle's result,
+    including word ranges that start and end off the grab alignment."""
+    monkeypatch.setenv("LEC_ES_JIT_REP", rep)
+    monkeypatch.setenv("LEC_ES_JIT_HOIST", hoist)
+    c = make_ctx(arena_bytes=64 << 20)
+    try:
+        rng = np.random.default_rng(700 + int(rep) + int(hoist))
+        cases = [(C.config2_mult12(mutant_seed=1), None), (C.config2_mult12(), None)]
+        for _ in range(4):
+            a = random_aig(rng, int(rng.integers(10, 16)), int(rng.integers(40, 160)))
+            cases.append((a, None))
+        for aig, _ in cases:
+            out = aig.outputs[0]
+            m = L.Miter(aig.num_pis, aig.flat_fanins(), out)
+            r = L.lec_es_check_ex(c, m, L.options(tier=L.TIER_JIT))
+            assert r.cex_or_none == oracle_cex(aig, out)
+            W = 1 << max(0, r.support_n - 6)
+            for wb, we in ((1, W), (W // 3 + 1, W - W // 5), (0, max(1, W // 7))):
+                if wb < we:
+                    g = L.lec_es_check_ex(c, m, L.options(wb, we, L.TIER_JIT))
+                    assert g.cex_or_none == oracle_cex(aig, out, wb, we), (wb, we)
+        mm = C.config3_mult16(mutant=True)
+        r = L.lec_es_check_ex(c, L.miter_of(mm), L.options((1 << 26) - 37, 1 << 26, L.TIER_JIT))
+        assert r.cex == (1 << 32) - 1
+    finally:
+        L.lec_es_destroy(c)
