@@ -60,6 +60,8 @@ struct JitKernel {
   uint32_t lut_live = 0;
   uint32_t work_per_chunk = 0;  // straight-line instructions per 32-pattern chunk (about)
   uint32_t rep_fixed = 0;       // passes per grab compiled into the kernel (0: a launch parameter)
+  uint64_t pass_bits = 0;       // chunk-index bits of the pass PIs (0: contiguous grabs of 32 * rep chunks)
+  uint32_t chunk_bits = 0;      // bits of the chunk index (support PIs - 5)
 };
 struct JitState;
 struct Server;
@@ -119,6 +121,8 @@ uint32_t jit_auto_tier(lec_es_ctx *c, const Program &g, uint64_t chunks);
 int jit_prepare(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt);
 // Passes of 32 chunks per grab for a launch of `grid` blocks over `chunks`.
 uint64_t jit_reps(const JitKernel *k, uint64_t chunks, uint64_t grid);
+// Grab numbers [q0, qend) covering chunks [cb, ce) for the kernel's layout.
+void jit_grab_range(const JitKernel *k, uint64_t rep, uint64_t cb, uint64_t ce, uint64_t *q0, uint64_t *qend);
 // Grid and passes per grab for a launch over `chunks` chunks.
 void jit_geometry(const JitKernel *k, uint64_t chunks, int sm_count, uint64_t *grid, uint64_t *rep);
 int jit_launch(lec_es_ctx *c, lec_es_plan *p, uint64_t chunk_begin, uint64_t chunk_end, int grid,

@@ -83,10 +83,13 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
                     const KernelProbe *probe = nullptr);
 
 // Tables of the specialised kernel evaluated once per grab (hoist.cpp):
-// hoisted[i] for lp.order[i]; support PIs [vary_lo, vary_hi) change from pass
-// to pass; at most `budget` hoisted values are read by per-pass code.
-void plan_hoist(const LutProgram &lp, uint32_t vary_lo, uint32_t vary_hi, uint32_t budget,
-                std::vector<uint8_t> &hoisted, uint32_t *roots);
+// hoisted[i] for lp.order[i]; the support PIs in the mask pass_pis change
+// from pass to pass; at most `budget` hoisted values are read by per-pass
+// code.
+void plan_hoist(const LutProgram &lp, uint64_t pass_pis, uint32_t budget, std::vector<uint8_t> &hoisted,
+                uint32_t *roots);
+// The k support PIs (index >= 10) that the fewest tables depend on, as a mask.
+uint64_t least_influential_pis(const LutProgram &lp, uint32_t k);
 
 // Words of 64 patterns for a support of n PIs.
 inline uint64_t num_words(uint32_t n) { return n <= 6 ? 1ull : (1ull << (n - 6)); }

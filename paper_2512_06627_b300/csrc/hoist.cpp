@@ -22,8 +22,8 @@
 
 namespace lec {
 
-void plan_hoist(const LutProgram &lp, uint32_t vary_lo, uint32_t vary_hi, uint32_t budget,
-                std::vector<uint8_t> &hoisted, uint32_t *roots_out) {
+void plan_hoist(const LutProgram &lp, uint64_t pass_pis, uint32_t budget, std::vector<uint8_t> &hoisted,
+                uint32_t *roots_out) {
   const uint32_t NA = lp.na, NP = lp.np;
   const size_t NL = lp.order.size();
   hoisted.assign(NL, 0);
@@ -38,7 +38,7 @@ void plan_hoist(const LutProgram &lp, uint32_t vary_lo, uint32_t vary_hi, uint32
     if (v < 0) return true;
     if ((uint32_t)v >= NA) {
       const uint32_t k = (uint32_t)v - NA;
-      return k >= NP || k < vary_lo || k >= vary_hi;  // k == NP is the constant
+      return k >= NP || !((pass_pis >> k) & 1u);  // k == NP is the constant
     }
     return pos[v] >= 0 && inv[pos[v]];
   };
@@ -123,6 +123,35 @@ void plan_hoist(const LutProgram &lp, uint32_t vary_lo, uint32_t vary_hi, uint32
   }
   hoisted = in;
   if (roots_out) *roots_out = have_cost;
+}
+
+uint64_t least_influential_pis(const LutProgram &lp, uint32_t k) {
+  const uint32_t NA = lp.na, NP = lp.np;
+  const size_t NL = lp.order.size();
+  if (NP <= 10 || k == 0) return 0;
+  std::vector<int32_t> pos(NA, -1);
+  for (size_t i = 0; i < NL; i++) pos[lp.order[i].node] = (int32_t)i;
+  std::vector<uint64_t> dep(NL, 0);  // support PIs each table depends on
+  for (size_t i = 0; i < NL; i++)
+    for (int q = 0; q < lp.order[i].n; q++) {
+      const int32_t v = lp.order[i].leaf[q];
+      if (v < 0) continue;
+      if ((uint32_t)v >= NA) {
+        if ((uint32_t)v - NA < NP && (uint32_t)v - NA < 64) dep[i] |= 1ull << ((uint32_t)v - NA);
+      } else if (pos[v] >= 0) {
+        dep[i] |= dep[pos[v]];
+      }
+    }
+  std::vector<std::pair<uint64_t, uint32_t>> infl;
+  for (uint32_t p = 10; p < NP && p < 64; p++) {
+    uint64_t c = 0;
+    for (size_t i = 0; i < NL; i++) c += (dep[i] >> p) & 1u;
+    infl.push_back({c, p});
+  }
+  std::sort(infl.begin(), infl.end());
+  uint64_t m = 0;
+  for (uint32_t i = 0; i < k && i < infl.size(); i++) m |= 1ull << infl[i].second;
+  return m;
 }
 
 }  // namespace lec

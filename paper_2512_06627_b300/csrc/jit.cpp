@@ -56,8 +56,8 @@ struct JitState {
 namespace {
 
 constexpr int kJitBlock = 128;
-constexpr int kCodegenVersion = 7;  // part of cached cubin names: bump when the kernel's interface changes
-constexpr uint32_t kHoistBudget = 128;  // hoisted values read per pass (registers); see jit_shape
+constexpr int kCodegenVersion = 8;  // part of cached cubin names: bump when the kernel's interface changes
+constexpr uint32_t kHoistBudget = 128;  // hoisted values read per pass (registers); see jit_layout
 constexpr uint64_t kGrabsWanted = 4 * 148 * 8;  // four grabs per warp at 8 warps on each of 148 SMs
 constexpr uint32_t kMaxJitLive = 230;        // table live set that still fits the register file
 
@@ -76,7 +76,8 @@ void emit_prologue(std::ostringstream &s) {
        "extern \"C\" __global__ void __launch_bounds__("
     << kJitBlock
     << ") es_jit(const u64 cb, const u64 ce, u64 *cex, u64 *evaluated, u64 *next, const u64 max_grabs,\n"
-       "    const u64 rep) {\n"
+       "    const u64 rep, const u64 q0_host, const u64 qend_host) {\n"
+       "  (void)q0_host; (void)qend_host;\n"
        "  const unsigned lane = threadIdx.x & 31u;\n"
        "  const u64 G = 32ull * rep, q0 = cb / G, qend = (ce + G - 1) / G;\n"
        "  u64 done = 0;\n"
@@ -228,12 +229,16 @@ std::string gen_source(const Program &g, bool lut_form) {
   return lut_form && !g.lut.order.empty() ? gen_source_lut(g) : gen_source_and(g);
 }
 
-// Passes per grab (a power of two) and the hoisting budget of a table-form
-// kernel.  Long grabs amortise hoisted tables (and the counter's atomic):
-// 16 to 32 passes, at least ~4k instructions per grab; but a small pattern
-// space keeps enough grabs to fill the GPU, which wins over both.
-// LEC_ES_JIT_REP / LEC_ES_JIT_HOIST override them (for measurements).
-void jit_shape(const Program &g, uint32_t *rep, uint32_t *budget) {
+// Passes per grab (a power of two), the hoisting budget and the pass PIs of
+// a table-form kernel.  Long grabs amortise hoisted tables (and the
+// counter's atomic): 16 to 32 passes, at least ~4k instructions per grab; but
+// a small pattern space keeps enough grabs to fill the GPU, which wins over
+// both.  The pass PIs are the support PIs (index >= 10) the fewest tables
+// depend on, so the most tables are the same in every pass of a grab.
+// LEC_ES_JIT_REP / LEC_ES_JIT_HOIST override passes and budget, and
+// LEC_ES_JIT_LOWPASS=1 takes PIs 10, 11, ... as the pass PIs (for
+// measurements).
+void jit_layout(const Program &g, uint32_t *rep, uint32_t *budget, uint64_t *pass_pis) {
   const uint32_t per = g.lut.count + 40;
   uint32_t r = 16;
   while (r < 32 && r * per < 4096) r <<= 1;
@@ -242,35 +247,61 @@ void jit_shape(const Program &g, uint32_t *rep, uint32_t *budget) {
   uint32_t h = kHoistBudget;
   if (const char *e = getenv("LEC_ES_JIT_REP")) r = (uint32_t)std::max(1, atoi(e));
   if (const char *e = getenv("LEC_ES_JIT_HOIST")) h = (uint32_t)std::max(0, atoi(e));
-  uint32_t p2 = 1;
-  while (p2 < r && p2 < 1024) p2 <<= 1;
-  *rep = p2;
+  uint32_t npass = 0;
+  while ((1u << (npass + 1)) <= r && npass < 10) npass++;
+  npass = std::min<uint32_t>(npass, g.n > 10 ? g.n - 10 : 0);  // pass PIs are support PIs 10..n-1
+  uint64_t m = 0;
+  if (getenv("LEC_ES_JIT_LOWPASS")) {
+    for (uint32_t k = 10; k < 10 + npass; k++) m |= 1ull << k;
+  } else {
+    m = least_influential_pis(g.lut, npass);
+  }
+  *rep = 1u << npass;
   *budget = h;
+  *pass_pis = m;
+}
+
+// Runs of consecutive chunk-index bits: (first bit, source bit, length).
+struct BitRun {
+  uint32_t at, from, len;
+};
+std::vector<BitRun> bit_runs(const std::vector<uint32_t> &pos) {  // pos ascending
+  std::vector<BitRun> r;
+  for (uint32_t i = 0; i < pos.size(); i++) {
+    if (!r.empty() && r.back().at + r.back().len == pos[i]) r.back().len++;
+    else r.push_back({pos[i], i, 1});
+  }
+  return r;
 }
 
 // PTX of the table form, written directly (no C++ front end), with virtual
 // registers left to ptxas; constants (PI masks 0..4, folded tables) are
 // immediate operands.
 //
-// Grabs: the counter hands out grab numbers; grab q is chunks [q*G, (q+1)*G)
-// of the whole pattern space, G = 32 * REP, intersected with [cb, ce).  In a
-// chunk index, bits 0..4 are the lane (support PIs 5..9, fixed per thread),
-// bits 5..log2(G)-1 the pass (PIs that change from pass to pass) and the
-// rest the grab's.  Tables chosen by plan_hoist (no pass PI among their
-// inputs) are evaluated once per grab, the others once per pass.  A warp
-// takes its next grab one ahead, stops at the end of the range, when its
-// grab's first pattern is not below the current counterexample, or after
-// max_grabs grabs.
-std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, uint32_t budget) {
+// Chunk index bits: 0..4 are the lane (support PIs 5..9, fixed per thread);
+// the bits of the pass PIs (k - 5 for PI k) change from pass to pass; the
+// others belong to the grab.  Grab q (handed out by a counter, one ahead,
+// from [q0, qend), computed on the host) is every chunk whose grab bits spell
+// q, REP passes of 32 chunks, masked to [cb, ce).  Tables chosen by
+// plan_hoist (no pass PI among their inputs) are evaluated once per grab,
+// the others once per pass.  Grabs and passes increase in chunk index, so a
+// warp stops at the end of its range or when its grab's lowest pattern is
+// not below the current counterexample; it also stops after max_grabs grabs.
+std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, uint32_t budget,
+                        uint64_t pass_pis) {
   const LutProgram &lp = g.lut;
   const uint32_t NA = lp.na, NP = lp.np;
   const size_t NV = NA + NP + 1;
-  uint32_t lgG = 5;
-  while ((1u << (lgG - 5)) < REP) lgG++;
-  const uint32_t vary_lo = 10, vary_hi = std::min<uint32_t>(NP, 5 + lgG);  // pass PIs [vary_lo, vary_hi)
   std::vector<uint8_t> hoisted;
   uint32_t roots = 0;
-  plan_hoist(lp, vary_lo, std::max(vary_lo, vary_hi), budget, hoisted, &roots);
+  plan_hoist(lp, pass_pis, budget, hoisted, &roots);
+  // chunk-index bit positions of the pass PIs and of the grab
+  const uint32_t cbits = NP > 5 ? NP - 5 : 0;
+  std::vector<uint32_t> ppos, gpos;
+  for (uint32_t b = 5; b < cbits; b++) ((pass_pis >> (b + 5)) & 1u ? ppos : gpos).push_back(b);
+  std::vector<int32_t> rank(64, -1);  // chunk bit -> rank among pass or grab bits
+  for (uint32_t i = 0; i < ppos.size(); i++) rank[ppos[i]] = (int32_t)i;
+  for (uint32_t i = 0; i < gpos.size(); i++) rank[gpos[i]] = (int32_t)i;
   std::vector<int8_t> isconst(NV, 0);
   std::vector<uint32_t> cval(NV, 0);
   static const uint32_t mask[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
@@ -295,21 +326,19 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     cval[l.node] = r;
   }
   std::ostringstream s;
-  char buf[160];
+  char buf[192];
   s << ".version 9.0\n.target sm_" << major << minor << "a\n.address_size 64\n\n"
     << ".visible .entry es_jit(.param .u64 p_cb, .param .u64 p_ce, .param .u64 p_cex, .param .u64 p_ev,\n"
-    << "    .param .u64 p_next, .param .u64 p_maxg, .param .u64 p_rep)\n.maxntid " << kJitBlock << ", 1, 1\n{\n"
+    << "    .param .u64 p_next, .param .u64 p_maxg, .param .u64 p_rep, .param .u64 p_q0, .param .u64 p_qend)\n"
+    << ".maxntid " << kJitBlock << ", 1, 1\n{\n"
     << "  .reg .pred %p<12>;\n  .reg .b32 %t<24>;\n  .reg .b64 %d<40>;\n"
     << "  .reg .b32 %v<" << (NA + 1) << ">;\n  .reg .b32 %q<" << (NP + 1) << ">;\n";
-  // parameters; grab range [d8, d9) of grab numbers; lane; first grab; first
-  // counterexample poll
-  snprintf(buf, sizeof(buf), "  shr.u64 %%d8, %%d1, %u;\n  add.u64 %%d9, %%d2, %u;\n  shr.u64 %%d9, %%d9, %u;\n", lgG,
-           (1u << lgG) - 1u, lgG);
+  // parameters; grab range [d8, d9); lane; first grab; first counterexample poll
   s << "  ld.param.u64 %d1, [p_cb];\n  ld.param.u64 %d2, [p_ce];\n  ld.param.u64 %d3, [p_cex];\n"
        "  ld.param.u64 %d4, [p_ev];\n  ld.param.u64 %d5, [p_next];\n  ld.param.u64 %d6, [p_maxg];\n"
+       "  ld.param.u64 %d8, [p_q0];\n  ld.param.u64 %d9, [p_qend];\n"
        "  cvta.to.global.u64 %d3, %d3;\n  cvta.to.global.u64 %d4, %d4;\n  cvta.to.global.u64 %d5, %d5;\n"
-    << buf
-    << "  mov.u32 %t1, %tid.x;\n  and.b32 %t2, %t1, 31;\n  setp.eq.u32 %p1, %t2, 0;\n"
+       "  mov.u32 %t1, %tid.x;\n  and.b32 %t2, %t1, 31;\n  setp.eq.u32 %p1, %t2, 0;\n"
        "  mov.u64 %d10, 0;\n  mov.u64 %d11, 0;\n  @%p1 atom.global.add.u64 %d11, [%d5], 1;\n"
        "  mov.b64 {%t3, %t4}, %d11;\n  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n"
        "  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n  mov.b64 %d11, {%t3, %t4};\n"
@@ -337,12 +366,6 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     snprintf(buf, sizeof(buf), "  bfe.s32 %%q%u, %%t2, %u, 1;\n", k, k - 5);
     if (pi_used[k]) s << buf;
   }
-  // PI k >= 5 from bit (k - 5) of the chunk index in (t5: low, t6: high word)
-  auto emit_pi = [&](uint32_t k) {
-    const uint32_t j = k - 5;
-    snprintf(buf, sizeof(buf), "  bfe.s32 %%q%u, %%t%d, %u, 1;\n", k, j < 32 ? 5 : 6, j < 32 ? j : j - 32);
-    s << buf;
-  };
   auto emit_table = [&](const LutCover::Lut &l) {
     name[l.node] = "%v" + std::to_string(l.node);
     auto op = [&](int32_t id) -> std::string { return id < 0 ? std::string("0") : name[id]; };
@@ -352,30 +375,47 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
              x0.c_str(), l.tt);
     s << buf;
   };
-  // grab loop: d14 grab number, d15 its first chunk
+  // scatter the bits of a 64-bit source register into chunk positions (runs
+  // of consecutive positions): dst = sum over runs of field << position
+  auto emit_deposit = [&](const char *dst, const char *src, const std::vector<uint32_t> &pos) {
+    s << "  mov.u64 " << dst << ", 0;\n";
+    for (const BitRun &r : bit_runs(pos)) {
+      snprintf(buf, sizeof(buf),
+               "  shr.u64 %%d30, %s, %u;\n  and.b64 %%d30, %%d30, 0x%016llx;\n  shl.b64 %%d30, %%d30, %u;\n"
+               "  or.b64 %s, %s, %%d30;\n",
+               src, r.from, (unsigned long long)((r.len >= 64 ? 0ull : (1ull << r.len)) - 1ull), r.at, dst, dst);
+      s << buf;
+    }
+  };
+  // grab loop: d14 grab number, d15 its lowest chunk (the grab bits of q)
   s << "$LOOP:\n"
        "  add.u64 %d14, %d8, %d11;\n  setp.ge.u64 %p2, %d14, %d9;\n  @%p2 bra $DONE;\n";
-  snprintf(buf, sizeof(buf), "  shl.b64 %%d15, %%d14, %u;\n", lgG);
-  s << buf
-    << "  max.u64 %d20, %d15, %d1;\n  shl.b64 %d21, %d20, 5;\n  setp.ge.u64 %p2, %d21, %d12;\n  @%p2 bra $DONE;\n"
+  emit_deposit("%d15", "%d14", gpos);
+  s << "  max.u64 %d20, %d15, %d1;\n  shl.b64 %d21, %d20, 5;\n  setp.ge.u64 %p2, %d21, %d12;\n  @%p2 bra $DONE;\n"
        "  setp.lt.u64 %p3, %d13, %d6;\n  and.pred %p4, %p1, %p3;\n  mov.u64 %d16, -1;\n"
        "  @%p4 atom.global.add.u64 %d16, [%d5], 1;\n  mov.u64 %d17, 0;\n"
        "  @%p1 ld.volatile.global.u64 %d17, [%d3];\n"
-       "  cvt.u32.u64 %t5, %d15;\n  shr.u64 %d20, %d15, 32;\n  cvt.u32.u64 %t6, %d20;\n";
-  // the grab's PIs, then the hoisted tables
-  for (uint32_t k = std::max(10u, vary_hi); k < NP; k++)
-    if (pi_used[k]) emit_pi(k);
+       "  cvt.u32.u64 %t5, %d14;\n  shr.u64 %d20, %d14, 32;\n  cvt.u32.u64 %t6, %d20;\n";
+  // the grab's PIs (bit rank of q), then the hoisted tables
+  for (uint32_t k = 10; k < NP; k++) {
+    if (!pi_used[k] || ((pass_pis >> k) & 1u)) continue;
+    const int32_t j = rank[k - 5];
+    snprintf(buf, sizeof(buf), "  bfe.s32 %%q%u, %%t%d, %d, 1;\n", k, j < 32 ? 5 : 6, j < 32 ? j : j - 32);
+    s << buf;
+  }
   for (size_t i = 0; i < lp.order.size(); i++)
     if (hoisted[i] && !isconst[lp.order[i].node]) emit_table(lp.order[i]);
-  // passes of 32 chunks from d27 up to the grab's end d28
-  snprintf(buf, sizeof(buf), "  mov.u64 %%d27, %%d15;\n  add.u64 %%d28, %%d15, %u;\n", 1u << lgG);
-  s << buf
-    << "$PASS:\n  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra $GRABEND;\n"
+  // passes: j in t20, its chunk bits in d29, the pass's first chunk d27
+  s << "  mov.u32 %t20, 0;\n$PASS:\n  cvt.u64.u32 %d31, %t20;\n";
+  emit_deposit("%d29", "%d31", ppos);
+  s << "  add.u64 %d27, %d15, %d29;\n  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra $GRABEND;\n"
        "  add.u64 %d22, %d27, 32;\n  setp.le.u64 %p10, %d22, %d1;\n  @%p10 bra $NEXTPASS;\n"
-       "  add.u64 %d19, %d27, %d18;\n"
-       "  cvt.u32.u64 %t5, %d19;\n  shr.u64 %d20, %d19, 32;\n  cvt.u32.u64 %t6, %d20;\n";
-  for (uint32_t k = vary_lo; k < vary_hi; k++)
-    if (pi_used[k]) emit_pi(k);
+       "  add.u64 %d19, %d27, %d18;\n";
+  for (uint32_t k = 10; k < NP; k++) {
+    if (!pi_used[k] || !((pass_pis >> k) & 1u)) continue;
+    snprintf(buf, sizeof(buf), "  bfe.s32 %%q%u, %%t20, %d, 1;\n", k, rank[k - 5]);
+    s << buf;
+  }
   for (size_t i = 0; i < lp.order.size(); i++)
     if (!hoisted[i] && !isconst[lp.order[i].node]) emit_table(lp.order[i]);
   const uint32_t vmask = g.n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << g.n)) - 1u);
@@ -395,7 +435,7 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
        "$NOFAIL:\n"
        "  selp.u64 %d24, 0, 1, %p5;\n  add.u64 %d10, %d10, %d24;\n"
        "$NEXTPASS:\n"
-       "  add.u64 %d27, %d27, 32;\n  setp.lt.u64 %p9, %d27, %d28;\n  @%p9 bra $PASS;\n"
+       "  add.u32 %t20, %t20, 1;\n  setp.lt.u32 %p9, %t20, " + std::to_string(REP) + ";\n  @%p9 bra $PASS;\n"
        "$GRABEND:\n"
        "  mov.b64 {%t3, %t4}, %d16;\n  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n"
        "  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n  mov.b64 %d11, {%t3, %t4};\n"
@@ -413,8 +453,9 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   s << "  setp.ne.u64 %p8, %d10, 0;\n  and.pred %p8, %p8, %p1;\n  shl.b64 %d26, %d10, 5;\n"
        "  @%p8 red.global.add.u64 [%d4], %d26;\n  ret;\n}\n";
   if (getenv("LEC_ES_JIT_LOG"))
-    fprintf(stderr, "lec_es JIT %016llx: %u tables, rep %u, %zu hoisted (%u roots)\n", (unsigned long long)g.hash,
-            lp.count, REP, (size_t)std::count(hoisted.begin(), hoisted.end(), (uint8_t)1), roots);
+    fprintf(stderr, "lec_es JIT %016llx: %u tables, rep %u, pass PIs %016llx, %zu hoisted (%u read per pass)\n",
+            (unsigned long long)g.hash, lp.count, REP, (unsigned long long)pass_pis,
+            (size_t)std::count(hoisted.begin(), hoisted.end(), (uint8_t)1), roots);
   return s.str();
 }
 
@@ -467,10 +508,11 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
     // hoisted values live in registers across the passes: if ptxas has to
     // spill, halve the budget and build again
     uint32_t rep = 0, budget = 0;
-    jit_shape(g, &rep, &budget);
+    uint64_t pass_pis = 0;
+    jit_layout(g, &rep, &budget, &pass_pis);
     for (;;) {
       std::string lg;
-      const int rc = compile_ptx(gen_ptx_lut(g, major, minor, rep, budget), major, minor, cubin, lg);
+      const int rc = compile_ptx(gen_ptx_lut(g, major, minor, rep, budget, pass_pis), major, minor, cubin, lg);
       const bool spills = rc == LEC_ES_OK && lg.find(" 0 bytes spill stores") == std::string::npos &&
                           lg.find("spill stores") != std::string::npos;
       if (rc != LEC_ES_OK || !spills || budget == 0) {
@@ -564,12 +606,13 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   std::string path;
   if (!c->jit_dir.empty()) {
     mkdir(c->jit_dir.c_str(), 0755);
-    char name[96];
+    char name[128];
     uint32_t rep = 0, budget = 0;
-    jit_shape(g, &rep, &budget);
-    snprintf(name, sizeof(name), "/es_v%d_%016llx_%s%s_r%u_h%u_sm%d%d.cubin", kCodegenVersion,
+    uint64_t pass_pis = 0;
+    jit_layout(g, &rep, &budget, &pass_pis);
+    snprintf(name, sizeof(name), "/es_v%d_%016llx_%s%s_r%u_h%u_p%llx_sm%d%d.cubin", kCodegenVersion,
              (unsigned long long)g.hash, lut_form ? "lut" : "and", getenv("LEC_ES_JIT_NVRTC") ? "_nvrtc" : "", rep,
-             budget, c->cc_major, c->cc_minor);
+             budget, (unsigned long long)pass_pis, c->cc_major, c->cc_minor);
     path = c->jit_dir + name;
   }
   double nvrtc_ms = 0;
@@ -605,10 +648,13 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   k->num_luts = g.lut.count;
   k->lut_live = g.lut.live;
   k->work_per_chunk = lut_form ? g.lut.count : (uint32_t)g.recs.size();
-  if (lut_form && !g.lut.order.empty() && !getenv("LEC_ES_JIT_NVRTC")) {  // the PTX form: passes per grab compiled in
+  k->chunk_bits = g.n > 5 ? g.n - 5 : 0;
+  if (lut_form && !g.lut.order.empty() && !getenv("LEC_ES_JIT_NVRTC")) {  // the PTX form: its grab layout
     uint32_t rep = 0, budget = 0;
-    jit_shape(g, &rep, &budget);
+    uint64_t pass_pis = 0;
+    jit_layout(g, &rep, &budget, &pass_pis);
     k->rep_fixed = rep;
+    k->pass_bits = pass_pis >> 5;
   }
   k->load_ms = now_ms() - tl;
   k->nvrtc_ms = nvrtc_ms;
@@ -747,6 +793,40 @@ uint64_t jit_reps(const JitKernel *k, uint64_t chunks, uint64_t grid) {
   return p2;
 }
 
+void jit_grab_range(const JitKernel *k, uint64_t rep, uint64_t cb, uint64_t ce, uint64_t *q0, uint64_t *qend) {
+  if (!k->pass_bits) {  // contiguous grabs of 32 * rep chunks
+    const uint64_t G = 32ull * rep;
+    *q0 = cb / G;
+    *qend = (ce + G - 1) / G;
+    return;
+  }
+  // grab bits: chunk bits from 5 up that are not pass bits; grab q is every
+  // chunk whose grab bits spell q.  Lowest chunk of q: its bits deposited;
+  // highest: plus every pass bit and the lane bits.  Both grow with q.
+  std::vector<uint32_t> pos;
+  for (uint32_t b = 5; b < k->chunk_bits && b < 64; b++)
+    if (!((k->pass_bits >> b) & 1u)) pos.push_back(b);
+  const uint64_t lanes_and_pass = k->pass_bits | 31ull;
+  auto lo = [&](uint64_t q) {
+    uint64_t c = 0;
+    for (size_t i = 0; i < pos.size(); i++) c |= ((q >> i) & 1ull) << pos[i];
+    return c;
+  };
+  const uint64_t nq = pos.size() >= 63 ? ~0ull : (1ull << pos.size());
+  auto first = [&](auto pred) {  // smallest q in [0, nq) with pred(q), else nq
+    uint64_t a = 0, b = nq;
+    while (a < b) {
+      const uint64_t m = a + (b - a) / 2;
+      if (pred(m)) b = m;
+      else a = m + 1;
+    }
+    return a;
+  };
+  *q0 = first([&](uint64_t q) { return (lo(q) | lanes_and_pass) >= cb; });
+  *qend = first([&](uint64_t q) { return lo(q) >= ce; });
+  if (*qend < *q0) *qend = *q0;
+}
+
 void jit_geometry(const JitKernel *k, uint64_t chunks, int sm_count, uint64_t *grid, uint64_t *rep) {
   // Every warp grab costs one atomic on a single counter, so a small cone
   // needs both long grabs (rep passes of 32 chunks, ~4k instructions) and a
@@ -787,7 +867,9 @@ int jit_launch(lec_es_ctx *c, lec_es_plan *p, uint64_t chunk_begin, uint64_t chu
   const int fixed = grid > 0 ? grid : p->jit_grid;
   const int g = fixed > 0 ? fixed : (int)geo_grid;
   if (fixed > 0) rep = jit_reps(p->jit, chunk_end - chunk_begin, (uint64_t)g);
-  void *args[] = {&chunk_begin, &chunk_end, &cex, &evaluated, &next, &max_grabs, &rep};
+  uint64_t q0 = 0, qend = 0;
+  jit_grab_range(p->jit, rep, chunk_begin, chunk_end, &q0, &qend);
+  void *args[] = {&chunk_begin, &chunk_end, &cex, &evaluated, &next, &max_grabs, &rep, &q0, &qend};
   cudaError_t e = cudaLaunchKernel((const void *)p->jit->kern, dim3(g), dim3(p->jit_block), args, 0, p->stream);
   return e == cudaSuccess ? 0 : (int)e;
 }

@@ -178,8 +178,9 @@ int launch(Server *s, Request *r) {
     uint64_t cb = 0, ce = C, grabs = 8;
     unsigned long long *cex = sl.d_res, *ev = sl.d_res + 1, *next = sl.d_res + 3;
     // passes per grab as for a full-GPU launch of this kernel
-    uint64_t rep = jit_reps(k, C, (uint64_t)c->sm_count * k->blocks_per_sm);
-    void *args[] = {&cb, &ce, &cex, &ev, &next, &grabs, &rep};
+    uint64_t rep = jit_reps(k, C, (uint64_t)c->sm_count * k->blocks_per_sm), q0 = 0, qend = 0;
+    jit_grab_range(k, rep, cb, ce, &q0, &qend);
+    void *args[] = {&cb, &ce, &cex, &ev, &next, &grabs, &rep, &q0, &qend};
     const uint64_t per_block = (uint64_t)(k->block / 32) * 32 * grabs * rep;
     const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>((C + per_block - 1) / per_block, 1u << 30));
     err = cudaLaunchKernel((const void *)k->kern, dim3((unsigned)grid), dim3(k->block), args, 0, st) ==
