@@ -360,6 +360,9 @@ int plan_prepare(lec_es_ctx *c, const lec_es_miter *m, const lec_es_options *opt
   }
   if (rc) return rc;
   const double front_ms = now_ms() - t0;
+  if (getenv("LEC_ES_FRONT_LOG"))
+    fprintf(stderr, "lec_es front end %016llx: %.3f ms, table cover %s\n", (unsigned long long)prog.hash, front_ms,
+            prog.lut.elided ? "reused from the kernel" : "built");
   rc = plan_prepare_program(c, std::move(prog), opt, out);
   if (!rc) (*out)->host_ms += front_ms;
   return rc;
