@@ -37,17 +37,17 @@ namespace {
 // single-launch device times of 71 (interpreter) and 74 (specialised kernel)
 // equivalent miters -- the 12x12 and 16x16 multiplier miters, the adders,
 // product-bit miters of 8..18-bit multipliers and node-pair miters of 4..28
-// PIs -- with median relative errors of 8% and 10%.
+// PIs -- with median relative errors of 7% and 14%.
 struct Builtin {
   double a_ms, c_ms, alpha_ms;
 };
 constexpr Builtin kRun[4] = {
     {0.0, 0.0, 0.0},                  // AUTO: unused
-    {1.098e-2, 3.017e-5, 1.236e-4},   // INTERP: word-wide interpreter
-    {7.674e-3, 1.842e-6, 3.340e-6},   // JIT: specialised kernel
+    {1.113e-2, 3.025e-5, 1.229e-4},   // INTERP: word-wide interpreter
+    {8.488e-3, 2.619e-6, 1.685e-6},   // JIT: specialised kernel
     {2.0e-2, 1.0e-4, 2.0e-3},         // SPILL: global-memory interpreter (rough)
 };
-constexpr Builtin kCompile = {9.6, 0.084, 0.0};  // kernel build: ms + ms per table
+constexpr Builtin kCompile = {11.1, 0.084, 0.0};  // kernel build: ms + ms per table
 constexpr double kPriorWeight = 4.0;             // the built-in values count as this many samples each
 constexpr double kBinCap = 8.0;                  // a (n, log2 gates) bin counts as at most this many
 
