@@ -353,8 +353,13 @@ int plan_prepare(lec_es_ctx *c, const lec_es_miter *m, const lec_es_options *opt
   MiterView v{m->num_pis, m->num_ands, m->fanins, m->out_lit};
   int rc;
   try {
-    const KernelProbe probe{jit_have_kernel, c};
-    rc = compile_program(v, opt ? opt->order : LEC_ES_ORDER_AUTO, c->max_pis, prog, &probe);
+    const uint32_t want = opt ? opt->tier : LEC_ES_TIER_AUTO;
+    JitProbe jp{c, want == LEC_ES_TIER_JIT ? JitProbe::kRun : JitProbe::kAuto};
+    const KernelProbe probe{jit_probe, &jp};
+    // the probe finds table-form kernels only
+    const bool may_skip = (want == LEC_ES_TIER_JIT || want == LEC_ES_TIER_AUTO) &&
+                          !(opt && (opt->flags & LEC_ES_FLAG_JIT_AND_FORM));
+    rc = compile_program(v, opt ? opt->order : LEC_ES_ORDER_AUTO, c->max_pis, prog, may_skip ? &probe : nullptr);
   } catch (const std::bad_alloc &) {
     return LEC_ES_ENOMEM;
   }
@@ -384,6 +389,7 @@ int plan_prepare_program(lec_es_ctx *c, Program &&prog, const lec_es_options *op
   const Program &g = p->prog;
   const uint64_t chunks = num_chunks(g.n);
   uint32_t want = opt ? opt->tier : LEC_ES_TIER_AUTO;
+  if (g.slots_elided) want = LEC_ES_TIER_JIT;  // the front end found this cone's kernel for this run
   if (want == LEC_ES_TIER_AUTO) want = jit_auto_tier(c, g, chunks);
   if (want == LEC_ES_TIER_JIT) {
     rc = jit_prepare(c, p.get(), opt);
@@ -593,7 +599,7 @@ extern "C" int lec_es_plan_info(const lec_es_plan *p, lec_es_program_info *info)
   info->out_slot = g.out_slot;
   info->out_compl = g.out_compl;
   info->order = g.order;
-  info->num_records = g.recs.size();
+  info->num_records = g.num_records;
   info->hash = g.hash;
   info->num_luts = g.lut.count;
   info->lut_live = g.lut.live;

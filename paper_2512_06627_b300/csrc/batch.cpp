@@ -128,7 +128,16 @@ void batch_release(lec_es_ctx *c, lec_es_batch_plan *b) {
   delete b;
 }
 
-int compile_all(lec_es_ctx *c, const lec_es_miter *m, size_t k, uint32_t order, std::vector<Program> &progs) {
+}  // namespace
+
+bool lec::batch_wants_kernel(lec_es_ctx *c, uint32_t n, uint32_t cone_ands, uint32_t luts, uint32_t live) {
+  return cost_run_ms(c, LEC_ES_TIER_INTERP, cone_ands, n) >= kBatchJitMs && luts && live <= kBatchJitLive;
+}
+
+namespace {
+
+int compile_all(lec_es_ctx *c, const lec_es_miter *m, size_t k, uint32_t order, bool allow_jit,
+                std::vector<Program> &progs) {
   progs.assign(k, Program());
   std::vector<int> rcs(k, LEC_ES_OK);
   const unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), 16u));
@@ -138,8 +147,9 @@ int compile_all(lec_es_ctx *c, const lec_es_miter *m, size_t k, uint32_t order, 
       for (size_t i = t; i < k; i += nt) {
         MiterView v{m[i].num_pis, m[i].num_ands, m[i].fanins, m[i].out_lit};
         try {
-          const KernelProbe probe{jit_have_kernel, c};
-          rcs[i] = compile_program(v, order, c->max_pis, progs[i], &probe);
+          JitProbe jp{c, allow_jit ? JitProbe::kBatch : JitProbe::kInfo};
+          const KernelProbe probe{jit_probe, &jp};
+          rcs[i] = compile_program(v, order, c->max_pis, progs[i], allow_jit ? &probe : nullptr);
         } catch (const std::bad_alloc &) {
           rcs[i] = LEC_ES_ENOMEM;
         }
@@ -155,7 +165,8 @@ int compile_all(lec_es_ctx *c, const lec_es_miter *m, size_t k, uint32_t order, 
 // Stage 1: programs, specialised kernels, fallbacks, packed records, buffers.
 int stage_programs(lec_es_ctx *c, lec_es_batch_plan *b, const lec_es_miter *m, size_t k,
                    const lec_es_options *opt) {
-  int rc = compile_all(c, m, k, opt ? opt->order : LEC_ES_ORDER_AUTO, b->progs);
+  const bool allow_jit = !(opt && (opt->tier == LEC_ES_TIER_INTERP || opt->tier == LEC_ES_TIER_SPILL));
+  int rc = compile_all(c, m, k, opt ? opt->order : LEC_ES_ORDER_AUTO, allow_jit, b->progs);
   if (rc) return rc;
   if (cudaSetDevice(c->device) != cudaSuccess) return LEC_ES_ECUDA;
   // live sets the tile kernel holds in shared memory at 64 threads per block
@@ -163,11 +174,9 @@ int stage_programs(lec_es_ctx *c, lec_es_batch_plan *b, const lec_es_miter *m, s
   const uint32_t max_fit64 = (uint32_t)((c->smem_optin - 64 - 4 * 512 * 16) / (64 * 8));
   b->jit_of.assign(k, -1);
   b->fallback_of.assign(k, -1);
-  const bool allow_jit = !(opt && (opt->tier == LEC_ES_TIER_INTERP || opt->tier == LEC_ES_TIER_SPILL));
   for (size_t i = 0; i < k; i++) {
     const Program &g = b->progs[i];
-    const double t_int = cost_run_ms(c, LEC_ES_TIER_INTERP, g.cone_ands, g.n);
-    if (allow_jit && t_int >= kBatchJitMs && g.lut.count && g.lut.live <= kBatchJitLive) {
+    if (g.slots_elided || (allow_jit && batch_wants_kernel(c, g.n, g.cone_ands, g.lut.count, g.lut.live))) {
       b->jit_of[i] = (int)b->jit_miters.size();
       b->jit_miters.push_back((uint32_t)i);
     } else if (g.num_slots > max_fit64) {

@@ -285,7 +285,8 @@ extern "C" int lec_es_cost_predict(lec_es_ctx *c, const lec_es_miter *m, uint32_
   int rc;
   try {
     if (c) {
-      const KernelProbe probe{jit_have_kernel, c};
+      JitProbe jp{c, JitProbe::kInfo};
+      const KernelProbe probe{jit_probe, &jp};
       rc = compile_program(v, LEC_ES_ORDER_AUTO, c->max_pis, g, &probe);
     } else {
       rc = compile_program(v, LEC_ES_ORDER_AUTO, 63, g);

@@ -58,6 +58,7 @@ struct JitKernel {
   double load_ms = 0;      // of which loading the cubin and querying the kernel
   uint32_t num_luts = 0;   // the program's table count and live count when built
   uint32_t lut_live = 0;
+  uint32_t num_slots = 0, order = 0, num_records = 0;  // its slot program's, for results
   uint32_t work_per_chunk = 0;  // straight-line instructions per 32-pattern chunk (about)
   uint32_t rep_fixed = 0;       // passes per grab compiled into the kernel (0: a launch parameter)
   uint64_t pass_bits = 0;       // chunk-index bits of the pass PIs (0: contiguous grabs of 32 * rep chunks)
@@ -133,9 +134,16 @@ lec::JitKernel *jit_lookup_or_schedule(lec_es_ctx *c, const Program &g);
 int jit_attach(lec_es_ctx *c, lec_es_plan *p, JitKernel *k, const lec_es_options *opt);
 // Cached kernel for a program (compiled on a miss; thread-safe).
 int jit_get_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out, double *compile_ms);
-// KernelProbe callback (arg = the context): the compiled table-form kernel
-// for a program hash, if this context holds one.
-bool jit_have_kernel(void *arg, uint64_t hash, uint32_t *luts, uint32_t *live);
+// KernelProbe callback: the compiled table-form kernel for a program hash,
+// if the context holds one and the caller will run it (arg = JitProbe).
+struct JitProbe {
+  enum Use { kRun, kAuto, kBatch, kInfo };
+  lec_es_ctx *c;
+  Use use;  // kRun: the kernel tier was asked for; kAuto: the AUTO choice; kBatch: the batch's split; kInfo: facts only
+};
+bool jit_probe(void *arg, uint64_t hash, uint32_t n, uint32_t cone_ands, KernelFacts *facts);
+// The batch gives a miter its own kernel (else the tile queue).
+bool batch_wants_kernel(lec_es_ctx *c, uint32_t n, uint32_t cone_ands, uint32_t luts, uint32_t live);
 void jit_release_all(lec_es_ctx *c);
 
 // single-miter plans (api.cpp)

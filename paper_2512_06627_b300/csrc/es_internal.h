@@ -59,8 +59,10 @@ struct Program {
   uint32_t out_compl = 0;
   uint32_t cone_ands = 0;
   uint32_t order = 0;
-  uint64_t hash = 0;
+  uint64_t hash = 0;                // of the cone's structure (dense ids, complements, output, n)
   LutProgram lut;                   // 3-input table cover (the JIT tier's instructions)
+  bool slots_elided = false;        // recs/order_vars not built: the specialised kernel runs this cone
+  uint32_t num_records = 0;         // recs.size(), or the kernel's record count when elided
 };
 
 struct MiterView {
@@ -70,12 +72,20 @@ struct MiterView {
 };
 
 // Front end.  Returns an lec_es_status code.
-// The table cover only feeds code generation for the specialised kernel.  A
-// caller that already holds that kernel (looked up by the program hash) can
-// pass `have_kernel`: when it returns true with the kernel's table count and
-// live count, the cover is not rebuilt and the LutProgram is marked elided.
+// The program hash depends only on the cone's structure, so it is known right
+// after the cone is extracted.  The table cover only feeds code generation
+// for the specialised kernel, and the slot program only the interpreter
+// tiers.  A caller that already holds the cone's kernel and will run it can
+// pass a probe: when have_kernel returns true (filling in what the kernel
+// was built from), neither is rebuilt -- the LutProgram is marked elided and
+// so is the slot program (no records; slot and record counts come from the
+// kernel).
+struct KernelFacts {
+  uint32_t luts = 0, live = 0;      // table count and live count
+  uint32_t num_slots = 0, order = 0, num_records = 0;
+};
 struct KernelProbe {
-  bool (*have_kernel)(void *arg, uint64_t hash, uint32_t *luts, uint32_t *live);
+  bool (*have_kernel)(void *arg, uint64_t hash, uint32_t n, uint32_t cone_ands, KernelFacts *facts);
   void *arg;
 };
 

@@ -444,6 +444,45 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
   if (c.pis.size() > max_pis || c.pis.size() > 63) return LEC_ES_ETOOBIG;
   ConeIndex ix(c, dense, (uint64_t)m.num_pis + m.num_ands);
   const uint32_t root_var = m.out_lit >> 1;
+  // the cone's structure: fanin value ids and complements of its ANDs in
+  // ascending order, the output's value id and complement, the support size
+  uint64_t chash = 1469598103934665603ull;
+  {
+    const uint32_t head[2] = {(uint32_t)c.pis.size(), (uint32_t)c.ands.size()};
+    chash = fnv1a(head, sizeof(head), chash);
+    std::vector<uint32_t> row(2 * c.ands.size());
+    for (size_t i = 0; i < c.ands.size(); i++) {
+      const uint32_t *f = fanin_of(m, c.ands[i]);
+      row[2 * i] = (uint32_t)ix.vid(f[0] >> 1) << 1 | (f[0] & 1u);
+      row[2 * i + 1] = (uint32_t)ix.vid(f[1] >> 1) << 1 | (f[1] & 1u);
+    }
+    for (uint32_t w : row) chash = (chash ^ w) * 0x100000001B3ull;  // word-wise FNV step
+    chash ^= chash >> 29;
+    const uint32_t tail[1] = {(uint32_t)ix.vid(root_var) << 1 | (m.out_lit & 1u)};
+    chash = fnv1a(tail, sizeof(tail), chash);
+  }
+  KernelFacts facts;
+  if (probe && probe->have_kernel(probe->arg, chash, (uint32_t)c.pis.size(), (uint32_t)c.ands.size(), &facts)) {
+    Program p;
+    p.n = (uint32_t)c.pis.size();
+    p.support.resize(c.pis.size());
+    for (size_t k = 0; k < c.pis.size(); k++) p.support[k] = c.pis[k] - 1;
+    p.cone_ands = (uint32_t)c.ands.size();
+    p.out_compl = m.out_lit & 1;
+    p.hash = chash;
+    p.num_slots = facts.num_slots;
+    p.order = facts.order;
+    p.num_records = facts.num_records;
+    p.slots_elided = true;
+    p.lut.na = (uint32_t)c.ands.size();
+    p.lut.np = (uint32_t)c.pis.size();
+    p.lut.root = ix.vid(root_var);
+    p.lut.count = facts.luts;
+    p.lut.live = facts.live;
+    p.lut.elided = true;
+    out = std::move(p);
+    return LEC_ES_OK;
+  }
   std::vector<uint32_t> level;
   order_levels(m, c, ix, level);
 
@@ -484,19 +523,9 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
   best.cone_ands = (uint32_t)c.ands.size();
   best.out_compl = m.out_lit & 1;
   if (best.num_slots == 0) best.num_slots = 1;
-  uint64_t h = 1469598103934665603ull;
-  h = fnv1a(best.recs.data(), best.recs.size() * sizeof(Rec), h);
-  uint32_t tail[3] = {best.n, best.out_slot, best.out_compl};
-  best.hash = fnv1a(tail, sizeof(tail), h);
-  uint32_t luts = 0, live = 0;
-  if (probe && probe->have_kernel(probe->arg, best.hash, &luts, &live)) {
-    best.lut.na = (uint32_t)c.ands.size();
-    best.lut.np = (uint32_t)c.pis.size();
-    best.lut.root = ix.vid(root_var);
-    best.lut.count = luts;
-    best.lut.live = live;
-    best.lut.elided = true;
-  } else {
+  best.hash = chash;
+  best.num_records = (uint32_t)best.recs.size();
+  {
     // the table cover (independent of the slot order), then its evaluation
     // order, one candidate of which follows the chosen slot order
     LutProgram lp;

@@ -598,9 +598,9 @@ namespace {
 
 // Compile (or read from the disk cache) and load one program's kernel.
 int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out) {
-  // an elided cover means the kernel was found by hash; generating code from
-  // it would drop the tables
-  if (lut_form && g.lut.elided) return LEC_ES_EINVAL;
+  // an elided cover or slot program means the kernel was found by hash;
+  // generating code from it would drop the program
+  if ((lut_form && g.lut.elided) || (!lut_form && g.slots_elided)) return LEC_ES_EINVAL;
   const double t0 = now_ms();
   std::vector<char> cubin;
   std::string path;
@@ -647,6 +647,9 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   k->block = kJitBlock;
   k->num_luts = g.lut.count;
   k->lut_live = g.lut.live;
+  k->num_slots = g.num_slots;
+  k->order = g.order;
+  k->num_records = g.num_records;
   k->work_per_chunk = lut_form ? g.lut.count : (uint32_t)g.recs.size();
   k->chunk_bits = g.n > 5 ? g.n - 5 : 0;
   if (lut_form && !g.lut.order.empty() && !getenv("LEC_ES_JIT_NVRTC")) {  // the PTX form: its grab layout
@@ -689,15 +692,37 @@ void worker_loop(lec_es_ctx *c) {
 
 uint64_t cache_key(const Program &g, bool lut_form) { return g.hash ^ (lut_form ? 0x9E3779B97F4A7C15ull : 0ull); }
 
-bool jit_have_kernel(void *arg, uint64_t hash, uint32_t *luts, uint32_t *live) {
-  lec_es_ctx *c = (lec_es_ctx *)arg;
+bool jit_probe(void *arg, uint64_t hash, uint32_t n, uint32_t cone_ands, KernelFacts *f) {
+  const JitProbe *p = (const JitProbe *)arg;
+  lec_es_ctx *c = p->c;
   if (!c->jit) return false;
-  JitState *js = c->jit;
-  std::lock_guard<std::mutex> lk(js->mu);
-  auto it = js->cache.find(hash ^ 0x9E3779B97F4A7C15ull);
-  if (it == js->cache.end() || it->second->num_luts == 0) return false;
-  *luts = it->second->num_luts;
-  *live = it->second->lut_live;
+  JitKernel *k = nullptr;
+  {
+    JitState *js = c->jit;
+    std::lock_guard<std::mutex> lk(js->mu);
+    auto it = js->cache.find(hash ^ 0x9E3779B97F4A7C15ull);
+    if (it == js->cache.end() || it->second->num_luts == 0) return false;
+    k = it->second;
+  }
+  // will the caller run this kernel?  (else it needs the slot program)
+  switch (p->use) {
+    case JitProbe::kRun:
+    case JitProbe::kInfo:
+      break;
+    case JitProbe::kAuto:
+      if (k->lut_live > kMaxJitLive ||
+          !(cost_run_ms(c, LEC_ES_TIER_JIT, cone_ands, n) < cost_run_ms(c, LEC_ES_TIER_INTERP, cone_ands, n)))
+        return false;
+      break;
+    case JitProbe::kBatch:
+      if (!batch_wants_kernel(c, n, cone_ands, k->num_luts, k->lut_live)) return false;
+      break;
+  }
+  f->luts = k->num_luts;
+  f->live = k->lut_live;
+  f->num_slots = k->num_slots;
+  f->order = k->order;
+  f->num_records = k->num_records;
   return true;
 }
 

@@ -102,7 +102,7 @@ size_t reserve_bytes(lec_es_ctx *c, const Program &g) {
   const uint64_t words = num_words(g.n);
   const uint64_t in_flight_words = (uint64_t)c->sm_count * 2048 / 2;  // 2048 lanes per SM, 2 lanes a word
   const uint64_t rw = std::min(words, in_flight_words);
-  return (size_t)g.num_slots * rw * 8 + g.recs.size() * sizeof(Rec);
+  return (size_t)g.num_slots * rw * 8 + (size_t)g.num_records * sizeof(Rec);
 }
 
 void finish(Server *s, Request *r, Request::State st) {
@@ -117,7 +117,8 @@ int launch(Server *s, Request *r) {
   const Program &g = r->prog;
   const uint64_t C = num_chunks(g.n);
   JitKernel *k = nullptr;
-  if (jit_auto_tier(c, g, C) == LEC_ES_TIER_JIT) k = jit_lookup_or_schedule(c, g);
+  if (g.slots_elided || jit_auto_tier(c, g, C) == LEC_ES_TIER_JIT) k = jit_lookup_or_schedule(c, g);
+  if (g.slots_elided && !k) return LEC_ES_EINVAL;  // found at submission; kernels are never evicted
   // stream: least loaded within the request's priority class, from the ES
   // time model on the tier it will run
   const double predicted = cost_run_ms(c, k ? LEC_ES_TIER_JIT : LEC_ES_TIER_INTERP, g.cone_ands, g.n);
@@ -425,7 +426,8 @@ extern "C" int lec_es_submit(lec_es_ctx *c, const lec_es_miter *m, uint64_t *tic
   MiterView v{m->num_pis, m->num_ands, m->fanins, m->out_lit};
   int rc;
   try {
-    const KernelProbe probe{jit_have_kernel, c};
+    JitProbe jp{c, JitProbe::kAuto};
+    const KernelProbe probe{jit_probe, &jp};
     rc = compile_program(v, LEC_ES_ORDER_AUTO, c->max_pis, r->prog, &probe);
   } catch (const std::bad_alloc &) {
     return LEC_ES_ENOMEM;
