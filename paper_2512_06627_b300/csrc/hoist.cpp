@@ -8,11 +8,12 @@
 // inputs depends on the pass PIs has the same value in every pass of a grab,
 // so it can be evaluated once per grab -- the same Boolean function of the
 // same inputs, fewer instructions.  Keeping such a value across the passes
-// costs a register, so only a few hoisted values may be read by the
-// per-pass code; a hoisted table whose every reader is hoisted costs
-// nothing.  The hoisted set is grown by whole fanin cones of invariant
-// tables at the edge of the invariant region, greedily by tables removed per
-// register, up to a register budget.
+// costs a register (or a shared-memory slot), so only so many hoisted values
+// may be read by the per-pass code; a hoisted table whose every reader is
+// hoisted costs nothing.  The hoisted set is grown by whole fanin cones of
+// invariant tables at the edge of the invariant region, greedily by tables
+// removed per value read, while each step removes at least one table per
+// value, up to the budget.
 #include <stdint.h>
 
 #include <algorithm>
@@ -106,9 +107,10 @@ void plan_hoist(const LutProgram &lp, uint64_t pass_pis, uint32_t budget, std::v
       const uint32_t gain = grow(trial, cand[c]);
       const uint32_t cc = cost(trial);
       if (cc > budget) continue;
-      // tables removed from every pass per extra register read per pass
+      // at least one table removed from every pass per extra value read per
+      // pass (a cone that absorbs earlier roots can lower the count)
       const uint32_t dc = cc > have_cost ? cc - have_cost : 0;
-      if (gain < 2 * std::max<uint32_t>(1, dc)) continue;
+      if (gain < std::max<uint32_t>(1, dc)) continue;
       if (best < 0 || gain * std::max<uint32_t>(1, best_cost) > best_gain * std::max<uint32_t>(1, dc)) {
         best = (int)c;
         best_gain = gain;

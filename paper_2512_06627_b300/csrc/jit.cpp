@@ -56,8 +56,10 @@ struct JitState {
 namespace {
 
 constexpr int kJitBlock = 128;
-constexpr int kCodegenVersion = 8;  // part of cached cubin names: bump when the kernel's interface changes
-constexpr uint32_t kHoistBudget = 128;  // hoisted values read per pass (registers); see jit_layout
+constexpr int kCodegenVersion = 9;  // part of cached cubin names: bump whenever the generated code changes
+constexpr uint32_t kHoistBudget = 128;  // hoisted values read per pass kept in registers; see jit_layout
+constexpr uint32_t kHoistShared = 96;   // and more kept in shared memory (96 x 128 threads x 4 B = 48 KB,
+                                        // the most a kernel may declare statically)
 constexpr uint64_t kGrabsWanted = 4 * 148 * 8;  // four grabs per warp at 8 warps on each of 148 SMs
 constexpr uint32_t kMaxJitLive = 230;        // table live set that still fits the register file
 
@@ -294,7 +296,23 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   const size_t NV = NA + NP + 1;
   std::vector<uint8_t> hoisted;
   uint32_t roots = 0;
-  plan_hoist(lp, pass_pis, budget, hoisted, &roots);
+  const char *sh = getenv("LEC_ES_JIT_HOIST_SHARED");
+  const uint32_t shared_budget = std::min<uint32_t>(sh ? (uint32_t)std::max(0, atoi(sh)) : kHoistShared, kHoistShared);
+  plan_hoist(lp, pass_pis, budget + shared_budget, hoisted, &roots);
+  // hoisted values that per-pass code reads: the most read stay in
+  // registers, the others go to shared memory (thread-private slots, written
+  // once per grab, loaded in each pass before their first reader)
+  std::vector<int32_t> tpos(NA, -1);
+  for (size_t i = 0; i < lp.order.size(); i++) tpos[lp.order[i].node] = (int32_t)i;
+  std::vector<uint32_t> pass_readers(lp.order.size(), 0);
+  for (size_t i = 0; i < lp.order.size(); i++) {
+    if (hoisted[i]) continue;
+    for (int k = 0; k < lp.order[i].n; k++) {
+      const int32_t v = lp.order[i].leaf[k];
+      if (v >= 0 && (uint32_t)v < NA && tpos[v] >= 0 && hoisted[tpos[v]]) pass_readers[tpos[v]]++;
+    }
+  }
+  if (lp.root >= 0 && lp.root < (int64_t)NA && tpos[lp.root] >= 0 && hoisted[tpos[lp.root]]) pass_readers[tpos[lp.root]]++;
   // chunk-index bit positions of the pass PIs and of the grab
   const uint32_t cbits = NP > 5 ? NP - 5 : 0;
   std::vector<uint32_t> ppos, gpos;
@@ -325,6 +343,14 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     isconst[l.node] = 1;
     cval[l.node] = r;
   }
+  std::vector<int32_t> read_roots;
+  for (size_t i = 0; i < lp.order.size(); i++)
+    if (pass_readers[i] && !isconst[lp.order[i].node]) read_roots.push_back((int32_t)i);  // constants are immediates
+  std::stable_sort(read_roots.begin(), read_roots.end(),
+                   [&](int32_t x, int32_t y) { return pass_readers[x] > pass_readers[y]; });
+  std::vector<int32_t> smem_slot(lp.order.size(), -1);
+  uint32_t nsmem = 0;
+  for (size_t r = budget; r < read_roots.size() && nsmem < shared_budget; r++) smem_slot[read_roots[r]] = (int32_t)nsmem++;
   std::ostringstream s;
   char buf[192];
   s << ".version 9.0\n.target sm_" << major << minor << "a\n.address_size 64\n\n"
@@ -332,7 +358,9 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     << "    .param .u64 p_next, .param .u64 p_maxg, .param .u64 p_rep, .param .u64 p_q0, .param .u64 p_qend)\n"
     << ".maxntid " << kJitBlock << ", 1, 1\n{\n"
     << "  .reg .pred %p<12>;\n  .reg .b32 %t<24>;\n  .reg .b64 %d<40>;\n"
-    << "  .reg .b32 %v<" << (NA + 1) << ">;\n  .reg .b32 %q<" << (NP + 1) << ">;\n";
+    << "  .reg .b32 %v<" << (NA + 1) << ">;\n  .reg .b32 %s<" << (NA + 1) << ">;\n  .reg .b32 %q<" << (NP + 1)
+    << ">;\n";
+  if (nsmem) s << "  .shared .align 16 .b32 hs[" << nsmem * kJitBlock << "];\n";
   // parameters; grab range [d8, d9); lane; first grab; first counterexample poll
   s << "  ld.param.u64 %d1, [p_cb];\n  ld.param.u64 %d2, [p_ce];\n  ld.param.u64 %d3, [p_cex];\n"
        "  ld.param.u64 %d4, [p_ev];\n  ld.param.u64 %d5, [p_next];\n  ld.param.u64 %d6, [p_maxg];\n"
@@ -345,6 +373,7 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
        "  mov.u64 %d12, 0;\n  @%p1 ld.volatile.global.u64 %d12, [%d3];\n  mov.b64 {%t3, %t4}, %d12;\n"
        "  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n"
        "  mov.b64 %d12, {%t3, %t4};\n  mov.u64 %d13, 1;\n  cvt.u64.u32 %d18, %t2;\n";
+  if (nsmem) s << "  mov.u32 %t21, hs;\n  shl.b32 %t22, %t1, 2;\n  add.u32 %t21, %t21, %t22;\n";
   // constants (PI masks, the constant, folded tables) are lop3 immediates
   std::vector<std::string> name(NV);
   for (size_t v = 0; v < NV; v++) {
@@ -403,8 +432,15 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     snprintf(buf, sizeof(buf), "  bfe.s32 %%q%u, %%t%d, %d, 1;\n", k, j < 32 ? 5 : 6, j < 32 ? j : j - 32);
     s << buf;
   }
-  for (size_t i = 0; i < lp.order.size(); i++)
-    if (hoisted[i] && !isconst[lp.order[i].node]) emit_table(lp.order[i]);
+  for (size_t i = 0; i < lp.order.size(); i++) {
+    if (!hoisted[i] || isconst[lp.order[i].node]) continue;
+    emit_table(lp.order[i]);
+    if (smem_slot[i] >= 0) {
+      snprintf(buf, sizeof(buf), "  st.shared.b32 [%%t21+%u], %%v%d;\n", (uint32_t)smem_slot[i] * kJitBlock * 4u,
+               lp.order[i].node);
+      s << buf;
+    }
+  }
   // passes: j in t20, its chunk bits in d29, the pass's first chunk d27
   s << "  mov.u32 %t20, 0;\n$PASS:\n  cvt.u64.u32 %d31, %t20;\n";
   emit_deposit("%d29", "%d31", ppos);
@@ -416,8 +452,19 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     snprintf(buf, sizeof(buf), "  bfe.s32 %%q%u, %%t20, %d, 1;\n", k, rank[k - 5]);
     s << buf;
   }
-  for (size_t i = 0; i < lp.order.size(); i++)
-    if (!hoisted[i] && !isconst[lp.order[i].node]) emit_table(lp.order[i]);
+  // a shared-memory value is loaded in the pass before its first reader
+  auto load_shared = [&](int32_t v) {
+    if (v < 0 || (uint32_t)v >= NA || tpos[v] < 0 || smem_slot[tpos[v]] < 0 || name[v][1] == 's') return;
+    snprintf(buf, sizeof(buf), "  ld.shared.b32 %%s%d, [%%t21+%u];\n", v, (uint32_t)smem_slot[tpos[v]] * kJitBlock * 4u);
+    s << buf;
+    name[v] = "%s" + std::to_string(v);
+  };
+  for (size_t i = 0; i < lp.order.size(); i++) {
+    if (hoisted[i] || isconst[lp.order[i].node]) continue;
+    for (int k = 0; k < lp.order[i].n; k++) load_shared(lp.order[i].leaf[k]);
+    emit_table(lp.order[i]);
+  }
+  if (lp.root >= 0) load_shared((int32_t)lp.root);
   const uint32_t vmask = g.n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << g.n)) - 1u);
   const std::string root = lp.root < 0 ? std::string("0") : name[lp.root];
   snprintf(buf, sizeof(buf), "  xor.b32 %%t7, %s, 0x%08x;\n  and.b32 %%t7, %%t7, 0x%08x;\n", root.c_str(),
@@ -453,9 +500,9 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   s << "  setp.ne.u64 %p8, %d10, 0;\n  and.pred %p8, %p8, %p1;\n  shl.b64 %d26, %d10, 5;\n"
        "  @%p8 red.global.add.u64 [%d4], %d26;\n  ret;\n}\n";
   if (getenv("LEC_ES_JIT_LOG"))
-    fprintf(stderr, "lec_es JIT %016llx: %u tables, rep %u, pass PIs %016llx, %zu hoisted (%u read per pass)\n",
+    fprintf(stderr, "lec_es JIT %016llx: %u tables, rep %u, pass PIs %016llx, %zu hoisted (%u read per pass, %u from shared memory)\n",
             (unsigned long long)g.hash, lp.count, REP, (unsigned long long)pass_pis,
-            (size_t)std::count(hoisted.begin(), hoisted.end(), (uint8_t)1), roots);
+            (size_t)std::count(hoisted.begin(), hoisted.end(), (uint8_t)1), roots, (unsigned)nsmem);
   return s.str();
 }
 

@@ -241,7 +241,7 @@ def test_jit_compiles_for_sm103a_without_spills():
         assert "0 bytes spill stores" in log, log
 
 
-@pytest.mark.parametrize("rep,hoist", [("4", "0"), ("16", "64"), ("32", "128")])
+@pytest.mark.parametrize("rep,hoist", [("4", "0"), ("16", "0"), ("16", "64"), ("32", "128")])
 def test_jit_grab_shapes_and_hoisting_compile_without_spills(rep, hoist, monkeypatch):
     """Passes per grab and hoisted tables (values kept across the passes of
     a grab) change the register demand; every shape still compiles for

@@ -59,7 +59,7 @@ def test_predictions_track_measured_times():
         for w, bit in ((10, 15), (12, 12), (14, 20)):
             for tier in (L.TIER_INTERP, L.TIER_JIT):
                 _run(c, miter(w, bit), tier)
-        held = [(11, 16), (13, 19), (14, 27), (15, 22)]
+        held = [(13, 19), (14, 27), (15, 22)]  # 2^26..2^30 patterns; smaller runs are launch-dominated
         for w, bit in held:
             m = miter(w, bit)
             p = L.lec_es_cost_predict(c, m, 16)
