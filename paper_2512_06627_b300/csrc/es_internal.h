@@ -98,8 +98,17 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
 // code.
 void plan_hoist(const LutProgram &lp, uint64_t pass_pis, uint32_t budget, std::vector<uint8_t> &hoisted,
                 uint32_t *roots);
+// The same, growing a fanin-closed base set (kept whole); the base's values
+// read outside it count against the budget too.
+void plan_hoist_from(const LutProgram &lp, uint64_t pass_pis, uint32_t budget, const std::vector<uint8_t> &base,
+                     std::vector<uint8_t> &hoisted, uint32_t *roots);
 // The k support PIs (index >= 10) that the fewest tables depend on, as a mask.
 uint64_t least_influential_pis(const LutProgram &lp, uint32_t k);
+// Pass PIs for an outer pass loop (a proper subset of pass_pis), chosen to
+// minimise table evaluations per grab; 0 when a second loop level would
+// save less than 5% (unless force, which takes one whenever pass_pis has
+// two PIs or more).
+uint64_t choose_outer_pis(const LutProgram &lp, uint64_t pass_pis, bool force = false);
 
 // Words of 64 patterns for a support of n PIs.
 inline uint64_t num_words(uint32_t n) { return n <= 6 ? 1ull : (1ull << (n - 6)); }

@@ -14,6 +14,13 @@
 // invariant tables at the edge of the invariant region, greedily by tables
 // removed per value read, while each step removes at least one table per
 // value, up to the budget.
+//
+// The passes of a grab may also run as two nested loops: an outer loop over
+// some of the pass PIs and an inner loop over the rest.  A table that reads
+// only outer pass PIs (and grab-level values) then runs once per outer
+// iteration.  Its set is planned the same way, starting from the grab-level
+// set, against the inner pass PIs; a value stays live across the inner loop
+// if it is read below its own level.
 #include <stdint.h>
 
 #include <algorithm>
@@ -25,9 +32,16 @@ namespace lec {
 
 void plan_hoist(const LutProgram &lp, uint64_t pass_pis, uint32_t budget, std::vector<uint8_t> &hoisted,
                 uint32_t *roots_out) {
+  plan_hoist_from(lp, pass_pis, budget, std::vector<uint8_t>(), hoisted, roots_out);
+}
+
+void plan_hoist_from(const LutProgram &lp, uint64_t pass_pis, uint32_t budget, const std::vector<uint8_t> &base_in,
+                     std::vector<uint8_t> &hoisted, uint32_t *roots_out) {
   const uint32_t NA = lp.na, NP = lp.np;
   const size_t NL = lp.order.size();
-  hoisted.assign(NL, 0);
+  std::vector<uint8_t> base = base_in;
+  base.resize(NL, 0);
+  hoisted = base;
   if (roots_out) *roots_out = 0;
   if (NL == 0 || lp.root < 0 || lp.root >= (int64_t)NA) return;
   std::vector<int32_t> pos(NA, -1);  // AND value id -> table index
@@ -59,8 +73,15 @@ void plan_hoist(const LutProgram &lp, uint64_t pass_pis, uint32_t budget, std::v
   const int32_t out_t = pos[lp.root];
   // A hoisted set is the fanin cone of its roots (every table a hoisted
   // table reads is hoisted too); its cost is the number of hoisted values
-  // the per-pass code reads (a table outside the set, or the output).
-  std::vector<uint8_t> in(NL, 0), trial(NL, 0);
+  // the per-pass code reads (a table outside the set, or the output), plus
+  // the base's values read outside the base (live across the loop too).
+  std::vector<uint8_t> in = base, trial(NL, 0), base_read(NL, 0);
+  for (size_t i = 0; i < NL; i++) {
+    if (!base[i]) continue;
+    bool read = (int32_t)i == out_t;
+    for (int32_t r : readers[i]) read = read || !base[r];
+    base_read[i] = read;
+  }
   auto grow = [&](std::vector<uint8_t> &h, int32_t r) -> uint32_t {  // add r's cone, return tables added
     uint32_t added = 0;
     std::vector<int32_t> st{r};
@@ -81,7 +102,7 @@ void plan_hoist(const LutProgram &lp, uint64_t pass_pis, uint32_t budget, std::v
     uint32_t c = 0;
     for (size_t i = 0; i < NL; i++) {
       if (!h[i]) continue;
-      bool read = (int32_t)i == out_t;
+      bool read = (int32_t)i == out_t || base_read[i];
       for (int32_t r : readers[i]) read = read || !h[r];
       c += read;
     }
@@ -91,12 +112,12 @@ void plan_hoist(const LutProgram &lp, uint64_t pass_pis, uint32_t budget, std::v
   // invariant, or the output itself when it is invariant
   std::vector<int32_t> cand;
   for (size_t i = 0; i < NL; i++) {
-    if (!inv[i]) continue;
+    if (!inv[i] || base[i]) continue;
     bool edge = (int32_t)i == out_t;
     for (int32_t r : readers[i]) edge = edge || !inv[r];
     if (edge) cand.push_back((int32_t)i);
   }
-  uint32_t have_cost = 0, roots = 0;
+  uint32_t have_cost = cost(in), roots = 0;
   std::vector<uint8_t> used(cand.size(), 0);
   for (;;) {
     int best = -1;
@@ -127,13 +148,14 @@ void plan_hoist(const LutProgram &lp, uint64_t pass_pis, uint32_t budget, std::v
   if (roots_out) *roots_out = have_cost;
 }
 
-uint64_t least_influential_pis(const LutProgram &lp, uint32_t k) {
+namespace {
+// support PIs each table depends on
+std::vector<uint64_t> table_support(const LutProgram &lp) {
   const uint32_t NA = lp.na, NP = lp.np;
   const size_t NL = lp.order.size();
-  if (NP <= 10 || k == 0) return 0;
   std::vector<int32_t> pos(NA, -1);
   for (size_t i = 0; i < NL; i++) pos[lp.order[i].node] = (int32_t)i;
-  std::vector<uint64_t> dep(NL, 0);  // support PIs each table depends on
+  std::vector<uint64_t> dep(NL, 0);
   for (size_t i = 0; i < NL; i++)
     for (int q = 0; q < lp.order[i].n; q++) {
       const int32_t v = lp.order[i].leaf[q];
@@ -144,6 +166,15 @@ uint64_t least_influential_pis(const LutProgram &lp, uint32_t k) {
         dep[i] |= dep[pos[v]];
       }
     }
+  return dep;
+}
+}  // namespace
+
+uint64_t least_influential_pis(const LutProgram &lp, uint32_t k) {
+  const uint32_t NP = lp.np;
+  const size_t NL = lp.order.size();
+  if (NP <= 10 || k == 0) return 0;
+  const std::vector<uint64_t> dep = table_support(lp);
   std::vector<std::pair<uint64_t, uint32_t>> infl;
   for (uint32_t p = 10; p < NP && p < 64; p++) {
     uint64_t c = 0;
@@ -154,6 +185,41 @@ uint64_t least_influential_pis(const LutProgram &lp, uint32_t k) {
   uint64_t m = 0;
   for (uint32_t i = 0; i < k && i < infl.size(); i++) m |= 1ull << infl[i].second;
   return m;
+}
+
+uint64_t choose_outer_pis(const LutProgram &lp, uint64_t pass_pis, bool force) {
+  const uint32_t k = (uint32_t)__builtin_popcountll(pass_pis);
+  if (k < 2 || lp.order.empty()) return 0;
+  const std::vector<uint64_t> dep = table_support(lp);
+  std::vector<uint32_t> bits;  // pass PIs in ascending order
+  for (uint32_t p = 0; p < 64; p++)
+    if ((pass_pis >> p) & 1u) bits.push_back(p);
+  // table evaluations per grab: grab-level tables once, outer-level ones
+  // 2^|outer| times, the rest 2^k times (hoisting limits ignored)
+  auto evals = [&](uint64_t outer) -> uint64_t {
+    uint64_t e = 0;
+    const uint64_t no = 1ull << __builtin_popcountll(outer), nk = 1ull << k;
+    for (uint64_t d : dep) {
+      const uint64_t pd = d & pass_pis;
+      e += pd == 0 ? 1 : (pd & ~outer) == 0 ? no : nk;
+    }
+    return e;
+  };
+  const uint64_t flat = evals(0);
+  uint64_t best = 0, best_e = flat;
+  for (uint32_t sub = 1; sub + 1 < (1u << k); sub++) {  // proper, non-empty subsets
+    uint64_t outer = 0;
+    for (uint32_t i = 0; i < k; i++)
+      if ((sub >> i) & 1u) outer |= 1ull << bits[i];
+    const uint64_t e = evals(outer);
+    if (e < best_e) {
+      best_e = e;
+      best = outer;
+    }
+  }
+  if (force) return best ? best : pass_pis & (~pass_pis + 1);  // else the lowest pass PI alone
+  // a second loop level pays only for a clear saving
+  return best_e * 100 <= flat * 95 ? best : 0;
 }
 
 }  // namespace lec

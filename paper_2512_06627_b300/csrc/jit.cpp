@@ -56,7 +56,7 @@ struct JitState {
 namespace {
 
 constexpr int kJitBlock = 128;
-constexpr int kCodegenVersion = 9;  // part of cached cubin names: bump whenever the generated code changes
+constexpr int kCodegenVersion = 10;  // part of cached cubin names: bump whenever the generated code changes
 constexpr uint32_t kHoistBudget = 128;  // hoisted values read per pass kept in registers; see jit_layout
 constexpr uint32_t kHoistShared = 96;   // and more kept in shared memory (96 x 128 threads x 4 B = 48 KB,
                                         // the most a kernel may declare statically)
@@ -237,10 +237,13 @@ std::string gen_source(const Program &g, bool lut_form) {
 // a small pattern space keeps enough grabs to fill the GPU, which wins over
 // both.  The pass PIs are the support PIs (index >= 10) the fewest tables
 // depend on, so the most tables are the same in every pass of a grab.
-// LEC_ES_JIT_REP / LEC_ES_JIT_HOIST override passes and budget, and
-// LEC_ES_JIT_LOWPASS=1 takes PIs 10, 11, ... as the pass PIs (for
-// measurements).
-void jit_layout(const Program &g, uint32_t *rep, uint32_t *budget, uint64_t *pass_pis) {
+// The passes run as two nested loops when an outer loop over some pass PIs
+// saves enough table evaluations (choose_outer_pis).
+// LEC_ES_JIT_REP / LEC_ES_JIT_HOIST override passes and budget,
+// LEC_ES_JIT_LOWPASS=1 takes PIs 10, 11, ... as the pass PIs and
+// LEC_ES_JIT_NEST=0 keeps one pass loop and =2 nests whenever there are two
+// pass PIs or more (for measurements and tests).
+void jit_layout(const Program &g, uint32_t *rep, uint32_t *budget, uint64_t *pass_pis, uint64_t *outer_pis) {
   const uint32_t per = g.lut.count + 40;
   uint32_t r = 16;
   while (r < 32 && r * per < 4096) r <<= 1;
@@ -261,6 +264,9 @@ void jit_layout(const Program &g, uint32_t *rep, uint32_t *budget, uint64_t *pas
   *rep = 1u << npass;
   *budget = h;
   *pass_pis = m;
+  const char *nest = getenv("LEC_ES_JIT_NEST");
+  const int nest_mode = nest ? atoi(nest) : 1;
+  *outer_pis = nest_mode == 0 ? 0 : choose_outer_pis(g.lut, m, nest_mode == 2);
 }
 
 // Runs of consecutive chunk-index bits: (first bit, source bit, length).
@@ -290,35 +296,46 @@ std::vector<BitRun> bit_runs(const std::vector<uint32_t> &pos) {  // pos ascendi
 // warp stops at the end of its range or when its grab's lowest pattern is
 // not below the current counterexample; it also stops after max_grabs grabs.
 std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, uint32_t budget,
-                        uint64_t pass_pis) {
+                        uint64_t pass_pis, uint64_t outer_pis) {
   const LutProgram &lp = g.lut;
   const uint32_t NA = lp.na, NP = lp.np;
   const size_t NV = NA + NP + 1;
-  std::vector<uint8_t> hoisted;
+  outer_pis &= pass_pis;
+  const uint64_t inner_pis = pass_pis & ~outer_pis;
+  const uint32_t REP_OUT = 1u << __builtin_popcountll(outer_pis), REP_IN = REP / REP_OUT;
   uint32_t roots = 0;
   const char *sh = getenv("LEC_ES_JIT_HOIST_SHARED");
   const uint32_t shared_budget = std::min<uint32_t>(sh ? (uint32_t)std::max(0, atoi(sh)) : kHoistShared, kHoistShared);
-  plan_hoist(lp, pass_pis, budget + shared_budget, hoisted, &roots);
-  // hoisted values that per-pass code reads: the most read stay in
-  // registers, the others go to shared memory (thread-private slots, written
-  // once per grab, loaded in each pass before their first reader)
+  // level of each table: 0 once per grab, 1 once per outer pass (tables
+  // reading only outer pass PIs), 2 once per pass
+  std::vector<uint8_t> h0, h1;
+  plan_hoist(lp, pass_pis, budget + shared_budget, h0, &roots);
+  if (outer_pis) plan_hoist_from(lp, inner_pis, budget + shared_budget, h0, h1, &roots);
+  else h1 = h0;
+  std::vector<uint8_t> level(lp.order.size(), 2);
+  for (size_t i = 0; i < lp.order.size(); i++) level[i] = h0[i] ? 0 : h1[i] ? 1 : 2;
+  // values read below their own level (live across a loop): the most read
+  // stay in registers, the others go to shared memory (thread-private
+  // slots, written where they are computed, loaded in each later section
+  // before their first reader there)
   std::vector<int32_t> tpos(NA, -1);
   for (size_t i = 0; i < lp.order.size(); i++) tpos[lp.order[i].node] = (int32_t)i;
   std::vector<uint32_t> pass_readers(lp.order.size(), 0);
   for (size_t i = 0; i < lp.order.size(); i++) {
-    if (hoisted[i]) continue;
     for (int k = 0; k < lp.order[i].n; k++) {
       const int32_t v = lp.order[i].leaf[k];
-      if (v >= 0 && (uint32_t)v < NA && tpos[v] >= 0 && hoisted[tpos[v]]) pass_readers[tpos[v]]++;
+      if (v >= 0 && (uint32_t)v < NA && tpos[v] >= 0 && level[tpos[v]] < level[i]) pass_readers[tpos[v]]++;
     }
   }
-  if (lp.root >= 0 && lp.root < (int64_t)NA && tpos[lp.root] >= 0 && hoisted[tpos[lp.root]]) pass_readers[tpos[lp.root]]++;
-  // chunk-index bit positions of the pass PIs and of the grab
+  if (lp.root >= 0 && lp.root < (int64_t)NA && tpos[lp.root] >= 0 && level[tpos[lp.root]] < 2) pass_readers[tpos[lp.root]]++;
+  // chunk-index bit positions of the inner and outer pass PIs and of the grab
   const uint32_t cbits = NP > 5 ? NP - 5 : 0;
-  std::vector<uint32_t> ppos, gpos;
-  for (uint32_t b = 5; b < cbits; b++) ((pass_pis >> (b + 5)) & 1u ? ppos : gpos).push_back(b);
-  std::vector<int32_t> rank(64, -1);  // chunk bit -> rank among pass or grab bits
-  for (uint32_t i = 0; i < ppos.size(); i++) rank[ppos[i]] = (int32_t)i;
+  std::vector<uint32_t> ipos, opos, gpos;
+  for (uint32_t b = 5; b < cbits; b++)
+    ((inner_pis >> (b + 5)) & 1u ? ipos : (outer_pis >> (b + 5)) & 1u ? opos : gpos).push_back(b);
+  std::vector<int32_t> rank(64, -1);  // chunk bit -> rank among its group's bits
+  for (uint32_t i = 0; i < ipos.size(); i++) rank[ipos[i]] = (int32_t)i;
+  for (uint32_t i = 0; i < opos.size(); i++) rank[opos[i]] = (int32_t)i;
   for (uint32_t i = 0; i < gpos.size(); i++) rank[gpos[i]] = (int32_t)i;
   std::vector<int8_t> isconst(NV, 0);
   std::vector<uint32_t> cval(NV, 0);
@@ -357,7 +374,7 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     << ".visible .entry es_jit(.param .u64 p_cb, .param .u64 p_ce, .param .u64 p_cex, .param .u64 p_ev,\n"
     << "    .param .u64 p_next, .param .u64 p_maxg, .param .u64 p_rep, .param .u64 p_q0, .param .u64 p_qend)\n"
     << ".maxntid " << kJitBlock << ", 1, 1\n{\n"
-    << "  .reg .pred %p<12>;\n  .reg .b32 %t<24>;\n  .reg .b64 %d<40>;\n"
+    << "  .reg .pred %p<12>;\n  .reg .b32 %t<26>;\n  .reg .b64 %d<40>;\n"
     << "  .reg .b32 %v<" << (NA + 1) << ">;\n  .reg .b32 %s<" << (NA + 1) << ">;\n  .reg .b32 %q<" << (NP + 1)
     << ">;\n";
   if (nsmem) s << "  .shared .align 16 .b32 hs[" << nsmem * kJitBlock << "];\n";
@@ -432,39 +449,58 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     snprintf(buf, sizeof(buf), "  bfe.s32 %%q%u, %%t%d, %d, 1;\n", k, j < 32 ? 5 : 6, j < 32 ? j : j - 32);
     s << buf;
   }
-  for (size_t i = 0; i < lp.order.size(); i++) {
-    if (!hoisted[i] || isconst[lp.order[i].node]) continue;
-    emit_table(lp.order[i]);
-    if (smem_slot[i] >= 0) {
-      snprintf(buf, sizeof(buf), "  st.shared.b32 [%%t21+%u], %%v%d;\n", (uint32_t)smem_slot[i] * kJitBlock * 4u,
-               lp.order[i].node);
-      s << buf;
-    }
-  }
-  // passes: j in t20, its chunk bits in d29, the pass's first chunk d27
-  s << "  mov.u32 %t20, 0;\n$PASS:\n  cvt.u64.u32 %d31, %t20;\n";
-  emit_deposit("%d29", "%d31", ppos);
-  s << "  add.u64 %d27, %d15, %d29;\n  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra $GRABEND;\n"
-       "  add.u64 %d22, %d27, 32;\n  setp.le.u64 %p10, %d22, %d1;\n  @%p10 bra $NEXTPASS;\n"
-       "  add.u64 %d19, %d27, %d18;\n";
-  for (uint32_t k = 10; k < NP; k++) {
-    if (!pi_used[k] || !((pass_pis >> k) & 1u)) continue;
-    snprintf(buf, sizeof(buf), "  bfe.s32 %%q%u, %%t20, %d, 1;\n", k, rank[k - 5]);
-    s << buf;
-  }
-  // a shared-memory value is loaded in the pass before its first reader
-  auto load_shared = [&](int32_t v) {
-    if (v < 0 || (uint32_t)v >= NA || tpos[v] < 0 || smem_slot[tpos[v]] < 0 || name[v][1] == 's') return;
+  // a shared-memory value is loaded in each section before its first
+  // reader there
+  std::vector<uint8_t> loaded(NA, 0);
+  auto load_shared = [&](int32_t v, uint8_t lv) {  // lv: the reading section's level
+    if (v < 0 || (uint32_t)v >= NA || tpos[v] < 0 || smem_slot[tpos[v]] < 0 || loaded[v] || level[tpos[v]] >= lv)
+      return;
     snprintf(buf, sizeof(buf), "  ld.shared.b32 %%s%d, [%%t21+%u];\n", v, (uint32_t)smem_slot[tpos[v]] * kJitBlock * 4u);
     s << buf;
     name[v] = "%s" + std::to_string(v);
+    loaded[v] = 1;
   };
-  for (size_t i = 0; i < lp.order.size(); i++) {
-    if (hoisted[i] || isconst[lp.order[i].node]) continue;
-    for (int k = 0; k < lp.order[i].n; k++) load_shared(lp.order[i].leaf[k]);
-    emit_table(lp.order[i]);
+  auto emit_level = [&](uint8_t lv) {
+    std::fill(loaded.begin(), loaded.end(), (uint8_t)0);
+    for (size_t i = 0; i < lp.order.size(); i++) {
+      if (level[i] != lv || isconst[lp.order[i].node]) continue;
+      for (int k = 0; k < lp.order[i].n; k++) load_shared(lp.order[i].leaf[k], lv);
+      emit_table(lp.order[i]);
+      if (smem_slot[i] >= 0) {
+        snprintf(buf, sizeof(buf), "  st.shared.b32 [%%t21+%u], %%v%d;\n", (uint32_t)smem_slot[i] * kJitBlock * 4u,
+                 lp.order[i].node);
+        s << buf;
+      }
+    }
+  };
+  auto emit_pass_pis = [&](uint64_t group, const char *idx) {
+    for (uint32_t k = 10; k < NP; k++) {
+      if (!pi_used[k] || !((group >> k) & 1u)) continue;
+      snprintf(buf, sizeof(buf), "  bfe.s32 %%q%u, %s, %d, 1;\n", k, idx, rank[k - 5]);
+      s << buf;
+    }
+  };
+  emit_level(0);
+  // outer passes (when there are outer pass PIs): index in t24, chunk bits in d28
+  if (outer_pis) {
+    s << "  mov.u32 %t24, 0;\n$OUTER:\n  cvt.u64.u32 %d32, %t24;\n";
+    emit_deposit("%d28", "%d32", opos);
+    s << "  add.u64 %d33, %d15, %d28;\n";
+    emit_pass_pis(outer_pis, "%t24");
+    emit_level(1);
   }
-  if (lp.root >= 0) load_shared((int32_t)lp.root);
+  // passes: j in t20, its chunk bits in d29, the pass's first chunk d27;
+  // outer passes do not run in chunk order, so a pass past the range is
+  // skipped rather than ending the grab
+  s << "  mov.u32 %t20, 0;\n$PASS:\n  cvt.u64.u32 %d31, %t20;\n";
+  emit_deposit("%d29", "%d31", ipos);
+  s << "  add.u64 %d27, " << (outer_pis ? "%d33" : "%d15") << ", %d29;\n  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra "
+    << (outer_pis ? "$NEXTPASS" : "$GRABEND") << ";\n"
+    << "  add.u64 %d22, %d27, 32;\n  setp.le.u64 %p10, %d22, %d1;\n  @%p10 bra $NEXTPASS;\n"
+       "  add.u64 %d19, %d27, %d18;\n";
+  emit_pass_pis(inner_pis, "%t20");
+  emit_level(2);
+  if (lp.root >= 0) load_shared((int32_t)lp.root, 2);
   const uint32_t vmask = g.n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << g.n)) - 1u);
   const std::string root = lp.root < 0 ? std::string("0") : name[lp.root];
   snprintf(buf, sizeof(buf), "  xor.b32 %%t7, %s, 0x%08x;\n  and.b32 %%t7, %%t7, 0x%08x;\n", root.c_str(),
@@ -482,8 +518,11 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
        "$NOFAIL:\n"
        "  selp.u64 %d24, 0, 1, %p5;\n  add.u64 %d10, %d10, %d24;\n"
        "$NEXTPASS:\n"
-       "  add.u32 %t20, %t20, 1;\n  setp.lt.u32 %p9, %t20, " + std::to_string(REP) + ";\n  @%p9 bra $PASS;\n"
-       "$GRABEND:\n"
+       "  add.u32 %t20, %t20, 1;\n  setp.lt.u32 %p9, %t20, " + std::to_string(REP_IN) + ";\n  @%p9 bra $PASS;\n" +
+           (outer_pis ? "  add.u32 %t24, %t24, 1;\n  setp.lt.u32 %p9, %t24, " + std::to_string(REP_OUT) +
+                            ";\n  @%p9 bra $OUTER;\n"
+                      : std::string()) +
+           "$GRABEND:\n"
        "  mov.b64 {%t3, %t4}, %d16;\n  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n"
        "  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n  mov.b64 %d11, {%t3, %t4};\n"
        "  mov.b64 {%t3, %t4}, %d17;\n  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n"
@@ -500,9 +539,12 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   s << "  setp.ne.u64 %p8, %d10, 0;\n  and.pred %p8, %p8, %p1;\n  shl.b64 %d26, %d10, 5;\n"
        "  @%p8 red.global.add.u64 [%d4], %d26;\n  ret;\n}\n";
   if (getenv("LEC_ES_JIT_LOG"))
-    fprintf(stderr, "lec_es JIT %016llx: %u tables, rep %u, pass PIs %016llx, %zu hoisted (%u read per pass, %u from shared memory)\n",
-            (unsigned long long)g.hash, lp.count, REP, (unsigned long long)pass_pis,
-            (size_t)std::count(hoisted.begin(), hoisted.end(), (uint8_t)1), roots, (unsigned)nsmem);
+    fprintf(stderr,
+            "lec_es JIT %016llx: %u tables, rep %u, pass PIs %016llx (outer %016llx), %zu per grab, %zu per outer "
+            "pass (%u read below their level, %u from shared memory)\n",
+            (unsigned long long)g.hash, lp.count, REP, (unsigned long long)pass_pis, (unsigned long long)outer_pis,
+            (size_t)std::count(level.begin(), level.end(), (uint8_t)0),
+            (size_t)std::count(level.begin(), level.end(), (uint8_t)1), roots, (unsigned)nsmem);
   return s.str();
 }
 
@@ -555,11 +597,12 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
     // hoisted values live in registers across the passes: if ptxas has to
     // spill, halve the budget and build again
     uint32_t rep = 0, budget = 0;
-    uint64_t pass_pis = 0;
-    jit_layout(g, &rep, &budget, &pass_pis);
+    uint64_t pass_pis = 0, outer_pis = 0;
+    jit_layout(g, &rep, &budget, &pass_pis, &outer_pis);
     for (;;) {
       std::string lg;
-      const int rc = compile_ptx(gen_ptx_lut(g, major, minor, rep, budget, pass_pis), major, minor, cubin, lg);
+      const int rc =
+          compile_ptx(gen_ptx_lut(g, major, minor, rep, budget, pass_pis, outer_pis), major, minor, cubin, lg);
       const bool spills = rc == LEC_ES_OK && lg.find(" 0 bytes spill stores") == std::string::npos &&
                           lg.find("spill stores") != std::string::npos;
       if (rc != LEC_ES_OK || !spills || budget == 0) {
@@ -653,13 +696,13 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   std::string path;
   if (!c->jit_dir.empty()) {
     mkdir(c->jit_dir.c_str(), 0755);
-    char name[128];
+    char name[160];
     uint32_t rep = 0, budget = 0;
-    uint64_t pass_pis = 0;
-    jit_layout(g, &rep, &budget, &pass_pis);
-    snprintf(name, sizeof(name), "/es_v%d_%016llx_%s%s_r%u_h%u_p%llx_sm%d%d.cubin", kCodegenVersion,
+    uint64_t pass_pis = 0, outer_pis = 0;
+    jit_layout(g, &rep, &budget, &pass_pis, &outer_pis);
+    snprintf(name, sizeof(name), "/es_v%d_%016llx_%s%s_r%u_h%u_p%llx_o%llx_sm%d%d.cubin", kCodegenVersion,
              (unsigned long long)g.hash, lut_form ? "lut" : "and", getenv("LEC_ES_JIT_NVRTC") ? "_nvrtc" : "", rep,
-             budget, (unsigned long long)pass_pis, c->cc_major, c->cc_minor);
+             budget, (unsigned long long)pass_pis, (unsigned long long)outer_pis, c->cc_major, c->cc_minor);
     path = c->jit_dir + name;
   }
   double nvrtc_ms = 0;
@@ -701,8 +744,8 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   k->chunk_bits = g.n > 5 ? g.n - 5 : 0;
   if (lut_form && !g.lut.order.empty() && !getenv("LEC_ES_JIT_NVRTC")) {  // the PTX form: its grab layout
     uint32_t rep = 0, budget = 0;
-    uint64_t pass_pis = 0;
-    jit_layout(g, &rep, &budget, &pass_pis);
+    uint64_t pass_pis = 0, outer_pis = 0;
+    jit_layout(g, &rep, &budget, &pass_pis, &outer_pis);
     k->rep_fixed = rep;
     k->pass_bits = pass_pis >> 5;
   }

@@ -241,14 +241,16 @@ def test_jit_compiles_for_sm103a_without_spills():
         assert "0 bytes spill stores" in log, log
 
 
-@pytest.mark.parametrize("rep,hoist", [("4", "0"), ("16", "0"), ("16", "64"), ("32", "128")])
-def test_jit_grab_shapes_and_hoisting_compile_without_spills(rep, hoist, monkeypatch):
-    """Passes per grab and hoisted tables (values kept across the passes of
-    a grab) change the register demand; every shape still compiles for
-    sm_103a with all values in registers."""
+@pytest.mark.parametrize("rep,hoist,nest", [("4", "0", "2"), ("16", "0", "1"), ("16", "64", "2"), ("32", "128", "1"),
+                                            ("16", "128", "0")])
+def test_jit_grab_shapes_and_hoisting_compile_without_spills(rep, hoist, nest, monkeypatch):
+    """Passes per grab, hoisted tables (values kept across the passes of a
+    grab) and nested pass loops change the register demand; every shape
+    still compiles for sm_103a with all values in registers."""
     import re as _re
     monkeypatch.setenv("LEC_ES_JIT_REP", rep)
     monkeypatch.setenv("LEC_ES_JIT_HOIST", hoist)
+    monkeypatch.setenv("LEC_ES_JIT_NEST", nest)
     for aig in (C.config2_mult12(), C.config3_mult16()):
         log, nbytes = L.lec_es_jit_compile(L.miter_of(aig), 10, 3)
         assert nbytes > 0

@@ -140,15 +140,18 @@ def test_cached_kernel_skips_table_cover():
         L.lec_es_destroy(c)
 
 
-@pytest.mark.parametrize("rep,hoist", [("4", "0"), ("16", "64"), ("32", "128"), ("8", "16")])
-def test_passes_per_grab_and_hoisted_tables_keep_results(rep, hoist, monkeypatch):
-    """Every grab shape and hoisting budget gives the oracle's result,
-    including word ranges that start and end off the grab alignment."""
+@pytest.mark.parametrize("rep,hoist,nest", [("4", "0", "2"), ("16", "64", "1"), ("32", "128", "2"), ("8", "16", "2"),
+                                            ("16", "128", "0"), ("16", "0", "2")])
+def test_passes_per_grab_and_hoisted_tables_keep_results(rep, hoist, nest, monkeypatch):
+    """Every grab shape, hoisting budget and pass-loop nesting gives the
+    oracle's result, including word ranges that start and end off the grab
+    alignment (nested passes do not run in chunk order)."""
     monkeypatch.setenv("LEC_ES_JIT_REP", rep)
     monkeypatch.setenv("LEC_ES_JIT_HOIST", hoist)
+    monkeypatch.setenv("LEC_ES_JIT_NEST", nest)
     c = make_ctx(arena_bytes=64 << 20)
     try:
-        rng = np.random.default_rng(700 + int(rep) + int(hoist))
+        rng = np.random.default_rng(700 + int(rep) + int(hoist) + 1000 * int(nest))
         cases = [(C.config2_mult12(mutant_seed=1), None), (C.config2_mult12(), None)]
         for _ in range(4):
             a = random_aig(rng, int(rng.integers(10, 16)), int(rng.integers(40, 160)))
