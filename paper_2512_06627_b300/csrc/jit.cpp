@@ -56,7 +56,7 @@ struct JitState {
 namespace {
 
 constexpr int kJitBlock = 128;
-constexpr int kCodegenVersion = 10;  // part of cached cubin names: bump whenever the generated code changes
+constexpr int kCodegenVersion = 11;  // part of cached cubin names: bump whenever the generated code changes
 constexpr uint32_t kHoistBudget = 128;  // hoisted values read per pass kept in registers; see jit_layout
 constexpr uint32_t kHoistShared = 96;   // and more kept in shared memory (96 x 128 threads x 4 B = 48 KB,
                                         // the most a kernel may declare statically)
@@ -374,7 +374,7 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     << ".visible .entry es_jit(.param .u64 p_cb, .param .u64 p_ce, .param .u64 p_cex, .param .u64 p_ev,\n"
     << "    .param .u64 p_next, .param .u64 p_maxg, .param .u64 p_rep, .param .u64 p_q0, .param .u64 p_qend)\n"
     << ".maxntid " << kJitBlock << ", 1, 1\n{\n"
-    << "  .reg .pred %p<12>;\n  .reg .b32 %t<26>;\n  .reg .b64 %d<40>;\n"
+    << "  .reg .pred %p<14>;\n  .reg .b32 %t<26>;\n  .reg .b64 %d<40>;\n"
     << "  .reg .b32 %v<" << (NA + 1) << ">;\n  .reg .b32 %s<" << (NA + 1) << ">;\n  .reg .b32 %q<" << (NP + 1)
     << ">;\n";
   if (nsmem) s << "  .shared .align 16 .b32 hs[" << nsmem * kJitBlock << "];\n";
@@ -442,6 +442,16 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
        "  @%p4 atom.global.add.u64 %d16, [%d5], 1;\n  mov.u64 %d17, 0;\n"
        "  @%p1 ld.volatile.global.u64 %d17, [%d3];\n"
        "  cvt.u32.u64 %t5, %d14;\n  shr.u64 %d20, %d14, 32;\n  cvt.u32.u64 %t6, %d20;\n";
+  // p12: every chunk of the grab lies in [cb, ce) -- its passes then skip
+  // all range work and it counts its chunks at the end
+  uint64_t span = 32;
+  for (uint32_t b : ipos) span += 1ull << b;
+  for (uint32_t b : opos) span += 1ull << b;
+  snprintf(buf, sizeof(buf),
+           "  add.u64 %%d34, %%d15, %llu;\n  setp.le.u64 %%p13, %%d34, %%d2;\n  setp.ge.u64 %%p12, %%d15, %%d1;\n"
+           "  and.pred %%p12, %%p12, %%p13;\n",
+           (unsigned long long)span);
+  s << buf;
   // the grab's PIs (bit rank of q), then the hoisted tables
   for (uint32_t k = 10; k < NP; k++) {
     if (!pi_used[k] || ((pass_pis >> k) & 1u)) continue;
@@ -492,12 +502,17 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   // passes: j in t20, its chunk bits in d29, the pass's first chunk d27;
   // outer passes do not run in chunk order, so a pass past the range is
   // skipped rather than ending the grab
-  s << "  mov.u32 %t20, 0;\n$PASS:\n  cvt.u64.u32 %d31, %t20;\n";
-  emit_deposit("%d29", "%d31", ipos);
-  s << "  add.u64 %d27, " << (outer_pis ? "%d33" : "%d15") << ", %d29;\n  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra "
-    << (outer_pis ? "$NEXTPASS" : "$GRABEND") << ";\n"
+  // this lane's chunk of the pass in d19 (first chunk of the pass in d27)
+  auto emit_chunk = [&]() {
+    s << "  cvt.u64.u32 %d31, %t20;\n";
+    emit_deposit("%d29", "%d31", ipos);
+    s << "  add.u64 %d27, " << (outer_pis ? "%d33" : "%d15") << ", %d29;\n";
+  };
+  s << "  mov.u32 %t20, 0;\n$PASS:\n  @%p12 bra $PBODY;\n";
+  emit_chunk();
+  s << "  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra " << (outer_pis ? "$NEXTPASS" : "$GRABEND") << ";\n"
     << "  add.u64 %d22, %d27, 32;\n  setp.le.u64 %p10, %d22, %d1;\n  @%p10 bra $NEXTPASS;\n"
-       "  add.u64 %d19, %d27, %d18;\n";
+       "  add.u64 %d19, %d27, %d18;\n$PBODY:\n";
   emit_pass_pis(inner_pis, "%t20");
   emit_level(2);
   if (lp.root >= 0) load_shared((int32_t)lp.root, 2);
@@ -506,22 +521,25 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   snprintf(buf, sizeof(buf), "  xor.b32 %%t7, %s, 0x%08x;\n  and.b32 %%t7, %%t7, 0x%08x;\n", root.c_str(),
            g.out_compl ? 0xFFFFFFFFu : 0u, vmask);
   s << buf;
-  // chunks outside [cb, ce) neither fail nor count
-  s << "  setp.ge.u64 %p5, %d19, %d2;\n  setp.lt.u64 %p11, %d19, %d1;\n  or.pred %p5, %p5, %p11;\n"
-       "  @%p5 mov.b32 %t7, 0;\n  setp.ne.u32 %p6, %t7, 0;\n"
-       "  vote.sync.ballot.b32 %t8, %p6, -1;\n  setp.eq.u32 %p7, %t8, 0;\n  @%p7 bra $NOFAIL;\n"
+  // in a partial grab, chunks outside [cb, ce) neither fail nor count
+  s << "  @%p12 bra $CHECK;\n"
+       "  setp.ge.u64 %p5, %d19, %d2;\n  setp.lt.u64 %p11, %d19, %d1;\n  or.pred %p5, %p5, %p11;\n"
+       "  @%p5 mov.b32 %t7, 0;\n  selp.u64 %d24, 0, 1, %p5;\n  add.u64 %d10, %d10, %d24;\n"
+       "$CHECK:\n  setp.ne.u32 %p6, %t7, 0;\n"
+       "  vote.sync.ballot.b32 %t8, %p6, -1;\n  setp.eq.u32 %p7, %t8, 0;\n  @%p7 bra $NEXTPASS;\n"
        "  neg.s32 %t9, %t8;\n  and.b32 %t9, %t9, %t8;\n  bfind.u32 %t10, %t9;\n"
-       "  setp.ne.u32 %p7, %t10, %t2;\n  @%p7 bra $NOFAIL;\n"
+       "  setp.ne.u32 %p7, %t10, %t2;\n  @%p7 bra $NEXTPASS;\n";
+  emit_chunk();  // a failing pass (rare) recomputes its chunk
+  s << "  add.u64 %d19, %d27, %d18;\n"
        "  neg.s32 %t11, %t7;\n  and.b32 %t11, %t11, %t7;\n  bfind.u32 %t12, %t11;\n"
        "  cvt.u64.u32 %d21, %t12;\n  shl.b64 %d22, %d19, 5;\n  add.u64 %d22, %d22, %d21;\n"
        "  atom.global.min.u64 %d23, [%d3], %d22;\n"
-       "$NOFAIL:\n"
-       "  selp.u64 %d24, 0, 1, %p5;\n  add.u64 %d10, %d10, %d24;\n"
        "$NEXTPASS:\n"
        "  add.u32 %t20, %t20, 1;\n  setp.lt.u32 %p9, %t20, " + std::to_string(REP_IN) + ";\n  @%p9 bra $PASS;\n" +
            (outer_pis ? "  add.u32 %t24, %t24, 1;\n  setp.lt.u32 %p9, %t24, " + std::to_string(REP_OUT) +
                             ";\n  @%p9 bra $OUTER;\n"
                       : std::string()) +
+           "  @%p12 add.u64 %d10, %d10, " + std::to_string(REP) + ";\n"
            "$GRABEND:\n"
        "  mov.b64 {%t3, %t4}, %d16;\n  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n"
        "  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n  mov.b64 %d11, {%t3, %t4};\n"
