@@ -104,11 +104,11 @@ void plan_hoist_from(const LutProgram &lp, uint64_t pass_pis, uint32_t budget, c
                      std::vector<uint8_t> &hoisted, uint32_t *roots);
 // The k support PIs (index >= 10) that the fewest tables depend on, as a mask.
 uint64_t least_influential_pis(const LutProgram &lp, uint32_t k);
-// Pass PIs for an outer pass loop (a proper subset of pass_pis), chosen to
-// minimise table evaluations per grab; 0 when a second loop level would
-// save less than 5% (unless force, which takes one whenever pass_pis has
-// two PIs or more).
-uint64_t choose_outer_pis(const LutProgram &lp, uint64_t pass_pis, bool force = false);
+// Nested pass loops: the pass PIs split into groups, outermost loop first,
+// chosen to minimise table evaluations per grab, each extra loop level
+// charged 3%.  mode 0: one loop; 1: chosen; 2: chosen among two levels or
+// more; 3: one loop per pass PI.
+std::vector<uint64_t> choose_pass_groups(const LutProgram &lp, uint64_t pass_pis, int mode);
 
 // Words of 64 patterns for a support of n PIs.
 inline uint64_t num_words(uint32_t n) { return n <= 6 ? 1ull : (1ull << (n - 6)); }

@@ -15,12 +15,12 @@
 // removed per value read, while each step removes at least one table per
 // value, up to the budget.
 //
-// The passes of a grab may also run as two nested loops: an outer loop over
-// some of the pass PIs and an inner loop over the rest.  A table that reads
-// only outer pass PIs (and grab-level values) then runs once per outer
-// iteration.  Its set is planned the same way, starting from the grab-level
-// set, against the inner pass PIs; a value stays live across the inner loop
-// if it is read below its own level.
+// The passes of a grab may also run as nested loops, each over a group of
+// the pass PIs.  A table that reads no PI of a deeper loop (and only values
+// of its own or outer levels) then runs once per iteration of its loop.
+// Each level's set is planned the same way, starting from the set of the
+// level outside it, against the PIs of the deeper loops; a value stays live
+// across the deeper loops if it is read below its own level.
 #include <stdint.h>
 
 #include <algorithm>
@@ -187,39 +187,70 @@ uint64_t least_influential_pis(const LutProgram &lp, uint32_t k) {
   return m;
 }
 
-uint64_t choose_outer_pis(const LutProgram &lp, uint64_t pass_pis, bool force) {
+std::vector<uint64_t> choose_pass_groups(const LutProgram &lp, uint64_t pass_pis, int mode) {
   const uint32_t k = (uint32_t)__builtin_popcountll(pass_pis);
-  if (k < 2 || lp.order.empty()) return 0;
-  const std::vector<uint64_t> dep = table_support(lp);
   std::vector<uint32_t> bits;  // pass PIs in ascending order
   for (uint32_t p = 0; p < 64; p++)
     if ((pass_pis >> p) & 1u) bits.push_back(p);
-  // table evaluations per grab: grab-level tables once, outer-level ones
-  // 2^|outer| times, the rest 2^k times (hoisting limits ignored)
-  auto evals = [&](uint64_t outer) -> uint64_t {
-    uint64_t e = 0;
-    const uint64_t no = 1ull << __builtin_popcountll(outer), nk = 1ull << k;
-    for (uint64_t d : dep) {
-      const uint64_t pd = d & pass_pis;
-      e += pd == 0 ? 1 : (pd & ~outer) == 0 ? no : nk;
-    }
-    return e;
-  };
-  const uint64_t flat = evals(0);
-  uint64_t best = 0, best_e = flat;
-  for (uint32_t sub = 1; sub + 1 < (1u << k); sub++) {  // proper, non-empty subsets
-    uint64_t outer = 0;
-    for (uint32_t i = 0; i < k; i++)
-      if ((sub >> i) & 1u) outer |= 1ull << bits[i];
-    const uint64_t e = evals(outer);
-    if (e < best_e) {
-      best_e = e;
-      best = outer;
-    }
+  if (k < 2 || lp.order.empty() || mode == 0) return {pass_pis};
+  if (mode == 3) {  // one loop per pass PI, lowest outermost
+    std::vector<uint64_t> g;
+    for (uint32_t p : bits) g.push_back(1ull << p);
+    return g;
   }
-  if (force) return best ? best : pass_pis & (~pass_pis + 1);  // else the lowest pass PI alone
-  // a second loop level pays only for a clear saving
-  return best_e * 100 <= flat * 95 ? best : 0;
+  // tables by the pass PIs they depend on
+  const std::vector<uint64_t> dep = table_support(lp);
+  std::vector<uint64_t> count(1u << k, 0);
+  for (uint64_t d : dep) {
+    uint32_t m = 0;
+    for (uint32_t i = 0; i < k; i++)
+      if ((d >> bits[i]) & 1u) m |= 1u << i;
+    count[m]++;
+  }
+  // every ordered partition of the pass PIs into groups (a group index per
+  // PI, groups 0..L-1 all used); evaluations per grab: a table runs once per
+  // iteration of the loop of its deepest group, 2^(PIs in that group and the
+  // groups outside it) times
+  std::vector<uint32_t> gi(k, 0), best_gi(k, 0);
+  double best_score = -1;
+  uint32_t best_L = 1;
+  for (;;) {
+    uint32_t L = 0;
+    for (uint32_t i = 0; i < k; i++) L = std::max(L, gi[i] + 1);
+    std::vector<uint32_t> used(L, 0), prefix(L + 1, 0);
+    for (uint32_t i = 0; i < k; i++) used[gi[i]]++;
+    bool ok = true;
+    for (uint32_t l = 0; l < L; l++) ok = ok && used[l] > 0;
+    if (ok && !(mode == 2 && L < 2)) {
+      for (uint32_t l = 0; l < L; l++) prefix[l + 1] = prefix[l] + used[l];
+      double e = 0;
+      for (uint32_t m = 0; m < (1u << k); m++) {
+        if (!count[m]) continue;
+        if (m == 0) {
+          e += (double)count[m];
+          continue;
+        }
+        uint32_t deep = 0;
+        for (uint32_t i = 0; i < k; i++)
+          if ((m >> i) & 1u) deep = std::max(deep, gi[i]);
+        e += (double)count[m] * (double)(1u << prefix[deep + 1]);
+      }
+      // a loop level costs registers and loop overhead: take one only for
+      // a clear saving
+      const double score = e * (1.0 + 0.03 * (L - 1));
+      if (best_score < 0 || score < best_score) {
+        best_score = score;
+        best_gi = gi;
+        best_L = L;
+      }
+    }
+    uint32_t i = 0;  // next assignment (base-k counter)
+    while (i < k && ++gi[i] == k) gi[i++] = 0;
+    if (i == k) break;
+  }
+  std::vector<uint64_t> g(best_L, 0);
+  for (uint32_t i = 0; i < k; i++) g[best_gi[i]] |= 1ull << bits[i];
+  return g;
 }
 
 }  // namespace lec

@@ -56,7 +56,7 @@ struct JitState {
 namespace {
 
 constexpr int kJitBlock = 128;
-constexpr int kCodegenVersion = 11;  // part of cached cubin names: bump whenever the generated code changes
+constexpr int kCodegenVersion = 12;  // part of cached cubin names: bump whenever the generated code changes
 constexpr uint32_t kHoistBudget = 128;  // hoisted values read per pass kept in registers; see jit_layout
 constexpr uint32_t kHoistShared = 96;   // and more kept in shared memory (96 x 128 threads x 4 B = 48 KB,
                                         // the most a kernel may declare statically)
@@ -237,13 +237,15 @@ std::string gen_source(const Program &g, bool lut_form) {
 // a small pattern space keeps enough grabs to fill the GPU, which wins over
 // both.  The pass PIs are the support PIs (index >= 10) the fewest tables
 // depend on, so the most tables are the same in every pass of a grab.
-// The passes run as two nested loops when an outer loop over some pass PIs
-// saves enough table evaluations (choose_outer_pis).
+// The passes run as nested loops over groups of pass PIs when that saves
+// enough table evaluations (choose_pass_groups).
 // LEC_ES_JIT_REP / LEC_ES_JIT_HOIST override passes and budget,
 // LEC_ES_JIT_LOWPASS=1 takes PIs 10, 11, ... as the pass PIs and
-// LEC_ES_JIT_NEST=0 keeps one pass loop and =2 nests whenever there are two
-// pass PIs or more (for measurements and tests).
-void jit_layout(const Program &g, uint32_t *rep, uint32_t *budget, uint64_t *pass_pis, uint64_t *outer_pis) {
+// LEC_ES_JIT_NEST=0 keeps one pass loop, =2 nests whenever there are two
+// pass PIs or more, =3 gives every pass PI its own loop (for measurements
+// and tests).
+void jit_layout(const Program &g, uint32_t *rep, uint32_t *budget, uint64_t *pass_pis,
+                std::vector<uint64_t> *groups) {
   const uint32_t per = g.lut.count + 40;
   uint32_t r = 16;
   while (r < 32 && r * per < 4096) r <<= 1;
@@ -266,7 +268,7 @@ void jit_layout(const Program &g, uint32_t *rep, uint32_t *budget, uint64_t *pas
   *pass_pis = m;
   const char *nest = getenv("LEC_ES_JIT_NEST");
   const int nest_mode = nest ? atoi(nest) : 1;
-  *outer_pis = nest_mode == 0 ? 0 : choose_outer_pis(g.lut, m, nest_mode == 2);
+  *groups = choose_pass_groups(g.lut, m, nest_mode);
 }
 
 // Runs of consecutive chunk-index bits: (first bit, source bit, length).
@@ -296,24 +298,30 @@ std::vector<BitRun> bit_runs(const std::vector<uint32_t> &pos) {  // pos ascendi
 // warp stops at the end of its range or when its grab's lowest pattern is
 // not below the current counterexample; it also stops after max_grabs grabs.
 std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, uint32_t budget,
-                        uint64_t pass_pis, uint64_t outer_pis) {
+                        uint64_t pass_pis, const std::vector<uint64_t> &groups) {
   const LutProgram &lp = g.lut;
   const uint32_t NA = lp.na, NP = lp.np;
   const size_t NV = NA + NP + 1;
-  outer_pis &= pass_pis;
-  const uint64_t inner_pis = pass_pis & ~outer_pis;
-  const uint32_t REP_OUT = 1u << __builtin_popcountll(outer_pis), REP_IN = REP / REP_OUT;
+  // pass loops, outermost first: loop l (level l + 1) runs over the PIs of grp[l]
+  const std::vector<uint64_t> grp = groups.empty() ? std::vector<uint64_t>{pass_pis} : groups;
+  const uint32_t L = (uint32_t)grp.size();
   uint32_t roots = 0;
   const char *sh = getenv("LEC_ES_JIT_HOIST_SHARED");
   const uint32_t shared_budget = std::min<uint32_t>(sh ? (uint32_t)std::max(0, atoi(sh)) : kHoistShared, kHoistShared);
-  // level of each table: 0 once per grab, 1 once per outer pass (tables
-  // reading only outer pass PIs), 2 once per pass
-  std::vector<uint8_t> h0, h1;
-  plan_hoist(lp, pass_pis, budget + shared_budget, h0, &roots);
-  if (outer_pis) plan_hoist_from(lp, inner_pis, budget + shared_budget, h0, h1, &roots);
-  else h1 = h0;
-  std::vector<uint8_t> level(lp.order.size(), 2);
-  for (size_t i = 0; i < lp.order.size(); i++) level[i] = h0[i] ? 0 : h1[i] ? 1 : 2;
+  // level of each table: 0 once per grab, l once per iteration of pass
+  // loop l (tables reading no PI of a deeper loop), L once per pass
+  std::vector<uint8_t> level(lp.order.size(), (uint8_t)L), h, hn;
+  plan_hoist(lp, pass_pis, budget + shared_budget, h, &roots);
+  for (size_t i = 0; i < lp.order.size(); i++)
+    if (h[i]) level[i] = 0;
+  uint64_t deeper = pass_pis;
+  for (uint32_t l = 1; l < L; l++) {
+    deeper &= ~grp[l - 1];
+    plan_hoist_from(lp, deeper, budget + shared_budget, h, hn, &roots);
+    for (size_t i = 0; i < lp.order.size(); i++)
+      if (hn[i] && !h[i]) level[i] = (uint8_t)l;
+    h.swap(hn);
+  }
   // values read below their own level (live across a loop): the most read
   // stay in registers, the others go to shared memory (thread-private
   // slots, written where they are computed, loaded in each later section
@@ -327,16 +335,20 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
       if (v >= 0 && (uint32_t)v < NA && tpos[v] >= 0 && level[tpos[v]] < level[i]) pass_readers[tpos[v]]++;
     }
   }
-  if (lp.root >= 0 && lp.root < (int64_t)NA && tpos[lp.root] >= 0 && level[tpos[lp.root]] < 2) pass_readers[tpos[lp.root]]++;
-  // chunk-index bit positions of the inner and outer pass PIs and of the grab
+  if (lp.root >= 0 && lp.root < (int64_t)NA && tpos[lp.root] >= 0 && level[tpos[lp.root]] < L)
+    pass_readers[tpos[lp.root]]++;
+  // chunk-index bit positions of each pass loop's PIs and of the grab
   const uint32_t cbits = NP > 5 ? NP - 5 : 0;
-  std::vector<uint32_t> ipos, opos, gpos;
-  for (uint32_t b = 5; b < cbits; b++)
-    ((inner_pis >> (b + 5)) & 1u ? ipos : (outer_pis >> (b + 5)) & 1u ? opos : gpos).push_back(b);
+  std::vector<std::vector<uint32_t>> lpos(L);
+  std::vector<uint32_t> gpos;
   std::vector<int32_t> rank(64, -1);  // chunk bit -> rank among its group's bits
-  for (uint32_t i = 0; i < ipos.size(); i++) rank[ipos[i]] = (int32_t)i;
-  for (uint32_t i = 0; i < opos.size(); i++) rank[opos[i]] = (int32_t)i;
-  for (uint32_t i = 0; i < gpos.size(); i++) rank[gpos[i]] = (int32_t)i;
+  for (uint32_t b = 5; b < cbits; b++) {
+    std::vector<uint32_t> *to = &gpos;
+    for (uint32_t l = 0; l < L; l++)
+      if ((grp[l] >> (b + 5)) & 1u) to = &lpos[l];
+    rank[b] = (int32_t)to->size();
+    to->push_back(b);
+  }
   std::vector<int8_t> isconst(NV, 0);
   std::vector<uint32_t> cval(NV, 0);
   static const uint32_t mask[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
@@ -374,7 +386,8 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     << ".visible .entry es_jit(.param .u64 p_cb, .param .u64 p_ce, .param .u64 p_cex, .param .u64 p_ev,\n"
     << "    .param .u64 p_next, .param .u64 p_maxg, .param .u64 p_rep, .param .u64 p_q0, .param .u64 p_qend)\n"
     << ".maxntid " << kJitBlock << ", 1, 1\n{\n"
-    << "  .reg .pred %p<14>;\n  .reg .b32 %t<26>;\n  .reg .b64 %d<40>;\n"
+    << "  .reg .pred %p<14>;\n  .reg .b32 %t<26>;\n  .reg .b64 %d<40>;\n  .reg .b32 %j<" << L << ">;\n"
+    << "  .reg .b64 %o<" << L << ">;\n"
     << "  .reg .b32 %v<" << (NA + 1) << ">;\n  .reg .b32 %s<" << (NA + 1) << ">;\n  .reg .b32 %q<" << (NP + 1)
     << ">;\n";
   if (nsmem) s << "  .shared .align 16 .b32 hs[" << nsmem * kJitBlock << "];\n";
@@ -445,8 +458,8 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   // p12: every chunk of the grab lies in [cb, ce) -- its passes then skip
   // all range work and it counts its chunks at the end
   uint64_t span = 32;
-  for (uint32_t b : ipos) span += 1ull << b;
-  for (uint32_t b : opos) span += 1ull << b;
+  for (const auto &ps : lpos)
+    for (uint32_t b : ps) span += 1ull << b;
   snprintf(buf, sizeof(buf),
            "  add.u64 %%d34, %%d15, %llu;\n  setp.le.u64 %%p13, %%d34, %%d2;\n  setp.ge.u64 %%p12, %%d15, %%d1;\n"
            "  and.pred %%p12, %%p12, %%p13;\n",
@@ -483,6 +496,15 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
       }
     }
   };
+  auto close_loops = [&]() {  // loop ends of the outer pass loops, innermost first
+    std::string c;
+    for (uint32_t l = L - 1; l >= 1; l--) {
+      const std::string j = "%j" + std::to_string(l);
+      c += "  add.u32 " + j + ", " + j + ", 1;\n  setp.lt.u32 %p9, " + j + ", " +
+           std::to_string(1u << __builtin_popcountll(grp[l - 1])) + ";\n  @%p9 bra $LV" + std::to_string(l) + ";\n";
+    }
+    return c;
+  };
   auto emit_pass_pis = [&](uint64_t group, const char *idx) {
     for (uint32_t k = 10; k < NP; k++) {
       if (!pi_used[k] || !((group >> k) & 1u)) continue;
@@ -491,31 +513,34 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     }
   };
   emit_level(0);
-  // outer passes (when there are outer pass PIs): index in t24, chunk bits in d28
-  if (outer_pis) {
-    s << "  mov.u32 %t24, 0;\n$OUTER:\n  cvt.u64.u32 %d32, %t24;\n";
-    emit_deposit("%d28", "%d32", opos);
-    s << "  add.u64 %d33, %d15, %d28;\n";
-    emit_pass_pis(outer_pis, "%t24");
-    emit_level(1);
+  // outer pass loops l = 1..L-1: index in j<l>, first chunk of the
+  // iteration in o<l>
+  for (uint32_t l = 1; l < L; l++) {
+    const std::string j = "%j" + std::to_string(l);
+    s << "  mov.u32 " << j << ", 0;\n$LV" << l << ":\n  cvt.u64.u32 %d32, " << j << ";\n";
+    emit_deposit("%d28", "%d32", lpos[l - 1]);
+    s << "  add.u64 %o" << l << ", " << (l == 1 ? std::string("%d15") : "%o" + std::to_string(l - 1)) << ", %d28;\n";
+    emit_pass_pis(grp[l - 1], j.c_str());
+    emit_level((uint8_t)l);
   }
+  const std::string base = L == 1 ? std::string("%d15") : "%o" + std::to_string(L - 1);
   // passes: j in t20, its chunk bits in d29, the pass's first chunk d27;
   // outer passes do not run in chunk order, so a pass past the range is
   // skipped rather than ending the grab
   // this lane's chunk of the pass in d19 (first chunk of the pass in d27)
   auto emit_chunk = [&]() {
     s << "  cvt.u64.u32 %d31, %t20;\n";
-    emit_deposit("%d29", "%d31", ipos);
-    s << "  add.u64 %d27, " << (outer_pis ? "%d33" : "%d15") << ", %d29;\n";
+    emit_deposit("%d29", "%d31", lpos[L - 1]);
+    s << "  add.u64 %d27, " << base << ", %d29;\n";
   };
   s << "  mov.u32 %t20, 0;\n$PASS:\n  @%p12 bra $PBODY;\n";
   emit_chunk();
-  s << "  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra " << (outer_pis ? "$NEXTPASS" : "$GRABEND") << ";\n"
+  s << "  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra " << (L > 1 ? "$NEXTPASS" : "$GRABEND") << ";\n"
     << "  add.u64 %d22, %d27, 32;\n  setp.le.u64 %p10, %d22, %d1;\n  @%p10 bra $NEXTPASS;\n"
        "  add.u64 %d19, %d27, %d18;\n$PBODY:\n";
-  emit_pass_pis(inner_pis, "%t20");
-  emit_level(2);
-  if (lp.root >= 0) load_shared((int32_t)lp.root, 2);
+  emit_pass_pis(grp[L - 1], "%t20");
+  emit_level((uint8_t)L);
+  if (lp.root >= 0) load_shared((int32_t)lp.root, (uint8_t)L);
   const uint32_t vmask = g.n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << g.n)) - 1u);
   const std::string root = lp.root < 0 ? std::string("0") : name[lp.root];
   snprintf(buf, sizeof(buf), "  xor.b32 %%t7, %s, 0x%08x;\n  and.b32 %%t7, %%t7, 0x%08x;\n", root.c_str(),
@@ -535,10 +560,8 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
        "  cvt.u64.u32 %d21, %t12;\n  shl.b64 %d22, %d19, 5;\n  add.u64 %d22, %d22, %d21;\n"
        "  atom.global.min.u64 %d23, [%d3], %d22;\n"
        "$NEXTPASS:\n"
-       "  add.u32 %t20, %t20, 1;\n  setp.lt.u32 %p9, %t20, " + std::to_string(REP_IN) + ";\n  @%p9 bra $PASS;\n" +
-           (outer_pis ? "  add.u32 %t24, %t24, 1;\n  setp.lt.u32 %p9, %t24, " + std::to_string(REP_OUT) +
-                            ";\n  @%p9 bra $OUTER;\n"
-                      : std::string()) +
+       "  add.u32 %t20, %t20, 1;\n  setp.lt.u32 %p9, %t20, " + std::to_string(1u << __builtin_popcountll(grp[L - 1])) +
+           ";\n  @%p9 bra $PASS;\n" + close_loops() +
            "  @%p12 add.u64 %d10, %d10, " + std::to_string(REP) + ";\n"
            "$GRABEND:\n"
        "  mov.b64 {%t3, %t4}, %d16;\n  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n"
@@ -556,13 +579,22 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   }
   s << "  setp.ne.u64 %p8, %d10, 0;\n  and.pred %p8, %p8, %p1;\n  shl.b64 %d26, %d10, 5;\n"
        "  @%p8 red.global.add.u64 [%d4], %d26;\n  ret;\n}\n";
-  if (getenv("LEC_ES_JIT_LOG"))
+  if (getenv("LEC_ES_JIT_LOG")) {
+    std::string lv;
+    for (uint32_t l = 0; l <= L; l++) {
+      char t[64];
+      snprintf(t, sizeof(t), "%s%zu", l ? "/" : "", (size_t)std::count(level.begin(), level.end(), (uint8_t)l));
+      lv += t;
+      if (l < L) {
+        snprintf(t, sizeof(t), " [%llx] ", (unsigned long long)grp[l]);
+        lv += t;
+      }
+    }
     fprintf(stderr,
-            "lec_es JIT %016llx: %u tables, rep %u, pass PIs %016llx (outer %016llx), %zu per grab, %zu per outer "
-            "pass (%u read below their level, %u from shared memory)\n",
-            (unsigned long long)g.hash, lp.count, REP, (unsigned long long)pass_pis, (unsigned long long)outer_pis,
-            (size_t)std::count(level.begin(), level.end(), (uint8_t)0),
-            (size_t)std::count(level.begin(), level.end(), (uint8_t)1), roots, (unsigned)nsmem);
+            "lec_es JIT %016llx: %u tables, rep %u, pass PIs %016llx; tables per level: %s "
+            "(%u read below their level, %u from shared memory)\n",
+            (unsigned long long)g.hash, lp.count, REP, (unsigned long long)pass_pis, lv.c_str(), roots, (unsigned)nsmem);
+  }
   return s.str();
 }
 
@@ -615,12 +647,12 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
     // hoisted values live in registers across the passes: if ptxas has to
     // spill, halve the budget and build again
     uint32_t rep = 0, budget = 0;
-    uint64_t pass_pis = 0, outer_pis = 0;
-    jit_layout(g, &rep, &budget, &pass_pis, &outer_pis);
+    uint64_t pass_pis = 0;
+    std::vector<uint64_t> groups;
+    jit_layout(g, &rep, &budget, &pass_pis, &groups);
     for (;;) {
       std::string lg;
-      const int rc =
-          compile_ptx(gen_ptx_lut(g, major, minor, rep, budget, pass_pis, outer_pis), major, minor, cubin, lg);
+      const int rc = compile_ptx(gen_ptx_lut(g, major, minor, rep, budget, pass_pis, groups), major, minor, cubin, lg);
       const bool spills = rc == LEC_ES_OK && lg.find(" 0 bytes spill stores") == std::string::npos &&
                           lg.find("spill stores") != std::string::npos;
       if (rc != LEC_ES_OK || !spills || budget == 0) {
@@ -716,11 +748,14 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
     mkdir(c->jit_dir.c_str(), 0755);
     char name[160];
     uint32_t rep = 0, budget = 0;
-    uint64_t pass_pis = 0, outer_pis = 0;
-    jit_layout(g, &rep, &budget, &pass_pis, &outer_pis);
-    snprintf(name, sizeof(name), "/es_v%d_%016llx_%s%s_r%u_h%u_p%llx_o%llx_sm%d%d.cubin", kCodegenVersion,
+    uint64_t pass_pis = 0;
+    std::vector<uint64_t> groups;
+    jit_layout(g, &rep, &budget, &pass_pis, &groups);
+    uint64_t nest = 1469598103934665603ull;  // FNV-1a over the loop groups
+    for (uint64_t m : groups) nest = (nest ^ m) * 1099511628211ull;
+    snprintf(name, sizeof(name), "/es_v%d_%016llx_%s%s_r%u_h%u_p%llx_n%llx_sm%d%d.cubin", kCodegenVersion,
              (unsigned long long)g.hash, lut_form ? "lut" : "and", getenv("LEC_ES_JIT_NVRTC") ? "_nvrtc" : "", rep,
-             budget, (unsigned long long)pass_pis, (unsigned long long)outer_pis, c->cc_major, c->cc_minor);
+             budget, (unsigned long long)pass_pis, (unsigned long long)nest, c->cc_major, c->cc_minor);
     path = c->jit_dir + name;
   }
   double nvrtc_ms = 0;
@@ -762,8 +797,9 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   k->chunk_bits = g.n > 5 ? g.n - 5 : 0;
   if (lut_form && !g.lut.order.empty() && !getenv("LEC_ES_JIT_NVRTC")) {  // the PTX form: its grab layout
     uint32_t rep = 0, budget = 0;
-    uint64_t pass_pis = 0, outer_pis = 0;
-    jit_layout(g, &rep, &budget, &pass_pis, &outer_pis);
+    uint64_t pass_pis = 0;
+    std::vector<uint64_t> groups;
+    jit_layout(g, &rep, &budget, &pass_pis, &groups);
     k->rep_fixed = rep;
     k->pass_bits = pass_pis >> 5;
   }

@@ -242,7 +242,7 @@ def test_jit_compiles_for_sm103a_without_spills():
 
 
 @pytest.mark.parametrize("rep,hoist,nest", [("4", "0", "2"), ("16", "0", "1"), ("16", "64", "2"), ("32", "128", "1"),
-                                            ("16", "128", "0")])
+                                            ("16", "128", "0"), ("32", "128", "3")])
 def test_jit_grab_shapes_and_hoisting_compile_without_spills(rep, hoist, nest, monkeypatch):
     """Passes per grab, hoisted tables (values kept across the passes of a
     grab) and nested pass loops change the register demand; every shape

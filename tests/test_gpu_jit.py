@@ -140,8 +140,8 @@ def test_cached_kernel_skips_table_cover():
         L.lec_es_destroy(c)
 
 
-@pytest.mark.parametrize("rep,hoist,nest", [("4", "0", "2"), ("16", "64", "1"), ("32", "128", "2"), ("8", "16", "2"),
-                                            ("16", "128", "0"), ("16", "0", "2")])
+@pytest.mark.parametrize("rep,hoist,nest", [("4", "0", "2"), ("16", "64", "1"), ("32", "128", "2"), ("8", "16", "3"),
+                                            ("16", "128", "0"), ("16", "0", "2"), ("32", "128", "3")])
 def test_passes_per_grab_and_hoisted_tables_keep_results(rep, hoist, nest, monkeypatch):
     """Every grab shape, hoisting budget and pass-loop nesting gives the
     oracle's result, including word ranges that start and end off the grab
