@@ -107,8 +107,11 @@ uint64_t least_influential_pis(const LutProgram &lp, uint32_t k);
 // Nested pass loops: the pass PIs split into groups, outermost loop first,
 // chosen to minimise table evaluations per grab, each extra loop level
 // charged 3%.  mode 0: one loop; 1: chosen; 2: chosen among two levels or
-// more; 3: one loop per pass PI.
-std::vector<uint64_t> choose_pass_groups(const LutProgram &lp, uint64_t pass_pis, int mode);
+// more; 3: one loop per pass PI.  *score: the chosen nesting's table
+// evaluations per grab (with the level charge; for modes 0 and 3, those of
+// one loop).
+std::vector<uint64_t> choose_pass_groups(const LutProgram &lp, uint64_t pass_pis, int mode,
+                                         double *score = nullptr);
 
 // Words of 64 patterns for a support of n PIs.
 inline uint64_t num_words(uint32_t n) { return n <= 6 ? 1ull : (1ull << (n - 6)); }

@@ -187,17 +187,11 @@ uint64_t least_influential_pis(const LutProgram &lp, uint32_t k) {
   return m;
 }
 
-std::vector<uint64_t> choose_pass_groups(const LutProgram &lp, uint64_t pass_pis, int mode) {
+std::vector<uint64_t> choose_pass_groups(const LutProgram &lp, uint64_t pass_pis, int mode, double *score_out) {
   const uint32_t k = (uint32_t)__builtin_popcountll(pass_pis);
   std::vector<uint32_t> bits;  // pass PIs in ascending order
   for (uint32_t p = 0; p < 64; p++)
     if ((pass_pis >> p) & 1u) bits.push_back(p);
-  if (k < 2 || lp.order.empty() || mode == 0) return {pass_pis};
-  if (mode == 3) {  // one loop per pass PI, lowest outermost
-    std::vector<uint64_t> g;
-    for (uint32_t p : bits) g.push_back(1ull << p);
-    return g;
-  }
   // tables by the pass PIs they depend on
   const std::vector<uint64_t> dep = table_support(lp);
   std::vector<uint64_t> count(1u << k, 0);
@@ -207,33 +201,38 @@ std::vector<uint64_t> choose_pass_groups(const LutProgram &lp, uint64_t pass_pis
       if ((d >> bits[i]) & 1u) m |= 1u << i;
     count[m]++;
   }
-  // every ordered partition of the pass PIs into groups (a group index per
-  // PI, groups 0..L-1 all used); evaluations per grab: a table runs once per
-  // iteration of the loop of its deepest group, 2^(PIs in that group and the
-  // groups outside it) times
-  std::vector<uint32_t> gi(k, 0), best_gi(k, 0);
+  if (score_out) {  // one loop: grab-level tables once, the others 2^k times
+    *score_out = 0;
+    for (uint32_t m = 0; m < (1u << k); m++) *score_out += (double)count[m] * (m ? (double)(1u << k) : 1.0);
+  }
+  if (k < 2 || lp.order.empty() || mode == 0) return {pass_pis};
+  if (mode == 3) {  // one loop per pass PI, lowest outermost
+    std::vector<uint64_t> g;
+    for (uint32_t p : bits) g.push_back(1ull << p);
+    return g;
+  }
+  // every ordered partition of the pass PIs into at most four groups (a
+  // group index per PI, groups 0..L-1 all used); evaluations per grab: a
+  // table runs once per iteration of the loop of its deepest group, 2^(PIs
+  // in that group and the groups outside it) times
+  const uint32_t G = std::min<uint32_t>(k, 4);
+  std::vector<uint32_t> gi(k, 0), best_gi(k, 0), deep(1u << k, 0);
   double best_score = -1;
   uint32_t best_L = 1;
   for (;;) {
     uint32_t L = 0;
     for (uint32_t i = 0; i < k; i++) L = std::max(L, gi[i] + 1);
-    std::vector<uint32_t> used(L, 0), prefix(L + 1, 0);
+    uint32_t used[4] = {0, 0, 0, 0}, prefix[5] = {0, 0, 0, 0, 0};
     for (uint32_t i = 0; i < k; i++) used[gi[i]]++;
     bool ok = true;
     for (uint32_t l = 0; l < L; l++) ok = ok && used[l] > 0;
     if (ok && !(mode == 2 && L < 2)) {
       for (uint32_t l = 0; l < L; l++) prefix[l + 1] = prefix[l] + used[l];
-      double e = 0;
-      for (uint32_t m = 0; m < (1u << k); m++) {
-        if (!count[m]) continue;
-        if (m == 0) {
-          e += (double)count[m];
-          continue;
-        }
-        uint32_t deep = 0;
-        for (uint32_t i = 0; i < k; i++)
-          if ((m >> i) & 1u) deep = std::max(deep, gi[i]);
-        e += (double)count[m] * (double)(1u << prefix[deep + 1]);
+      double e = (double)count[0];
+      for (uint32_t m = 1; m < (1u << k); m++) {  // deepest group of m from m without its lowest PI
+        const uint32_t i = (uint32_t)__builtin_ctz(m);
+        deep[m] = std::max(deep[m & (m - 1)], gi[i]);
+        if (count[m]) e += (double)count[m] * (double)(1u << prefix[deep[m] + 1]);
       }
       // a loop level costs registers and loop overhead: take one only for
       // a clear saving
@@ -244,12 +243,13 @@ std::vector<uint64_t> choose_pass_groups(const LutProgram &lp, uint64_t pass_pis
         best_L = L;
       }
     }
-    uint32_t i = 0;  // next assignment (base-k counter)
-    while (i < k && ++gi[i] == k) gi[i++] = 0;
+    uint32_t i = 0;  // next assignment (base-G counter)
+    while (i < k && ++gi[i] == G) gi[i++] = 0;
     if (i == k) break;
   }
   std::vector<uint64_t> g(best_L, 0);
   for (uint32_t i = 0; i < k; i++) g[best_gi[i]] |= 1ull << bits[i];
+  if (score_out) *score_out = best_score;
   return g;
 }
 

@@ -56,10 +56,14 @@ struct JitState {
 namespace {
 
 constexpr int kJitBlock = 128;
-constexpr int kCodegenVersion = 12;  // part of cached cubin names: bump whenever the generated code changes
-constexpr uint32_t kHoistBudget = 128;  // hoisted values read per pass kept in registers; see jit_layout
-constexpr uint32_t kHoistShared = 96;   // and more kept in shared memory (96 x 128 threads x 4 B = 48 KB,
-                                        // the most a kernel may declare statically)
+constexpr int kCodegenVersion = 15;  // part of cached cubin names: bump whenever the generated code changes
+// Values computed at one loop level and read at a deeper one: at most
+// kHoistPlan of them (see plan_hoist), those read by the innermost loop in
+// registers, the others in up to kHoistShared shared-memory slots per
+// thread (96 x 128 threads x 4 B = 48 KB, the most a kernel may declare
+// statically).
+constexpr uint32_t kHoistPlan = 224;
+constexpr uint32_t kHoistShared = 96;
 constexpr uint64_t kGrabsWanted = 4 * 148 * 8;  // four grabs per warp at 8 warps on each of 148 SMs
 constexpr uint32_t kMaxJitLive = 230;        // table live set that still fits the register file
 
@@ -241,19 +245,45 @@ std::string gen_source(const Program &g, bool lut_form) {
 // enough table evaluations (choose_pass_groups).
 // LEC_ES_JIT_REP / LEC_ES_JIT_HOIST override passes and budget,
 // LEC_ES_JIT_LOWPASS=1 takes PIs 10, 11, ... as the pass PIs and
+// The grab layout of a table-form kernel (jit_layout).
+struct GrabLayout {
+  uint32_t rep = 0;
+  uint32_t regs = 0;  // values read below their level that may stay in registers
+  uint32_t plan = 0;  // values read below their level, in all (plan_hoist's budget)
+  uint64_t pass_pis = 0;
+  std::vector<uint64_t> groups;
+};
+// Slots of one generated kernel: values read below their level, how many in
+// registers and how many in shared memory.
+struct SlotSplit {
+  uint32_t read = 0, in_regs = 0, in_shared = 0;
+  uint32_t inner_in_regs = 0;  // of those in registers, values the innermost loop reads
+};
+// shared-memory slots per thread (LEC_ES_JIT_HOIST_SHARED lowers it)
+uint32_t shared_slots() {
+  const char *sh = getenv("LEC_ES_JIT_HOIST_SHARED");
+  return std::min<uint32_t>(sh ? (uint32_t)std::max(0, atoi(sh)) : kHoistShared, kHoistShared);
+}
+
 // LEC_ES_JIT_NEST=0 keeps one pass loop, =2 nests whenever there are two
 // pass PIs or more, =3 gives every pass PI its own loop (for measurements
 // and tests).
-void jit_layout(const Program &g, uint32_t *rep, uint32_t *budget, uint64_t *pass_pis,
-                std::vector<uint64_t> *groups) {
+void jit_layout(const Program &g, GrabLayout *out) {
+  uint64_t *const pass_pis = &out->pass_pis;
+  std::vector<uint64_t> *const groups = &out->groups;
   const uint32_t per = g.lut.count + 40;
   uint32_t r = 16;
   while (r < 32 && r * per < 4096) r <<= 1;
   const uint64_t chunks = num_chunks(g.n);
   while (r > 1 && chunks / (32ull * r) < kGrabsWanted) r >>= 1;
-  uint32_t h = kHoistBudget;
+  // LEC_ES_JIT_HOIST=h: at most h values in registers, the plan h plus the
+  // shared-memory slots
+  uint32_t regs = 255, plan = kHoistPlan;
   if (const char *e = getenv("LEC_ES_JIT_REP")) r = (uint32_t)std::max(1, atoi(e));
-  if (const char *e = getenv("LEC_ES_JIT_HOIST")) h = (uint32_t)std::max(0, atoi(e));
+  if (const char *e = getenv("LEC_ES_JIT_HOIST")) {
+    regs = (uint32_t)std::max(0, atoi(e));
+    plan = regs + shared_slots();
+  }
   uint32_t npass = 0;
   while ((1u << (npass + 1)) <= r && npass < 10) npass++;
   npass = std::min<uint32_t>(npass, g.n > 10 ? g.n - 10 : 0);  // pass PIs are support PIs 10..n-1
@@ -263,13 +293,64 @@ void jit_layout(const Program &g, uint32_t *rep, uint32_t *budget, uint64_t *pas
   } else {
     m = least_influential_pis(g.lut, npass);
   }
-  *rep = 1u << npass;
-  *budget = h;
-  *pass_pis = m;
   const char *nest = getenv("LEC_ES_JIT_NEST");
   const int nest_mode = nest ? atoi(nest) : 1;
-  *groups = choose_pass_groups(g.lut, m, nest_mode);
+  double score = 0;
+  *groups = choose_pass_groups(g.lut, m, nest_mode, &score);
+  // With nested loops, a pass PI in a loop of its own outside the others
+  // never makes a table run more often and halves the grab-level tables
+  // that do not read it: add up to two more pass PIs (six at most), each
+  // the best of the next six least influential, while table evaluations
+  // per pass fall by 2% and enough grabs remain.
+  if (nest_mode != 0 && !getenv("LEC_ES_JIT_REP") && !getenv("LEC_ES_JIT_LOWPASS")) {
+    for (uint32_t k = npass + 1; k <= npass + 2 && k <= 6 && g.n > 10 && k <= g.n - 10; k++) {
+      if (chunks / (32ull << k) < kGrabsWanted) break;
+      const uint64_t cand = least_influential_pis(g.lut, std::min<uint32_t>(k + 5, g.n - 10)) & ~m;
+      uint64_t best_m = 0;
+      double best_s = 0;
+      std::vector<uint64_t> best_g;
+      for (uint32_t p = 0; p < 64; p++) {
+        if (!((cand >> p) & 1u)) continue;
+        double sk = 0;
+        std::vector<uint64_t> gk = choose_pass_groups(g.lut, m | (1ull << p), nest_mode, &sk);
+        if (!best_m || sk < best_s) {
+          best_m = m | (1ull << p);
+          best_s = sk;
+          best_g = std::move(gk);
+        }
+      }
+      if (!best_m || best_s / (double)(1u << k) >= 0.98 * score / (double)(1u << npass)) break;
+      npass = k;
+      m = best_m;
+      score = best_s;
+      *groups = std::move(best_g);
+    }
+  }
+  out->rep = 1u << npass;
+  out->regs = regs;
+  out->plan = plan;
+  *pass_pis = m;
 }
+
+// 3-input truth tables (bit m = f(x0 = m&1, x1 = m>>1&1, x2 = m>>2&1)):
+// input k complemented, fixed to b, or made equal to input a.
+uint8_t tt_flip(uint8_t tt, int k) {
+  uint8_t r = 0;
+  for (int m = 0; m < 8; m++) r |= (uint8_t)(((tt >> (m ^ (1 << k))) & 1) << m);
+  return r;
+}
+uint8_t tt_fix(uint8_t tt, int k, int b) {
+  uint8_t r = 0;
+  for (int m = 0; m < 8; m++) r |= (uint8_t)(((tt >> ((m & ~(1 << k)) | (b << k))) & 1) << m);
+  return r;
+}
+uint8_t tt_same(uint8_t tt, int a, int k) {  // x_k := x_a
+  uint8_t r = 0;
+  for (int m = 0; m < 8; m++) r |= (uint8_t)(((tt >> ((m & ~(1 << k)) | (((m >> a) & 1) << k))) & 1) << m);
+  return r;
+}
+bool tt_reads(uint8_t tt, int k) { return tt_flip(tt, k) != tt; }
+constexpr uint8_t kVarTT[3] = {0xAA, 0xCC, 0xF0};
 
 // Runs of consecutive chunk-index bits: (first bit, source bit, length).
 struct BitRun {
@@ -297,8 +378,9 @@ std::vector<BitRun> bit_runs(const std::vector<uint32_t> &pos) {  // pos ascendi
 // the others once per pass.  Grabs and passes increase in chunk index, so a
 // warp stops at the end of its range or when its grab's lowest pattern is
 // not below the current counterexample; it also stops after max_grabs grabs.
-std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, uint32_t budget,
-                        uint64_t pass_pis, const std::vector<uint64_t> &groups) {
+std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, uint32_t reg_budget,
+                        uint32_t plan_budget, uint64_t pass_pis, const std::vector<uint64_t> &groups,
+                        SlotSplit *split = nullptr) {
   const LutProgram &lp = g.lut;
   const uint32_t NA = lp.na, NP = lp.np;
   const size_t NV = NA + NP + 1;
@@ -306,18 +388,17 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   const std::vector<uint64_t> grp = groups.empty() ? std::vector<uint64_t>{pass_pis} : groups;
   const uint32_t L = (uint32_t)grp.size();
   uint32_t roots = 0;
-  const char *sh = getenv("LEC_ES_JIT_HOIST_SHARED");
-  const uint32_t shared_budget = std::min<uint32_t>(sh ? (uint32_t)std::max(0, atoi(sh)) : kHoistShared, kHoistShared);
+  const uint32_t shared_budget = shared_slots();
   // level of each table: 0 once per grab, l once per iteration of pass
   // loop l (tables reading no PI of a deeper loop), L once per pass
   std::vector<uint8_t> level(lp.order.size(), (uint8_t)L), h, hn;
-  plan_hoist(lp, pass_pis, budget + shared_budget, h, &roots);
+  plan_hoist(lp, pass_pis, plan_budget, h, &roots);
   for (size_t i = 0; i < lp.order.size(); i++)
     if (h[i]) level[i] = 0;
   uint64_t deeper = pass_pis;
   for (uint32_t l = 1; l < L; l++) {
     deeper &= ~grp[l - 1];
-    plan_hoist_from(lp, deeper, budget + shared_budget, h, hn, &roots);
+    plan_hoist_from(lp, deeper, plan_budget, h, hn, &roots);
     for (size_t i = 0; i < lp.order.size(); i++)
       if (hn[i] && !h[i]) level[i] = (uint8_t)l;
     h.swap(hn);
@@ -372,14 +453,44 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     isconst[l.node] = 1;
     cval[l.node] = r;
   }
+  // a value in shared memory is loaded once in every run of each section
+  // that reads it (runs per grab of a level-l section: 2^(PIs of loops
+  // 1..l)): registers go to the values the innermost loop reads, most
+  // loaded first, up to reg_budget; the others take shared-memory slots
+  std::vector<double> runs(L + 1, 1.0);
+  for (uint32_t l = 1; l <= L; l++) runs[l] = runs[l - 1] * (double)(1u << __builtin_popcountll(grp[l - 1]));
+  std::vector<double> load_cost(lp.order.size(), 0.0);
+  std::vector<uint32_t> read_at(lp.order.size(), 0);  // bit l: read by a level-l section
+  {
+    for (size_t i = 0; i < lp.order.size(); i++)
+      for (int k = 0; k < lp.order[i].n; k++) {
+        const int32_t v = lp.order[i].leaf[k];
+        if (v >= 0 && (uint32_t)v < NA && tpos[v] >= 0 && level[tpos[v]] < level[i]) read_at[tpos[v]] |= 1u << level[i];
+      }
+    if (lp.root >= 0 && lp.root < (int64_t)NA && tpos[lp.root] >= 0 && level[tpos[lp.root]] < L)
+      read_at[tpos[lp.root]] |= 1u << L;
+    for (size_t i = 0; i < lp.order.size(); i++)
+      for (uint32_t l = 1; l <= L; l++)
+        if ((read_at[i] >> l) & 1u) load_cost[i] += runs[l];
+  }
   std::vector<int32_t> read_roots;
   for (size_t i = 0; i < lp.order.size(); i++)
     if (pass_readers[i] && !isconst[lp.order[i].node]) read_roots.push_back((int32_t)i);  // constants are immediates
-  std::stable_sort(read_roots.begin(), read_roots.end(),
-                   [&](int32_t x, int32_t y) { return pass_readers[x] > pass_readers[y]; });
+  std::stable_sort(read_roots.begin(), read_roots.end(), [&](int32_t x, int32_t y) {
+    return load_cost[x] > load_cost[y] || (load_cost[x] == load_cost[y] && pass_readers[x] > pass_readers[y]);
+  });
+  uint32_t inner = 0;  // read by the innermost loop: sorted first (their loads run most often)
+  for (int32_t i : read_roots) inner += (read_at[i] >> L) & 1u;
+  const uint32_t in_regs = std::min<uint32_t>(reg_budget, inner);
   std::vector<int32_t> smem_slot(lp.order.size(), -1);
   uint32_t nsmem = 0;
-  for (size_t r = budget; r < read_roots.size() && nsmem < shared_budget; r++) smem_slot[read_roots[r]] = (int32_t)nsmem++;
+  for (size_t r = in_regs; r < read_roots.size() && nsmem < shared_budget; r++) smem_slot[read_roots[r]] = (int32_t)nsmem++;
+  if (split) {
+    split->read = (uint32_t)read_roots.size();
+    split->in_regs = (uint32_t)read_roots.size() - nsmem;
+    split->in_shared = nsmem;
+    split->inner_in_regs = in_regs;
+  }
   std::ostringstream s;
   char buf[192];
   s << ".version 9.0\n.target sm_" << major << minor << "a\n.address_size 64\n\n"
@@ -533,37 +644,181 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     emit_deposit("%d29", "%d31", lpos[L - 1]);
     s << "  add.u64 %d27, " << base << ", %d29;\n";
   };
-  s << "  mov.u32 %t20, 0;\n$PASS:\n  @%p12 bra $PBODY;\n";
-  emit_chunk();
-  s << "  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra " << (L > 1 ? "$NEXTPASS" : "$GRABEND") << ";\n"
-    << "  add.u64 %d22, %d27, 32;\n  setp.le.u64 %p10, %d22, %d1;\n  @%p10 bra $NEXTPASS;\n"
-       "  add.u64 %d19, %d27, %d18;\n$PBODY:\n";
-  emit_pass_pis(grp[L - 1], "%t20");
-  emit_level((uint8_t)L);
-  if (lp.root >= 0) load_shared((int32_t)lp.root, (uint8_t)L);
-  const uint32_t vmask = g.n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << g.n)) - 1u);
-  const std::string root = lp.root < 0 ? std::string("0") : name[lp.root];
-  snprintf(buf, sizeof(buf), "  xor.b32 %%t7, %s, 0x%08x;\n  and.b32 %%t7, %%t7, 0x%08x;\n", root.c_str(),
-           g.out_compl ? 0xFFFFFFFFu : 0u, vmask);
-  s << buf;
-  // in a partial grab, chunks outside [cb, ce) neither fail nor count
-  s << "  @%p12 bra $CHECK;\n"
-       "  setp.ge.u64 %p5, %d19, %d2;\n  setp.lt.u64 %p11, %d19, %d1;\n  or.pred %p5, %p5, %p11;\n"
-       "  @%p5 mov.b32 %t7, 0;\n  selp.u64 %d24, 0, 1, %p5;\n  add.u64 %d10, %d10, %d24;\n"
-       "$CHECK:\n  setp.ne.u32 %p6, %t7, 0;\n"
-       "  vote.sync.ballot.b32 %t8, %p6, -1;\n  setp.eq.u32 %p7, %t8, 0;\n  @%p7 bra $NEXTPASS;\n"
-       "  neg.s32 %t9, %t8;\n  and.b32 %t9, %t9, %t8;\n  bfind.u32 %t10, %t9;\n"
-       "  setp.ne.u32 %p7, %t10, %t2;\n  @%p7 bra $NEXTPASS;\n";
-  emit_chunk();  // a failing pass (rare) recomputes its chunk
-  s << "  add.u64 %d19, %d27, %d18;\n"
-       "  neg.s32 %t11, %t7;\n  and.b32 %t11, %t11, %t7;\n  bfind.u32 %t12, %t11;\n"
-       "  cvt.u64.u32 %d21, %t12;\n  shl.b64 %d22, %d19, 5;\n  add.u64 %d22, %d22, %d21;\n"
-       "  atom.global.min.u64 %d23, [%d3], %d22;\n"
-       "$NEXTPASS:\n"
-       "  add.u32 %t20, %t20, 1;\n  setp.lt.u32 %p9, %t20, " + std::to_string(1u << __builtin_popcountll(grp[L - 1])) +
-           ";\n  @%p9 bra $PASS;\n" + close_loops() +
-           "  @%p12 add.u64 %d10, %d10, " + std::to_string(REP) + ";\n"
-           "$GRABEND:\n"
+  const uint32_t ninner = 1u << __builtin_popcountll(grp[L - 1]);
+  const size_t inner_tables = (size_t)std::count(level.begin(), level.end(), (uint8_t)L);
+  const char *unroll_env = getenv("LEC_ES_JIT_UNROLL");
+  const bool unroll = (unroll_env ? atoi(unroll_env) != 0 : true) && ninner <= 4 && inner_tables * ninner <= 4096;
+  if (unroll) {
+    // The innermost loop unrolled: one copy per value of its pass PIs, in
+    // which those PIs are the constants 0 or all-ones.  Through each copy
+    // they propagate: a table reading one is cofactored, complements fold
+    // into the readers' tables, a table left with one input becomes an alias
+    // and one left with none a constant -- the same Boolean functions with
+    // fewer instructions.
+    struct SVal {
+      bool imm = false;  // an immediate (imm) or a register (reg, complemented if inv)
+      bool inv = false;
+      uint32_t imm_v = 0;
+      std::string reg;
+    };
+    std::vector<uint32_t> ipis;  // the innermost pass PIs in rank order (ascending)
+    for (uint32_t k = 10; k < NP; k++)
+      if ((grp[L - 1] >> k) & 1u) ipis.push_back(k);
+    std::vector<SVal> sv(NV);
+    for (uint32_t j = 0; j < ninner; j++) {
+      const std::string J = std::to_string(j);
+      uint64_t off = 0;  // chunk offset of this copy's pass
+      for (uint32_t r = 0; r < lpos[L - 1].size(); r++)
+        if ((j >> r) & 1u) off |= 1ull << lpos[L - 1][r];
+      const std::string chunk = "  add.u64 %d27, " + base + ", " + std::to_string(off) + ";\n";
+      s << "  @%p12 bra $PB" << J << ";\n" << chunk << "  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra $NX" << J
+        << ";\n  add.u64 %d22, %d27, 32;\n  setp.le.u64 %p10, %d22, %d1;\n  @%p10 bra $NX" << J
+        << ";\n  add.u64 %d19, %d27, %d18;\n$PB" << J << ":\n";
+      std::fill(loaded.begin(), loaded.end(), (uint8_t)0);
+      auto value = [&](int32_t v) -> SVal {  // a leaf's value in this copy
+        SVal x;
+        if (v < 0 || isconst[v]) {
+          x.imm = true;
+          x.imm_v = v < 0 ? 0u : cval[v];
+          return x;
+        }
+        if ((uint32_t)v >= NA) {
+          const uint32_t k = (uint32_t)v - NA;
+          for (uint32_t r = 0; r < ipis.size(); r++)
+            if (ipis[r] == k) {
+              x.imm = true;
+              x.imm_v = (j >> r) & 1u ? 0xFFFFFFFFu : 0u;
+              return x;
+            }
+          x.reg = name[v];
+          return x;
+        }
+        if (tpos[v] >= 0 && level[tpos[v]] == L) return sv[v];
+        load_shared(v, (uint8_t)L);
+        x.reg = name[v];
+        return x;
+      };
+      for (size_t i = 0; i < lp.order.size(); i++) {
+        const LutCover::Lut &l = lp.order[i];
+        if (level[i] != L || isconst[l.node]) continue;
+        SVal op[3];
+        bool live[3] = {false, false, false};
+        uint8_t tt = l.tt;
+        for (int k = 0; k < 3; k++) {
+          op[k] = value(k < l.n ? l.leaf[k] : -1);
+          live[k] = true;
+          if (!op[k].imm && op[k].inv) tt = tt_flip(tt, k);
+          if (op[k].imm && (op[k].imm_v == 0u || op[k].imm_v == 0xFFFFFFFFu)) {
+            tt = tt_fix(tt, k, op[k].imm_v != 0);
+            live[k] = false;
+          }
+        }
+        for (int a = 0; a < 3; a++)
+          for (int k = a + 1; k < 3; k++)
+            if (live[a] && live[k] && op[a].imm == op[k].imm &&
+                (op[a].imm ? op[a].imm_v == op[k].imm_v : op[a].reg == op[k].reg)) {
+              tt = tt_same(tt, a, k);
+              live[k] = false;
+            }
+        int nlive = 0, nreg = 0, last = -1;
+        for (int k = 0; k < 3; k++) {
+          live[k] = live[k] && tt_reads(tt, k);
+          if (live[k]) {
+            nlive++;
+            nreg += !op[k].imm;
+            last = k;
+          }
+        }
+        SVal res;
+        if (nreg == 0) {  // every input a constant: evaluate bitwise
+          res.imm = true;
+          for (int b = 0; b < 32; b++) {
+            int m = 0;
+            for (int k = 0; k < 3; k++)
+              if (live[k]) m |= (int)((op[k].imm_v >> b) & 1u) << k;
+            res.imm_v |= (uint32_t)((tt >> m) & 1) << b;
+          }
+        } else if (nlive == 1 && (tt == kVarTT[last] || tt == (uint8_t)~kVarTT[last])) {
+          res.reg = op[last].reg;  // an alias of its input, or of its complement
+          res.inv = tt != kVarTT[last];
+        } else {
+          res.reg = "%v" + std::to_string(l.node);
+          std::string x[3];
+          for (int k = 0; k < 3; k++) {
+            if (!live[k]) x[k] = "0";
+            else if (op[k].imm) {
+              snprintf(buf, sizeof(buf), "0x%08x", op[k].imm_v);
+              x[k] = buf;
+            } else {
+              x[k] = op[k].reg;
+            }
+          }
+          snprintf(buf, sizeof(buf), "  lop3.b32 %s, %s, %s, %s, 0x%02x;\n", res.reg.c_str(), x[2].c_str(),
+                   x[1].c_str(), x[0].c_str(), tt);
+          s << buf;
+        }
+        sv[l.node] = res;
+      }
+      // the miter output of this copy (t7), then the same check as a pass
+      const uint32_t vmask = g.n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << g.n)) - 1u);
+      const SVal out = value(lp.root < 0 ? -1 : (int32_t)lp.root);
+      const bool never = out.imm && ((out.imm_v ^ (g.out_compl ? 0xFFFFFFFFu : 0u)) & vmask) == 0;
+      if (out.imm) {
+        snprintf(buf, sizeof(buf), "  mov.b32 %%t7, 0x%08x;\n", (out.imm_v ^ (g.out_compl ? 0xFFFFFFFFu : 0u)) & vmask);
+      } else {
+        snprintf(buf, sizeof(buf), "  xor.b32 %%t7, %s, 0x%08x;\n  and.b32 %%t7, %%t7, 0x%08x;\n", out.reg.c_str(),
+                 (out.inv != (g.out_compl != 0)) ? 0xFFFFFFFFu : 0u, vmask);
+      }
+      s << buf;
+      s << "  @%p12 bra $CK" << J << ";\n"
+        << "  setp.ge.u64 %p5, %d19, %d2;\n  setp.lt.u64 %p11, %d19, %d1;\n  or.pred %p5, %p5, %p11;\n"
+           "  @%p5 mov.b32 %t7, 0;\n  selp.u64 %d24, 0, 1, %p5;\n  add.u64 %d10, %d10, %d24;\n"
+        << "$CK" << J << ":\n";
+      if (!never) {  // a copy whose output is the constant 0 cannot fail
+        s << "  setp.ne.u32 %p6, %t7, 0;\n  vote.sync.ballot.b32 %t8, %p6, -1;\n  setp.eq.u32 %p7, %t8, 0;\n"
+          << "  @%p7 bra $NX" << J << ";\n"
+          << "  neg.s32 %t9, %t8;\n  and.b32 %t9, %t9, %t8;\n  bfind.u32 %t10, %t9;\n"
+          << "  setp.ne.u32 %p7, %t10, %t2;\n  @%p7 bra $NX" << J << ";\n"
+          << chunk
+          << "  add.u64 %d19, %d27, %d18;\n"
+             "  neg.s32 %t11, %t7;\n  and.b32 %t11, %t11, %t7;\n  bfind.u32 %t12, %t11;\n"
+             "  cvt.u64.u32 %d21, %t12;\n  shl.b64 %d22, %d19, 5;\n  add.u64 %d22, %d22, %d21;\n"
+             "  atom.global.min.u64 %d23, [%d3], %d22;\n";
+      }
+      s << "$NX" << J << ":\n";
+    }
+  } else {
+    s << "  mov.u32 %t20, 0;\n$PASS:\n  @%p12 bra $PBODY;\n";
+    emit_chunk();
+    s << "  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra " << (L > 1 ? "$NEXTPASS" : "$GRABEND") << ";\n"
+      << "  add.u64 %d22, %d27, 32;\n  setp.le.u64 %p10, %d22, %d1;\n  @%p10 bra $NEXTPASS;\n"
+         "  add.u64 %d19, %d27, %d18;\n$PBODY:\n";
+    emit_pass_pis(grp[L - 1], "%t20");
+    emit_level((uint8_t)L);
+    if (lp.root >= 0) load_shared((int32_t)lp.root, (uint8_t)L);
+    const uint32_t vmask = g.n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << g.n)) - 1u);
+    const std::string root = lp.root < 0 ? std::string("0") : name[lp.root];
+    snprintf(buf, sizeof(buf), "  xor.b32 %%t7, %s, 0x%08x;\n  and.b32 %%t7, %%t7, 0x%08x;\n", root.c_str(),
+             g.out_compl ? 0xFFFFFFFFu : 0u, vmask);
+    s << buf;
+    // in a partial grab, chunks outside [cb, ce) neither fail nor count
+    s << "  @%p12 bra $CHECK;\n"
+         "  setp.ge.u64 %p5, %d19, %d2;\n  setp.lt.u64 %p11, %d19, %d1;\n  or.pred %p5, %p5, %p11;\n"
+         "  @%p5 mov.b32 %t7, 0;\n  selp.u64 %d24, 0, 1, %p5;\n  add.u64 %d10, %d10, %d24;\n"
+         "$CHECK:\n  setp.ne.u32 %p6, %t7, 0;\n"
+         "  vote.sync.ballot.b32 %t8, %p6, -1;\n  setp.eq.u32 %p7, %t8, 0;\n  @%p7 bra $NEXTPASS;\n"
+         "  neg.s32 %t9, %t8;\n  and.b32 %t9, %t9, %t8;\n  bfind.u32 %t10, %t9;\n"
+         "  setp.ne.u32 %p7, %t10, %t2;\n  @%p7 bra $NEXTPASS;\n";
+    emit_chunk();  // a failing pass (rare) recomputes its chunk
+    s << "  add.u64 %d19, %d27, %d18;\n"
+         "  neg.s32 %t11, %t7;\n  and.b32 %t11, %t11, %t7;\n  bfind.u32 %t12, %t11;\n"
+         "  cvt.u64.u32 %d21, %t12;\n  shl.b64 %d22, %d19, 5;\n  add.u64 %d22, %d22, %d21;\n"
+         "  atom.global.min.u64 %d23, [%d3], %d22;\n"
+         "$NEXTPASS:\n"
+         "  add.u32 %t20, %t20, 1;\n  setp.lt.u32 %p9, %t20, " + std::to_string(ninner) + ";\n  @%p9 bra $PASS;\n";
+  }
+  s << close_loops() + "  @%p12 add.u64 %d10, %d10, " + std::to_string(REP) + ";\n"
+       "$GRABEND:\n"
        "  mov.b64 {%t3, %t4}, %d16;\n  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n"
        "  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n  mov.b64 %d11, {%t3, %t4};\n"
        "  mov.b64 {%t3, %t4}, %d17;\n  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n"
@@ -639,27 +894,38 @@ int compile_cubin(const std::string &src, int major, int minor, std::vector<char
 // The table form goes straight to PTX and the PTX compiler; the AND form
 // goes through NVRTC.
 int compile_program_kernel(const Program &g, bool lut_form, int major, int minor, std::vector<char> &cubin,
-                           std::string &log) {
+                           std::string &log, const GrabLayout *layout = nullptr) {
   // LEC_ES_JIT_NVRTC=1 compiles the table form from CUDA C++ through NVRTC
   // instead (same tables, for comparing the two compilation paths)
   static const bool via_nvrtc = getenv("LEC_ES_JIT_NVRTC") != nullptr;
   if (lut_form && !g.lut.order.empty() && !via_nvrtc) {
-    // hoisted values live in registers across the passes: if ptxas has to
-    // spill, halve the budget and build again
-    uint32_t rep = 0, budget = 0;
-    uint64_t pass_pis = 0;
-    std::vector<uint64_t> groups;
-    jit_layout(g, &rep, &budget, &pass_pis, &groups);
+    // values kept across loops live in registers: if ptxas has to spill,
+    // move 16 more of them into shared memory while slots remain, else
+    // halve the plan, and build again
+    GrabLayout own;
+    if (!layout) {
+      jit_layout(g, &own);
+      layout = &own;
+    }
+    uint32_t regs = layout->regs, plan = layout->plan;
     for (;;) {
       std::string lg;
-      const int rc = compile_ptx(gen_ptx_lut(g, major, minor, rep, budget, pass_pis, groups), major, minor, cubin, lg);
+      SlotSplit split;
+      const int rc = compile_ptx(
+          gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis, layout->groups, &split), major,
+          minor, cubin, lg);
       const bool spills = rc == LEC_ES_OK && lg.find(" 0 bytes spill stores") == std::string::npos &&
                           lg.find("spill stores") != std::string::npos;
-      if (rc != LEC_ES_OK || !spills || budget == 0) {
+      if (rc != LEC_ES_OK || !spills || plan == 0) {
         log += lg;
         return rc;
       }
-      budget /= 2;
+      if (split.inner_in_regs > 0 && split.in_shared < shared_slots()) {
+        regs = split.inner_in_regs - std::min<uint32_t>(16, split.inner_in_regs);
+      } else {
+        plan -= std::min<uint32_t>(16, plan);
+        regs = std::min(regs, plan);
+      }
     }
   }
   return compile_cubin(gen_source(g, lut_form), major, minor, cubin, log);
@@ -744,25 +1010,26 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   const double t0 = now_ms();
   std::vector<char> cubin;
   std::string path;
+  // the PTX form's grab layout (computed once: it searches loop nestings)
+  const bool ptx_form = lut_form && !g.lut.order.empty() && !getenv("LEC_ES_JIT_NVRTC");
+  GrabLayout lay;
+  if (ptx_form) jit_layout(g, &lay);
   if (!c->jit_dir.empty()) {
     mkdir(c->jit_dir.c_str(), 0755);
     char name[160];
-    uint32_t rep = 0, budget = 0;
-    uint64_t pass_pis = 0;
-    std::vector<uint64_t> groups;
-    jit_layout(g, &rep, &budget, &pass_pis, &groups);
     uint64_t nest = 1469598103934665603ull;  // FNV-1a over the loop groups
-    for (uint64_t m : groups) nest = (nest ^ m) * 1099511628211ull;
+    for (uint64_t m : lay.groups) nest = (nest ^ m) * 1099511628211ull;
     snprintf(name, sizeof(name), "/es_v%d_%016llx_%s%s_r%u_h%u_p%llx_n%llx_sm%d%d.cubin", kCodegenVersion,
-             (unsigned long long)g.hash, lut_form ? "lut" : "and", getenv("LEC_ES_JIT_NVRTC") ? "_nvrtc" : "", rep,
-             budget, (unsigned long long)pass_pis, (unsigned long long)nest, c->cc_major, c->cc_minor);
+             (unsigned long long)g.hash, lut_form ? "lut" : "and", getenv("LEC_ES_JIT_NVRTC") ? "_nvrtc" : "",
+             lay.rep, lay.regs * 1000 + lay.plan, (unsigned long long)lay.pass_pis, (unsigned long long)nest, c->cc_major,
+             c->cc_minor);
     path = c->jit_dir + name;
   }
   double nvrtc_ms = 0;
   if (path.empty() || !read_file(path, cubin)) {
     std::string log;
     const double tn = now_ms();
-    int rc = compile_program_kernel(g, lut_form, c->cc_major, c->cc_minor, cubin, log);
+    int rc = compile_program_kernel(g, lut_form, c->cc_major, c->cc_minor, cubin, log, ptx_form ? &lay : nullptr);
     nvrtc_ms = now_ms() - tn;
     if (rc) {
       if (getenv("LEC_ES_JIT_LOG")) fprintf(stderr, "lec_es JIT failed:\n%s\n", log.c_str());
@@ -795,13 +1062,9 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   k->num_records = g.num_records;
   k->work_per_chunk = lut_form ? g.lut.count : (uint32_t)g.recs.size();
   k->chunk_bits = g.n > 5 ? g.n - 5 : 0;
-  if (lut_form && !g.lut.order.empty() && !getenv("LEC_ES_JIT_NVRTC")) {  // the PTX form: its grab layout
-    uint32_t rep = 0, budget = 0;
-    uint64_t pass_pis = 0;
-    std::vector<uint64_t> groups;
-    jit_layout(g, &rep, &budget, &pass_pis, &groups);
-    k->rep_fixed = rep;
-    k->pass_bits = pass_pis >> 5;
+  if (ptx_form) {  // the PTX form: its grab layout
+    k->rep_fixed = lay.rep;
+    k->pass_bits = lay.pass_pis >> 5;
   }
   k->load_ms = now_ms() - tl;
   k->nvrtc_ms = nvrtc_ms;
