@@ -148,7 +148,6 @@ void plan_hoist_from(const LutProgram &lp, uint64_t pass_pis, uint32_t budget, c
   if (roots_out) *roots_out = have_cost;
 }
 
-namespace {
 // support PIs each table depends on
 std::vector<uint64_t> table_support(const LutProgram &lp) {
   const uint32_t NA = lp.na, NP = lp.np;
@@ -168,7 +167,6 @@ std::vector<uint64_t> table_support(const LutProgram &lp) {
     }
   return dep;
 }
-}  // namespace
 
 uint64_t least_influential_pis(const LutProgram &lp, uint32_t k) {
   const uint32_t NP = lp.np;

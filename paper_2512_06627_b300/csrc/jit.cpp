@@ -56,7 +56,7 @@ struct JitState {
 namespace {
 
 constexpr int kJitBlock = 128;
-constexpr int kCodegenVersion = 15;  // part of cached cubin names: bump whenever the generated code changes
+constexpr int kCodegenVersion = 17;  // part of cached cubin names: bump whenever the generated code changes
 // Values computed at one loop level and read at a deeper one: at most
 // kHoistPlan of them (see plan_hoist), those read by the innermost loop in
 // registers, the others in up to kHoistShared shared-memory slots per
@@ -389,35 +389,69 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   const uint32_t L = (uint32_t)grp.size();
   uint32_t roots = 0;
   const uint32_t shared_budget = shared_slots();
-  // level of each table: 0 once per grab, l once per iteration of pass
-  // loop l (tables reading no PI of a deeper loop), L once per pass
-  std::vector<uint8_t> level(lp.order.size(), (uint8_t)L), h, hn;
-  plan_hoist(lp, pass_pis, plan_budget, h, &roots);
-  for (size_t i = 0; i < lp.order.size(); i++)
-    if (h[i]) level[i] = 0;
-  uint64_t deeper = pass_pis;
-  for (uint32_t l = 1; l < L; l++) {
-    deeper &= ~grp[l - 1];
-    plan_hoist_from(lp, deeper, plan_budget, h, hn, &roots);
-    for (size_t i = 0; i < lp.order.size(); i++)
-      if (hn[i] && !h[i]) level[i] = (uint8_t)l;
-    h.swap(hn);
+  // natural level of each table: its deepest pass loop (0: reads no pass PI)
+  const size_t NL = lp.order.size();
+  std::vector<uint8_t> natural(NL, 0);
+  {
+    const std::vector<uint64_t> dep = table_support(lp);
+    for (size_t i = 0; i < NL; i++)
+      for (uint32_t l = 0; l < L; l++)
+        if (dep[i] & grp[l]) natural[i] = (uint8_t)(l + 1);
   }
-  // values read below their own level (live across a loop): the most read
-  // stay in registers, the others go to shared memory (thread-private
-  // slots, written where they are computed, loaded in each later section
-  // before their first reader there)
-  std::vector<int32_t> tpos(NA, -1);
-  for (size_t i = 0; i < lp.order.size(); i++) tpos[lp.order[i].node] = (int32_t)i;
-  std::vector<uint32_t> pass_readers(lp.order.size(), 0);
-  for (size_t i = 0; i < lp.order.size(); i++) {
-    for (int k = 0; k < lp.order[i].n; k++) {
-      const int32_t v = lp.order[i].leaf[k];
-      if (v >= 0 && (uint32_t)v < NA && tpos[v] >= 0 && level[tpos[v]] < level[i]) pass_readers[tpos[v]]++;
+  // The innermost U levels are unrolled: straight-line copies, one per value
+  // of their pass PIs (at most max_copies passes and 4,096 table
+  // evaluations before folding); levels 1..Lr stay loops.  Four copies
+  // measured best on the 16x16 miter (two: 3.72 ms, four: 3.48 ms, eight:
+  // 4.10 ms -- a 90 KB kernel).  LEC_ES_JIT_UNROLL sets the copies (0: none).
+  const char *unroll_env = getenv("LEC_ES_JIT_UNROLL");
+  const uint32_t max_copies = unroll_env ? (uint32_t)std::max(0, atoi(unroll_env)) : 4u;
+  uint32_t U = 0;
+  {
+    uint64_t copies = 1, evals = 0;
+    for (uint32_t l = L; l >= 1 && max_copies > 1; l--) {
+      const uint64_t c = copies << __builtin_popcountll(grp[l - 1]);
+      evals += (uint64_t)std::count(natural.begin(), natural.end(), (uint8_t)l) * c;
+      if (c > max_copies || evals > 4096) break;
+      copies = c;
+      U++;
     }
   }
-  if (lp.root >= 0 && lp.root < (int64_t)NA && tpos[lp.root] >= 0 && level[tpos[lp.root]] < L)
-    pass_readers[tpos[lp.root]]++;
+  const uint32_t Lr = L - U;
+  // level of each table: 0 once per grab, l <= Lr once per iteration of
+  // pass loop l (tables planned there: reading no PI of a deeper loop),
+  // unrolled levels at their natural level, the rest at level Lr
+  std::vector<uint8_t> level(NL, (uint8_t)Lr), h, hn;
+  if (Lr >= 1) {
+    plan_hoist(lp, pass_pis, plan_budget, h, &roots);
+    for (size_t i = 0; i < NL; i++)
+      if (h[i]) level[i] = 0;
+    uint64_t deeper = pass_pis;
+    for (uint32_t l = 1; l < Lr; l++) {
+      deeper &= ~grp[l - 1];
+      plan_hoist_from(lp, deeper, plan_budget, h, hn, &roots);
+      for (size_t i = 0; i < NL; i++)
+        if (hn[i] && !h[i]) level[i] = (uint8_t)l;
+      h.swap(hn);
+    }
+  }
+  for (size_t i = 0; i < NL; i++)
+    if (natural[i] > Lr || Lr == 0) level[i] = natural[i];
+  // values read below their own level across a loop (computed above level
+  // Lr): those read in the innermost loop's iterations stay in registers,
+  // the others go to shared memory (thread-private slots, written where
+  // they are computed, loaded in each later section before their first
+  // reader there)
+  std::vector<int32_t> tpos(NA, -1);
+  for (size_t i = 0; i < lp.order.size(); i++) tpos[lp.order[i].node] = (int32_t)i;
+  auto crosses = [&](int32_t v, uint32_t reader_level) {
+    return v >= 0 && (uint32_t)v < NA && tpos[v] >= 0 && level[tpos[v]] < reader_level && level[tpos[v]] < Lr;
+  };
+  std::vector<uint32_t> pass_readers(lp.order.size(), 0);
+  for (size_t i = 0; i < lp.order.size(); i++) {
+    for (int k = 0; k < lp.order[i].n; k++)
+      if (crosses(lp.order[i].leaf[k], level[i])) pass_readers[tpos[lp.order[i].leaf[k]]]++;
+  }
+  if (lp.root >= 0 && crosses((int32_t)lp.root, L)) pass_readers[tpos[lp.root]]++;
   // chunk-index bit positions of each pass loop's PIs and of the grab
   const uint32_t cbits = NP > 5 ? NP - 5 : 0;
   std::vector<std::vector<uint32_t>> lpos(L);
@@ -463,12 +497,9 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   std::vector<uint32_t> read_at(lp.order.size(), 0);  // bit l: read by a level-l section
   {
     for (size_t i = 0; i < lp.order.size(); i++)
-      for (int k = 0; k < lp.order[i].n; k++) {
-        const int32_t v = lp.order[i].leaf[k];
-        if (v >= 0 && (uint32_t)v < NA && tpos[v] >= 0 && level[tpos[v]] < level[i]) read_at[tpos[v]] |= 1u << level[i];
-      }
-    if (lp.root >= 0 && lp.root < (int64_t)NA && tpos[lp.root] >= 0 && level[tpos[lp.root]] < L)
-      read_at[tpos[lp.root]] |= 1u << L;
+      for (int k = 0; k < lp.order[i].n; k++)
+        if (crosses(lp.order[i].leaf[k], level[i])) read_at[tpos[lp.order[i].leaf[k]]] |= 1u << level[i];
+    if (lp.root >= 0 && crosses((int32_t)lp.root, L)) read_at[tpos[lp.root]] |= 1u << L;
     for (size_t i = 0; i < lp.order.size(); i++)
       for (uint32_t l = 1; l <= L; l++)
         if ((read_at[i] >> l) & 1u) load_cost[i] += runs[l];
@@ -479,8 +510,8 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   std::stable_sort(read_roots.begin(), read_roots.end(), [&](int32_t x, int32_t y) {
     return load_cost[x] > load_cost[y] || (load_cost[x] == load_cost[y] && pass_readers[x] > pass_readers[y]);
   });
-  uint32_t inner = 0;  // read by the innermost loop: sorted first (their loads run most often)
-  for (int32_t i : read_roots) inner += (read_at[i] >> L) & 1u;
+  uint32_t inner = 0;  // read in the innermost loop's iterations: sorted first (their loads run most often)
+  for (int32_t i : read_roots) inner += (read_at[i] >> Lr) != 0;
   const uint32_t in_regs = std::min<uint32_t>(reg_budget, inner);
   std::vector<int32_t> smem_slot(lp.order.size(), -1);
   uint32_t nsmem = 0;
@@ -607,9 +638,12 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
       }
     }
   };
+  // pass loops 1..NLOOP ($LV, index j<l>, first chunk of the iteration
+  // o<l>); without unrolling the innermost level L is the pass loop ($PASS)
+  const uint32_t NLOOP = U > 0 ? Lr : L - 1;
   auto close_loops = [&]() {  // loop ends of the outer pass loops, innermost first
     std::string c;
-    for (uint32_t l = L - 1; l >= 1; l--) {
+    for (uint32_t l = NLOOP; l >= 1; l--) {
       const std::string j = "%j" + std::to_string(l);
       c += "  add.u32 " + j + ", " + j + ", 1;\n  setp.lt.u32 %p9, " + j + ", " +
            std::to_string(1u << __builtin_popcountll(grp[l - 1])) + ";\n  @%p9 bra $LV" + std::to_string(l) + ";\n";
@@ -624,9 +658,7 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     }
   };
   emit_level(0);
-  // outer pass loops l = 1..L-1: index in j<l>, first chunk of the
-  // iteration in o<l>
-  for (uint32_t l = 1; l < L; l++) {
+  for (uint32_t l = 1; l <= NLOOP; l++) {
     const std::string j = "%j" + std::to_string(l);
     s << "  mov.u32 " << j << ", 0;\n$LV" << l << ":\n  cvt.u64.u32 %d32, " << j << ";\n";
     emit_deposit("%d28", "%d32", lpos[l - 1]);
@@ -634,7 +666,7 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     emit_pass_pis(grp[l - 1], j.c_str());
     emit_level((uint8_t)l);
   }
-  const std::string base = L == 1 ? std::string("%d15") : "%o" + std::to_string(L - 1);
+  const std::string base = NLOOP == 0 ? std::string("%d15") : "%o" + std::to_string(NLOOP);
   // passes: j in t20, its chunk bits in d29, the pass's first chunk d27;
   // outer passes do not run in chunk order, so a pass past the range is
   // skipped rather than ending the grab
@@ -644,149 +676,163 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     emit_deposit("%d29", "%d31", lpos[L - 1]);
     s << "  add.u64 %d27, " << base << ", %d29;\n";
   };
-  const uint32_t ninner = 1u << __builtin_popcountll(grp[L - 1]);
-  const size_t inner_tables = (size_t)std::count(level.begin(), level.end(), (uint8_t)L);
-  const char *unroll_env = getenv("LEC_ES_JIT_UNROLL");
-  const bool unroll = (unroll_env ? atoi(unroll_env) != 0 : true) && ninner <= 4 && inner_tables * ninner <= 4096;
-  if (unroll) {
-    // The innermost loop unrolled: one copy per value of its pass PIs, in
-    // which those PIs are the constants 0 or all-ones.  Through each copy
-    // they propagate: a table reading one is cofactored, complements fold
-    // into the readers' tables, a table left with one input becomes an alias
-    // and one left with none a constant -- the same Boolean functions with
-    // fewer instructions.
+  const uint32_t vmask = g.n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << g.n)) - 1u);
+  if (U > 0) {
+    // Levels Lr+1..L unrolled: nested straight-line copies, one per value of
+    // each level's pass PIs, in which those PIs are the constants 0 or
+    // all-ones.  Through each copy they propagate: a table reading one is
+    // cofactored, complements fold into the readers' tables, a table left
+    // with one input becomes an alias and one left with none a constant --
+    // the same Boolean functions with fewer instructions.  The innermost
+    // copies are the passes.
     struct SVal {
-      bool imm = false;  // an immediate (imm) or a register (reg, complemented if inv)
+      bool imm = false;  // an immediate (imm_v) or a register (reg, complemented if inv)
       bool inv = false;
       uint32_t imm_v = 0;
       std::string reg;
     };
-    std::vector<uint32_t> ipis;  // the innermost pass PIs in rank order (ascending)
-    for (uint32_t k = 10; k < NP; k++)
-      if ((grp[L - 1] >> k) & 1u) ipis.push_back(k);
     std::vector<SVal> sv(NV);
-    for (uint32_t j = 0; j < ninner; j++) {
-      const std::string J = std::to_string(j);
-      uint64_t off = 0;  // chunk offset of this copy's pass
-      for (uint32_t r = 0; r < lpos[L - 1].size(); r++)
-        if ((j >> r) & 1u) off |= 1ull << lpos[L - 1][r];
-      const std::string chunk = "  add.u64 %d27, " + base + ", " + std::to_string(off) + ";\n";
-      s << "  @%p12 bra $PB" << J << ";\n" << chunk << "  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra $NX" << J
-        << ";\n  add.u64 %d22, %d27, 32;\n  setp.le.u64 %p10, %d22, %d1;\n  @%p10 bra $NX" << J
-        << ";\n  add.u64 %d19, %d27, %d18;\n$PB" << J << ":\n";
-      std::fill(loaded.begin(), loaded.end(), (uint8_t)0);
-      auto value = [&](int32_t v) -> SVal {  // a leaf's value in this copy
-        SVal x;
-        if (v < 0 || isconst[v]) {
+    std::vector<int8_t> pic(NP, -1);  // pass PIs fixed in the current copy: 0 or 1
+    uint32_t ncopy = 0;                // pass copies emitted (label numbers)
+    auto value = [&](int32_t v, uint8_t lv) -> SVal {  // a leaf's value in the current copy
+      SVal x;
+      if (v < 0 || isconst[v]) {
+        x.imm = true;
+        x.imm_v = v < 0 ? 0u : cval[v];
+        return x;
+      }
+      if ((uint32_t)v >= NA) {
+        const uint32_t k = (uint32_t)v - NA;
+        if (k < NP && pic[k] >= 0) {
           x.imm = true;
-          x.imm_v = v < 0 ? 0u : cval[v];
+          x.imm_v = pic[k] ? 0xFFFFFFFFu : 0u;
           return x;
         }
-        if ((uint32_t)v >= NA) {
-          const uint32_t k = (uint32_t)v - NA;
-          for (uint32_t r = 0; r < ipis.size(); r++)
-            if (ipis[r] == k) {
-              x.imm = true;
-              x.imm_v = (j >> r) & 1u ? 0xFFFFFFFFu : 0u;
-              return x;
-            }
-          x.reg = name[v];
-          return x;
-        }
-        if (tpos[v] >= 0 && level[tpos[v]] == L) return sv[v];
-        load_shared(v, (uint8_t)L);
         x.reg = name[v];
         return x;
-      };
-      for (size_t i = 0; i < lp.order.size(); i++) {
-        const LutCover::Lut &l = lp.order[i];
-        if (level[i] != L || isconst[l.node]) continue;
-        SVal op[3];
-        bool live[3] = {false, false, false};
-        uint8_t tt = l.tt;
-        for (int k = 0; k < 3; k++) {
-          op[k] = value(k < l.n ? l.leaf[k] : -1);
-          live[k] = true;
-          if (!op[k].imm && op[k].inv) tt = tt_flip(tt, k);
-          if (op[k].imm && (op[k].imm_v == 0u || op[k].imm_v == 0xFFFFFFFFu)) {
-            tt = tt_fix(tt, k, op[k].imm_v != 0);
+      }
+      if (tpos[v] >= 0 && level[tpos[v]] > Lr) return sv[v];
+      load_shared(v, lv);
+      x.reg = name[v];
+      return x;
+    };
+    auto emit_spec = [&](const LutCover::Lut &l, uint8_t lv) {
+      SVal op[3];
+      bool live[3] = {false, false, false};
+      uint8_t tt = l.tt;
+      for (int k = 0; k < 3; k++) {
+        op[k] = value(k < l.n ? l.leaf[k] : -1, lv);
+        live[k] = true;
+        if (!op[k].imm && op[k].inv) tt = tt_flip(tt, k);
+        if (op[k].imm && (op[k].imm_v == 0u || op[k].imm_v == 0xFFFFFFFFu)) {
+          tt = tt_fix(tt, k, op[k].imm_v != 0);
+          live[k] = false;
+        }
+      }
+      for (int a = 0; a < 3; a++)
+        for (int k = a + 1; k < 3; k++)
+          if (live[a] && live[k] && op[a].imm == op[k].imm &&
+              (op[a].imm ? op[a].imm_v == op[k].imm_v : op[a].reg == op[k].reg)) {
+            tt = tt_same(tt, a, k);
             live[k] = false;
           }
+      int nlive = 0, nreg = 0, last = -1;
+      for (int k = 0; k < 3; k++) {
+        live[k] = live[k] && tt_reads(tt, k);
+        if (live[k]) {
+          nlive++;
+          nreg += !op[k].imm;
+          last = k;
         }
-        for (int a = 0; a < 3; a++)
-          for (int k = a + 1; k < 3; k++)
-            if (live[a] && live[k] && op[a].imm == op[k].imm &&
-                (op[a].imm ? op[a].imm_v == op[k].imm_v : op[a].reg == op[k].reg)) {
-              tt = tt_same(tt, a, k);
-              live[k] = false;
-            }
-        int nlive = 0, nreg = 0, last = -1;
-        for (int k = 0; k < 3; k++) {
-          live[k] = live[k] && tt_reads(tt, k);
-          if (live[k]) {
-            nlive++;
-            nreg += !op[k].imm;
-            last = k;
-          }
-        }
-        SVal res;
-        if (nreg == 0) {  // every input a constant: evaluate bitwise
-          res.imm = true;
-          for (int b = 0; b < 32; b++) {
-            int m = 0;
-            for (int k = 0; k < 3; k++)
-              if (live[k]) m |= (int)((op[k].imm_v >> b) & 1u) << k;
-            res.imm_v |= (uint32_t)((tt >> m) & 1) << b;
-          }
-        } else if (nlive == 1 && (tt == kVarTT[last] || tt == (uint8_t)~kVarTT[last])) {
-          res.reg = op[last].reg;  // an alias of its input, or of its complement
-          res.inv = tt != kVarTT[last];
-        } else {
-          res.reg = "%v" + std::to_string(l.node);
-          std::string x[3];
-          for (int k = 0; k < 3; k++) {
-            if (!live[k]) x[k] = "0";
-            else if (op[k].imm) {
-              snprintf(buf, sizeof(buf), "0x%08x", op[k].imm_v);
-              x[k] = buf;
-            } else {
-              x[k] = op[k].reg;
-            }
-          }
-          snprintf(buf, sizeof(buf), "  lop3.b32 %s, %s, %s, %s, 0x%02x;\n", res.reg.c_str(), x[2].c_str(),
-                   x[1].c_str(), x[0].c_str(), tt);
-          s << buf;
-        }
-        sv[l.node] = res;
       }
-      // the miter output of this copy (t7), then the same check as a pass
-      const uint32_t vmask = g.n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << g.n)) - 1u);
-      const SVal out = value(lp.root < 0 ? -1 : (int32_t)lp.root);
-      const bool never = out.imm && ((out.imm_v ^ (g.out_compl ? 0xFFFFFFFFu : 0u)) & vmask) == 0;
-      if (out.imm) {
-        snprintf(buf, sizeof(buf), "  mov.b32 %%t7, 0x%08x;\n", (out.imm_v ^ (g.out_compl ? 0xFFFFFFFFu : 0u)) & vmask);
+      SVal res;
+      if (nreg == 0) {  // every input a constant: evaluate bitwise
+        res.imm = true;
+        for (int b = 0; b < 32; b++) {
+          int m = 0;
+          for (int k = 0; k < 3; k++)
+            if (live[k]) m |= (int)((op[k].imm_v >> b) & 1u) << k;
+          res.imm_v |= (uint32_t)((tt >> m) & 1) << b;
+        }
+      } else if (nlive == 1 && (tt == kVarTT[last] || tt == (uint8_t)~kVarTT[last])) {
+        res.reg = op[last].reg;  // an alias of its input, or of its complement
+        res.inv = tt != kVarTT[last];
       } else {
-        snprintf(buf, sizeof(buf), "  xor.b32 %%t7, %s, 0x%08x;\n  and.b32 %%t7, %%t7, 0x%08x;\n", out.reg.c_str(),
-                 (out.inv != (g.out_compl != 0)) ? 0xFFFFFFFFu : 0u, vmask);
+        res.reg = "%v" + std::to_string(l.node);
+        std::string x[3];
+        for (int k = 0; k < 3; k++) {
+          if (!live[k]) {
+            x[k] = "0";
+          } else if (op[k].imm) {
+            snprintf(buf, sizeof(buf), "0x%08x", op[k].imm_v);
+            x[k] = buf;
+          } else {
+            x[k] = op[k].reg;
+          }
+        }
+        snprintf(buf, sizeof(buf), "  lop3.b32 %s, %s, %s, %s, 0x%02x;\n", res.reg.c_str(), x[2].c_str(), x[1].c_str(),
+                 x[0].c_str(), tt);
+        s << buf;
       }
-      s << buf;
-      s << "  @%p12 bra $CK" << J << ";\n"
-        << "  setp.ge.u64 %p5, %d19, %d2;\n  setp.lt.u64 %p11, %d19, %d1;\n  or.pred %p5, %p5, %p11;\n"
-           "  @%p5 mov.b32 %t7, 0;\n  selp.u64 %d24, 0, 1, %p5;\n  add.u64 %d10, %d10, %d24;\n"
-        << "$CK" << J << ":\n";
-      if (!never) {  // a copy whose output is the constant 0 cannot fail
-        s << "  setp.ne.u32 %p6, %t7, 0;\n  vote.sync.ballot.b32 %t8, %p6, -1;\n  setp.eq.u32 %p7, %t8, 0;\n"
-          << "  @%p7 bra $NX" << J << ";\n"
-          << "  neg.s32 %t9, %t8;\n  and.b32 %t9, %t9, %t8;\n  bfind.u32 %t10, %t9;\n"
-          << "  setp.ne.u32 %p7, %t10, %t2;\n  @%p7 bra $NX" << J << ";\n"
-          << chunk
-          << "  add.u64 %d19, %d27, %d18;\n"
-             "  neg.s32 %t11, %t7;\n  and.b32 %t11, %t11, %t7;\n  bfind.u32 %t12, %t11;\n"
-             "  cvt.u64.u32 %d21, %t12;\n  shl.b64 %d22, %d19, 5;\n  add.u64 %d22, %d22, %d21;\n"
-             "  atom.global.min.u64 %d23, [%d3], %d22;\n";
+      sv[l.node] = res;
+    };
+    auto unrolled = [&](auto &&self, uint32_t lv, uint64_t off) -> void {
+      std::vector<uint32_t> pis;  // this level's pass PIs in rank order (ascending)
+      for (uint32_t k = 10; k < NP; k++)
+        if ((grp[lv - 1] >> k) & 1u) pis.push_back(k);
+      for (uint32_t j = 0; j < (1u << pis.size()); j++) {
+        uint64_t o = off;  // chunk offset of this copy
+        for (uint32_t r = 0; r < pis.size(); r++) {
+          if ((j >> r) & 1u) o |= 1ull << lpos[lv - 1][r];
+          pic[pis[r]] = (int8_t)((j >> r) & 1u);
+        }
+        const std::vector<SVal> saved = sv;
+        if (lv < L) {
+          std::fill(loaded.begin(), loaded.end(), (uint8_t)0);
+          for (size_t i = 0; i < lp.order.size(); i++)
+            if (level[i] == lv && !isconst[lp.order[i].node]) emit_spec(lp.order[i], (uint8_t)lv);
+          self(self, lv + 1, o);
+        } else {  // a pass: its range work, its tables, its output check
+          const std::string J = std::to_string(ncopy++);
+          const std::string chunk = "  add.u64 %d27, " + base + ", " + std::to_string(o) + ";\n";
+          s << "  @%p12 bra $PB" << J << ";\n" << chunk << "  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra $NX" << J
+            << ";\n  add.u64 %d22, %d27, 32;\n  setp.le.u64 %p10, %d22, %d1;\n  @%p10 bra $NX" << J
+            << ";\n  add.u64 %d19, %d27, %d18;\n$PB" << J << ":\n";
+          std::fill(loaded.begin(), loaded.end(), (uint8_t)0);
+          for (size_t i = 0; i < lp.order.size(); i++)
+            if (level[i] == L && !isconst[lp.order[i].node]) emit_spec(lp.order[i], (uint8_t)L);
+          const SVal out = value(lp.root < 0 ? -1 : (int32_t)lp.root, (uint8_t)L);
+          const uint32_t outc = g.out_compl ? 0xFFFFFFFFu : 0u;
+          const bool never = out.imm && ((out.imm_v ^ outc) & vmask) == 0;
+          if (out.imm) {
+            snprintf(buf, sizeof(buf), "  mov.b32 %%t7, 0x%08x;\n", (out.imm_v ^ outc) & vmask);
+          } else {
+            snprintf(buf, sizeof(buf), "  xor.b32 %%t7, %s, 0x%08x;\n  and.b32 %%t7, %%t7, 0x%08x;\n",
+                     out.reg.c_str(), out.inv ? ~outc : outc, vmask);
+          }
+          s << buf;
+          s << "  @%p12 bra $CK" << J << ";\n"
+            << "  setp.ge.u64 %p5, %d19, %d2;\n  setp.lt.u64 %p11, %d19, %d1;\n  or.pred %p5, %p5, %p11;\n"
+               "  @%p5 mov.b32 %t7, 0;\n  selp.u64 %d24, 0, 1, %p5;\n  add.u64 %d10, %d10, %d24;\n"
+            << "$CK" << J << ":\n";
+          if (!never) {  // a pass whose output is the constant 0 cannot fail
+            s << "  setp.ne.u32 %p6, %t7, 0;\n  vote.sync.ballot.b32 %t8, %p6, -1;\n  setp.eq.u32 %p7, %t8, 0;\n"
+              << "  @%p7 bra $NX" << J << ";\n"
+              << "  neg.s32 %t9, %t8;\n  and.b32 %t9, %t9, %t8;\n  bfind.u32 %t10, %t9;\n"
+              << "  setp.ne.u32 %p7, %t10, %t2;\n  @%p7 bra $NX" << J << ";\n"
+              << chunk
+              << "  add.u64 %d19, %d27, %d18;\n"
+                 "  neg.s32 %t11, %t7;\n  and.b32 %t11, %t11, %t7;\n  bfind.u32 %t12, %t11;\n"
+                 "  cvt.u64.u32 %d21, %t12;\n  shl.b64 %d22, %d19, 5;\n  add.u64 %d22, %d22, %d21;\n"
+                 "  atom.global.min.u64 %d23, [%d3], %d22;\n";
+          }
+          s << "$NX" << J << ":\n";
+        }
+        sv = saved;
+        for (uint32_t r = 0; r < pis.size(); r++) pic[pis[r]] = -1;
       }
-      s << "$NX" << J << ":\n";
-    }
+    };
+    unrolled(unrolled, Lr + 1, 0);
   } else {
     s << "  mov.u32 %t20, 0;\n$PASS:\n  @%p12 bra $PBODY;\n";
     emit_chunk();
@@ -796,7 +842,6 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     emit_pass_pis(grp[L - 1], "%t20");
     emit_level((uint8_t)L);
     if (lp.root >= 0) load_shared((int32_t)lp.root, (uint8_t)L);
-    const uint32_t vmask = g.n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << g.n)) - 1u);
     const std::string root = lp.root < 0 ? std::string("0") : name[lp.root];
     snprintf(buf, sizeof(buf), "  xor.b32 %%t7, %s, 0x%08x;\n  and.b32 %%t7, %%t7, 0x%08x;\n", root.c_str(),
              g.out_compl ? 0xFFFFFFFFu : 0u, vmask);
@@ -815,7 +860,7 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
          "  cvt.u64.u32 %d21, %t12;\n  shl.b64 %d22, %d19, 5;\n  add.u64 %d22, %d22, %d21;\n"
          "  atom.global.min.u64 %d23, [%d3], %d22;\n"
          "$NEXTPASS:\n"
-         "  add.u32 %t20, %t20, 1;\n  setp.lt.u32 %p9, %t20, " + std::to_string(ninner) + ";\n  @%p9 bra $PASS;\n";
+         "  add.u32 %t20, %t20, 1;\n  setp.lt.u32 %p9, %t20, " + std::to_string(1u << __builtin_popcountll(grp[L - 1])) + ";\n  @%p9 bra $PASS;\n";
   }
   s << close_loops() + "  @%p12 add.u64 %d10, %d10, " + std::to_string(REP) + ";\n"
        "$GRABEND:\n"
@@ -846,9 +891,10 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
       }
     }
     fprintf(stderr,
-            "lec_es JIT %016llx: %u tables, rep %u, pass PIs %016llx; tables per level: %s "
+            "lec_es JIT %016llx: %u tables, rep %u, pass PIs %016llx; tables per level: %s, %u unrolled "
             "(%u read below their level, %u from shared memory)\n",
-            (unsigned long long)g.hash, lp.count, REP, (unsigned long long)pass_pis, lv.c_str(), roots, (unsigned)nsmem);
+            (unsigned long long)g.hash, lp.count, REP, (unsigned long long)pass_pis, lv.c_str(), U, roots,
+            (unsigned)nsmem);
   }
   return s.str();
 }
