@@ -391,6 +391,7 @@ int plan_prepare_program(lec_es_ctx *c, Program &&prog, const lec_es_options *op
   uint32_t want = opt ? opt->tier : LEC_ES_TIER_AUTO;
   if (g.slots_elided) want = LEC_ES_TIER_JIT;  // the front end found this cone's kernel for this run
   if (want == LEC_ES_TIER_AUTO) want = jit_auto_tier(c, g, chunks);
+  const double tj = now_ms();
   if (want == LEC_ES_TIER_JIT) {
     rc = jit_prepare(c, p.get(), opt);
     if (rc) {
@@ -408,12 +409,16 @@ int plan_prepare_program(lec_es_ctx *c, Program &&prog, const lec_es_options *op
       p->tier = p->geom.spill ? LEC_ES_TIER_SPILL : LEC_ES_TIER_INTERP;
     }
   }
+  const double td = now_ms();
   rc = plan_finish_device(c, p.get());
   if (rc) {
     plan_release(c, p.release());
     return rc;
   }
   p->host_ms = now_ms() - t0 - p->jit_ms;
+  if (getenv("LEC_ES_FRONT_LOG"))
+    fprintf(stderr, "lec_es plan: set-up %.3f ms, tier choice and kernel %.3f ms, device buffers %.3f ms\n", tj - t0,
+            td - tj, now_ms() - td);
   *out = p.release();
   return LEC_ES_OK;
 }

@@ -44,37 +44,51 @@ int extract_cone(const MiterView &m, std::vector<uint8_t> &mark, Cone &c) {
   const uint32_t root = m.out_lit >> 1;
   if (root > maxvar) return LEC_ES_EINVAL;
   if (m.num_ands && !m.fanins) return LEC_ES_EINVAL;
-  // sparse marking: only visited variables are touched, so many miters can
-  // share one large graph
-  std::vector<uint32_t> stack{root};
-  std::vector<uint32_t> visited;
+  // Fanins precede their AND, so one scan from the output down visits the
+  // cone in descending order: a marked AND marks its fanins.  The scan stops
+  // when no marked AND is left below it, so a small cone of a large shared
+  // graph costs the span of its variables (sequential byte reads), and the
+  // lists come out sorted.  Marks are cleared as the scan passes them.
   mark.resize(maxvar + 1, 0);
+  mark[root] = 1;
+  uint64_t pending_ands = root > m.num_pis ? 1 : 0, pending_pis = root > 0 && root <= m.num_pis ? 1 : 0;
   int rc = LEC_ES_OK;
-  while (!stack.empty()) {
-    uint32_t v = stack.back();
-    stack.pop_back();
-    if (mark[v]) continue;
-    mark[v] = 1;
-    visited.push_back(v);
-    if (v == 0) {
-      c.uses_const = true;
-    } else if (v <= m.num_pis) {
-      c.pis.push_back(v);
-    } else {
-      c.ands.push_back(v);
-      const uint32_t *f = fanin_of(m, v);
-      for (int e = 0; e < 2; e++) {
-        uint32_t u = f[e] >> 1;
-        if (u >= v) { rc = LEC_ES_EINVAL; break; }
-        if (!mark[u]) stack.push_back(u);
+  uint32_t v = root;
+  for (; v > m.num_pis && pending_ands; v--) {
+    if (!mark[v]) continue;
+    mark[v] = 0;
+    pending_ands--;
+    c.ands.push_back(v);
+    const uint32_t *f = fanin_of(m, v);
+    for (int e = 0; e < 2; e++) {
+      const uint32_t u = f[e] >> 1;
+      if (u >= v) {
+        rc = LEC_ES_EINVAL;
+        break;
       }
-      if (rc) break;
+      if (mark[u]) continue;
+      mark[u] = 1;
+      if (u > m.num_pis) pending_ands++;
+      else if (u > 0) pending_pis++;
     }
+    if (rc) break;
   }
-  for (uint32_t v : visited) mark[v] = 0;
-  if (rc) return rc;
-  std::sort(c.ands.begin(), c.ands.end());
-  std::sort(c.pis.begin(), c.pis.end());
+  if (rc) {  // clear what is still marked below the scan
+    for (uint32_t u = v; u > 0; u--) mark[u] = 0;
+    mark[0] = 0;
+    c.ands.clear();
+    return rc;
+  }
+  for (uint32_t u = std::min<uint64_t>(m.num_pis, root); u > 0 && pending_pis; u--) {
+    if (!mark[u]) continue;
+    mark[u] = 0;
+    pending_pis--;
+    c.pis.push_back(u);
+  }
+  c.uses_const = mark[0] != 0;
+  mark[0] = 0;
+  std::reverse(c.ands.begin(), c.ands.end());
+  std::reverse(c.pis.begin(), c.pis.end());
   return LEC_ES_OK;
 }
 
