@@ -326,6 +326,34 @@ void jit_layout(const Program &g, GrabLayout *out) {
       *groups = std::move(best_g);
     }
   }
+  // LEC_ES_JIT_GROUPS="27,28|29|30|31": the pass loops given explicitly,
+  // outermost first, as support PI indices (for measurements)
+  if (const char *e = getenv("LEC_ES_JIT_GROUPS")) {
+    std::vector<uint64_t> gs(1, 0);
+    uint64_t all = 0;
+    for (const char *q = e; *q;) {
+      if (*q == '|') {
+        gs.push_back(0);
+        q++;
+      } else if (*q >= '0' && *q <= '9') {
+        char *endp = nullptr;
+        const unsigned long k = strtoul(q, &endp, 10);
+        if (k >= 10 && k < g.n && k < 64) {
+          gs.back() |= 1ull << k;
+          all |= 1ull << k;
+        }
+        q = endp;
+      } else {
+        q++;
+      }
+    }
+    gs.erase(std::remove(gs.begin(), gs.end(), 0ull), gs.end());
+    if (!gs.empty()) {
+      npass = (uint32_t)__builtin_popcountll(all);
+      m = all;
+      *groups = gs;
+    }
+  }
   out->rep = 1u << npass;
   out->regs = regs;
   out->plan = plan;
@@ -677,6 +705,7 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     s << "  add.u64 %d27, " << base << ", %d29;\n";
   };
   const uint32_t vmask = g.n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << g.n)) - 1u);
+  uint64_t unrolled_lop3 = 0;  // lop3 of the unrolled levels (one run of level Lr)
   if (U > 0) {
     // Levels Lr+1..L unrolled: nested straight-line copies, one per value of
     // each level's pass PIs, in which those PIs are the constants 0 or
@@ -694,6 +723,7 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     std::vector<SVal> sv(NV);
     std::vector<int8_t> pic(NP, -1);  // pass PIs fixed in the current copy: 0 or 1
     uint32_t ncopy = 0;                // pass copies emitted (label numbers)
+    unrolled_lop3 = 0;
     auto value = [&](int32_t v, uint8_t lv) -> SVal {  // a leaf's value in the current copy
       SVal x;
       if (v < 0 || isconst[v]) {
@@ -770,6 +800,7 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
             x[k] = op[k].reg;
           }
         }
+        unrolled_lop3++;
         snprintf(buf, sizeof(buf), "  lop3.b32 %s, %s, %s, %s, 0x%02x;\n", res.reg.c_str(), x[2].c_str(), x[1].c_str(),
                  x[0].c_str(), tt);
         s << buf;
@@ -890,11 +921,17 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
         lv += t;
       }
     }
+    // lop3 executed per pass: loop levels' tables times their runs, the
+    // unrolled levels' lop3 once per run of level Lr
+    double per_grab = 0;
+    for (size_t i = 0; i < lp.order.size(); i++)
+      if (!isconst[lp.order[i].node] && (U == 0 || level[i] <= Lr)) per_grab += runs[level[i]];
+    per_grab += (double)unrolled_lop3 * runs[Lr];
     fprintf(stderr,
             "lec_es JIT %016llx: %u tables, rep %u, pass PIs %016llx; tables per level: %s, %u unrolled "
-            "(%u read below their level, %u from shared memory)\n",
+            "(%u read below their level, %u from shared memory); %.1f lop3 per pass\n",
             (unsigned long long)g.hash, lp.count, REP, (unsigned long long)pass_pis, lv.c_str(), U, roots,
-            (unsigned)nsmem);
+            (unsigned)nsmem, per_grab / REP);
   }
   return s.str();
 }
