@@ -368,7 +368,9 @@ int stage_layout(lec_es_ctx *c, lec_es_batch_plan *b, const Layout &L, int grid_
     uint64_t cb = 0, ce = num_chunks(b->progs[i].n), grabs = ~0ull;
     unsigned long long *cex = b->d_cex + i, *ev = b->d_aux + 2 * j, *next = b->d_aux + 2 * j + 1;
     uint64_t grid = 1, rep = 1, q0 = 0, qend = 0;
-    jit_geometry(kk, ce - cb, c->sm_count, &grid, &rep);
+    bool strided = false;
+    jit_geometry(kk, ce - cb, c->sm_count, &grid, &rep, &strided);
+    if (strided) next = nullptr;  // grabs by static stride: no counter
     jit_grab_range(kk, rep, cb, ce, &q0, &qend);
     void *args[] = {&cb, &ce, &cex, &ev, &next, &grabs, &rep, &q0, &qend};
     if (cudaLaunchKernel((const void *)kk->kern, dim3((unsigned)grid), dim3(kk->block), args, 0,

@@ -125,7 +125,8 @@ uint64_t jit_reps(const JitKernel *k, uint64_t chunks, uint64_t grid);
 // Grab numbers [q0, qend) covering chunks [cb, ce) for the kernel's layout.
 void jit_grab_range(const JitKernel *k, uint64_t rep, uint64_t cb, uint64_t ce, uint64_t *q0, uint64_t *qend);
 // Grid and passes per grab for a launch over `chunks` chunks.
-void jit_geometry(const JitKernel *k, uint64_t chunks, int sm_count, uint64_t *grid, uint64_t *rep);
+void jit_geometry(const JitKernel *k, uint64_t chunks, int sm_count, uint64_t *grid, uint64_t *rep,
+                  bool *strided = nullptr);
 int jit_launch(lec_es_ctx *c, lec_es_plan *p, uint64_t chunk_begin, uint64_t chunk_end, int grid,
                uint64_t max_grabs);
 // Non-blocking lookup for the server: the compiled kernel if ready, else
