@@ -61,6 +61,7 @@ struct JitKernel {
   uint32_t num_slots = 0, order = 0, num_records = 0;  // its slot program's, for results
   uint32_t work_per_chunk = 0;  // straight-line instructions per 32-pattern chunk (about)
   uint32_t rep_fixed = 0;       // passes per grab compiled into the kernel (0: a launch parameter)
+  bool stride_ok = false;       // the kernel can take grabs by static stride (a null counter)
   uint64_t pass_bits = 0;       // chunk-index bits of the pass PIs (0: contiguous grabs of 32 * rep chunks)
   uint32_t chunk_bits = 0;      // bits of the chunk index (support PIs - 5)
 };

@@ -56,7 +56,7 @@ struct JitState {
 namespace {
 
 constexpr int kJitBlock = 128;
-constexpr int kCodegenVersion = 18;  // part of cached cubin names: bump whenever the generated code changes
+constexpr int kCodegenVersion = 19;  // part of cached cubin names: bump whenever the generated code changes
 // Values computed at one loop level and read at a deeper one: at most
 // kHoistPlan of them (see plan_hoist), those read by the innermost loop in
 // registers, the others in up to kHoistShared shared-memory slots per
@@ -65,6 +65,11 @@ constexpr int kCodegenVersion = 18;  // part of cached cubin names: bump wheneve
 constexpr uint32_t kHoistPlan = 224;
 constexpr uint32_t kHoistShared = 96;
 constexpr uint64_t kGrabsWanted = 4 * 148 * 8;  // four grabs per warp at 8 warps on each of 148 SMs
+// A kernel takes grabs by a static warp stride only when a launch has at
+// most two per resident warp; one whose full range has more grabs than
+// twice the most warps that can be resident (148 SMs x 64 warps) never
+// does, and is generated without that code (it would hold two registers).
+constexpr uint64_t kStrideMaxGrabs = 2 * 148 * 64;
 constexpr uint32_t kMaxJitLive = 230;        // table live set that still fits the register file
 
 const char *kMask32[5] = {"0xAAAAAAAAu", "0xCCCCCCCCu", "0xF0F0F0F0u", "0xFF00FF00u", "0xFFFF0000u"};
@@ -380,6 +385,12 @@ uint8_t tt_same(uint8_t tt, int a, int k) {  // x_k := x_a
 bool tt_reads(uint8_t tt, int k) { return tt_flip(tt, k) != tt; }
 constexpr uint8_t kVarTT[3] = {0xAA, 0xCC, 0xF0};
 
+// Whether a kernel of n support PIs and rep passes per grab carries the
+// static-stride grab code (see kStrideMaxGrabs).
+bool jit_stride_ok(uint32_t n, uint32_t rep) {
+  return num_chunks(n) / (32ull * std::max<uint32_t>(1, rep)) + 1 <= kStrideMaxGrabs;
+}
+
 // Runs of consecutive chunk-index bits: (first bit, source bit, length).
 struct BitRun {
   uint32_t at, from, len;
@@ -415,6 +426,7 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   // pass loops, outermost first: loop l (level l + 1) runs over the PIs of grp[l]
   const std::vector<uint64_t> grp = groups.empty() ? std::vector<uint64_t>{pass_pis} : groups;
   const uint32_t L = (uint32_t)grp.size();
+  const bool stride_ok = jit_stride_ok(g.n, REP);
   uint32_t roots = 0;
   const uint32_t shared_budget = shared_slots();
   // natural level of each table: its deepest pass loop (0: reads no pass PI)
@@ -565,19 +577,25 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   s << "  ld.param.u64 %d1, [p_cb];\n  ld.param.u64 %d2, [p_ce];\n  ld.param.u64 %d3, [p_cex];\n"
        "  ld.param.u64 %d4, [p_ev];\n  ld.param.u64 %d5, [p_next];\n  ld.param.u64 %d6, [p_maxg];\n"
        "  ld.param.u64 %d8, [p_q0];\n  ld.param.u64 %d9, [p_qend];\n"
-       "  setp.eq.u64 %p14, %d5, 0;\n"
-       "  cvta.to.global.u64 %d3, %d3;\n  cvta.to.global.u64 %d4, %d4;\n  cvta.to.global.u64 %d5, %d5;\n"
-       "  mov.u32 %t1, %tid.x;\n  and.b32 %t2, %t1, 31;\n  setp.eq.u32 %p1, %t2, 0;\n"
-       // p14: no grab counter -- warp w takes grabs w, w + W, w + 2W, ... (W
-       // warps in the grid); else lane 0 (p15) takes them from the counter
-       "  not.pred %p15, %p14;\n  and.pred %p15, %p15, %p1;\n"
-       "  mov.u32 %t17, %ctaid.x;\n  mov.u32 %t18, %nctaid.x;\n  shr.u32 %t19, %t1, 5;\n"
-       "  mul.wide.u32 %d35, %t17, " << (kJitBlock / 32) << ";\n  cvt.u64.u32 %d37, %t19;\n  add.u64 %d35, %d35, %d37;\n"
-       "  mul.wide.u32 %d36, %t18, " << (kJitBlock / 32) << ";\n"
-       "  mov.u64 %d10, 0;\n  mov.u64 %d11, 0;\n  @%p15 atom.global.add.u64 %d11, [%d5], 1;\n"
+       << (stride_ok ? "  setp.eq.u64 %p14, %d5, 0;\n" : "")
+    << "  cvta.to.global.u64 %d3, %d3;\n  cvta.to.global.u64 %d4, %d4;\n  cvta.to.global.u64 %d5, %d5;\n"
+       "  mov.u32 %t1, %tid.x;\n  and.b32 %t2, %t1, 31;\n  setp.eq.u32 %p1, %t2, 0;\n";
+  if (stride_ok) {
+    // p14: no grab counter -- warp w takes grabs w, w + W, w + 2W, ... (W
+    // warps in the grid); else lane 0 (p15) takes them from the counter
+    s << "  not.pred %p15, %p14;\n  and.pred %p15, %p15, %p1;\n"
+         "  mov.u32 %t17, %ctaid.x;\n  mov.u32 %t18, %nctaid.x;\n  shr.u32 %t19, %t1, 5;\n"
+         "  mul.wide.u32 %d35, %t17, "
+      << (kJitBlock / 32) << ";\n  cvt.u64.u32 %d37, %t19;\n  add.u64 %d35, %d35, %d37;\n"
+      << "  mul.wide.u32 %d36, %t18, " << (kJitBlock / 32) << ";\n";
+  } else {
+    s << "  mov.pred %p15, %p1;\n";
+  }
+  s << "  mov.u64 %d10, 0;\n  mov.u64 %d11, 0;\n  @%p15 atom.global.add.u64 %d11, [%d5], 1;\n"
        "  mov.b64 {%t3, %t4}, %d11;\n  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n"
-       "  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n  mov.b64 %d11, {%t3, %t4};\n  @%p14 mov.u64 %d11, %d35;\n"
-       "  mov.u64 %d12, 0;\n  @%p1 ld.volatile.global.u64 %d12, [%d3];\n  mov.b64 {%t3, %t4}, %d12;\n"
+       "  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n  mov.b64 %d11, {%t3, %t4};\n"
+    << (stride_ok ? "  @%p14 mov.u64 %d11, %d35;\n" : "")
+    << "  mov.u64 %d12, 0;\n  @%p1 ld.volatile.global.u64 %d12, [%d3];\n  mov.b64 {%t3, %t4}, %d12;\n"
        "  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n"
        "  mov.b64 %d12, {%t3, %t4};\n  mov.u64 %d13, 1;\n  cvt.u64.u32 %d18, %t2;\n";
   if (nsmem) s << "  mov.u32 %t21, hs;\n  shl.b32 %t22, %t1, 2;\n  add.u32 %t21, %t21, %t22;\n";
@@ -629,7 +647,8 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   emit_deposit("%d15", "%d14", gpos);
   s << "  max.u64 %d20, %d15, %d1;\n  shl.b64 %d21, %d20, 5;\n  setp.ge.u64 %p2, %d21, %d12;\n  @%p2 bra $DONE;\n"
        "  setp.lt.u64 %p3, %d13, %d6;\n  and.pred %p4, %p15, %p3;\n  mov.u64 %d16, -1;\n"
-       "  @%p4 atom.global.add.u64 %d16, [%d5], 1;\n  @%p14 add.u64 %d16, %d11, %d36;\n  mov.u64 %d17, 0;\n"
+       "  @%p4 atom.global.add.u64 %d16, [%d5], 1;\n" << (stride_ok ? "  @%p14 add.u64 %d16, %d11, %d36;\n" : "")
+    << "  mov.u64 %d17, 0;\n"
        "  @%p1 ld.volatile.global.u64 %d17, [%d3];\n"
        "  cvt.u32.u64 %t5, %d14;\n  shr.u64 %d20, %d14, 32;\n  cvt.u32.u64 %t6, %d20;\n";
   // p12: every chunk of the grab lies in [cb, ce) -- its passes then skip
@@ -1155,6 +1174,7 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   if (ptx_form) {  // the PTX form: its grab layout
     k->rep_fixed = lay.rep;
     k->pass_bits = lay.pass_pis >> 5;
+    k->stride_ok = jit_stride_ok(g.n, lay.rep);
   }
   k->load_ms = now_ms() - tl;
   k->nvrtc_ms = nvrtc_ms;
@@ -1369,7 +1389,7 @@ void jit_geometry(const JitKernel *k, uint64_t chunks, int sm_count, uint64_t *g
     const uint64_t r = k->rep_fixed;
     const uint64_t grabs = std::max<uint64_t>(1, (chunks + 32ull * r - 1) / (32ull * r)) + 1;  // + an unaligned end
     uint64_t w = std::min<uint64_t>(w_full, std::max(std::min(w_min, grabs), grabs / 4));
-    if (strided && grabs <= 2 * w_full) {
+    if (strided && k->stride_ok && grabs <= 2 * w_full) {
       *strided = true;
       w = std::min<uint64_t>(w_full, std::max(std::min(w_min, grabs), (grabs + 7) / 8));
     }
