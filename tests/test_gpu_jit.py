@@ -171,3 +171,34 @@ def test_passes_per_grab_and_hoisted_tables_keep_results(rep, hoist, nest, monke
         assert r.cex == (1 << 32) - 1
     finally:
         L.lec_es_destroy(c)
+
+
+@pytest.mark.parametrize("rep,unroll", [("", "0"), ("", "4"), ("16", "2"), ("16", "4"), ("32", "4")])
+def test_unrolled_pass_levels_keep_results(rep, unroll, monkeypatch):
+    """Nested pass loops whose innermost levels are unrolled into copies with
+    their PIs folded as constants (none, up to two or four copies): every
+    verdict and lowest counterexample equals the oracle's, also over word
+    ranges off the grab alignment."""
+    if rep:
+        monkeypatch.setenv("LEC_ES_JIT_REP", rep)
+    monkeypatch.setenv("LEC_ES_JIT_UNROLL", unroll)
+    c = make_ctx(arena_bytes=64 << 20)
+    try:
+        rng = np.random.default_rng(800 + int(unroll) + 7 * int(rep or 0))
+        cases = [C.config2_mult12(), C.config2_mult12(mutant_seed=2)]
+        for _ in range(3):
+            cases.append(random_aig(rng, int(rng.integers(12, 17)), int(rng.integers(60, 200))))
+        for aig in cases:
+            out = aig.outputs[0]
+            m = L.Miter(aig.num_pis, aig.flat_fanins(), out)
+            r = L.lec_es_check_ex(c, m, L.options(tier=L.TIER_JIT))
+            assert r.tier == L.TIER_JIT
+            assert r.cex_or_none == oracle_cex(aig, out)
+            W = 1 << max(0, r.support_n - 6)
+            for wb, we in ((W // 5 + 3, W - W // 7), (W // 2 - 1, W // 2 + 5)):
+                wb, we = max(0, wb), min(W, we)
+                if wb < we:
+                    g = L.lec_es_check_ex(c, m, L.options(wb, we, L.TIER_JIT))
+                    assert g.cex_or_none == oracle_cex(aig, out, wb, we), (wb, we)
+    finally:
+        L.lec_es_destroy(c)
