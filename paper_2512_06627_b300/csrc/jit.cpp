@@ -70,6 +70,10 @@ constexpr uint64_t kGrabsWanted = 4 * 148 * 8;  // four grabs per warp at 8 warp
 // twice the most warps that can be resident (148 SMs x 64 warps) never
 // does, and is generated without that code (it would hold two registers).
 constexpr uint64_t kStrideMaxGrabs = 2 * 148 * 64;
+// Cones of at least this many tables build their chain of layouts in
+// parallel (see compile_program_kernel), at most kMaxChain layouts at once.
+constexpr uint32_t kParallelChainTables = 1000;
+constexpr uint32_t kMaxChain = 12;
 constexpr uint32_t kMaxJitLive = 230;        // table live set that still fits the register file
 
 const char *kMask32[5] = {"0xAAAAAAAAu", "0xCCCCCCCCu", "0xF0F0F0F0u", "0xFF00FF00u", "0xFFFF0000u"};
@@ -1010,31 +1014,83 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
   if (lut_form && !g.lut.order.empty() && !via_nvrtc) {
     // values kept across loops live in registers: if ptxas has to spill,
     // move 16 more of them into shared memory while slots remain, else
-    // halve the plan, and build again
+    // shrink the plan by 16 values, and build again
     GrabLayout own;
     if (!layout) {
       jit_layout(g, &own);
       layout = &own;
     }
     uint32_t regs = layout->regs, plan = layout->plan;
-    for (;;) {
-      std::string lg;
-      SlotSplit split;
-      const int rc = compile_ptx(
-          gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis, layout->groups, &split), major,
-          minor, cubin, lg);
-      const bool spills = rc == LEC_ES_OK && lg.find(" 0 bytes spill stores") == std::string::npos &&
-                          lg.find("spill stores") != std::string::npos;
-      if (rc != LEC_ES_OK || !spills || plan == 0) {
-        log += lg;
-        return rc;
-      }
+    auto spilled = [](const std::string &lg) {
+      return lg.find(" 0 bytes spill stores") == std::string::npos && lg.find("spill stores") != std::string::npos;
+    };
+    auto next_layout = [&](const SlotSplit &split) {  // the step after a spill
       if (split.inner_in_regs > 0 && split.in_shared < shared_slots()) {
         regs = split.inner_in_regs - std::min<uint32_t>(16, split.inner_in_regs);
       } else {
         plan -= std::min<uint32_t>(16, plan);
         regs = std::min(regs, plan);
       }
+    };
+    // A large cone may need several builds.  Each step depends only on the
+    // previous layout's slot split, so the chain of layouts is generated up
+    // front and compiled on host threads at once; the first without spills
+    // in chain order is the one the serial search would keep.
+    if (g.lut.count >= kParallelChainTables && !getenv("LEC_ES_JIT_SERIAL_BUILD")) {
+      std::vector<std::string> ptx;
+      for (uint32_t i = 0; i < kMaxChain; i++) {
+        SlotSplit split;
+        ptx.push_back(gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis, layout->groups, &split));
+        if (plan == 0) break;
+        next_layout(split);
+      }
+      const size_t n = ptx.size();
+      std::vector<int> rcs(n, LEC_ES_EJIT);
+      std::vector<std::string> logs(n);
+      std::vector<std::vector<char>> bins(n);
+      std::vector<uint8_t> done(n, 0);
+      std::mutex mu;
+      size_t next_i = 0, first_ok = n;
+      auto work = [&]() {
+        for (;;) {
+          size_t i;
+          {
+            std::lock_guard<std::mutex> lk(mu);
+            if (next_i >= n || next_i > first_ok) return;  // a layout earlier in the chain already built clean
+            i = next_i++;
+          }
+          const int rc = compile_ptx(ptx[i], major, minor, bins[i], logs[i]);
+          std::lock_guard<std::mutex> lk(mu);
+          rcs[i] = rc;
+          done[i] = 1;
+          if (rc == LEC_ES_OK && !spilled(logs[i])) first_ok = std::min(first_ok, i);
+        }
+      };
+      const unsigned nt = (unsigned)std::min<size_t>(n, std::max(1u, std::thread::hardware_concurrency()));
+      std::vector<std::thread> pool;
+      for (unsigned t = 1; t < nt; t++) pool.emplace_back(work);
+      work();
+      for (auto &t : pool) t.join();
+      for (size_t i = 0; i < n && done[i]; i++) {
+        if (rcs[i] != LEC_ES_OK || !spilled(logs[i]) || i + 1 == n) {
+          log += logs[i];
+          cubin = std::move(bins[i]);
+          if (rcs[i] != LEC_ES_OK || !spilled(logs[i]) || plan == 0) return rcs[i];
+        }
+      }
+      // every layout of the chain spilled: go on from the chain's end
+    }
+    for (;;) {
+      std::string lg;
+      SlotSplit split;
+      const int rc = compile_ptx(
+          gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis, layout->groups, &split), major,
+          minor, cubin, lg);
+      if (rc != LEC_ES_OK || !spilled(lg) || plan == 0) {
+        log += lg;
+        return rc;
+      }
+      next_layout(split);
     }
   }
   return compile_cubin(gen_source(g, lut_form), major, minor, cubin, log);
