@@ -37,15 +37,15 @@ namespace {
 // single-launch device times of 71 (interpreter) and 74 (specialised kernel)
 // equivalent miters -- the 12x12 and 16x16 multiplier miters, the adders,
 // product-bit miters of 8..18-bit multipliers and node-pair miters of 4..28
-// PIs -- with median relative errors of 9% and 15% (small kernels are
+// PIs -- with median relative errors of 8% and 18% (small kernels are
 // dominated by launch latency, which three terms only approximate).
 struct Builtin {
   double a_ms, c_ms, alpha_ms;
 };
 constexpr Builtin kRun[4] = {
     {0.0, 0.0, 0.0},                  // AUTO: unused
-    {1.042e-2, 3.342e-5, 1.219e-4},   // INTERP: word-wide interpreter
-    {8.320e-3, 3.596e-6, 6.545e-7},   // JIT: specialised kernel
+    {1.112e-2, 3.176e-5, 1.227e-4},   // INTERP: word-wide interpreter
+    {7.743e-3, 2.742e-6, 6.018e-7},   // JIT: specialised kernel
     {2.0e-2, 1.0e-4, 2.0e-3},         // SPILL: global-memory interpreter (rough)
 };
 constexpr Builtin kCompile = {14.2, 0.084, 0.0};  // kernel build: ms + ms per table
