@@ -1033,10 +1033,23 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
       }
     };
     // A large cone may need several builds.  Each step depends only on the
-    // previous layout's slot split, so the chain of layouts is generated up
-    // front and compiled on host threads at once; the first without spills
-    // in chain order is the one the serial search would keep.
+    // previous layout's slot split, so after a first build that spills the
+    // rest of the chain of layouts is generated up front and compiled on
+    // host threads at once; the first without spills in chain order is the
+    // one the serial search would keep.
     if (g.lut.count >= kParallelChainTables && !getenv("LEC_ES_JIT_SERIAL_BUILD")) {
+      {
+        std::string lg;
+        SlotSplit split;
+        const int rc = compile_ptx(
+            gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis, layout->groups, &split), major,
+            minor, cubin, lg);
+        if (rc != LEC_ES_OK || !spilled(lg) || plan == 0) {
+          log += lg;
+          return rc;
+        }
+        next_layout(split);
+      }
       std::vector<std::string> ptx;
       for (uint32_t i = 0; i < kMaxChain; i++) {
         SlotSplit split;
