@@ -449,9 +449,63 @@ uint64_t fnv1a(const void *data, size_t len, uint64_t h) {
 
 }  // namespace
 
+namespace {
+// The cone facts of a miter whose kernel was found, kept with a copy of its
+// fanin array: a later call on byte-identical input skips cone extraction
+// and hashing (a sequential compare instead), then asks for the kernel again.
+struct ConeMemo {
+  const uint32_t *fanins = nullptr;
+  uint32_t num_pis = 0, num_ands = 0, out_lit = 0;
+  std::vector<uint32_t> copy;  // 2 * num_ands fanin literals
+  uint64_t hash = 0;
+  std::vector<uint32_t> support;  // 0-based PI indices
+  uint32_t cone_ands = 0;
+  int64_t root_vid = -1;
+};
+constexpr size_t kConeMemos = 4;
+
+// The elided program of a cone whose kernel the probe found.
+void elided_program(uint32_t n, const uint32_t *support, uint32_t cone_ands, uint32_t out_lit, uint64_t hash,
+                    int64_t root_vid, const KernelFacts &facts, Program &out) {
+  Program p;
+  p.n = n;
+  p.support.assign(support, support + n);
+  p.cone_ands = cone_ands;
+  p.out_compl = out_lit & 1;
+  p.hash = hash;
+  p.num_slots = facts.num_slots;
+  p.order = facts.order;
+  p.num_records = facts.num_records;
+  p.slots_elided = true;
+  p.lut.na = cone_ands;
+  p.lut.np = n;
+  p.lut.root = root_vid;
+  p.lut.count = facts.luts;
+  p.lut.live = facts.live;
+  p.lut.elided = true;
+  out = std::move(p);
+}
+}  // namespace
+
 int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Program &out, const KernelProbe *probe) {
   thread_local std::vector<uint8_t> mark;
   thread_local std::vector<int32_t> dense;
+  thread_local std::vector<ConeMemo> memos;
+  if (probe && m.fanins) {
+    for (size_t i = 0; i < memos.size(); i++) {
+      ConeMemo &e = memos[i];
+      if (e.fanins != m.fanins || e.num_pis != m.num_pis || e.num_ands != m.num_ands || e.out_lit != m.out_lit ||
+          memcmp(e.copy.data(), m.fanins, 8ull * m.num_ands) != 0)
+        continue;
+      if (e.support.size() > max_pis) return LEC_ES_ETOOBIG;
+      KernelFacts facts;
+      if (!probe->have_kernel(probe->arg, e.hash, (uint32_t)e.support.size(), e.cone_ands, &facts)) break;
+      elided_program((uint32_t)e.support.size(), e.support.data(), e.cone_ands, m.out_lit, e.hash, e.root_vid, facts,
+                     out);
+      if (i) std::rotate(memos.begin(), memos.begin() + i, memos.begin() + i + 1);  // most recent first
+      return LEC_ES_OK;
+    }
+  }
   Cone c;
   int rc = extract_cone(m, mark, c);
   if (rc) return rc;
@@ -477,24 +531,26 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
   }
   KernelFacts facts;
   if (probe && probe->have_kernel(probe->arg, chash, (uint32_t)c.pis.size(), (uint32_t)c.ands.size(), &facts)) {
-    Program p;
-    p.n = (uint32_t)c.pis.size();
-    p.support.resize(c.pis.size());
-    for (size_t k = 0; k < c.pis.size(); k++) p.support[k] = c.pis[k] - 1;
-    p.cone_ands = (uint32_t)c.ands.size();
-    p.out_compl = m.out_lit & 1;
-    p.hash = chash;
-    p.num_slots = facts.num_slots;
-    p.order = facts.order;
-    p.num_records = facts.num_records;
-    p.slots_elided = true;
-    p.lut.na = (uint32_t)c.ands.size();
-    p.lut.np = (uint32_t)c.pis.size();
-    p.lut.root = ix.vid(root_var);
-    p.lut.count = facts.luts;
-    p.lut.live = facts.live;
-    p.lut.elided = true;
-    out = std::move(p);
+    std::vector<uint32_t> sup(c.pis.size());
+    for (size_t k = 0; k < c.pis.size(); k++) sup[k] = c.pis[k] - 1;
+    const int64_t root_vid = ix.vid(root_var);
+    // remember it when the cone is most of the graph (the compare then costs
+    // about what extraction would)
+    if (m.fanins && m.num_ands <= (1u << 20) && (uint64_t)m.num_ands <= 4ull * c.ands.size() + 64) {
+      ConeMemo e;
+      e.fanins = m.fanins;
+      e.num_pis = m.num_pis;
+      e.num_ands = m.num_ands;
+      e.out_lit = m.out_lit;
+      e.copy.assign(m.fanins, m.fanins + 2ull * m.num_ands);
+      e.hash = chash;
+      e.support = sup;
+      e.cone_ands = (uint32_t)c.ands.size();
+      e.root_vid = root_vid;
+      memos.insert(memos.begin(), std::move(e));
+      if (memos.size() > kConeMemos) memos.pop_back();
+    }
+    elided_program((uint32_t)sup.size(), sup.data(), (uint32_t)c.ands.size(), m.out_lit, chash, root_vid, facts, out);
     return LEC_ES_OK;
   }
   std::vector<uint32_t> level;

@@ -202,3 +202,23 @@ def test_unrolled_pass_levels_keep_results(rep, unroll, monkeypatch):
                     assert g.cex_or_none == oracle_cex(aig, out, wb, we), (wb, we)
     finally:
         L.lec_es_destroy(c)
+
+
+def test_repeated_checks_see_a_changed_fanin_buffer(ctx):
+    """Repeated checks of one fanin buffer reuse the cone's facts only while
+    the buffer is byte-identical: after the buffer is overwritten in place
+    with a mutant (same sizes and output), the result is the mutant's, as the
+    oracle gives it."""
+    good = C.config2_mult12()
+    bad = C.config2_mult12(mutant_seed=1)
+    assert good.num_ands == bad.num_ands and good.outputs == bad.outputs
+    good_f = np.array(good.flat_fanins(), dtype=np.uint32).reshape(-1)  # private copies: the
+    bad_f = np.array(bad.flat_fanins(), dtype=np.uint32).reshape(-1)    # buffer is written below
+    m = L.Miter(good.num_pis, good_f.copy(), good.outputs[0])
+    for _ in range(3):
+        assert L.lec_es_check_ex(ctx, m, L.options(tier=L.TIER_JIT)).verdict == L.EQUIVALENT
+    m.fanins[:] = bad_f
+    r = L.lec_es_check_ex(ctx, m, L.options(tier=L.TIER_JIT))
+    assert r.cex_or_none == oracle_cex(bad, bad.outputs[0])
+    m.fanins[:] = good_f
+    assert L.lec_es_check_ex(ctx, m, L.options(tier=L.TIER_JIT)).verdict == L.EQUIVALENT
