@@ -56,7 +56,7 @@ struct JitState {
 namespace {
 
 constexpr int kJitBlock = 128;
-constexpr int kCodegenVersion = 19;  // part of cached cubin names: bump whenever the generated code changes
+constexpr int kCodegenVersion = 21;  // part of cached cubin names: bump whenever the generated code changes
 // Values computed at one loop level and read at a deeper one: at most
 // kHoistPlan of them (see plan_hoist), those read by the innermost loop in
 // registers, the others in up to kHoistShared shared-memory slots per
@@ -74,6 +74,7 @@ constexpr uint64_t kStrideMaxGrabs = 2 * 148 * 64;
 // parallel (see compile_program_kernel), at most kMaxChain layouts at once.
 constexpr uint32_t kParallelChainTables = 1000;
 constexpr uint32_t kMaxChain = 12;
+constexpr uint32_t kDryPlan = 160;  // plan of the layout search's dry runs (see jit_layout)
 constexpr uint32_t kMaxJitLive = 230;        // table live set that still fits the register file
 
 const char *kMask32[5] = {"0xAAAAAAAAu", "0xCCCCCCCCu", "0xF0F0F0F0u", "0xFF00FF00u", "0xFFFF0000u"};
@@ -277,6 +278,10 @@ uint32_t shared_slots() {
 // LEC_ES_JIT_NEST=0 keeps one pass loop, =2 nests whenever there are two
 // pass PIs or more, =3 gives every pass PI its own loop (for measurements
 // and tests).
+std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, uint32_t reg_budget,
+                        uint32_t plan_budget, uint64_t pass_pis, const std::vector<uint64_t> &groups,
+                        SlotSplit *split = nullptr, double *lop3_per_pass = nullptr);
+
 void jit_layout(const Program &g, GrabLayout *out) {
   uint64_t *const pass_pis = &out->pass_pis;
   std::vector<uint64_t> *const groups = &out->groups;
@@ -334,6 +339,70 @@ void jit_layout(const Program &g, GrabLayout *out) {
       score = best_s;
       *groups = std::move(best_g);
     }
+  }
+  // Large cones: rank candidate layouts by the lop3 the generated kernel
+  // executes per pass (a dry run of the generator, no compile), since the
+  // evaluation count above ignores the hoisting limits and the folding in
+  // unrolled levels.  Candidates: the layout above; its pass PIs, and those
+  // plus each of the next four least influential, with the m = 1, 2 most
+  // influential in the outermost loop and the others a level each, least
+  // influential (or highest PI) innermost (on the 16x16 miter b10, b11 |
+  // b12 | b13 | b14 | b15: 454 lop3 per pass against 471, 3.35 against 3.49
+  // ms).
+  if (nest_mode == 1 && g.lut.count >= kParallelChainTables && !g.lut.order.empty() && !getenv("LEC_ES_JIT_REP") &&
+      !getenv("LEC_ES_JIT_LOWPASS") && !getenv("LEC_ES_JIT_GROUPS") && npass >= 2) {
+    const std::vector<uint64_t> dep = table_support(g.lut);
+    auto influence = [&](uint32_t p) {
+      uint64_t c = 0;
+      for (uint64_t d : dep) c += (d >> p) & 1u;
+      return c;
+    };
+    struct Cand {
+      uint32_t npass;
+      uint64_t m;
+      std::vector<uint64_t> groups;
+    };
+    std::vector<Cand> cands{{npass, m, *groups}};
+    auto patterns = [&](uint32_t k, uint64_t mk) {  // most influential m in the outer loop, then one each
+      std::vector<uint32_t> ps;
+      for (uint32_t p = 0; p < 64; p++)
+        if ((mk >> p) & 1u) ps.push_back(p);
+      std::stable_sort(ps.begin(), ps.end(), [&](uint32_t a, uint32_t b) { return influence(a) > influence(b); });
+      for (uint32_t mo = 1; mo <= 2 && mo < ps.size(); mo++)
+        for (int by_index = 0; by_index < 2; by_index++) {  // the single levels by influence or by PI index
+          std::vector<uint32_t> rest(ps.begin() + mo, ps.end());
+          if (by_index) std::sort(rest.begin(), rest.end());
+          std::vector<uint64_t> gs(1, 0);
+          for (uint32_t i = 0; i < mo; i++) gs[0] |= 1ull << ps[i];
+          for (uint32_t q : rest) gs.push_back(1ull << q);
+          cands.push_back({k, mk, gs});
+        }
+    };
+    patterns(npass, m);
+    // one more pass PI: each of the next four least influential
+    const uint32_t k1 = npass + 1;
+    if (k1 <= 6 && g.n > 10 && k1 <= g.n - 10 && chunks / (32ull << k1) >= kGrabsWanted) {
+      const uint64_t more = least_influential_pis(g.lut, std::min<uint32_t>(npass + 4, g.n - 10)) & ~m;
+      for (uint32_t p = 0; p < 64; p++)
+        if ((more >> p) & 1u) patterns(k1, m | (1ull << p));
+    }
+    // compared at a plan of kDryPlan values kept across loops, about where
+    // large cones end after spill retries, so that a layout good only with
+    // more of them does not win
+    double best = -1;
+    size_t bi = 0;
+    for (size_t i = 0; i < cands.size(); i++) {
+      double per = 0;
+      gen_ptx_lut(g, 10, 3, 1u << cands[i].npass, regs, std::min(plan, kDryPlan), cands[i].m, cands[i].groups, nullptr,
+                  &per);
+      if (best < 0 || per < best) {
+        best = per;
+        bi = i;
+      }
+    }
+    npass = cands[bi].npass;
+    m = cands[bi].m;
+    *groups = cands[bi].groups;
   }
   // LEC_ES_JIT_GROUPS="27,28|29|30|31": the pass loops given explicitly,
   // outermost first, as support PI indices (for measurements)
@@ -423,7 +492,7 @@ std::vector<BitRun> bit_runs(const std::vector<uint32_t> &pos) {  // pos ascendi
 // not below the current counterexample; it also stops after max_grabs grabs.
 std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, uint32_t reg_budget,
                         uint32_t plan_budget, uint64_t pass_pis, const std::vector<uint64_t> &groups,
-                        SlotSplit *split = nullptr) {
+                        SlotSplit *split, double *lop3_per_pass) {
   const LutProgram &lp = g.lut;
   const uint32_t NA = lp.na, NP = lp.np;
   const size_t NV = NA + NP + 1;
@@ -940,6 +1009,13 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   }
   s << "  setp.ne.u64 %p8, %d10, 0;\n  and.pred %p8, %p8, %p1;\n  shl.b64 %d26, %d10, 5;\n"
        "  @%p8 red.global.add.u64 [%d4], %d26;\n  ret;\n}\n";
+  // lop3 executed per pass: loop levels' tables times their runs, the
+  // unrolled levels' lop3 once per run of level Lr
+  double per_grab = 0;
+  for (size_t i = 0; i < lp.order.size(); i++)
+    if (!isconst[lp.order[i].node] && (U == 0 || level[i] <= Lr)) per_grab += runs[level[i]];
+  per_grab += (double)unrolled_lop3 * runs[Lr];
+  if (lop3_per_pass) *lop3_per_pass = per_grab / REP;
   if (getenv("LEC_ES_JIT_LOG")) {
     std::string lv;
     for (uint32_t l = 0; l <= L; l++) {
@@ -951,12 +1027,6 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
         lv += t;
       }
     }
-    // lop3 executed per pass: loop levels' tables times their runs, the
-    // unrolled levels' lop3 once per run of level Lr
-    double per_grab = 0;
-    for (size_t i = 0; i < lp.order.size(); i++)
-      if (!isconst[lp.order[i].node] && (U == 0 || level[i] <= Lr)) per_grab += runs[level[i]];
-    per_grab += (double)unrolled_lop3 * runs[Lr];
     fprintf(stderr,
             "lec_es JIT %016llx: %u tables, rep %u, pass PIs %016llx; tables per level: %s, %u unrolled "
             "(%u read below their level, %u from shared memory); %.1f lop3 per pass\n",
