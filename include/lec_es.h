@@ -158,6 +158,9 @@ typedef struct {
   uint64_t hash;            /* structural hash of the program */
   uint32_t num_luts;        /* 3-input tables covering the cone (JIT instructions) */
   uint32_t lut_live;        /* peak live values when evaluating the tables */
+  double lop3_per_pass;     /* plan_info of a specialised-kernel plan: lop3 the kernel executes per
+                               32-pattern chunk and thread (tables once per loop level that needs them,
+                               folded copies); 0 otherwise or when unknown */
 } lec_es_program_info;
 
 /* ---- context ---------------------------------------------------------- */

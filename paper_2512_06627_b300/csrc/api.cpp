@@ -608,6 +608,7 @@ extern "C" int lec_es_plan_info(const lec_es_plan *p, lec_es_program_info *info)
   info->hash = g.hash;
   info->num_luts = g.lut.count;
   info->lut_live = g.lut.live;
+  info->lop3_per_pass = p->tier == LEC_ES_TIER_JIT && p->jit ? p->jit->lop3_per_pass : 0.0;
   return LEC_ES_OK;
 }
 

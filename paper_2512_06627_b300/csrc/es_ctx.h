@@ -62,6 +62,7 @@ struct JitKernel {
   uint32_t work_per_chunk = 0;  // straight-line instructions per 32-pattern chunk (about)
   uint32_t rep_fixed = 0;       // passes per grab compiled into the kernel (0: a launch parameter)
   bool stride_ok = false;       // the kernel can take grabs by static stride (a null counter)
+  double lop3_per_pass = 0;     // lop3 it executes per 32-pattern chunk and thread (0: unknown)
   uint64_t pass_bits = 0;       // chunk-index bits of the pass PIs (0: contiguous grabs of 32 * rep chunks)
   uint32_t chunk_bits = 0;      // bits of the chunk index (support PIs - 5)
 };

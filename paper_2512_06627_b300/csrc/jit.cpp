@@ -1077,7 +1077,10 @@ int compile_cubin(const std::string &src, int major, int minor, std::vector<char
 // The table form goes straight to PTX and the PTX compiler; the AND form
 // goes through NVRTC.
 int compile_program_kernel(const Program &g, bool lut_form, int major, int minor, std::vector<char> &cubin,
-                           std::string &log, const GrabLayout *layout = nullptr) {
+                           std::string &log, const GrabLayout *layout = nullptr, double *lop3_per_pass = nullptr) {
+  double per_sink = 0;
+  if (!lop3_per_pass) lop3_per_pass = &per_sink;
+  *lop3_per_pass = 0;
   // LEC_ES_JIT_NVRTC=1 compiles the table form from CUDA C++ through NVRTC
   // instead (same tables, for comparing the two compilation paths)
   static const bool via_nvrtc = getenv("LEC_ES_JIT_NVRTC") != nullptr;
@@ -1111,9 +1114,9 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
       {
         std::string lg;
         SlotSplit split;
-        const int rc = compile_ptx(
-            gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis, layout->groups, &split), major,
-            minor, cubin, lg);
+        const int rc = compile_ptx(gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis,
+                                               layout->groups, &split, lop3_per_pass),
+                                   major, minor, cubin, lg);
         if (rc != LEC_ES_OK || !spilled(lg) || plan == 0) {
           log += lg;
           return rc;
@@ -1121,9 +1124,13 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
         next_layout(split);
       }
       std::vector<std::string> ptx;
+      std::vector<double> pers;
       for (uint32_t i = 0; i < kMaxChain; i++) {
         SlotSplit split;
-        ptx.push_back(gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis, layout->groups, &split));
+        double per = 0;
+        ptx.push_back(
+            gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis, layout->groups, &split, &per));
+        pers.push_back(per);
         if (plan == 0) break;
         next_layout(split);
       }
@@ -1158,6 +1165,7 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
         if (rcs[i] != LEC_ES_OK || !spilled(logs[i]) || i + 1 == n) {
           log += logs[i];
           cubin = std::move(bins[i]);
+          *lop3_per_pass = pers[i];
           if (rcs[i] != LEC_ES_OK || !spilled(logs[i]) || plan == 0) return rcs[i];
         }
       }
@@ -1166,9 +1174,9 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
     for (;;) {
       std::string lg;
       SlotSplit split;
-      const int rc = compile_ptx(
-          gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis, layout->groups, &split), major,
-          minor, cubin, lg);
+      const int rc = compile_ptx(gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis,
+                                             layout->groups, &split, lop3_per_pass),
+                                 major, minor, cubin, lg);
       if (rc != LEC_ES_OK || !spilled(lg) || plan == 0) {
         log += lg;
         return rc;
@@ -1274,16 +1282,25 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
     path = c->jit_dir + name;
   }
   double nvrtc_ms = 0;
+  double lop3_per_pass = 0;  // of the PTX form's kernel (a sidecar file next to a cached cubin)
   if (path.empty() || !read_file(path, cubin)) {
     std::string log;
     const double tn = now_ms();
-    int rc = compile_program_kernel(g, lut_form, c->cc_major, c->cc_minor, cubin, log, ptx_form ? &lay : nullptr);
+    int rc = compile_program_kernel(g, lut_form, c->cc_major, c->cc_minor, cubin, log, ptx_form ? &lay : nullptr,
+                                    &lop3_per_pass);
     nvrtc_ms = now_ms() - tn;
     if (rc) {
       if (getenv("LEC_ES_JIT_LOG")) fprintf(stderr, "lec_es JIT failed:\n%s\n", log.c_str());
       return rc;
     }
-    if (!path.empty()) write_file(path, cubin);
+    if (!path.empty()) {
+      write_file(path, cubin);
+      const std::string txt = std::to_string(lop3_per_pass);
+      write_file(path + ".lop3", std::vector<char>(txt.begin(), txt.end()));
+    }
+  } else {
+    std::vector<char> txt;
+    if (read_file(path + ".lop3", txt)) lop3_per_pass = atof(std::string(txt.begin(), txt.end()).c_str());
   }
   cudaSetDevice(c->device);
   const double tl = now_ms();
@@ -1314,6 +1331,7 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
     k->rep_fixed = lay.rep;
     k->pass_bits = lay.pass_pis >> 5;
     k->stride_ok = jit_stride_ok(g.n, lay.rep);
+    k->lop3_per_pass = lop3_per_pass;
   }
   k->load_ms = now_ms() - tl;
   k->nvrtc_ms = nvrtc_ms;
