@@ -222,3 +222,21 @@ def test_repeated_checks_see_a_changed_fanin_buffer(ctx):
     assert r.cex_or_none == oracle_cex(bad, bad.outputs[0])
     m.fanins[:] = good_f
     assert L.lec_es_check_ex(ctx, m, L.options(tier=L.TIER_JIT)).verdict == L.EQUIVALENT
+
+
+def test_plan_info_reports_lop3_per_pass(ctx):
+    """A specialised-kernel plan reports the lop3 its kernel executes per
+    32-pattern chunk (at most one per table, fewer where tables run once per
+    loop level or fold in unrolled copies); an interpreter plan reports 0."""
+    m = L.miter_of(C.config2_mult12())
+    p = L.lec_es_prepare(ctx, m, L.options(tier=L.TIER_JIT))
+    try:
+        info = L.lec_es_plan_info(p)
+        assert 0 < info.lop3_per_pass <= info.num_luts
+    finally:
+        L.lec_es_plan_free(ctx, p)
+    p = L.lec_es_prepare(ctx, m, L.options(tier=L.TIER_INTERP))
+    try:
+        assert L.lec_es_plan_info(p).lop3_per_pass == 0
+    finally:
+        L.lec_es_plan_free(ctx, p)
