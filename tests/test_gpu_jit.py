@@ -240,3 +240,44 @@ def test_plan_info_reports_lop3_per_pass(ctx):
         assert L.lec_es_plan_info(p).lop3_per_pass == 0
     finally:
         L.lec_es_plan_free(ctx, p)
+
+
+def test_searched_layouts_agree_with_the_flat_kernel(monkeypatch):
+    """Cones of 1,000 tables or more get a layout chosen by dry runs of the
+    generator (more pass PIs, nested and unrolled levels).  Too large for
+    the oracle's enumeration, their lowest counterexamples are compared with
+    those of the simplest kernel form (one pass loop, nothing unrolled),
+    itself pinned to the oracle on small cones, over the full pattern space
+    and random word ranges."""
+    pm = C.ProductBitMiters(seed=5)
+    cases = [pm.miter(15, 22, mutant=True, mutant_seed=s) for s in (1, 2)]
+    cases.append(pm.miter(14, 26, mutant=True, mutant_seed=3))
+    rng = np.random.default_rng(77)
+
+    def lowest(env):
+        for k in ("LEC_ES_JIT_NEST", "LEC_ES_JIT_UNROLL"):
+            monkeypatch.delenv(k, raising=False)
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        c = make_ctx(arena_bytes=64 << 20)
+        try:
+            out = []
+            for (aig, o), ranges in zip(cases, spans):
+                m = L.Miter(aig.num_pis, aig.flat_fanins(), o)
+                for wb, we in ranges:
+                    r = L.lec_es_check_ex(c, m, L.options(wb, we, L.TIER_JIT))
+                    assert r.tier == L.TIER_JIT
+                    out.append(r.cex_or_none)
+            return out
+        finally:
+            L.lec_es_destroy(c)
+
+    spans = []
+    for aig, o in cases:
+        info, _ = L.lec_es_compile(L.Miter(aig.num_pis, aig.flat_fanins(), o))
+        W = 1 << (info.n - 6)
+        spans.append([(0, W)] + [tuple(sorted(int(x) for x in rng.integers(0, W, 2))) for _ in range(3)])
+    searched = lowest({})
+    flat = lowest({"LEC_ES_JIT_NEST": "0", "LEC_ES_JIT_UNROLL": "0"})
+    assert searched == flat
+    assert any(x is not None for x in searched)
