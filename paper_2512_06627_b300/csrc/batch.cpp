@@ -46,7 +46,12 @@
 using namespace lec;
 
 namespace {
-constexpr double kBatchJitMs = 0.05;     // predicted interpreter time above which a miter gets its own kernel
+// Predicted interpreter time above which a miter gets its own kernel; the
+// rest share the tile queue, which runs beside the kernels and must not
+// outlast them.  On the 4,096 node-pair batch (B300): 0.2 / 0.1 / 0.05 /
+// 0.03 / 0.025 / 0.02 / 0.0125 / 0.005 ms -> 25.3 / 10.5 / 5.39 / 4.09 /
+// 3.89 / 3.84 / 4.05 / 5.12 ms per batch.
+constexpr double kBatchJitMs = 0.02;
 constexpr uint32_t kBatchJitLive = 230;  // table live set that still fits the register file
 constexpr int kMaxBranches = 16;         // parallel graph branches (at most)
 constexpr int kDefaultBranches = 4;
