@@ -54,7 +54,7 @@ namespace {
 constexpr double kBatchJitMs = 0.02;
 constexpr uint32_t kBatchJitLive = 230;  // table live set that still fits the register file
 constexpr int kMaxBranches = 16;         // parallel graph branches (at most)
-constexpr int kDefaultBranches = 4;
+constexpr int kDefaultBranches = 8;  // 4 / 8 / 16 branches: 3.85 / 3.80 / 3.78 ms on the 4,096-pair batch
 
 struct Layout {
   int block = 256;            // threads (64-pattern words) per tile pass
