@@ -48,7 +48,11 @@ namespace lec {
 namespace {
 
 constexpr uint32_t kNone = 0xFFFFFFFFu;
-constexpr uint32_t kMissRun = 1024;  // consecutive too-wide regions that end a round's cutting
+// Consecutive too-wide regions that end a round's cutting: the pairs above
+// the merged frontier fail until lower pairs merge.  128, 256 and 1,024 all
+// prove the 32x32 array and Booth pairs in the same 35 and 6 rounds; 128
+// bounds a round's trailing failed cuts at 128 instead of 1,024.
+constexpr uint32_t kMissRun = 128;
 constexpr uint32_t kNoMeet = 48;     // region ANDs walked before the two cones must have met
 
 struct Graph {
