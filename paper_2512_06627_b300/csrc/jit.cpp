@@ -389,17 +389,31 @@ void jit_layout(const Program &g, GrabLayout *out) {
     // compared at a plan of kDryPlan values kept across loops, about where
     // large cones end after spill retries, so that a layout good only with
     // more of them does not win
-    double best = -1;
-    size_t bi = 0;
-    for (size_t i = 0; i < cands.size(); i++) {
-      double per = 0;
-      gen_ptx_lut(g, 10, 3, 1u << cands[i].npass, regs, std::min(plan, kDryPlan), cands[i].m, cands[i].groups, nullptr,
-                  &per);
-      if (best < 0 || per < best) {
-        best = per;
-        bi = i;
-      }
+    std::vector<double> per(cands.size(), 0.0);
+    {  // independent dry runs, on host threads
+      std::mutex mu;
+      size_t next = 0;
+      auto work = [&]() {
+        for (;;) {
+          size_t i;
+          {
+            std::lock_guard<std::mutex> lk(mu);
+            if (next >= cands.size()) return;
+            i = next++;
+          }
+          gen_ptx_lut(g, 10, 3, 1u << cands[i].npass, regs, std::min(plan, kDryPlan), cands[i].m, cands[i].groups,
+                      nullptr, &per[i]);
+        }
+      };
+      const unsigned nt = (unsigned)std::min<size_t>(cands.size(), std::max(1u, std::thread::hardware_concurrency()));
+      std::vector<std::thread> pool;
+      for (unsigned t = 1; t < nt; t++) pool.emplace_back(work);
+      work();
+      for (auto &t : pool) t.join();
     }
+    size_t bi = 0;
+    for (size_t i = 1; i < cands.size(); i++)
+      if (per[i] < per[bi]) bi = i;
     npass = cands[bi].npass;
     m = cands[bi].m;
     *groups = cands[bi].groups;
