@@ -1,22 +1,31 @@
 // jit.cpp -- specialised exact-simulation kernels compiled at run time.
 //
-// The slot program of one cone (paper §3.3: a branch-free instruction stream
-// over reference-counted registers) is emitted as straight-line CUDA C++ in
-// which every AND is one 32-bit expression (one LOP3 after compilation, with
-// the complements folded into the LUT) and every value lives in a register.
-// The register allocator sees exactly the live ranges the slot program's
-// evaluation order creates, so the slot count bounds the register demand.
-// NVRTC compiles the source for sm_103a straight to a cubin (cached in
-// memory by program hash and optionally on disk); the runtime's library API
-// loads it, so the library never links the driver API.
+// The cone of one miter (paper §3.3: a branch-free instruction stream over
+// reference-counted registers) becomes straight-line code in which every
+// value lives in a register.  Two forms:
 //
-// Work split: thread t of the grid takes 32-pattern chunks c = begin + t,
-// begin + t + T, ... (T = threads in the grid).  For each chunk it forms the
-// support PI words (constant masks for PIs 0..4, all-ones/all-zeros from the
-// bits of c for PIs >= 5), runs the body, and reduces the miter output with a
-// warp ballot; the lowest failing lane does atomicMin on the counterexample.
-// Before every chunk a warp compares its first pattern with the current
-// counterexample (loaded one iteration ahead) and stops if it is not lower.
+//   table form (default): the cone's 3-input table cover (lutmap.cpp) is
+//     written directly as PTX, one lop3 per table with constants as
+//     immediates, and compiled for sm_103a by the PTX compiler library;
+//   C++ forms: one expression per AND (LEC_ES_FLAG_JIT_AND_FORM), or the
+//     tables as C++ (LEC_ES_JIT_NVRTC), compiled by NVRTC -- kept for the
+//     AND option and for comparing the compilation paths.
+//
+// Cubins are cached in memory by the cone's structural hash and optionally
+// on disk; the runtime's library API loads them (no driver API).
+//
+// Work split of the table form: bits 0..4 of a 32-pattern chunk index are
+// the lane (support PIs 5..9, fixed per thread); a few support PIs are pass
+// PIs and the rest select the grab.  Warps take grabs from a counter (one
+// ahead) or, on small launches, by a static stride; a grab is every chunk
+// whose grab bits spell its number, run as passes over the pass PIs in
+// nested loops (jit_layout, choose_pass_groups, and dry runs of the
+// generator for large cones).  Each table runs once per iteration of the
+// loop of its deepest pass PI (plan_hoist decides what survives a loop);
+// the innermost levels are unrolled with their PIs folded as constants.
+// The miter output is reduced with a warp ballot and the lowest failing
+// lane does atomicMin on the counterexample; a warp stops when its grab's
+// lowest pattern is not below the current counterexample.
 #include <cuda_runtime.h>
 #include <nvPTXCompiler.h>
 #include <nvrtc.h>
