@@ -84,6 +84,10 @@ constexpr uint64_t kStrideMaxGrabs = 2 * 148 * 64;
 constexpr uint32_t kParallelChainTables = 1000;
 constexpr uint32_t kMaxChain = 12;
 constexpr uint32_t kDryPlan = 160;  // plan of the layout search's dry runs (see jit_layout)
+// Set while a single plan's kernel builds on the calling thread (the host is
+// otherwise idle): a large cone's first layout and the rest of its chain then
+// build at once, instead of the rest only after the first spills.
+thread_local bool t_single_build = false;
 constexpr uint32_t kMaxJitLive = 230;        // table live set that still fits the register file
 
 const char *kMask32[5] = {"0xAAAAAAAAu", "0xCCCCCCCCu", "0xF0F0F0F0u", "0xFF00FF00u", "0xFFFF0000u"};
@@ -1129,12 +1133,12 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
       }
     };
     // A large cone may need several builds.  Each step depends only on the
-    // previous layout's slot split, so after a first build that spills the
-    // rest of the chain of layouts is generated up front and compiled on
-    // host threads at once; the first without spills in chain order is the
-    // one the serial search would keep.
+    // previous layout's slot split, so after a first build that spills (or
+    // at once, for a single plan's build) the chain of layouts is generated
+    // up front and compiled on host threads together; the first without
+    // spills in chain order is the one the serial search would keep.
     if (g.lut.count >= kParallelChainTables && !getenv("LEC_ES_JIT_SERIAL_BUILD")) {
-      {
+      if (!t_single_build) {
         std::string lg;
         SlotSplit split;
         const int rc = compile_ptx(gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis,
@@ -1477,7 +1481,9 @@ int jit_prepare(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt) {
   JitState *js = state(c);
   (void)js;
   JitKernel *k = nullptr;
+  t_single_build = true;
   int rc = jit_get_kernel(c, g, p->jit_lut, &k, &p->jit_ms);
+  t_single_build = false;
   if (rc) return rc;
   return jit_attach(c, p, k, opt);
 }
