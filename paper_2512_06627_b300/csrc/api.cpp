@@ -125,15 +125,19 @@ void run_res_destroy_all(lec_es_ctx *c) {
 }
 
 // Wait for an event with a host-side deadline (no unbounded synchronize).
+// Polls the event: for the first 20 ms it yields between polls (a check's
+// caller is blocked anyway, and a 50 us sleep would add up to its length
+// plus the scheduler's slack to every run), then sleeps 50 us per poll.
 int wait_event(cudaEvent_t ev, double timeout_s) {
   const double t0 = now_ms();
-  unsigned spins = 0;
   for (;;) {
     cudaError_t e = cudaEventQuery(ev);
     if (e == cudaSuccess) return LEC_ES_OK;
     if (e != cudaErrorNotReady) return LEC_ES_ECUDA;
-    if (now_ms() - t0 > timeout_s * 1e3) return LEC_ES_ETIMEOUT;
-    if (++spins > 200) std::this_thread::sleep_for(std::chrono::microseconds(50));
+    const double waited = now_ms() - t0;
+    if (waited > timeout_s * 1e3) return LEC_ES_ETIMEOUT;
+    if (waited < 20.0) std::this_thread::yield();
+    else std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
 }
 
