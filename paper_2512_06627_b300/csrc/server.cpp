@@ -320,9 +320,9 @@ void dispatcher(Server *s) {
     }
     if (s->running.empty()) {
       s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
-    } else {
+    } else {  // requests in flight: poll again soon (this thread only schedules)
       lk.unlock();
-      std::this_thread::sleep_for(std::chrono::microseconds(50));
+      std::this_thread::yield();
       lk.lock();
     }
   }
