@@ -258,16 +258,6 @@ std::string gen_source(const Program &g, bool lut_form) {
   return lut_form && !g.lut.order.empty() ? gen_source_lut(g) : gen_source_and(g);
 }
 
-// Passes per grab (a power of two), the hoisting budget and the pass PIs of
-// a table-form kernel.  Long grabs amortise hoisted tables (and the
-// counter's atomic): 16 to 32 passes, at least ~4k instructions per grab; but
-// a small pattern space keeps enough grabs to fill the GPU, which wins over
-// both.  The pass PIs are the support PIs (index >= 10) the fewest tables
-// depend on, so the most tables are the same in every pass of a grab.
-// The passes run as nested loops over groups of pass PIs when that saves
-// enough table evaluations (choose_pass_groups).
-// LEC_ES_JIT_REP / LEC_ES_JIT_HOIST override passes and budget,
-// LEC_ES_JIT_LOWPASS=1 takes PIs 10, 11, ... as the pass PIs and
 // The grab layout of a table-form kernel (jit_layout).
 struct GrabLayout {
   uint32_t rep = 0;
@@ -288,13 +278,24 @@ uint32_t shared_slots() {
   return std::min<uint32_t>(sh ? (uint32_t)std::max(0, atoi(sh)) : kHoistShared, kHoistShared);
 }
 
-// LEC_ES_JIT_NEST=0 keeps one pass loop, =2 nests whenever there are two
-// pass PIs or more, =3 gives every pass PI its own loop (for measurements
-// and tests).
 std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, uint32_t reg_budget,
                         uint32_t plan_budget, uint64_t pass_pis, const std::vector<uint64_t> &groups,
                         SlotSplit *split = nullptr, double *lop3_per_pass = nullptr);
 
+// Passes per grab (a power of two), the hoisting budget and the pass PIs of
+// a table-form kernel.  Long grabs amortise hoisted tables (and the
+// counter's atomic): 16 to 32 passes, at least ~4k instructions per grab; but
+// a small pattern space keeps enough grabs to fill the GPU, which wins over
+// both.  The pass PIs are the support PIs (index >= 10) the fewest tables
+// depend on, so the most tables are the same in every pass of a grab.  The
+// passes run as nested loops over groups of pass PIs when that saves enough
+// table evaluations (choose_pass_groups), with up to two more pass PIs, and
+// large cones then pick among candidate layouts by dry runs of the generator.
+// LEC_ES_JIT_REP / LEC_ES_JIT_HOIST override passes and budget,
+// LEC_ES_JIT_LOWPASS=1 takes PIs 10, 11, ... as the pass PIs,
+// LEC_ES_JIT_NEST=0 keeps one pass loop, =2 nests whenever there are two
+// pass PIs or more, =3 gives every pass PI its own loop, and
+// LEC_ES_JIT_GROUPS gives the loops explicitly (for measurements and tests).
 void jit_layout(const Program &g, GrabLayout *out) {
   uint64_t *const pass_pis = &out->pass_pis;
   std::vector<uint64_t> *const groups = &out->groups;
