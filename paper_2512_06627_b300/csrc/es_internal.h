@@ -106,9 +106,9 @@ void plan_hoist_from(const LutProgram &lp, uint64_t pass_pis, uint32_t budget, c
 uint64_t least_influential_pis(const LutProgram &lp, uint32_t k);
 // The support PIs (bit k: support PI k, k < 64) each table of lp.order depends on.
 std::vector<uint64_t> table_support(const LutProgram &lp);
-// Nested pass loops: the pass PIs split into groups, outermost loop first,
-// chosen to minimise table evaluations per grab, each extra loop level
-// charged 3%.  mode 0: one loop; 1: chosen; 2: chosen among two levels or
+// Nested pass loops: the pass PIs split into at most four groups, outermost
+// loop first, chosen to minimise table evaluations per grab, each extra loop
+// level charged 3%.  mode 0: one loop; 1: chosen; 2: chosen among two levels or
 // more; 3: one loop per pass PI.  *score: the chosen nesting's table
 // evaluations per grab (with the level charge; for modes 0 and 3, those of
 // one loop).
