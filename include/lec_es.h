@@ -374,7 +374,12 @@ int lec_es_sweep(lec_es_ctx *c, const lec_es_miter *m, const lec_es_sweep_option
  * the program (the floor of a small support on a GPU):
  *   t_ms = a_ms + c_ms * gates + alpha_ms * gates * 2^(n - 23),
  * gates = cone ANDs, n = support PIs.  Build time of a specialised kernel:
- * a_ms + c_ms * tables (alpha_ms = 0). */
+ * a_ms + c_ms * tables (alpha_ms = 0).  Once a context holds a cone's
+ * kernel, its predicted time follows what that kernel executes instead of
+ * the gates (hoisting and folded pass PIs make the two differ by up to 4x):
+ *   t_ms = a_ms + c_ms * gates + alpha_ms * (lop3_per_pass + 40) * 2^(n - 23),
+ * lop3_per_pass as in lec_es_program_info and 40 the per-pass overhead of
+ * the kernel's loop and result check in lop3-equivalents (fitted on B300). */
 typedef struct {
   double a_ms;              /* fixed cost per run (ms) */
   double c_ms;              /* ms per gate, independent of n */
@@ -384,7 +389,8 @@ typedef struct {
 
 typedef struct {
   double interp_ms;         /* predicted device time on the interpreter tier */
-  double jit_ms;            /* predicted device time of the specialised kernel */
+  double jit_ms;            /* predicted device time of the specialised kernel (by its
+                               executed lop3 when the context holds it, else by gates) */
   double jit_compile_ms;    /* predicted build time (0 if the context holds the kernel) */
   double paper_cpu_s;       /* the paper's one-core CPU model: 0.0003 s * gates * 2^(n-23) */
   uint32_t gates, n, num_luts;
@@ -399,9 +405,11 @@ typedef struct {
 int lec_es_cost_fit(const uint32_t *gates, const uint32_t *n, const double *ms, size_t k,
                     lec_es_cost_coeffs *out);
 /* The context's current coefficients for tier (LEC_ES_TIER_INTERP, _JIT,
- * _SPILL) or 4 for kernel builds.  Each context starts from built-in B300
- * values and folds in its own full, equivalent runs (single checks and
- * served requests) and kernel builds.  c may be NULL: built-in values. */
+ * _SPILL), 4 for kernel builds or 5 for the specialised kernel's time by
+ * its executed lop3 (the second form above).  Each context starts from
+ * built-in B300 values and folds in its own full, equivalent runs (single
+ * checks and served requests) and kernel builds.  c may be NULL: built-in
+ * values. */
 int lec_es_cost_model(lec_es_ctx *c, uint32_t tier, lec_es_cost_coeffs *out);
 /* Predicted times of miter m (front end on the host; nothing runs on the
  * GPU) and the tier an AUTO check would take.  c may be NULL: built-in

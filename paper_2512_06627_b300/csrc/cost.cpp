@@ -13,7 +13,13 @@
 // The fit minimises relative error (weights 1/t^2) with a, c, alpha >= 0.  A
 // context starts from values measured on B300 (entered as pseudo-samples, so
 // they act as a prior) and folds in every full, equivalent single run it
-// times; kernel builds are fitted as a + c * tables.  The model decides the
+// times; kernel builds are fitted as a + c * tables.  A built specialised
+// kernel reports the lop3 it executes per 32-pattern pass, which tracks its
+// time far better than the gates do (hoisted tables and folded pass PIs
+// remove 10-90% of the work, by cone), so runs of a known kernel are also
+// fitted and predicted with x = (lop3 + 40) * 2^(n - 23), 40 being the
+// per-pass loop and result-check overhead in lop3-equivalents (the value
+// with the least median error over the calibration set).  The model decides the
 // tier of AUTO runs (jit_auto_tier), which batch miters get their own
 // kernel, and the priority class of served requests.
 #include <math.h>
@@ -48,6 +54,10 @@ constexpr Builtin kRun[4] = {
     {7.743e-3, 2.742e-6, 6.018e-7},   // JIT: specialised kernel
     {2.0e-2, 1.0e-4, 2.0e-3},         // SPILL: global-memory interpreter (rough)
 };
+// By the kernel's executed lop3, over the same 74 kernel times: median
+// relative error 6% (15% by gates), 4% on supports of 24 PIs and more.
+constexpr Builtin kKernel = {7.969e-3, 9.354e-7, 1.2574e-5};
+constexpr double kPassOverhead = 40.0;  // lop3-equivalents per pass outside the tables
 constexpr Builtin kCompile = {14.2, 0.084, 0.0};  // kernel build: ms + ms per table
 constexpr double kPriorWeight = 4.0;             // the built-in values count as this many samples each
 constexpr double kBinCap = 8.0;                  // a (n, log2 gates) bin counts as at most this many
@@ -160,6 +170,7 @@ void seed_compile(CostFit &f) {
 void ensure(CostModel &m) {
   if (m.ready) return;
   for (int t = 0; t < 4; t++) seed(m.tier[t], kRun[t]);
+  seed(m.kernel, kKernel);
   seed_compile(m.compile);
   m.ready = true;
 }
@@ -168,16 +179,20 @@ void ensure(CostModel &m) {
 
 double cost_x(uint32_t gates, uint32_t n) { return (double)gates * ldexp(1.0, (int)n - 23); }
 
-double cost_run_ms(lec_es_ctx *c, uint32_t tier, uint32_t gates, uint32_t n) {
+double cost_kernel_x(double lop3, uint32_t n) { return (lop3 + kPassOverhead) * ldexp(1.0, (int)n - 23); }
+
+double cost_run_ms(lec_es_ctx *c, uint32_t tier, uint32_t gates, uint32_t n, double lop3) {
   if (tier > 3 || tier == 0) tier = LEC_ES_TIER_INTERP;
-  const double x = cost_x(gates, n);
+  const bool by_lop3 = tier == LEC_ES_TIER_JIT && lop3 > 0;
+  const double x = by_lop3 ? cost_kernel_x(lop3, n) : cost_x(gates, n);
   if (!c) {
-    const double co[3] = {kRun[tier].a_ms, kRun[tier].c_ms, kRun[tier].alpha_ms};
+    const Builtin b = by_lop3 ? kKernel : kRun[tier];
+    const double co[3] = {b.a_ms, b.c_ms, b.alpha_ms};
     return eval(co, gates, x);
   }
   std::lock_guard<std::mutex> g(c->cost.mu);
   ensure(c->cost);
-  return eval(c->cost.tier[tier].coef, gates, x);
+  return eval(by_lop3 ? c->cost.kernel.coef : c->cost.tier[tier].coef, gates, x);
 }
 
 double cost_compile_ms(lec_es_ctx *c, uint32_t tables) {
@@ -187,19 +202,22 @@ double cost_compile_ms(lec_es_ctx *c, uint32_t tables) {
   return c->cost.compile.coef[0] + c->cost.compile.coef[1] * tables;
 }
 
-void cost_add_run(lec_es_ctx *c, uint32_t tier, uint32_t gates, uint32_t n, double ms) {
+void cost_add_run(lec_es_ctx *c, uint32_t tier, uint32_t gates, uint32_t n, double ms, double lop3) {
   if (!c || tier == 0 || tier > 3 || !(ms > 0)) return;
   std::lock_guard<std::mutex> g(c->cost.mu);
   ensure(c->cost);
-  CostFit &f = c->cost.tier[tier];
   const uint32_t lg = gates ? 32u - (uint32_t)__builtin_clz(gates) : 0u;
-  CostSums &bin = f.bins[n << 8 | lg];
-  add_point(bin, gates, cost_x(gates, n), ms, 1.0);
-  bin.count++;
-  f.samples++;
-  CostFit tot;
-  totals(f, tot);
-  solve(tot, f.coef);
+  auto fold = [&](CostFit &f, double x) {
+    CostSums &bin = f.bins[n << 8 | lg];
+    add_point(bin, gates, x, ms, 1.0);
+    bin.count++;
+    f.samples++;
+    CostFit tot;
+    totals(f, tot);
+    solve(tot, f.coef);
+  };
+  fold(c->cost.tier[tier], cost_x(gates, n));
+  if (tier == LEC_ES_TIER_JIT && lop3 > 0) fold(c->cost.kernel, cost_kernel_x(lop3, n));
 }
 
 void cost_add_compile(lec_es_ctx *c, uint32_t tables, double ms) {
@@ -260,9 +278,9 @@ extern "C" int lec_es_cost_fit(const uint32_t *gates, const uint32_t *n, const d
 }
 
 extern "C" int lec_es_cost_model(lec_es_ctx *c, uint32_t tier, lec_es_cost_coeffs *out) {
-  if (!out || tier == 0 || tier > 4) return LEC_ES_EINVAL;
+  if (!out || tier == 0 || tier > 5) return LEC_ES_EINVAL;
   if (!c) {
-    const Builtin b = tier == 4 ? kCompile : kRun[tier];
+    const Builtin b = tier == 5 ? kKernel : tier == 4 ? kCompile : kRun[tier];
     out->a_ms = b.a_ms;
     out->c_ms = b.c_ms;
     out->alpha_ms = b.alpha_ms;
@@ -271,7 +289,7 @@ extern "C" int lec_es_cost_model(lec_es_ctx *c, uint32_t tier, lec_es_cost_coeff
   }
   std::lock_guard<std::mutex> g(c->cost.mu);
   ensure(c->cost);
-  const CostFit &f = tier == 4 ? c->cost.compile : c->cost.tier[tier];
+  const CostFit &f = tier == 5 ? c->cost.kernel : tier == 4 ? c->cost.compile : c->cost.tier[tier];
   out->a_ms = f.coef[0];
   out->c_ms = f.coef[1];
   out->alpha_ms = f.coef[2];
@@ -301,7 +319,7 @@ extern "C" int lec_es_cost_predict(lec_es_ctx *c, const lec_es_miter *m, uint32_
   out->n = g.n;
   out->num_luts = g.lut.count;
   out->interp_ms = cost_run_ms(c, LEC_ES_TIER_INTERP, g.cone_ands, g.n);
-  out->jit_ms = cost_run_ms(c, LEC_ES_TIER_JIT, g.cone_ands, g.n);
+  out->jit_ms = cost_run_ms(c, LEC_ES_TIER_JIT, g.cone_ands, g.n, c ? jit_held_lop3(c, g) : 0.0);
   out->jit_compile_ms = g.lut.elided ? 0.0 : cost_compile_ms(c, g.lut.count);
   out->tier = jit_auto_tier(c, g, num_chunks(g.n));
   // the paper's one-core CPU model and its GPU-offload rule (§3.2): ES goes

@@ -92,6 +92,7 @@ struct CostModel {
   std::mutex mu;
   CostFit tier[4];       // indexed by LEC_ES_TIER_*
   CostFit compile;       // specialised-kernel build: a + c * tables (coef[0], coef[1])
+  CostFit kernel;        // specialised kernel by its executed lop3: x = (lop3 + 40) * 2^(n - 23)
   bool ready = false;
 };
 
@@ -104,10 +105,12 @@ int simulate(lec_es_ctx *c, uint32_t num_pis, uint32_t num_ands, const uint32_t 
              uint32_t nwords, uint64_t *h_sigs, uint64_t *h_hash, uint64_t *h_sup, bool norm);
 
 // ES time model (cost.cpp).  c may be null (built-in values only).
+// lop3 > 0 (the executed lop3 per pass of a built specialised kernel)
+// predicts or fits a JIT run by that kernel's work instead of its gates.
 double cost_x(uint32_t gates, uint32_t n);
-double cost_run_ms(lec_es_ctx *c, uint32_t tier, uint32_t gates, uint32_t n);
+double cost_run_ms(lec_es_ctx *c, uint32_t tier, uint32_t gates, uint32_t n, double lop3 = 0);
 double cost_compile_ms(lec_es_ctx *c, uint32_t tables);
-void cost_add_run(lec_es_ctx *c, uint32_t tier, uint32_t gates, uint32_t n, double ms);
+void cost_add_run(lec_es_ctx *c, uint32_t tier, uint32_t gates, uint32_t n, double ms, double lop3 = 0);
 void cost_add_compile(lec_es_ctx *c, uint32_t tables, double ms);
 // Weighted (relative-error) least squares of t = a + c g + alpha x with all
 // three coefficients >= 0; coef = (a, c, alpha).
@@ -121,6 +124,8 @@ bool choose_word_geometry(lec_es_ctx *c, const Program &prog, const lec_es_optio
 
 // JIT tier (jit.cpp)
 uint32_t jit_auto_tier(lec_es_ctx *c, const Program &g, uint64_t chunks);
+// Executed lop3 per pass of the held kernel of g's cone (0: none held).
+double jit_held_lop3(lec_es_ctx *c, const Program &g);
 int jit_prepare(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt);
 // Passes of 32 chunks per grab for a launch of `grid` blocks over `chunks`.
 uint64_t jit_reps(const JitKernel *k, uint64_t chunks, uint64_t grid);

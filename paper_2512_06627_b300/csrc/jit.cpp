@@ -1266,6 +1266,16 @@ int compile_cubin(const std::string &src, int major, int minor, std::vector<char
 uint64_t cache_key(const Program &g, bool lut_form);
 JitState *state(lec_es_ctx *c);
 
+// Executed lop3 per pass of the kernel this context holds for g's cone, or
+// 0 if it holds none (or does not know the figure).
+double jit_held_lop3(lec_es_ctx *c, const Program &g) {
+  if (!c || g.lut.count == 0) return 0.0;
+  JitState *js = state(c);
+  std::lock_guard<std::mutex> lk(js->mu);
+  auto it = js->cache.find(cache_key(g, true));
+  return it == js->cache.end() ? 0.0 : it->second->lop3_per_pass;
+}
+
 // The ES time model (cost.cpp) decides: the specialised kernel when its
 // predicted time, plus the predicted build time unless this context already
 // holds the kernel, is below the interpreter's.  Cones whose table live set
@@ -1280,7 +1290,8 @@ uint32_t jit_auto_tier(lec_es_ctx *c, const Program &g, uint64_t chunks) {
     cached = js->cache.count(cache_key(g, true)) != 0;
   }
   const double t_int = cost_run_ms(c, LEC_ES_TIER_INTERP, g.cone_ands, g.n);
-  const double t_jit = cost_run_ms(c, LEC_ES_TIER_JIT, g.cone_ands, g.n) + (cached ? 0.0 : cost_compile_ms(c, g.lut.count));
+  const double t_jit = cached ? cost_run_ms(c, LEC_ES_TIER_JIT, g.cone_ands, g.n, c ? jit_held_lop3(c, g) : 0.0)
+                              : cost_run_ms(c, LEC_ES_TIER_JIT, g.cone_ands, g.n) + cost_compile_ms(c, g.lut.count);
   return t_jit < t_int ? LEC_ES_TIER_JIT : LEC_ES_TIER_INTERP;
 }
 
@@ -1412,8 +1423,8 @@ bool jit_probe(void *arg, uint64_t hash, uint32_t n, uint32_t cone_ands, KernelF
     case JitProbe::kInfo:
       break;
     case JitProbe::kAuto:
-      if (k->lut_live > kMaxJitLive ||
-          !(cost_run_ms(c, LEC_ES_TIER_JIT, cone_ands, n) < cost_run_ms(c, LEC_ES_TIER_INTERP, cone_ands, n)))
+      if (k->lut_live > kMaxJitLive || !(cost_run_ms(c, LEC_ES_TIER_JIT, cone_ands, n, k->lop3_per_pass) <
+                                         cost_run_ms(c, LEC_ES_TIER_INTERP, cone_ands, n)))
         return false;
       break;
     case JitProbe::kBatch:

@@ -460,6 +460,7 @@ def lec_es_codegen_version() -> int:
 
 
 TIER_COMPILE = 4  # lec_es_cost_model: the kernel-build model
+TIER_KERNEL = 5   # lec_es_cost_model: the specialised kernel by its executed lop3
 
 
 def lec_es_cost_fit(gates, n, ms) -> lec_es_cost_coeffs:

@@ -91,9 +91,12 @@ def test_fit_rejects_bad_input():
 
 
 def test_builtin_model_and_prediction_without_a_context():
-    for tier in (L.TIER_INTERP, L.TIER_JIT, L.TIER_SPILL, L.TIER_COMPILE):
+    for tier in (L.TIER_INTERP, L.TIER_JIT, L.TIER_SPILL, L.TIER_COMPILE, L.TIER_KERNEL):
         f = L.lec_es_cost_model(None, tier)
         assert f.a_ms > 0 and f.samples == 0
+    for tier in (0, 6):
+        with pytest.raises(L.LecEsError):
+            L.lec_es_cost_model(None, tier)
     fi = L.lec_es_cost_model(None, L.TIER_INTERP)
     fj = L.lec_es_cost_model(None, L.TIER_JIT)
     fc = L.lec_es_cost_model(None, L.TIER_COMPILE)

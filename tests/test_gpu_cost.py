@@ -51,12 +51,13 @@ def test_model_learns_from_full_equivalent_runs_only():
 
 def test_predictions_track_measured_times():
     """Learn from a few product-bit miters, predict others (different widths
-    and bits) within 40% on the interpreter and 50% on the specialised
-    kernel, or 20 us for launch-sized runs; the model is the paper's form
-    plus a launch and a one-pass term, fitted in relative error.  The
-    kernel's time follows the tables it runs per pass, not the gates, and
-    hoisting and unrolled levels make that ratio vary from cone to cone
-    (0.07-0.10 lop3 per AND and pass on these miters)."""
+    and bits) within 40% on the interpreter, or 20 us for launch-sized runs;
+    the model is the paper's form plus a launch and a one-pass term, fitted
+    in relative error.  The specialised kernel's time follows the lop3 it
+    executes per pass, not the gates (hoisting and folded pass PIs make the
+    ratio vary from cone to cone), so once the context holds a cone's kernel
+    its prediction uses that figure and lands within 30%; before, by gates,
+    within a factor of two."""
     c = make_ctx(arena_bytes=512 << 20)
     try:
         pm = C.ProductBitMiters(seed=5)
@@ -70,11 +71,24 @@ def test_predictions_track_measured_times():
         for w, bit in held:
             m = miter(w, bit)
             p = L.lec_es_cost_predict(c, m, 16)
-            for tier, pred in ((L.TIER_INTERP, p.interp_ms), (L.TIER_JIT, p.jit_ms)):
-                r = _run(c, m, tier, runs=2)
-                assert r.verdict == L.EQUIVALENT
-                rel = 0.4 if tier == L.TIER_INTERP else 0.5
-                assert pred == pytest.approx(r.device_ms, rel=rel, abs=0.02), (w, bit, tier, pred, r.device_ms)
+            r = _run(c, m, L.TIER_INTERP, runs=2)
+            assert r.verdict == L.EQUIVALENT
+            assert p.interp_ms == pytest.approx(r.device_ms, rel=0.4, abs=0.02), (w, bit, p.interp_ms, r.device_ms)
+            opt = L.options(tier=L.TIER_JIT)
+            plan = L.lec_es_prepare(c, m, opt)
+            try:
+                held_pred = L.lec_es_cost_predict(c, m, 16)  # the context holds the kernel, no run of it yet
+                for _ in range(3):
+                    L.lec_es_run_async(c, plan, opt)
+                    r = L.lec_es_plan_result(c, plan)
+            finally:
+                L.lec_es_plan_free(c, plan)
+            assert r.verdict == L.EQUIVALENT
+            assert 0.5 * r.device_ms - 0.02 <= p.jit_ms <= 2.0 * r.device_ms + 0.02, (w, bit, p.jit_ms, r.device_ms)
+            assert held_pred.jit_compile_ms == 0.0
+            assert held_pred.jit_ms == pytest.approx(r.device_ms, rel=0.3, abs=0.02), (w, bit, held_pred.jit_ms,
+                                                                                      r.device_ms)
+        assert L.lec_es_cost_model(c, L.TIER_KERNEL).samples > 0
     finally:
         L.lec_es_destroy(c)
 
