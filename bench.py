@@ -317,6 +317,11 @@ def measure_serve(ctx, args):
                       "requests": len(errs),
                       "median_rel_err": float(np.median(errs)) if errs else None,
                       "p90_rel_err": float(np.percentile(errs, 90)) if errs else None}
+    # the JIT predictions above use the held kernel's executed lop3 per pass:
+    # t = a + c * gates + alpha * (lop3 + 40) * 2^(n - 23)
+    co = L.lec_es_cost_model(ctx, L.TIER_KERNEL)
+    cost["jit"]["by_executed_lop3"] = {"a_ms": co.a_ms, "c_ms": co.c_ms, "alpha_ms": co.alpha_ms,
+                                       "samples": int(co.samples)}
     cost["paper_cpu_alpha_ms"] = 0.3
     cost["beta"] = 23
     # capacity: every request submitted at once
