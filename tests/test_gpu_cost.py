@@ -78,16 +78,18 @@ def test_predictions_track_measured_times():
             plan = L.lec_es_prepare(c, m, opt)
             try:
                 held_pred = L.lec_es_cost_predict(c, m, 16)  # the context holds the kernel, no run of it yet
-                for _ in range(3):
+                times = []
+                for _ in range(3):  # back to back; the least is the steady time (clocks ramped up)
                     L.lec_es_run_async(c, plan, opt)
                     r = L.lec_es_plan_result(c, plan)
+                    assert r.verdict == L.EQUIVALENT
+                    times.append(r.device_ms)
             finally:
                 L.lec_es_plan_free(c, plan)
-            assert r.verdict == L.EQUIVALENT
-            assert 0.5 * r.device_ms - 0.02 <= p.jit_ms <= 2.0 * r.device_ms + 0.02, (w, bit, p.jit_ms, r.device_ms)
+            t = min(times)
+            assert 0.5 * t - 0.02 <= p.jit_ms <= 2.0 * t + 0.02, (w, bit, p.jit_ms, times)
             assert held_pred.jit_compile_ms == 0.0
-            assert held_pred.jit_ms == pytest.approx(r.device_ms, rel=0.3, abs=0.02), (w, bit, held_pred.jit_ms,
-                                                                                      r.device_ms)
+            assert held_pred.jit_ms == pytest.approx(t, rel=0.3, abs=0.02), (w, bit, held_pred.jit_ms, times)
         assert L.lec_es_cost_model(c, L.TIER_KERNEL).samples > 0
     finally:
         L.lec_es_destroy(c)
