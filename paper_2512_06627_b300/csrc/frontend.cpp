@@ -44,51 +44,63 @@ int extract_cone(const MiterView &m, std::vector<uint8_t> &mark, Cone &c) {
   const uint32_t root = m.out_lit >> 1;
   if (root > maxvar) return LEC_ES_EINVAL;
   if (m.num_ands && !m.fanins) return LEC_ES_EINVAL;
-  // Fanins precede their AND, so one scan from the output down visits the
-  // cone in descending order: a marked AND marks its fanins.  The scan stops
-  // when no marked AND is left below it, so a small cone of a large shared
-  // graph costs the span of its variables (sequential byte reads), and the
-  // lists come out sorted.  Marks are cleared as the scan passes them.
+  // A walk from the output over the cone's own fanins marks its variables
+  // (cost: the cone, not the graph it is cut from).  The lists must come out
+  // ascending: a cone that fills most of its variable span is collected by
+  // one scan of the marks over that span (sequential bytes), a sparse one
+  // (a small cone of a large shared graph) by sorting what the walk found.
+  // Marks are cleared before returning.
   mark.resize(maxvar + 1, 0);
-  mark[root] = 1;
-  uint64_t pending_ands = root > m.num_pis ? 1 : 0, pending_pis = root > 0 && root <= m.num_pis ? 1 : 0;
+  thread_local std::vector<uint32_t> stack;
+  stack.clear();
   int rc = LEC_ES_OK;
-  uint32_t v = root;
-  for (; v > m.num_pis && pending_ands; v--) {
-    if (!mark[v]) continue;
-    mark[v] = 0;
-    pending_ands--;
-    c.ands.push_back(v);
-    const uint32_t *f = fanin_of(m, v);
-    for (int e = 0; e < 2; e++) {
-      const uint32_t u = f[e] >> 1;
-      if (u >= v) {
-        rc = LEC_ES_EINVAL;
-        break;
-      }
-      if (mark[u]) continue;
-      mark[u] = 1;
-      if (u > m.num_pis) pending_ands++;
-      else if (u > 0) pending_pis++;
+  uint32_t lowest = root;
+  auto visit = [&](uint32_t u) {
+    if (mark[u]) return;
+    mark[u] = 1;
+    if (u > m.num_pis) {
+      c.ands.push_back(u);
+      stack.push_back(u);
+      lowest = std::min(lowest, u);
+    } else if (u > 0) {
+      c.pis.push_back(u);
     }
-    if (rc) break;
-  }
-  if (rc) {  // clear what is still marked below the scan
-    for (uint32_t u = v; u > 0; u--) mark[u] = 0;
-    mark[0] = 0;
-    c.ands.clear();
-    return rc;
-  }
-  for (uint32_t u = std::min<uint64_t>(m.num_pis, root); u > 0 && pending_pis; u--) {
-    if (!mark[u]) continue;
-    mark[u] = 0;
-    pending_pis--;
-    c.pis.push_back(u);
+  };
+  visit(root);
+  while (!stack.empty()) {
+    const uint32_t v = stack.back();
+    stack.pop_back();
+    const uint32_t *f = fanin_of(m, v);
+    const uint32_t a = f[0] >> 1, b = f[1] >> 1;
+    if (a >= v || b >= v) {  // fanins must precede their AND
+      rc = LEC_ES_EINVAL;
+      break;
+    }
+    visit(a);
+    visit(b);
   }
   c.uses_const = mark[0] != 0;
   mark[0] = 0;
-  std::reverse(c.ands.begin(), c.ands.end());
-  std::reverse(c.pis.begin(), c.pis.end());
+  for (uint32_t u : c.pis) mark[u] = 0;
+  if (rc) {
+    for (uint32_t u : c.ands) mark[u] = 0;
+    c.ands.clear();
+    c.pis.clear();
+    return rc;
+  }
+  const size_t k = c.ands.size();
+  if (k > 1 && (uint64_t)(root - lowest + 1) <= 16ull * k) {
+    c.ands.clear();
+    for (uint32_t u = lowest; u <= root; u++)
+      if (mark[u]) {
+        mark[u] = 0;
+        c.ands.push_back(u);
+      }
+  } else {
+    for (uint32_t u : c.ands) mark[u] = 0;
+    std::sort(c.ands.begin(), c.ands.end());
+  }
+  std::sort(c.pis.begin(), c.pis.end());
   return LEC_ES_OK;
 }
 
