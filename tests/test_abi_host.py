@@ -221,12 +221,19 @@ def test_errors():
 
 
 def test_shared_graph_cones_are_independent():
+    """Cones cut from one large graph (sparse in its variable span: listed
+    by sorting what the walk found) and a cone that fills its span (listed
+    by scanning the marks) have the oracle's AND count and support."""
     pb = C.config4_pairs(num_pairs=64)
     f = pb.aig.flat_fanins()
-    for out in pb.aig.outputs[:16]:
+    for out in pb.aig.outputs:
         info, _ = L.lec_es_compile(L.Miter(pb.aig.num_pis, f, out))
         sup, na = O.support(pb.aig.num_pis, pb.aig.fanins, out)
         assert info.cone_ands == na and info.n == len(sup)
+    aig = C.config3_mult16()
+    info, _ = L.lec_es_compile(L.miter_of(aig))
+    sup, na = O.support(aig.num_pis, aig.fanins, aig.outputs[0])
+    assert info.cone_ands == na and info.n == len(sup)
 
 
 def test_jit_compiles_for_sm103a_without_spills():
