@@ -212,6 +212,15 @@ def test_errors():
     with pytest.raises(L.LecEsError) as e:
         L.lec_es_compile(L.Miter(2, np.array([2, 4], dtype=np.uint32), 2 * 9))
     assert e.value.status == L.EINVAL
+    # a forward fanin below the output (var 4 reads var 5): the error leaves
+    # no marks behind, so later cones of the same buffer come out whole
+    fwd = np.array([2, 4, 6, 10, 2, 4], dtype=np.uint32)
+    with pytest.raises(L.LecEsError) as e:
+        L.lec_es_compile(L.Miter(2, fwd, 8))
+    assert e.value.status == L.EINVAL
+    for out in (6, 10):
+        info, _ = L.lec_es_compile(L.Miter(2, fwd, out))
+        assert (info.n, info.cone_ands) == (2, 1)
     g = C.AigBuilder(64)
     out = g.and_tree([g.pi(i) for i in range(64)])
     aig = g.finish([out])
