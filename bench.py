@@ -8,9 +8,11 @@ equivalent, so the whole space is enumerated).  The unit of work is one AIG
 AND node evaluated for one input pattern: cone ANDs x 2^32 per step.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+    python bench.py --case <name> [--runs N] [--n N]
 
 Prints one JSON line.  With --impl reference the CPU oracle is timed on a
-bounded sample of the same workload on the host cores.
+bounded sample of the same workload on the host cores.  --case runs one
+small fixed workload for a profiler instead (see run_case).
 """
 from __future__ import annotations
 
@@ -29,10 +31,14 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "16x16 array vs radix-4 Booth/Dadda multiplier miter, 32 PIs, 2^32 patterns, equivalent"
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture (profiles/es_jit_mult16.md), keyed by (tier, program hash, number of
+# capture of `bench.py --case mult16-jit`, keyed by (tier, program hash, number of
 # 3-input tables, code-generator version); reported only while the program and
 # the generated kernel are the ones that were captured.
 NCU_TRAFFIC = {("jit", 0xdfdebdb6dd06a0a8, 1714, 21): 57600}
+
+
+CASES = ["mult16-jit", "mult16-interp", "mult12-interp", "pairs-light", "pairs-all", "pair-jit", "sweep-32x32",
+         "mult16-planted-jit"]
 
 
 def parse():
@@ -49,6 +55,11 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-load", type=float, default=0.7)
+    ap.add_argument("--case", choices=CASES, default=None,
+                    help="run one fixed profiling workload (prepared first, then --runs launches) instead of "
+                         "the benchmark")
+    ap.add_argument("--runs", type=int, default=2)
+    ap.add_argument("--n", type=int, default=24, help="support size of the pair-jit case")
     ap.add_argument("--serve-full", action="store_true",
                     help="the served workload at full size: a Poisson stream over all --serve-requests "
                          "(e.g. 20000) at --serve-load of a capacity measured on the first 400, verdicts "
@@ -382,6 +393,51 @@ def measure_sweep(ctx):
     return out
 
 
+def measure_mutants(ctx, full_ms):
+    """Time to verdict of non-equivalent miters, whose check ends at the
+    lowest counterexample (early exit, paper §2.2): the 12x12 workload's
+    three seeded mutants, the 16x16 mutant whose only failing pattern is the
+    last (2^32 - 1), and 16x16 miters with one planted minterm at p = 2^20,
+    2^28 and 2^31 (+ 12,345).  Each kernel is built by a first check; the
+    time is the median of five checks (kernel time by CUDA events, and the
+    whole call).  'expected_ms' = the launch floor (the kernel time of a
+    counterexample in the first chunk) + (cex / 2^n) x the equivalent miter's
+    full-enumeration kernel time."""
+    from paper_2512_06627_b300 import circuits as C
+    from paper_2512_06627_b300 import lec_es as L
+
+    def timed(aig):
+        m = L.miter_of(aig)
+        r = L.lec_es_check(ctx, m)
+        dev, wall = [], []
+        for _ in range(5):
+            t0 = time.perf_counter()
+            r = L.lec_es_check(ctx, m)
+            wall.append((time.perf_counter() - t0) * 1e3)
+            dev.append(r.device_ms)
+        return r, statistics.median(dev), statistics.median(wall)
+
+    full = {}
+    for name, aig in (("12x12", C.config2_mult12()),):
+        full[name] = timed(aig)[1]
+    full["16x16"] = full_ms
+    floors = {"12x12": timed(C.build_multiplier_pair(12, tree="wallace", planted_minterm=37))[1],
+              "16x16": timed(C.config3_mult16(minterm=37))[1]}
+    cases = [("12x12", f"12x12 mutant seed {s}", C.config2_mult12(mutant_seed=s)) for s in (1, 2, 3)]
+    cases.append(("16x16", "16x16 mutant a=b=0xFFFF", C.config3_mult16(mutant=True)))
+    for e in (20, 28, 31):
+        cases.append(("16x16", f"16x16 planted minterm 2^{e}+12345", C.config3_mult16(minterm=(1 << e) + 12345)))
+    out = []
+    for cfg, name, aig in cases:
+        r, dev, wall = timed(aig)
+        frac = r.cex / float(1 << r.support_n)
+        exp = floors[cfg] + frac * full[cfg]
+        out.append({"miter": name, "cex": r.cex, "cex_fraction_of_space": frac, "tier": int(r.tier),
+                    "kernel_ms": dev, "call_ms": wall, "full_enumeration_ms": full[cfg],
+                    "expected_ms": exp, "kernel_over_expected": dev / exp})
+    return {"launch_floor_ms": floors, "cases": out}
+
+
 def measure_serve_full(ctx, args):
     """The served workload at its full size: every request of the seeded
     Poisson stream (array-vs-Booth product-bit miters, w in 8..18, 1%
@@ -585,6 +641,8 @@ def run_ours(args, ws, rank, local):
         "time_to_verdict": ttv,
         "clocks": clocks,
     }
+    if rank == 0:
+        line["mutant_time_to_verdict"] = measure_mutants(ctx, statistics.median(kern_ms))
     if rank == 0 and not args.no_batch:
         line["batched"] = measure_batch(ctx, args)
     if rank == 0 and args.serve_requests > 0:
@@ -631,8 +689,83 @@ def run_reference(args, ws, rank):
     }
 
 
+def run_case(args):
+    """Small fixed workloads for profiling one kernel at a time.  Each case
+    prepares its work, then launches it --runs times, so a profiler can skip
+    the first launch(es) and capture one:
+      mult16-jit         the 16x16 miter on the specialised kernel
+      mult16-interp      the same miter on the shared-memory interpreter
+      mult12-interp      the 12x12 miter on the interpreter (short launches)
+      pairs-light        the node-pair miters light enough for the tile queue, one batch
+      pairs-all          all 4,096 node-pair miters, one prepared batch
+      pair-jit           one node-pair miter of support --n on the specialised kernel
+      sweep-32x32        random-simulation signatures of the 32x32 four-multiplier graph
+      mult16-planted-jit the 16x16 miter with a minterm planted at 2^31 + 12,345 (early exit)"""
+    from paper_2512_06627_b300 import build as B
+    from paper_2512_06627_b300 import circuits as C
+    from paper_2512_06627_b300 import lec_es as L
+    B.build()
+    ctx = L.lec_es_create(0, arena_bytes=1 << 30)
+    a = args
+    if a.case == "sweep-32x32":
+        base = C.build_golden_revised_multipliers(32)
+        pw = C.signature_words(base, 64, 4)
+        for _ in range(a.runs):
+            pairs = L.lec_es_match_pairs(ctx, base.num_pis, base.flat_fanins(), pw, 28)
+            print(f"pairs {len(pairs)}")
+    elif a.case.startswith("mult"):
+        if a.case == "mult16-planted-jit":
+            aig = C.config3_mult16(minterm=(1 << 31) + 12345)
+        else:
+            aig = C.config3_mult16() if a.case.startswith("mult16") else C.config2_mult12()
+        tier = L.TIER_JIT if a.case.endswith("jit") else L.TIER_INTERP
+        p = L.lec_es_prepare(ctx, L.miter_of(aig), L.options(tier=tier))
+        for _ in range(a.runs):
+            L.lec_es_run_async(ctx, p)
+            r = L.lec_es_plan_result(ctx, p)
+            print(f"verdict {r.verdict} cex {r.cex} tier {r.tier} device_ms {r.device_ms:.3f}")
+        L.lec_es_plan_free(ctx, p)
+    elif a.case == "pair-jit":
+        pb = C.config4_pairs()
+        f = pb.aig.flat_fanins()
+        m = info = None
+        for o in pb.aig.outputs:
+            cand = L.Miter(pb.aig.num_pis, f, o)
+            info = L.lec_es_compile(cand)[0]
+            if info.n == a.n and info.num_luts >= 64:
+                m = cand
+                break
+        if m is None:
+            sys.exit(f"no node-pair miter with support {a.n}")
+        p = L.lec_es_prepare(ctx, m, L.options(tier=L.TIER_JIT))
+        for _ in range(a.runs):
+            L.lec_es_run_async(ctx, p)
+            r = L.lec_es_plan_result(ctx, p)
+            print(f"n {info.n} tables {info.num_luts} verdict {r.verdict} device_ms {r.device_ms:.4f}")
+        L.lec_es_plan_free(ctx, p)
+    else:
+        pb = C.config4_pairs()
+        f = pb.aig.flat_fanins()
+        ms = [L.Miter(pb.aig.num_pis, f, o) for o in pb.aig.outputs]
+        opt = None
+        if a.case == "pairs-light":
+            infos = [L.lec_es_compile(m)[0] for m in ms]
+            ms = [m for m, i in zip(ms, infos) if i.num_records * float(1 << max(0, i.n - 5)) < 5e7]
+            opt = L.options(tier=L.TIER_INTERP)
+        b = L.lec_es_batch_prepare(ctx, ms, opt)
+        for _ in range(a.runs):
+            L.lec_es_batch_run_async(ctx, b)
+            rs = L.lec_es_batch_results(ctx, b, len(ms))
+            print(f"miters {len(ms)} device_ms {rs[0].device_ms:.3f}")
+        L.lec_es_batch_free(ctx, b)
+    L.lec_es_destroy(ctx)
+
+
 def main():
     args = parse()
+    if args.case:
+        run_case(args)
+        return
     ws, rank, local = dist_setup(args.gpus)
     if args.impl == "reference":
         line = run_reference(args, ws, rank)

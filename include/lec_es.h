@@ -169,7 +169,8 @@ typedef struct {
  * 63), ECUDA (device not usable), ENOMEM. */
 int lec_es_create(lec_es_ctx **out, const lec_es_config *cfg);
 /* Frees everything the ctx owns (not a caller-provided arena or stream).
- * Outstanding submitted requests are cancelled first. */
+ * Outstanding submitted requests are cancelled first.  Must not run
+ * concurrently with any other call on the same ctx. */
 void lec_es_destroy(lec_es_ctx *c);
 const char *lec_es_strerror(int status);
 
@@ -192,8 +193,15 @@ int lec_es_jit_compile(const lec_es_miter *m, int cc_major, int cc_minor, char *
 
 /* ---- single miter ----------------------------------------------------- */
 
-/* Full ES of one miter, synchronous on the ctx stream.  Equivalent to
- * prepare + run + plan_free with default options. */
+/* Full ES of one miter, synchronous on the ctx stream: the problem of
+ * paper §2.1 (is the miter output constant 0?) decided by exact simulation
+ * as §2.2 defines it (every assignment of the output's PI support), with the
+ * cone compiled to a reference-counted instruction stream (§3.3).  m and its
+ * fanins are read during the call only; *out is written on LEC_ES_OK:
+ * verdict EQUIVALENT or NONEQUIVALENT with the lowest failing pattern.
+ * Equivalent to prepare + run + plan_free with default options (AUTO tier).
+ * Errors: EINVAL (NULL or malformed graph), ETOOBIG (n > max_pis or more
+ * than 65535 value slots), ENOMEM, ECUDA, EJIT, EDEVICE_WAIT, ETIMEOUT. */
 int lec_es_check(lec_es_ctx *c, const lec_es_miter *m, lec_es_result *out);
 /* As lec_es_check over a word sub-range and with explicit options; a
  * passing proper sub-range gives LEC_ES_UNDECIDED. */
@@ -248,8 +256,16 @@ int lec_es_check_noalloc(const uint64_t *d_records, uint64_t records_capacity,
 
 /* ---- batch: many miters, one persistent launch ------------------------- */
 
-/* ES of k miters in one persistent launch over a queue of (miter, word
- * range) tiles; out[i] is identical to lec_es_check on m[i]. */
+/* ES of many sub-miters at once: the per-pair sub-miters a sweeping
+ * scheduler hands to ES (paper §3.2, local sub-miters of candidate pairs;
+ * ES cost linear in gates and exponential in PIs), each decided as in
+ * lec_es_check (§2.1, §2.2, §3.3).  m[0..k-1] (host; they may share one
+ * fanins array) are read during the call only; out[0..k-1] (caller-owned)
+ * receive results identical to lec_es_check on each m[i].  Heavy miters run
+ * as their own specialised kernels and light ones in one persistent launch
+ * over a queue of (miter, word range) tiles, all in one CUDA graph.
+ * Errors: as lec_es_check for any miter (the whole call fails; out is then
+ * unspecified), EINVAL for k = 0. */
 int lec_es_batch(lec_es_ctx *c, const lec_es_miter *m, size_t k, lec_es_result *out);
 /* Prepared form: compile and upload k miters once, then run repeatedly
  * (the launch sequence is captured in a CUDA graph and replayed). */
@@ -277,7 +293,13 @@ void lec_es_batch_free(lec_es_ctx *c, lec_es_batch_plan *b);
 
 /* ---- serving: asynchronous requests, continuous batching ----------------- */
 
-/* Admit a request; returns a ticket at once.  The miter is copied.
+/* Admit one ES request (the problem of paper §2.1 decided as in §2.2 and
+ * §3.3, like lec_es_check) and return a ticket at once; requests that
+ * arrive while others run are admitted as device memory and result slots
+ * free up, and their kernels overlap on the GPU (continuous batching).  The
+ * miter is compiled (or its cone copied) before the call returns, so the
+ * caller may free m at once.  The result, identical to lec_es_check on m,
+ * comes from lec_es_poll / lec_es_wait.  Thread-safe.
  * Errors: EINVAL, ETOOBIG, ENOMEM (queue full). */
 int lec_es_submit(lec_es_ctx *c, const lec_es_miter *m, uint64_t *ticket);
 /* EBUSY while the request runs; OK and *out once done (the ticket is then

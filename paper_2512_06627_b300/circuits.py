@@ -391,13 +391,18 @@ def build_adder_pair(w: int = 8) -> Aig:
 
 
 def build_multiplier_pair(w: int, tree: str = "wallace", msb_all_ones_mutant: bool = False,
-                          product_bits: Optional[Sequence[int]] = None) -> Aig:
+                          product_bits: Optional[Sequence[int]] = None,
+                          planted_minterm: Optional[int] = None, planted_bit: Optional[int] = None) -> Aig:
     """w x w array multiplier (side A) vs radix-4 Booth multiplier (side B),
     built in separate hashing scopes.  Outputs: the miter of all 2w product
     bits (default) or one XOR output per requested product bit.
 
     ``msb_all_ones_mutant`` XORs the AND of all 2w PIs into side B's MSB, so the
-    two sides differ only at a = b = 2^w - 1.
+    two sides differ only at a = b = 2^w - 1.  ``planted_minterm`` = p
+    generalises it: the minterm of p (PI k taken plain where bit k of p is 1,
+    complemented where it is 0) is XORed into side B's product bit
+    ``planted_bit`` (default the MSB), so the sides differ at pattern p alone
+    and p is the miter's only (hence lowest) counterexample.
     """
     g, a, b = _two_operand_builder(w)
     sa = g.next_var
@@ -408,6 +413,13 @@ def build_multiplier_pair(w: int, tree: str = "wallace", msb_all_ones_mutant: bo
     if msb_all_ones_mutant:
         allp = g.and_tree(a + b)
         ob = ob[:-1] + [g.XOR(ob[-1], allp)]
+    if planted_minterm is not None:
+        assert 0 <= planted_minterm < (1 << (2 * w))
+        k = 2 * w - 1 if planted_bit is None else planted_bit
+        pis = a + b
+        lits = [pis[i] if (planted_minterm >> i) & 1 else pis[i] ^ 1 for i in range(2 * w)]
+        ob = list(ob)
+        ob[k] = g.XOR(ob[k], g.and_tree(lits))
     eb = g.next_var
     g.new_scope()
     if product_bits is None:
@@ -550,10 +562,13 @@ def config2_mult12(mutant_seed: Optional[int] = None) -> Aig:
     return m
 
 
-def config3_mult16(mutant: bool = False) -> Aig:
+def config3_mult16(mutant: bool = False, minterm: Optional[int] = None, bit: Optional[int] = None) -> Aig:
     """16x16 array vs Booth/Dadda miter (32 PIs, no hashing across sides);
-    the mutant differs only at a = b = 0xFFFF."""
-    return build_multiplier_pair(16, tree="dadda", msb_all_ones_mutant=mutant)
+    the mutant differs only at a = b = 0xFFFF.  ``minterm`` = p plants the
+    minterm of p into product bit ``bit`` of the Booth side instead (see
+    build_multiplier_pair): the only counterexample is then p = a | b << 16."""
+    return build_multiplier_pair(16, tree="dadda", msb_all_ones_mutant=mutant,
+                                 planted_minterm=minterm, planted_bit=bit)
 
 
 def build_golden_revised_multipliers(w: int) -> Aig:

@@ -6,9 +6,9 @@
 // and thousands of ANDs.  One launch per miter leaves the GPU idle on the
 // small ones.  Preparation has two stages:
 //   programs  every miter is compiled (front end, 16 host threads); miters
-//             whose interpreter cost exceeds ~50 us get their specialised
-//             kernel (compiled in parallel); the others' slot programs are
-//             packed into one record arena;
+//             whose predicted interpreter time exceeds kBatchJitMs (0.02 ms)
+//             get their specialised kernel (compiled in parallel); the
+//             others' slot programs are packed into one record arena;
 //   layout    the light miters' pattern spaces are cut into (miter, chunk
 //             range) tiles sized by cost_ES = records x chunks; a persistent
 //             kernel pulls tiles from a queue head with atomicAdd; the graph

@@ -65,6 +65,7 @@ struct JitKernel {
   double lop3_per_pass = 0;     // lop3 it executes per 32-pattern chunk and thread (0: unknown)
   uint64_t pass_bits = 0;       // chunk-index bits of the pass PIs (0: contiguous grabs of 32 * rep chunks)
   uint32_t chunk_bits = 0;      // bits of the chunk index (support PIs - 5)
+  uint64_t hash2 = 0;           // the program's second structure hash (checked on every cache hit)
 };
 struct JitState;
 struct Server;
@@ -149,7 +150,7 @@ struct JitProbe {
   lec_es_ctx *c;
   Use use;  // kRun: the kernel tier was asked for; kAuto: the AUTO choice; kBatch: the batch's split; kInfo: facts only
 };
-bool jit_probe(void *arg, uint64_t hash, uint32_t n, uint32_t cone_ands, KernelFacts *facts);
+bool jit_probe(void *arg, uint64_t hash, uint64_t hash2, uint32_t n, uint32_t cone_ands, KernelFacts *facts);
 // The batch gives a miter its own kernel (else the tile queue).
 bool batch_wants_kernel(lec_es_ctx *c, uint32_t n, uint32_t cone_ands, uint32_t luts, uint32_t live);
 void jit_release_all(lec_es_ctx *c);

@@ -60,6 +60,8 @@ struct Program {
   uint32_t cone_ands = 0;
   uint32_t order = 0;
   uint64_t hash = 0;                // of the cone's structure (dense ids, complements, output, n)
+  uint64_t hash2 = 0;               // a second, independent hash of the same structure: a cached
+                                    // kernel or resident program is used only when both match
   LutProgram lut;                   // 3-input table cover (the JIT tier's instructions)
   bool slots_elided = false;        // recs/order_vars not built: the specialised kernel runs this cone
   uint32_t num_records = 0;         // recs.size(), or the kernel's record count when elided
@@ -85,7 +87,7 @@ struct KernelFacts {
   uint32_t num_slots = 0, order = 0, num_records = 0;
 };
 struct KernelProbe {
-  bool (*have_kernel)(void *arg, uint64_t hash, uint32_t n, uint32_t cone_ands, KernelFacts *facts);
+  bool (*have_kernel)(void *arg, uint64_t hash, uint64_t hash2, uint32_t n, uint32_t cone_ands, KernelFacts *facts);
   void *arg;
 };
 

@@ -469,7 +469,7 @@ struct ConeMemo {
   const uint32_t *fanins = nullptr;
   uint32_t num_pis = 0, num_ands = 0, out_lit = 0;
   std::vector<uint32_t> copy;  // 2 * num_ands fanin literals
-  uint64_t hash = 0;
+  uint64_t hash = 0, hash2 = 0;
   std::vector<uint32_t> support;  // 0-based PI indices
   uint32_t cone_ands = 0;
   int64_t root_vid = -1;
@@ -478,13 +478,14 @@ constexpr size_t kConeMemos = 4;
 
 // The elided program of a cone whose kernel the probe found.
 void elided_program(uint32_t n, const uint32_t *support, uint32_t cone_ands, uint32_t out_lit, uint64_t hash,
-                    int64_t root_vid, const KernelFacts &facts, Program &out) {
+                    uint64_t hash2, int64_t root_vid, const KernelFacts &facts, Program &out) {
   Program p;
   p.n = n;
   p.support.assign(support, support + n);
   p.cone_ands = cone_ands;
   p.out_compl = out_lit & 1;
   p.hash = hash;
+  p.hash2 = hash2;
   p.num_slots = facts.num_slots;
   p.order = facts.order;
   p.num_records = facts.num_records;
@@ -511,9 +512,9 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
         continue;
       if (e.support.size() > max_pis) return LEC_ES_ETOOBIG;
       KernelFacts facts;
-      if (!probe->have_kernel(probe->arg, e.hash, (uint32_t)e.support.size(), e.cone_ands, &facts)) break;
-      elided_program((uint32_t)e.support.size(), e.support.data(), e.cone_ands, m.out_lit, e.hash, e.root_vid, facts,
-                     out);
+      if (!probe->have_kernel(probe->arg, e.hash, e.hash2, (uint32_t)e.support.size(), e.cone_ands, &facts)) break;
+      elided_program((uint32_t)e.support.size(), e.support.data(), e.cone_ands, m.out_lit, e.hash, e.hash2,
+                     e.root_vid, facts, out);
       if (i) std::rotate(memos.begin(), memos.begin() + i, memos.begin() + i + 1);  // most recent first
       return LEC_ES_OK;
     }
@@ -525,8 +526,11 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
   ConeIndex ix(c, dense, (uint64_t)m.num_pis + m.num_ands);
   const uint32_t root_var = m.out_lit >> 1;
   // the cone's structure: fanin value ids and complements of its ANDs in
-  // ascending order, the output's value id and complement, the support size
-  uint64_t chash = 1469598103934665603ull;
+  // ascending order, the output's value id and complement, the support size;
+  // hashed twice, by FNV and by a multiply-xorshift chain, so that a kernel
+  // or resident program found by the first is used only if the second
+  // agrees too
+  uint64_t chash = 1469598103934665603ull, chash2 = 0x243F6A8885A308D3ull;
   {
     const uint32_t head[2] = {(uint32_t)c.pis.size(), (uint32_t)c.ands.size()};
     chash = fnv1a(head, sizeof(head), chash);
@@ -540,9 +544,18 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
     chash ^= chash >> 29;
     const uint32_t tail[1] = {(uint32_t)ix.vid(root_var) << 1 | (m.out_lit & 1u)};
     chash = fnv1a(tail, sizeof(tail), chash);
+    auto mix = [](uint64_t h, uint64_t w) {
+      h = (h ^ (w + 0x9E3779B97F4A7C15ull)) * 0xFF51AFD7ED558CCDull;
+      return h ^ (h >> 32);
+    };
+    chash2 = mix(chash2, (uint64_t)head[0] << 32 | head[1]);
+    for (size_t i = 0; i + 1 < row.size(); i += 2) chash2 = mix(chash2, (uint64_t)row[i] << 32 | row[i + 1]);
+    chash2 = mix(chash2, tail[0]);
+    chash2 = (chash2 ^ (chash2 >> 29)) * 0xC4CEB9FE1A85EC53ull;
+    chash2 ^= chash2 >> 32;
   }
   KernelFacts facts;
-  if (probe && probe->have_kernel(probe->arg, chash, (uint32_t)c.pis.size(), (uint32_t)c.ands.size(), &facts)) {
+  if (probe && probe->have_kernel(probe->arg, chash, chash2, (uint32_t)c.pis.size(), (uint32_t)c.ands.size(), &facts)) {
     std::vector<uint32_t> sup(c.pis.size());
     for (size_t k = 0; k < c.pis.size(); k++) sup[k] = c.pis[k] - 1;
     const int64_t root_vid = ix.vid(root_var);
@@ -556,13 +569,15 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
       e.out_lit = m.out_lit;
       e.copy.assign(m.fanins, m.fanins + 2ull * m.num_ands);
       e.hash = chash;
+      e.hash2 = chash2;
       e.support = sup;
       e.cone_ands = (uint32_t)c.ands.size();
       e.root_vid = root_vid;
       memos.insert(memos.begin(), std::move(e));
       if (memos.size() > kConeMemos) memos.pop_back();
     }
-    elided_program((uint32_t)sup.size(), sup.data(), (uint32_t)c.ands.size(), m.out_lit, chash, root_vid, facts, out);
+    elided_program((uint32_t)sup.size(), sup.data(), (uint32_t)c.ands.size(), m.out_lit, chash, chash2, root_vid, facts,
+                   out);
     return LEC_ES_OK;
   }
   std::vector<uint32_t> level;
@@ -606,6 +621,7 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
   best.out_compl = m.out_lit & 1;
   if (best.num_slots == 0) best.num_slots = 1;
   best.hash = chash;
+  best.hash2 = chash2;
   best.num_records = (uint32_t)best.recs.size();
   {
     // the table cover (independent of the slot order), then its evaluation

@@ -24,8 +24,12 @@
 // loop of its deepest pass PI (plan_hoist decides what survives a loop);
 // the innermost levels are unrolled with their PIs folded as constants.
 // The miter output is reduced with a warp ballot and the lowest failing
-// lane does atomicMin on the counterexample; a warp stops when its grab's
-// lowest pattern is not below the current counterexample.
+// lane does atomicMin on the counterexample.  Early exit: a warp stops when
+// its grab's lowest pattern is not below the counterexample, and inside a
+// grab it skips every loop iteration and pass whose first pattern is not
+// below it (the poll is refreshed once per iteration of the innermost
+// loop), so a counterexample in the high pass PIs prunes the passes above
+// it in every later grab, not only the grabs above it.
 #include <cuda_runtime.h>
 #include <nvPTXCompiler.h>
 #include <nvrtc.h>
@@ -53,7 +57,8 @@ namespace lec {
 
 struct JitState {
   std::mutex mu;
-  std::map<uint64_t, JitKernel *> cache;
+  std::map<uint64_t, JitKernel *> cache;  // by cache_key; an entry serves a program only if hash2 matches too
+  std::vector<JitKernel *> unshared;      // built for a program whose key another program holds
   // background compiles for the server
   std::map<uint64_t, bool> scheduled;
   std::vector<std::thread> workers;
@@ -65,7 +70,7 @@ struct JitState {
 namespace {
 
 constexpr int kJitBlock = 128;
-constexpr int kCodegenVersion = 21;  // part of cached cubin names: bump whenever the generated code changes
+constexpr int kCodegenVersion = 22;  // part of cached cubin names: bump whenever the generated code changes
 // Values computed at one loop level and read at a deeper one: at most
 // kHoistPlan of them (see plan_hoist), those read by the innermost loop in
 // registers, the others in up to kHoistShared shared-memory slots per
@@ -89,6 +94,19 @@ constexpr uint32_t kDryPlan = 160;  // plan of the layout search's dry runs (see
 // build at once, instead of the rest only after the first spills.
 thread_local bool t_single_build = false;
 constexpr uint32_t kMaxJitLive = 230;        // table live set that still fits the register file
+
+// The counterexample word (a pattern; UINT64_MAX while none is known) as
+// the first 32-pattern chunk it rules out, ceil(cex / 32), kept in %d12
+// (a found cex is below 2^63, so the clamp changes only "none").
+const std::string kCexToChunk =
+    "  min.u64 %d12, %d12, 0x8000000000000000;\n  add.u64 %d12, %d12, 31;\n  shr.u64 %d12, %d12, 5;\n";
+// Inside a grab: lane 0's earlier poll (%d17) becomes the warp's %d12 and
+// lane 0 polls again for the next refresh, so the load's latency is hidden
+// behind the work in between.
+const std::string kCexRefresh =
+    "  mov.b64 {%t3, %t4}, %d17;\n  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n"
+    "  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n  mov.b64 %d12, {%t3, %t4};\n" +
+    kCexToChunk + "  @%p1 ld.volatile.global.u64 %d17, [%d3];\n";
 
 const char *kMask32[5] = {"0xAAAAAAAAu", "0xCCCCCCCCu", "0xF0F0F0F0u", "0xFF00FF00u", "0xFFFF0000u"};
 
@@ -123,6 +141,7 @@ void emit_prologue(std::ostringstream &s) {
        "    for (u64 r = 0; r < rep; r++) {\n"
        "    const u64 base = gfirst + 32ull * r;\n"
        "    if (base >= ce) break;\n"
+       "    if (base * 32ull >= cur) break;\n"
        "    if (base + 32ull <= cb) continue;\n"
        "    const u64 c = base + lane;\n"
        "    const u32 clo = (u32)c, chi = (u32)(c >> 32);\n"
@@ -515,9 +534,13 @@ std::vector<BitRun> bit_runs(const std::vector<uint32_t> &pos) {  // pos ascendi
 // from [q0, qend), computed on the host) is every chunk whose grab bits spell
 // q, REP passes of 32 chunks, masked to [cb, ce).  Tables chosen by
 // plan_hoist (no pass PI among their inputs) are evaluated once per grab,
-// the others once per pass.  Grabs and passes increase in chunk index, so a
-// warp stops at the end of its range or when its grab's lowest pattern is
-// not below the current counterexample; it also stops after max_grabs grabs.
+// the others once per pass.  Grabs increase in chunk index, so a warp stops
+// at the end of its range or when its grab's lowest pattern is not below
+// the current counterexample; it also stops after max_grabs grabs.  Within
+// a grab the counterexample (in %d12 as the first chunk it rules out) is
+// re-polled at each iteration of the innermost loop, and a loop iteration
+// or pass that starts at or above it is skipped: every chunk of it is
+// higher, so none can be the lowest failing one.
 std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, uint32_t reg_budget,
                         uint32_t plan_budget, uint64_t pass_pis, const std::vector<uint64_t> &groups,
                         SlotSplit *split, double *lop3_per_pass) {
@@ -698,7 +721,8 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     << (stride_ok ? "  @%p14 mov.u64 %d11, %d35;\n" : "")
     << "  mov.u64 %d12, 0;\n  @%p1 ld.volatile.global.u64 %d12, [%d3];\n  mov.b64 {%t3, %t4}, %d12;\n"
        "  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n"
-       "  mov.b64 %d12, {%t3, %t4};\n  mov.u64 %d13, 1;\n  cvt.u64.u32 %d18, %t2;\n";
+       "  mov.b64 %d12, {%t3, %t4};\n"
+    << kCexToChunk << "  mov.u64 %d13, 1;\n  cvt.u64.u32 %d18, %t2;\n";
   if (nsmem) s << "  mov.u32 %t21, hs;\n  shl.b32 %t22, %t1, 2;\n  add.u32 %t21, %t21, %t22;\n";
   // constants (PI masks, the constant, folded tables) are lop3 immediates
   std::vector<std::string> name(NV);
@@ -746,7 +770,7 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   s << "$LOOP:\n"
        "  add.u64 %d14, %d8, %d11;\n  setp.ge.u64 %p2, %d14, %d9;\n  @%p2 bra $DONE;\n";
   emit_deposit("%d15", "%d14", gpos);
-  s << "  max.u64 %d20, %d15, %d1;\n  shl.b64 %d21, %d20, 5;\n  setp.ge.u64 %p2, %d21, %d12;\n  @%p2 bra $DONE;\n"
+  s << "  max.u64 %d20, %d15, %d1;\n  setp.ge.u64 %p2, %d20, %d12;\n  @%p2 bra $DONE;\n"
        "  setp.lt.u64 %p3, %d13, %d6;\n  and.pred %p4, %p15, %p3;\n  mov.u64 %d16, -1;\n"
        "  @%p4 atom.global.add.u64 %d16, [%d5], 1;\n" << (stride_ok ? "  @%p14 add.u64 %d16, %d11, %d36;\n" : "")
     << "  mov.u64 %d17, 0;\n"
@@ -796,11 +820,12 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   // pass loops 1..NLOOP ($LV, index j<l>, first chunk of the iteration
   // o<l>); without unrolling the innermost level L is the pass loop ($PASS)
   const uint32_t NLOOP = U > 0 ? Lr : L - 1;
+  std::string stubs;  // out-of-line skip paths, emitted after the kernel's ret
   auto close_loops = [&]() {  // loop ends of the outer pass loops, innermost first
     std::string c;
     for (uint32_t l = NLOOP; l >= 1; l--) {
       const std::string j = "%j" + std::to_string(l);
-      c += "  add.u32 " + j + ", " + j + ", 1;\n  setp.lt.u32 %p9, " + j + ", " +
+      c += "$LE" + std::to_string(l) + ":\n  add.u32 " + j + ", " + j + ", 1;\n  setp.lt.u32 %p9, " + j + ", " +
            std::to_string(1u << __builtin_popcountll(grp[l - 1])) + ";\n  @%p9 bra $LV" + std::to_string(l) + ";\n";
     }
     return c;
@@ -818,6 +843,12 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     s << "  mov.u32 " << j << ", 0;\n$LV" << l << ":\n  cvt.u64.u32 %d32, " << j << ";\n";
     emit_deposit("%d28", "%d32", lpos[l - 1]);
     s << "  add.u64 %o" << l << ", " << (l == 1 ? std::string("%d15") : "%o" + std::to_string(l - 1)) << ", %d28;\n";
+    if (l == NLOOP) s << kCexRefresh;
+    // an iteration whose first chunk is not below the counterexample is
+    // skipped, and so are the later ones (they start higher)
+    s << "  setp.ge.u64 %p9, %o" << l << ", %d12;\n  @%p9 bra $SKL" << l << ";\n";
+    stubs += "$SKL" + std::to_string(l) + ":\n  @%p12 sub.u64 %d10, %d10, " +
+             std::to_string((uint64_t)REP / (uint64_t)runs[l]) + ";\n  bra $LE" + std::to_string(l) + ";\n";
     emit_pass_pis(grp[l - 1], j.c_str());
     emit_level((uint8_t)l);
   }
@@ -953,7 +984,15 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
         } else {  // a pass: its range work, its tables, its output check
           const std::string J = std::to_string(ncopy++);
           const std::string chunk = "  add.u64 %d27, " + base + ", " + std::to_string(o) + ";\n";
-          s << "  @%p12 bra $PB" << J << ";\n" << chunk << "  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra $NX" << J
+          // a pass whose first chunk is not below the counterexample is
+          // skipped (the first copy of a loop iteration was checked with it)
+          const bool checked = o != 0 || NLOOP == 0;
+          if (checked) {
+            s << chunk << "  setp.ge.u64 %p9, %d27, %d12;\n  @%p9 bra $SKP" << J << ";\n";
+            stubs += "$SKP" + J + ":\n  @%p12 sub.u64 %d10, %d10, 1;\n  bra $NX" + J + ";\n";
+          }
+          s << "  @%p12 bra $PB" << J << ";\n" << (checked ? std::string() : chunk)
+            << "  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra $NX" << J
             << ";\n  add.u64 %d22, %d27, 32;\n  setp.le.u64 %p10, %d22, %d1;\n  @%p10 bra $NX" << J
             << ";\n  add.u64 %d19, %d27, %d18;\n$PB" << J << ":\n";
           std::fill(loaded.begin(), loaded.end(), (uint8_t)0);
@@ -992,8 +1031,11 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     };
     unrolled(unrolled, Lr + 1, 0);
   } else {
-    s << "  mov.u32 %t20, 0;\n$PASS:\n  @%p12 bra $PBODY;\n";
+    s << "  mov.u32 %t20, 0;\n$PASS:\n";
+    if (NLOOP == 0) s << kCexRefresh;
     emit_chunk();
+    s << "  setp.ge.u64 %p9, %d27, %d12;\n  @%p9 bra $SKPP;\n  @%p12 bra $PBODY;\n";
+    stubs += "$SKPP:\n  @%p12 sub.u64 %d10, %d10, 1;\n  bra $NEXTPASS;\n";
     s << "  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra " << (L > 1 ? "$NEXTPASS" : "$GRABEND") << ";\n"
       << "  add.u64 %d22, %d27, 32;\n  setp.le.u64 %p10, %d22, %d1;\n  @%p10 bra $NEXTPASS;\n"
          "  add.u64 %d19, %d27, %d18;\n$PBODY:\n";
@@ -1025,7 +1067,7 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
        "  mov.b64 {%t3, %t4}, %d16;\n  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n"
        "  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n  mov.b64 %d11, {%t3, %t4};\n"
        "  mov.b64 {%t3, %t4}, %d17;\n  shfl.sync.idx.b32 %t3, %t3, 0, 31, -1;\n"
-       "  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n  mov.b64 %d12, {%t3, %t4};\n"
+       "  shfl.sync.idx.b32 %t4, %t4, 0, 31, -1;\n  mov.b64 %d12, {%t3, %t4};\n" + kCexToChunk +
        "  add.u64 %d13, %d13, 1;\n  @!%p3 bra $DONE;\n  bra $LOOP;\n"
        "$DONE:\n";
   // warp sum of chunks done, then one reduction per warp
@@ -1036,7 +1078,7 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
       << "  add.u64 %d10, %d10, %d25;\n";
   }
   s << "  setp.ne.u64 %p8, %d10, 0;\n  and.pred %p8, %p8, %p1;\n  shl.b64 %d26, %d10, 5;\n"
-       "  @%p8 red.global.add.u64 [%d4], %d26;\n  ret;\n}\n";
+       "  @%p8 red.global.add.u64 [%d4], %d26;\n  ret;\n" << stubs << "}\n";
   // lop3 executed per pass: loop levels' tables times their runs, the
   // unrolled levels' lop3 once per run of level Lr
   double per_grab = 0;
@@ -1266,14 +1308,21 @@ int compile_cubin(const std::string &src, int major, int minor, std::vector<char
 uint64_t cache_key(const Program &g, bool lut_form);
 JitState *state(lec_es_ctx *c);
 
+// The kernel cached for g's structure (both hashes), or null.  Called with
+// js->mu held.
+JitKernel *cached_kernel(JitState *js, const Program &g, bool lut_form) {
+  auto it = js->cache.find(cache_key(g, lut_form));
+  return it != js->cache.end() && it->second->hash2 == g.hash2 ? it->second : nullptr;
+}
+
 // Executed lop3 per pass of the kernel this context holds for g's cone, or
 // 0 if it holds none (or does not know the figure).
 double jit_held_lop3(lec_es_ctx *c, const Program &g) {
   if (!c || g.lut.count == 0) return 0.0;
   JitState *js = state(c);
   std::lock_guard<std::mutex> lk(js->mu);
-  auto it = js->cache.find(cache_key(g, true));
-  return it == js->cache.end() ? 0.0 : it->second->lop3_per_pass;
+  const JitKernel *k = cached_kernel(js, g, true);
+  return k ? k->lop3_per_pass : 0.0;
 }
 
 // The ES time model (cost.cpp) decides: the specialised kernel when its
@@ -1287,7 +1336,7 @@ uint32_t jit_auto_tier(lec_es_ctx *c, const Program &g, uint64_t chunks) {
   if (!cached && c) {
     JitState *js = state(c);
     std::lock_guard<std::mutex> lk(js->mu);
-    cached = js->cache.count(cache_key(g, true)) != 0;
+    cached = cached_kernel(js, g, true) != nullptr;
   }
   const double t_int = cost_run_ms(c, LEC_ES_TIER_INTERP, g.cone_ands, g.n);
   const double t_jit = cached ? cost_run_ms(c, LEC_ES_TIER_JIT, g.cone_ands, g.n, c ? jit_held_lop3(c, g) : 0.0)
@@ -1314,8 +1363,9 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
     char name[160];
     uint64_t nest = 1469598103934665603ull;  // FNV-1a over the loop groups
     for (uint64_t m : lay.groups) nest = (nest ^ m) * 1099511628211ull;
-    snprintf(name, sizeof(name), "/es_v%d_%016llx_%s%s_r%u_h%u_p%llx_n%llx_sm%d%d.cubin", kCodegenVersion,
-             (unsigned long long)g.hash, lut_form ? "lut" : "and", getenv("LEC_ES_JIT_NVRTC") ? "_nvrtc" : "",
+    snprintf(name, sizeof(name), "/es_v%d_%016llx%016llx_%s%s_r%u_h%u_p%llx_n%llx_sm%d%d.cubin", kCodegenVersion,
+             (unsigned long long)g.hash, (unsigned long long)g.hash2, lut_form ? "lut" : "and",
+             getenv("LEC_ES_JIT_NVRTC") ? "_nvrtc" : "",
              lay.rep, lay.regs * 1000 + lay.plan, (unsigned long long)lay.pass_pis, (unsigned long long)nest, c->cc_major,
              c->cc_minor);
     path = c->jit_dir + name;
@@ -1366,6 +1416,7 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   k->num_records = g.num_records;
   k->work_per_chunk = lut_form ? g.lut.count : (uint32_t)g.recs.size();
   k->chunk_bits = g.n > 5 ? g.n - 5 : 0;
+  k->hash2 = g.hash2;
   if (ptx_form) {  // the PTX form: its grab layout
     k->rep_fixed = lay.rep;
     k->pass_bits = lay.pass_pis >> 5;
@@ -1397,7 +1448,10 @@ void worker_loop(lec_es_ctx *c) {
     JitKernel *k = nullptr;
     int rc = build_kernel(c, g, true, &k);
     std::lock_guard<std::mutex> lk(js->mu);
-    if (rc == LEC_ES_OK) js->cache[cache_key(g, true)] = k;
+    if (rc == LEC_ES_OK) {
+      if (!js->cache.count(cache_key(g, true))) js->cache[cache_key(g, true)] = k;
+      else js->unshared.push_back(k);  // the key is another structure's: never found by lookup
+    }
   }
 }
 
@@ -1405,7 +1459,7 @@ void worker_loop(lec_es_ctx *c) {
 
 uint64_t cache_key(const Program &g, bool lut_form) { return g.hash ^ (lut_form ? 0x9E3779B97F4A7C15ull : 0ull); }
 
-bool jit_probe(void *arg, uint64_t hash, uint32_t n, uint32_t cone_ands, KernelFacts *f) {
+bool jit_probe(void *arg, uint64_t hash, uint64_t hash2, uint32_t n, uint32_t cone_ands, KernelFacts *f) {
   const JitProbe *p = (const JitProbe *)arg;
   lec_es_ctx *c = p->c;
   if (!c->jit) return false;
@@ -1414,7 +1468,7 @@ bool jit_probe(void *arg, uint64_t hash, uint32_t n, uint32_t cone_ands, KernelF
     JitState *js = c->jit;
     std::lock_guard<std::mutex> lk(js->mu);
     auto it = js->cache.find(hash ^ 0x9E3779B97F4A7C15ull);
-    if (it == js->cache.end() || it->second->num_luts == 0) return false;
+    if (it == js->cache.end() || it->second->num_luts == 0 || it->second->hash2 != hash2) return false;
     k = it->second;
   }
   // will the caller run this kernel?  (else it needs the slot program)
@@ -1451,9 +1505,8 @@ int jit_get_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **o
   const uint64_t key = cache_key(g, lut_form);
   {
     std::lock_guard<std::mutex> lk(js->mu);
-    auto it = js->cache.find(key);
-    if (it != js->cache.end()) {
-      *out = it->second;
+    if (JitKernel *k = cached_kernel(js, g, lut_form)) {
+      *out = k;
       if (compile_ms) *compile_ms = 0;
       return LEC_ES_OK;
     }
@@ -1464,12 +1517,14 @@ int jit_get_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **o
   if (compile_ms) *compile_ms = k->compile_ms;
   std::lock_guard<std::mutex> lk(js->mu);
   auto it = js->cache.find(key);
-  if (it != js->cache.end()) {  // another thread built it first
+  if (it == js->cache.end()) {
+    js->cache[key] = k;
+  } else if (it->second->hash2 == g.hash2) {  // another thread built it first
     cudaLibraryUnload(k->lib);
     delete k;
     k = it->second;
-  } else {
-    js->cache[key] = k;
+  } else {  // the key belongs to another structure: keep this kernel out of the cache
+    js->unshared.push_back(k);
   }
   *out = k;
   return LEC_ES_OK;
@@ -1504,8 +1559,7 @@ JitKernel *jit_lookup_or_schedule(lec_es_ctx *c, const Program &g) {
   JitState *js = state(c);
   std::lock_guard<std::mutex> lk(js->mu);
   const uint64_t key = cache_key(g, true);
-  auto it = js->cache.find(key);
-  if (it != js->cache.end()) return it->second;
+  if (JitKernel *k = cached_kernel(js, g, true)) return k;
   if (!js->scheduled[key]) {
     js->scheduled[key] = true;
     js->todo.push_back(g);
@@ -1639,6 +1693,10 @@ void jit_release_all(lec_es_ctx *c) {
   for (auto &kv : js->cache) {
     if (kv.second->lib) cudaLibraryUnload(kv.second->lib);
     delete kv.second;
+  }
+  for (JitKernel *k : js->unshared) {
+    if (k->lib) cudaLibraryUnload(k->lib);
+    delete k;
   }
   delete js;
   c->jit = nullptr;

@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -50,6 +51,11 @@ struct Slot {
   unsigned long long *d_res = nullptr;  // kResWords result words
   unsigned long long *h_res = nullptr;  // pinned
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  // recorded on the control stream after a cancellation's zero write into
+  // d_res; the slot's next reset copy waits for it, so a late zero can never
+  // land on the next request's counterexample word
+  cudaEvent_t zeroed = nullptr;
+  bool zero_pending = false;
   bool busy = false;
 };
 
@@ -89,7 +95,7 @@ struct Server {
   std::vector<int> stream_load;
   cudaStream_t ctl = nullptr;
   unsigned long long *h_zero = nullptr;
-  std::unordered_map<uint64_t, Resident> resident;
+  std::map<std::pair<uint64_t, uint64_t>, Resident> resident;  // by both structure hashes
   size_t used = 0;
   uint64_t next_ticket = 1;
   bool stop = false;
@@ -140,7 +146,7 @@ int launch(Server *s, Request *r) {
 
   Resident *res = nullptr;
   if (!k) {
-    auto it = s->resident.find(g.hash);
+    auto it = s->resident.find({g.hash, g.hash2});
     if (it == s->resident.end()) {
       Resident rr;
       if (!choose_word_geometry(c, g, nullptr, rr.geom)) return LEC_ES_ETOOBIG;  // slots stay on chip
@@ -165,9 +171,13 @@ int launch(Server *s, Request *r) {
         c->arena.free(rr.d_loads);
         return LEC_ES_ECUDA;
       }
-      it = s->resident.emplace(g.hash, rr).first;
+      it = s->resident.emplace(std::make_pair(g.hash, g.hash2), rr).first;
     }
     res = &it->second;
+  }
+  if (sl.zero_pending) {  // a cancellation's zero write into this slot must land first
+    if (cudaStreamWaitEvent(st, sl.zeroed, 0) != cudaSuccess) return LEC_ES_ECUDA;
+    sl.zero_pending = false;
   }
   if (cudaMemcpyAsync(sl.d_res, c->h_init, kResWords * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return LEC_ES_ECUDA;
@@ -268,6 +278,8 @@ void dispatcher(Server *s) {
         // the request's reset copy has run: zero its counterexample word so
         // every later pass of its kernel sees "nothing lower to find"
         cudaMemcpyAsync(sl.d_res, s->h_zero, 8, cudaMemcpyHostToDevice, s->ctl);
+        cudaEventRecord(sl.zeroed, s->ctl);
+        sl.zero_pending = true;
         r->cancel_sent = true;
       }
       cudaError_t q = cudaEventQuery(sl.e2);
@@ -353,13 +365,22 @@ int ensure_server(lec_es_ctx *c) {
     if (!sl.d_res) return LEC_ES_ENOMEM;
     if (cudaMallocHost((void **)&sl.h_res, kResWords * 8) != cudaSuccess) return LEC_ES_ENOMEM;
     if (cudaEventCreate(&sl.e0) != cudaSuccess || cudaEventCreate(&sl.e1) != cudaSuccess ||
-        cudaEventCreateWithFlags(&sl.e2, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&sl.e2, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.zeroed, cudaEventDisableTiming) != cudaSuccess)
       return LEC_ES_ECUDA;
   }
   Server *raw = s.get();
   raw->th = std::thread(dispatcher, raw);
   c->server = s.release();
   return LEC_ES_OK;
+}
+
+// The ctx's server, read under server_mu (ensure_server and server_shutdown
+// write it under the same lock).  lec_es_destroy must not run concurrently
+// with other calls on the same ctx.
+Server *server_of(lec_es_ctx *c) {
+  std::lock_guard<std::mutex> g(c->server_mu);
+  return c->server;
 }
 
 }  // namespace
@@ -395,6 +416,7 @@ void server_shutdown(lec_es_ctx *c) {
     if (sl.e0) cudaEventDestroy(sl.e0);
     if (sl.e1) cudaEventDestroy(sl.e1);
     if (sl.e2) cudaEventDestroy(sl.e2);
+    if (sl.zeroed) cudaEventDestroy(sl.zeroed);
   }
   for (auto &kv : s->resident) {
     c->arena.free(kv.second.d_recs);
@@ -435,7 +457,7 @@ extern "C" int lec_es_submit(lec_es_ctx *c, const lec_es_miter *m, uint64_t *tic
   if (rc) return rc;
   rc = ensure_server(c);
   if (rc) return rc;
-  Server *s = c->server;
+  Server *s = server_of(c);
   r->t_submit = t0;
   r->res.host_ms = now_ms() - t0;
   std::lock_guard<std::mutex> lk(s->mu);
@@ -465,7 +487,7 @@ int collect(Server *s, uint64_t ticket, lec_es_result *out) {
 
 extern "C" int lec_es_poll(lec_es_ctx *c, uint64_t ticket, lec_es_result *out) {
   if (!c || !out) return LEC_ES_EINVAL;
-  Server *s = c->server;
+  Server *s = server_of(c);
   if (!s) return LEC_ES_ENOTFOUND;
   std::lock_guard<std::mutex> lk(s->mu);
   return collect(s, ticket, out);
@@ -473,7 +495,7 @@ extern "C" int lec_es_poll(lec_es_ctx *c, uint64_t ticket, lec_es_result *out) {
 
 extern "C" int lec_es_wait(lec_es_ctx *c, uint64_t ticket, double timeout_s, lec_es_result *out) {
   if (!c || !out) return LEC_ES_EINVAL;
-  Server *s = c->server;
+  Server *s = server_of(c);
   if (!s) return LEC_ES_ENOTFOUND;
   std::unique_lock<std::mutex> lk(s->mu);
   const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
@@ -489,7 +511,7 @@ extern "C" int lec_es_wait(lec_es_ctx *c, uint64_t ticket, double timeout_s, lec
 
 extern "C" int lec_es_cancel(lec_es_ctx *c, uint64_t ticket) {
   if (!c) return LEC_ES_EINVAL;
-  Server *s = c->server;
+  Server *s = server_of(c);
   if (!s) return LEC_ES_ENOTFOUND;
   std::lock_guard<std::mutex> lk(s->mu);
   auto it = s->reqs.find(ticket);

@@ -200,6 +200,10 @@ def test_unrolled_pass_levels_keep_results(rep, unroll, monkeypatch):
                 if wb < we:
                     g = L.lec_es_check_ex(c, m, L.options(wb, we, L.TIER_JIT))
                     assert g.cex_or_none == oracle_cex(aig, out, wb, we), (wb, we)
+        # planted 16x16 counterexamples (closed form) under the forced layout
+        for p in ((1 << 31) | 0x2345, (1 << 28) | (1 << 26) | 7, 0x6A09E667):
+            mm = C.config3_mult16(minterm=p)
+            assert L.lec_es_check_ex(c, L.miter_of(mm), L.options(tier=L.TIER_JIT)).cex == p, hex(p)
     finally:
         L.lec_es_destroy(c)
 
@@ -242,17 +246,27 @@ def test_plan_info_reports_lop3_per_pass(ctx):
         L.lec_es_plan_free(ctx, p)
 
 
-def test_searched_layouts_agree_with_the_flat_kernel(monkeypatch):
+def test_searched_layouts_match_the_oracle(monkeypatch):
     """Cones of 1,000 tables or more get a layout chosen by dry runs of the
-    generator (more pass PIs, nested and unrolled levels).  Too large for
-    the oracle's enumeration, their lowest counterexamples are compared with
-    those of the simplest kernel form (one pass loop, nothing unrolled),
-    itself pinned to the oracle on small cones, over the full pattern space
-    and random word ranges."""
+    generator (more pass PIs, nested and unrolled levels).  On 28-30-PI
+    node-pair mutants (up to 2^24 words) that layout's lowest
+    counterexample equals the oracle's over the full pattern space and over
+    seeded word ranges; so does the simplest kernel form (one pass loop,
+    nothing unrolled)."""
+    import os
     pm = C.ProductBitMiters(seed=5)
     cases = [pm.miter(15, 22, mutant=True, mutant_seed=s) for s in (1, 2)]
     cases.append(pm.miter(14, 26, mutant=True, mutant_seed=3))
     rng = np.random.default_rng(77)
+    threads = max(4, os.cpu_count() or 4)
+    spans, want = [], []
+    for aig, o in cases:
+        info, _ = L.lec_es_compile(L.Miter(aig.num_pis, aig.flat_fanins(), o))
+        W = 1 << (info.n - 6)
+        rs = [(0, W)] + [tuple(sorted(int(x) for x in rng.integers(0, W, 2))) for _ in range(3)]
+        spans.append(rs)
+        want.append([O.check_parallel(aig.num_pis, aig.fanins, o, threads, wb, we)[0] for wb, we in rs])
+    assert any(x is not None for w in want for x in w)
 
     def lowest(env):
         for k in ("LEC_ES_JIT_NEST", "LEC_ES_JIT_UNROLL"):
@@ -264,20 +278,54 @@ def test_searched_layouts_agree_with_the_flat_kernel(monkeypatch):
             out = []
             for (aig, o), ranges in zip(cases, spans):
                 m = L.Miter(aig.num_pis, aig.flat_fanins(), o)
+                got = []
                 for wb, we in ranges:
                     r = L.lec_es_check_ex(c, m, L.options(wb, we, L.TIER_JIT))
                     assert r.tier == L.TIER_JIT
-                    out.append(r.cex_or_none)
+                    got.append(r.cex_or_none)
+                out.append(got)
             return out
         finally:
             L.lec_es_destroy(c)
 
-    spans = []
-    for aig, o in cases:
-        info, _ = L.lec_es_compile(L.Miter(aig.num_pis, aig.flat_fanins(), o))
-        W = 1 << (info.n - 6)
-        spans.append([(0, W)] + [tuple(sorted(int(x) for x in rng.integers(0, W, 2))) for _ in range(3)])
-    searched = lowest({})
-    flat = lowest({"LEC_ES_JIT_NEST": "0", "LEC_ES_JIT_UNROLL": "0"})
-    assert searched == flat
-    assert any(x is not None for x in searched)
+    assert lowest({}) == want
+    assert lowest({"LEC_ES_JIT_NEST": "0", "LEC_ES_JIT_UNROLL": "0"}) == want
+
+
+# Planted counterexamples of the 16x16 miter (the benchmark's cone plus one
+# minterm): below the grab bits (lane and mask PIs), in the low and high
+# grab bits, at each of the six least influential PIs b10..b15 (PIs 26..31:
+# the pass PIs of its loop and unrolled levels), in pairs of them, and at
+# seeded points of the whole space.
+_PLANTED = ([37, (1 << 10) | 5, (1 << 14) | 0x3FF, (1 << 25) | 0xABCD]
+            + [(1 << k) | 0x1234 for k in range(26, 32)]
+            + [(1 << 31) | (1 << 30) | 99, (1 << 29) | (1 << 27) | (1 << 12), (1 << 30) | (1 << 26)]
+            + [int(x) for x in np.random.default_rng(1616).integers(0, 1 << 32, 3)])
+
+
+def test_planted_minterms_16x16_default_layout(ctx):
+    """The 16x16 miter with one planted minterm fails at that pattern alone
+    (closed form, pinned on the CPU).  The specialised kernel in the layout
+    its search picks for the cone (the benchmark's layout: nested and
+    unrolled pass levels, in-grab early exit) returns exactly that pattern
+    wherever it sits, so does the default AUTO check (whichever tier it
+    takes), and the oracle agrees on the 64 words around it."""
+    for p in _PLANTED:
+        mm = C.config3_mult16(minterm=p)
+        out = mm.outputs[0]
+        r = L.lec_es_check_ex(ctx, L.miter_of(mm), L.options(tier=L.TIER_JIT))
+        assert r.tier == L.TIER_JIT, p
+        assert r.verdict == L.NONEQUIVALENT and r.cex == p, (hex(p), hex(r.cex))
+        assert L.lec_es_check(ctx, L.miter_of(mm)).cex == p
+        lo = max(0, (p >> 6) - 32)
+        assert oracle_cex(mm, out, lo, lo + 64) == p
+        # a range that starts past p passes (UNDECIDED); one that ends at p's word misses it
+        w = p >> 6
+        if w + 1 < (1 << 26):
+            g = L.lec_es_check_ex(ctx, L.miter_of(mm), L.options(w + 1, 1 << 26, L.TIER_JIT))
+            assert g.cex_or_none is None and g.verdict == L.UNDECIDED
+        if w > 0:
+            g = L.lec_es_check_ex(ctx, L.miter_of(mm), L.options(0, w, L.TIER_JIT))
+            assert g.cex_or_none is None
+        g = L.lec_es_check_ex(ctx, L.miter_of(mm), L.options(w, w + 1, L.TIER_JIT))
+        assert g.cex == p

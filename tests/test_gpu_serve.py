@@ -81,3 +81,34 @@ def test_cancel_timeout_and_unknown_ticket():
     r = L.lec_es_wait(ctx, t1, 60.0)
     assert r.cex_or_none == oracle_cex(C.config1_adders(1), C.config1_adders(1).outputs[0])
     L.lec_es_destroy(ctx)
+
+
+def test_cancel_then_resubmit_resident_program():
+    """Cancelling a running request zeroes its counterexample word on a
+    control stream; the result slot it frees is reused at once by the next
+    request.  With the small program already resident (no upload, no sync
+    on admission), the next requests must still get their own verdicts:
+    every equivalent request EQUIVALENT and every mutant the oracle's cex."""
+    ctx = make_ctx()
+    L.lec_es_server_config(ctx, 32 << 30, 2)  # two result slots: the freed one is reused at once
+    good_a = C.config1_adders()
+    bad_a = C.config1_adders(1)
+    good, bad = L.miter_of(good_a), L.miter_of(bad_a)
+    want_bad = oracle_cex(bad_a, bad_a.outputs[0])
+    for m in (good, bad):  # make both programs resident on the server
+        L.lec_es_wait(ctx, L.lec_es_submit(ctx, m), 60.0)
+    pm = C.ProductBitMiters(seed=5)
+    big_aig, big_out = pm.miter(16, 20)
+    big = L.Miter(big_aig.num_pis, big_aig.flat_fanins(), big_out)
+    for i in range(40):
+        t = L.lec_es_submit(ctx, big)
+        time.sleep(0.0005 * (i % 4))
+        L.lec_es_cancel(ctx, t)
+        ts = [L.lec_es_submit(ctx, good if j % 2 == 0 else bad) for j in range(4)]
+        with pytest.raises(L.LecEsError) as e:
+            L.lec_es_wait(ctx, t, 60.0)
+        assert e.value.status in (L.ECANCELLED,)
+        got = [L.lec_es_wait(ctx, x, 60.0) for x in ts]
+        assert [r.verdict for r in got] == [L.EQUIVALENT, L.NONEQUIVALENT] * 2, i
+        assert got[1].cex == want_bad and got[3].cex == want_bad
+    L.lec_es_destroy(ctx)

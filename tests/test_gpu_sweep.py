@@ -1,7 +1,8 @@
 """Sweeping step (1) on the GPU: random-simulation signatures and candidate
 pairs.  Signatures must equal the oracle's evaluation of every node at the
-same patterns (bit-exact); the candidate pairs must equal the pairing the
-workload generator computes from its own simulator on the same words."""
+same patterns (bit-exact); the candidate pairs must equal the pairing
+defined from the oracle's evaluation of every node at the same patterns
+(tests/reference_pairs.py)."""
 import numpy as np
 import pytest
 
@@ -10,6 +11,7 @@ from paper_2512_06627_b300 import circuits as C
 from paper_2512_06627_b300 import lec_es as L
 from tests.gpu_common import make_ctx
 from tests.reference_eval import random_aig
+from tests.reference_pairs import pairs_from_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -61,9 +63,22 @@ def test_signatures_32x32_pair_graph_sampled(ctx):
     assert np.array_equal(got, bits)
 
 
-def test_pairs_equal_generator_pairing(ctx):
+def test_pairs_equal_oracle_pairing(ctx):
+    """The GPU matcher's pairs on the 32x32 four-multiplier graph equal the
+    pairs defined from the oracle's own evaluation of every node at the same
+    random patterns (tests/reference_pairs.py)."""
     base = C.build_golden_revised_multipliers(32)
     pw = C.signature_words(base, 64, 4)
     gpu = L.lec_es_match_pairs(ctx, base.num_pis, base.flat_fanins(), pw, 28)
-    ref, _ = C.candidate_pairs(base, 64, 4, 28)
+    ref = pairs_from_oracle(base, pw, 28)
     assert gpu == ref and len(gpu) == 4238
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_pairs_equal_oracle_pairing_random_graphs(ctx, seed):
+    rng = np.random.default_rng(500 + seed)
+    aig = random_aig(rng, int(rng.integers(4, 20)), int(rng.integers(50, 400)))
+    pw = rng.integers(0, 2**63, size=(aig.num_pis, 3), dtype=np.uint64)
+    for ms in (4, 8, 64):
+        gpu = L.lec_es_match_pairs(ctx, aig.num_pis, aig.flat_fanins(), pw, ms)
+        assert gpu == pairs_from_oracle(aig, pw, ms), ms

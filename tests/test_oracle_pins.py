@@ -283,3 +283,61 @@ def test_oracle_rejects_bad_graphs():
     ok = _aig(2, [2, 4], 6)
     with pytest.raises(ValueError):
         O.check(2, ok.fanins, 2 * 9)  # literal out of range
+
+
+# --- planted minterms: one failing pattern by construction -----------------------
+
+@pytest.mark.parametrize("w,p,bit", [(6, 0, None), (6, 0xABC, 3), (8, 0x8000, None), (8, 0x1234, 7),
+                                     (8, 0xFFFF, 0), (8, 0x0400, 15)])
+def test_planted_minterm_is_the_only_failing_pattern(w, p, bit):
+    """XORing the minterm of p into one product bit of the Booth side makes p
+    the only pattern where the sides differ: the oracle's lowest cex and
+    failing count (1) match the independent per-pattern evaluation of both
+    sides over the whole space."""
+    m = C.build_multiplier_pair(w, tree="dadda", planted_minterm=p, planted_bit=bit)
+    cex, count, n = O.check(m.num_pis, m.fanins, m.outputs[0], count_all=True)
+    assert (cex, count, n) == (p, 1, 2 * w)
+    P = np.arange(1 << (2 * w), dtype=np.uint64)
+    diff = to_int(eval_vectors(m, P, m.side_outputs["A"])) != to_int(eval_vectors(m, P, m.side_outputs["B"]))
+    assert np.flatnonzero(diff).tolist() == [p]
+
+
+@pytest.mark.parametrize("p", [1 << 20, (1 << 28) + 0x5A5A, (1 << 31) + (1 << 26) + 77, 0x9E3779B9])
+def test_planted_minterm_16x16_closed_form(p):
+    """The 16x16 planted mutant fails at p and nowhere near it: the oracle on
+    the 64 words around p's word finds p with count 1, seeded word ranges
+    elsewhere pass, and both netlists evaluated directly differ at p only."""
+    m = C.config3_mult16(minterm=p)
+    w = p >> 6
+    lo = max(0, w - 32)
+    cex, count, n = O.check(m.num_pis, m.fanins, m.outputs[0], lo, lo + 64, count_all=True)
+    assert (cex, count, n) == (p, 1, 32)
+    rng = np.random.default_rng(p & 0xFFFF)
+    for w0 in rng.integers(0, (1 << 26) - 32, size=6):
+        if not (w0 <= w < w0 + 32):
+            assert O.check(m.num_pis, m.fanins, m.outputs[0], int(w0), int(w0) + 32)[0] is None
+    A, B = m.side_outputs["A"], m.side_outputs["B"]
+    assert eval_one(m, p, A) != eval_one(m, p, B)
+    for q in (p - 1, p + 1, p ^ (1 << 31)):
+        assert eval_one(m, q, A) == eval_one(m, q, B)
+
+
+def test_reference_pairs_find_the_equal_sum_bits():
+    """The test-side pair reference (oracle evaluation at random patterns)
+    pairs every sum bit of a ripple-carry adder with the same bit of a
+    Kogge-Stone adder built in another hashing scope: equal functions have
+    equal signatures, and the lower variable (the ripple-carry side) is the
+    representative."""
+    from tests.reference_pairs import pairs_from_oracle
+    g = C.AigBuilder(16)
+    a = [g.pi(i) for i in range(8)]
+    b = [g.pi(8 + i) for i in range(8)]
+    x = C.ripple_carry_adder(g, a, b)
+    g.new_scope()
+    y = C.kogge_stone_adder(g, a, b)
+    aig = g.finish(x + y)
+    pw = C.signature_words(aig, 4, 9)
+    pairs = set(pairs_from_oracle(aig, pw, 16))
+    for lx, ly in zip(x[1:], y[1:]):  # bit 0 is a single XOR (hashed the same way on both sides)
+        if (lx >> 1) != (ly >> 1) and (lx & 1) == (ly & 1):
+            assert (min(lx, ly) >> 1, max(lx, ly) >> 1) in pairs, (lx, ly)
