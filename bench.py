@@ -53,16 +53,19 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-pairs", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=3)
-    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-load", type=float, default=0.7)
+    ap.add_argument("--serve-quick", action="store_true",
+                    help="the served measurement on --serve-requests requests (e.g. 200) with capacity, "
+                         "one-launch-each and Poisson figures instead of the full stream")
     ap.add_argument("--case", choices=CASES, default=None,
                     help="run one fixed profiling workload (prepared first, then --runs launches) instead of "
                          "the benchmark")
     ap.add_argument("--runs", type=int, default=2)
     ap.add_argument("--n", type=int, default=24, help="support size of the pair-jit case")
     ap.add_argument("--serve-full", action="store_true",
-                    help="the served workload at full size: a Poisson stream over all --serve-requests "
-                         "(e.g. 20000) at --serve-load of a capacity measured on the first 400, verdicts "
+                    help="(default) the served workload at full size: a Poisson stream over all "
+                         "--serve-requests at --serve-load of a capacity measured on the first 400, verdicts "
                          "checked against the generator, a seeded sample of 200 re-run alone")
     return ap.parse_args()
 
@@ -193,6 +196,53 @@ def cpu_oracle_rate(aig, seconds: float):
     return rate, cores, f"oracle over words [0, {words}) of 2^26 ({words * 64} of 2^32 patterns), {dt:.1f} s"
 
 
+def cpu_baselines(seconds: float):
+    """The CPU side of the paper's Table 1 comparison, on this host: the
+    oracle on one thread (configs 1-3; config 3 projected from a bounded
+    sample, marked), and the CPU-ES baseline (reference-counted instruction
+    stream, 2^14 patterns per pass and thread, every host thread) on configs
+    1-3 (config 3 over a sample when the whole space would exceed the time
+    bound, marked).  Times are wall-clock seconds for the whole pattern
+    space."""
+    import oracle as O
+    from paper_2512_06627_b300 import circuits as C
+    cores = os.cpu_count() or 1
+    out = {"cores": cores, "oracle_1_thread": {}, "cpu_es_all_threads": {}}
+    for name, aig in (("8-bit adders (2^16)", C.config1_adders()), ("12x12 (2^24)", C.config2_mult12()),
+                      ("16x16 (2^32)", C.config3_mult16())):
+        o = aig.outputs[0]
+        _, cone = O.support(aig.num_pis, aig.fanins, o)
+        n = aig.num_pis
+        W = O.num_words(n)
+        # oracle, one thread: the whole space, or a sample sized from a probe
+        probe = min(W, 4096)
+        t0 = time.perf_counter()
+        O.check(aig.num_pis, aig.fanins, o, 0, probe)
+        per_word = (time.perf_counter() - t0) / probe
+        words = W if per_word * W <= seconds else max(probe, int(seconds / per_word))
+        t0 = time.perf_counter()
+        cex = O.check(aig.num_pis, aig.fanins, o, 0, words)[0]
+        dt = time.perf_counter() - t0
+        assert cex is None
+        out["oracle_1_thread"][name] = {"s": dt * W / words, "measured_s": dt, "words": words, "of_words": W,
+                                        "projected": words < W,
+                                        "evals_per_s": cone * 64.0 * words / dt}
+        # CPU-ES baseline, all threads
+        probe = min(W, cores * 256 * 8)
+        t0 = time.perf_counter()
+        O.cpu_es_blocked(aig.num_pis, aig.fanins, o, 0, probe)
+        per_word = (time.perf_counter() - t0) / probe
+        words = W if per_word * W <= 2 * seconds else max(probe, int(2 * seconds / per_word))
+        t0 = time.perf_counter()
+        cex = O.cpu_es_blocked(aig.num_pis, aig.fanins, o, 0, words)[0]
+        dt = time.perf_counter() - t0
+        assert cex is None
+        out["cpu_es_all_threads"][name] = {"s": dt * W / words, "measured_s": dt, "words": words, "of_words": W,
+                                           "projected": words < W, "block_words": 256,
+                                           "evals_per_s": cone * 64.0 * words / dt}
+    return out
+
+
 # ---------------------------------------------------------------------------
 # batched and served sub-measurements
 # ---------------------------------------------------------------------------
@@ -262,6 +312,19 @@ def measure_batch(ctx, args):
     for p in plans:
         L.lec_es_plan_free(ctx, p)
     a_s, s_s = min(one_async), min(one_sync)
+    # the same miters as served requests (all submitted, then waited; the
+    # front end runs on the server's threads) against one lec_es_check each
+    served_s, check_s = [], []
+    for _ in range(2):
+        t0 = time.perf_counter()
+        tk = [L.lec_es_submit(ctx, m) for m in ms]
+        got = [L.lec_es_wait(ctx, t, 600.0).cex for t in tk]
+        served_s.append(time.perf_counter() - t0)
+        assert got == ref
+        t0 = time.perf_counter()
+        got = [L.lec_es_check(ctx, m).cex for m in ms]
+        check_s.append(time.perf_counter() - t0)
+        assert got == ref
     big = work >= np.sort(work)[-max(1, k // 100)]
     return {
         "pairs": k, "nonequivalent": int(sum(1 for x in ref if x != L.NO_CEX)),
@@ -273,6 +336,8 @@ def measure_batch(ctx, args):
         "one_launch_per_miter_sync_miters_per_s": k / s_s,
         "speedup_vs_async": batched / (k / a_s),
         "speedup_vs_sync": batched / (k / s_s),
+        "served": {"miters_per_s": k / min(served_s), "one_check_each_miters_per_s": k / min(check_s),
+                   "speedup": min(check_s) / min(served_s), "results_equal": True},
         "work_share_top_1pct": float(work[big].sum() / work.sum()),
         "prepare_s": prep, "jit_compile_s": layout.jit_ms / 1e3, "autotune_s": layout.tune_ms / 1e3,
         "sweep_step1": {"graph_ands": int(base.num_ands), "signature_words": 64, "candidate_pairs": len(cand),
@@ -280,6 +345,93 @@ def measure_batch(ctx, args):
         "layout": {"tile_miters": layout.tile_miters, "tiles": layout.tiles,
                    "threads_per_tile_pass": layout.block_threads, "tiles_per_block_slot": layout.tile_granularity,
                    "stage_records": layout.stage_records, "grid_blocks": layout.grid_blocks},
+    }
+
+
+def measure_batch_spread(ctx, args):
+    """The batched workload at its stated spread (circuits.config4_spread):
+    4,096 miters of 10..28 PIs, node pairs of five multiplier graphs up to
+    whole four-multiplier miters (56..~7.9k cone ANDs), ~2% mutants.  One
+    prepared batch (autotuned; CUDA-graph replay) against one launch per
+    miter with the same kernel each (back to back with one sync, and with a
+    sync per miter), identical results asserted.  Also: the spread, the
+    work-weighted share per support size, and the Amdahl bound of batching
+    (one-launch time over the summed kernel time of the miters whose kernel
+    alone runs for at least 0.2 ms, which batching cannot shorten)."""
+    import numpy as np
+    import torch
+    from paper_2512_06627_b300 import circuits as C
+    from paper_2512_06627_b300 import lec_es as L
+    trip = C.config4_spread(num=args.batch_pairs)
+    flat = {}
+    ms = []
+    for aig, out, _ in trip:
+        f = flat.get(id(aig))
+        if f is None:
+            f = flat[id(aig)] = (aig, aig.flat_fanins())
+        ms.append(L.Miter(aig.num_pis, f[1], out))
+    k = len(ms)
+    t0 = time.perf_counter()
+    b = L.lec_es_batch_prepare(ctx, ms, L.options(flags=L.FLAG_AUTOTUNE))
+    prep = time.perf_counter() - t0
+    layout = L.lec_es_batch_info(b)
+    L.lec_es_batch_run_async(ctx, b)
+    first = L.lec_es_batch_results(ctx, b, k)
+    ref = [r.cex for r in first]
+    tiers = [int(r.tier) for r in first]
+    infos = [L.lec_es_compile(m)[0] for m in ms]
+    ts = []
+    res = (L.lec_es_result * k)()
+    lib = L.load()
+    for _ in range(args.batch_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L.lec_es_batch_run_async(ctx, b)
+        rc = lib.lec_es_batch_results(ctx.handle, b, res, k)
+        ts.append(time.perf_counter() - t0)
+        assert rc == 0 and [r.cex for r in res] == ref
+    L.lec_es_batch_free(ctx, b)
+    plans = [L.lec_es_prepare(ctx, m, L.options(tier=t)) for m, t in zip(ms, tiers)]
+    one_async, one_sync, dev = [], [], []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for p in plans:
+            L.lec_es_run_async(ctx, p)
+        torch.cuda.synchronize()
+        one_async.append(time.perf_counter() - t0)
+        assert [L.lec_es_plan_result(ctx, p).cex for p in plans] == ref
+        t0 = time.perf_counter()
+        dev = []
+        for p in plans:
+            L.lec_es_run_async(ctx, p)
+            dev.append(L.lec_es_plan_result(ctx, p).device_ms)
+        one_sync.append(time.perf_counter() - t0)
+    for p in plans:
+        L.lec_es_plan_free(ctx, p)
+    ns = np.array([i.n for i in infos])
+    ands = np.array([i.cone_ands for i in infos], dtype=np.float64)
+    work = ands * np.exp2(ns)
+    dev = np.array(dev)
+    heavy_ms = float(dev[dev >= 0.2].sum())
+    batched = k / statistics.median(ts)
+    a_s, s_s = min(one_async), min(one_sync)
+    from collections import Counter
+    return {
+        "miters": k, "sources": dict(Counter(src for _, _, src in trip)),
+        "nonequivalent": int(sum(1 for x in ref if x != L.NO_CEX)),
+        "support_pis": {"min": int(ns.min()), "max": int(ns.max())},
+        "cone_ands": {"min": int(ands.min()), "median": float(np.median(ands)), "max": int(ands.max())},
+        "work_share_by_support": {int(n): float(work[ns == n].sum() / work.sum()) for n in np.unique(ns)},
+        "work_share_top_1pct": float(np.sort(work)[-max(1, k // 100):].sum() / work.sum()),
+        "jit_miters": int(sum(1 for t in tiers if t == L.TIER_JIT)),
+        "batched_miters_per_s": batched, "batched_ms": statistics.median(ts) * 1e3,
+        "one_launch_per_miter_async_miters_per_s": k / a_s,
+        "one_launch_per_miter_sync_miters_per_s": k / s_s,
+        "speedup_vs_async": batched / (k / a_s), "speedup_vs_sync": batched / (k / s_s),
+        "one_launch_kernel_ms_sum": float(dev.sum()), "kernels_of_0p2ms_or_more_ms": heavy_ms,
+        "amdahl_bound_vs_async": a_s * 1e3 / heavy_ms if heavy_ms > 0 else None,
+        "prepare_s": prep, "jit_compile_s": layout.jit_ms / 1e3,
     }
 
 
@@ -393,14 +545,54 @@ def measure_sweep(ctx):
     return out
 
 
+def measure_cold(dev):
+    """Time to verdict of a first check of the 16x16 miter in a fresh
+    context that holds no kernel (no disk cache): lec_es_check starts the
+    interpreter at once and builds the specialised kernel in the background,
+    handing the rest of the range to it if it lands first.  Beside it: the
+    same check on the interpreter alone, when the background build lands,
+    and a check once the kernel is held."""
+    from paper_2512_06627_b300 import circuits as C
+    from paper_2512_06627_b300 import lec_es as L
+    c2 = L.lec_es_create(dev, arena_bytes=512 << 20)
+    try:
+        m = L.miter_of(C.config3_mult16())
+        t0 = time.perf_counter()
+        r = L.lec_es_check(c2, m)
+        cold_ms = (time.perf_counter() - t0) * 1e3
+        assert r.verdict == L.EQUIVALENT
+        out = {"cold_check_ms": cold_ms, "cold_check_tier": int(r.tier), "cold_check_device_ms": r.device_ms,
+               "cold_check_front_end_ms": r.host_ms}
+        t1 = time.perf_counter()
+        ri = L.lec_es_check_ex(c2, m, L.options(tier=L.TIER_INTERP))
+        out["interpreter_only_ms"] = (time.perf_counter() - t1) * 1e3
+        out["interpreter_only_device_ms"] = ri.device_ms
+        landed = None
+        while time.perf_counter() - t0 < 120:
+            p = L.lec_es_cost_predict(c2, m, 1)
+            if p.jit_compile_ms == 0.0:
+                landed = time.perf_counter() - t0
+                break
+            time.sleep(0.05)
+        out["kernel_landed_after_s"] = landed
+        L.lec_es_check(c2, m)
+        t2 = time.perf_counter()
+        rw = L.lec_es_check(c2, m)
+        out["held_kernel_check_ms"] = (time.perf_counter() - t2) * 1e3
+        out["held_kernel_tier"] = int(rw.tier)
+        return out
+    finally:
+        L.lec_es_destroy(c2)
+
+
 def measure_mutants(ctx, full_ms):
     """Time to verdict of non-equivalent miters, whose check ends at the
     lowest counterexample (early exit, paper §2.2): the 12x12 workload's
     three seeded mutants, the 16x16 mutant whose only failing pattern is the
     last (2^32 - 1), and 16x16 miters with one planted minterm at p = 2^20,
-    2^28 and 2^31 (+ 12,345).  Each kernel is built by a first check; the
-    time is the median of five checks (kernel time by CUDA events, and the
-    whole call).  'expected_ms' = the launch floor (the kernel time of a
+    2^28 and 2^31 (+ 12,345).  Each kernel is built by a first check on the
+    specialised tier; the time is the median of five default (AUTO) checks
+    (kernel time by CUDA events, and the whole call).  'expected_ms' = the launch floor (the kernel time of a
     counterexample in the first chunk) + (cex / 2^n) x the equivalent miter's
     full-enumeration kernel time."""
     from paper_2512_06627_b300 import circuits as C
@@ -408,6 +600,7 @@ def measure_mutants(ctx, full_ms):
 
     def timed(aig):
         m = L.miter_of(aig)
+        L.lec_es_check_ex(ctx, m, L.options(tier=L.TIER_JIT))  # build the cone's kernel
         r = L.lec_es_check(ctx, m)
         dev, wall = [], []
         for _ in range(5):
@@ -531,7 +724,7 @@ def run_ours(args, ws, rank, local):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")  # > 126 MB L2
     st = ctx.stream
     tier_ran = None
-    ttv = None  # time to verdict of this first, cold check: front end and kernel build, then the run
+    ttv = None  # the plan's preparation (front end, kernel build or disk-cache read) and its first run
     for i in range(args.warmup):
         t1 = time.perf_counter()
         L.lec_es_run_async(ctx, plan)
@@ -595,11 +788,11 @@ def run_ours(args, ws, rank, local):
     traffic = NCU_TRAFFIC.get((tier_name, int(info.hash), int(info.num_luts), L.lec_es_codegen_version()))
     # the LOP3 the generated kernel executes: per 32-pattern chunk and thread
     # (from the code generator) x chunks per launch
-    executed = None
-    if info.lop3_per_pass > 0:
-        ex_lop3 = info.lop3_per_pass * float(1 << max(0, n - 5))
-        executed = {"lop3_per_pass": info.lop3_per_pass, "lop3_per_launch": ex_lop3,
-                    "achieved": ex_lop3 / kern_s, "frac": ex_lop3 / kern_s / peak}
+    and_basis = {"lop3_per_launch": lop3_per_launch, "achieved": achieved, "frac": achieved / peak,
+                 "note": "one 2-input LOP3 per AIG AND per 32 patterns (the metric's unit of work); the kernel "
+                         "covers the cone with 3-input tables and runs most of them less often than once per "
+                         "pass, so this basis exceeds the peak"}
+    ex_lop3 = info.lop3_per_pass * float(1 << max(0, n - 5)) if info.lop3_per_pass > 0 else lop3_per_launch
     line = {
         "metric": "node-pattern evals/s",
         "value": value,
@@ -624,42 +817,47 @@ def run_ours(args, ws, rank, local):
                 "kernel_ms": statistics.mean(e2e_dev)},
         "gpu_launches": args.steps,
         "gpu_launches_e2e": e2e_steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "LOP3/s",
-                     "frac": achieved / peak, "traffic": traffic,
+        "roofline": {"bound": "alu", "achieved": ex_lop3 / kern_s, "peak": peak, "unit": "LOP3/s",
+                     "frac": ex_lop3 / kern_s / peak, "traffic": traffic,
                      "peak_basis": f"{sms} SMs x {per_clk:.1f} LOP3/clk/SM (measured) x {sm_max:.0f} MHz max",
-                     "algorithmic_unit": "one 2-input LOP3 per AIG AND per 32 patterns",
-                     "note": "the JIT tier covers the cone with 3-input tables and runs most of them less "
-                             "often than once per pass (loop levels, folded unrolled copies), so it executes "
-                             "far fewer LOP3 than ANDs and frac exceeds 1; 'executed' is the same kernel time "
-                             "against the LOP3 the generated kernel executes",
-                     "executed": executed},
+                     "work_per_launch": ex_lop3, "lop3_per_pass": info.lop3_per_pass,
+                     "algorithmic_unit": "the LOP3 the generated kernel executes: lop3 per 32-pattern pass "
+                                         "(from the code generator) x 2^(n-5) passes",
+                     "and_basis": and_basis},
+        "ms_per_full_enumeration": statistics.median(kern_ms),
         "tables": {"num_luts": int(info.num_luts), "luts_per_and": info.num_luts / max(1, info.cone_ands),
                    "lut_live_values": int(info.lut_live)},
         "lop3_measured": {"per_clk_per_sm": per_clk, "sm_clock_mhz_during": khz / 1e3, "lop3_per_s": lop3_rate},
         "kernel_ms_mean": statistics.mean(kern_ms),
         "prepare_s": prep_s,
-        "time_to_verdict": ttv,
+        "plan_prepare": ttv,
+        "time_to_verdict": measure_cold(dev),
         "clocks": clocks,
     }
     if rank == 0:
         line["mutant_time_to_verdict"] = measure_mutants(ctx, statistics.median(kern_ms))
     if rank == 0 and not args.no_batch:
         line["batched"] = measure_batch(ctx, args)
+        line["batched_spread"] = measure_batch_spread(ctx, args)
     if rank == 0 and args.serve_requests > 0:
-        line["served"] = measure_serve_full(ctx, args) if args.serve_full else measure_serve(ctx, args)
+        line["served"] = measure_serve(ctx, args) if args.serve_quick else measure_serve_full(ctx, args)
     if rank == 0 and not args.no_batch:
         line["sweep"] = measure_sweep(ctx)
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, sample = cpu_oracle_rate(aig, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "node-pattern evals/s", "cores": cores, "kind": "oracle",
                                 "sample": sample}
+        line["cpu_baselines"] = cpu_baselines(args.cpu_seconds / 3)
     L.lec_es_plan_free(ctx, plan)
     L.lec_es_destroy(ctx)
     return line
 
 
 def run_reference(args, ws, rank):
-    """The oracle as it stands on the host cores, one bounded sample per step."""
+    """The oracle as it stands on the host cores, one bounded sample of the
+    16x16 workload's words per step.  ms_per_step is the measured wall time
+    of a step (its sample); the time a whole 2^32-pattern enumeration would
+    take at that rate is reported separately, as a projection."""
     from paper_2512_06627_b300 import circuits as C
     aig = C.config3_mult16()
     if rank != 0:
@@ -669,20 +867,25 @@ def run_reference(args, ws, rank):
     per = max(2.0, min(20.0, 60.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         cpu_oracle_rate(aig, per / 4)
-    rates, samples = [], []
+    rates, samples, step_s = [], [], []
     for _ in range(args.steps):
-        r, cores, s = cpu_oracle_rate(aig, per)
+        t0 = time.perf_counter()
+        r, cores, smp = cpu_oracle_rate(aig, per)
+        step_s.append(time.perf_counter() - t0)
         rates.append(r)
-        samples.append(s)
+        samples.append(smp)
     value = statistics.mean(rates)
     units = cone * float(1 << 32)
     return {
         "impl": "reference",
         "metric": "node-pattern evals/s", "value": value, "unit": "node-pattern evals/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": units / value * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_s) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic (seeded generated netlists)",
-        "config": {"workload": WORKLOAD, "cone_ands": cone, "support_pis": 32},
+        "config": {"workload": WORKLOAD, "cone_ands": cone, "support_pis": 32,
+                   "step": "one bounded sample of the workload's words (see cpu_baseline.sample)"},
+        "projection": {"ms_per_full_enumeration": units / value * 1e3,
+                       "note": "a whole 2^32-pattern enumeration at the sampled rate; projected, not run"},
         "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count() or 1, "sample": samples[-1], "value": value,
                          "unit": "node-pattern evals/s"},
         "e2e": {"value": value, "unit": "node-pattern evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

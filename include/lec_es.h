@@ -199,7 +199,12 @@ int lec_es_jit_compile(const lec_es_miter *m, int cc_major, int cc_minor, char *
  * cone compiled to a reference-counted instruction stream (§3.3).  m and its
  * fanins are read during the call only; *out is written on LEC_ES_OK:
  * verdict EQUIVALENT or NONEQUIVALENT with the lowest failing pattern.
- * Equivalent to prepare + run + plan_free with default options (AUTO tier).
+ * Tier (AUTO): the ES time model's choice (§3.2, refit), except that a check
+ * never waits for a kernel build -- a cone whose specialised kernel would
+ * pay off but is not built yet starts on the interpreter in ascending word
+ * slices while the kernel builds in the background; a failing slice ends
+ * the check, and once the kernel lands it takes the rest of the range.
+ * out->tier is the tier that finished the check.
  * Errors: EINVAL (NULL or malformed graph), ETOOBIG (n > max_pis or more
  * than 65535 value slots), ENOMEM, ECUDA, EJIT, EDEVICE_WAIT, ETIMEOUT. */
 int lec_es_check(lec_es_ctx *c, const lec_es_miter *m, lec_es_result *out);
@@ -228,6 +233,29 @@ void lec_es_plan_free(lec_es_ctx *c, lec_es_plan *p);
  * Errors: EINVAL if the range is empty or outside the cone's words. */
 int lec_es_truth_tables(lec_es_ctx *c, const lec_es_miter *m, uint64_t word_begin,
                         uint64_t word_end, uint32_t *vars_out, uint64_t *host_out);
+
+/* Per-node values from a chosen kernel tier, for checking the kernels that
+ * carry the work node by node (paper §3.3: every register of the
+ * instruction stream holds one node's value over the current patterns).
+ * Same row layout as lec_es_truth_tables:
+ *   tier       LEC_ES_TIER_SPILL: the chunk interpreter (lec_es_truth_tables);
+ *              LEC_ES_TIER_INTERP: the word interpreter with its value slots
+ *              in shared memory, a store after every AND record (all rows);
+ *              LEC_ES_TIER_JIT: the specialised kernel in the layout it runs
+ *              in (its dump variant: the same generated code plus a store of
+ *              every 3-input table's value where the layout computes it,
+ *              built for this call; the context's kernel is built first if
+ *              it holds none) -- the rows of the nodes the tables compute;
+ *   vars_out   host, cone_ands entries: row j's AND variable (ascending);
+ *   row_valid  host, cone_ands bytes, or NULL: 1 where row j was written;
+ *   host_out   host, cone_ands x (word_end - word_begin) words; JIT rows
+ *              that no table computes are zero.
+ * The JIT dump holds tables x 2^max(n-5, 5) x 4 bytes of the arena during
+ * the call.  Errors: EINVAL (bad tier, empty range or outside the cone's
+ * words), ETOOBIG (INTERP: the live set does not fit shared memory),
+ * ENOMEM, ECUDA, EJIT. */
+int lec_es_truth_tables_ex(lec_es_ctx *c, const lec_es_miter *m, uint64_t word_begin, uint64_t word_end,
+                           uint32_t tier, uint32_t *vars_out, uint8_t *row_valid, uint64_t *host_out);
 
 /* For callers that cannot allocate device memory (a framework's caching
  * allocator owns it all, or a service may not allocate after start-up).
@@ -297,10 +325,13 @@ void lec_es_batch_free(lec_es_ctx *c, lec_es_batch_plan *b);
  * §3.3, like lec_es_check) and return a ticket at once; requests that
  * arrive while others run are admitted as device memory and result slots
  * free up, and their kernels overlap on the GPU (continuous batching).  The
- * miter is compiled (or its cone copied) before the call returns, so the
- * caller may free m at once.  The result, identical to lec_es_check on m,
- * comes from lec_es_poll / lec_es_wait.  Thread-safe.
- * Errors: EINVAL, ETOOBIG, ENOMEM (queue full). */
+ * miter's output cone is copied before the call returns (so the caller may
+ * free m at once) and compiled by the server's front-end threads.  The
+ * result, identical to lec_es_check on m, comes from lec_es_poll /
+ * lec_es_wait.  Thread-safe.
+ * Errors: EINVAL (malformed cone), ETOOBIG (n > max_pis), ENOMEM; an error
+ * the front end finds later (more than 65535 value slots) is returned by
+ * lec_es_poll / lec_es_wait for the ticket. */
 int lec_es_submit(lec_es_ctx *c, const lec_es_miter *m, uint64_t *ticket);
 /* EBUSY while the request runs; OK and *out once done (the ticket is then
  * released); ECANCELLED if cancelled; ENOTFOUND for an unknown ticket. */
@@ -416,7 +447,11 @@ typedef struct {
   double jit_compile_ms;    /* predicted build time (0 if the context holds the kernel) */
   double paper_cpu_s;       /* the paper's one-core CPU model: 0.0003 s * gates * 2^(n-23) */
   uint32_t gates, n, num_luts;
-  uint32_t tier;            /* tier an AUTO run picks (LEC_ES_TIER_*) */
+  uint32_t tier;            /* tier an AUTO check starts on (LEC_ES_TIER_*): the kernel only
+                               if the context holds it; a cone whose kernel would pay off
+                               but is not built starts on the interpreter while the kernel
+                               builds in the background, and the check's result reports
+                               LEC_ES_TIER_JIT if the kernel took over */
   uint32_t gpu_offload;     /* the paper's rule: 1 if paper_cpu_s / cpu_threads > 0.1 s */
   uint32_t pad;
 } lec_es_cost;

@@ -13,6 +13,12 @@ with gcc on first use (``build()``).
 Parity status of each function is pinned by ``tests/test_oracle_pins.py``
 (brute force, integer closed forms, named identities, mutants confirmed by
 evaluating both netlists directly, a closed-form counterexample).
+
+``cpu_es_blocked`` (``cpu_es_blocked.c``, its own library) is not the oracle
+but a CPU exact-simulation baseline in the paper's CPU setting (an
+instruction stream over reference-counted value rows, 2^14 patterns per pass
+and thread, all host threads); the benchmark times it beside the oracle, and
+``tests/test_oracle_pins.py`` pins it to the oracle.
 """
 from __future__ import annotations
 
@@ -28,6 +34,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "es_oracle.c")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "libes_oracle.so")
+CPU_ES_SRC = os.path.join(HERE, "cpu_es_blocked.c")
+CPU_ES_LIB = os.path.join(BUILD_DIR, "libcpu_es_blocked.so")
 
 NONE = (1 << 64) - 1
 _lock = threading.Lock()
@@ -38,12 +46,14 @@ _u64p = ctypes.POINTER(ctypes.c_uint64)
 
 
 def build(force: bool = False) -> str:
-    """Compile es_oracle.c with gcc (plain -O2, no vectorisation flags)."""
+    """Compile es_oracle.c with gcc (plain -O2, no vectorisation flags), and
+    the CPU-ES baseline (-O3, portable x86-64 code, pthreads)."""
     os.makedirs(BUILD_DIR, exist_ok=True)
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, SRC])
-        os.replace(tmp, LIB)
+    for src, lib, flags in ((SRC, LIB, ["-O2"]), (CPU_ES_SRC, CPU_ES_LIB, ["-O3", "-pthread"])):
+        if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+            tmp = lib + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc"] + flags + ["-std=c11", "-shared", "-fPIC", "-o", tmp, src])
+            os.replace(tmp, lib)
     return LIB
 
 
@@ -64,6 +74,37 @@ def _load() -> ctypes.CDLL:
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
+
+
+_cpu_es: Optional[ctypes.CDLL] = None
+
+
+def _load_cpu_es() -> ctypes.CDLL:
+    global _cpu_es
+    with _lock:
+        if _cpu_es is None:
+            build()
+            lib = ctypes.CDLL(CPU_ES_LIB)
+            lib.cpu_es_blocked.argtypes = [ctypes.c_uint32, ctypes.c_uint32, _u32p, ctypes.c_uint32,
+                                           ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                           _u64p, _u32p]
+            lib.cpu_es_blocked.restype = ctypes.c_int
+            _cpu_es = lib
+    return _cpu_es
+
+
+def cpu_es_blocked(num_pis: int, fanins, out_lit: int, word_begin: int = 0, word_end: int = NONE,
+                   block_words: int = 256, threads: Optional[int] = None) -> Tuple[Optional[int], int]:
+    """CPU-ES baseline (not the oracle): lowest failing pattern over the word
+    range or None, and n.  block_words = 256 is the paper's 2^14 patterns
+    per pass; threads defaults to every host thread."""
+    f = _arr32(fanins)
+    first = ctypes.c_uint64()
+    n = ctypes.c_uint32()
+    t = threads or (os.cpu_count() or 1)
+    _check(_load_cpu_es().cpu_es_blocked(num_pis, len(f) // 2, _p32(f), out_lit, word_begin, word_end,
+                                         block_words, t, ctypes.byref(first), ctypes.byref(n)))
+    return (None if first.value == NONE else int(first.value)), int(n.value)
 
 
 def _arr32(x) -> np.ndarray:

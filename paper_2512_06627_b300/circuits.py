@@ -851,6 +851,74 @@ class ProductBitMiters:
         raise RuntimeError("no observable mutant")
 
 
+def build_four_multiplier_miter(w: int) -> Aig:
+    """The four w x w multipliers of build_golden_revised_multipliers (array,
+    Booth, and their re-synthesized copies) mitered together: the OR of the
+    array-vs-copy, Booth-vs-copy and array-vs-Booth miters over all 2w
+    product bits, one output whose cone holds all four multipliers."""
+    g, a, b = _two_operand_builder(w)
+    outs = {}
+    for name, style, kind in (("A", "plain", "array"), ("B", "plain", "booth"),
+                              ("A*", "alt", "array"), ("B*", "alt", "booth")):
+        g.new_scope()
+        g.style = style
+        outs[name] = array_multiplier(g, a, b) if kind == "array" else booth_multiplier(g, a, b)
+    g.style = "plain"
+    g.new_scope()
+    out = g.or_tree([miter_outputs(g, outs["A"], outs["A*"]), miter_outputs(g, outs["B"], outs["B*"]),
+                     miter_outputs(g, outs["A"], outs["B"])])
+    return g.finish([out], side_outputs=outs)
+
+
+def config4_spread(num: int = 4096, seed: int = 4, min_support: int = 10, max_support: int = 28,
+                   mutant_frac: float = 0.02) -> List[Tuple[Aig, int, str]]:
+    """The batched workload at its stated spread: ``num`` miters of
+    ``min_support``..``max_support`` PIs, from node pairs up to whole
+    multiplier miters.  Sources (all seeded):
+      pair      node-pair miters (as config4_pairs) from the w x w
+                four-multiplier graphs, w = 32 and 14..10, whose joint
+                support has at least min_support PIs (~2% mutated);
+      bit       product-bit miters of w x w array vs Booth, w = 5..14,
+                every product bit whose support has at least min_support
+                PIs, 1 in 50 a seeded Booth-side mutant;
+      revised   whole array (and Booth) multipliers against their
+                re-synthesized copies, w = 5..14;
+      four      the four w x w multipliers mitered together, w = 5..14.
+    Every bit, revised and four miter is kept (the heavy end); the node
+    pairs fill the rest by a seeded sample.  Returns (aig, out_lit, source)
+    triples; many share one aig."""
+    heavy: List[Tuple[Aig, int, str]] = []
+    pm = ProductBitMiters(seed=seed)
+    rng = Xoshiro256ss(seed ^ 0x5EED5)
+    for w in range(min_support // 2, max_support // 2 + 1):
+        masks = support_masks(pm.base(w))
+        for bit in range(2 * w):
+            mut = rng.below(50) == 0
+            if bin(masks[pm.base(w).outputs[bit] >> 1]).count("1") < min_support:
+                continue  # a low product bit: too few PIs
+            aig, out = pm.miter(w, bit, mut, mutant_seed=bit)
+            heavy.append((aig, out, "bit"))
+        for kind in ("array", "booth"):
+            r = build_revised_pair(w, kind)
+            heavy.append((r, r.outputs[0], "revised"))
+        f = build_four_multiplier_miter(w)
+        heavy.append((f, f.outputs[0], "four"))
+    pairs: List[Tuple[Aig, int, str]] = []
+    for w in (32, 14, 13, 12, 11, 10):
+        pb = config4_pairs(num_pairs=1 << 30, w=w, max_support=max_support, seed=seed + w,
+                           mutant_frac=mutant_frac)
+        pairs += [(pb.aig, pb.aig.outputs[j], "pair") for j, n in enumerate(pb.support_sizes)
+                  if n >= min_support]
+    want = max(0, num - len(heavy))
+    if len(pairs) > want:
+        idx = list(range(len(pairs)))
+        for i in range(want):  # partial Fisher-Yates
+            j = i + rng.below(len(idx) - i)
+            idx[i], idx[j] = idx[j], idx[i]
+        pairs = [pairs[i] for i in sorted(idx[:want])]
+    return heavy + pairs
+
+
 # ----------------------------------------------------------------------------
 # AIGER I/O (format of Biere's AIGER 1.9 documentation, combinational subset)
 # ----------------------------------------------------------------------------

@@ -377,6 +377,10 @@ int plan_prepare(lec_es_ctx *c, const lec_es_miter *m, const lec_es_options *opt
   return rc;
 }
 
+// Set by lec_es_check_ex around its AUTO prepare: a cold kernel is then
+// not built synchronously (see check_race).
+thread_local bool t_check_race = false;
+
 // Device side of a plan for an already compiled program.
 int plan_prepare_program(lec_es_ctx *c, Program &&prog, const lec_es_options *opt, lec_es_plan **out) {
   *out = nullptr;
@@ -394,7 +398,12 @@ int plan_prepare_program(lec_es_ctx *c, Program &&prog, const lec_es_options *op
   const uint64_t chunks = num_chunks(g.n);
   uint32_t want = opt ? opt->tier : LEC_ES_TIER_AUTO;
   if (g.slots_elided) want = LEC_ES_TIER_JIT;  // the front end found this cone's kernel for this run
-  if (want == LEC_ES_TIER_AUTO) want = jit_auto_tier(c, g, chunks);
+  if (want == LEC_ES_TIER_AUTO) {
+    want = jit_auto_tier(c, g, chunks);
+    // a one-off check does not wait for a kernel build: it races the
+    // interpreter against a background build instead (check_race)
+    if (want == LEC_ES_TIER_JIT && t_check_race && !jit_held(c, g)) want = LEC_ES_TIER_INTERP;
+  }
   const double tj = now_ms();
   if (want == LEC_ES_TIER_JIT) {
     rc = jit_prepare(c, p.get(), opt);
@@ -624,14 +633,102 @@ extern "C" void lec_es_plan_free(lec_es_ctx *c, lec_es_plan *p) {
   plan_release(c, p);
 }
 
+namespace lec {
+
+// A check the AUTO tier sends to the interpreter while its cone could run
+// as a specialised kernel that the context does not hold yet: the kernel's
+// build is scheduled in the background at once, and the interpreter runs
+// the word range in ascending slices of about kRaceSliceMs each.  A slice
+// that fails ends the check (its counterexample is the lowest: every lower
+// word has passed); once the kernel lands, the rest of the range goes to it.
+// So a cold check takes about the lesser of the interpreter's time and the
+// build's plus the kernel's on what is left, and the next check of the cone
+// finds the kernel built.  Worth it only where a build can pay off.
+constexpr double kRaceMinMs = 20.0;     // predicted interpreter time below this: no race
+constexpr double kRaceSliceMs = 20.0;
+
+bool race_wanted(lec_es_ctx *c, const lec_es_plan *p, const lec_es_options *opt) {
+  if (opt && (opt->tier != LEC_ES_TIER_AUTO || opt->grid_blocks || opt->block_threads || opt->flags)) return false;
+  if (p->tier == LEC_ES_TIER_JIT || !jit_eligible(p->prog) || jit_held(c, p->prog)) return false;
+  const Program &g = p->prog;
+  const uint64_t W = num_words(g.n);
+  uint64_t wb = opt ? opt->word_begin : 0, we = opt ? std::min<uint64_t>(opt->word_end, W) : W;
+  if (wb >= we) return false;
+  const double t = cost_run_ms(c, LEC_ES_TIER_INTERP, g.cone_ands, g.n) * (double)(we - wb) / (double)W;
+  return t >= kRaceMinMs;
+}
+
+int check_race(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt, lec_es_result *out) {
+  const Program &g = p->prog;
+  const uint64_t W = num_words(g.n);
+  const uint64_t wb = opt ? opt->word_begin : 0, we = opt ? std::min<uint64_t>(opt->word_end, W) : W;
+  const double t_int = std::max(1e-3, cost_run_ms(c, LEC_ES_TIER_INTERP, g.cone_ands, g.n));
+  const uint64_t slice = std::max<uint64_t>(1u << 16, (uint64_t)((double)W * kRaceSliceMs / t_int));
+  jit_lookup_or_schedule(c, g, true);
+  lec_es_options o{};
+  o.tier = LEC_ES_TIER_AUTO;
+  double dev_ms = 0;
+  uint64_t w = wb, cex = UINT64_MAX;
+  uint32_t tier = p->tier;
+  int rc = LEC_ES_OK;
+  lec_es_result r{};
+  while (w < we && cex == UINT64_MAX) {
+    if (jit_lookup_or_schedule(c, g, true)) {  // the kernel has landed: it takes the rest
+      lec_es_plan *jp = nullptr;
+      lec_es_options oj{};
+      oj.tier = LEC_ES_TIER_JIT;
+      oj.word_begin = w;
+      oj.word_end = we;
+      Program copy = g;
+      rc = plan_prepare_program(c, std::move(copy), &oj, &jp);
+      if (!rc) rc = plan_run_async(c, jp, &oj);
+      if (!rc) rc = plan_result(c, jp, &r);
+      if (jp) lec_es_plan_free(c, jp);
+      if (rc) return rc;
+      dev_ms += r.device_ms;
+      cex = r.cex;
+      tier = LEC_ES_TIER_JIT;
+      w = we;
+      break;
+    }
+    o.word_begin = w;
+    o.word_end = std::min(we, w + slice);
+    rc = plan_run_async(c, p, &o);
+    if (!rc) rc = plan_result(c, p, &r);
+    if (rc) return rc;
+    dev_ms += r.device_ms;
+    cex = r.cex;
+    w = o.word_end;
+  }
+  fill_result(p, out);
+  out->tier = tier;
+  out->cex = cex;
+  out->words_checked = we - wb;
+  out->device_ms = dev_ms;
+  if (cex != UINT64_MAX) out->verdict = LEC_ES_NONEQUIVALENT;
+  else if (wb == 0 && we >= W) out->verdict = LEC_ES_EQUIVALENT;
+  else out->verdict = LEC_ES_UNDECIDED;
+  return LEC_ES_OK;
+}
+
+}  // namespace lec
+
 extern "C" int lec_es_check_ex(lec_es_ctx *c, const lec_es_miter *m, const lec_es_options *opt,
                                lec_es_result *out) {
   if (!c || !m || !out) return LEC_ES_EINVAL;
   lec_es_plan *p = nullptr;
+  const bool auto_tier = !opt || (opt->tier == LEC_ES_TIER_AUTO && !opt->grid_blocks && !opt->block_threads &&
+                                  !opt->flags);
+  t_check_race = auto_tier;
   int rc = lec_es_prepare(c, m, opt, &p);
+  t_check_race = false;
   if (rc) return rc;
-  rc = plan_run_async(c, p, opt);
-  if (!rc) rc = plan_result(c, p, out);
+  if (race_wanted(c, p, opt)) {
+    rc = check_race(c, p, opt, out);
+  } else {
+    rc = plan_run_async(c, p, opt);
+    if (!rc) rc = plan_result(c, p, out);
+  }
   lec_es_plan_free(c, p);
   return rc;
 }
@@ -734,6 +831,106 @@ extern "C" int lec_es_truth_tables(lec_es_ctx *c, const lec_es_miter *m, uint64_
   if (err || !sync_ok) return LEC_ES_ECUDA;
   if (status & DEV_WAIT_TIMEOUT) return LEC_ES_EDEVICE_WAIT;
   return status ? LEC_ES_ECUDA : LEC_ES_OK;
+}
+
+// Per-node values from a chosen kernel tier: SPILL the chunk interpreter
+// (lec_es_truth_tables), INTERP the word interpreter es_interp_w with a
+// store per AND record, JIT the specialised kernel's dump variant (its
+// tables' nodes only; jit_dump_tables).
+extern "C" int lec_es_truth_tables_ex(lec_es_ctx *c, const lec_es_miter *m, uint64_t word_begin, uint64_t word_end,
+                                      uint32_t tier, uint32_t *vars_out, uint8_t *row_valid, uint64_t *host_out) {
+  if (!c || !m || !vars_out || !host_out) return LEC_ES_EINVAL;
+  if (tier != LEC_ES_TIER_SPILL && tier != LEC_ES_TIER_INTERP && tier != LEC_ES_TIER_JIT) return LEC_ES_EINVAL;
+  Program g;
+  MiterView v{m->num_pis, m->num_ands, m->fanins, m->out_lit};
+  int rc = compile_program(v, LEC_ES_ORDER_AUTO, c->max_pis, g);
+  if (rc) return rc;
+  const uint64_t W = num_words(g.n);
+  if (word_begin >= word_end || word_end > W) return LEC_ES_EINVAL;
+  if (tier == LEC_ES_TIER_SPILL) {
+    rc = lec_es_truth_tables(c, m, word_begin, word_end, vars_out, host_out);
+    if (!rc && row_valid) memset(row_valid, 1, g.cone_ands);
+    return rc;
+  }
+  const uint64_t nw = word_end - word_begin;
+  std::vector<uint32_t> sorted(g.order_vars);
+  std::sort(sorted.begin(), sorted.end());
+  for (size_t j = 0; j < sorted.size(); j++) vars_out[j] = sorted[j];
+  std::vector<uint8_t> valid(g.cone_ands, 0);
+  if (tier == LEC_ES_TIER_JIT) {
+    memset(host_out, 0, (size_t)g.cone_ands * nw * 8u);
+    rc = jit_dump_tables(c, g, word_begin, word_end, host_out, valid.data());
+    if (rc) return rc;
+    if (row_valid) memcpy(row_valid, valid.data(), valid.size());
+    return LEC_ES_OK;
+  }
+  PlanGeom geom{};
+  if (!choose_word_geometry(c, g, nullptr, geom)) return LEC_ES_ETOOBIG;  // slots beyond shared memory
+  std::vector<XRec> xr;
+  std::vector<XLoad> xl;
+  uint32_t out_off = 0;
+  encode_w(g, geom.block, xr, xl, out_off);
+  for (size_t j = 0; j < xr.size(); j++) {  // the j-th AND record computes order_vars[j]
+    const uint32_t row = (uint32_t)(std::lower_bound(sorted.begin(), sorted.end(), g.order_vars[j]) - sorted.begin());
+    xr[j].ctl |= (row + 1u) << 2;
+  }
+  const size_t out_bytes = (size_t)g.cone_ands * nw * 8u;
+  cudaSetDevice(c->device);
+  void *d_recs = c->arena.alloc(std::max<size_t>(16, xr.size() * sizeof(XRec)));
+  void *d_loads = c->arena.alloc(std::max<size_t>(16, xl.size() * sizeof(XLoad)));
+  void *d_out = c->arena.alloc(std::max<size_t>(out_bytes, 8));
+  unsigned long long *d_res = (unsigned long long *)c->arena.alloc(kResWords * 8);
+  auto cleanup = [&]() {
+    c->arena.free(d_recs);
+    c->arena.free(d_loads);
+    c->arena.free(d_out);
+    c->arena.free(d_res);
+  };
+  if (!d_recs || !d_loads || !d_out || !d_res) {
+    cleanup();
+    return LEC_ES_ENOMEM;
+  }
+  cudaStream_t st = c->stream;
+  cudaError_t e = cudaSuccess;
+  if (!xr.empty()) e = cudaMemcpyAsync(d_recs, xr.data(), xr.size() * sizeof(XRec), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !xl.empty())
+    e = cudaMemcpyAsync(d_loads, xl.data(), xl.size() * sizeof(XLoad), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_out, 0, std::max<size_t>(out_bytes, 8), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_res, c->h_init, kResWords * 8, cudaMemcpyHostToDevice, st);
+  int err = e == cudaSuccess ? 0 : 1;
+  if (!err) {
+    XParams xp{};
+    xp.recs = (const XRec *)d_recs;
+    xp.loads = (const XLoad *)d_loads;
+    xp.nrec = geom.nrec_padded;
+    xp.nload = (uint32_t)xl.size();
+    xp.out_off = out_off;
+    xp.out_compl = g.out_compl;
+    xp.n = g.n;
+    xp.ring_recs = geom.ring_recs;
+    xp.resident = geom.resident;
+    xp.word_begin = word_begin;
+    xp.word_end = word_end;
+    xp.cex = d_res + 4;  // never lowered: the dump variant reports nothing
+    xp.evaluated = d_res + 1;
+    xp.status = (uint32_t *)(d_res + 2);
+    xp.tt_out = (uint64_t *)d_out;
+    xp.tt_words = nw;
+    err = launch_interp_w_tt(xp, geom.block, geom.grid, geom.smem, st);
+  }
+  uint32_t status = 0;
+  if (!err) {
+    e = cudaMemcpyAsync(host_out, d_out, out_bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, d_res + 2, 4, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) err = 1;
+  }
+  const bool sync_ok = cudaStreamSynchronize(st) == cudaSuccess;
+  cleanup();
+  if (err || !sync_ok) return LEC_ES_ECUDA;
+  if (status & DEV_WAIT_TIMEOUT) return LEC_ES_EDEVICE_WAIT;
+  if (status) return LEC_ES_ECUDA;
+  if (row_valid) memset(row_valid, 1, g.cone_ands);
+  return LEC_ES_OK;
 }
 
 // ---- LOP3 peak microbenchmark ------------------------------------------------------

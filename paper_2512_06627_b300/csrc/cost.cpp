@@ -322,6 +322,10 @@ extern "C" int lec_es_cost_predict(lec_es_ctx *c, const lec_es_miter *m, uint32_
   out->jit_ms = cost_run_ms(c, LEC_ES_TIER_JIT, g.cone_ands, g.n, c ? jit_held_lop3(c, g) : 0.0);
   out->jit_compile_ms = g.lut.elided ? 0.0 : cost_compile_ms(c, g.lut.count);
   out->tier = jit_auto_tier(c, g, num_chunks(g.n));
+  // an AUTO check never waits for a build: a cone whose kernel the context
+  // does not hold starts on the interpreter (and may hand the rest of its
+  // range to the kernel once the background build lands)
+  if (out->tier == LEC_ES_TIER_JIT && c && !jit_held(c, g)) out->tier = LEC_ES_TIER_INTERP;
   // the paper's one-core CPU model and its GPU-offload rule (§3.2): ES goes
   // to the GPU when its predicted time on the given CPU threads exceeds 0.1 s
   out->paper_cpu_s = 0.0003 * cost_x(g.cone_ands, g.n);

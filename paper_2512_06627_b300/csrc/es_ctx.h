@@ -66,6 +66,7 @@ struct JitKernel {
   uint64_t pass_bits = 0;       // chunk-index bits of the pass PIs (0: contiguous grabs of 32 * rep chunks)
   uint32_t chunk_bits = 0;      // bits of the chunk index (support PIs - 5)
   uint64_t hash2 = 0;           // the program's second structure hash (checked on every cache hit)
+  uint32_t built_regs = 0, built_plan = 0;  // budgets of the layout it was generated with (PTX form)
 };
 struct JitState;
 struct Server;
@@ -139,10 +140,19 @@ int jit_launch(lec_es_ctx *c, lec_es_plan *p, uint64_t chunk_begin, uint64_t chu
                uint64_t max_grabs);
 // Non-blocking lookup for the server: the compiled kernel if ready, else
 // schedules a background compile (once per program) and returns nullptr.
-lec::JitKernel *jit_lookup_or_schedule(lec_es_ctx *c, const Program &g);
+// urgent: a single check races the interpreter against this build (it goes
+// to the front of the queue and builds its chain of layouts at once).
+lec::JitKernel *jit_lookup_or_schedule(lec_es_ctx *c, const Program &g, bool urgent = false);
+// Whether g's cone can run as a specialised kernel (a table cover whose live
+// set fits the register file).
+bool jit_eligible(const Program &g);
+// Whether the context holds g's table-form kernel.
+bool jit_held(lec_es_ctx *c, const Program &g);
 int jit_attach(lec_es_ctx *c, lec_es_plan *p, JitKernel *k, const lec_es_options *opt);
 // Cached kernel for a program (compiled on a miss; thread-safe).
 int jit_get_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out, double *compile_ms);
+// Per-table values of g's specialised kernel over words [wb, we) (see jit.cpp).
+int jit_dump_tables(lec_es_ctx *c, const Program &g, uint64_t wb, uint64_t we, uint64_t *rows, uint8_t *valid);
 // KernelProbe callback: the compiled table-form kernel for a program hash,
 // if the context holds one and the caller will run it (arg = JitProbe).
 struct JitProbe {

@@ -73,6 +73,21 @@ struct MiterView {
   uint32_t out_lit;
 };
 
+// A miter's output cone as a self-contained AIG: its support PIs renumbered
+// 1..n in ascending order, its ANDs after them in ascending order, so a
+// request can keep the cone (not the caller's whole graph) until its front
+// end runs.  compile_program on view() gives the program of the original
+// miter (same structure and hashes) except its support, which is `support`.
+struct CompactMiter {
+  uint32_t num_pis = 0;
+  std::vector<uint32_t> fanins;    // 2 literals per AND
+  uint32_t out_lit = 0;
+  std::vector<uint32_t> support;   // original PI index (0-based) of compact PI k + 1
+  MiterView view() const { return MiterView{num_pis, (uint32_t)(fanins.size() / 2), fanins.data(), out_lit}; }
+};
+// Errors: EINVAL (malformed cone), ETOOBIG (more than max_pis support PIs).
+int compact_cone(const MiterView &m, uint32_t max_pis, CompactMiter &out);
+
 // Front end.  Returns an lec_es_status code.
 // The program hash depends only on the cone's structure, so it is known right
 // after the cone is extracted.  The table cover only feeds code generation
@@ -167,6 +182,8 @@ struct XParams {
   unsigned long long *cex;
   unsigned long long *evaluated;
   uint32_t *status;
+  uint64_t *tt_out;    // truth-table dump only: rows of tt_words words (see interp_w.cu)
+  uint64_t tt_words;
 };
 struct XMiter {
   uint32_t rec_off, nrec, load_off, nload, out_off, out_compl, n, pad;
@@ -192,6 +209,8 @@ void encode_w(const Program &g, int block, std::vector<XRec> &recs, std::vector<
 size_t interp_w_smem_bytes(uint32_t nslots, uint32_t nrec, int block, uint32_t *ring_recs, uint32_t *resident);
 size_t batch_w_smem_bytes(uint32_t max_slots, int block, uint32_t ring_recs);
 int launch_interp_w(const XParams &p, int block, int grid, size_t smem, void *stream);
+// The same kernel with per-record truth-table stores (interp_w.cu, TTSink).
+int launch_interp_w_tt(const XParams &p, int block, int grid, size_t smem, void *stream);
 int configure_batch_w(int block, size_t smem);
 int batch_w_blocks_per_sm(int block, size_t smem);
 int launch_batch_w(const XBatchParams &p, int block, int grid, size_t smem, void *stream);

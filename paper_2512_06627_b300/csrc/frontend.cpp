@@ -500,6 +500,36 @@ void elided_program(uint32_t n, const uint32_t *support, uint32_t cone_ands, uin
 }
 }  // namespace
 
+int compact_cone(const MiterView &m, uint32_t max_pis, CompactMiter &out) {
+  thread_local std::vector<uint8_t> mark;
+  thread_local std::vector<int32_t> dense;
+  Cone c;
+  int rc = extract_cone(m, mark, c);
+  if (rc) return rc;
+  if (c.pis.size() > max_pis || c.pis.size() > 63) return LEC_ES_ETOOBIG;
+  ConeIndex ix(c, dense, (uint64_t)m.num_pis + m.num_ands);
+  const uint32_t n = (uint32_t)c.pis.size(), na = (uint32_t)c.ands.size();
+  // value id -> compact variable: ANDs (ids 0..na-1) after the PIs (ids
+  // na..na+n-1), the constant (id na+n) stays 0
+  auto var_of = [&](uint32_t v) -> uint32_t {
+    const int64_t id = ix.vid(v);
+    if (id < (int64_t)na) return n + 1 + (uint32_t)id;
+    if (id < (int64_t)(na + n)) return (uint32_t)(id - na) + 1;
+    return 0;
+  };
+  out.num_pis = n;
+  out.support.resize(n);
+  for (uint32_t k = 0; k < n; k++) out.support[k] = c.pis[k] - 1;
+  out.fanins.resize(2ull * na);
+  for (uint32_t i = 0; i < na; i++) {
+    const uint32_t *f = fanin_of(m, c.ands[i]);
+    out.fanins[2ull * i] = var_of(f[0] >> 1) << 1 | (f[0] & 1u);
+    out.fanins[2ull * i + 1] = var_of(f[1] >> 1) << 1 | (f[1] & 1u);
+  }
+  out.out_lit = var_of(m.out_lit >> 1) << 1 | (m.out_lit & 1u);
+  return LEC_ES_OK;
+}
+
 int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Program &out, const KernelProbe *probe) {
   thread_local std::vector<uint8_t> mark;
   thread_local std::vector<int32_t> dense;

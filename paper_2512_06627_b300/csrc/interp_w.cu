@@ -135,8 +135,25 @@ __device__ __forceinline__ uint2 pick(uint32_t off, uint32_t d, uint2 v, uint2 x
   return off == d ? v : x;
 }
 
-template <int K>
-__device__ __forceinline__ void run_ands_k(const uint4 *r4, uint32_t cnt, uint8_t *S, uint32_t &i) {
+// Truth-table dump (TT = true, lec_es_truth_tables_ex): a record whose ctl
+// carries row + 1 in bits 2..31 also stores its value, as one 64-bit word,
+// at row x tt_words + (w - word_begin) of tt_out (words outside the range
+// are not stored).
+struct TTSink {
+  uint64_t *out;
+  uint64_t words, wb, w;
+};
+
+template <bool TT>
+__device__ __forceinline__ void tt_store(const TTSink &k, uint32_t ctl, uint2 v) {
+  if (!TT) return;
+  const uint32_t row = ctl >> 2;
+  if (row && k.w >= k.wb && k.w - k.wb < k.words)
+    k.out[(uint64_t)(row - 1) * k.words + (k.w - k.wb)] = (uint64_t)v.y << 32 | v.x;
+}
+
+template <int K, bool TT>
+__device__ __forceinline__ void run_ands_k(const uint4 *r4, uint32_t cnt, uint8_t *S, uint32_t &i, const TTSink &tk) {
   uint4 r[K];
 #pragma unroll
   for (int j = 0; j < K; j++) r[j] = r4[i + j];  // broadcast reads
@@ -158,6 +175,7 @@ __device__ __forceinline__ void run_ands_k(const uint4 *r4, uint32_t cnt, uint8_
         y[j] = pick(r[j].y, r[q].z, v[q], y[j]);
       }
       v[j] = and_w(x[j], y[j], r[j].w);
+      tt_store<TT>(tk, r[j].w, v[j]);
     }
 #pragma unroll
     for (int j = 0; j < K; j++) *reinterpret_cast<uint2 *>(S + r[j].z) = v[j];
@@ -166,21 +184,26 @@ __device__ __forceinline__ void run_ands_k(const uint4 *r4, uint32_t cnt, uint8_
   }
 }
 
-__device__ __forceinline__ void run_ands(const XRec *rr, uint32_t cnt, uint8_t *S) {
+template <bool TT>
+__device__ __forceinline__ void run_ands(const XRec *rr, uint32_t cnt, uint8_t *S, const TTSink &tk) {
   const uint4 *r4 = reinterpret_cast<const uint4 *>(rr);
   uint32_t i = 0;
-  if (cnt >= (uint32_t)kStep) run_ands_k<kStep>(r4, cnt, S, i);
+  if (cnt >= (uint32_t)kStep) run_ands_k<kStep, TT>(r4, cnt, S, i, tk);
   for (; i < cnt; i++) {
     const uint4 r = r4[i];
-    *reinterpret_cast<uint2 *>(S + r.z) = and_w(ld_slot(S, r.x), ld_slot(S, r.y), r.w);
+    const uint2 v = and_w(ld_slot(S, r.x), ld_slot(S, r.y), r.w);
+    *reinterpret_cast<uint2 *>(S + r.z) = v;
+    tt_store<TT>(tk, r.w, v);
   }
 }
 
 // Execute one staged block of records [base, base + cnt) of the program,
 // applying each load exactly before the record it precedes (a PI may take a
 // slot an earlier record has just freed).  li is the next load (updated).
+template <bool TT = false>
 __device__ __forceinline__ void run_block(const XRec *rr, uint32_t base, uint32_t cnt, const XLoad *loads,
-                                          uint32_t nload, uint32_t &li, uint8_t *S, uint64_t w) {
+                                          uint32_t nload, uint32_t &li, uint8_t *S, uint64_t w,
+                                          const TTSink &tk = TTSink{}) {
   uint32_t i = 0;
   for (;;) {
     while (li < nload && loads[li].at <= base + i) {
@@ -191,7 +214,7 @@ __device__ __forceinline__ void run_block(const XRec *rr, uint32_t base, uint32_
     if (i >= cnt) break;
     uint32_t stop = cnt;
     if (li < nload && loads[li].at < base + cnt) stop = loads[li].at - base;
-    run_ands(rr + i, stop - i, S);
+    run_ands<TT>(rr + i, stop - i, S, tk);
     i = stop;
   }
 }
@@ -210,7 +233,7 @@ __device__ __forceinline__ void report(uint2 out, uint64_t w, bool valid, unsign
     atomicMin(cex, (unsigned long long)(w * 64ull + (uint64_t)(__ffsll((long long)o) - 1)));
 }
 
-template <int T>
+template <int T, bool TT = false>
 __global__ void __launch_bounds__(T) es_interp_w(const XParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
@@ -246,9 +269,10 @@ __global__ void __launch_bounds__(T) es_interp_w(const XParams p) {
     __syncthreads();
     if (w0 * 64ull >= *bcast) break;  // block-uniform early exit
     const uint64_t w = w0 + t;
+    const TTSink tk{p.tt_out, p.tt_words, p.word_begin, w};
     uint32_t li = 0;
     if (p.resident) {
-      run_block(ring, 0, p.nrec, p.loads, p.nload, li, S, w);
+      run_block<TT>(ring, 0, p.nrec, p.loads, p.nload, li, S, w, tk);
     } else {
       for (uint32_t k = 0; k < nch && k < (uint32_t)NSTAGE; k++) {
         if (t == 0) {
@@ -269,7 +293,8 @@ __global__ void __launch_bounds__(T) es_interp_w(const XParams p) {
         parity ^= 1u << s;
         inflight &= ~(1u << s);
         const uint32_t off = k * p.ring_recs;
-        run_block(ring + (size_t)s * p.ring_recs, off, min(p.ring_recs, p.nrec - off), p.loads, p.nload, li, S, w);
+        run_block<TT>(ring + (size_t)s * p.ring_recs, off, min(p.ring_recs, p.nrec - off), p.loads, p.nload, li, S, w,
+                      tk);
         __syncthreads();
         if (k + NSTAGE < nch) {
           if (t == 0) {
@@ -294,7 +319,7 @@ __global__ void __launch_bounds__(T) es_interp_w(const XParams p) {
     uint2 out = *reinterpret_cast<const uint2 *>(S + p.out_off);
     out.x = (out.x ^ oc) & vm.x;
     out.y = (out.y ^ oc) & vm.y;
-    report(out, w, w < p.word_end, p.cex);
+    if (!TT) report(out, w, w < p.word_end, p.cex);  // a dump checks nothing, so nothing exits early
     done += (unsigned long long)min((uint64_t)T, p.word_end - w0);
     __syncthreads();
   }
@@ -422,11 +447,11 @@ __global__ void __launch_bounds__(T) es_batch_w(const XBatchParams p) {
   }
 }
 
-template <int T>
+template <int T, bool TT = false>
 int launch_w(const XParams &p, int grid, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(es_interp_w<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(es_interp_w<T, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
-  es_interp_w<T><<<grid, T, smem, st>>>(p);
+  es_interp_w<T, TT><<<grid, T, smem, st>>>(p);
   return (int)cudaGetLastError();
 }
 
@@ -457,6 +482,17 @@ int launch_interp_w(const XParams &p, int block, int grid, size_t smem, void *st
     case 64: return launch_w<64>(p, grid, smem, st);
     case 128: return launch_w<128>(p, grid, smem, st);
     case 256: return launch_w<256>(p, grid, smem, st);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
+
+int launch_interp_w_tt(const XParams &p, int block, int grid, size_t smem, void *stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (block) {
+    case 32: return launch_w<32, true>(p, grid, smem, st);
+    case 64: return launch_w<64, true>(p, grid, smem, st);
+    case 128: return launch_w<128, true>(p, grid, smem, st);
+    case 256: return launch_w<256, true>(p, grid, smem, st);
     default: return (int)cudaErrorInvalidValue;
   }
 }

@@ -46,6 +46,7 @@
 #include <thread>
 #include <map>
 #include <mutex>
+#include <set>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -59,11 +60,14 @@ struct JitState {
   std::mutex mu;
   std::map<uint64_t, JitKernel *> cache;  // by cache_key; an entry serves a program only if hash2 matches too
   std::vector<JitKernel *> unshared;      // built for a program whose key another program holds
-  // background compiles for the server
+  // background compiles (the server, and a single check racing the
+  // interpreter against its kernel's build); inflight: scheduled and not
+  // finished (jit_get_kernel waits for those instead of building twice)
   std::map<uint64_t, bool> scheduled;
+  std::set<uint64_t> inflight;
   std::vector<std::thread> workers;
-  std::deque<Program> todo;
-  std::condition_variable cv;
+  std::deque<std::pair<Program, bool>> todo;  // (program, build its chain of layouts at once)
+  std::condition_variable cv, built;
   bool stop = false;
 };
 
@@ -299,7 +303,8 @@ uint32_t shared_slots() {
 
 std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, uint32_t reg_budget,
                         uint32_t plan_budget, uint64_t pass_pis, const std::vector<uint64_t> &groups,
-                        SlotSplit *split = nullptr, double *lop3_per_pass = nullptr);
+                        SlotSplit *split = nullptr, double *lop3_per_pass = nullptr,
+                        std::vector<uint64_t> *dump_clear = nullptr);
 
 // Passes per grab (a power of two), the hoisting budget and the pass PIs of
 // a table-form kernel.  Long grabs amortise hoisted tables (and the
@@ -538,12 +543,27 @@ std::vector<BitRun> bit_runs(const std::vector<uint32_t> &pos) {  // pos ascendi
 // at the end of its range or when its grab's lowest pattern is not below
 // the current counterexample; it also stops after max_grabs grabs.  Within
 // a grab the counterexample (in %d12 as the first chunk it rules out) is
-// re-polled at each iteration of the innermost loop, and a loop iteration
-// or pass that starts at or above it is skipped: every chunk of it is
-// higher, so none can be the lowest failing one.
+// re-polled at each iteration of the innermost loop, and a loop iteration,
+// unrolled copy or pass that starts at or above it is skipped: every chunk
+// of it is higher, so none can be the lowest failing one.  Branches whose
+// predicate depends only on warp-uniform values (grab, loop, range and skip
+// tests) are emitted as bra.uni; the lane-dependent ones (which lane
+// reports a failure) stay bra.
+//
+// Dump variant (dump_clear non-null; a diagnostic, never cached): the same
+// kernel with one extra parameter, a buffer of 32-bit values, row i for
+// table lp.order[i] with stride 2^max(n-5, 5) chunks.  Every table's value
+// is stored where this layout computes it -- once per grab, per loop
+// iteration, per unrolled copy or per pass -- at the chunk index of that
+// site plus the lane (the chunk bits of deeper pass PIs zero); constant
+// tables are stored at grab level.  (*dump_clear)[i] receives those cleared
+// chunk bits, so table i's value at chunk c is row i at c & ~clear.  The
+// dump variant reports no counterexample (its cex word stays "none"), so no
+// early exit skips a site.
 std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, uint32_t reg_budget,
                         uint32_t plan_budget, uint64_t pass_pis, const std::vector<uint64_t> &groups,
-                        SlotSplit *split, double *lop3_per_pass) {
+                        SlotSplit *split, double *lop3_per_pass, std::vector<uint64_t> *dump_clear) {
+  const bool dump = dump_clear != nullptr;
   const LutProgram &lp = g.lut;
   const uint32_t NA = lp.na, NP = lp.np;
   const size_t NV = NA + NP + 1;
@@ -690,13 +710,15 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   char buf[192];
   s << ".version 9.0\n.target sm_" << major << minor << "a\n.address_size 64\n\n"
     << ".visible .entry es_jit(.param .u64 p_cb, .param .u64 p_ce, .param .u64 p_cex, .param .u64 p_ev,\n"
-    << "    .param .u64 p_next, .param .u64 p_maxg, .param .u64 p_rep, .param .u64 p_q0, .param .u64 p_qend)\n"
+    << "    .param .u64 p_next, .param .u64 p_maxg, .param .u64 p_rep, .param .u64 p_q0, .param .u64 p_qend"
+    << (dump ? ", .param .u64 p_tt" : "") << ")\n"
     << ".maxntid " << kJitBlock << ", 1, 1\n{\n"
     << "  .reg .pred %p<16>;\n  .reg .b32 %t<26>;\n  .reg .b64 %d<40>;\n  .reg .b32 %j<" << L << ">;\n"
     << "  .reg .b64 %o<" << L << ">;\n"
     << "  .reg .b32 %v<" << (NA + 1) << ">;\n  .reg .b32 %s<" << (NA + 1) << ">;\n  .reg .b32 %q<" << (NP + 1)
     << ">;\n";
   if (nsmem) s << "  .shared .align 16 .b32 hs[" << nsmem * kJitBlock << "];\n";
+  if (dump) s << "  .reg .b32 %z<2>;\n  ld.param.u64 %d38, [p_tt];\n  cvta.to.global.u64 %d38, %d38;\n";
   // parameters; grab range [d8, d9); lane; first grab; first counterexample poll
   s << "  ld.param.u64 %d1, [p_cb];\n  ld.param.u64 %d2, [p_ce];\n  ld.param.u64 %d3, [p_cex];\n"
        "  ld.param.u64 %d4, [p_ev];\n  ld.param.u64 %d5, [p_next];\n  ld.param.u64 %d6, [p_maxg];\n"
@@ -754,6 +776,29 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
              x0.c_str(), l.tt);
     s << buf;
   };
+  // dump variant: store table i's value (a register, its complement, or an
+  // immediate) at row i, chunk site + off + lane; clear(lv) = chunk bits of
+  // the pass PIs of levels deeper than lv
+  const uint64_t dump_stride = 1ull << std::max<uint32_t>(g.n > 5 ? g.n - 5 : 0, 5);
+  if (dump) dump_clear->assign(NL, 0);
+  auto clear_below = [&](uint32_t lv) {
+    uint64_t m = 0;
+    for (uint32_t l = lv; l < L; l++) m |= grp[l];
+    return m >> 5;
+  };
+  auto dump_store = [&](size_t i, const std::string &site, uint64_t off, const std::string &val, bool imm, bool inv,
+                        uint32_t lv) {
+    if (!dump) return;
+    (*dump_clear)[i] = clear_below(lv);
+    snprintf(buf, sizeof(buf),
+             "  add.u64 %%d39, %s, %llu;\n  add.u64 %%d39, %%d39, %%d18;\n  shl.b64 %%d39, %%d39, 2;\n"
+             "  add.u64 %%d39, %%d39, %%d38;\n",
+             site.c_str(), (unsigned long long)(i * dump_stride + off));
+    s << buf;
+    if (imm) s << "  mov.b32 %z0, " << val << ";\n";
+    else if (inv) s << "  not.b32 %z0, " << val << ";\n";
+    s << "  st.global.b32 [%d39], " << (imm || inv ? std::string("%z0") : val) << ";\n";
+  };
   // scatter the bits of a 64-bit source register into chunk positions (runs
   // of consecutive positions): dst = sum over runs of field << position
   auto emit_deposit = [&](const char *dst, const char *src, const std::vector<uint32_t> &pos) {
@@ -768,9 +813,9 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   };
   // grab loop: d14 grab number, d15 its lowest chunk (the grab bits of q)
   s << "$LOOP:\n"
-       "  add.u64 %d14, %d8, %d11;\n  setp.ge.u64 %p2, %d14, %d9;\n  @%p2 bra $DONE;\n";
+       "  add.u64 %d14, %d8, %d11;\n  setp.ge.u64 %p2, %d14, %d9;\n  @%p2 bra.uni $DONE;\n";
   emit_deposit("%d15", "%d14", gpos);
-  s << "  max.u64 %d20, %d15, %d1;\n  setp.ge.u64 %p2, %d20, %d12;\n  @%p2 bra $DONE;\n"
+  s << "  max.u64 %d20, %d15, %d1;\n  setp.ge.u64 %p2, %d20, %d12;\n  @%p2 bra.uni $DONE;\n"
        "  setp.lt.u64 %p3, %d13, %d6;\n  and.pred %p4, %p15, %p3;\n  mov.u64 %d16, -1;\n"
        "  @%p4 atom.global.add.u64 %d16, [%d5], 1;\n" << (stride_ok ? "  @%p14 add.u64 %d16, %d11, %d36;\n" : "")
     << "  mov.u64 %d17, 0;\n"
@@ -804,12 +849,18 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     name[v] = "%s" + std::to_string(v);
     loaded[v] = 1;
   };
+  // pass loops 1..NLOOP ($LV, index j<l>, first chunk of the iteration
+  // o<l>); without unrolling the innermost level L is the pass loop ($PASS)
+  const uint32_t NLOOP = U > 0 ? Lr : L - 1;
+  std::string stubs;  // out-of-line skip paths, emitted after the kernel's ret
   auto emit_level = [&](uint8_t lv) {
     std::fill(loaded.begin(), loaded.end(), (uint8_t)0);
+    const std::string site = lv == 0 ? std::string("%d15") : lv <= NLOOP ? "%o" + std::to_string(lv) : "%d27";
     for (size_t i = 0; i < lp.order.size(); i++) {
       if (level[i] != lv || isconst[lp.order[i].node]) continue;
       for (int k = 0; k < lp.order[i].n; k++) load_shared(lp.order[i].leaf[k], lv);
       emit_table(lp.order[i]);
+      dump_store(i, site, 0, name[lp.order[i].node], false, false, lv);
       if (smem_slot[i] >= 0) {
         snprintf(buf, sizeof(buf), "  st.shared.b32 [%%t21+%u], %%v%d;\n", (uint32_t)smem_slot[i] * kJitBlock * 4u,
                  lp.order[i].node);
@@ -817,16 +868,12 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
       }
     }
   };
-  // pass loops 1..NLOOP ($LV, index j<l>, first chunk of the iteration
-  // o<l>); without unrolling the innermost level L is the pass loop ($PASS)
-  const uint32_t NLOOP = U > 0 ? Lr : L - 1;
-  std::string stubs;  // out-of-line skip paths, emitted after the kernel's ret
   auto close_loops = [&]() {  // loop ends of the outer pass loops, innermost first
     std::string c;
     for (uint32_t l = NLOOP; l >= 1; l--) {
       const std::string j = "%j" + std::to_string(l);
       c += "$LE" + std::to_string(l) + ":\n  add.u32 " + j + ", " + j + ", 1;\n  setp.lt.u32 %p9, " + j + ", " +
-           std::to_string(1u << __builtin_popcountll(grp[l - 1])) + ";\n  @%p9 bra $LV" + std::to_string(l) + ";\n";
+           std::to_string(1u << __builtin_popcountll(grp[l - 1])) + ";\n  @%p9 bra.uni $LV" + std::to_string(l) + ";\n";
     }
     return c;
   };
@@ -838,6 +885,12 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     }
   };
   emit_level(0);
+  if (dump)
+    for (size_t i = 0; i < lp.order.size(); i++)
+      if (isconst[lp.order[i].node]) {
+        snprintf(buf, sizeof(buf), "0x%08x", cval[lp.order[i].node]);
+        dump_store(i, "%d15", 0, buf, true, false, 0);
+      }
   for (uint32_t l = 1; l <= NLOOP; l++) {
     const std::string j = "%j" + std::to_string(l);
     s << "  mov.u32 " << j << ", 0;\n$LV" << l << ":\n  cvt.u64.u32 %d32, " << j << ";\n";
@@ -846,9 +899,9 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     if (l == NLOOP) s << kCexRefresh;
     // an iteration whose first chunk is not below the counterexample is
     // skipped, and so are the later ones (they start higher)
-    s << "  setp.ge.u64 %p9, %o" << l << ", %d12;\n  @%p9 bra $SKL" << l << ";\n";
+    s << "  setp.ge.u64 %p9, %o" << l << ", %d12;\n  @%p9 bra.uni $SKL" << l << ";\n";
     stubs += "$SKL" + std::to_string(l) + ":\n  @%p12 sub.u64 %d10, %d10, " +
-             std::to_string((uint64_t)REP / (uint64_t)runs[l]) + ";\n  bra $LE" + std::to_string(l) + ";\n";
+             std::to_string((uint64_t)REP / (uint64_t)runs[l]) + ";\n  bra.uni $LE" + std::to_string(l) + ";\n";
     emit_pass_pis(grp[l - 1], j.c_str());
     emit_level((uint8_t)l);
   }
@@ -881,6 +934,7 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     std::vector<SVal> sv(NV);
     std::vector<int8_t> pic(NP, -1);  // pass PIs fixed in the current copy: 0 or 1
     uint32_t ncopy = 0;                // pass copies emitted (label numbers)
+    uint32_t nouter = 0;               // checked copies of outer unrolled levels (label numbers)
     unrolled_lop3 = 0;
     auto value = [&](int32_t v, uint8_t lv) -> SVal {  // a leaf's value in the current copy
       SVal x;
@@ -965,6 +1019,12 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
       }
       sv[l.node] = res;
     };
+    auto dump_spec = [&](size_t i, uint64_t o, uint32_t lv) {  // a copy's value of table i (dump variant)
+      const SVal &r = sv[lp.order[i].node];
+      char imm[16];
+      snprintf(imm, sizeof(imm), "0x%08x", r.imm_v);
+      dump_store(i, base, o, r.imm ? std::string(imm) : r.reg, r.imm, r.inv, lv);
+    };
     auto unrolled = [&](auto &&self, uint32_t lv, uint64_t off) -> void {
       std::vector<uint32_t> pis;  // this level's pass PIs in rank order (ascending)
       for (uint32_t k = 10; k < NP; k++)
@@ -977,27 +1037,49 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
         }
         const std::vector<SVal> saved = sv;
         if (lv < L) {
+          // a copy that starts at or above the counterexample's chunk
+          // (o >= %t23) skips its tables and every pass below it; the
+          // first copy (o = off) starts where its parent does, checked there
+          const bool chk = o != off && o <= 0xFFFFFFFEull;
+          const std::string U = std::to_string(nouter);
+          if (chk) {
+            nouter++;
+            s << "  setp.le.u32 %p9, %t23, " << o << ";\n  @%p9 bra.uni $UK" << U << ";\n";
+            stubs += "$UK" + U + ":\n  @%p12 sub.u64 %d10, %d10, " +
+                     std::to_string((uint64_t)REP / (uint64_t)runs[lv]) + ";\n  bra.uni $UE" + U + ";\n";
+          }
           std::fill(loaded.begin(), loaded.end(), (uint8_t)0);
           for (size_t i = 0; i < lp.order.size(); i++)
-            if (level[i] == lv && !isconst[lp.order[i].node]) emit_spec(lp.order[i], (uint8_t)lv);
+            if (level[i] == lv && !isconst[lp.order[i].node]) {
+              emit_spec(lp.order[i], (uint8_t)lv);
+              dump_spec(i, o, lv);
+            }
           self(self, lv + 1, o);
+          if (chk) s << "$UE" << U << ":\n";
         } else {  // a pass: its range work, its tables, its output check
           const std::string J = std::to_string(ncopy++);
           const std::string chunk = "  add.u64 %d27, " + base + ", " + std::to_string(o) + ";\n";
-          // a pass whose first chunk is not below the counterexample is
-          // skipped (the first copy of a loop iteration was checked with it)
-          const bool checked = o != 0 || NLOOP == 0;
-          if (checked) {
-            s << chunk << "  setp.ge.u64 %p9, %d27, %d12;\n  @%p9 bra $SKP" << J << ";\n";
-            stubs += "$SKP" + J + ":\n  @%p12 sub.u64 %d10, %d10, 1;\n  bra $NX" + J + ";\n";
+          // a pass whose first chunk (base + o) is not below the
+          // counterexample's is skipped: o >= %t23 = min(cex chunk - base,
+          // 2^32 - 1); the first copy (o = off) starts where its parent
+          // copy does, checked there
+          const bool wide = o > 0xFFFFFFFEull;
+          if (o != off) {
+            if (wide) s << chunk << "  setp.ge.u64 %p9, %d27, %d12;\n";
+            else s << "  setp.le.u32 %p9, %t23, " << o << ";\n";
+            s << "  @%p9 bra.uni $SKP" << J << ";\n";
+            stubs += "$SKP" + J + ":\n  @%p12 sub.u64 %d10, %d10, 1;\n  bra.uni $NX" + J + ";\n";
           }
-          s << "  @%p12 bra $PB" << J << ";\n" << (checked ? std::string() : chunk)
-            << "  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra $NX" << J
-            << ";\n  add.u64 %d22, %d27, 32;\n  setp.le.u64 %p10, %d22, %d1;\n  @%p10 bra $NX" << J
+          s << "  @%p12 bra.uni $PB" << J << ";\n" << (o != off && wide ? std::string() : chunk)
+            << "  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra.uni $NX" << J
+            << ";\n  add.u64 %d22, %d27, 32;\n  setp.le.u64 %p10, %d22, %d1;\n  @%p10 bra.uni $NX" << J
             << ";\n  add.u64 %d19, %d27, %d18;\n$PB" << J << ":\n";
           std::fill(loaded.begin(), loaded.end(), (uint8_t)0);
           for (size_t i = 0; i < lp.order.size(); i++)
-            if (level[i] == L && !isconst[lp.order[i].node]) emit_spec(lp.order[i], (uint8_t)L);
+            if (level[i] == L && !isconst[lp.order[i].node]) {
+              emit_spec(lp.order[i], (uint8_t)L);
+              dump_spec(i, o, L);
+            }
           const SVal out = value(lp.root < 0 ? -1 : (int32_t)lp.root, (uint8_t)L);
           const uint32_t outc = g.out_compl ? 0xFFFFFFFFu : 0u;
           const bool never = out.imm && ((out.imm_v ^ outc) & vmask) == 0;
@@ -1021,7 +1103,7 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
               << "  add.u64 %d19, %d27, %d18;\n"
                  "  neg.s32 %t11, %t7;\n  and.b32 %t11, %t11, %t7;\n  bfind.u32 %t12, %t11;\n"
                  "  cvt.u64.u32 %d21, %t12;\n  shl.b64 %d22, %d19, 5;\n  add.u64 %d22, %d22, %d21;\n"
-                 "  atom.global.min.u64 %d23, [%d3], %d22;\n";
+              << (dump ? "" : "  atom.global.min.u64 %d23, [%d3], %d22;\n");
           }
           s << "$NX" << J << ":\n";
         }
@@ -1029,15 +1111,18 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
         for (uint32_t r = 0; r < pis.size(); r++) pic[pis[r]] = -1;
       }
     };
+    // %t23: the counterexample's chunk minus base, at most 2^32 - 1 (base is
+    // below it here: the innermost loop's iteration, or the grab, was checked)
+    s << "  sub.u64 %d33, %d12, " << base << ";\n  min.u64 %d33, %d33, 4294967295;\n  cvt.u32.u64 %t23, %d33;\n";
     unrolled(unrolled, Lr + 1, 0);
   } else {
     s << "  mov.u32 %t20, 0;\n$PASS:\n";
     if (NLOOP == 0) s << kCexRefresh;
     emit_chunk();
-    s << "  setp.ge.u64 %p9, %d27, %d12;\n  @%p9 bra $SKPP;\n  @%p12 bra $PBODY;\n";
-    stubs += "$SKPP:\n  @%p12 sub.u64 %d10, %d10, 1;\n  bra $NEXTPASS;\n";
-    s << "  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra " << (L > 1 ? "$NEXTPASS" : "$GRABEND") << ";\n"
-      << "  add.u64 %d22, %d27, 32;\n  setp.le.u64 %p10, %d22, %d1;\n  @%p10 bra $NEXTPASS;\n"
+    s << "  setp.ge.u64 %p9, %d27, %d12;\n  @%p9 bra.uni $SKPP;\n  @%p12 bra.uni $PBODY;\n";
+    stubs += "$SKPP:\n  @%p12 sub.u64 %d10, %d10, 1;\n  bra.uni $NEXTPASS;\n";
+    s << "  setp.ge.u64 %p9, %d27, %d2;\n  @%p9 bra.uni " << (L > 1 ? "$NEXTPASS" : "$GRABEND") << ";\n"
+      << "  add.u64 %d22, %d27, 32;\n  setp.le.u64 %p10, %d22, %d1;\n  @%p10 bra.uni $NEXTPASS;\n"
          "  add.u64 %d19, %d27, %d18;\n$PBODY:\n";
     emit_pass_pis(grp[L - 1], "%t20");
     emit_level((uint8_t)L);
@@ -1057,10 +1142,10 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     emit_chunk();  // a failing pass (rare) recomputes its chunk
     s << "  add.u64 %d19, %d27, %d18;\n"
          "  neg.s32 %t11, %t7;\n  and.b32 %t11, %t11, %t7;\n  bfind.u32 %t12, %t11;\n"
-         "  cvt.u64.u32 %d21, %t12;\n  shl.b64 %d22, %d19, 5;\n  add.u64 %d22, %d22, %d21;\n"
-         "  atom.global.min.u64 %d23, [%d3], %d22;\n"
-         "$NEXTPASS:\n"
-         "  add.u32 %t20, %t20, 1;\n  setp.lt.u32 %p9, %t20, " + std::to_string(1u << __builtin_popcountll(grp[L - 1])) + ";\n  @%p9 bra $PASS;\n";
+         "  cvt.u64.u32 %d21, %t12;\n  shl.b64 %d22, %d19, 5;\n  add.u64 %d22, %d22, %d21;\n";
+    if (!dump) s << "  atom.global.min.u64 %d23, [%d3], %d22;\n";
+    s << "$NEXTPASS:\n"
+         "  add.u32 %t20, %t20, 1;\n  setp.lt.u32 %p9, %t20, " + std::to_string(1u << __builtin_popcountll(grp[L - 1])) + ";\n  @%p9 bra.uni $PASS;\n";
   }
   s << close_loops() + "  @%p12 add.u64 %d10, %d10, " + std::to_string(REP) + ";\n"
        "$GRABEND:\n"
@@ -1146,10 +1231,15 @@ int compile_cubin(const std::string &src, int major, int minor, std::vector<char
 
 // The table form goes straight to PTX and the PTX compiler; the AND form
 // goes through NVRTC.
+// built (optional) receives the register and plan budgets of the layout the
+// returned kernel was generated with (the dump variant reuses them).
 int compile_program_kernel(const Program &g, bool lut_form, int major, int minor, std::vector<char> &cubin,
-                           std::string &log, const GrabLayout *layout = nullptr, double *lop3_per_pass = nullptr) {
+                           std::string &log, const GrabLayout *layout = nullptr, double *lop3_per_pass = nullptr,
+                           uint32_t *built = nullptr) {
   double per_sink = 0;
+  uint32_t built_sink[2];
   if (!lop3_per_pass) lop3_per_pass = &per_sink;
+  if (!built) built = built_sink;
   *lop3_per_pass = 0;
   // LEC_ES_JIT_NVRTC=1 compiles the table form from CUDA C++ through NVRTC
   // instead (same tables, for comparing the two compilation paths)
@@ -1184,6 +1274,8 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
       if (!t_single_build) {
         std::string lg;
         SlotSplit split;
+        built[0] = regs;
+        built[1] = plan;
         const int rc = compile_ptx(gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis,
                                                layout->groups, &split, lop3_per_pass),
                                    major, minor, cubin, lg);
@@ -1195,12 +1287,14 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
       }
       std::vector<std::string> ptx;
       std::vector<double> pers;
+      std::vector<std::pair<uint32_t, uint32_t>> budgets;
       for (uint32_t i = 0; i < kMaxChain; i++) {
         SlotSplit split;
         double per = 0;
         ptx.push_back(
             gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis, layout->groups, &split, &per));
         pers.push_back(per);
+        budgets.emplace_back(regs, plan);
         if (plan == 0) break;
         next_layout(split);
       }
@@ -1236,6 +1330,8 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
           log += logs[i];
           cubin = std::move(bins[i]);
           *lop3_per_pass = pers[i];
+          built[0] = budgets[i].first;
+          built[1] = budgets[i].second;
           if (rcs[i] != LEC_ES_OK || !spilled(logs[i]) || plan == 0) return rcs[i];
         }
       }
@@ -1244,6 +1340,8 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
     for (;;) {
       std::string lg;
       SlotSplit split;
+      built[0] = regs;
+      built[1] = plan;
       const int rc = compile_ptx(gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis,
                                              layout->groups, &split, lop3_per_pass),
                                  major, minor, cubin, lg);
@@ -1325,6 +1423,15 @@ double jit_held_lop3(lec_es_ctx *c, const Program &g) {
   return k ? k->lop3_per_pass : 0.0;
 }
 
+bool jit_eligible(const Program &g) { return g.lut.count > 0 && !g.lut.order.empty() && g.lut.live <= kMaxJitLive; }
+
+bool jit_held(lec_es_ctx *c, const Program &g) {
+  if (g.lut.elided) return true;
+  JitState *js = state(c);
+  std::lock_guard<std::mutex> lk(js->mu);
+  return cached_kernel(js, g, true) != nullptr;
+}
+
 // The ES time model (cost.cpp) decides: the specialised kernel when its
 // predicted time, plus the predicted build time unless this context already
 // holds the kernel, is below the interpreter's.  Cones whose table live set
@@ -1372,11 +1479,12 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   }
   double nvrtc_ms = 0;
   double lop3_per_pass = 0;  // of the PTX form's kernel (a sidecar file next to a cached cubin)
+  uint32_t budgets[2] = {lay.regs, lay.plan};  // register and plan budgets it was generated with
   if (path.empty() || !read_file(path, cubin)) {
     std::string log;
     const double tn = now_ms();
     int rc = compile_program_kernel(g, lut_form, c->cc_major, c->cc_minor, cubin, log, ptx_form ? &lay : nullptr,
-                                    &lop3_per_pass);
+                                    &lop3_per_pass, budgets);
     nvrtc_ms = now_ms() - tn;
     if (rc) {
       if (getenv("LEC_ES_JIT_LOG")) fprintf(stderr, "lec_es JIT failed:\n%s\n", log.c_str());
@@ -1384,12 +1492,20 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
     }
     if (!path.empty()) {
       write_file(path, cubin);
-      const std::string txt = std::to_string(lop3_per_pass);
+      const std::string txt =
+          std::to_string(lop3_per_pass) + " " + std::to_string(budgets[0]) + " " + std::to_string(budgets[1]);
       write_file(path + ".lop3", std::vector<char>(txt.begin(), txt.end()));
     }
   } else {
     std::vector<char> txt;
-    if (read_file(path + ".lop3", txt)) lop3_per_pass = atof(std::string(txt.begin(), txt.end()).c_str());
+    if (read_file(path + ".lop3", txt)) {
+      const std::string t(txt.begin(), txt.end());
+      double per = 0;
+      unsigned r = budgets[0], pl = budgets[1];
+      if (sscanf(t.c_str(), "%lf %u %u", &per, &r, &pl) >= 1) lop3_per_pass = per;
+      budgets[0] = r;
+      budgets[1] = pl;
+    }
   }
   cudaSetDevice(c->device);
   const double tl = now_ms();
@@ -1417,6 +1533,8 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   k->work_per_chunk = lut_form ? g.lut.count : (uint32_t)g.recs.size();
   k->chunk_bits = g.n > 5 ? g.n - 5 : 0;
   k->hash2 = g.hash2;
+  k->built_regs = budgets[0];
+  k->built_plan = budgets[1];
   if (ptx_form) {  // the PTX form: its grab layout
     k->rep_fixed = lay.rep;
     k->pass_bits = lay.pass_pis >> 5;
@@ -1442,16 +1560,20 @@ void worker_loop(lec_es_ctx *c) {
       std::unique_lock<std::mutex> lk(js->mu);
       js->cv.wait(lk, [&] { return js->stop || !js->todo.empty(); });
       if (js->stop) return;
-      g = std::move(js->todo.front());
+      g = std::move(js->todo.front().first);
+      t_single_build = js->todo.front().second;
       js->todo.pop_front();
     }
     JitKernel *k = nullptr;
     int rc = build_kernel(c, g, true, &k);
+    t_single_build = false;
     std::lock_guard<std::mutex> lk(js->mu);
     if (rc == LEC_ES_OK) {
       if (!js->cache.count(cache_key(g, true))) js->cache[cache_key(g, true)] = k;
       else js->unshared.push_back(k);  // the key is another structure's: never found by lookup
     }
+    js->inflight.erase(cache_key(g, true));
+    js->built.notify_all();
   }
 }
 
@@ -1504,7 +1626,9 @@ int jit_get_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **o
   JitState *js = state(c);
   const uint64_t key = cache_key(g, lut_form);
   {
-    std::lock_guard<std::mutex> lk(js->mu);
+    std::unique_lock<std::mutex> lk(js->mu);
+    // a background build of this program is under way: wait for it
+    js->built.wait(lk, [&] { return !js->inflight.count(key) || js->stop; });
     if (JitKernel *k = cached_kernel(js, g, lut_form)) {
       *out = k;
       if (compile_ms) *compile_ms = 0;
@@ -1555,14 +1679,18 @@ int jit_prepare(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt) {
   return jit_attach(c, p, k, opt);
 }
 
-JitKernel *jit_lookup_or_schedule(lec_es_ctx *c, const Program &g) {
+JitKernel *jit_lookup_or_schedule(lec_es_ctx *c, const Program &g, bool urgent) {
   JitState *js = state(c);
   std::lock_guard<std::mutex> lk(js->mu);
   const uint64_t key = cache_key(g, true);
   if (JitKernel *k = cached_kernel(js, g, true)) return k;
   if (!js->scheduled[key]) {
     js->scheduled[key] = true;
-    js->todo.push_back(g);
+    js->inflight.insert(key);
+    // a single check waiting on it goes first, and builds its chain of
+    // layouts at once (the host is otherwise idle then)
+    if (urgent) js->todo.emplace_front(g, true);
+    else js->todo.emplace_back(g, false);
     if (js->workers.empty()) {
       const unsigned nw = std::max(1u, std::min(4u, std::thread::hardware_concurrency() / 2));
       for (unsigned i = 0; i < nw; i++) js->workers.emplace_back(worker_loop, c);
@@ -1681,6 +1809,91 @@ int jit_launch(lec_es_ctx *c, lec_es_plan *p, uint64_t chunk_begin, uint64_t chu
   return e == cudaSuccess ? 0 : (int)e;
 }
 
+// Per-table values of g's specialised kernel (lec_es_truth_tables_ex, JIT
+// tier).  The context's kernel for g is built first if it holds none; the
+// dump variant is generated with that kernel's layout and budgets, compiled
+// and loaded for this call only, and run over words [wb, we).  rows (host,
+// cone_ands x (we - wb) words) receives the row of every table's node (its
+// dense AND id: rank in ascending variable order) and valid[row] = 1; other
+// rows are left alone.
+int jit_dump_tables(lec_es_ctx *c, const Program &g, uint64_t wb, uint64_t we, uint64_t *rows, uint8_t *valid) {
+  const LutProgram &lp = g.lut;
+  if (lp.elided) return LEC_ES_EINVAL;
+  if (lp.order.empty()) return LEC_ES_OK;
+  JitKernel *k = nullptr;
+  t_single_build = true;
+  int rc = jit_get_kernel(c, g, true, &k, nullptr);
+  t_single_build = false;
+  if (rc) return rc;
+  GrabLayout lay;
+  jit_layout(g, &lay);
+  const bool known = k->built_regs || k->built_plan;
+  std::vector<uint64_t> clear;
+  const std::string ptx = gen_ptx_lut(g, c->cc_major, c->cc_minor, lay.rep, known ? k->built_regs : lay.regs,
+                                      known ? k->built_plan : lay.plan, lay.pass_pis, lay.groups, nullptr, nullptr,
+                                      &clear);
+  std::vector<char> cubin;
+  std::string log;
+  rc = compile_ptx(ptx, c->cc_major, c->cc_minor, cubin, log);
+  if (rc) return rc;
+  cudaSetDevice(c->device);
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t kern = nullptr;
+  if (cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess ||
+      cudaLibraryGetKernel(&kern, lib, "es_jit") != cudaSuccess) {
+    if (lib) cudaLibraryUnload(lib);
+    return LEC_ES_EJIT;
+  }
+  const size_t NT = lp.order.size();
+  const uint64_t NCH = num_chunks(g.n);
+  const uint64_t stride = 1ull << std::max<uint32_t>(g.n > 5 ? g.n - 5 : 0, 5);  // as gen_ptx_lut's
+  const size_t bytes = NT * stride * 4u;
+  void *d_tt = c->arena.alloc(bytes);
+  unsigned long long *d_res = (unsigned long long *)c->arena.alloc(kResWords * 8);
+  std::vector<uint32_t> h;
+  int err = 0;
+  if (!d_tt || !d_res) {
+    err = LEC_ES_ENOMEM;
+  } else {
+    cudaStream_t st = c->stream;
+    uint64_t cb = std::min<uint64_t>(2 * wb, NCH), ce = std::min<uint64_t>(2 * we, NCH);
+    uint64_t rep = lay.rep, q0 = 0, qend = 0, maxg = ~0ull;
+    jit_grab_range(k, rep, cb, ce, &q0, &qend);
+    int bps = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void *)kern, kJitBlock, 0);
+    const unsigned grid = (unsigned)std::max(1, c->sm_count * std::max(1, bps));
+    unsigned long long *cex = d_res, *ev = d_res + 1, *next = d_res + 3;  // a counter: no static stride
+    void *tt = d_tt;
+    void *args[] = {&cb, &ce, &cex, &ev, &next, &maxg, &rep, &q0, &qend, &tt};
+    h.resize(NT * stride);
+    cudaError_t e = cudaMemsetAsync(d_tt, 0, bytes, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_res, c->h_init, kResWords * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaLaunchKernel((const void *)kern, dim3(grid), dim3(kJitBlock), args, 0, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d_tt, bytes, cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess || e != cudaSuccess) err = LEC_ES_ECUDA;
+  }
+  c->arena.free(d_tt);
+  c->arena.free(d_res);
+  cudaLibraryUnload(lib);
+  if (err) return err;
+  // table i's value at chunk c is row i at c with the chunk bits of deeper
+  // pass PIs cleared (where this layout computes it); word w = chunks 2w, 2w+1
+  const uint64_t nw = we - wb;
+  for (size_t i = 0; i < NT; i++) {
+    const uint32_t row = (uint32_t)lp.order[i].node;
+    valid[row] = 1;
+    const uint32_t *src = h.data() + i * stride;
+    for (uint64_t w = wb; w < we; w++) {
+      const uint64_t c0 = 2 * w, c1 = 2 * w + 1;
+      const uint32_t v0 = src[c0 & ~clear[i]];
+      const uint32_t v1 = c1 < NCH ? src[c1 & ~clear[i]] : v0;
+      rows[(uint64_t)row * nw + (w - wb)] = (uint64_t)v1 << 32 | v0;
+    }
+  }
+  return LEC_ES_OK;
+}
+
 void jit_release_all(lec_es_ctx *c) {
   if (!c->jit) return;
   JitState *js = c->jit;
@@ -1689,6 +1902,7 @@ void jit_release_all(lec_es_ctx *c) {
     js->stop = true;
   }
   js->cv.notify_all();
+  js->built.notify_all();
   for (auto &t : js->workers) t.join();
   for (auto &kv : js->cache) {
     if (kv.second->lib) cudaLibraryUnload(kv.second->lib);

@@ -1,8 +1,12 @@
 // server.cpp -- served exact simulation: continuous batching of ES requests.
 //
-// A request is one miter.  lec_es_submit runs the host front end in the
-// caller's thread (cone, support, order, reference-count slots), keeps only
-// the compiled program and returns a ticket.  A dispatcher thread
+// A request is one miter.  lec_es_submit copies the miter's output cone
+// (a self-contained, renumbered AIG of the cone alone) in the caller's
+// thread and returns a ticket; a pool of front-end threads then compiles it
+// (support, order, reference-count slots, table cover) and queues it for
+// admission, so submissions of many small cones are not bound by one host
+// thread.  Errors the front end finds later (too many value slots) are
+// reported by lec_es_poll / lec_es_wait.  A dispatcher thread
 //   * admits queued requests in arrival order while the requests on the GPU
 //     hold less than the slot budget (value slots x resident 64-pattern words
 //     x 8 bytes: the live set a request keeps per word in flight) and fewer
@@ -67,8 +71,9 @@ struct Resident {  // device copy of one program's records (word-wide kernel)
 };
 
 struct Request {
-  enum State { QUEUED, RUNNING, DONE, CANCELLED, FAILED };
+  enum State { PREPARING, QUEUED, RUNNING, DONE, CANCELLED, FAILED };
   uint64_t ticket = 0;
+  CompactMiter cone;  // until the front end has run
   Program prog;
   State state = QUEUED;
   int slot = -1;
@@ -86,8 +91,10 @@ struct Request {
 struct Server {
   lec_es_ctx *c = nullptr;
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
-  std::deque<uint64_t> queue;
+  std::condition_variable cv_work, cv_done, cv_prep;
+  std::deque<uint64_t> prep;   // tickets waiting for the front end
+  std::vector<std::thread> prep_threads;
+  std::deque<uint64_t> queue;  // compiled, waiting for admission
   std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
   std::vector<uint64_t> running;
   std::vector<Slot> slots;
@@ -265,6 +272,52 @@ void retire(Server *s, Request *r) {
   }
 }
 
+// Front-end thread: compiles submitted cones and queues them for admission.
+void prep_worker(Server *s) {
+  lec_es_ctx *c = s->c;
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    s->cv_prep.wait(lk, [&] { return s->stop || !s->prep.empty(); });
+    if (s->stop) return;
+    const uint64_t t = s->prep.front();
+    s->prep.pop_front();
+    auto it = s->reqs.find(t);
+    if (it == s->reqs.end()) continue;
+    Request *r = it->second.get();  // stays put: a preparing request is never collected
+    if (r->cancel) {
+      finish(s, r, Request::CANCELLED);
+      continue;
+    }
+    CompactMiter cone = std::move(r->cone);
+    lk.unlock();
+    const double t0 = now_ms();
+    Program g;
+    int rc;
+    try {
+      JitProbe jp{c, JitProbe::kAuto};
+      const KernelProbe probe{jit_probe, &jp};
+      rc = compile_program(cone.view(), LEC_ES_ORDER_AUTO, c->max_pis, g, &probe);
+      if (!rc) g.support = cone.support;
+    } catch (const std::bad_alloc &) {
+      rc = LEC_ES_ENOMEM;
+    }
+    const double front_ms = now_ms() - t0;
+    lk.lock();
+    r->res.host_ms += front_ms;
+    if (rc) {
+      r->err = rc;
+      finish(s, r, Request::FAILED);
+    } else if (r->cancel) {
+      finish(s, r, Request::CANCELLED);
+    } else {
+      r->prog = std::move(g);
+      r->state = Request::QUEUED;
+      s->queue.push_back(t);
+      s->cv_work.notify_one();
+    }
+  }
+}
+
 void dispatcher(Server *s) {
   lec_es_ctx *c = s->c;
   cudaSetDevice(c->device);
@@ -371,6 +424,8 @@ int ensure_server(lec_es_ctx *c) {
   }
   Server *raw = s.get();
   raw->th = std::thread(dispatcher, raw);
+  const unsigned nprep = std::max(2u, std::min(8u, std::thread::hardware_concurrency() / 2));
+  for (unsigned i = 0; i < nprep; i++) raw->prep_threads.emplace_back(prep_worker, raw);
   c->server = s.release();
   return LEC_ES_OK;
 }
@@ -402,7 +457,9 @@ void server_shutdown(lec_es_ctx *c) {
     }
   }
   s->cv_work.notify_all();
+  s->cv_prep.notify_all();
   if (s->th.joinable()) s->th.join();
+  for (auto &t : s->prep_threads) t.join();
   cudaSetDevice(c->device);
   for (cudaStream_t st : s->streams) {
     cudaStreamSynchronize(st);
@@ -448,9 +505,7 @@ extern "C" int lec_es_submit(lec_es_ctx *c, const lec_es_miter *m, uint64_t *tic
   MiterView v{m->num_pis, m->num_ands, m->fanins, m->out_lit};
   int rc;
   try {
-    JitProbe jp{c, JitProbe::kAuto};
-    const KernelProbe probe{jit_probe, &jp};
-    rc = compile_program(v, LEC_ES_ORDER_AUTO, c->max_pis, r->prog, &probe);
+    rc = compact_cone(v, c->max_pis, r->cone);  // the caller may free m once this returns
   } catch (const std::bad_alloc &) {
     return LEC_ES_ENOMEM;
   }
@@ -460,12 +515,13 @@ extern "C" int lec_es_submit(lec_es_ctx *c, const lec_es_miter *m, uint64_t *tic
   Server *s = server_of(c);
   r->t_submit = t0;
   r->res.host_ms = now_ms() - t0;
+  r->state = Request::PREPARING;
   std::lock_guard<std::mutex> lk(s->mu);
   r->ticket = s->next_ticket++;
   *ticket = r->ticket;
-  s->queue.push_back(r->ticket);
+  s->prep.push_back(r->ticket);
   s->reqs[r->ticket] = std::move(r);
-  s->cv_work.notify_one();
+  s->cv_prep.notify_one();
   return LEC_ES_OK;
 }
 
@@ -475,7 +531,8 @@ int collect(Server *s, uint64_t ticket, lec_es_result *out) {
   auto it = s->reqs.find(ticket);
   if (it == s->reqs.end()) return LEC_ES_ENOTFOUND;
   Request *r = it->second.get();
-  if (r->state == Request::QUEUED || r->state == Request::RUNNING) return LEC_ES_EBUSY;
+  if (r->state == Request::PREPARING || r->state == Request::QUEUED || r->state == Request::RUNNING)
+    return LEC_ES_EBUSY;
   int rc = LEC_ES_OK;
   if (r->state == Request::CANCELLED) rc = LEC_ES_ECANCELLED;
   else if (r->state == Request::FAILED) rc = r->err ? r->err : LEC_ES_ECUDA;
@@ -519,8 +576,8 @@ extern "C" int lec_es_cancel(lec_es_ctx *c, uint64_t ticket) {
   Request *r = it->second.get();
   if (r->state == Request::QUEUED) {
     finish(s, r, Request::CANCELLED);
-  } else if (r->state == Request::RUNNING) {
-    r->cancel = true;
+  } else if (r->state == Request::RUNNING || r->state == Request::PREPARING) {
+    r->cancel = true;  // a preparing request is finished by its front-end thread
   }
   return LEC_ES_OK;
 }

@@ -30,7 +30,7 @@ NO_CEX = (1 << 64) - 1
 EXPORTS = [
     "lec_es_create", "lec_es_destroy", "lec_es_strerror", "lec_es_compile", "lec_es_check",
     "lec_es_check_ex", "lec_es_prepare", "lec_es_run_async", "lec_es_plan_result", "lec_es_plan_info",
-    "lec_es_plan_free", "lec_es_truth_tables", "lec_es_batch", "lec_es_batch_prepare",
+    "lec_es_plan_free", "lec_es_truth_tables", "lec_es_truth_tables_ex", "lec_es_batch", "lec_es_batch_prepare",
     "lec_es_batch_run_async", "lec_es_batch_results", "lec_es_batch_free", "lec_es_submit", "lec_es_poll",
     "lec_es_wait", "lec_es_cancel", "lec_es_server_config", "lec_es_lop3_peak", "lec_es_jit_compile",
     "lec_es_check_noalloc", "lec_es_batch_info", "lec_es_signatures", "lec_es_match_pairs",
@@ -161,6 +161,8 @@ def load() -> ctypes.CDLL:
         "lec_es_wait": ([_P, ctypes.c_uint64, ctypes.c_double, R], ctypes.c_int),
         "lec_es_cancel": ([_P, ctypes.c_uint64], ctypes.c_int),
         "lec_es_server_config": ([_P, ctypes.c_size_t, ctypes.c_uint32], ctypes.c_int),
+        "lec_es_truth_tables_ex": ([_P, M, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _u32p,
+                                    ctypes.POINTER(ctypes.c_uint8), _u64p], ctypes.c_int),
         "lec_es_jit_compile": ([M, ctypes.c_int, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t, _u64p],
                                ctypes.c_int),
         "lec_es_check_noalloc": ([_P, ctypes.c_uint64, ctypes.POINTER(lec_es_program_info), ctypes.c_uint64,
@@ -325,6 +327,23 @@ def lec_es_truth_tables(ctx: Context, m: Miter, word_begin: int, word_end: int):
                                    vars_.ctypes.data_as(_u32p), out.ctypes.data_as(_u64p)),
         "lec_es_truth_tables")
     return vars_[: info.cone_ands], out[: info.cone_ands]
+
+
+def lec_es_truth_tables_ex(ctx: Context, m: Miter, word_begin: int, word_end: int, tier: int):
+    """(vars, (cone_ands, words) uint64 table, row_valid bool array) from the
+    given kernel tier (TIER_SPILL, TIER_INTERP or TIER_JIT)."""
+    info, _ = lec_es_compile(m)
+    nw = word_end - word_begin
+    k = max(1, info.cone_ands)
+    vars_ = np.zeros(k, dtype=np.uint32)
+    valid = np.zeros(k, dtype=np.uint8)
+    out = np.zeros((k, nw), dtype=np.uint64)
+    _ok(load().lec_es_truth_tables_ex(ctx.handle, ctypes.byref(m.c), word_begin, word_end, tier,
+                                      vars_.ctypes.data_as(_u32p), valid.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                      out.ctypes.data_as(_u64p)),
+        "lec_es_truth_tables_ex")
+    n = info.cone_ands
+    return vars_[:n], out[:n], valid[:n].astype(bool)
 
 
 def _miter_array(ms: Sequence[Miter]):

@@ -114,3 +114,35 @@ def test_every_mutated_pair_and_sampled_ranges_of_heavy_pairs_vs_oracle(ctx, pai
         we = min(W, wb + 1024)
         g = L.lec_es_check_ex(ctx, ms[i], L.options(wb, we, L.TIER_JIT))
         assert g.cex_or_none == oracle_cex(pairs.aig, pairs.aig.outputs[i], wb, we), (i, wb, we)
+
+
+def test_spread_batch_equals_single_and_oracle():
+    """The batched workload at its stated spread (10..28 PIs, node pairs up
+    to whole four-multiplier miters): one prepared batch gives every miter's
+    lec_es_check result, and the oracle's -- on every miter of up to 16 PIs,
+    every mutant, and a seeded sample of the rest."""
+    import os
+    from tests.gpu_common import make_ctx
+    ctx = make_ctx()
+    try:
+        trip = C.config4_spread(num=1024, seed=9)
+        flat = {}
+        ms = []
+        for aig, out, _ in trip:
+            f = flat.setdefault(id(aig), aig.flat_fanins())
+            ms.append(L.Miter(aig.num_pis, f, out))
+        got = L.lec_es_batch(ctx, ms)
+        one = [L.lec_es_check(ctx, m) for m in ms]
+        assert [r.cex for r in got] == [r.cex for r in one]
+        rng = np.random.default_rng(33)
+        sample = set(int(x) for x in rng.choice(len(ms), size=10, replace=False))
+        threads = max(4, os.cpu_count() or 4)
+        checked = 0
+        for i, ((aig, out, _), r) in enumerate(zip(trip, got)):
+            if r.support_n <= 16 or r.cex_or_none is not None or i in sample:
+                want = O.check_parallel(aig.num_pis, aig.fanins, out, threads)[0]
+                assert r.cex_or_none == want, i
+                checked += 1
+        assert checked >= 20 and any(r.cex_or_none is not None for r in got)
+    finally:
+        L.lec_es_destroy(ctx)

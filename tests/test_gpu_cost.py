@@ -102,7 +102,10 @@ def test_auto_takes_the_predicted_tier():
             m = L.miter_of(aig)
             p = L.lec_es_cost_predict(c, m, 16)
             r = L.lec_es_check(c, m)
-            assert r.tier == p.tier and r.verdict == L.EQUIVALENT
+            # a cold cone starts on the interpreter; its kernel, built in the
+            # background, may take over the rest of the range
+            assert r.tier == p.tier or (p.tier == L.TIER_INTERP and r.tier == L.TIER_JIT)
+            assert r.verdict == L.EQUIVALENT
         # after its kernel is built the 12x12 miter goes to the kernel
         m = L.miter_of(C.config2_mult12())
         _run(c, m, L.TIER_JIT)

@@ -329,3 +329,43 @@ def test_planted_minterms_16x16_default_layout(ctx):
             assert g.cex_or_none is None
         g = L.lec_es_check_ex(ctx, L.miter_of(mm), L.options(w, w + 1, L.TIER_JIT))
         assert g.cex == p
+
+
+def test_cold_check_races_interpreter_against_kernel_build():
+    """A one-off AUTO check of a cone whose kernel the context does not hold
+    starts on the interpreter (ascending word slices) while the kernel builds
+    in the background.  Results are exact either way: the 16x16 miter is
+    EQUIVALENT, and a planted 16x16 mutant and 30-PI node-pair mutants (where
+    the build lands first and the kernel takes the rest of the range) give
+    the closed-form or oracle counterexample.  Once built, the kernel serves
+    the next check."""
+    import os
+    import time
+    c = make_ctx(arena_bytes=256 << 20)
+    try:
+        m = L.miter_of(C.config3_mult16())
+        r = L.lec_es_check(c, m)
+        assert r.verdict == L.EQUIVALENT and r.tier in (L.TIER_INTERP, L.TIER_JIT)
+        t0 = time.time()
+        while time.time() - t0 < 120:  # the background build lands
+            r = L.lec_es_check(c, m)
+            if r.tier == L.TIER_JIT:
+                break
+            time.sleep(0.2)
+        assert r.tier == L.TIER_JIT and r.verdict == L.EQUIVALENT
+        p = (1 << 31) | 0x5EED
+        mm = C.config3_mult16(minterm=p)
+        assert L.lec_es_check(c, L.miter_of(mm)).cex == p
+        pm = C.ProductBitMiters(seed=5)
+        handed = 0
+        for s in (4, 5, 6):
+            aig, o = pm.miter(15, 22, mutant=True, mutant_seed=s)
+            r = L.lec_es_check(c, L.Miter(aig.num_pis, aig.flat_fanins(), o))
+            want = O.check_parallel(aig.num_pis, aig.fanins, o, max(4, os.cpu_count() or 4))[0]
+            assert r.cex_or_none == want, s
+            handed += r.tier == L.TIER_JIT
+        aig, o = pm.miter(15, 22)
+        r = L.lec_es_check(c, L.Miter(aig.num_pis, aig.flat_fanins(), o))
+        assert r.verdict == L.EQUIVALENT
+    finally:
+        L.lec_es_destroy(c)

@@ -341,3 +341,35 @@ def test_reference_pairs_find_the_equal_sum_bits():
     for lx, ly in zip(x[1:], y[1:]):  # bit 0 is a single XOR (hashed the same way on both sides)
         if (lx >> 1) != (ly >> 1) and (lx & 1) == (ly & 1):
             assert (min(lx, ly) >> 1, max(lx, ly) >> 1) in pairs, (lx, ly)
+
+
+# --- the CPU-ES baseline (reference counting, 2^14 patterns per pass) ------------
+
+@pytest.mark.parametrize("seed", range(20))
+def test_cpu_es_baseline_matches_oracle_random_graphs(seed):
+    """The blocked, reference-counted CPU-ES baseline gives the oracle's
+    lowest counterexample on random graphs (all supports 0..12, blocks that
+    do not divide the words, one to several threads, word ranges)."""
+    rng = np.random.default_rng(7000 + seed)
+    aig = random_aig(rng, int(rng.integers(1, 13)), int(rng.integers(1, 120)))
+    out = aig.outputs[0]
+    n = O.support(aig.num_pis, aig.fanins, out)[0]
+    W = O.num_words(len(n))
+    for block, threads in ((256, 4), (3, 1), (1, 7)):
+        assert O.cpu_es_blocked(aig.num_pis, aig.fanins, out, block_words=block, threads=threads)[0] == \
+            O.check(aig.num_pis, aig.fanins, out)[0]
+    wb, we = sorted(int(x) for x in rng.integers(0, W + 1, 2))
+    assert O.cpu_es_blocked(aig.num_pis, aig.fanins, out, wb, we, 5, 3)[0] == \
+        O.check(aig.num_pis, aig.fanins, out, wb, we)[0]
+
+
+@pytest.mark.parametrize("seed", [None, 1, 2, 3])
+def test_cpu_es_baseline_matches_oracle_12x12(seed):
+    m = C.config2_mult12(mutant_seed=seed)
+    out = m.outputs[0]
+    if seed is None:  # the whole space would take the baseline seconds; a range of it
+        assert O.cpu_es_blocked(m.num_pis, m.fanins, out, 1000, 9000)[0] is None
+    else:
+        assert O.cpu_es_blocked(m.num_pis, m.fanins, out)[0] == O.check(m.num_pis, m.fanins, out)[0]
+    assert O.cpu_es_blocked(C.config1_adders().num_pis, C.config1_adders().fanins,
+                            C.config1_adders().outputs[0]) == (None, 16)
