@@ -135,8 +135,15 @@ void batch_release(lec_es_ctx *c, lec_es_batch_plan *b) {
 
 }  // namespace
 
+namespace {
+// The own-kernel threshold of the batch being prepared (the split search of
+// lec_es_batch_prepare sets it; otherwise kBatchJitMs).
+thread_local double t_split_ms = -1.0;
+}  // namespace
+
 bool lec::batch_wants_kernel(lec_es_ctx *c, uint32_t n, uint32_t cone_ands, uint32_t luts, uint32_t live) {
-  return cost_run_ms(c, LEC_ES_TIER_INTERP, cone_ands, n) >= kBatchJitMs && luts && live <= kBatchJitLive;
+  const double th = t_split_ms >= 0 ? t_split_ms : kBatchJitMs;
+  return cost_run_ms(c, LEC_ES_TIER_INTERP, cone_ands, n) >= th && luts && live <= kBatchJitLive;
 }
 
 namespace {
@@ -474,9 +481,72 @@ int autotune(lec_es_ctx *c, lec_es_batch_plan *b, int grid_override, Layout &bes
 
 }  // namespace
 
+namespace {
+int batch_prepare_one(lec_es_ctx *c, const lec_es_miter *m, size_t k, const lec_es_options *opt,
+                      lec_es_batch_plan **out);
+}  // namespace
+
+// With LEC_ES_FLAG_AUTOTUNE the split between miters that get their own
+// specialised kernel (a node of the CUDA graph each, about 6 us of launch
+// overhead) and miters left to the tile queue is searched too: the batch is
+// prepared for a few own-kernel thresholds on the predicted interpreter
+// time, each replayed and timed, and the fastest is kept.  On the 4,096
+// node pairs the base threshold wins; on a batch of heavier miters (10-28
+// PIs) thousands of own kernels would make the graph launch-bound.
+constexpr double kSplitCandidatesMs[] = {kBatchJitMs, 0.05, 0.12, 0.3};
+
 extern "C" int lec_es_batch_prepare(lec_es_ctx *c, const lec_es_miter *m, size_t k, const lec_es_options *opt,
                                     lec_es_batch_plan **out) {
   if (!c || !m || !out || k == 0 || k > 0xFFFFFFFFull) return LEC_ES_EINVAL;
+  *out = nullptr;
+  const bool interp_only = opt && (opt->tier == LEC_ES_TIER_INTERP || opt->tier == LEC_ES_TIER_SPILL);
+  if (!(opt && (opt->flags & LEC_ES_FLAG_AUTOTUNE)) || interp_only) return batch_prepare_one(c, m, k, opt, out);
+  const double t0 = now_ms();
+  lec_es_batch_plan *best = nullptr;
+  double best_ms = 1e300;
+  double jit_ms = 0;
+  for (double th : kSplitCandidatesMs) {
+    lec_es_batch_plan *b = nullptr;
+    t_split_ms = th;
+    int rc = batch_prepare_one(c, m, k, opt, &b);
+    t_split_ms = -1.0;
+    if (rc) {
+      if (best) lec_es_batch_free(c, best);
+      return rc;
+    }
+    jit_ms += b->jit_ms;
+    double ms = 1e300;
+    for (int r = 0; r < 3 && !rc; r++) {  // the least of three replays
+      const double ts = now_ms();
+      rc = lec_es_batch_run_async(c, b);
+      if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = LEC_ES_ECUDA;
+      ms = std::min(ms, now_ms() - ts);
+    }
+    if (rc) {
+      lec_es_batch_free(c, b);
+      if (best) lec_es_batch_free(c, best);
+      return rc;
+    }
+    const bool no_kernels = b->jit_miters.empty();  // a higher threshold cannot change the split
+    if (ms < best_ms) {
+      if (best) lec_es_batch_free(c, best);
+      best = b;
+      best_ms = ms;
+    } else {
+      lec_es_batch_free(c, b);
+    }
+    if (no_kernels) break;
+  }
+  best->host_ms = now_ms() - t0;
+  best->tune_ms = best->host_ms - jit_ms;
+  best->jit_ms = jit_ms;
+  *out = best;
+  return LEC_ES_OK;
+}
+
+namespace {
+int batch_prepare_one(lec_es_ctx *c, const lec_es_miter *m, size_t k, const lec_es_options *opt,
+                      lec_es_batch_plan **out) {
   *out = nullptr;
   const double t0 = now_ms();
   lec_es_batch_plan *b = new (std::nothrow) lec_es_batch_plan();
@@ -509,6 +579,7 @@ extern "C" int lec_es_batch_prepare(lec_es_ctx *c, const lec_es_miter *m, size_t
   *out = b;
   return LEC_ES_OK;
 }
+}  // namespace
 
 extern "C" int lec_es_batch_info(const lec_es_batch_plan *b, lec_es_batch_layout *info) {
   if (!b || !info) return LEC_ES_EINVAL;

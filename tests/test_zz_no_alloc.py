@@ -47,7 +47,7 @@ def _cases():
     a = C.config2_mult12()
     out.append((a, L.miter_of(a), 12_345, 200_001))  # a partial range, off any alignment
     a = C.config2_mult12(2)
-    out.append((a, L.miter_of(a), 7, 1 << 18))
+    out.append((a, L.miter_of(a), 7, 1 << 18))  # every miter's output is a.outputs[0]
     return out
 
 
@@ -69,7 +69,7 @@ def test_noalloc_matches_check_ex_and_oracle_twice():
             d_recs = torch.from_numpy(host.view(np.int64)).to("cuda")
             d_res = torch.zeros(4, dtype=torch.int64, device="cuda")
             ref = L.lec_es_check_ex(ctx, m, L.options(wb, we, tier=L.TIER_INTERP))
-            want = O.check(aig.num_pis, aig.fanins, m.out_lit, wb, we)[0]
+            want = O.check(aig.num_pis, aig.fanins, aig.outputs[0], wb, we)[0]
             assert ref.cex_or_none == want
             for _ in range(2):
                 L.lec_es_check_noalloc(d_recs.data_ptr(), len(host), info, wb, we, d_res.data_ptr(),
