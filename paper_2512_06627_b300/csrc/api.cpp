@@ -359,7 +359,7 @@ int plan_prepare(lec_es_ctx *c, const lec_es_miter *m, const lec_es_options *opt
   try {
     const uint32_t want = opt ? opt->tier : LEC_ES_TIER_AUTO;
     JitProbe jp{c, want == LEC_ES_TIER_JIT ? JitProbe::kRun : JitProbe::kAuto};
-    const KernelProbe probe{jit_probe, &jp};
+    const KernelProbe probe{jit_probe, &jp, jit_want_cover};
     // the probe finds table-form kernels only
     const bool may_skip = (want == LEC_ES_TIER_JIT || want == LEC_ES_TIER_AUTO) &&
                           !(opt && (opt->flags & LEC_ES_FLAG_JIT_AND_FORM));

@@ -254,7 +254,9 @@ int stage_layout(lec_es_ctx *c, lec_es_batch_plan *b, const Layout &L, int grid_
   b->layout = L;
   b->smem = batch_w_smem_bytes(b->max_slots, L.block, L.ring_recs);
   if (b->smem > (size_t)c->smem_optin) return LEC_ES_ETOOBIG;
-  if (configure_batch_w(L.block, b->smem) != 0) return LEC_ES_ECUDA;
+  // the limit is a property of the kernel function, which the request
+  // server's grouped launches set too: both set the device's maximum
+  if (configure_batch_w(L.block, (size_t)c->smem_optin) != 0) return LEC_ES_ECUDA;
   const int bps = std::max(1, batch_w_blocks_per_sm(L.block, b->smem));
   b->grid = grid_override > 0 ? grid_override : c->sm_count * bps;
   cudaStream_t st = c->stream;

@@ -161,6 +161,10 @@ struct JitProbe {
   Use use;  // kRun: the kernel tier was asked for; kAuto: the AUTO choice; kBatch: the batch's split; kInfo: facts only
 };
 bool jit_probe(void *arg, uint64_t hash, uint64_t hash2, uint32_t n, uint32_t cone_ands, KernelFacts *facts);
+// KernelProbe::want_cover for an AUTO caller: a cone whose interpreter run
+// is predicted below kCoverMinMs never gets a kernel built by AUTO (a build
+// takes tens of milliseconds at least), so it needs no table cover.
+bool jit_want_cover(void *arg, uint32_t n, uint32_t cone_ands);
 // The batch gives a miter its own kernel (else the tile queue).
 bool batch_wants_kernel(lec_es_ctx *c, uint32_t n, uint32_t cone_ands, uint32_t luts, uint32_t live);
 void jit_release_all(lec_es_ctx *c);

@@ -104,6 +104,10 @@ struct KernelFacts {
 struct KernelProbe {
   bool (*have_kernel)(void *arg, uint64_t hash, uint64_t hash2, uint32_t n, uint32_t cone_ands, KernelFacts *facts);
   void *arg;
+  // optional: whether the caller may build this cone's specialised kernel at
+  // all; if not, the table cover (which only feeds code generation, and is
+  // most of the front end's time on small cones) is not built: lut.count = 0
+  bool (*want_cover)(void *arg, uint32_t n, uint32_t cone_ands) = nullptr;
 };
 
 int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Program &out,

@@ -653,7 +653,7 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
   best.hash = chash;
   best.hash2 = chash2;
   best.num_records = (uint32_t)best.recs.size();
-  {
+  if (!probe || !probe->want_cover || probe->want_cover(probe->arg, best.n, best.cone_ands)) {
     // the table cover (independent of the slot order), then its evaluation
     // order, one candidate of which follows the chosen slot order
     LutProgram lp;

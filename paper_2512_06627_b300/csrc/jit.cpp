@@ -1581,6 +1581,13 @@ void worker_loop(lec_es_ctx *c) {
 
 uint64_t cache_key(const Program &g, bool lut_form) { return g.hash ^ (lut_form ? 0x9E3779B97F4A7C15ull : 0ull); }
 
+bool jit_want_cover(void *arg, uint32_t n, uint32_t cone_ands) {
+  const JitProbe *p = (const JitProbe *)arg;
+  if (p->use != JitProbe::kAuto) return true;
+  constexpr double kCoverMinMs = 5.0;
+  return cost_run_ms(p->c, LEC_ES_TIER_INTERP, cone_ands, n) >= kCoverMinMs;
+}
+
 bool jit_probe(void *arg, uint64_t hash, uint64_t hash2, uint32_t n, uint32_t cone_ands, KernelFacts *f) {
   const JitProbe *p = (const JitProbe *)arg;
   lec_es_ctx *c = p->c;
