@@ -348,16 +348,17 @@ def measure_batch(ctx, args):
     }
 
 
-def measure_batch_spread(ctx, args):
+def measure_batch_spread(ctx, args, headline_evals_per_s):
     """The batched workload at its stated spread (circuits.config4_spread):
     4,096 miters of 10..28 PIs, node pairs of five multiplier graphs up to
     whole four-multiplier miters (56..~7.9k cone ANDs), ~2% mutants.  One
     prepared batch (autotuned; CUDA-graph replay) against one launch per
     miter with the same kernel each (back to back with one sync, and with a
     sync per miter), identical results asserted.  Also: the spread, the
-    work-weighted share per support size, and the Amdahl bound of batching
-    (one-launch time over the summed kernel time of the miters whose kernel
-    alone runs for at least 0.2 ms, which batching cannot shorten)."""
+    work-weighted share per support size, and the batch's node-pattern
+    evaluations per second beside the time its work would take at the
+    headline kernel's rate (the 16x16 miter's), a work bound for the
+    batch."""
     import numpy as np
     import torch
     from paper_2512_06627_b300 import circuits as C
@@ -430,7 +431,9 @@ def measure_batch_spread(ctx, args):
         "one_launch_per_miter_sync_miters_per_s": k / s_s,
         "speedup_vs_async": batched / (k / a_s), "speedup_vs_sync": batched / (k / s_s),
         "one_launch_kernel_ms_sum": float(dev.sum()), "kernels_of_0p2ms_or_more_ms": heavy_ms,
-        "amdahl_bound_vs_async": a_s * 1e3 / heavy_ms if heavy_ms > 0 else None,
+        "node_pattern_evals": float(work.sum()),
+        "batched_evals_per_s": float(work.sum()) / statistics.median(ts),
+        "work_at_headline_rate_ms": float(work.sum()) / headline_evals_per_s * 1e3,
         "prepare_s": prep, "jit_compile_s": layout.jit_ms / 1e3,
     }
 
@@ -838,7 +841,7 @@ def run_ours(args, ws, rank, local):
         line["mutant_time_to_verdict"] = measure_mutants(ctx, statistics.median(kern_ms))
     if rank == 0 and not args.no_batch:
         line["batched"] = measure_batch(ctx, args)
-        line["batched_spread"] = measure_batch_spread(ctx, args)
+        line["batched_spread"] = measure_batch_spread(ctx, args, value)
     if rank == 0 and args.serve_requests > 0:
         line["served"] = measure_serve(ctx, args) if args.serve_quick else measure_serve_full(ctx, args)
     if rank == 0 and not args.no_batch:

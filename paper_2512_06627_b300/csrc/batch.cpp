@@ -53,7 +53,7 @@ namespace {
 // 3.89 / 3.84 / 4.05 / 5.12 ms per batch.
 constexpr double kBatchJitMs = 0.02;
 constexpr uint32_t kBatchJitLive = 230;  // table live set that still fits the register file
-constexpr int kMaxBranches = 16;         // parallel graph branches (at most)
+constexpr int kMaxBranches = 64;         // parallel graph branches (at most)
 constexpr int kDefaultBranches = 8;  // 4 / 8 / 16 branches: 3.85 / 3.80 / 3.78 ms on the 4,096-pair batch
 
 struct Layout {
