@@ -333,6 +333,12 @@ void lec_es_batch_free(lec_es_ctx *c, lec_es_batch_plan *b);
  * the front end finds later (more than 65535 value slots) is returned by
  * lec_es_poll / lec_es_wait for the ticket. */
 int lec_es_submit(lec_es_ctx *c, const lec_es_miter *m, uint64_t *ticket);
+/* lec_es_submit for k miters in one call (m[0..k-1], host; they may share
+ * one fanins array): every cone is copied before any request is queued, so
+ * on an error nothing is submitted; tickets (host, k entries) receive the
+ * tickets in order.  Thread-safe.  Errors: as lec_es_submit for any miter;
+ * EINVAL for NULL arrays with k > 0. */
+int lec_es_submit_many(lec_es_ctx *c, const lec_es_miter *m, size_t k, uint64_t *tickets);
 /* EBUSY while the request runs; OK and *out once done (the ticket is then
  * released); ECANCELLED if cancelled; ENOTFOUND for an unknown ticket. */
 int lec_es_poll(lec_es_ctx *c, uint64_t ticket, lec_es_result *out);

@@ -896,6 +896,42 @@ extern "C" int lec_es_submit(lec_es_ctx *c, const lec_es_miter *m, uint64_t *tic
   return LEC_ES_OK;
 }
 
+extern "C" int lec_es_submit_many(lec_es_ctx *c, const lec_es_miter *m, size_t k, uint64_t *tickets) {
+  if (!c || (!m && k) || (!tickets && k)) return LEC_ES_EINVAL;
+  if (k == 0) return LEC_ES_OK;
+  const double t0 = now_ms();
+  // every cone is copied (and checked) before any request is queued, so an
+  // error leaves nothing submitted
+  std::vector<std::unique_ptr<Request>> rs(k);
+  try {
+    for (size_t i = 0; i < k; i++) {
+      rs[i].reset(new Request());
+      MiterView v{m[i].num_pis, m[i].num_ands, m[i].fanins, m[i].out_lit};
+      const int rc = compact_cone(v, c->max_pis, rs[i]->cone);
+      if (rc) return rc;
+    }
+  } catch (const std::bad_alloc &) {
+    return LEC_ES_ENOMEM;
+  }
+  int rc = ensure_server(c);
+  if (rc) return rc;
+  Server *s = server_of(c);
+  const double per = (now_ms() - t0) / (double)k;
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (size_t i = 0; i < k; i++) {
+    Request *r = rs[i].get();
+    r->t_submit = t0;
+    r->res.host_ms = per;
+    r->state = Request::PREPARING;
+    r->ticket = s->next_ticket++;
+    tickets[i] = r->ticket;
+    s->prep.push_back(r->ticket);
+    s->reqs[r->ticket] = std::move(rs[i]);
+  }
+  if (s->prep_waiting > 0) s->cv_prep.notify_all();
+  return LEC_ES_OK;
+}
+
 namespace {
 // Called with s->mu held: result of a finished request (and release).
 int collect(Server *s, uint64_t ticket, lec_es_result *out) {

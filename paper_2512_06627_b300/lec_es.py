@@ -32,7 +32,7 @@ EXPORTS = [
     "lec_es_check_ex", "lec_es_prepare", "lec_es_run_async", "lec_es_plan_result", "lec_es_plan_info",
     "lec_es_plan_free", "lec_es_truth_tables", "lec_es_truth_tables_ex", "lec_es_batch", "lec_es_batch_prepare",
     "lec_es_batch_run_async", "lec_es_batch_results", "lec_es_batch_free", "lec_es_submit", "lec_es_poll",
-    "lec_es_wait", "lec_es_cancel", "lec_es_server_config", "lec_es_lop3_peak", "lec_es_jit_compile",
+    "lec_es_submit_many", "lec_es_wait", "lec_es_cancel", "lec_es_server_config", "lec_es_lop3_peak", "lec_es_jit_compile",
     "lec_es_check_noalloc", "lec_es_batch_info", "lec_es_signatures", "lec_es_match_pairs",
     "lec_es_codegen_version", "lec_es_cost_fit", "lec_es_cost_model", "lec_es_cost_predict", "lec_es_sweep",
 ]
@@ -157,6 +157,7 @@ def load() -> ctypes.CDLL:
         "lec_es_batch_results": ([_P, _P, R, ctypes.c_size_t], ctypes.c_int),
         "lec_es_batch_free": ([_P, _P], None),
         "lec_es_submit": ([_P, M, _u64p], ctypes.c_int),
+        "lec_es_submit_many": ([_P, M, ctypes.c_size_t, _u64p], ctypes.c_int),
         "lec_es_poll": ([_P, ctypes.c_uint64, R], ctypes.c_int),
         "lec_es_wait": ([_P, ctypes.c_uint64, ctypes.c_double, R], ctypes.c_int),
         "lec_es_cancel": ([_P, ctypes.c_uint64], ctypes.c_int),
@@ -396,6 +397,15 @@ def lec_es_submit(ctx: Context, m: Miter) -> int:
     t = ctypes.c_uint64()
     _ok(load().lec_es_submit(ctx.handle, ctypes.byref(m.c), ctypes.byref(t)), "lec_es_submit")
     return int(t.value)
+
+
+def lec_es_submit_many(ctx: Context, ms: Sequence[Miter]) -> List[int]:
+    """Submit many miters in one call; their tickets, in order."""
+    k = len(ms)
+    t = np.zeros(max(1, k), dtype=np.uint64)
+    arr = _miter_array(ms)
+    _ok(load().lec_es_submit_many(ctx.handle, arr, k, t.ctypes.data_as(_u64p)), "lec_es_submit_many")
+    return [int(x) for x in t[:k]]
 
 
 def lec_es_poll(ctx: Context, ticket: int) -> Optional[lec_es_result]:

@@ -143,6 +143,8 @@ def test_submit_copies_the_cone_before_returning():
         got = [L.lec_es_wait(ctx, x, 300.0) for x in ts]
         alone = [L.lec_es_check(ctx, x) for x in ms]
         assert [r.cex for r in got] == [r.cex for r in alone]
+        many = [L.lec_es_wait(ctx, x, 300.0) for x in L.lec_es_submit_many(ctx, ms)]  # one call for all
+        assert [r.cex for r in many] == [r.cex for r in alone]
         assert [list(r.support[: r.support_n]) for r in got] == [list(r.support[: r.support_n]) for r in alone]
         for j in range(0, 512, 37):
             o = pb.aig.outputs[j]
