@@ -841,19 +841,22 @@ def run_ours(args, ws, rank, local):
         "kernel_ms_mean": statistics.mean(kern_ms),
         "prepare_s": prep_s,
         "plan_prepare": ttv,
-        "time_to_verdict": measure_cold(dev),
         "clocks": clocks,
     }
-    if rank == 0:
+    # the single-GPU sub-measurements run once, at N = 1 (a scaling run
+    # measures the step on every rank and nothing else)
+    solo = rank == 0 and ws == 1
+    if solo:
+        line["time_to_verdict"] = measure_cold(dev)
         line["mutant_time_to_verdict"] = measure_mutants(ctx, statistics.median(kern_ms))
-    if rank == 0 and not args.no_batch:
+    if solo and not args.no_batch:
         line["batched"] = measure_batch(ctx, args)
         line["batched_spread"] = measure_batch_spread(ctx, args, value)
-    if rank == 0 and args.serve_requests > 0:
+    if solo and args.serve_requests > 0:
         line["served"] = measure_serve(ctx, args) if args.serve_quick else measure_serve_full(ctx, args)
-    if rank == 0 and not args.no_batch:
+    if solo and not args.no_batch:
         line["sweep"] = measure_sweep(ctx)
-    if rank == 0 and not args.no_cpu_baseline:
+    if solo and not args.no_cpu_baseline:
         rate, cores, sample = cpu_oracle_rate(aig, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "node-pattern evals/s", "cores": cores, "kind": "oracle",
                                 "sample": sample}
