@@ -63,6 +63,13 @@ def test_full_4096_pairs_batch_equals_single(ctx, pairs):
     assert outs[0] == single
     nonequiv = sum(1 for x in single if x != L.NO_CEX)
     assert nonequiv >= sum(pairs.mutated) // 2
+    # every miter against the oracle (its results stored by
+    # tests/golden/make_config4_oracle.py; the fingerprint pins the inputs)
+    import json
+    from tests.golden.make_config4_oracle import OUT, fingerprint
+    stored = json.load(open(OUT))
+    assert stored["fingerprint"] == fingerprint(pairs.aig)
+    assert outs[0] == [L.NO_CEX if x is None else x for x in stored["cex"]]
 
 
 def test_layouts_and_autotune_give_identical_results(ctx, pairs, tmp_path):

@@ -373,3 +373,25 @@ def test_cpu_es_baseline_matches_oracle_12x12(seed):
         assert O.cpu_es_blocked(m.num_pis, m.fanins, out)[0] == O.check(m.num_pis, m.fanins, out)[0]
     assert O.cpu_es_blocked(C.config1_adders().num_pis, C.config1_adders().fanins,
                             C.config1_adders().outputs[0]) == (None, 16)
+
+
+# --- stored oracle values -------------------------------------------------------
+
+def test_stored_node_pair_results_are_current():
+    """The stored per-miter oracle results of the 4,096 node-pair batch
+    (written by tests/golden/make_config4_oracle.py) belong to the graph the
+    generator builds today, and a seeded sample of them (every
+    non-equivalent one of small support, plus equivalent ones) re-checks."""
+    from tests.golden.make_config4_oracle import OUT, fingerprint
+    pb = C.config4_pairs()
+    stored = json.load(open(OUT))
+    assert stored["fingerprint"] == fingerprint(pb.aig)
+    assert len(stored["cex"]) == len(pb.aig.outputs) == 4096
+    a = pb.aig
+    small = [i for i, s in enumerate(pb.support_sizes) if s <= 16]
+    rng = np.random.default_rng(4)
+    sample = [i for i in small if stored["cex"][i] is not None]
+    sample += [int(i) for i in rng.choice(small, size=min(40, len(small)), replace=False)]
+    assert any(stored["cex"][i] is not None for i in sample)
+    for i in sorted(set(sample)):
+        assert O.check(a.num_pis, a.fanins, a.outputs[i])[0] == stored["cex"][i], i
