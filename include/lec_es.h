@@ -143,9 +143,13 @@ typedef struct {
 } lec_es_config;
 
 /* Host-only view of a compiled slot program (no GPU needed).  Records are
- * 8 bytes: {u16 dst, u16 a, u16 b, u8 op, u8 pad}; op 0..3 = AND of slots a
+ * 8 bytes: {u16 dst, u16 a, u16 b, u8 op, u8 flags}; op 0..3 = AND of slots a
  * and b, operand a complemented if op&1, b if op&2; op 4 = load support PI a;
- * op 5 = load constant 0.  Caller provides records[cap]. */
+ * op 5 = load constant 0.  flags 1 marks a load of the constant into a free
+ * slot that only separates an AND from a recent AND whose result it reads
+ * (cones of 256 ANDs or more: no AND reads one of the 3 ANDs before it
+ * without a load between, so the interpreter can evaluate 4 at once).
+ * Caller provides records[cap]. */
 typedef struct {
   uint32_t n;
   uint32_t support[64];

@@ -207,11 +207,11 @@ bool choose_word_geometry(lec_es_ctx *c, const Program &prog, const lec_es_optio
     }
   }
   if (!g.word) return false;
-  const uint64_t words = num_words(prog.n);
+  const uint64_t lanes = kLaneBytes == 8 ? num_words(prog.n) : num_chunks(prog.n);
   const size_t per_sm = 228u * 1024u;
   int bps = (int)std::max<size_t>(1, per_sm / (g.smem + 1024));
   bps = std::min(bps, 2048 / g.block);
-  const uint64_t passes = (words + g.block - 1) / g.block;
+  const uint64_t passes = (lanes + g.block - 1) / g.block;
   uint64_t grid = (uint64_t)c->sm_count * bps;
   if (opt && opt->grid_blocks) grid = opt->grid_blocks;
   g.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(grid, passes));
@@ -513,6 +513,7 @@ int plan_run_async_grid(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt
     xp.loads = (const XLoad *)p->d_loads;
     xp.nrec = p->geom.nrec_padded;
     xp.nload = p->nload;
+    xp.step = g.step;
     xp.out_off = p->out_off;
     xp.out_compl = g.out_compl;
     xp.n = g.n;
@@ -872,7 +873,7 @@ extern "C" int lec_es_truth_tables_ex(lec_es_ctx *c, const lec_es_miter *m, uint
   encode_w(g, geom.block, xr, xl, out_off);
   for (size_t j = 0; j < xr.size(); j++) {  // the j-th AND record computes order_vars[j]
     const uint32_t row = (uint32_t)(std::lower_bound(sorted.begin(), sorted.end(), g.order_vars[j]) - sorted.begin());
-    xr[j].ctl |= (row + 1u) << 2;
+    xr[j].ctl |= (row + 1u) << kCtlRowShift;
   }
   const size_t out_bytes = (size_t)g.cone_ands * nw * 8u;
   cudaSetDevice(c->device);
@@ -904,6 +905,7 @@ extern "C" int lec_es_truth_tables_ex(lec_es_ctx *c, const lec_es_miter *m, uint
     xp.loads = (const XLoad *)d_loads;
     xp.nrec = geom.nrec_padded;
     xp.nload = (uint32_t)xl.size();
+    xp.step = g.step;
     xp.out_off = out_off;
     xp.out_compl = g.out_compl;
     xp.n = g.n;

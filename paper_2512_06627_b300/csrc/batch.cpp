@@ -182,8 +182,8 @@ int stage_programs(lec_es_ctx *c, lec_es_batch_plan *b, const lec_es_miter *m, s
   if (rc) return rc;
   if (cudaSetDevice(c->device) != cudaSuccess) return LEC_ES_ECUDA;
   // live sets the tile kernel holds in shared memory at 64 threads per block
-  // (8 bytes per slot per thread, a 4 x 512-record ring)
-  const uint32_t max_fit64 = (uint32_t)((c->smem_optin - 64 - 4 * 512 * 16) / (64 * 8));
+  // (kLaneBytes per slot per thread, a 4 x 512-record ring)
+  const uint32_t max_fit64 = (uint32_t)((c->smem_optin - 64 - 4 * 512 * 16) / (64 * kLaneBytes));
   b->jit_of.assign(k, -1);
   b->fallback_of.assign(k, -1);
   for (size_t i = 0; i < k; i++) {
@@ -270,7 +270,7 @@ int stage_layout(lec_es_ctx *c, lec_es_batch_plan *b, const Layout &L, int grid_
     std::vector<XLoad> xl;
     for (size_t i : b->light) {
       XMiter &x = mt[i];
-      encode_w(b->progs[i], L.block, xr, xl, x.out_off);
+      encode_w(b->progs[i], L.block, xr, xl, x.out_off, false);  // the tile queue forwards
       x.rec_off = (uint32_t)arec.size();
       x.nrec = (uint32_t)xr.size();
       x.load_off = (uint32_t)aload.size();

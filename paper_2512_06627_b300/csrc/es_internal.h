@@ -19,6 +19,9 @@ struct Rec {
 static_assert(sizeof(Rec) == 8, "record is 8 bytes");
 
 enum : uint8_t { OP_AND = 0, OP_PI = 4, OP_CONST0 = 5 };
+// Rec.pad of a load of the constant into a free slot that only ends a run of
+// AND records (see Program::step).
+constexpr uint8_t kRecBreak = 1;
 
 // Cover of a cone by 3-input lookup tables (lutmap.cpp).  Value ids: ANDs
 // 0..NA-1 (ascending variable), support PIs NA..NA+n-1, the constant NA+n.
@@ -65,6 +68,9 @@ struct Program {
   LutProgram lut;                   // 3-input table cover (the JIT tier's instructions)
   bool slots_elided = false;        // recs/order_vars not built: the specialised kernel runs this cone
   uint32_t num_records = 0;         // recs.size(), or the kernel's record count when elided
+  uint32_t step = 1;                // kInterpStep: no AND reads one of the kInterpStep - 1 ANDs
+                                    // before it without a load between (records with pad =
+                                    // kRecBreak are such loads); 1: no such rule
 };
 
 struct MiterView {
@@ -166,9 +172,30 @@ struct InterpParams {
   uint32_t extra_tx;        // test hook: bytes expected beyond the record copy (0 normally)
 };
 
-// ---- word-wide interpreter (interp_w.cu) -------------------------------------
-// Records pre-decoded for one block size T: byte offsets slot * T * 8 of the
-// two operand slots and the result slot; ctl bit 0/1 complement operand a/b.
+// ---- lane-wide interpreter (interp_w.cu) -------------------------------------
+// Patterns per thread of the interpreter: 64 (a word as two 32-bit halves)
+// or 32 (one chunk); slots are that many bits wide.
+#ifndef LEC_ES_INTERP_LANE
+#define LEC_ES_INTERP_LANE 64
+#endif
+static_assert(LEC_ES_INTERP_LANE == 32 || LEC_ES_INTERP_LANE == 64, "interpreter lane: 32 or 64 patterns");
+constexpr uint32_t kLaneBytes = LEC_ES_INTERP_LANE / 8;
+// AND records the interpreter evaluates together (operand loads of a step
+// issued before any of its stores) in a program whose step is kInterpStep:
+// no AND there reads one of the kInterpStep - 1 ANDs before it without a
+// load record between.  Other programs run kFwdStep records per step, an
+// operand written within the step taken from the writer's register.
+#ifndef LEC_ES_INTERP_STEP
+#define LEC_ES_INTERP_STEP 4
+#endif
+constexpr int kInterpStep = LEC_ES_INTERP_STEP;
+constexpr int kFwdStep = 2;
+// Cones of at least this many ANDs get kInterpStep programs.
+constexpr uint32_t kStepMinAnds = 256;
+// Records pre-decoded for one block size T: byte offsets slot * T * kLaneBytes
+// of the two operand slots and the result slot; ctl bit 0/1 complement
+// operand a/b; bits 2.. the truth-table row + 1 (dump only).
+constexpr uint32_t kCtlRowShift = 2;
 struct XRec {
   uint32_t a_off, b_off, d_off, ctl;
 };
@@ -180,6 +207,7 @@ struct XParams {
   const XRec *recs;
   const XLoad *loads;
   uint32_t nrec, nload;
+  uint32_t step;            // Program::step of the encoded program
   uint32_t out_off, out_compl, n;
   uint32_t ring_recs, resident, extra_tx;
   uint64_t word_begin, word_end;  // 64-pattern words
@@ -209,7 +237,10 @@ struct XBatchParams {
 };
 
 // Encode a slot program for the word-wide kernels at block size `block`.
-void encode_w(const Program &g, int block, std::vector<XRec> &recs, std::vector<XLoad> &loads, uint32_t &out_off);
+// Run-break loads (kRecBreak) are kept when `breaks` (kernels that rely on
+// Program::step) and dropped otherwise (forwarding kernels).
+void encode_w(const Program &g, int block, std::vector<XRec> &recs, std::vector<XLoad> &loads, uint32_t &out_off,
+              bool breaks = true);
 size_t interp_w_smem_bytes(uint32_t nslots, uint32_t nrec, int block, uint32_t *ring_recs, uint32_t *resident);
 size_t batch_w_smem_bytes(uint32_t max_slots, int block, uint32_t ring_recs);
 int launch_interp_w(const XParams &p, int block, int grid, size_t smem, void *stream);

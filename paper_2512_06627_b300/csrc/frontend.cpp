@@ -269,9 +269,82 @@ void order_greedy(const MiterView &m, const Cone &c, const ConeIndex &ix, uint32
   }
 }
 
+// Spread reads away from writes: reorder a topological AND order so that,
+// where it can, no AND reads the result of one of the `window` ANDs just
+// before it -- list scheduling with the given order as priority, taking the
+// first ready AND (looking at most kLook ready ANDs ahead) that reads none of
+// them, else the first ready one.  The interpreter evaluates kInterpStep
+// records at once and needs no forwarding between records of a step that
+// are independent.  Nearby ready ANDs are taken, so the live set barely
+// changes.
+void separate_reads(const MiterView &m, const Cone &c, const ConeIndex &ix, uint32_t window,
+                    std::vector<uint32_t> &ord) {
+  constexpr int kLook = 16;
+  const size_t NA = c.ands.size();
+  if (window == 0 || NA < 3 || ord.size() != NA) return;
+  std::vector<uint32_t> prio(NA), pending(NA, 0);
+  for (size_t k = 0; k < NA; k++) prio[ord[k]] = (uint32_t)k;
+  std::vector<uint32_t> ustart(NA + 1, 0), users;
+  std::vector<int64_t> fa(2 * NA);
+  for (size_t i = 0; i < NA; i++) {
+    const uint32_t *f = fanin_of(m, c.ands[i]);
+    for (int e = 0; e < 2; e++) {
+      const int64_t p = ix.and_pos(f[e] >> 1);
+      fa[2 * i + e] = (e == 1 && p == fa[2 * i]) ? -1 : p;  // a repeated fanin counts once
+      if (fa[2 * i + e] >= 0) {
+        ustart[p + 1]++;
+        pending[i]++;
+      }
+    }
+  }
+  for (size_t i = 0; i < NA; i++) ustart[i + 1] += ustart[i];
+  users.resize(ustart[NA]);
+  {
+    std::vector<uint32_t> fill(ustart.begin(), ustart.end() - 1);
+    for (size_t i = 0; i < NA; i++)
+      for (int e = 0; e < 2; e++)
+        if (fa[2 * i + e] >= 0) users[fill[fa[2 * i + e]]++] = (uint32_t)i;
+  }
+  // ready ANDs by priority (a min-heap of (priority, index))
+  std::priority_queue<std::pair<uint32_t, uint32_t>, std::vector<std::pair<uint32_t, uint32_t>>,
+                      std::greater<std::pair<uint32_t, uint32_t>>>
+      ready;
+  for (size_t i = 0; i < NA; i++)
+    if (!pending[i]) ready.push({prio[i], (uint32_t)i});
+  std::vector<uint32_t> out;
+  out.reserve(NA);
+  std::vector<uint32_t> recent;  // the last `window` emitted
+  std::pair<uint32_t, uint32_t> held[kLook];
+  while (!ready.empty()) {
+    int nh = 0, pick = -1;
+    while (!ready.empty() && nh < kLook) {
+      held[nh] = ready.top();
+      ready.pop();
+      const uint32_t i = held[nh].second;
+      bool near = false;
+      for (uint32_t r : recent) near |= (int64_t)r == fa[2 * i] || (int64_t)r == fa[2 * i + 1];
+      nh++;
+      if (!near) {
+        pick = nh - 1;
+        break;
+      }
+    }
+    if (pick < 0) pick = 0;
+    for (int h = 0; h < nh; h++)
+      if (h != pick) ready.push(held[h]);
+    const uint32_t i = held[pick].second;
+    out.push_back(i);
+    recent.push_back(i);
+    if (recent.size() > window) recent.erase(recent.begin());
+    for (uint32_t k = ustart[i]; k < ustart[i + 1]; k++)
+      if (--pending[users[k]] == 0) ready.push({prio[users[k]], users[k]});
+  }
+  if (out.size() == NA) ord.swap(out);
+}
+
 // Reference-count slot assignment over a given order.
 int assign_slots(const MiterView &m, const Cone &c, const ConeIndex &ix, const std::vector<uint32_t> &ord,
-                 uint32_t root_var, Program &p) {
+                 uint32_t root_var, uint32_t step, Program &p) {
   const size_t NA = c.ands.size(), NP = c.pis.size();
   // value ids: [0, NA) ANDs, [NA, NA+NP) PIs, NA+NP the constant
   const size_t NV = NA + NP + 1;
@@ -298,8 +371,11 @@ int assign_slots(const MiterView &m, const Cone &c, const ConeIndex &ix, const s
     }
     return high++;
   };
+  // AND records emitted since the last load record (at most step - 1)
+  std::vector<uint16_t> recent;
   auto load = [&](int64_t v) {
     if (slot[v] >= 0) return;
+    recent.clear();
     uint32_t s = alloc();
     slot[v] = (int32_t)s;
     Rec r{};
@@ -324,6 +400,21 @@ int assign_slots(const MiterView &m, const Cone &c, const ConeIndex &ix, const s
     r.b = (uint16_t)slot[b];
     const uint32_t *f = fanin_of(m, c.ands[i]);
     r.op = (uint8_t)(OP_AND | (f[0] & 1) | ((f[1] & 1) << 1));
+    // A step-`step` program is evaluated `step` AND records of a run (records
+    // between two loads) at once, all operand loads first: an AND that reads
+    // the result of one of the step - 1 ANDs before it in its run starts a
+    // new run, behind a load of the constant into a free slot.
+    bool near = false;
+    for (uint16_t d : recent) near |= d == r.a || d == r.b;
+    if (near) {
+      Rec z{};
+      z.op = OP_CONST0;
+      z.pad = kRecBreak;
+      if (freel.empty()) freel.push(high++);
+      z.dst = (uint16_t)freel.top();
+      p.recs.push_back(z);
+      recent.clear();
+    }
     // when a == b both edges count, so the count reaches zero at most once
     if (--refs[a] == 0) freel.push((uint32_t)slot[a]);
     if (--refs[b] == 0) freel.push((uint32_t)slot[b]);
@@ -332,11 +423,16 @@ int assign_slots(const MiterView &m, const Cone &c, const ConeIndex &ix, const s
     slot[i] = (int32_t)d;
     p.recs.push_back(r);
     p.order_vars.push_back(c.ands[i]);
+    if (step > 1) {
+      recent.push_back(r.dst);
+      if (recent.size() > (size_t)step - 1) recent.erase(recent.begin());
+    }
     if (high > 65535) return LEC_ES_ETOOBIG;
   }
   if (root >= (int64_t)NA) load(root);  // output is a PI or the constant
   p.num_slots = high;
   p.out_slot = (uint32_t)slot[root];
+  p.step = step;
   return LEC_ES_OK;
 }
 
@@ -622,6 +718,7 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
   else return LEC_ES_EINVAL;
 
   std::vector<Program> cand(tried.size());
+  std::vector<std::vector<uint32_t>> base(tried.size());  // each order before separate_reads
   std::vector<int> crc(tried.size(), LEC_ES_OK);
   auto run_order = [&](size_t t) {
     const uint32_t o = tried[t];
@@ -634,7 +731,11 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
       crc[t] = LEC_ES_EINVAL;
       return;
     }
-    crc[t] = assign_slots(m, c, ix, ord, root_var, cand[t]);
+    base[t].reserve(ord.size());
+    for (uint32_t i : ord) base[t].push_back((uint32_t)i);
+    const uint32_t step = c.ands.size() >= kStepMinAnds ? (uint32_t)kInterpStep : 1u;
+    if (step > 1) separate_reads(m, c, ix, step - 1, ord);
+    crc[t] = assign_slots(m, c, ix, ord, root_var, step, cand[t]);
     cand[t].order = o;
   };
   for (size_t t = 0; t < tried.size(); t++) run_order(t);
@@ -659,10 +760,7 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
     LutProgram lp;
     LutCover cov;
     cover_cone(m, c, ix, root_var, lp, cov);
-    std::vector<uint32_t> and_order;
-    and_order.reserve(best.order_vars.size());
-    for (uint32_t var : best.order_vars) and_order.push_back((uint32_t)ix.and_pos(var));
-    order_luts(c, and_order, cov, lp);
+    order_luts(c, base[bi], cov, lp);
     lp.count = (uint32_t)lp.order.size();
     best.lut = std::move(lp);
   }
@@ -670,15 +768,16 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
   return LEC_ES_OK;
 }
 
-void encode_w(const Program &g, int block, std::vector<XRec> &recs, std::vector<XLoad> &loads, uint32_t &out_off) {
-  const uint32_t unit = (uint32_t)block * 8u;  // bytes between consecutive slots of one thread
+void encode_w(const Program &g, int block, std::vector<XRec> &recs, std::vector<XLoad> &loads, uint32_t &out_off,
+              bool breaks) {
+  const uint32_t unit = (uint32_t)block * kLaneBytes;  // bytes between consecutive slots of one thread
   recs.clear();
   loads.clear();
   recs.reserve(g.recs.size());
   for (const Rec &r : g.recs) {
     if (r.op < 4) {
       recs.push_back(XRec{r.a * unit, r.b * unit, r.dst * unit, (uint32_t)(r.op & 3u)});
-    } else {
+    } else if (breaks || r.pad != kRecBreak) {
       loads.push_back(XLoad{(uint32_t)recs.size(), r.dst * unit, r.op == OP_PI ? (uint32_t)r.a : 63u, 0u});
     }
   }

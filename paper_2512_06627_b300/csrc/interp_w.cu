@@ -1,11 +1,13 @@
-// interp_w.cu -- word-wide interpreter: one 64-bit word (two 32-bit halves)
-// per thread, pre-decoded records.
+// interp_w.cu -- lane-wide interpreter: one lane of patterns per thread,
+// pre-decoded records.
 //
 // The generic tier for cones without a specialised kernel.  Each thread holds
-// the value slots of one 64-pattern word as two 32-bit halves (uint2, so a
-// slot access is one 8-byte shared-memory operation) and evaluates each AND
-// as one LOP3 per half.  The record stream is prepared on the host for the
-// launch's block size:
+// the value slots of one lane of patterns and evaluates each AND as one LOP3
+// per 32 patterns.  The lane is fixed at build time (LEC_ES_INTERP_LANE):
+// 64 -- one 64-pattern word as two 32-bit halves (uint2, so a slot access is
+// one 8-byte shared-memory operation); 32 -- one 32-pattern chunk (4-byte
+// slots, so the same shared memory holds twice the threads).  The record
+// stream is prepared on the host for the launch's block size:
 //   record  {a_off, b_off, d_off, ctl}: byte offsets of the two operand slots
 //           and the result slot from the thread's slot base, complement bits
 //           in ctl (bit 0: a, bit 1: b), turned into all-zero/all-one masks
@@ -19,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "es_internal.h"
 
 namespace lec {
@@ -26,13 +30,14 @@ namespace {
 
 constexpr int NSTAGE = 4;
 // AND records per interpreter step.  Measured on B300 (12x12 miter, 16x16
-// miter, 3,630 light node-pair miters): 1 -> 1.11 / 596 / 1.45 ms, 2 -> 0.90
-// / 427 / 1.42 ms, 3 -> 1.17 / 515 / 1.45 ms, 4 -> 1.08 / 525 / 1.61 ms,
-// 8 -> 1.39 / 699 / 2.12 ms.
-#ifndef LEC_ES_INTERP_STEP
-#define LEC_ES_INTERP_STEP 2
-#endif
-constexpr int kStep = LEC_ES_INTERP_STEP;
+// miter, 3,630 light node-pair miters in one tile queue) with forwarding in
+// every step: 1 -> 1.11 / 596 / 1.45 ms, 2 -> 0.90 / 427 / 1.42 ms, 3 ->
+// 1.17 / 515 / 1.45 ms, 4 -> 1.08 / 525 / 1.61 ms, 8 -> 1.39 / 699 / 2.12 ms;
+// without forwarding, on programs whose ANDs never read one of the K - 1
+// before them in a run: 2 -> 0.91 / 415 / 1.57 ms, 3 -> 0.82 / 383 / 1.65
+// ms, 4 -> 0.78 / 362 / 1.70 ms (the node pairs' small cones need many run
+// breaks, so the tile queue keeps forwarding, kFwdStep = 2, and only cones of
+// kStepMinAnds ANDs or more get step-kInterpStep programs).
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr uint64_t kWaitNs = 1000000000ull;
 
@@ -97,8 +102,12 @@ __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long lo
   return *(const volatile unsigned long long *)p;
 }
 
+// The thread's lane: a 64-pattern word (two halves) or a 32-pattern chunk.
+using Lane = std::conditional<kLaneBytes == 8, uint2, uint32_t>::type;
+constexpr uint32_t kLanePatterns = kLaneBytes * 8;
+
 // Support PI k for 64-pattern word w, as (low half, high half).
-__device__ __forceinline__ uint2 pi_pair(uint32_t k, uint64_t w) {
+__device__ __forceinline__ uint2 pi_lane(uint32_t k, uint64_t w, uint2) {
   if (k < 5) return make_uint2(kMaskW[k], kMaskW[k]);
   if (k == 5) return make_uint2(0u, 0xFFFFFFFFu);
   if (k == 63) return make_uint2(0u, 0u);  // the constant
@@ -106,53 +115,107 @@ __device__ __forceinline__ uint2 pi_pair(uint32_t k, uint64_t w) {
   return make_uint2(v, v);
 }
 
-__device__ __forceinline__ uint2 ld_slot(const uint8_t *S, uint32_t off) {
-  return *reinterpret_cast<const uint2 *>(S + off);
+// Support PI k for 32-pattern chunk c.
+__device__ __forceinline__ uint32_t pi_lane(uint32_t k, uint64_t c, uint32_t) {
+  if (k < 5) return kMaskW[k];
+  if (k == 63) return 0u;  // the constant
+  return 0u - (uint32_t)((c >> (k - 5)) & 1ull);
 }
 
-// One AND on both halves; the complement bits of ctl become all-zero /
-// all-one masks by a bit-field extract each.
-__device__ __forceinline__ uint2 and_w(uint2 x, uint2 y, uint32_t ctl) {
-  int ma, mb;
-  asm("bfe.s32 %0, %1, 0, 1;" : "=r"(ma) : "r"(ctl));
-  asm("bfe.s32 %0, %1, 1, 1;" : "=r"(mb) : "r"(ctl));
-  return make_uint2((x.x ^ (uint32_t)ma) & (y.x ^ (uint32_t)mb), (x.y ^ (uint32_t)ma) & (y.y ^ (uint32_t)mb));
+__device__ __forceinline__ Lane pi_value(uint32_t k, uint64_t u) { return pi_lane(k, u, Lane{}); }
+
+__device__ __forceinline__ Lane ld_slot(const uint8_t *S, uint32_t off) {
+  return *reinterpret_cast<const Lane *>(S + off);
+}
+
+__device__ __forceinline__ void st_slot(uint8_t *S, uint32_t off, Lane v) { *reinterpret_cast<Lane *>(S + off) = v; }
+
+// One AND; the complement bits of ctl become all-zero / all-one masks by a
+// bit-field extract each.
+__device__ __forceinline__ void ctl_masks(uint32_t ctl, uint32_t &ma, uint32_t &mb) {
+  int a, b;
+  asm("bfe.s32 %0, %1, 0, 1;" : "=r"(a) : "r"(ctl));
+  asm("bfe.s32 %0, %1, 1, 1;" : "=r"(b) : "r"(ctl));
+  ma = (uint32_t)a;
+  mb = (uint32_t)b;
+}
+
+__device__ __forceinline__ uint2 and_lane(uint2 x, uint2 y, uint32_t ctl) {
+  uint32_t ma, mb;
+  ctl_masks(ctl, ma, mb);
+  return make_uint2((x.x ^ ma) & (y.x ^ mb), (x.y ^ ma) & (y.y ^ mb));
+}
+
+__device__ __forceinline__ uint32_t and_lane(uint32_t x, uint32_t y, uint32_t ctl) {
+  uint32_t ma, mb;
+  ctl_masks(ctl, ma, mb);
+  return (x ^ ma) & (y ^ mb);
+}
+
+__device__ __forceinline__ uint64_t lane_bits(uint2 v) { return (uint64_t)v.y << 32 | v.x; }
+__device__ __forceinline__ uint64_t lane_bits(uint32_t v) { return v; }
+
+// Valid patterns of a lane (bits above the lane's patterns clear): all of
+// them unless the support has fewer PIs than the lane has pattern bits.
+__device__ __forceinline__ uint64_t lane_valid(uint32_t n) {
+  const uint64_t lane = kLanePatterns == 64 ? ~0ull : 0xFFFFFFFFull;
+  return n >= 6 ? lane : ((1ull << (1u << n)) - 1ull) & lane;
+}
+
+// Lanes covering words [wb, we) of an n-PI support.
+__device__ __forceinline__ void lane_range(uint64_t wb, uint64_t we, uint32_t n, uint64_t &ub, uint64_t &ue) {
+  if (kLanePatterns == 64) {
+    ub = wb;
+    ue = we;
+    return;
+  }
+  const uint64_t C = n <= 5 ? 1ull : 1ull << (n - 5);
+  ub = min(2 * wb, C);
+  ue = min(2 * we, C);
 }
 
 // Run AND records [0, cnt) of a staged block.  S is this thread's slot base
 // (a byte address in shared memory); record offsets are added to it.
 //
-// kStep records per step: all operand loads are issued first, so their
-// shared-memory latencies overlap, and an operand that an earlier record of
-// the same step writes is taken from that record's result instead (the
-// nearest earlier writer wins, as in sequential order); the stores follow in
-// order.  The next step's records are read before this step's stores.
-// Leftover records (fewer than kStep) run one at a time.  Record reads may
-// run up to kStep records past cnt; they stay inside the shared-memory
-// allocation (the slot area follows the records) and their values are not
-// used.
-__device__ __forceinline__ uint2 pick(uint32_t off, uint32_t d, uint2 v, uint2 x) {
-  return off == d ? v : x;
-}
+// K records per step: all operand loads are issued first, so their
+// shared-memory latencies overlap; the stores follow in order.  FWD = false
+// (programs of step kInterpStep, K = kInterpStep): no record of a step reads
+// what an earlier record of the step writes -- runs end at load records, and
+// the slot program puts a load between an AND and any of the K - 1 ANDs
+// before it whose result it reads (write-after-read and write-after-write
+// within a step are safe: loads come first, stores in order).  FWD = true
+// (any program, K = kFwdStep): an operand that an earlier record of the step
+// writes is taken from that record's result instead (the nearest earlier
+// writer wins, as in sequential order).  The next step's records are read
+// before this step's stores.  Record reads may run up to K records past
+// cnt; they stay inside the shared-memory allocation (the slot area follows
+// the records) and their values are not used.
+__device__ __forceinline__ Lane pick(uint32_t off, uint32_t d, Lane v, Lane x) { return off == d ? v : x; }
 
 // Truth-table dump (TT = true, lec_es_truth_tables_ex): a record whose ctl
-// carries row + 1 in bits 2..31 also stores its value, as one 64-bit word,
-// at row x tt_words + (w - word_begin) of tt_out (words outside the range
-// are not stored).
+// carries row + 1 in bits kCtlRowShift.. also stores its value into word
+// row x tt_words + (w - word_begin) of tt_out, where w is the lane's word
+// (a 32-pattern lane fills its half of it); words outside the range are not
+// stored.
 struct TTSink {
   uint64_t *out;
-  uint64_t words, wb, w;
+  uint64_t words, wb, u;  // u: the thread's lane
 };
 
 template <bool TT>
-__device__ __forceinline__ void tt_store(const TTSink &k, uint32_t ctl, uint2 v) {
+__device__ __forceinline__ void tt_store(const TTSink &k, uint32_t ctl, Lane v) {
   if (!TT) return;
-  const uint32_t row = ctl >> 2;
-  if (row && k.w >= k.wb && k.w - k.wb < k.words)
-    k.out[(uint64_t)(row - 1) * k.words + (k.w - k.wb)] = (uint64_t)v.y << 32 | v.x;
+  const uint32_t row = ctl >> kCtlRowShift;
+  const uint64_t w = kLanePatterns == 64 ? k.u : k.u >> 1;
+  if (!row || w < k.wb || w - k.wb >= k.words) return;
+  const uint64_t at = (uint64_t)(row - 1) * k.words + (w - k.wb);
+  if (kLanePatterns == 64)
+    k.out[at] = lane_bits(v);
+  else
+    reinterpret_cast<uint32_t *>(k.out)[2 * at + (k.u & 1)] = (uint32_t)lane_bits(v);
 }
 
-template <int K, bool TT>
+template <int K, bool FWD, bool TT>
 __device__ __forceinline__ void run_ands_k(const uint4 *r4, uint32_t cnt, uint8_t *S, uint32_t &i, const TTSink &tk) {
   uint4 r[K];
 #pragma unroll
@@ -161,7 +224,7 @@ __device__ __forceinline__ void run_ands_k(const uint4 *r4, uint32_t cnt, uint8_
     uint4 n[K];
 #pragma unroll
     for (int j = 0; j < K; j++) n[j] = r4[i + K + j];
-    uint2 x[K], y[K], v[K];
+    Lane x[K], y[K], v[K];
 #pragma unroll
     for (int j = 0; j < K; j++) {
       x[j] = ld_slot(S, r[j].x);
@@ -169,78 +232,85 @@ __device__ __forceinline__ void run_ands_k(const uint4 *r4, uint32_t cnt, uint8_
     }
 #pragma unroll
     for (int j = 0; j < K; j++) {
+      if (FWD) {
 #pragma unroll
-      for (int q = 0; q < j; q++) {  // later writers override earlier ones
-        x[j] = pick(r[j].x, r[q].z, v[q], x[j]);
-        y[j] = pick(r[j].y, r[q].z, v[q], y[j]);
+        for (int q = 0; q < j; q++) {  // later writers override earlier ones
+          x[j] = pick(r[j].x, r[q].z, v[q], x[j]);
+          y[j] = pick(r[j].y, r[q].z, v[q], y[j]);
+        }
       }
-      v[j] = and_w(x[j], y[j], r[j].w);
+      v[j] = and_lane(x[j], y[j], r[j].w);
       tt_store<TT>(tk, r[j].w, v[j]);
     }
 #pragma unroll
-    for (int j = 0; j < K; j++) *reinterpret_cast<uint2 *>(S + r[j].z) = v[j];
+    for (int j = 0; j < K; j++) st_slot(S, r[j].z, v[j]);
 #pragma unroll
     for (int j = 0; j < K; j++) r[j] = n[j];
   }
 }
 
-template <bool TT>
+template <int K, bool FWD, bool TT>
 __device__ __forceinline__ void run_ands(const XRec *rr, uint32_t cnt, uint8_t *S, const TTSink &tk) {
   const uint4 *r4 = reinterpret_cast<const uint4 *>(rr);
   uint32_t i = 0;
-  if (cnt >= (uint32_t)kStep) run_ands_k<kStep, TT>(r4, cnt, S, i, tk);
+  if (cnt >= (uint32_t)K) run_ands_k<K, FWD, TT>(r4, cnt, S, i, tk);
+  // without forwarding, any two records of a run are independent too
+  if (!FWD && K > 2 && cnt - i >= 2) run_ands_k<2, false, TT>(r4, i + 2, S, i, tk);
   for (; i < cnt; i++) {
     const uint4 r = r4[i];
-    const uint2 v = and_w(ld_slot(S, r.x), ld_slot(S, r.y), r.w);
-    *reinterpret_cast<uint2 *>(S + r.z) = v;
+    const Lane v = and_lane(ld_slot(S, r.x), ld_slot(S, r.y), r.w);
+    st_slot(S, r.z, v);
     tt_store<TT>(tk, r.w, v);
   }
 }
 
 // Execute one staged block of records [base, base + cnt) of the program,
 // applying each load exactly before the record it precedes (a PI may take a
-// slot an earlier record has just freed).  li is the next load (updated).
-template <bool TT = false>
+// slot an earlier record has just freed).  li is the next load (updated);
+// u is the thread's lane.
+template <int K, bool FWD, bool TT = false>
 __device__ __forceinline__ void run_block(const XRec *rr, uint32_t base, uint32_t cnt, const XLoad *loads,
-                                          uint32_t nload, uint32_t &li, uint8_t *S, uint64_t w,
+                                          uint32_t nload, uint32_t &li, uint8_t *S, uint64_t u,
                                           const TTSink &tk = TTSink{}) {
   uint32_t i = 0;
   for (;;) {
     while (li < nload && loads[li].at <= base + i) {
       const XLoad l = loads[li];
-      *reinterpret_cast<uint2 *>(S + l.d_off) = pi_pair(l.k, w);
+      st_slot(S, l.d_off, pi_value(l.k, u));
       li++;
     }
     if (i >= cnt) break;
     uint32_t stop = cnt;
     if (li < nload && loads[li].at < base + cnt) stop = loads[li].at - base;
-    run_ands<TT>(rr + i, stop - i, S, tk);
+    run_ands<K, FWD, TT>(rr + i, stop - i, S, tk);
     i = stop;
   }
 }
 
-__device__ __forceinline__ uint2 valid_pair(uint32_t n) {
-  if (n >= 6) return make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
-  if (n == 5) return make_uint2(0xFFFFFFFFu, 0u);
-  return make_uint2((1u << (1u << n)) - 1u, 0u);
+// The miter output of the thread's lane: complemented as the output literal
+// says, invalid patterns (n below the lane's pattern bits) and lanes outside
+// the range cleared.
+__device__ __forceinline__ uint64_t out_bits(const uint8_t *S, uint32_t off, uint32_t compl_out, uint32_t n,
+                                             bool in_range) {
+  const uint64_t o = lane_bits(ld_slot(S, off)) ^ (compl_out ? ~0ull : 0ull);
+  return in_range ? o & lane_valid(n) : 0ull;
 }
 
-// Lowest failing pattern of the warp's words (lane order = word order).
-__device__ __forceinline__ void report(uint2 out, uint64_t w, bool valid, unsigned long long *cex) {
-  const unsigned long long o = valid ? ((unsigned long long)out.y << 32 | out.x) : 0ull;
+// Lowest failing pattern of the warp's lanes (thread order = lane order).
+__device__ __forceinline__ void report(uint64_t o, uint64_t u, unsigned long long *cex) {
   const unsigned bal = __ballot_sync(0xFFFFFFFFu, o != 0ull);
   if (bal && (int)(threadIdx.x & 31) == __ffs(bal) - 1)
-    atomicMin(cex, (unsigned long long)(w * 64ull + (uint64_t)(__ffsll((long long)o) - 1)));
+    atomicMin(cex, (unsigned long long)(u * kLanePatterns + (uint64_t)(__ffsll((long long)o) - 1)));
 }
 
-template <int T, bool TT = false>
+template <int T, bool TT, int K, bool FWD>
 __global__ void __launch_bounds__(T) es_interp_w(const XParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   volatile unsigned long long *bcast = reinterpret_cast<unsigned long long *>(smem + 48);
   XRec *ring = reinterpret_cast<XRec *>(smem + 64);
   const uint32_t ring_bytes = p.resident ? p.nrec * 16u : NSTAGE * p.ring_recs * 16u;
-  uint8_t *S = smem + 64 + ((ring_bytes + 15u) & ~15u) + threadIdx.x * 8u;
+  uint8_t *S = smem + 64 + ((ring_bytes + 15u) & ~15u) + threadIdx.x * kLaneBytes;
   const int t = threadIdx.x;
   if (t == 0) {
     for (int s = 0; s < NSTAGE; s++) mbar_init(bar + s);
@@ -258,21 +328,20 @@ __global__ void __launch_bounds__(T) es_interp_w(const XParams p) {
     }
   }
   uint32_t parity = 0, inflight = 0;
-  const uint64_t total = p.word_end - p.word_begin;
-  const uint64_t passes = (total + T - 1) / T;
-  const uint2 vm = valid_pair(p.n);
-  const uint32_t oc = p.out_compl ? 0xFFFFFFFFu : 0u;
+  uint64_t ub, ue;
+  lane_range(p.word_begin, p.word_end, p.n, ub, ue);
+  const uint64_t passes = (ue - ub + T - 1) / T;
   unsigned long long done = 0;
   for (uint64_t pass = blockIdx.x; pass < passes; pass += gridDim.x) {
-    const uint64_t w0 = p.word_begin + pass * T;
+    const uint64_t u0 = ub + pass * T;
     if (t == 0) *bcast = ld_volatile(p.cex);
     __syncthreads();
-    if (w0 * 64ull >= *bcast) break;  // block-uniform early exit
-    const uint64_t w = w0 + t;
-    const TTSink tk{p.tt_out, p.tt_words, p.word_begin, w};
+    if (u0 * kLanePatterns >= *bcast) break;  // block-uniform early exit
+    const uint64_t u = u0 + t;
+    const TTSink tk{p.tt_out, p.tt_words, p.word_begin, u};
     uint32_t li = 0;
     if (p.resident) {
-      run_block<TT>(ring, 0, p.nrec, p.loads, p.nload, li, S, w, tk);
+      run_block<K, FWD, TT>(ring, 0, p.nrec, p.loads, p.nload, li, S, u, tk);
     } else {
       for (uint32_t k = 0; k < nch && k < (uint32_t)NSTAGE; k++) {
         if (t == 0) {
@@ -293,7 +362,7 @@ __global__ void __launch_bounds__(T) es_interp_w(const XParams p) {
         parity ^= 1u << s;
         inflight &= ~(1u << s);
         const uint32_t off = k * p.ring_recs;
-        run_block<TT>(ring + (size_t)s * p.ring_recs, off, min(p.ring_recs, p.nrec - off), p.loads, p.nload, li, S, w,
+        run_block<K, FWD, TT>(ring + (size_t)s * p.ring_recs, off, min(p.ring_recs, p.nrec - off), p.loads, p.nload, li, S, u,
                       tk);
         __syncthreads();
         if (k + NSTAGE < nch) {
@@ -313,17 +382,15 @@ __global__ void __launch_bounds__(T) es_interp_w(const XParams p) {
     }
     // loads after the last record (an output that is a PI or the constant)
     while (li < p.nload) {
-      *reinterpret_cast<uint2 *>(S + p.loads[li].d_off) = pi_pair(p.loads[li].k, w);
+      st_slot(S, p.loads[li].d_off, pi_value(p.loads[li].k, u));
       li++;
     }
-    uint2 out = *reinterpret_cast<const uint2 *>(S + p.out_off);
-    out.x = (out.x ^ oc) & vm.x;
-    out.y = (out.y ^ oc) & vm.y;
-    if (!TT) report(out, w, w < p.word_end, p.cex);  // a dump checks nothing, so nothing exits early
-    done += (unsigned long long)min((uint64_t)T, p.word_end - w0);
+    // a dump checks nothing, so nothing exits early
+    if (!TT) report(out_bits(S, p.out_off, p.out_compl, p.n, u < ue), u, p.cex);
+    done += (unsigned long long)min((uint64_t)T, ue - u0);
     __syncthreads();
   }
-  if (t == 0 && done) atomicAdd(p.evaluated, done * 64ull);
+  if (t == 0 && done) atomicAdd(p.evaluated, done * kLanePatterns);
 }
 
 // Tile-queue form: blocks pull (miter, word range) tiles.
@@ -334,7 +401,7 @@ __global__ void __launch_bounds__(T) es_batch_w(const XBatchParams p) {
   volatile unsigned long long *bcast = reinterpret_cast<unsigned long long *>(smem + 40);
   volatile uint32_t *btile = reinterpret_cast<uint32_t *>(smem + 56);
   XRec *ring = reinterpret_cast<XRec *>(smem + 64);
-  uint8_t *S = smem + 64 + NSTAGE * p.ring_recs * 16u + threadIdx.x * 8u;
+  uint8_t *S = smem + 64 + NSTAGE * p.ring_recs * 16u + threadIdx.x * kLaneBytes;
   const int t = threadIdx.x;
   if (t == 0) {
     for (int s = 0; s < NSTAGE; s++) mbar_init(bar + s);
@@ -353,8 +420,6 @@ __global__ void __launch_bounds__(T) es_batch_w(const XBatchParams p) {
     const XRec *recs = p.recs + bm.rec_off;
     const XLoad *loads = p.loads + bm.load_off;
     const uint32_t nch = (bm.nrec + p.ring_recs - 1) / p.ring_recs;
-    const uint2 vm = valid_pair(bm.n);
-    const uint32_t oc = bm.out_compl ? 0xFFFFFFFFu : 0u;
     const bool resident = nch <= (uint32_t)NSTAGE;  // the whole program fits the ring
     if (resident && bm.nrec) {
       uint32_t inflight = 0;
@@ -380,7 +445,9 @@ __global__ void __launch_bounds__(T) es_batch_w(const XBatchParams p) {
         return;
       }
     }
-    for (uint64_t w0 = bt.word_begin; w0 < bt.word_end; w0 += T) {
+    uint64_t ub, ue;
+    lane_range(bt.word_begin, bt.word_end, bm.n, ub, ue);
+    for (uint64_t u0 = ub; u0 < ue; u0 += T) {
       if (t == 0) {
         unsigned long long cur = ld_volatile(p.cex + bt.miter);
         if (p.cancel && p.cancel[bt.miter]) cur = 0;
@@ -389,11 +456,11 @@ __global__ void __launch_bounds__(T) es_batch_w(const XBatchParams p) {
       __syncthreads();
       const unsigned long long cur = *bcast;
       __syncthreads();
-      if (w0 * 64ull >= cur) break;
-      const uint64_t w = w0 + t;
+      if (u0 * kLanePatterns >= cur) break;
+      const uint64_t u = u0 + t;
       uint32_t li = 0;
       if (resident) {
-        run_block(ring, 0, bm.nrec, loads, bm.nload, li, S, w);
+        run_block<kFwdStep, true>(ring, 0, bm.nrec, loads, bm.nload, li, S, u);
       } else {
         uint32_t inflight = 0;
         for (uint32_t k = 0; k < (uint32_t)NSTAGE; k++) {
@@ -415,8 +482,8 @@ __global__ void __launch_bounds__(T) es_batch_w(const XBatchParams p) {
           parity ^= 1u << s;
           inflight &= ~(1u << s);
           const uint32_t off = k * p.ring_recs;
-          run_block(ring + (size_t)s * p.ring_recs, off, min(p.ring_recs, bm.nrec - off), loads, bm.nload, li, S,
-                    w);
+          run_block<kFwdStep, true>(ring + (size_t)s * p.ring_recs, off, min(p.ring_recs, bm.nrec - off), loads, bm.nload, li, S,
+                    u);
           __syncthreads();
           if (k + NSTAGE < nch) {
             if (t == 0) {
@@ -434,32 +501,37 @@ __global__ void __launch_bounds__(T) es_batch_w(const XBatchParams p) {
         }
       }
       while (li < bm.nload) {
-        *reinterpret_cast<uint2 *>(S + loads[li].d_off) = pi_pair(loads[li].k, w);
+        st_slot(S, loads[li].d_off, pi_value(loads[li].k, u));
         li++;
       }
-      uint2 out = *reinterpret_cast<const uint2 *>(S + bm.out_off);
-      out.x = (out.x ^ oc) & vm.x;
-      out.y = (out.y ^ oc) & vm.y;
-      report(out, w, w < bt.word_end, p.cex + bt.miter);
+      report(out_bits(S, bm.out_off, bm.out_compl, bm.n, u < ue), u, p.cex + bt.miter);
       __syncthreads();
     }
     __syncthreads();  // ring reuse by the next tile
   }
 }
 
+template <int T, bool TT, int K, bool FWD>
+int launch_wk(const XParams &p, int grid, size_t smem, cudaStream_t st) {
+  cudaError_t e =
+      cudaFuncSetAttribute(es_interp_w<T, TT, K, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  es_interp_w<T, TT, K, FWD><<<grid, T, smem, st>>>(p);
+  return (int)cudaGetLastError();
+}
+
+// Programs of step kInterpStep run without forwarding, others with it.
 template <int T, bool TT = false>
 int launch_w(const XParams &p, int grid, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(es_interp_w<T, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return (int)e;
-  es_interp_w<T, TT><<<grid, T, smem, st>>>(p);
-  return (int)cudaGetLastError();
+  if (p.step == (uint32_t)kInterpStep) return launch_wk<T, TT, kInterpStep, false>(p, grid, smem, st);
+  return launch_wk<T, TT, kFwdStep, true>(p, grid, smem, st);
 }
 
 }  // namespace
 
 size_t interp_w_smem_bytes(uint32_t nslots, uint32_t nrec, int block, uint32_t *ring_recs, uint32_t *resident) {
   const size_t limit = 227u * 1024u;
-  const size_t slots = (size_t)nslots * block * 8u;
+  const size_t slots = (size_t)nslots * block * kLaneBytes;
   const size_t whole = 64 + (size_t)nrec * 16u + slots;
   if (whole <= limit) {
     *resident = 1;
@@ -472,7 +544,7 @@ size_t interp_w_smem_bytes(uint32_t nslots, uint32_t nrec, int block, uint32_t *
 }
 
 size_t batch_w_smem_bytes(uint32_t max_slots, int block, uint32_t ring_recs) {
-  return 64 + (size_t)NSTAGE * ring_recs * 16u + (size_t)max_slots * block * 8u;
+  return 64 + (size_t)NSTAGE * ring_recs * 16u + (size_t)max_slots * block * kLaneBytes;
 }
 
 int launch_interp_w(const XParams &p, int block, int grid, size_t smem, void *stream) {

@@ -258,6 +258,7 @@ int launch(Server *s, Request *r) {
     xp.loads = (const XLoad *)res->d_loads;
     xp.nrec = res->geom.nrec_padded;
     xp.nload = res->nload;
+    xp.step = g.step;
     xp.out_off = res->out_off;
     xp.out_compl = g.out_compl;
     xp.n = g.n;
@@ -269,7 +270,8 @@ int launch(Server *s, Request *r) {
     xp.evaluated = sl.d_res + 1;
     xp.status = (uint32_t *)(sl.d_res + 2);
     // a few passes per block, so blocks retire and other requests interleave
-    const uint64_t passes = (xp.word_end + res->geom.block - 1) / res->geom.block;
+    const uint64_t lanes = kLaneBytes == 8 ? xp.word_end : num_chunks(g.n);
+    const uint64_t passes = (lanes + res->geom.block - 1) / res->geom.block;
     const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>((passes + 3) / 4, 1u << 30));
     err = launch_interp_w(xp, res->geom.block, (int)grid, res->geom.smem, st);
     r->tier = LEC_ES_TIER_INTERP;
@@ -383,7 +385,8 @@ bool groupable(Server *s, Request *r) {
   // small on the interpreter: grouped even when a specialised kernel is held
   // (one launch for the whole group costs less than one launch each)
   if (cost_run_ms(c, LEC_ES_TIER_INTERP, g.cone_ands, g.n) >= kGroupMs) return false;
-  const size_t fit = (s->group_smem_max - batch_w_smem_bytes(0, kGroupBlock, kGroupRing)) / ((size_t)kGroupBlock * 8);
+  const size_t fit =
+      (s->group_smem_max - batch_w_smem_bytes(0, kGroupBlock, kGroupRing)) / ((size_t)kGroupBlock * kLaneBytes);
   if (g.num_slots > fit || (size_t)g.recs.size() * 32u > kGroupStage) return false;
   if ((num_words(g.n) + kGroupTileWords - 1) / kGroupTileWords > (uint64_t)kGroupTiles) return false;
   auto it = s->resident.find({g.hash, g.hash2});
@@ -765,7 +768,7 @@ int ensure_server(lec_es_ctx *c) {
   if (cudaStreamCreateWithFlags(&s->group_stream, cudaStreamNonBlocking) != cudaSuccess) return LEC_ES_ECUDA;
   {
     const size_t fit = ((size_t)c->smem_optin - batch_w_smem_bytes(0, kGroupBlock, kGroupRing)) /
-                       ((size_t)kGroupBlock * 8);
+                       ((size_t)kGroupBlock * kLaneBytes);
     s->group_smem_max = batch_w_smem_bytes((uint32_t)fit, kGroupBlock, kGroupRing);
     if (configure_batch_w(kGroupBlock, (size_t)c->smem_optin) != 0) return LEC_ES_ECUDA;
   }

@@ -159,8 +159,52 @@ def _check_program(aig, out, order):
         want = sorted(tts[row[v]].tobytes() for v in cone)
         assert got == want
     peak = check_liveness(info, recs)
-    assert peak == info.num_slots or (info.num_slots == 1 and peak <= 1)
+    # the one slot a run-break load may add (the constant, never read) is not live
+    dst, a, b, op = decode(recs)
+    top = info.num_slots - 1
+    break_only = all(op[i] == 5 for i in range(len(recs)) if dst[i] == top) and \
+        not any(op[i] < 4 and top in (a[i], b[i]) for i in range(len(recs))) and top != info.out_slot
+    assert peak == info.num_slots or (info.num_slots == 1 and peak <= 1) or (break_only and peak == top)
+    if info.cone_ands >= 256:
+        _check_runs(recs)
+    else:  # no run breaks in small cones
+        assert not (recs >> np.uint64(56)).any()
     return info
+
+
+def _check_runs(recs, step=4):
+    """Cones of 256 ANDs or more: the interpreter evaluates `step` AND records
+    of a run (records between load records) together, operand loads first,
+    so no AND reads the result of one of the step - 1 ANDs before it in its
+    run; the loads that only end a run carry flags 1 and load the constant
+    into a slot nobody reads before it is written again."""
+    dst, a, b, op = decode(recs)
+    flags = (recs >> np.uint64(56)).astype(np.uint8)
+    recent = []
+    for i in range(len(recs)):
+        if flags[i]:
+            assert op[i] == 5 and flags[i] == 1
+            for j in range(i + 1, len(recs)):  # the slot is written before any read
+                if op[j] < 4 and dst[i] in (a[j], b[j]):
+                    raise AssertionError(f"break load {i} read at {j}")
+                if dst[j] == dst[i]:
+                    break
+        if op[i] >= 4:
+            recent = []
+            continue
+        assert int(a[i]) not in recent and int(b[i]) not in recent, i
+        recent = (recent + [int(dst[i])])[-(step - 1):]
+
+
+def test_run_breaks_in_large_cones():
+    """Adder and multiplier miters of 256 ANDs or more keep the step-4 rule
+    with few break loads and no more slots than the unbroken order needs."""
+    for aig in (C.config2_mult12(), C.build_multiplier_pair(8, "dadda"), C.config3_mult16()):
+        info = _check_program(aig, aig.outputs[0], L.ORDER_AUTO)
+        _, recs = L.lec_es_compile(L.miter_of(aig))
+        _check_runs(recs)
+        breaks = int(((recs >> np.uint64(56)) == 1).sum())
+        assert info.cone_ands >= 256 and breaks < info.cone_ands // 50, breaks
 
 
 @pytest.mark.parametrize("seed", range(30))
