@@ -203,6 +203,7 @@ struct XRec {
 struct XLoad {
   uint32_t at, d_off, k, pad;
 };
+static_assert(sizeof(XLoad) == 16, "the kernels read a load as one 16-byte vector");
 struct XParams {
   const XRec *recs;
   const XLoad *loads;

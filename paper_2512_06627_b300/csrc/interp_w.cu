@@ -272,16 +272,20 @@ template <int K, bool FWD, bool TT = false>
 __device__ __forceinline__ void run_block(const XRec *rr, uint32_t base, uint32_t cnt, const XLoad *loads,
                                           uint32_t nload, uint32_t &li, uint8_t *S, uint64_t u,
                                           const TTSink &tk = TTSink{}) {
+  // the next load {at, d_off, k} is held in registers, fetched as soon as the
+  // one before it is applied, so its latency hides behind the records between
+  const uint4 *l4 = reinterpret_cast<const uint4 *>(loads);
+  const uint4 none = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+  uint4 nl = li < nload ? __ldg(l4 + li) : none;
   uint32_t i = 0;
   for (;;) {
-    while (li < nload && loads[li].at <= base + i) {
-      const XLoad l = loads[li];
-      st_slot(S, l.d_off, pi_value(l.k, u));
+    while (nl.x <= base + i) {
+      st_slot(S, nl.y, pi_value(nl.z, u));
       li++;
+      nl = li < nload ? __ldg(l4 + li) : none;
     }
     if (i >= cnt) break;
-    uint32_t stop = cnt;
-    if (li < nload && loads[li].at < base + cnt) stop = loads[li].at - base;
+    const uint32_t stop = nl.x < base + cnt ? nl.x - base : cnt;
     run_ands<K, FWD, TT>(rr + i, stop - i, S, tk);
     i = stop;
   }
