@@ -40,17 +40,19 @@ namespace lec {
 namespace {
 
 // Built-in B300 values (148 SMs at 2,032 MHz): lec_es_cost_fit over the
-// single-launch device times of 71 (interpreter) and 74 (specialised kernel)
-// equivalent miters -- the 12x12 and 16x16 multiplier miters, the adders,
-// product-bit miters of 8..18-bit multipliers and node-pair miters of 4..28
-// PIs -- with median relative errors of 8% and 18% (small kernels are
-// dominated by launch latency, which three terms only approximate).
+// single-launch device times of equivalent miters -- the 12x12 and 16x16
+// multiplier miters, the adders, product-bit miters of 8..18-bit multipliers
+// and node-pair miters of 4..28 PIs (python -m paper_2512_06627_b300.calibrate
+// times that set).  Interpreter: 71 miters with the four-record steps,
+// median relative error 9%; specialised kernel: 74 miters, 18% (small
+// kernels are dominated by launch latency, which three terms only
+// approximate).
 struct Builtin {
   double a_ms, c_ms, alpha_ms;
 };
 constexpr Builtin kRun[4] = {
     {0.0, 0.0, 0.0},                  // AUTO: unused
-    {1.112e-2, 3.176e-5, 1.227e-4},   // INTERP: word-wide interpreter
+    {9.419e-3, 3.451e-5, 1.4144e-4},  // INTERP: word-wide interpreter
     {7.743e-3, 2.742e-6, 6.018e-7},   // JIT: specialised kernel
     {2.0e-2, 1.0e-4, 2.0e-3},         // SPILL: global-memory interpreter (rough)
 };
