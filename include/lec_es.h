@@ -165,6 +165,11 @@ typedef struct {
   double lop3_per_pass;     /* plan_info of a specialised-kernel plan: lop3 the kernel executes per
                                32-pattern chunk and thread (tables once per loop level that needs them,
                                folded copies); 0 otherwise or when unknown */
+  uint32_t interp_step;     /* AND records the interpreter may evaluate at once without forwarding:
+                               4 when no AND reads one of the 3 ANDs before it without a load record
+                               between (cones of 256+ ANDs that need at most one run-break load per
+                               16 ANDs), else 1 */
+  uint32_t pad;
 } lec_es_program_info;
 
 /* ---- context ---------------------------------------------------------- */

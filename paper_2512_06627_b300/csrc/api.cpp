@@ -318,6 +318,7 @@ extern "C" int lec_es_compile(const lec_es_miter *m, uint32_t order, lec_es_prog
   info->hash = p.hash;
   info->num_luts = p.lut.count;
   info->lut_live = p.lut.live;
+  info->interp_step = p.step;
   if (records && cap) memcpy(records, p.recs.data(), sizeof(Rec) * std::min<uint64_t>(cap, p.recs.size()));
   return LEC_ES_OK;
 }
@@ -624,6 +625,7 @@ extern "C" int lec_es_plan_info(const lec_es_plan *p, lec_es_program_info *info)
   info->num_luts = g.lut.count;
   info->lut_live = g.lut.live;
   info->lop3_per_pass = p->tier == LEC_ES_TIER_JIT && p->jit ? p->jit->lop3_per_pass : 0.0;
+  info->interp_step = g.step;
   return LEC_ES_OK;
 }
 

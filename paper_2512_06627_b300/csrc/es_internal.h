@@ -190,8 +190,10 @@ constexpr uint32_t kLaneBytes = LEC_ES_INTERP_LANE / 8;
 #endif
 constexpr int kInterpStep = LEC_ES_INTERP_STEP;
 constexpr int kFwdStep = 2;
-// Cones of at least this many ANDs get kInterpStep programs.
+// Cones of at least this many ANDs get kInterpStep programs, unless they
+// would need more than one run-break load per kMaxBreakShare ANDs.
 constexpr uint32_t kStepMinAnds = 256;
+constexpr size_t kMaxBreakShare = 16;
 // Records pre-decoded for one block size T: byte offsets slot * T * kLaneBytes
 // of the two operand slots and the result slot; ctl bit 0/1 complement
 // operand a/b; bits 2.. the truth-table row + 1 (dump only).

@@ -733,9 +733,20 @@ int compile_program(const MiterView &m, uint32_t order, uint32_t max_pis, Progra
     }
     base[t].reserve(ord.size());
     for (uint32_t i : ord) base[t].push_back((uint32_t)i);
-    const uint32_t step = c.ands.size() >= kStepMinAnds ? (uint32_t)kInterpStep : 1u;
-    if (step > 1) separate_reads(m, c, ix, step - 1, ord);
-    crc[t] = assign_slots(m, c, ix, ord, root_var, step, cand[t]);
+    if (c.ands.size() >= kStepMinAnds) {
+      separate_reads(m, c, ix, (uint32_t)kInterpStep - 1, ord);
+      crc[t] = assign_slots(m, c, ix, ord, root_var, (uint32_t)kInterpStep, cand[t]);
+      // a narrow cone that needs many run breaks runs better with forwarding
+      const size_t breaks = cand[t].recs.size() - c.ands.size() -
+                            (size_t)std::count_if(cand[t].recs.begin(), cand[t].recs.end(),
+                                                  [](const Rec &r) { return r.op >= 4 && r.pad != kRecBreak; });
+      if (crc[t] || breaks * kMaxBreakShare <= c.ands.size()) {
+        cand[t].order = o;
+        return;
+      }
+      cand[t] = Program{};
+    }
+    crc[t] = assign_slots(m, c, ix, base[t], root_var, 1u, cand[t]);
     cand[t].order = o;
   };
   for (size_t t = 0; t < tried.size(); t++) run_order(t);

@@ -82,7 +82,8 @@ class lec_es_program_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint32), ("support", ctypes.c_uint32 * 64), ("cone_ands", ctypes.c_uint32),
                 ("num_slots", ctypes.c_uint32), ("out_slot", ctypes.c_uint32), ("out_compl", ctypes.c_uint32),
                 ("order", ctypes.c_uint32), ("num_records", ctypes.c_uint64), ("hash", ctypes.c_uint64),
-                ("num_luts", ctypes.c_uint32), ("lut_live", ctypes.c_uint32), ("lop3_per_pass", ctypes.c_double)]
+                ("num_luts", ctypes.c_uint32), ("lut_live", ctypes.c_uint32), ("lop3_per_pass", ctypes.c_double),
+                ("interp_step", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
 class lec_es_cost_coeffs(ctypes.Structure):

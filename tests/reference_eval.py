@@ -60,3 +60,38 @@ def random_aig(rng, num_pis, num_ands, p_const=0.03):
                 f[i, e] = 2 * u + int(rng.integers(0, 2))
     out = 2 * (num_pis + num_ands) + int(rng.integers(0, 2))
     return Aig(num_pis, f, [out])
+
+
+def narrow_aig(rng, num_pis, num_ands, reach):
+    """A deep, narrow random AIG (fanins mostly among the `reach` previous
+    variables): its slot program, at 256 ANDs or more, needs many run-break
+    loads.  Three outputs: the last AND x, and x and not-x each ANDed with
+    the three highest PIs (failing patterns only in the top eighth of the
+    space; at least one of the two fails)."""
+    from paper_2512_06627_b300.circuits import Aig
+    rows = []
+
+    def new_and(a, b):
+        rows.append((a, b))
+        return 2 * (num_pis + len(rows))
+
+    def recent():
+        top = num_pis + len(rows)
+        if rng.random() < 0.15 or top == num_pis:
+            return 2 * int(rng.integers(1, num_pis + 1)) + int(rng.integers(0, 2))
+        return 2 * max(1, top + 1 - int(rng.geometric(1.0 / reach))) + int(rng.integers(0, 2))
+
+    while len(rows) < num_ands:  # ANDs, and XORs (three ANDs) so values stay balanced
+        a, b = recent(), recent()
+        if rng.random() < 0.5:
+            new_and(a, b)
+        else:
+            new_and(new_and(a, b ^ 1) ^ 1, new_and(a ^ 1, b) ^ 1)
+    last = 2 * (num_pis + len(rows))
+    outs = [last]
+    for start in (last, last ^ 1):
+        prev = start
+        for j in range(3):
+            prev = new_and(prev, 2 * (num_pis - j))
+        outs.append(prev)
+    return Aig(num_pis, np.array(rows, dtype=np.uint32), outs)

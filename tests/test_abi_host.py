@@ -165,10 +165,12 @@ def _check_program(aig, out, order):
     break_only = all(op[i] == 5 for i in range(len(recs)) if dst[i] == top) and \
         not any(op[i] < 4 and top in (a[i], b[i]) for i in range(len(recs))) and top != info.out_slot
     assert peak == info.num_slots or (info.num_slots == 1 and peak <= 1) or (break_only and peak == top)
-    if info.cone_ands >= 256:
+    if info.interp_step == 4:
+        assert info.cone_ands >= 256
         _check_runs(recs)
-    else:  # no run breaks in small cones
-        assert not (recs >> np.uint64(56)).any()
+        assert int(((recs >> np.uint64(56)) == 1).sum()) * 16 <= info.cone_ands
+    else:  # no run breaks
+        assert info.interp_step == 1 and not (recs >> np.uint64(56)).any()
     return info
 
 
@@ -202,9 +204,31 @@ def test_run_breaks_in_large_cones():
     for aig in (C.config2_mult12(), C.build_multiplier_pair(8, "dadda"), C.config3_mult16()):
         info = _check_program(aig, aig.outputs[0], L.ORDER_AUTO)
         _, recs = L.lec_es_compile(L.miter_of(aig))
-        _check_runs(recs)
         breaks = int(((recs >> np.uint64(56)) == 1).sum())
-        assert info.cone_ands >= 256 and breaks < info.cone_ands // 50, breaks
+        assert info.interp_step == 4 and breaks < info.cone_ands // 50, breaks
+
+
+@pytest.mark.parametrize("reach", [4, 32])
+def test_narrow_cones_step_or_forwarding(reach):
+    """Deep, narrow cones of 300+ ANDs: with fanins reaching back about 32
+    variables the step-4 rule mostly costs a few dozen break loads and is
+    kept; reaching back about 4 it would cost more than one per 16 ANDs, and
+    the program keeps its forwarding order (step 1, no breaks).  Either way
+    the program computes every node's truth table, and a step-4 program
+    obeys its rule (_check_program)."""
+    from tests.reference_eval import narrow_aig
+    rng = np.random.default_rng(77 + reach)
+    steps = []
+    for _ in range(40):
+        aig = narrow_aig(rng, 12, int(rng.integers(600, 1500)), float(reach))
+        info = _check_program(aig, aig.outputs[0], L.ORDER_AUTO)
+        if info.cone_ands >= 300:
+            steps.append(info.interp_step)
+    assert len(steps) >= 5
+    if reach == 4:
+        assert set(steps) == {1}
+    else:
+        assert steps.count(4) >= len(steps) // 2
 
 
 @pytest.mark.parametrize("seed", range(30))

@@ -10,7 +10,7 @@ import pytest
 import oracle as O
 from paper_2512_06627_b300 import circuits as C
 from paper_2512_06627_b300 import lec_es as L
-from tests.reference_eval import random_aig
+from tests.reference_eval import narrow_aig, random_aig
 
 pytestmark = pytest.mark.gpu
 
@@ -176,3 +176,49 @@ def test_bounded_wait_gives_up_and_context_survives(ctx):
     assert time.time() - t0 < 15
     r = L.lec_es_check_ex(ctx, m, L.options(tier=L.TIER_INTERP))
     assert r.cex_or_none == _oracle(mm, mm.outputs[0])[0]
+
+
+@pytest.mark.parametrize("seed,reach", [(0, 32), (1, 32), (2, 48), (3, 4)])
+def test_step_programs_with_run_breaks(ctx, seed, reach):
+    """Cones of 256 ANDs or more run four independent records per step on
+    the interpreter; where an AND reads one of the three ANDs before it the
+    slot program ends the run with a load (reach 32-48: a few dozen), and a
+    cone that would need more than one per 16 ANDs keeps the forwarding
+    program instead (reach 4).  Every node's value (single-miter
+    interpreter, breaks kept) and the lowest counterexample (single miter;
+    tile queue, breaks dropped and forwarding on; served) equal the
+    oracle's, over the whole space and ragged ranges."""
+    rng = np.random.default_rng(900 + seed)
+    for _ in range(100):  # the first seeded graph whose output cone has 300+ ANDs
+        aig = narrow_aig(rng, int(rng.integers(12, 15)), int(rng.integers(600, 2000)), float(reach))
+        f = aig.flat_fanins()
+        ms = [L.Miter(aig.num_pis, f, o) for o in aig.outputs]
+        info, recs = L.lec_es_compile(ms[0])
+        if info.cone_ands >= 300:
+            break
+    breaks = int(((recs >> np.uint64(56)) == 1).sum())
+    assert info.cone_ands >= 300 and (breaks > 3 if reach >= 32 else breaks == 0)
+    assert breaks * 16 <= info.cone_ands
+    W = O.num_words(info.n)
+    for wb, we in ((0, W), (W // 3 + 1, W - 3)):
+        vars_, tt, valid = L.lec_es_truth_tables_ex(ctx, ms[0], wb, we, L.TIER_INTERP)
+        exp = O.truth_tables(aig.num_pis, aig.fanins, aig.outputs[0], [int(v) for v in vars_], wb, we)
+        assert valid.all() and np.array_equal(tt, exp), (wb, we)
+    want = [_oracle(aig, o)[0] for o in aig.outputs]
+    n1 = L.lec_es_compile(ms[1])[0].n
+    assert want[1] is not None or want[2] is not None
+    assert all(x is None or x >= 7 << (n1 - 3) for x in want[1:])
+    single = [L.lec_es_check_ex(ctx, m, L.options(tier=L.TIER_INTERP)).cex_or_none for m in ms]
+    assert single == want
+    b = L.lec_es_batch_prepare(ctx, ms, L.options(tier=L.TIER_INTERP))
+    L.lec_es_batch_run_async(ctx, b)
+    got = [r.cex for r in L.lec_es_batch_results(ctx, b, len(ms))]
+    L.lec_es_batch_free(ctx, b)
+    assert got == [L.NO_CEX if x is None else x for x in want]
+    W = O.num_words(n1)
+    for o in aig.outputs[1:]:
+        for wb, we in ((1, W - 1), (W // 2 + 3, W)):
+            r = _gpu(ctx, aig, o, L.TIER_INTERP, wb, we)
+            assert r.cex_or_none == _oracle(aig, o, wb, we)[0], (wb, we)
+    t = [L.lec_es_submit(ctx, m) for m in ms]
+    assert [L.lec_es_wait(ctx, x, 60.0).cex_or_none for x in t] == want
