@@ -350,6 +350,10 @@ void plan_release(lec_es_ctx *c, lec_es_plan *p) {
   delete p;
 }
 
+// Set by lec_es_check_ex around its AUTO prepare: a cold kernel is then
+// not built synchronously (see check_race).
+thread_local bool t_check_race = false;
+
 int plan_prepare(lec_es_ctx *c, const lec_es_miter *m, const lec_es_options *opt, lec_es_plan **out) {
   if (!c || !m || !out) return LEC_ES_EINVAL;
   *out = nullptr;
@@ -360,11 +364,15 @@ int plan_prepare(lec_es_ctx *c, const lec_es_miter *m, const lec_es_options *opt
   try {
     const uint32_t want = opt ? opt->tier : LEC_ES_TIER_AUTO;
     JitProbe jp{c, want == LEC_ES_TIER_JIT ? JitProbe::kRun : JitProbe::kAuto};
+    // a one-off AUTO check never builds a kernel it does not hold on its own
+    // path (check_race): the table cover is left to the background build
+    jp.defer = t_check_race;
     const KernelProbe probe{jit_probe, &jp, jit_want_cover};
     // the probe finds table-form kernels only
     const bool may_skip = (want == LEC_ES_TIER_JIT || want == LEC_ES_TIER_AUTO) &&
                           !(opt && (opt->flags & LEC_ES_FLAG_JIT_AND_FORM));
     rc = compile_program(v, opt ? opt->order : LEC_ES_ORDER_AUTO, c->max_pis, prog, may_skip ? &probe : nullptr);
+    if (!rc && jp.deferred && !prog.lut.elided && prog.lut.count == 0) prog.lut.deferred = true;
   } catch (const std::bad_alloc &) {
     return LEC_ES_ENOMEM;
   }
@@ -372,15 +380,11 @@ int plan_prepare(lec_es_ctx *c, const lec_es_miter *m, const lec_es_options *opt
   const double front_ms = now_ms() - t0;
   if (getenv("LEC_ES_FRONT_LOG"))
     fprintf(stderr, "lec_es front end %016llx: %.3f ms, table cover %s\n", (unsigned long long)prog.hash, front_ms,
-            prog.lut.elided ? "reused from the kernel" : "built");
+            prog.lut.elided ? "reused from the kernel" : prog.lut.deferred ? "left to the background build" : "built");
   rc = plan_prepare_program(c, std::move(prog), opt, out);
   if (!rc) (*out)->host_ms += front_ms;
   return rc;
 }
-
-// Set by lec_es_check_ex around its AUTO prepare: a cold kernel is then
-// not built synchronously (see check_race).
-thread_local bool t_check_race = false;
 
 // Device side of a plan for an already compiled program.
 int plan_prepare_program(lec_es_ctx *c, Program &&prog, const lec_es_options *opt, lec_es_plan **out) {
@@ -652,7 +656,8 @@ constexpr double kRaceSliceMs = 20.0;
 
 bool race_wanted(lec_es_ctx *c, const lec_es_plan *p, const lec_es_options *opt) {
   if (opt && (opt->tier != LEC_ES_TIER_AUTO || opt->grid_blocks || opt->block_threads || opt->flags)) return false;
-  if (p->tier == LEC_ES_TIER_JIT || !jit_eligible(p->prog) || jit_held(c, p->prog)) return false;
+  if (p->tier == LEC_ES_TIER_JIT || jit_held(c, p->prog)) return false;
+  if (!jit_eligible(p->prog) && !p->prog.lut.deferred) return false;
   const Program &g = p->prog;
   const uint64_t W = num_words(g.n);
   uint64_t wb = opt ? opt->word_begin : 0, we = opt ? std::min<uint64_t>(opt->word_end, W) : W;
@@ -661,13 +666,18 @@ bool race_wanted(lec_es_ctx *c, const lec_es_plan *p, const lec_es_options *opt)
   return t >= kRaceMinMs;
 }
 
-int check_race(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt, lec_es_result *out) {
+int check_race(lec_es_ctx *c, lec_es_plan *p, const lec_es_miter *m, const lec_es_options *opt, lec_es_result *out) {
   const Program &g = p->prog;
   const uint64_t W = num_words(g.n);
   const uint64_t wb = opt ? opt->word_begin : 0, we = opt ? std::min<uint64_t>(opt->word_end, W) : W;
   const double t_int = std::max(1e-3, cost_run_ms(c, LEC_ES_TIER_INTERP, g.cone_ands, g.n));
   const uint64_t slice = std::max<uint64_t>(1u << 16, (uint64_t)((double)W * kRaceSliceMs / t_int));
-  jit_lookup_or_schedule(c, g, true);
+  std::shared_ptr<CompactMiter> cone;
+  if (g.lut.deferred) {  // the build makes the table cover from its own copy of the cone
+    cone = std::make_shared<CompactMiter>();
+    if (compact_cone(MiterView{m->num_pis, m->num_ands, m->fanins, m->out_lit}, c->max_pis, *cone)) cone.reset();
+  }
+  jit_lookup_or_schedule(c, g, true, cone);
   lec_es_options o{};
   o.tier = LEC_ES_TIER_AUTO;
   double dev_ms = 0;
@@ -727,7 +737,7 @@ extern "C" int lec_es_check_ex(lec_es_ctx *c, const lec_es_miter *m, const lec_e
   t_check_race = false;
   if (rc) return rc;
   if (race_wanted(c, p, opt)) {
-    rc = check_race(c, p, opt, out);
+    rc = check_race(c, p, m, opt, out);
   } else {
     rc = plan_run_async(c, p, opt);
     if (!rc) rc = plan_result(c, p, out);

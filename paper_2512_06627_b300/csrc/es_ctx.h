@@ -142,7 +142,9 @@ int jit_launch(lec_es_ctx *c, lec_es_plan *p, uint64_t chunk_begin, uint64_t chu
 // schedules a background compile (once per program) and returns nullptr.
 // urgent: a single check races the interpreter against this build (it goes
 // to the front of the queue and builds its chain of layouts at once).
-lec::JitKernel *jit_lookup_or_schedule(lec_es_ctx *c, const Program &g, bool urgent = false);
+// cone: g's cone, needed when g's cover is deferred (the build makes it).
+lec::JitKernel *jit_lookup_or_schedule(lec_es_ctx *c, const Program &g, bool urgent = false,
+                                       std::shared_ptr<const CompactMiter> cone = nullptr);
 // Whether g's cone can run as a specialised kernel (a table cover whose live
 // set fits the register file).
 bool jit_eligible(const Program &g);
@@ -159,6 +161,10 @@ struct JitProbe {
   enum Use { kRun, kAuto, kBatch, kInfo };
   lec_es_ctx *c;
   Use use;  // kRun: the kernel tier was asked for; kAuto: the AUTO choice; kBatch: the batch's split; kInfo: facts only
+  // kAuto only: a cone that would get a cover gets none, and `deferred` is
+  // set (a one-off check builds the kernel in the background from the cone)
+  bool defer = false;
+  bool deferred = false;
 };
 bool jit_probe(void *arg, uint64_t hash, uint64_t hash2, uint32_t n, uint32_t cone_ands, KernelFacts *facts);
 // KernelProbe::want_cover for an AUTO caller: a cone whose interpreter run

@@ -48,6 +48,7 @@ struct LutProgram {
   uint32_t live = 0;                     // peak number of live values in this order
   uint32_t count = 0;                    // tables in the cover (order.size() unless elided)
   bool elided = false;                   // cover not built: the specialised kernel exists
+  bool deferred = false;                 // cover not built: a background build makes it from the cone
 };
 
 // Compiled cone (paper §3.3 "Instructionalized ES"): branch-free instruction

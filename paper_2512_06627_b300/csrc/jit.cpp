@@ -66,7 +66,12 @@ struct JitState {
   std::map<uint64_t, bool> scheduled;
   std::set<uint64_t> inflight;
   std::vector<std::thread> workers;
-  std::deque<std::pair<Program, bool>> todo;  // (program, build its chain of layouts at once)
+  struct Job {
+    Program prog;
+    bool urgent;                                // build its chain of layouts at once
+    std::shared_ptr<const CompactMiter> cone;   // for a program whose cover is deferred
+  };
+  std::deque<Job> todo;
   std::condition_variable cv, built;
   bool stop = false;
 };
@@ -1556,16 +1561,26 @@ void worker_loop(lec_es_ctx *c) {
   JitState *js = c->jit;
   for (;;) {
     Program g;
+    std::shared_ptr<const CompactMiter> cone;
     {
       std::unique_lock<std::mutex> lk(js->mu);
       js->cv.wait(lk, [&] { return js->stop || !js->todo.empty(); });
       if (js->stop) return;
-      g = std::move(js->todo.front().first);
-      t_single_build = js->todo.front().second;
+      g = std::move(js->todo.front().prog);
+      t_single_build = js->todo.front().urgent;
+      cone = std::move(js->todo.front().cone);
       js->todo.pop_front();
     }
     JitKernel *k = nullptr;
-    int rc = build_kernel(c, g, true, &k);
+    int rc = LEC_ES_OK;
+    if (g.lut.deferred) {  // the front end left the table cover to this build
+      Program full;
+      rc = cone ? compile_program(cone->view(), LEC_ES_ORDER_AUTO, 63, full) : LEC_ES_EINVAL;
+      if (!rc && (full.hash != g.hash || full.hash2 != g.hash2)) rc = LEC_ES_EINVAL;
+      if (!rc && !jit_eligible(full)) rc = LEC_ES_ETOOBIG;
+      if (!rc) g.lut = std::move(full.lut);
+    }
+    if (!rc) rc = build_kernel(c, g, true, &k);
     t_single_build = false;
     std::lock_guard<std::mutex> lk(js->mu);
     if (rc == LEC_ES_OK) {
@@ -1582,10 +1597,15 @@ void worker_loop(lec_es_ctx *c) {
 uint64_t cache_key(const Program &g, bool lut_form) { return g.hash ^ (lut_form ? 0x9E3779B97F4A7C15ull : 0ull); }
 
 bool jit_want_cover(void *arg, uint32_t n, uint32_t cone_ands) {
-  const JitProbe *p = (const JitProbe *)arg;
+  JitProbe *p = (JitProbe *)arg;
   if (p->use != JitProbe::kAuto) return true;
   constexpr double kCoverMinMs = 5.0;
-  return cost_run_ms(p->c, LEC_ES_TIER_INTERP, cone_ands, n) >= kCoverMinMs;
+  const bool want = cost_run_ms(p->c, LEC_ES_TIER_INTERP, cone_ands, n) >= kCoverMinMs;
+  if (want && p->defer) {
+    p->deferred = true;
+    return false;
+  }
+  return want;
 }
 
 bool jit_probe(void *arg, uint64_t hash, uint64_t hash2, uint32_t n, uint32_t cone_ands, KernelFacts *f) {
@@ -1686,7 +1706,8 @@ int jit_prepare(lec_es_ctx *c, lec_es_plan *p, const lec_es_options *opt) {
   return jit_attach(c, p, k, opt);
 }
 
-JitKernel *jit_lookup_or_schedule(lec_es_ctx *c, const Program &g, bool urgent) {
+JitKernel *jit_lookup_or_schedule(lec_es_ctx *c, const Program &g, bool urgent,
+                                  std::shared_ptr<const CompactMiter> cone) {
   JitState *js = state(c);
   std::lock_guard<std::mutex> lk(js->mu);
   const uint64_t key = cache_key(g, true);
@@ -1696,8 +1717,8 @@ JitKernel *jit_lookup_or_schedule(lec_es_ctx *c, const Program &g, bool urgent) 
     js->inflight.insert(key);
     // a single check waiting on it goes first, and builds its chain of
     // layouts at once (the host is otherwise idle then)
-    if (urgent) js->todo.emplace_front(g, true);
-    else js->todo.emplace_back(g, false);
+    if (urgent) js->todo.push_front(JitState::Job{g, true, std::move(cone)});
+    else js->todo.push_back(JitState::Job{g, false, std::move(cone)});
     if (js->workers.empty()) {
       const unsigned nw = std::max(1u, std::min(4u, std::thread::hardware_concurrency() / 2));
       for (unsigned i = 0; i < nw; i++) js->workers.emplace_back(worker_loop, c);
