@@ -111,17 +111,69 @@ def max_over_ranks(x: float, ws: int) -> float:
 # ---------------------------------------------------------------------------
 
 class ClockSampler:
+    """SM clock and throttle reasons while the timed region runs: NVML read
+    every ~2 ms from a thread (the timed region of a few steps lasts tens of
+    milliseconds), nvidia-smi at its 200 ms floor beside it as a fallback.
+    Reads only; changes no GPU setting."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, device: int):
         self.device = device
         self.proc = None
         self.lines = []
         self.th = None
+        self.nv = []          # (sm MHz, max sm MHz, reasons bitmask)
+        self.nv_th = None
+        self.running = False
+        self.nvml = None
+        self.handle = None
+        self.bits = {}
+
+    def _nvml_handle(self):
+        """NVML through ctypes (libnvidia-ml ships with the driver): the
+        handle of this CUDA device, found by its PCI address."""
+        import ctypes
+        import torch
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        pr = torch.cuda.get_device_properties(self.device)
+        bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0".encode()
+        if nv.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(h)) != 0 and \
+                nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.device), ctypes.byref(h)) != 0:
+            raise RuntimeError("no NVML handle")
+        self.nvml, self.handle = nv, h
+        # nvmlClocksEventReason* bits of the NVML API
+        self.bits = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20,
+                     "sw_power_cap": 0x4}
+
+    def _poll(self):
+        import ctypes
+        nv, h = self.nvml, self.handle
+        sm_clock = 1  # NVML_CLOCK_SM
+        v, mxv, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        mx = float(mxv.value) if nv.nvmlDeviceGetMaxClockInfo(h, sm_clock, ctypes.byref(mxv)) == 0 else None
+        get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        while self.running:
+            if nv.nvmlDeviceGetClockInfo(h, sm_clock, ctypes.byref(v)) != 0:
+                return
+            r = int(rs.value) if get_reasons(h, ctypes.byref(rs)) == 0 else 0
+            self.nv.append((float(v.value), mx, r))
+            time.sleep(0.002)
 
     def start(self):
+        try:
+            self._nvml_handle()
+            self.running = True
+            self.nv_th = threading.Thread(target=self._poll, daemon=True)
+            self.nv_th.start()
+        except Exception:
+            self.nvml = None
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -137,17 +189,26 @@ class ClockSampler:
             self.lines.append(ln.strip())
 
     def stop(self) -> dict:
+        self.running = False
+        if self.nv_th:
+            self.nv_th.join(timeout=2)
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.th:
+                self.th.join(timeout=2)
+        if self.nv:
+            reasons = sorted(nm for nm in self.NAMES if any(r & self.bits[nm] for _, _, r in self.nv if self.bits[nm]))
+            mxs = [m for _, m, _ in self.nv if m]
+            return {"sm_mhz": statistics.median(c for c, _, _ in self.nv), "sm_max_mhz": max(mxs) if mxs else None,
+                    "reasons": reasons, "samples": len(self.nv), "source": "NVML every ~2 ms in the timed region",
+                    "sm_mhz_min": min(c for c, _, _ in self.nv)}
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        if self.th:
-            self.th.join(timeout=2)
         sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
@@ -157,11 +218,11 @@ class ClockSampler:
                 mx.append(float(parts[2]))
             except ValueError:
                 continue
-            for nm, val in zip(names, parts[5:9]):
+            for nm, val in zip(self.NAMES, parts[5:9]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi -lms 200"}
 
 
 def measured_peaks() -> dict:
@@ -749,7 +810,6 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     sampler = ClockSampler(dev)
     sampler.start()
-    time.sleep(0.3)
     step_ms, kern_ms = [], []
     for _ in range(args.steps):
         with torch.cuda.stream(st):
