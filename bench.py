@@ -754,8 +754,19 @@ def measure_serve_full(ctx, args):
     assert [r.verdict for r in res] == want
     rng = np.random.default_rng(11)
     sample = sorted(rng.choice(R, size=min(R, 200), replace=False).tolist())
+    # the ES time model's prediction for each sampled request, made before
+    # it runs alone, against its device time
+    errs = {L.TIER_INTERP: [], L.TIER_JIT: []}
     for i in sample:
-        assert L.lec_es_check(ctx, ms[i]).cex == res[i].cex
+        pr = L.lec_es_cost_predict(ctx, ms[i], os.cpu_count() or 1)
+        r1 = L.lec_es_check(ctx, ms[i])
+        assert r1.cex == res[i].cex
+        if r1.verdict == L.EQUIVALENT and r1.device_ms > 0 and r1.tier in errs:
+            errs[r1.tier].append(abs((pr.jit_ms if r1.tier == L.TIER_JIT else pr.interp_ms) / r1.device_ms - 1.0))
+    cost = {name: {"requests": len(errs[t]),
+                   "median_rel_err": float(np.median(errs[t])) if errs[t] else None,
+                   "p90_rel_err": float(np.percentile(errs[t], 90)) if errs[t] else None}
+            for t, name in ((L.TIER_INTERP, "interp"), (L.TIER_JIT, "jit"))}
     lat = np.array([r.latency_ms for r in res])
     return {
         "requests": R, "distinct_programs": len(uniq), "mutants": int(sum(r.mutant for r in base)),
@@ -764,6 +775,7 @@ def measure_serve_full(ctx, args):
         "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
         "p999_latency_ms": float(np.percentile(lat, 99.9)),
         "verdicts_match_generator": True, "sample_equal_alone": len(sample), "jit_warmup_s": warm_s,
+        "cost_model": cost,
     }
 
 
