@@ -79,7 +79,7 @@ struct JitState {
 namespace {
 
 constexpr int kJitBlock = 128;
-constexpr int kCodegenVersion = 22;  // part of cached cubin names: bump whenever the generated code changes
+constexpr int kCodegenVersion = 23;  // part of cached cubin names: bump whenever the generated code changes
 // Values computed at one loop level and read at a deeper one: at most
 // kHoistPlan of them (see plan_hoist), those read by the innermost loop in
 // registers, the others in up to kHoistShared shared-memory slots per
@@ -589,11 +589,17 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   }
   // The innermost U levels are unrolled: straight-line copies, one per value
   // of their pass PIs (at most max_copies passes and 4,096 table
-  // evaluations before folding); levels 1..Lr stay loops.  Four copies
-  // measured best on the 16x16 miter (two: 3.72 ms, four: 3.48 ms, eight:
-  // 4.10 ms -- a 90 KB kernel).  LEC_ES_JIT_UNROLL sets the copies (0: none).
+  // evaluations before folding); levels 1..Lr stay loops.  A cone whose
+  // tables keep many values live is register-bound: four copies measured
+  // best on the 16x16 miter (live set 198; two: 3.72 ms, four: 3.48 ms,
+  // eight: 4.10 ms -- a 90 KB kernel).  One with at most kFewLive live
+  // values gets up to 64 (node-pair miters of 26-28 PIs, live sets 30-73:
+  // four copies 0.019-0.078 ms, 8-64 copies 0.015-0.045 ms).
+  // LEC_ES_JIT_UNROLL sets the most copies (0: none).
+  constexpr uint32_t kFewLive = 96;
   const char *unroll_env = getenv("LEC_ES_JIT_UNROLL");
-  const uint32_t max_copies = unroll_env ? (uint32_t)std::max(0, atoi(unroll_env)) : 4u;
+  const uint32_t max_copies =
+      unroll_env ? (uint32_t)std::max(0, atoi(unroll_env)) : (lp.live <= kFewLive ? 64u : 4u);
   uint32_t U = 0;
   {
     uint64_t copies = 1, evals = 0;
