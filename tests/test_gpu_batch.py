@@ -126,8 +126,10 @@ def test_every_mutated_pair_and_sampled_ranges_of_heavy_pairs_vs_oracle(ctx, pai
 def test_spread_batch_equals_single_and_oracle():
     """The batched workload at its stated spread (10..28 PIs, node pairs up
     to whole four-multiplier miters): one prepared batch gives every miter's
-    lec_es_check result, and the oracle's -- on every miter of up to 16 PIs,
-    every mutant, and a seeded sample of the rest."""
+    lec_es_check result, and the oracle's -- all 1,024 against the oracle's
+    stored results (tests/golden/make_spread_oracle.py; the fingerprint pins
+    the inputs), and live on every miter of up to 16 PIs, every mutant and a
+    seeded sample of the rest."""
     import os
     from tests.gpu_common import make_ctx
     ctx = make_ctx()
@@ -151,5 +153,11 @@ def test_spread_batch_equals_single_and_oracle():
                 assert r.cex_or_none == want, i
                 checked += 1
         assert checked >= 20 and any(r.cex_or_none is not None for r in got)
+        import json
+        from tests.golden.make_spread_oracle import NUM, OUT, SEED, fingerprint
+        assert (NUM, SEED) == (1024, 9)
+        stored = json.load(open(OUT))
+        assert stored["fingerprint"] == fingerprint(trip)
+        assert [r.cex_or_none for r in got] == stored["cex"]
     finally:
         L.lec_es_destroy(ctx)

@@ -395,3 +395,24 @@ def test_stored_node_pair_results_are_current():
     assert any(stored["cex"][i] is not None for i in sample)
     for i in sorted(set(sample)):
         assert O.check(a.num_pis, a.fanins, a.outputs[i])[0] == stored["cex"][i], i
+
+
+def test_stored_spread_results_are_current():
+    """The stored oracle results of the 1,024-miter spread batch (written by
+    tests/golden/make_spread_oracle.py) belong to the miters the generator
+    builds today, and a seeded sample of the small ones (plus every
+    non-equivalent one of up to 18 PIs) re-checks."""
+    from tests.golden.make_spread_oracle import NUM, OUT, SEED, fingerprint
+    trip = C.config4_spread(num=NUM, seed=SEED)
+    stored = json.load(open(OUT))
+    assert stored["fingerprint"] == fingerprint(trip)
+    assert len(stored["cex"]) == len(trip) == NUM
+    sup = [len(O.support(a.num_pis, a.fanins, o)[0]) for a, o, _ in trip]
+    small = [i for i, s in enumerate(sup) if s <= 18]
+    rng = np.random.default_rng(6)
+    sample = [i for i in small if stored["cex"][i] is not None]
+    sample += [int(i) for i in rng.choice(small, size=min(30, len(small)), replace=False)]
+    assert any(stored["cex"][i] is not None for i in sample)
+    for i in sorted(set(sample)):
+        a, o, _ = trip[i]
+        assert O.check(a.num_pis, a.fanins, o)[0] == stored["cex"][i], i
