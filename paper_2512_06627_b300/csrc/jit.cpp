@@ -79,7 +79,7 @@ struct JitState {
 namespace {
 
 constexpr int kJitBlock = 128;
-constexpr int kCodegenVersion = 23;  // part of cached cubin names: bump whenever the generated code changes
+constexpr int kCodegenVersion = 24;  // part of cached cubin names: bump whenever the generated code changes
 // Values computed at one loop level and read at a deeper one: at most
 // kHoistPlan of them (see plan_hoist), those read by the innermost loop in
 // registers, the others in up to kHoistShared shared-memory slots per
@@ -103,6 +103,19 @@ constexpr uint32_t kDryPlan = 160;  // plan of the layout search's dry runs (see
 // build at once, instead of the rest only after the first spills.
 thread_local bool t_single_build = false;
 constexpr uint32_t kMaxJitLive = 230;        // table live set that still fits the register file
+// A cone whose tables keep at most kFewLive values live is not register-bound:
+// its innermost pass levels unroll into up to 64 copies, and the passes run
+// in straight-line groups of up to kGroupPasses passes and kGroupEvals table
+// evaluations (gen_ptx_lut).  Measured on the 4,096-pair batch and the
+// 4,096-miter spread batch (batch ms / preparation s): no groups 3.83 / 2.8
+// and 24.8 / 19.6; groups of 8 passes with at most 256, 512, 1,024 or any
+// number of evaluations 2.61 / 1.8 and 21.0 / 19.0, 2.59 / 1.9 and 20.1 /
+// 28.1, 2.59 / 1.9 and 19.7 / 40.1, 2.58 / 1.9 and 19.8 / 45.8 (longer
+// straight-line blocks cost the PTX compiler more); groups of 4: 2.72 / 2.6
+// and 20.1 / 40.4.
+constexpr uint32_t kFewLive = 96;
+constexpr uint32_t kGroupPasses = 8;
+constexpr uint64_t kGroupEvals = 512;
 
 // The counterexample word (a pattern; UINT64_MAX while none is known) as
 // the first 32-pattern chunk it rules out, ceil(cex / 32), kept in %d12
@@ -596,7 +609,6 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   // values gets up to 64 (node-pair miters of 26-28 PIs, live sets 30-73:
   // four copies 0.019-0.078 ms, 8-64 copies 0.015-0.045 ms).
   // LEC_ES_JIT_UNROLL sets the most copies (0: none).
-  constexpr uint32_t kFewLive = 96;
   const char *unroll_env = getenv("LEC_ES_JIT_UNROLL");
   const uint32_t max_copies =
       unroll_env ? (uint32_t)std::max(0, atoi(unroll_env)) : (lp.live <= kFewLive ? 64u : 4u);
@@ -727,7 +739,7 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     << "  .reg .pred %p<16>;\n  .reg .b32 %t<26>;\n  .reg .b64 %d<40>;\n  .reg .b32 %j<" << L << ">;\n"
     << "  .reg .b64 %o<" << L << ">;\n"
     << "  .reg .b32 %v<" << (NA + 1) << ">;\n  .reg .b32 %s<" << (NA + 1) << ">;\n  .reg .b32 %q<" << (NP + 1)
-    << ">;\n";
+    << ">;\n  .reg .b32 %po<" << kGroupPasses << ">;\n";
   if (nsmem) s << "  .shared .align 16 .b32 hs[" << nsmem * kJitBlock << "];\n";
   if (dump) s << "  .reg .b32 %z<2>;\n  ld.param.u64 %d38, [p_tt];\n  cvta.to.global.u64 %d38, %d38;\n";
   // parameters; grab range [d8, d9); lane; first grab; first counterexample poll
@@ -947,6 +959,59 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     uint32_t ncopy = 0;                // pass copies emitted (label numbers)
     uint32_t nouter = 0;               // checked copies of outer unrolled levels (label numbers)
     unrolled_lop3 = 0;
+    // Pass groups (a cone with few live values, not the dump): the passes
+    // under one copy of level Lg -- at most kGroupPasses -- are one
+    // straight-line block, with no skip check or output branch between them
+    // (so their independent table chains interleave): each pass's output is
+    // kept in %po<k>, and one check after the group looks at them (pass by
+    // pass only in a partial grab, or when one of them fails).  The group is
+    // skipped or run as a whole.
+    uint32_t Lg = L + 1;  // L + 1: no groups
+    if (!dump && lp.live <= kFewLive)
+      for (uint32_t lv = Lr + 1; lv <= L && Lg == L + 1; lv++) {
+        uint64_t per = 1, evals = 0;  // passes and table evaluations in one group
+        for (uint32_t l2 = lv; l2 <= L; l2++) {
+          per <<= __builtin_popcountll(grp[l2 - 1]);
+          evals += (uint64_t)std::count(level.begin(), level.end(), (uint8_t)l2) * per;
+        }
+        if (per >= 2 && per <= kGroupPasses && evals <= kGroupEvals) Lg = lv;
+      }
+    struct GroupPass {
+      uint64_t o;   // chunk offset of the pass
+      bool never;   // its output folds to 0
+    };
+    std::vector<GroupPass> gp;  // passes of the open group
+    bool in_group = false;
+    uint32_t ngroup = 0;
+    const uint32_t vmask_g = g.n >= 5 ? 0xFFFFFFFFu : ((1u << (1u << g.n)) - 1u);
+    auto flush_group = [&]() {
+      const std::string G = std::to_string(ngroup++);
+      // a partial grab: lanes outside [cb, ce) neither fail nor count
+      s << "  @%p12 bra.uni $GF" << G << ";\n";
+      for (size_t k = 0; k < gp.size(); k++) {
+        const std::string P = "%po" + std::to_string(k);
+        s << "  add.u64 %d27, " << base << ", " << gp[k].o << ";\n  add.u64 %d19, %d27, %d18;\n"
+          << "  setp.ge.u64 %p5, %d19, %d2;\n  setp.lt.u64 %p11, %d19, %d1;\n  or.pred %p5, %p5, %p11;\n"
+          << "  @%p5 mov.b32 " << P << ", 0;\n  selp.u64 %d24, 0, 1, %p5;\n  add.u64 %d10, %d10, %d24;\n";
+      }
+      s << "$GF" << G << ":\n  mov.b32 %t7, 0;\n";
+      for (size_t k = 0; k < gp.size(); k++)
+        if (!gp[k].never) s << "  or.b32 %t7, %t7, %po" << k << ";\n";
+      s << "  setp.ne.u32 %p6, %t7, 0;\n  vote.sync.any.pred %p7, %p6, -1;\n  @!%p7 bra.uni $GE" << G << ";\n";
+      for (size_t k = 0; k < gp.size(); k++) {  // a failure (rare): each pass's lowest failing lane
+        if (gp[k].never) continue;
+        const std::string P = "%po" + std::to_string(k), N = "$GN" + G + "_" + std::to_string(k);
+        s << "  setp.ne.u32 %p6, " << P << ", 0;\n  vote.sync.ballot.b32 %t8, %p6, -1;\n  setp.eq.u32 %p7, %t8, 0;\n"
+          << "  @%p7 bra " << N << ";\n  neg.s32 %t9, %t8;\n  and.b32 %t9, %t9, %t8;\n  bfind.u32 %t10, %t9;\n"
+          << "  setp.ne.u32 %p7, %t10, %t2;\n  @%p7 bra " << N << ";\n"
+          << "  add.u64 %d27, " << base << ", " << gp[k].o << ";\n  add.u64 %d19, %d27, %d18;\n"
+          << "  neg.s32 %t11, " << P << ";\n  and.b32 %t11, %t11, " << P << ";\n  bfind.u32 %t12, %t11;\n"
+          << "  cvt.u64.u32 %d21, %t12;\n  shl.b64 %d22, %d19, 5;\n  add.u64 %d22, %d22, %d21;\n"
+          << "  atom.global.min.u64 %d23, [%d3], %d22;\n" << N << ":\n";
+      }
+      s << "$GE" << G << ":\n";
+      gp.clear();
+    };
     auto value = [&](int32_t v, uint8_t lv) -> SVal {  // a leaf's value in the current copy
       SVal x;
       if (v < 0 || isconst[v]) {
@@ -1037,6 +1102,8 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
       dump_store(i, base, o, r.imm ? std::string(imm) : r.reg, r.imm, r.inv, lv);
     };
     auto unrolled = [&](auto &&self, uint32_t lv, uint64_t off) -> void {
+      const bool opens = lv == Lg && !in_group;
+      if (opens) in_group = true;
       std::vector<uint32_t> pis;  // this level's pass PIs in rank order (ascending)
       for (uint32_t k = 10; k < NP; k++)
         if ((grp[lv - 1] >> k) & 1u) pis.push_back(k);
@@ -1051,7 +1118,7 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
           // a copy that starts at or above the counterexample's chunk
           // (o >= %t23) skips its tables and every pass below it; the
           // first copy (o = off) starts where its parent does, checked there
-          const bool chk = o != off && o <= 0xFFFFFFFEull;
+          const bool chk = o != off && o <= 0xFFFFFFFEull && !in_group;
           const std::string U = std::to_string(nouter);
           if (chk) {
             nouter++;
@@ -1067,6 +1134,22 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
             }
           self(self, lv + 1, o);
           if (chk) s << "$UE" << U << ":\n";
+        } else if (in_group) {  // a pass of a group: its tables and its output, kept in %po<k>
+          ncopy++;
+          std::fill(loaded.begin(), loaded.end(), (uint8_t)0);
+          for (size_t i = 0; i < lp.order.size(); i++)
+            if (level[i] == L && !isconst[lp.order[i].node]) emit_spec(lp.order[i], (uint8_t)L);
+          const SVal out = value(lp.root < 0 ? -1 : (int32_t)lp.root, (uint8_t)L);
+          const uint32_t outc = g.out_compl ? 0xFFFFFFFFu : 0u;
+          const bool never = out.imm && ((out.imm_v ^ outc) & vmask_g) == 0;
+          const std::string P = "%po" + std::to_string(gp.size());
+          if (out.imm)
+            snprintf(buf, sizeof(buf), "  mov.b32 %s, 0x%08x;\n", P.c_str(), (out.imm_v ^ outc) & vmask_g);
+          else
+            snprintf(buf, sizeof(buf), "  xor.b32 %s, %s, 0x%08x;\n  and.b32 %s, %s, 0x%08x;\n", P.c_str(),
+                     out.reg.c_str(), out.inv ? ~outc : outc, P.c_str(), P.c_str(), vmask_g);
+          s << buf;
+          gp.push_back(GroupPass{o, never});
         } else {  // a pass: its range work, its tables, its output check
           const std::string J = std::to_string(ncopy++);
           const std::string chunk = "  add.u64 %d27, " + base + ", " + std::to_string(o) + ";\n";
@@ -1120,6 +1203,10 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
         }
         sv = saved;
         for (uint32_t r = 0; r < pis.size(); r++) pic[pis[r]] = -1;
+      }
+      if (opens) {
+        flush_group();
+        in_group = false;
       }
     };
     // %t23: the counterexample's chunk minus base, at most 2^32 - 1 (base is
