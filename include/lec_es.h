@@ -411,6 +411,9 @@ typedef struct {
   uint32_t final_support;   /* PIs of the output's remaining cone */
   uint32_t decided_by;      /* 0 the output became a constant, 1 random simulation, 2 the final ES check, 3 undecided */
   double sim_ms, es_ms, host_ms, total_ms;
+  uint32_t rounds_reused;   /* rounds that checked the previous round's uncut candidates without
+                               simulating again (it had refuted at most a tenth of its pairs) */
+  uint32_t pad;
 } lec_es_sweep_result;
 
 /* Sweep a miter (no counterpart entry point in the paper; its flow, §2.3,

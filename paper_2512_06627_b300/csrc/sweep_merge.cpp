@@ -12,7 +12,10 @@
 // pairs, and finally the miter's output, collapse, which proves miters whose
 // output has far too many PIs to enumerate (64-PI multipliers).
 //
-// Per round, on the working AIG g (the output's cone, structurally hashed):
+// Per round, on the working AIG g (the output's cone, structurally hashed)
+// (a round after one that refuted at most a tenth of its pairs skips the
+// first two steps and takes that round's uncut candidates, mapped into the
+// rebuilt graph -- no random words of its own, so no new refutations):
 //   * simulate every node on fresh random words (GPU, sweep.cu) with
 //     phase-normalised hashes; a nonzero output signature is a real
 //     counterexample and ends the sweep;
@@ -88,8 +91,10 @@ struct Strash {
 };
 
 // g with the substitutions (subst[v] = replacement literal in g's numbering,
-// from a lower variable) applied, then only the output's cone kept.
-Graph rebuild(const Graph &g, const std::vector<uint32_t> &subst) {
+// from a lower variable) applied, then only the output's cone kept.  If
+// vmap is given, (*vmap)[v] is the literal of g's variable v in the result,
+// or kNone if v's function is no longer in the output's cone.
+Graph rebuild(const Graph &g, const std::vector<uint32_t> &subst, std::vector<uint32_t> *vmap = nullptr) {
   Graph t;
   t.P = g.P;
   t.orig.assign(g.orig.begin(), g.orig.begin() + g.P + 1);
@@ -132,6 +137,13 @@ Graph rebuild(const Graph &g, const std::vector<uint32_t> &subst) {
     r.orig.push_back(t.orig[v]);
   }
   r.out = 2u * ren[out >> 1] | (out & 1u);
+  if (vmap) {
+    vmap->assign(V, kNone);
+    for (uint32_t v = 0; v < V; v++) {
+      const uint32_t tv = map[v] >> 1;
+      if (tv <= t.P || keep[tv]) (*vmap)[v] = 2u * ren[tv] | (map[v] & 1u);
+    }
+  }
   return r;
 }
 
@@ -310,12 +322,22 @@ extern "C" int lec_es_sweep(lec_es_ctx *c, const lec_es_miter *m, const lec_es_s
     std::vector<uint32_t> touched;
     Heap heap, heap2;
     uint32_t idle = 0;
+    // candidates of the previous round that were not cut, in g's numbering;
+    // a round that proved nearly all its pairs hands them on instead of
+    // simulating again (its classes are still true: nothing was refuted)
+    std::vector<Region> pending;
+    bool reuse = false;
     for (uint32_t round = 0; round < max_rounds; round++) {
       if ((g.out >> 1) == 0) break;  // the output is a constant
       out->rounds = round + 1;
       const uint32_t V = g.vars();
-      // (1) random simulation
       auto t0 = std::chrono::steady_clock::now();
+      std::vector<Region> cands;
+      if (reuse) {
+        cands = std::move(pending);
+        out->rounds_reused++;
+      } else {
+      // (1) random simulation
       Rng rng(seed ^ (0xA5A5A5A5ull + round * 0x100000001B3ull));
       words.resize((size_t)g.P * nwords);
       for (auto &w : words) w = rng.next();
@@ -358,11 +380,6 @@ extern "C" int lec_es_sweep(lec_es_ctx *c, const lec_es_miter *m, const lec_es_s
           if ((a[w] ^ f) != b[w]) return false;
         return true;
       };
-      level.assign(V, 0);
-      for (uint32_t v = g.P + 1; v < V; v++)
-        level[v] = std::max(level[g.fan[2 * (v - g.P - 1)] >> 1], level[g.fan[2 * (v - g.P - 1) + 1] >> 1]) + 1;
-      mask.assign(V, 0);
-      std::vector<Region> cands;
       for (size_t i = 0; i < order.size();) {
         size_t j = i + 1;
         while (j < order.size() && hash[order[j]] == hash[order[i]]) j++;
@@ -385,6 +402,12 @@ extern "C" int lec_es_sweep(lec_es_ctx *c, const lec_es_miter *m, const lec_es_s
         }
         i = j;
       }
+      }  // simulation and classes
+      pending.clear();
+      level.assign(V, 0);
+      for (uint32_t v = g.P + 1; v < V; v++)
+        level[v] = std::max(level[g.fan[2 * (v - g.P - 1)] >> 1], level[g.fan[2 * (v - g.P - 1) + 1] >> 1]) + 1;
+      mask.assign(V, 0);
       // lowest pairs first; a long run of pairs whose regions are too wide
       // means the merged frontier is below them, so the rest wait for the
       // next round
@@ -405,12 +428,19 @@ extern "C" int lec_es_sweep(lec_es_ctx *c, const lec_es_miter *m, const lec_es_s
       }
       std::vector<Region> regions;
       for (size_t i = 0; i < cands.size(); i++) {
-        if (cut_ok[i]) regions.push_back(std::move(cands[i]));
-        else out->pairs_skipped++;
+        if (cut_ok[i]) {
+          regions.push_back(std::move(cands[i]));
+        } else {
+          out->pairs_skipped++;
+          pending.push_back(std::move(cands[i]));
+        }
       }
       if (regions.empty()) {
         out->host_ms += ms_since(t0);
-        break;
+        if (!reuse) break;
+        reuse = false;  // the handed-on candidates all stay too wide: simulate afresh
+        pending.clear();
+        continue;
       }
       const double t_cut = ms_since(t0) - t_class;
       // (3) one AIG holding every local sub-miter: leaf i of a region is PI
@@ -448,7 +478,7 @@ extern "C" int lec_es_sweep(lec_es_ctx *c, const lec_es_miter *m, const lec_es_s
       out->host_ms += ms_since(t0);
       t0 = std::chrono::steady_clock::now();
       std::vector<lec_es_result> br(regions.size());
-      rc = lec_es_batch(c, bm.data(), bm.size(), br.data());
+      const int rc = lec_es_batch(c, bm.data(), bm.size(), br.data());
       if (rc) return rc;
       out->es_ms += ms_since(t0);
       t0 = std::chrono::steady_clock::now();
@@ -467,7 +497,33 @@ extern "C" int lec_es_sweep(lec_es_ctx *c, const lec_es_miter *m, const lec_es_s
         proven++;
       }
       out->pairs_proven += proven;
-      if (proven) g = rebuild(g, subst);
+      // the next round reuses the uncut candidates if this one refuted
+      // (almost) nothing, mapped into the rebuilt graph: a pair whose two
+      // sides became one node, or left the output's cone, drops out
+      const bool next_reuse = proven && (uint64_t)proven * 10 >= (uint64_t)regions.size() * 9 && !pending.empty();
+      if (proven) {
+        std::vector<uint32_t> vmap;
+        g = rebuild(g, subst, next_reuse ? &vmap : nullptr);
+        if (next_reuse) {
+          std::vector<uint8_t> taken(g.vars(), 0);  // a member takes one representative
+          size_t k = 0;
+          for (Region &r : pending) {
+            uint32_t a = vmap[r.rep], b = vmap[r.mem];
+            if (a == kNone || b == kNone || (a >> 1) == (b >> 1)) continue;
+            if ((a >> 1) > (b >> 1)) std::swap(a, b);
+            if ((b >> 1) <= g.P || taken[b >> 1]) continue;
+            taken[b >> 1] = 1;
+            Region nr;
+            nr.rep = a >> 1;
+            nr.mem = b >> 1;
+            nr.phase = r.phase ^ (a & 1u) ^ (b & 1u);
+            pending[k++] = std::move(nr);
+          }
+          pending.resize(k);
+        }
+      }
+      reuse = next_reuse && !pending.empty();
+      if (!reuse) pending.clear();
       const double t_merge = ms_since(t0);
       out->host_ms += t_merge;
       if (log)

@@ -110,7 +110,7 @@ class lec_es_sweep_result(ctypes.Structure):
                 ("pairs_skipped", ctypes.c_uint64), ("ands_initial", ctypes.c_uint32),
                 ("ands_final", ctypes.c_uint32), ("final_support", ctypes.c_uint32), ("decided_by", ctypes.c_uint32),
                 ("sim_ms", ctypes.c_double), ("es_ms", ctypes.c_double), ("host_ms", ctypes.c_double),
-                ("total_ms", ctypes.c_double)]
+                ("total_ms", ctypes.c_double), ("rounds_reused", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
 _lib: Optional[ctypes.CDLL] = None
