@@ -369,3 +369,61 @@ def test_cold_check_races_interpreter_against_kernel_build():
         assert r.verdict == L.EQUIVALENT
     finally:
         L.lec_es_destroy(c)
+
+
+def _plant(aig, out, p):
+    """aig with one more output: out XOR (the minterm of pattern p over out's
+    support), so with out equivalent to 0 the only failing pattern is p."""
+    from paper_2512_06627_b300.circuits import Aig
+    sup, _ = O.support(aig.num_pis, aig.fanins, out)
+    rows = [tuple(int(x) for x in r) for r in np.asarray(aig.fanins)]
+    base = aig.num_pis + len(rows)
+
+    def new_and(x, y):
+        rows.append((x, y))
+        return 2 * (aig.num_pis + len(rows))
+    m = 1  # constant 1
+    for k, pi in enumerate(sup):
+        lit = 2 * (pi + 1) + (0 if (p >> k) & 1 else 1)
+        m = lit if m == 1 else new_and(m, lit)
+    x = new_and(new_and(out, m ^ 1) ^ 1, new_and(out ^ 1, m) ^ 1) ^ 1
+    assert base < x // 2
+    return Aig(aig.num_pis, np.array(rows, dtype=np.uint32), [x]), len(sup)
+
+
+def test_grouped_passes_find_planted_minterms_in_ranges(ctx):
+    """Specialised kernels of small-live cones run their passes in groups
+    with one output check per group.  On equivalent 28-PI node-pair miters
+    with one failing pattern planted (at low bits, in pass PIs, at the end of
+    the space), the kernel returns exactly that pattern over the whole space
+    and over ranges that start and end next to it (partial grabs), and
+    nothing over a range that leaves it out -- the closed form, and the
+    oracle's answer on the ranges."""
+    import json
+    from tests.golden.make_config4_oracle import OUT
+    pb = C.config4_pairs()
+    stored = json.load(open(OUT))["cex"]
+    f = pb.aig.flat_fanins()
+    picks = []
+    for i, o in enumerate(pb.aig.outputs):
+        if stored[i] is None and not pb.mutated[i]:
+            info = L.lec_es_compile(L.Miter(pb.aig.num_pis, f, o))[0]
+            if info.n == 28 and info.lut_live <= 80:
+                picks.append(i)
+    assert len(picks) >= 2
+    for i in picks[:2]:
+        for p in (12345, (1 << 20) + 7, (1 << 24) + 99, (3 << 25) + 5, (1 << 27) + (1 << 23) + 3, (1 << 28) - 1):
+            aig, n = _plant(pb.aig, pb.aig.outputs[i], p)
+            assert n == 28
+            m = L.Miter(aig.num_pis, aig.flat_fanins(), aig.outputs[0])
+            r = L.lec_es_check_ex(ctx, m, L.options(tier=L.TIER_JIT))
+            assert r.cex_or_none == p, (i, p)
+            w = p // 64
+            W = 1 << 22
+            for wb, we in ((max(0, w - 3), min(W, w + 4)), (w, w + 1), (w + 1, W), (0, w)):
+                if wb >= we:
+                    continue
+                g = L.lec_es_check_ex(ctx, m, L.options(wb, we, L.TIER_JIT))
+                want = p if wb <= w < we else None
+                assert g.cex_or_none == want, (i, p, wb, we)
+            assert O.check(aig.num_pis, aig.fanins, aig.outputs[0], max(0, w - 3), w + 4)[0] == p
