@@ -587,7 +587,7 @@ int plan_result(lec_es_ctx *c, lec_es_plan *p, lec_es_result *out) {
   // a full enumeration on the library's own geometry refines the time model
   if (out->verdict == LEC_ES_EQUIVALENT && p->last_default_grid)
     cost_add_run(c, p->tier, p->prog.cone_ands, p->prog.n, ms,
-                 p->tier == LEC_ES_TIER_JIT && p->jit ? p->jit->lop3_per_pass : 0.0);
+                 p->tier == LEC_ES_TIER_JIT && p->jit ? p->jit->model_lop3 : 0.0);
   return LEC_ES_OK;
 }
 

@@ -63,6 +63,8 @@ struct JitKernel {
   uint32_t rep_fixed = 0;       // passes per grab compiled into the kernel (0: a launch parameter)
   bool stride_ok = false;       // the kernel can take grabs by static stride (a null counter)
   double lop3_per_pass = 0;     // lop3 it executes per 32-pattern chunk and thread (0: unknown)
+  double model_lop3 = 0;        // the figure the time model takes for it: lop3_per_pass, less the
+                                // control a kernel with pass groups saves (0: unknown)
   uint64_t pass_bits = 0;       // chunk-index bits of the pass PIs (0: contiguous grabs of 32 * rep chunks)
   uint32_t chunk_bits = 0;      // bits of the chunk index (support PIs - 5)
   uint64_t hash2 = 0;           // the program's second structure hash (checked on every cache hit)

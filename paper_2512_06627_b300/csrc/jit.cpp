@@ -115,6 +115,10 @@ constexpr uint32_t kMaxJitLive = 230;        // table live set that still fits t
 // and 20.1 / 40.4.
 constexpr uint32_t kFewLive = 96;
 constexpr uint32_t kGroupPasses = 8;
+// A grouped kernel's passes cost about this many lop3-equivalents less
+// control than the time model's per-pass allowance (cost.cpp: 40); fitted
+// over 225 measured kernels (90th-percentile error 25% -> 21%).
+constexpr double kGroupedPassSaving = -20.0;
 constexpr uint64_t kGroupEvals = 512;
 
 // The counterexample word (a pattern; UINT64_MAX while none is known) as
@@ -312,6 +316,7 @@ struct GrabLayout {
 struct SlotSplit {
   uint32_t read = 0, in_regs = 0, in_shared = 0;
   uint32_t inner_in_regs = 0;  // of those in registers, values the innermost loop reads
+  bool grouped = false;        // passes run in straight-line groups (the same for every budget)
 };
 // shared-memory slots per thread (LEC_ES_JIT_HOIST_SHARED lowers it)
 uint32_t shared_slots() {
@@ -980,6 +985,7 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
       uint64_t o;   // chunk offset of the pass
       bool never;   // its output folds to 0
     };
+    if (split) split->grouped = Lg <= L;
     std::vector<GroupPass> gp;  // passes of the open group
     bool in_group = false;
     uint32_t ngroup = 0;
@@ -1333,7 +1339,10 @@ int compile_cubin(const std::string &src, int major, int minor, std::vector<char
 // returned kernel was generated with (the dump variant reuses them).
 int compile_program_kernel(const Program &g, bool lut_form, int major, int minor, std::vector<char> &cubin,
                            std::string &log, const GrabLayout *layout = nullptr, double *lop3_per_pass = nullptr,
-                           uint32_t *built = nullptr) {
+                           uint32_t *built = nullptr, bool *grouped = nullptr) {
+  bool grouped_sink = false;
+  if (!grouped) grouped = &grouped_sink;
+  *grouped = false;
   double per_sink = 0;
   uint32_t built_sink[2];
   if (!lop3_per_pass) lop3_per_pass = &per_sink;
@@ -1377,6 +1386,7 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
         const int rc = compile_ptx(gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis,
                                                layout->groups, &split, lop3_per_pass),
                                    major, minor, cubin, lg);
+        *grouped = split.grouped;
         if (rc != LEC_ES_OK || !spilled(lg) || plan == 0) {
           log += lg;
           return rc;
@@ -1391,6 +1401,7 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
         double per = 0;
         ptx.push_back(
             gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis, layout->groups, &split, &per));
+        *grouped = split.grouped;
         pers.push_back(per);
         budgets.emplace_back(regs, plan);
         if (plan == 0) break;
@@ -1443,6 +1454,7 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
       const int rc = compile_ptx(gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis,
                                              layout->groups, &split, lop3_per_pass),
                                  major, minor, cubin, lg);
+      *grouped = split.grouped;
       if (rc != LEC_ES_OK || !spilled(lg) || plan == 0) {
         log += lg;
         return rc;
@@ -1518,7 +1530,7 @@ double jit_held_lop3(lec_es_ctx *c, const Program &g) {
   JitState *js = state(c);
   std::lock_guard<std::mutex> lk(js->mu);
   const JitKernel *k = cached_kernel(js, g, true);
-  return k ? k->lop3_per_pass : 0.0;
+  return k ? k->model_lop3 : 0.0;
 }
 
 bool jit_eligible(const Program &g) { return g.lut.count > 0 && !g.lut.order.empty() && g.lut.live <= kMaxJitLive; }
@@ -1578,11 +1590,12 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   double nvrtc_ms = 0;
   double lop3_per_pass = 0;  // of the PTX form's kernel (a sidecar file next to a cached cubin)
   uint32_t budgets[2] = {lay.regs, lay.plan};  // register and plan budgets it was generated with
+  bool grouped = false;                         // its passes run in straight-line groups
   if (path.empty() || !read_file(path, cubin)) {
     std::string log;
     const double tn = now_ms();
     int rc = compile_program_kernel(g, lut_form, c->cc_major, c->cc_minor, cubin, log, ptx_form ? &lay : nullptr,
-                                    &lop3_per_pass, budgets);
+                                    &lop3_per_pass, budgets, &grouped);
     nvrtc_ms = now_ms() - tn;
     if (rc) {
       if (getenv("LEC_ES_JIT_LOG")) fprintf(stderr, "lec_es JIT failed:\n%s\n", log.c_str());
@@ -1591,7 +1604,8 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
     if (!path.empty()) {
       write_file(path, cubin);
       const std::string txt =
-          std::to_string(lop3_per_pass) + " " + std::to_string(budgets[0]) + " " + std::to_string(budgets[1]);
+          std::to_string(lop3_per_pass) + " " + std::to_string(budgets[0]) + " " + std::to_string(budgets[1]) + " " +
+          std::to_string(grouped ? 1 : 0);
       write_file(path + ".lop3", std::vector<char>(txt.begin(), txt.end()));
     }
   } else {
@@ -1599,10 +1613,11 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
     if (read_file(path + ".lop3", txt)) {
       const std::string t(txt.begin(), txt.end());
       double per = 0;
-      unsigned r = budgets[0], pl = budgets[1];
-      if (sscanf(t.c_str(), "%lf %u %u", &per, &r, &pl) >= 1) lop3_per_pass = per;
+      unsigned r = budgets[0], pl = budgets[1], gr = 0;
+      if (sscanf(t.c_str(), "%lf %u %u %u", &per, &r, &pl, &gr) >= 1) lop3_per_pass = per;
       budgets[0] = r;
       budgets[1] = pl;
+      grouped = gr != 0;
     }
   }
   cudaSetDevice(c->device);
@@ -1638,6 +1653,7 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
     k->pass_bits = lay.pass_pis >> 5;
     k->stride_ok = jit_stride_ok(g.n, lay.rep);
     k->lop3_per_pass = lop3_per_pass;
+    k->model_lop3 = lop3_per_pass > 0 ? lop3_per_pass + (grouped ? kGroupedPassSaving : 0.0) : 0.0;
   }
   k->load_ms = now_ms() - tl;
   k->nvrtc_ms = nvrtc_ms;
@@ -1719,7 +1735,7 @@ bool jit_probe(void *arg, uint64_t hash, uint64_t hash2, uint32_t n, uint32_t co
     case JitProbe::kInfo:
       break;
     case JitProbe::kAuto:
-      if (k->lut_live > kMaxJitLive || !(cost_run_ms(c, LEC_ES_TIER_JIT, cone_ands, n, k->lop3_per_pass) <
+      if (k->lut_live > kMaxJitLive || !(cost_run_ms(c, LEC_ES_TIER_JIT, cone_ands, n, k->model_lop3) <
                                          cost_run_ms(c, LEC_ES_TIER_INTERP, cone_ands, n)))
         return false;
       break;

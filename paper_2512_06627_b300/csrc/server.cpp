@@ -178,7 +178,7 @@ int launch(Server *s, Request *r) {
   if (g.slots_elided && !k) return LEC_ES_EINVAL;  // found at submission; kernels are never evicted
   // stream: least loaded within the request's priority class, from the ES
   // time model on the tier it will run
-  const double predicted = cost_run_ms(c, k ? LEC_ES_TIER_JIT : LEC_ES_TIER_INTERP, g.cone_ands, g.n, k ? k->lop3_per_pass : 0.0);
+  const double predicted = cost_run_ms(c, k ? LEC_ES_TIER_JIT : LEC_ES_TIER_INTERP, g.cone_ands, g.n, k ? k->model_lop3 : 0.0);
   const int half = kStreams / 2;
   const int lo = predicted < kSmallMs ? 0 : half;
   int best = lo;
