@@ -427,3 +427,56 @@ def test_grouped_passes_find_planted_minterms_in_ranges(ctx):
                 want = p if wb <= w < we else None
                 assert g.cex_or_none == want, (i, p, wb, we)
             assert O.check(aig.num_pis, aig.fanins, aig.outputs[0], max(0, w - 3), w + 4)[0] == p
+
+
+def _too_wide(n_pis, nterms, seed, planted=None):
+    """An AND of `nterms` random 3-literal clauses whose tables keep too many
+    values live for a specialised kernel (each clause meets a near and a far
+    one); with 600 clauses over 30 PIs it is unsatisfiable.  planted: OR in
+    the minterm of that pattern (its only failing pattern then)."""
+    from paper_2512_06627_b300.circuits import Aig
+    rng = np.random.default_rng(seed)
+    rows = []
+
+    def a(x, y):
+        rows.append((x, y))
+        return 2 * (n_pis + len(rows))
+    terms = []
+    for _ in range(nterms):
+        lit = [2 * int(rng.integers(1, n_pis + 1)) + int(rng.integers(0, 2)) for _ in range(3)]
+        terms.append(a(a(lit[0] ^ 1, lit[1] ^ 1), lit[2] ^ 1) ^ 1)
+    acc = None
+    for j in range(nterms):
+        x = a(terms[j], terms[(j * 7 + nterms // 2) % nterms])
+        acc = x if acc is None else a(acc, x)
+    if planted is not None:
+        m = None
+        for k in range(n_pis):
+            lit = 2 * (k + 1) + (0 if (planted >> k) & 1 else 1)
+            m = lit if m is None else a(m, lit)
+        acc = a(acc ^ 1, m ^ 1) ^ 1
+    return Aig(n_pis, np.array(rows, dtype=np.uint32), [acc])
+
+
+def test_cold_check_of_a_cone_too_wide_for_a_kernel():
+    """A one-off AUTO check leaves the table cover to the background build;
+    for a cone whose tables keep more values live than a kernel can hold
+    that build gives up, and the interpreter's slices finish the check: the
+    oracle's verdict, and the planted pattern of the variant with one."""
+    import os
+    c = make_ctx(arena_bytes=1 << 30)
+    try:
+        aig = _too_wide(30, 600, 3)
+        m = L.Miter(aig.num_pis, aig.flat_fanins(), aig.outputs[0])
+        info = L.lec_es_compile(m)[0]
+        assert info.n == 30 and info.lut_live > 230
+        want = O.check_parallel(aig.num_pis, aig.fanins, aig.outputs[0], max(4, os.cpu_count() or 4))[0]
+        for _ in range(2):  # the second check finds the build given up, not a kernel
+            r = L.lec_es_check(c, m)
+            assert r.tier == L.TIER_INTERP and r.cex_or_none == want
+        p = (1 << 29) + 123457
+        mp = _too_wide(30, 600, 3, planted=p)
+        r = L.lec_es_check(c, L.Miter(mp.num_pis, mp.flat_fanins(), mp.outputs[0]))
+        assert want is None and r.cex_or_none == p
+    finally:
+        L.lec_es_destroy(c)
