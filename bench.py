@@ -354,6 +354,14 @@ def measure_batch(ctx, args):
     L.lec_es_batch_free(ctx, b)
     batched = k / statistics.median(ts)
     plans = [L.lec_es_prepare(ctx, m, L.options(tier=t)) for m, t in zip(ms, tiers)]
+    # the specialised kernels' work at the LOP3 peak: the lop3 each executes
+    # per 32-pattern pass (from the code generator) x its passes
+    _, _, _, lop3_rate = L.lec_es_lop3_peak(ctx)
+    jit_lop3 = 0.0
+    for p, t in zip(plans, tiers):
+        if t == L.TIER_JIT:
+            inf = L.lec_es_plan_info(p)
+            jit_lop3 += inf.lop3_per_pass * float(1 << max(0, inf.n - 5))
     one_async, one_sync = [], []
     for _ in range(2):
         # (i) back to back on one stream, one sync at the end
@@ -408,6 +416,10 @@ def measure_batch(ctx, args):
                    "submit_many_miters_per_s": k / min(served_many_s),
                    "submit_many_speedup": min(check_s) / min(served_many_s), "results_equal": True},
         "work_share_top_1pct": float(work[big].sum() / work.sum()),
+        "jit_lop3_at_peak_ms": jit_lop3 / lop3_rate * 1e3,
+        "jit_lop3_at_peak_note": "the specialised kernels' generator lop3 count at the measured LOP3 peak; the "
+                                 "batch's device time against it is its roofline fraction (the light miters' tile "
+                                 "queue runs beside them)",
         "prepare_s": prep, "jit_compile_s": layout.jit_ms / 1e3, "autotune_s": layout.tune_ms / 1e3,
         "sweep_step1": {"graph_ands": int(base.num_ands), "signature_words": 64, "candidate_pairs": len(cand),
                         "ms": sweep_ms},
