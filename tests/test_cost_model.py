@@ -63,7 +63,7 @@ def test_fit_equals_nonnegative_weighted_least_squares(seed):
     assert np.all(got >= 0)
     A = F / t[:, None]
     err = lambda c: np.sum((A @ c - 1.0) ** 2)
-    # same minimiser (up to rounding), judged by the objective and the values
+    # same minimiser (up to rounding), compared by the objective and the values
     assert err(got) == pytest.approx(err(want), rel=1e-9, abs=1e-12)
     assert got == pytest.approx(want, rel=1e-6, abs=1e-12)
 
