@@ -109,7 +109,9 @@ typedef struct {
   uint64_t word_end;        /* one past the last; UINT64_MAX = all words */
   uint32_t tier;            /* LEC_ES_TIER_* (default AUTO) */
   uint32_t order;           /* LEC_ES_ORDER_* (default AUTO) */
-  uint32_t block_threads;   /* 0 = library choice */
+  uint32_t block_threads;   /* 0 = library choice; single miter: an upper bound (a power of two
+                               32..256 is used); batch: threads per tile pass, a multiple of 32 in
+                               64..512 (a smaller multiple of 32 if it does not fit shared memory) */
   uint32_t grid_blocks;     /* 0 = library choice */
   uint32_t flags;           /* LEC_ES_FLAG_* */
   uint32_t tile_granularity;/* batch: tiles per resident block slot (0 = 16) */

@@ -188,7 +188,7 @@ int choose_interp_geometry(lec_es_ctx *c, const Program &prog, uint64_t chunks, 
   return LEC_ES_OK;
 }
 
-bool choose_word_geometry(lec_es_ctx *c, const Program &prog, const lec_es_options *opt, PlanGeom &g) {
+bool choose_word_geometry(lec_es_ctx *c, const Program &prog, const lec_es_options *opt, PlanGeom &g, bool widest) {
   const uint32_t nand = (uint32_t)std::count_if(prog.recs.begin(), prog.recs.end(), [](const Rec &r) { return r.op < 4; });
   const int pref = opt && opt->block_threads ? (int)opt->block_threads : 256;
   g = PlanGeom{};
@@ -207,6 +207,23 @@ bool choose_word_geometry(lec_es_ctx *c, const Program &prog, const lec_es_optio
     }
   }
   if (!g.word) return false;
+  if (widest && !(opt && opt->block_threads)) {
+    const int base = word_warps_per_sm(g.smem, g.block);
+    int best = base;
+    for (int b = 128; b <= kMaxWordBlock; b += 128)  // whole warps on each of the SM's four schedulers
+      for (int allow_res = 1; allow_res >= 0; allow_res--) {
+        uint32_t ring, res;
+        const size_t bytes = interp_w_smem_bytes(prog.num_slots, nand, b, &ring, &res, allow_res != 0);
+        if (bytes > (size_t)c->smem_optin) continue;
+        const int w = word_warps_per_sm(bytes, b);
+        if (w < best || 4 * w < 5 * base || (w == best && b <= g.block)) continue;
+        g.block = b;
+        g.ring_recs = ring;
+        g.resident = res;
+        g.smem = bytes;
+        best = w;
+      }
+  }
   const uint64_t lanes = kLaneBytes == 8 ? num_words(prog.n) : num_chunks(prog.n);
   const size_t per_sm = 228u * 1024u;
   int bps = (int)std::max<size_t>(1, per_sm / (g.smem + 1024));
@@ -419,7 +436,7 @@ int plan_prepare_program(lec_es_ctx *c, Program &&prog, const lec_es_options *op
     p->tier = LEC_ES_TIER_JIT;
   } else {
     const bool want_spill = want == LEC_ES_TIER_SPILL;
-    if (!want_spill && choose_word_geometry(c, g, opt, p->geom)) {
+    if (!want_spill && choose_word_geometry(c, g, opt, p->geom, true)) {
       p->tier = LEC_ES_TIER_INTERP;
     } else {
       rc = choose_interp_geometry(c, g, chunks, opt, p->geom);

@@ -123,8 +123,15 @@ int wait_event(cudaEvent_t ev, double timeout_s);
 int choose_interp_geometry(lec_es_ctx *c, const Program &prog, uint64_t chunks, const lec_es_options *opt,
                            PlanGeom &g);
 // Geometry of the word-wide kernel; false if the live set does not fit
-// shared memory even at 32 threads per block.
-bool choose_word_geometry(lec_es_ctx *c, const Program &prog, const lec_es_options *opt, PlanGeom &g);
+// shared memory even at 32 threads per block.  The block is the largest
+// power of two up to 256 (or opt->block_threads) that fits; with `widest`
+// and no block asked for, a block of a multiple of 128 threads up to
+// kMaxWordBlock (the same number of warps on each of the SM's four
+// schedulers), records resident or in the ring, replaces it when that keeps
+// at least a quarter more warps on each SM (a live set that leaves one
+// 256-thread block per SM is latency-bound).
+bool choose_word_geometry(lec_es_ctx *c, const Program &prog, const lec_es_options *opt, PlanGeom &g,
+                          bool widest = false);
 
 // JIT tier (jit.cpp)
 uint32_t jit_auto_tier(lec_es_ctx *c, const Program &g, uint64_t chunks);

@@ -245,7 +245,25 @@ struct XBatchParams {
 // Program::step) and dropped otherwise (forwarding kernels).
 void encode_w(const Program &g, int block, std::vector<XRec> &recs, std::vector<XLoad> &loads, uint32_t &out_off,
               bool breaks = true);
-size_t interp_w_smem_bytes(uint32_t nslots, uint32_t nrec, int block, uint32_t *ring_recs, uint32_t *resident);
+// Threads per block of the word-wide kernels: any multiple of 32 up to
+// kMaxWordBlock (the record offsets are encoded for the block's size, so the
+// block need not be a power of two; wider blocks put more warps on an SM
+// whose shared memory one 256-thread block of a large live set leaves half
+// empty).
+constexpr int kMaxWordBlock = 512;
+inline bool word_block_ok(int b) { return b >= 32 && b <= kMaxWordBlock && b % 32 == 0; }
+// Shared memory of the single-miter word kernel: the whole record stream
+// resident when it fits (and `allow_resident`), else a 4-stage ring.
+size_t interp_w_smem_bytes(uint32_t nslots, uint32_t nrec, int block, uint32_t *ring_recs, uint32_t *resident,
+                           bool allow_resident = true);
+// Warps per SM that blocks of `block` threads holding `bytes` of shared
+// memory each keep resident (228 KB per SM, 1 KB reserved per block, at most
+// 64 warps).
+inline int word_warps_per_sm(size_t bytes, int block) {
+  const size_t per_sm = 228u * 1024u;
+  const int bps = (int)(per_sm / (bytes + 1024));
+  return (bps < 2048 / block ? bps : 2048 / block) * block / 32;
+}
 size_t batch_w_smem_bytes(uint32_t max_slots, int block, uint32_t ring_recs);
 int launch_interp_w(const XParams &p, int block, int grid, size_t smem, void *stream);
 // The same kernel with per-record truth-table stores (interp_w.cu, TTSink).

@@ -124,11 +124,41 @@ __device__ __forceinline__ uint32_t pi_lane(uint32_t k, uint64_t c, uint32_t) {
 
 __device__ __forceinline__ Lane pi_value(uint32_t k, uint64_t u) { return pi_lane(k, u, Lane{}); }
 
-__device__ __forceinline__ Lane ld_slot(const uint8_t *S, uint32_t off) {
-  return *reinterpret_cast<const Lane *>(S + off);
+// Shared-memory accesses by 32-bit shared-window address (S: the thread's
+// slot base; off: a record's byte offset), written out as ld/st.shared so
+// the address arithmetic is one 32-bit add whatever the compiler infers
+// about the pointer; volatile keeps them in the order written (a step's
+// loads, then its stores), which is the order the record semantics need.
+template <typename V>
+__device__ __forceinline__ V lds_lane(uint32_t a) {
+  if constexpr (sizeof(V) == 8) {
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+    return v;
+  } else {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+  }
+}
+template <typename V>
+__device__ __forceinline__ void sts_lane(uint32_t a, V v) {
+  if constexpr (sizeof(V) == 8)
+    asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(a), "r"(v.x), "r"(v.y) : "memory");
+  else
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ void st_slot(uint8_t *S, uint32_t off, Lane v) { *reinterpret_cast<Lane *>(S + off) = v; }
+__device__ __forceinline__ Lane ld_slot(uint32_t S, uint32_t off) { return lds_lane<Lane>(S + off); }
+
+__device__ __forceinline__ void st_slot(uint32_t S, uint32_t off, Lane v) { sts_lane<Lane>(S + off, v); }
+
+// One 16-byte record (read by every thread of the warp: a broadcast).
+__device__ __forceinline__ uint4 ld_rec(uint32_t a) {
+  uint4 r;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "r"(a));
+  return r;
+}
 
 // One AND; the complement bits of ctl become all-zero / all-one masks by a
 // bit-field extract each.
@@ -216,14 +246,14 @@ __device__ __forceinline__ void tt_store(const TTSink &k, uint32_t ctl, Lane v) 
 }
 
 template <int K, bool FWD, bool TT>
-__device__ __forceinline__ void run_ands_k(const uint4 *r4, uint32_t cnt, uint8_t *S, uint32_t &i, const TTSink &tk) {
+__device__ __forceinline__ void run_ands_k(uint32_t R, uint32_t cnt, uint32_t S, uint32_t &i, const TTSink &tk) {
   uint4 r[K];
 #pragma unroll
-  for (int j = 0; j < K; j++) r[j] = r4[i + j];  // broadcast reads
+  for (int j = 0; j < K; j++) r[j] = ld_rec(R + 16u * (i + j));
   for (; i + K <= cnt; i += K) {
     uint4 n[K];
 #pragma unroll
-    for (int j = 0; j < K; j++) n[j] = r4[i + K + j];
+    for (int j = 0; j < K; j++) n[j] = ld_rec(R + 16u * (i + K + j));
     Lane x[K], y[K], v[K];
 #pragma unroll
     for (int j = 0; j < K; j++) {
@@ -250,14 +280,13 @@ __device__ __forceinline__ void run_ands_k(const uint4 *r4, uint32_t cnt, uint8_
 }
 
 template <int K, bool FWD, bool TT>
-__device__ __forceinline__ void run_ands(const XRec *rr, uint32_t cnt, uint8_t *S, const TTSink &tk) {
-  const uint4 *r4 = reinterpret_cast<const uint4 *>(rr);
+__device__ __forceinline__ void run_ands(uint32_t R, uint32_t cnt, uint32_t S, const TTSink &tk) {
   uint32_t i = 0;
-  if (cnt >= (uint32_t)K) run_ands_k<K, FWD, TT>(r4, cnt, S, i, tk);
+  if (cnt >= (uint32_t)K) run_ands_k<K, FWD, TT>(R, cnt, S, i, tk);
   // without forwarding, any two records of a run are independent too
-  if (!FWD && K > 2 && cnt - i >= 2) run_ands_k<2, false, TT>(r4, i + 2, S, i, tk);
+  if (!FWD && K > 2 && cnt - i >= 2) run_ands_k<2, false, TT>(R, i + 2, S, i, tk);
   for (; i < cnt; i++) {
-    const uint4 r = r4[i];
+    const uint4 r = ld_rec(R + 16u * i);
     const Lane v = and_lane(ld_slot(S, r.x), ld_slot(S, r.y), r.w);
     st_slot(S, r.z, v);
     tt_store<TT>(tk, r.w, v);
@@ -269,8 +298,8 @@ __device__ __forceinline__ void run_ands(const XRec *rr, uint32_t cnt, uint8_t *
 // slot an earlier record has just freed).  li is the next load (updated);
 // u is the thread's lane.
 template <int K, bool FWD, bool TT = false>
-__device__ __forceinline__ void run_block(const XRec *rr, uint32_t base, uint32_t cnt, const XLoad *loads,
-                                          uint32_t nload, uint32_t &li, uint8_t *S, uint64_t u,
+__device__ __forceinline__ void run_block(uint32_t R, uint32_t base, uint32_t cnt, const XLoad *loads,
+                                          uint32_t nload, uint32_t &li, uint32_t S, uint64_t u,
                                           const TTSink &tk = TTSink{}) {
   // the next load {at, d_off, k} is held in registers, fetched as soon as the
   // one before it is applied, so its latency hides behind the records between
@@ -286,7 +315,7 @@ __device__ __forceinline__ void run_block(const XRec *rr, uint32_t base, uint32_
     }
     if (i >= cnt) break;
     const uint32_t stop = nl.x < base + cnt ? nl.x - base : cnt;
-    run_ands<K, FWD, TT>(rr + i, stop - i, S, tk);
+    run_ands<K, FWD, TT>(R + 16u * i, stop - i, S, tk);
     i = stop;
   }
 }
@@ -294,7 +323,7 @@ __device__ __forceinline__ void run_block(const XRec *rr, uint32_t base, uint32_
 // The miter output of the thread's lane: complemented as the output literal
 // says, invalid patterns (n below the lane's pattern bits) and lanes outside
 // the range cleared.
-__device__ __forceinline__ uint64_t out_bits(const uint8_t *S, uint32_t off, uint32_t compl_out, uint32_t n,
+__device__ __forceinline__ uint64_t out_bits(uint32_t S, uint32_t off, uint32_t compl_out, uint32_t n,
                                              bool in_range) {
   const uint64_t o = lane_bits(ld_slot(S, off)) ^ (compl_out ? ~0ull : 0ull);
   return in_range ? o & lane_valid(n) : 0ull;
@@ -307,22 +336,28 @@ __device__ __forceinline__ void report(uint64_t o, uint64_t u, unsigned long lon
     atomicMin(cex, (unsigned long long)(u * kLanePatterns + (uint64_t)(__ffsll((long long)o) - 1)));
 }
 
-template <int T, bool TT, int K, bool FWD>
-__global__ void __launch_bounds__(T) es_interp_w(const XParams p) {
+// T (threads per block, the lanes of one pass) is the launch's block size,
+// any multiple of 32 up to kMaxWordBlock; the records are encoded for it.
+// RES: the whole record stream is resident in shared memory (p.resident);
+// the two forms are separate instantiations, so each is compiled alone.
+template <bool TT, int K, bool FWD, bool RES>
+__global__ void __launch_bounds__(kMaxWordBlock, 1) es_interp_w(const XParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
+  const uint32_t T = blockDim.x;
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   volatile unsigned long long *bcast = reinterpret_cast<unsigned long long *>(smem + 48);
   XRec *ring = reinterpret_cast<XRec *>(smem + 64);
-  const uint32_t ring_bytes = p.resident ? p.nrec * 16u : NSTAGE * p.ring_recs * 16u;
-  uint8_t *S = smem + 64 + ((ring_bytes + 15u) & ~15u) + threadIdx.x * kLaneBytes;
+  const uint32_t ring_bytes = RES ? p.nrec * 16u : NSTAGE * p.ring_recs * 16u;
+  const uint32_t R = smem_u32(ring);  // shared-window address of the records
+  const uint32_t S = smem_u32(smem) + 64u + ((ring_bytes + 15u) & ~15u) + threadIdx.x * kLaneBytes;
   const int t = threadIdx.x;
   if (t == 0) {
     for (int s = 0; s < NSTAGE; s++) mbar_init(bar + s);
     fence_init();
   }
   __syncthreads();
-  const uint32_t nch = p.resident ? 1u : (p.nrec + p.ring_recs - 1) / p.ring_recs;
-  if (p.resident && p.nrec) {
+  const uint32_t nch = RES ? 1u : (p.nrec + p.ring_recs - 1) / p.ring_recs;
+  if (RES && p.nrec) {
     if (t == 0) expect_and_copy(bar, ring, p.recs, p.nrec * 16u, p.extra_tx);
     const bool ok = wait(bar, 0);
     if (__syncthreads_or(!ok)) {
@@ -335,18 +370,42 @@ __global__ void __launch_bounds__(T) es_interp_w(const XParams p) {
   uint64_t ub, ue;
   lane_range(p.word_begin, p.word_end, p.n, ub, ue);
   const uint64_t passes = (ue - ub + T - 1) / T;
-  unsigned long long done = 0;
-  for (uint64_t pass = blockIdx.x; pass < passes; pass += gridDim.x) {
-    const uint64_t u0 = ub + pass * T;
-    if (t == 0) *bcast = ld_volatile(p.cex);
-    __syncthreads();
-    if (u0 * kLanePatterns >= *bcast) break;  // block-uniform early exit
-    const uint64_t u = u0 + t;
-    const TTSink tk{p.tt_out, p.tt_words, p.word_begin, u};
-    uint32_t li = 0;
-    if (p.resident) {
-      run_block<K, FWD, TT>(ring, 0, p.nrec, p.loads, p.nload, li, S, u, tk);
-    } else {
+  if constexpr (RES) {
+    // The records stay put for the whole launch, so the warps need no block
+    // barrier: each runs its 32 lanes of every pass on its own, reads the
+    // counterexample word itself (lane 0, shuffled to the warp) and counts
+    // the patterns it evaluated.  The skip test is on the warp's first
+    // pattern: a warp skips only lanes at or above the current minimum.
+    const uint32_t lane = t & 31u;
+    unsigned long long wdone = 0;
+    for (uint64_t pass = blockIdx.x; pass < passes; pass += gridDim.x) {
+      const uint64_t w0 = ub + pass * T + (t - lane);
+      if (w0 >= ue) break;  // this warp's lanes of this pass and of every later one are past the range
+      unsigned long long cur = lane == 0 ? ld_volatile(p.cex) : 0ull;
+      cur = __shfl_sync(0xFFFFFFFFu, cur, 0);
+      if (w0 * kLanePatterns >= cur) break;
+      const uint64_t u = w0 + lane;
+      const TTSink tk{p.tt_out, p.tt_words, p.word_begin, u};
+      uint32_t li = 0;
+      run_block<K, FWD, TT>(R, 0, p.nrec, p.loads, p.nload, li, S, u, tk);
+      while (li < p.nload) {  // loads after the last record
+        st_slot(S, p.loads[li].d_off, pi_value(p.loads[li].k, u));
+        li++;
+      }
+      if (!TT) report(out_bits(S, p.out_off, p.out_compl, p.n, u < ue), u, p.cex);
+      wdone += (unsigned long long)min((uint64_t)32, ue - w0);
+    }
+    if (lane == 0 && wdone) atomicAdd(p.evaluated, wdone * kLanePatterns);
+  } else {
+    unsigned long long done = 0;
+    for (uint64_t pass = blockIdx.x; pass < passes; pass += gridDim.x) {
+      const uint64_t u0 = ub + pass * T;
+      if (t == 0) *bcast = ld_volatile(p.cex);
+      __syncthreads();
+      if (u0 * kLanePatterns >= *bcast) break;  // block-uniform early exit
+      const uint64_t u = u0 + t;
+      const TTSink tk{p.tt_out, p.tt_words, p.word_begin, u};
+      uint32_t li = 0;
       for (uint32_t k = 0; k < nch && k < (uint32_t)NSTAGE; k++) {
         if (t == 0) {
           const uint32_t off = k * p.ring_recs;
@@ -366,7 +425,7 @@ __global__ void __launch_bounds__(T) es_interp_w(const XParams p) {
         parity ^= 1u << s;
         inflight &= ~(1u << s);
         const uint32_t off = k * p.ring_recs;
-        run_block<K, FWD, TT>(ring + (size_t)s * p.ring_recs, off, min(p.ring_recs, p.nrec - off), p.loads, p.nload, li, S, u,
+        run_block<K, FWD, TT>(R + 16u * s * p.ring_recs, off, min(p.ring_recs, p.nrec - off), p.loads, p.nload, li, S, u,
                       tk);
         __syncthreads();
         if (k + NSTAGE < nch) {
@@ -383,29 +442,30 @@ __global__ void __launch_bounds__(T) es_interp_w(const XParams p) {
         drain(bar, inflight, parity);
         return;
       }
+      // loads after the last record (an output that is a PI or the constant)
+      while (li < p.nload) {
+        st_slot(S, p.loads[li].d_off, pi_value(p.loads[li].k, u));
+        li++;
+      }
+      // a dump checks nothing, so nothing exits early
+      if (!TT) report(out_bits(S, p.out_off, p.out_compl, p.n, u < ue), u, p.cex);
+      done += (unsigned long long)min((uint64_t)T, ue - u0);
+      __syncthreads();
     }
-    // loads after the last record (an output that is a PI or the constant)
-    while (li < p.nload) {
-      st_slot(S, p.loads[li].d_off, pi_value(p.loads[li].k, u));
-      li++;
-    }
-    // a dump checks nothing, so nothing exits early
-    if (!TT) report(out_bits(S, p.out_off, p.out_compl, p.n, u < ue), u, p.cex);
-    done += (unsigned long long)min((uint64_t)T, ue - u0);
-    __syncthreads();
+    if (t == 0 && done) atomicAdd(p.evaluated, done * kLanePatterns);
   }
-  if (t == 0 && done) atomicAdd(p.evaluated, done * kLanePatterns);
 }
 
-// Tile-queue form: blocks pull (miter, word range) tiles.
-template <int T>
-__global__ void __launch_bounds__(T) es_batch_w(const XBatchParams p) {
+// Tile-queue form: blocks pull (miter, word range) tiles.  T as above.
+__global__ void __launch_bounds__(kMaxWordBlock, 1) es_batch_w(const XBatchParams p) {
   extern __shared__ __align__(128) uint8_t smem[];
+  const uint32_t T = blockDim.x;
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   volatile unsigned long long *bcast = reinterpret_cast<unsigned long long *>(smem + 40);
   volatile uint32_t *btile = reinterpret_cast<uint32_t *>(smem + 56);
   XRec *ring = reinterpret_cast<XRec *>(smem + 64);
-  uint8_t *S = smem + 64 + NSTAGE * p.ring_recs * 16u + threadIdx.x * kLaneBytes;
+  const uint32_t R = smem_u32(ring);
+  const uint32_t S = smem_u32(smem) + 64u + NSTAGE * p.ring_recs * 16u + threadIdx.x * kLaneBytes;
   const int t = threadIdx.x;
   if (t == 0) {
     for (int s = 0; s < NSTAGE; s++) mbar_init(bar + s);
@@ -451,6 +511,30 @@ __global__ void __launch_bounds__(T) es_batch_w(const XBatchParams p) {
     }
     uint64_t ub, ue;
     lane_range(bt.word_begin, bt.word_end, bm.n, ub, ue);
+    if (resident) {
+      // the whole program is staged: warps run the tile's passes on their
+      // own, as in es_interp_w (no block barrier per pass)
+      const uint32_t lane = t & 31u;
+      for (uint64_t w0 = ub + (t - lane); w0 < ue; w0 += T) {
+        unsigned long long cur = 0;
+        if (lane == 0) {
+          cur = ld_volatile(p.cex + bt.miter);
+          if (p.cancel && p.cancel[bt.miter]) cur = 0;
+        }
+        cur = __shfl_sync(0xFFFFFFFFu, cur, 0);
+        if (w0 * kLanePatterns >= cur) break;
+        const uint64_t u = w0 + lane;
+        uint32_t li = 0;
+        run_block<kFwdStep, true>(R, 0, bm.nrec, loads, bm.nload, li, S, u);
+        while (li < bm.nload) {
+          st_slot(S, loads[li].d_off, pi_value(loads[li].k, u));
+          li++;
+        }
+        report(out_bits(S, bm.out_off, bm.out_compl, bm.n, u < ue), u, p.cex + bt.miter);
+      }
+      __syncthreads();  // ring reuse by the next tile
+      continue;
+    }
     for (uint64_t u0 = ub; u0 < ue; u0 += T) {
       if (t == 0) {
         unsigned long long cur = ld_volatile(p.cex + bt.miter);
@@ -463,46 +547,42 @@ __global__ void __launch_bounds__(T) es_batch_w(const XBatchParams p) {
       if (u0 * kLanePatterns >= cur) break;
       const uint64_t u = u0 + t;
       uint32_t li = 0;
-      if (resident) {
-        run_block<kFwdStep, true>(ring, 0, bm.nrec, loads, bm.nload, li, S, u);
-      } else {
-        uint32_t inflight = 0;
-        for (uint32_t k = 0; k < (uint32_t)NSTAGE; k++) {
-          if (t == 0) {
-            const uint32_t off = k * p.ring_recs;
-            expect_and_copy(bar + k, ring + (size_t)k * p.ring_recs, recs + off,
-                            min(p.ring_recs, bm.nrec - off) * 16u, 0u);
-          }
-          inflight |= 1u << k;
-        }
-        bool bad = false;
-        for (uint32_t k = 0; k < nch; k++) {
-          const uint32_t s = k % NSTAGE;
-          const bool ok = wait(bar + s, (parity >> s) & 1u);
-          if (__syncthreads_or(!ok)) {
-            bad = true;
-            break;
-          }
-          parity ^= 1u << s;
-          inflight &= ~(1u << s);
+      uint32_t inflight = 0;
+      for (uint32_t k = 0; k < (uint32_t)NSTAGE; k++) {
+        if (t == 0) {
           const uint32_t off = k * p.ring_recs;
-          run_block<kFwdStep, true>(ring + (size_t)s * p.ring_recs, off, min(p.ring_recs, bm.nrec - off), loads, bm.nload, li, S,
-                    u);
-          __syncthreads();
-          if (k + NSTAGE < nch) {
-            if (t == 0) {
-              const uint32_t off2 = (k + NSTAGE) * p.ring_recs;
-              expect_and_copy(bar + s, ring + (size_t)s * p.ring_recs, recs + off2,
-                              min(p.ring_recs, bm.nrec - off2) * 16u, 0u);
-            }
-            inflight |= 1u << s;
+          expect_and_copy(bar + k, ring + (size_t)k * p.ring_recs, recs + off,
+                          min(p.ring_recs, bm.nrec - off) * 16u, 0u);
+        }
+        inflight |= 1u << k;
+      }
+      bool bad = false;
+      for (uint32_t k = 0; k < nch; k++) {
+        const uint32_t s = k % NSTAGE;
+        const bool ok = wait(bar + s, (parity >> s) & 1u);
+        if (__syncthreads_or(!ok)) {
+          bad = true;
+          break;
+        }
+        parity ^= 1u << s;
+        inflight &= ~(1u << s);
+        const uint32_t off = k * p.ring_recs;
+        run_block<kFwdStep, true>(R + 16u * s * p.ring_recs, off, min(p.ring_recs, bm.nrec - off), loads, bm.nload, li,
+                                  S, u);
+        __syncthreads();
+        if (k + NSTAGE < nch) {
+          if (t == 0) {
+            const uint32_t off2 = (k + NSTAGE) * p.ring_recs;
+            expect_and_copy(bar + s, ring + (size_t)s * p.ring_recs, recs + off2,
+                            min(p.ring_recs, bm.nrec - off2) * 16u, 0u);
           }
+          inflight |= 1u << s;
         }
-        if (bad) {
-          if (t == 0) atomicOr(p.status, DEV_WAIT_TIMEOUT);
-          drain(bar, inflight, parity);
-          return;
-        }
+      }
+      if (bad) {
+        if (t == 0) atomicOr(p.status, DEV_WAIT_TIMEOUT);
+        drain(bar, inflight, parity);
+        return;
       }
       while (li < bm.nload) {
         st_slot(S, loads[li].d_off, pi_value(loads[li].k, u));
@@ -515,29 +595,37 @@ __global__ void __launch_bounds__(T) es_batch_w(const XBatchParams p) {
   }
 }
 
-template <int T, bool TT, int K, bool FWD>
-int launch_wk(const XParams &p, int grid, size_t smem, cudaStream_t st) {
+template <bool TT, int K, bool FWD, bool RES>
+int launch_wkr(const XParams &p, int block, int grid, size_t smem, cudaStream_t st) {
   cudaError_t e =
-      cudaFuncSetAttribute(es_interp_w<T, TT, K, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(es_interp_w<TT, K, FWD, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
-  es_interp_w<T, TT, K, FWD><<<grid, T, smem, st>>>(p);
+  es_interp_w<TT, K, FWD, RES><<<grid, block, smem, st>>>(p);
   return (int)cudaGetLastError();
 }
 
+template <bool TT, int K, bool FWD>
+int launch_wk(const XParams &p, int block, int grid, size_t smem, cudaStream_t st) {
+  return p.resident ? launch_wkr<TT, K, FWD, true>(p, block, grid, smem, st)
+                    : launch_wkr<TT, K, FWD, false>(p, block, grid, smem, st);
+}
+
 // Programs of step kInterpStep run without forwarding, others with it.
-template <int T, bool TT = false>
-int launch_w(const XParams &p, int grid, size_t smem, cudaStream_t st) {
-  if (p.step == (uint32_t)kInterpStep) return launch_wk<T, TT, kInterpStep, false>(p, grid, smem, st);
-  return launch_wk<T, TT, kFwdStep, true>(p, grid, smem, st);
+template <bool TT = false>
+int launch_w(const XParams &p, int block, int grid, size_t smem, cudaStream_t st) {
+  if (!word_block_ok(block)) return (int)cudaErrorInvalidValue;
+  if (p.step == (uint32_t)kInterpStep) return launch_wk<TT, kInterpStep, false>(p, block, grid, smem, st);
+  return launch_wk<TT, kFwdStep, true>(p, block, grid, smem, st);
 }
 
 }  // namespace
 
-size_t interp_w_smem_bytes(uint32_t nslots, uint32_t nrec, int block, uint32_t *ring_recs, uint32_t *resident) {
+size_t interp_w_smem_bytes(uint32_t nslots, uint32_t nrec, int block, uint32_t *ring_recs, uint32_t *resident,
+                           bool allow_resident) {
   const size_t limit = 227u * 1024u;
   const size_t slots = (size_t)nslots * block * kLaneBytes;
   const size_t whole = 64 + (size_t)nrec * 16u + slots;
-  if (whole <= limit) {
+  if (allow_resident && whole <= limit) {
     *resident = 1;
     *ring_recs = nrec;
     return whole;
@@ -552,58 +640,27 @@ size_t batch_w_smem_bytes(uint32_t max_slots, int block, uint32_t ring_recs) {
 }
 
 int launch_interp_w(const XParams &p, int block, int grid, size_t smem, void *stream) {
-  cudaStream_t st = (cudaStream_t)stream;
-  switch (block) {
-    case 32: return launch_w<32>(p, grid, smem, st);
-    case 64: return launch_w<64>(p, grid, smem, st);
-    case 128: return launch_w<128>(p, grid, smem, st);
-    case 256: return launch_w<256>(p, grid, smem, st);
-    default: return (int)cudaErrorInvalidValue;
-  }
+  return launch_w<false>(p, block, grid, smem, (cudaStream_t)stream);
 }
 
 int launch_interp_w_tt(const XParams &p, int block, int grid, size_t smem, void *stream) {
-  cudaStream_t st = (cudaStream_t)stream;
-  switch (block) {
-    case 32: return launch_w<32, true>(p, grid, smem, st);
-    case 64: return launch_w<64, true>(p, grid, smem, st);
-    case 128: return launch_w<128, true>(p, grid, smem, st);
-    case 256: return launch_w<256, true>(p, grid, smem, st);
-    default: return (int)cudaErrorInvalidValue;
-  }
+  return launch_w<true>(p, block, grid, smem, (cudaStream_t)stream);
 }
 
 int configure_batch_w(int block, size_t smem) {
-  cudaError_t e;
-  switch (block) {
-    case 64: e = cudaFuncSetAttribute(es_batch_w<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-    case 128: e = cudaFuncSetAttribute(es_batch_w<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-    case 256: e = cudaFuncSetAttribute(es_batch_w<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-    default: return (int)cudaErrorInvalidValue;
-  }
-  return (int)e;
+  if (!word_block_ok(block)) return (int)cudaErrorInvalidValue;
+  return (int)cudaFuncSetAttribute(es_batch_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 int batch_w_blocks_per_sm(int block, size_t smem) {
   int n = 0;
-  cudaError_t e;
-  switch (block) {
-    case 64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, es_batch_w<64>, 64, smem); break;
-    case 128: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, es_batch_w<128>, 128, smem); break;
-    case 256: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, es_batch_w<256>, 256, smem); break;
-    default: return 0;
-  }
-  return e == cudaSuccess ? n : 0;
+  if (!word_block_ok(block)) return 0;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, es_batch_w, block, smem) == cudaSuccess ? n : 0;
 }
 
 int launch_batch_w(const XBatchParams &p, int block, int grid, size_t smem, void *stream) {
-  cudaStream_t st = (cudaStream_t)stream;
-  switch (block) {
-    case 64: es_batch_w<64><<<grid, 64, smem, st>>>(p); break;
-    case 128: es_batch_w<128><<<grid, 128, smem, st>>>(p); break;
-    case 256: es_batch_w<256><<<grid, 256, smem, st>>>(p); break;
-    default: return (int)cudaErrorInvalidValue;
-  }
+  if (!word_block_ok(block)) return (int)cudaErrorInvalidValue;
+  es_batch_w<<<grid, block, smem, (cudaStream_t)stream>>>(p);
   return (int)cudaGetLastError();
 }
 

@@ -79,11 +79,18 @@ def test_layouts_and_autotune_give_identical_results(ctx, pairs, tmp_path):
     sel = list(range(0, 4096, 5))
     ms = [L.Miter(pairs.aig.num_pis, f, pairs.aig.outputs[i]) for i in sel]
     ref = None
-    for blk, gran, ring in [(256, 16, 256), (128, 4, 128), (64, 64, 1024), (256, 1, 2)]:
+    # blocks need not be powers of two; 512 threads do not fit this selection's
+    # largest live set, so the library steps down by 32 to a block that fits
+    for blk, gran, ring in [(256, 16, 256), (128, 4, 128), (64, 64, 1024), (256, 1, 2), (224, 16, 256),
+                            (160, 4, 128), (96, 16, 256), (512, 16, 256)]:
         b = L.lec_es_batch_prepare(ctx, ms, L.options(tier=L.TIER_INTERP, block_threads=blk,
                                                        tile_granularity=gran, stage_records=ring))
         info = L.lec_es_batch_info(b)
-        assert info.block_threads == blk and info.stage_records == ring and info.tile_granularity == gran
+        assert info.stage_records == ring and info.tile_granularity == gran
+        if blk < 512:
+            assert info.block_threads == blk
+        else:
+            assert 64 <= info.block_threads < 512 and info.block_threads % 32 == 0
         L.lec_es_batch_run_async(ctx, b)
         got = [r.cex for r in L.lec_es_batch_results(ctx, b, len(ms))]
         L.lec_es_batch_free(ctx, b)
@@ -92,7 +99,8 @@ def test_layouts_and_autotune_give_identical_results(ctx, pairs, tmp_path):
     tuned = L.lec_es_create(0, arena_bytes=1 << 30, jit_cache_dir=str(tmp_path))
     b = L.lec_es_batch_prepare(tuned, ms, L.options(flags=L.FLAG_AUTOTUNE))
     info = L.lec_es_batch_info(b)
-    assert info.block_threads in (64, 128, 256) and info.tile_granularity in (4, 16, 64)
+    assert info.block_threads % 32 == 0 and 64 <= info.block_threads <= 512
+    assert info.tile_granularity in (4, 16, 64)
     L.lec_es_batch_run_async(tuned, b)
     assert [r.cex for r in L.lec_es_batch_results(tuned, b, len(ms))] == ref
     L.lec_es_batch_free(tuned, b)
