@@ -473,19 +473,25 @@ __global__ void __launch_bounds__(kMaxWordBlock, 1) es_batch_w(const XBatchParam
   }
   __syncthreads();
   uint32_t parity = 0;
+  // The miter whose whole program the ring holds: a block's next tile is
+  // often another range of the same miter (a miter's tiles are queued
+  // together), and then its records are not staged again.
+  uint32_t staged = 0xFFFFFFFFu;
+  if (t == 0) *btile = atomicAdd(p.head, 1u);
+  __syncthreads();
+  uint32_t tile = *btile;
   for (;;) {
-    if (t == 0) *btile = atomicAdd(p.head, 1u);
-    __syncthreads();
-    const uint32_t tile = *btile;
-    __syncthreads();
+    __syncthreads();  // every thread has read btile
     if (tile >= p.num_tiles) break;
+    // the next tile's index, taken now so that its latency hides behind this tile
+    if (t == 0) *btile = atomicAdd(p.head, 1u);
     const XTile bt = p.tiles[tile];
     const XMiter bm = p.miters[bt.miter];
     const XRec *recs = p.recs + bm.rec_off;
     const XLoad *loads = p.loads + bm.load_off;
     const uint32_t nch = (bm.nrec + p.ring_recs - 1) / p.ring_recs;
     const bool resident = nch <= (uint32_t)NSTAGE;  // the whole program fits the ring
-    if (resident && bm.nrec) {
+    if (resident && bm.nrec && bt.miter != staged) {
       uint32_t inflight = 0;
       for (uint32_t k = 0; k < nch; k++) {
         if (t == 0) {
@@ -509,6 +515,7 @@ __global__ void __launch_bounds__(kMaxWordBlock, 1) es_batch_w(const XBatchParam
         return;
       }
     }
+    staged = resident ? bt.miter : 0xFFFFFFFFu;
     uint64_t ub, ue;
     lane_range(bt.word_begin, bt.word_end, bm.n, ub, ue);
     if (resident) {
@@ -532,7 +539,8 @@ __global__ void __launch_bounds__(kMaxWordBlock, 1) es_batch_w(const XBatchParam
         }
         report(out_bits(S, bm.out_off, bm.out_compl, bm.n, u < ue), u, p.cex + bt.miter);
       }
-      __syncthreads();  // ring reuse by the next tile
+      __syncthreads();  // ring reuse by the next tile; btile written
+      tile = *btile;
       continue;
     }
     for (uint64_t u0 = ub; u0 < ue; u0 += T) {
@@ -591,7 +599,8 @@ __global__ void __launch_bounds__(kMaxWordBlock, 1) es_batch_w(const XBatchParam
       report(out_bits(S, bm.out_off, bm.out_compl, bm.n, u < ue), u, p.cex + bt.miter);
       __syncthreads();
     }
-    __syncthreads();  // ring reuse by the next tile
+    __syncthreads();  // ring reuse by the next tile; btile written
+    tile = *btile;
   }
 }
 
