@@ -44,8 +44,9 @@ namespace {
 // single-launch device times of equivalent miters -- the 12x12 and 16x16
 // multiplier miters, the adders, product-bit miters of 8..18-bit multipliers
 // and node-pair miters of 4..28 PIs (python -m paper_2512_06627_b300.calibrate
-// times that set).  Interpreter: 71 miters with the four-record steps,
-// median relative error 9%; specialised kernel: 74 miters, 18% (small
+// times that set).  Interpreter: 71 miters (four-record steps, barrier-free
+// resident passes, wider blocks where shared memory allows), median relative
+// error 8%; specialised kernel: 74 miters, 18% (small
 // kernels are dominated by launch latency, which three terms only
 // approximate).
 struct Builtin {
@@ -53,7 +54,7 @@ struct Builtin {
 };
 constexpr Builtin kRun[4] = {
     {0.0, 0.0, 0.0},                  // AUTO: unused
-    {9.419e-3, 3.451e-5, 1.4144e-4},  // INTERP: word-wide interpreter
+    {8.360e-3, 4.120e-5, 1.3133e-4},  // INTERP: word-wide interpreter
     {7.743e-3, 2.742e-6, 6.018e-7},   // JIT: specialised kernel
     {2.0e-2, 1.0e-4, 2.0e-3},         // SPILL: global-memory interpreter (rough)
 };
