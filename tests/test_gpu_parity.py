@@ -222,3 +222,37 @@ def test_step_programs_with_run_breaks(ctx, seed, reach):
             assert r.cex_or_none == _oracle(aig, o, wb, we)[0], (wb, we)
     t = [L.lec_es_submit(ctx, m) for m in ms]
     assert [L.lec_es_wait(ctx, x, 60.0).cex_or_none for x in t] == want
+
+
+def test_wide_interpreter_blocks_vs_oracle(ctx):
+    """Node-pair miters with 52..68 live slots are the ones whose
+    single-miter interpreter run takes a 384-thread block (at 256 threads
+    their slots leave room for one block per SM, at 384 for one 12-warp
+    block).  Every such miter is checked whole against the stored oracle
+    result, and a sample over partial word ranges against the oracle run on
+    the same range."""
+    import json
+    from tests.golden.make_config4_oracle import OUT, fingerprint
+    pb = C.config4_pairs()
+    stored = json.load(open(OUT))
+    assert stored["fingerprint"] == fingerprint(pb.aig)
+    f = pb.aig.flat_fanins()
+    picked = []
+    for i, o in enumerate(pb.aig.outputs):
+        m = L.Miter(pb.aig.num_pis, f, o)
+        info = L.lec_es_compile(m)[0]
+        if 52 <= info.num_slots <= 68 and info.n >= 16:
+            picked.append((i, m, info))
+    assert len(picked) >= 20
+    for i, m, _ in picked:
+        r = L.lec_es_check_ex(ctx, m, L.options(tier=L.TIER_INTERP))
+        assert r.cex_or_none == stored["cex"][i], i
+    rng = np.random.default_rng(5)
+    small = [x for x in picked if x[2].n <= 22]
+    for i, m, info in small[:: max(1, len(small) // 8)]:
+        W = 1 << (info.n - 6)
+        wb = int(rng.integers(0, W // 2))
+        we = int(rng.integers(wb + 1, W + 1))
+        want, _ = _oracle(pb.aig, pb.aig.outputs[i], wb, we)
+        r = L.lec_es_check_ex(ctx, m, L.options(wb, we, L.TIER_INTERP))
+        assert r.cex_or_none == want, (i, wb, we)
