@@ -114,7 +114,7 @@ typedef struct {
                                64..512 (a smaller multiple of 32 if it does not fit shared memory) */
   uint32_t grid_blocks;     /* 0 = library choice */
   uint32_t flags;           /* LEC_ES_FLAG_* */
-  uint32_t tile_granularity;/* batch: tiles per resident block slot (0 = 16) */
+  uint32_t tile_granularity;/* batch: tiles per resident block slot (0 = 8) */
   uint32_t stage_records;   /* batch: 16-byte records per staging stage, even, <= 2048 (0 = 256) */
 } lec_es_options;
 

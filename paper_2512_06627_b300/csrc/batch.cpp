@@ -59,7 +59,7 @@ constexpr int kDefaultBranches = 8;  // 4 / 8 / 16 branches: 3.85 / 3.80 / 3.78 
 struct Layout {
   int block = 256;            // threads (64-pattern words) per tile pass
   uint32_t ring_recs = 256;   // 16-byte records per staging stage (4 stages)
-  uint32_t granularity = 16;  // tiles per resident block slot
+  uint32_t granularity = 8;   // tiles per resident block slot (8 / 16 / 32 on the light node pairs at 384 threads: 1.13 / 1.16 / 1.19 ms)
 };
 }  // namespace
 
@@ -482,7 +482,7 @@ int autotune(lec_es_ctx *c, lec_es_batch_plan *b, int grid_override, Layout &bes
     for (int blk : {256, 128, 64})
       if (blk != blocks[0]) blocks.push_back(blk);
     for (int blk : blocks)
-      for (uint32_t gran : {4u, 16u, 64u}) {
+      for (uint32_t gran : {4u, 8u, 16u, 64u}) {
         Layout L{blk, ring, gran};
         if (batch_w_smem_bytes(b->max_slots, blk, ring) > (size_t)c->smem_optin) continue;
         if (stage_layout(c, b, L, grid_override, true) != LEC_ES_OK) continue;

@@ -100,7 +100,7 @@ def test_layouts_and_autotune_give_identical_results(ctx, pairs, tmp_path):
     b = L.lec_es_batch_prepare(tuned, ms, L.options(flags=L.FLAG_AUTOTUNE))
     info = L.lec_es_batch_info(b)
     assert info.block_threads % 32 == 0 and 64 <= info.block_threads <= 512
-    assert info.tile_granularity in (4, 16, 64)
+    assert info.tile_granularity in (4, 8, 16, 64)
     L.lec_es_batch_run_async(tuned, b)
     assert [r.cex for r in L.lec_es_batch_results(tuned, b, len(ms))] == ref
     L.lec_es_batch_free(tuned, b)
