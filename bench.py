@@ -474,6 +474,13 @@ def measure_batch_spread(ctx, args, headline_evals_per_s):
         assert rc == 0 and [r.cex for r in res] == ref
     L.lec_es_batch_free(ctx, b)
     plans = [L.lec_es_prepare(ctx, m, L.options(tier=t)) for m, t in zip(ms, tiers)]
+    # the specialised kernels' work at the LOP3 peak (as for the node pairs)
+    _, _, _, lop3_rate = L.lec_es_lop3_peak(ctx)
+    jit_lop3 = 0.0
+    for p, t in zip(plans, tiers):
+        if t == L.TIER_JIT:
+            inf = L.lec_es_plan_info(p)
+            jit_lop3 += inf.lop3_per_pass * float(1 << max(0, inf.n - 5))
     one_async, one_sync, dev = [], [], []
     for _ in range(2):
         torch.cuda.synchronize()
@@ -515,6 +522,9 @@ def measure_batch_spread(ctx, args, headline_evals_per_s):
         "node_pattern_evals": float(work.sum()),
         "batched_evals_per_s": float(work.sum()) / statistics.median(ts),
         "work_at_headline_rate_ms": float(work.sum()) / headline_evals_per_s * 1e3,
+        "jit_lop3_at_peak_ms": jit_lop3 / lop3_rate * 1e3,
+        "jit_lop3_at_peak_note": "the specialised kernels' generator lop3 count at the measured LOP3 peak: a "
+                                 "bound on the batch's time from its own-kernel miters alone",
         "prepare_s": prep, "jit_compile_s": layout.jit_ms / 1e3,
     }
 
