@@ -731,6 +731,45 @@ def measure_mutants(ctx, full_ms):
     return {"launch_floor_ms": floors, "cases": out}
 
 
+# The paper's Table 1 GPU-ES times (s) for its own n x n multiplier miters on
+# one RTX 4090 (its netlists are not published): context beside ours, not a
+# target.
+PAPER_TABLE1_GPU_ES_S = {14: 0.05, 15: 0.29, 16: 2.06, 17: 10.57, 18: 46.93, 19: 215.89, 20: 983.99}
+
+
+def measure_table1(ctx):
+    """Full enumerations of w x w array vs Booth/Dadda multiplier miters,
+    w = 12..20 (24..40 PIs, 2^24..2^40 patterns), on the specialised kernel:
+    the workload class of the paper's Table 1, whose GPU-ES time is quoted
+    beside each as context (other netlists, another GPU).  Each miter's
+    kernel is built first (the build time is reported; the 16x16 kernel is
+    already held); the time is the median of three launches up to w = 18 and
+    one launch for w = 19 and 20 (0.3 and 1.4 s).  Every verdict must be
+    EQUIVALENT."""
+    from paper_2512_06627_b300 import circuits as C
+    from paper_2512_06627_b300 import lec_es as L
+    out = {}
+    for w in (12, 14, 16, 17, 18, 19, 20):
+        m = L.miter_of(C.build_multiplier_pair(w, tree="dadda"))
+        t0 = time.perf_counter()
+        p = L.lec_es_prepare(ctx, m, L.options(tier=L.TIER_JIT))
+        build_s = time.perf_counter() - t0
+        info = L.lec_es_plan_info(p)
+        ts = []
+        for _ in range(3 if w <= 18 else 1):
+            L.lec_es_run_async(ctx, p)
+            r = L.lec_es_plan_result(ctx, p)
+            assert r.verdict == L.EQUIVALENT, (w, r.verdict, r.cex)
+            ts.append(r.device_ms)
+        L.lec_es_plan_free(ctx, p)
+        ms = statistics.median(ts)
+        out[f"{w}x{w}"] = {"pis": int(info.n), "cone_ands": int(info.cone_ands), "kernel_ms": ms,
+                           "node_pattern_evals_per_s": info.cone_ands * 2.0 ** info.n / (ms / 1e3),
+                           "lop3_per_pass": info.lop3_per_pass, "build_s": build_s,
+                           "paper_gpu_es_s": PAPER_TABLE1_GPU_ES_S.get(w)}
+    return out
+
+
 def measure_serve_full(ctx, args):
     """The served workload at its full size: every request of the seeded
     Poisson stream (array-vs-Booth product-bit miters, w in 8..18, 1%
@@ -955,6 +994,7 @@ def run_ours(args, ws, rank, local):
     if solo:
         line["time_to_verdict"] = measure_cold(dev)
         line["mutant_time_to_verdict"] = measure_mutants(ctx, statistics.median(kern_ms))
+        line["table1_multipliers"] = measure_table1(ctx)
     if solo and not args.no_batch:
         line["batched"] = measure_batch(ctx, args)
         line["batched_spread"] = measure_batch_spread(ctx, args, value)

@@ -69,6 +69,7 @@ struct JitKernel {
   uint32_t chunk_bits = 0;      // bits of the chunk index (support PIs - 5)
   uint64_t hash2 = 0;           // the program's second structure hash (checked on every cache hit)
   uint32_t built_regs = 0, built_plan = 0;  // budgets of the layout it was generated with (PTX form)
+  uint32_t built_copies = 0;                // its cap on unrolled copies (0: the default rule)
 };
 struct JitState;
 struct Server;

@@ -79,7 +79,7 @@ struct JitState {
 namespace {
 
 constexpr int kJitBlock = 128;
-constexpr int kCodegenVersion = 24;  // part of cached cubin names: bump whenever the generated code changes
+constexpr int kCodegenVersion = 25;  // part of cached cubin names: bump whenever the generated code changes
 // Values computed at one loop level and read at a deeper one: at most
 // kHoistPlan of them (see plan_hoist), those read by the innermost loop in
 // registers, the others in up to kHoistShared shared-memory slots per
@@ -318,6 +318,11 @@ struct SlotSplit {
   uint32_t inner_in_regs = 0;  // of those in registers, values the innermost loop reads
   bool grouped = false;        // passes run in straight-line groups (the same for every budget)
 };
+// Most straight-line copies of the innermost pass levels (see gen_ptx_lut).
+uint32_t unroll_copies(const LutProgram &lp) {
+  const char *unroll_env = getenv("LEC_ES_JIT_UNROLL");
+  return unroll_env ? (uint32_t)std::max(0, atoi(unroll_env)) : (lp.live <= kFewLive ? 64u : 4u);
+}
 // shared-memory slots per thread (LEC_ES_JIT_HOIST_SHARED lowers it)
 uint32_t shared_slots() {
   const char *sh = getenv("LEC_ES_JIT_HOIST_SHARED");
@@ -327,7 +332,7 @@ uint32_t shared_slots() {
 std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, uint32_t reg_budget,
                         uint32_t plan_budget, uint64_t pass_pis, const std::vector<uint64_t> &groups,
                         SlotSplit *split = nullptr, double *lop3_per_pass = nullptr,
-                        std::vector<uint64_t> *dump_clear = nullptr);
+                        std::vector<uint64_t> *dump_clear = nullptr, uint32_t copies_cap = 0);
 
 // Passes per grab (a power of two), the hoisting budget and the pass PIs of
 // a table-form kernel.  Long grabs amortise hoisted tables (and the
@@ -585,7 +590,8 @@ std::vector<BitRun> bit_runs(const std::vector<uint32_t> &pos) {  // pos ascendi
 // early exit skips a site.
 std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, uint32_t reg_budget,
                         uint32_t plan_budget, uint64_t pass_pis, const std::vector<uint64_t> &groups,
-                        SlotSplit *split, double *lop3_per_pass, std::vector<uint64_t> *dump_clear) {
+                        SlotSplit *split, double *lop3_per_pass, std::vector<uint64_t> *dump_clear,
+                        uint32_t copies_cap) {
   const bool dump = dump_clear != nullptr;
   const LutProgram &lp = g.lut;
   const uint32_t NA = lp.na, NP = lp.np;
@@ -613,10 +619,10 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   // eight: 4.10 ms -- a 90 KB kernel).  One with at most kFewLive live
   // values gets up to 64 (node-pair miters of 26-28 PIs, live sets 30-73:
   // four copies 0.019-0.078 ms, 8-64 copies 0.015-0.045 ms).
-  // LEC_ES_JIT_UNROLL sets the most copies (0: none).
-  const char *unroll_env = getenv("LEC_ES_JIT_UNROLL");
-  const uint32_t max_copies =
-      unroll_env ? (uint32_t)std::max(0, atoi(unroll_env)) : (lp.live <= kFewLive ? 64u : 4u);
+  // LEC_ES_JIT_UNROLL sets the most copies (0: none); a build whose
+  // unrolled copies spill may cap them lower (copies_cap, see
+  // compile_program_kernel).
+  const uint32_t max_copies = std::min(unroll_copies(lp), copies_cap ? copies_cap : ~0u);
   uint32_t U = 0;
   {
     uint64_t copies = 1, evals = 0;
@@ -1335,7 +1341,8 @@ int compile_cubin(const std::string &src, int major, int minor, std::vector<char
 
 // The table form goes straight to PTX and the PTX compiler; the AND form
 // goes through NVRTC.
-// built (optional) receives the register and plan budgets of the layout the
+// built (optional, three entries) receives the register and plan budgets
+// and the cap on unrolled copies (0: the default rule) of the layout the
 // returned kernel was generated with (the dump variant reuses them).
 int compile_program_kernel(const Program &g, bool lut_form, int major, int minor, std::vector<char> &cubin,
                            std::string &log, const GrabLayout *layout = nullptr, double *lop3_per_pass = nullptr,
@@ -1344,10 +1351,11 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
   if (!grouped) grouped = &grouped_sink;
   *grouped = false;
   double per_sink = 0;
-  uint32_t built_sink[2];
+  uint32_t built_sink[3];
   if (!lop3_per_pass) lop3_per_pass = &per_sink;
   if (!built) built = built_sink;
   *lop3_per_pass = 0;
+  built[2] = 0;  // copies cap (0: the default rule)
   // LEC_ES_JIT_NVRTC=1 compiles the table form from CUDA C++ through NVRTC
   // instead (same tables, for comparing the two compilation paths)
   static const bool via_nvrtc = getenv("LEC_ES_JIT_NVRTC") != nullptr;
@@ -1375,8 +1383,14 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
     // A large cone may need several builds.  Each step depends only on the
     // previous layout's slot split, so after a first build that spills (or
     // at once, for a single plan's build) the chain of layouts is generated
-    // up front and compiled on host threads together; the first without
-    // spills in chain order is the one the serial search would keep.
+    // up front and compiled on host threads together.  The spill usually
+    // comes from the unrolled copies' working set, which moving values to
+    // shared memory or shrinking the plan does not lower predictably, so a
+    // second chain halves the copies (from four to two, starting from the
+    // search's budgets).  Candidates are tried in order of the lop3 per pass
+    // they execute (chain order among equals); the first without spills is
+    // kept.  (17x17 multiplier miter: the four-copy chain ended at 726 lop3
+    // per pass and still spilled.)
     if (g.lut.count >= kParallelChainTables && !getenv("LEC_ES_JIT_SERIAL_BUILD")) {
       if (!t_single_build) {
         std::string lg;
@@ -1393,21 +1407,52 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
         }
         next_layout(split);
       }
-      std::vector<std::string> ptx;
-      std::vector<double> pers;
-      std::vector<std::pair<uint32_t, uint32_t>> budgets;
-      for (uint32_t i = 0; i < kMaxChain; i++) {
-        SlotSplit split;
+      struct Cand {
+        std::string ptx;
         double per = 0;
-        ptx.push_back(
-            gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis, layout->groups, &split, &per));
-        *grouped = split.grouped;
-        pers.push_back(per);
-        budgets.emplace_back(regs, plan);
+        uint32_t regs = 0, plan = 0, cap = 0;
+        bool grouped = false;
+      };
+      std::vector<Cand> cands;
+      for (uint32_t i = 0; i < 2 * kMaxChain; i++) {  // to its end (plan 0), the fallback when all spill
+        SlotSplit split;
+        Cand cd;
+        cd.ptx = gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis, layout->groups, &split, &cd.per);
+        cd.regs = regs;
+        cd.plan = plan;
+        cd.grouped = split.grouped;
+        cands.push_back(std::move(cd));
         if (plan == 0) break;
         next_layout(split);
       }
-      const size_t n = ptx.size();
+      const size_t chain_a = cands.size();
+      const bool a_ends_at_zero = plan == 0;
+      const uint32_t copies = unroll_copies(g.lut);
+      if (copies > 2 && copies <= 4) {
+        uint32_t r2 = layout->regs, p2 = layout->plan;
+        for (uint32_t i = 0; i < 2 * kMaxChain; i++) {  // its clean layout can be many steps down
+          SlotSplit split;
+          Cand cd;
+          cd.ptx = gen_ptx_lut(g, major, minor, layout->rep, r2, p2, layout->pass_pis, layout->groups, &split, &cd.per,
+                               nullptr, 2);
+          cd.regs = r2;
+          cd.plan = p2;
+          cd.cap = 2;
+          cd.grouped = split.grouped;
+          cands.push_back(std::move(cd));
+          if (p2 == 0) break;
+          if (split.inner_in_regs > 0 && split.in_shared < shared_slots()) {
+            r2 = split.inner_in_regs - std::min<uint32_t>(16, split.inner_in_regs);
+          } else {
+            p2 -= std::min<uint32_t>(16, p2);
+            r2 = std::min(r2, p2);
+          }
+        }
+      }
+      std::vector<size_t> order(cands.size());
+      for (size_t i = 0; i < order.size(); i++) order[i] = i;
+      std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cands[x].per < cands[y].per; });
+      const size_t n = order.size();
       std::vector<int> rcs(n, LEC_ES_EJIT);
       std::vector<std::string> logs(n);
       std::vector<std::vector<char>> bins(n);
@@ -1419,10 +1464,10 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
           size_t i;
           {
             std::lock_guard<std::mutex> lk(mu);
-            if (next_i >= n || next_i > first_ok) return;  // a layout earlier in the chain already built clean
+            if (next_i >= n || next_i > first_ok) return;  // a candidate earlier in the order already built clean
             i = next_i++;
           }
-          const int rc = compile_ptx(ptx[i], major, minor, bins[i], logs[i]);
+          const int rc = compile_ptx(cands[order[i]].ptx, major, minor, bins[i], logs[i]);
           std::lock_guard<std::mutex> lk(mu);
           rcs[i] = rc;
           done[i] = 1;
@@ -1434,23 +1479,37 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
       for (unsigned t = 1; t < nt; t++) pool.emplace_back(work);
       work();
       for (auto &t : pool) t.join();
-      for (size_t i = 0; i < n && done[i]; i++) {
-        if (rcs[i] != LEC_ES_OK || !spilled(logs[i]) || i + 1 == n) {
-          log += logs[i];
-          cubin = std::move(bins[i]);
-          *lop3_per_pass = pers[i];
-          built[0] = budgets[i].first;
-          built[1] = budgets[i].second;
-          if (rcs[i] != LEC_ES_OK || !spilled(logs[i]) || plan == 0) return rcs[i];
-        }
+      auto take = [&](size_t i) {
+        const Cand &cd = cands[order[i]];
+        if (getenv("LEC_ES_JIT_LOG"))
+          fprintf(stderr, "lec_es JIT %016llx: kept %.1f lop3 per pass (copies cap %u, %s), candidate %zu of %zu in order\n",
+                  (unsigned long long)g.hash, cd.per, cd.cap, spilled(logs[i]) ? "spills" : "no spills", i + 1, n);
+        log += logs[i];
+        cubin = std::move(bins[i]);
+        *lop3_per_pass = cd.per;
+        *grouped = cd.grouped;
+        built[0] = cd.regs;
+        built[1] = cd.plan;
+        built[2] = cd.cap;
+        return rcs[i];
+      };
+      for (size_t i = 0; i < n && done[i]; i++)
+        if (rcs[i] != LEC_ES_OK || !spilled(logs[i])) return take(i);
+      if (a_ends_at_zero) {  // every candidate spilled and the four-copy chain has no plan left: its last
+        for (size_t i = 0; i < n; i++)
+          if (order[i] == chain_a - 1) {
+            if (!done[i]) rcs[i] = compile_ptx(cands[order[i]].ptx, major, minor, bins[i], logs[i]);
+            return take(i);
+          }
       }
-      // every layout of the chain spilled: go on from the chain's end
+      // every candidate spilled: go on from the four-copy chain's end
     }
     for (;;) {
       std::string lg;
       SlotSplit split;
       built[0] = regs;
       built[1] = plan;
+      built[2] = 0;
       const int rc = compile_ptx(gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis,
                                              layout->groups, &split, lop3_per_pass),
                                  major, minor, cubin, lg);
@@ -1589,7 +1648,7 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   }
   double nvrtc_ms = 0;
   double lop3_per_pass = 0;  // of the PTX form's kernel (a sidecar file next to a cached cubin)
-  uint32_t budgets[2] = {lay.regs, lay.plan};  // register and plan budgets it was generated with
+  uint32_t budgets[3] = {lay.regs, lay.plan, 0};  // register, plan and copies budgets it was generated with
   bool grouped = false;                         // its passes run in straight-line groups
   if (path.empty() || !read_file(path, cubin)) {
     std::string log;
@@ -1605,7 +1664,7 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
       write_file(path, cubin);
       const std::string txt =
           std::to_string(lop3_per_pass) + " " + std::to_string(budgets[0]) + " " + std::to_string(budgets[1]) + " " +
-          std::to_string(grouped ? 1 : 0);
+          std::to_string(grouped ? 1 : 0) + " " + std::to_string(budgets[2]);
       write_file(path + ".lop3", std::vector<char>(txt.begin(), txt.end()));
     }
   } else {
@@ -1613,10 +1672,11 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
     if (read_file(path + ".lop3", txt)) {
       const std::string t(txt.begin(), txt.end());
       double per = 0;
-      unsigned r = budgets[0], pl = budgets[1], gr = 0;
-      if (sscanf(t.c_str(), "%lf %u %u %u", &per, &r, &pl, &gr) >= 1) lop3_per_pass = per;
+      unsigned r = budgets[0], pl = budgets[1], gr = 0, cp = 0;
+      if (sscanf(t.c_str(), "%lf %u %u %u %u", &per, &r, &pl, &gr, &cp) >= 1) lop3_per_pass = per;
       budgets[0] = r;
       budgets[1] = pl;
+      budgets[2] = cp;
       grouped = gr != 0;
     }
   }
@@ -1648,6 +1708,7 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   k->hash2 = g.hash2;
   k->built_regs = budgets[0];
   k->built_plan = budgets[1];
+  k->built_copies = budgets[2];
   if (ptx_form) {  // the PTX form: its grab layout
     k->rep_fixed = lay.rep;
     k->pass_bits = lay.pass_pis >> 5;
@@ -1968,7 +2029,7 @@ int jit_dump_tables(lec_es_ctx *c, const Program &g, uint64_t wb, uint64_t we, u
   std::vector<uint64_t> clear;
   const std::string ptx = gen_ptx_lut(g, c->cc_major, c->cc_minor, lay.rep, known ? k->built_regs : lay.regs,
                                       known ? k->built_plan : lay.plan, lay.pass_pis, lay.groups, nullptr, nullptr,
-                                      &clear);
+                                      &clear, k->built_copies);
   std::vector<char> cubin;
   std::string log;
   rc = compile_ptx(ptx, c->cc_major, c->cc_minor, cubin, log);

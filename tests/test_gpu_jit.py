@@ -480,3 +480,19 @@ def test_cold_check_of_a_cone_too_wide_for_a_kernel():
         assert want is None and r.cex_or_none == p
     finally:
         L.lec_es_destroy(c)
+
+
+def test_19x19_planted_minterms_past_2_to_32_chunks(ctx):
+    """A 19x19 multiplier miter has 38 PIs, so its 2^33 chunks of 32
+    patterns are indexed past 2^32.  With one planted minterm the only
+    counterexample is that pattern (closed form, pinned on the CPU for
+    small widths); the specialised kernel returns it for minterms whose
+    chunk index has bit 32 set and for the very last pattern (the whole
+    space enumerated), and the oracle agrees on the 64 words around it."""
+    for p in ((1 << 37) + (1 << 33) + 12345, (1 << 38) - 1):
+        mm = C.build_multiplier_pair(19, tree="dadda", planted_minterm=p)
+        r = jit(ctx, mm, mm.outputs[0])
+        assert r.support_n == 38
+        assert r.verdict == L.NONEQUIVALENT and r.cex == p, (hex(p), hex(r.cex))
+        lo = max(0, (p >> 6) - 32)
+        assert oracle_cex(mm, mm.outputs[0], lo, lo + 64) == p
