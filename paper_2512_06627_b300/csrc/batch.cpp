@@ -387,7 +387,7 @@ int stage_layout(lec_es_ctx *c, lec_es_batch_plan *b, const Layout &L, int grid_
     if (strided) next = nullptr;  // grabs by static stride: no counter
     jit_grab_range(kk, rep, cb, ce, &q0, &qend);
     void *args[] = {&cb, &ce, &cex, &ev, &next, &grabs, &rep, &q0, &qend};
-    if (cudaLaunchKernel((const void *)kk->kern, dim3((unsigned)grid), dim3(kk->block), args, 0,
+    if (cudaLaunchKernel((const void *)kk->kern, dim3((unsigned)grid), dim3(kk->block), args, kk->dyn_smem,
                          b->side[(q + 1) % b->branches]) != cudaSuccess)
       lerr = 1;
   }

@@ -70,6 +70,7 @@ struct JitKernel {
   uint64_t hash2 = 0;           // the program's second structure hash (checked on every cache hit)
   uint32_t built_regs = 0, built_plan = 0;  // budgets of the layout it was generated with (PTX form)
   uint32_t built_copies = 0;                // its cap on unrolled copies (0: the default rule)
+  size_t dyn_smem = 0;                      // dynamic shared memory every launch passes (bytes)
 };
 struct JitState;
 struct Server;

@@ -79,14 +79,21 @@ struct JitState {
 namespace {
 
 constexpr int kJitBlock = 128;
-constexpr int kCodegenVersion = 25;  // part of cached cubin names: bump whenever the generated code changes
+constexpr int kCodegenVersion = 26;  // part of cached cubin names: bump whenever the generated code changes
 // Values computed at one loop level and read at a deeper one: at most
 // kHoistPlan of them (see plan_hoist), those read by the innermost loop in
 // registers, the others in up to kHoistShared shared-memory slots per
-// thread (96 x 128 threads x 4 B = 48 KB, the most a kernel may declare
-// statically).
+// thread.  Up to kStaticShared slots (96 x 128 threads x 4 B = 48 KB, the
+// most a kernel may declare statically) are a static array; a kernel with
+// more declares them as dynamic shared memory and is launched with that size
+// (192 slots = 96 KB per block: two blocks still fit an SM, as the register
+// file allows).
 constexpr uint32_t kHoistPlan = 224;
-constexpr uint32_t kHoistShared = 96;
+constexpr uint32_t kHoistShared = 192;
+constexpr uint32_t kStaticShared = 96;
+// Dynamic shared memory a kernel with `slots` shared slots per thread is
+// launched with (0 when they fit the static array).
+size_t jit_dyn_smem(uint32_t slots) { return slots > kStaticShared ? (size_t)slots * kJitBlock * 4u : 0; }
 constexpr uint64_t kGrabsWanted = 4 * 148 * 8;  // four grabs per warp at 8 warps on each of 148 SMs
 // A kernel takes grabs by a static warp stride only when a launch has at
 // most two per resident warp; one whose full range has more grabs than
@@ -742,8 +749,11 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
   }
   std::ostringstream s;
   char buf[192];
-  s << ".version 9.0\n.target sm_" << major << minor << "a\n.address_size 64\n\n"
-    << ".visible .entry es_jit(.param .u64 p_cb, .param .u64 p_ce, .param .u64 p_cex, .param .u64 p_ev,\n"
+  s << ".version 9.0\n.target sm_" << major << minor << "a\n.address_size 64\n\n";
+  // more slots than a static array may hold: dynamic shared memory of
+  // nsmem * kJitBlock words, sized at launch (JitKernel::dyn_smem)
+  if (nsmem > kStaticShared) s << ".extern .shared .align 16 .b32 hs[];\n\n";
+  s << ".visible .entry es_jit(.param .u64 p_cb, .param .u64 p_ce, .param .u64 p_cex, .param .u64 p_ev,\n"
     << "    .param .u64 p_next, .param .u64 p_maxg, .param .u64 p_rep, .param .u64 p_q0, .param .u64 p_qend"
     << (dump ? ", .param .u64 p_tt" : "") << ")\n"
     << ".maxntid " << kJitBlock << ", 1, 1\n{\n"
@@ -751,7 +761,7 @@ std::string gen_ptx_lut(const Program &g, int major, int minor, uint32_t REP, ui
     << "  .reg .b64 %o<" << L << ">;\n"
     << "  .reg .b32 %v<" << (NA + 1) << ">;\n  .reg .b32 %s<" << (NA + 1) << ">;\n  .reg .b32 %q<" << (NP + 1)
     << ">;\n  .reg .b32 %po<" << kGroupPasses << ">;\n";
-  if (nsmem) s << "  .shared .align 16 .b32 hs[" << nsmem * kJitBlock << "];\n";
+  if (nsmem && nsmem <= kStaticShared) s << "  .shared .align 16 .b32 hs[" << nsmem * kJitBlock << "];\n";
   if (dump) s << "  .reg .b32 %z<2>;\n  ld.param.u64 %d38, [p_tt];\n  cvta.to.global.u64 %d38, %d38;\n";
   // parameters; grab range [d8, d9); lane; first grab; first counterexample poll
   s << "  ld.param.u64 %d1, [p_cb];\n  ld.param.u64 %d2, [p_ce];\n  ld.param.u64 %d3, [p_cex];\n"
@@ -1341,9 +1351,10 @@ int compile_cubin(const std::string &src, int major, int minor, std::vector<char
 
 // The table form goes straight to PTX and the PTX compiler; the AND form
 // goes through NVRTC.
-// built (optional, three entries) receives the register and plan budgets
+// built (optional, four entries) receives the register and plan budgets
 // and the cap on unrolled copies (0: the default rule) of the layout the
-// returned kernel was generated with (the dump variant reuses them).
+// returned kernel was generated with (the dump variant reuses them), and
+// its shared-memory slots per thread (above kStaticShared: dynamic).
 int compile_program_kernel(const Program &g, bool lut_form, int major, int minor, std::vector<char> &cubin,
                            std::string &log, const GrabLayout *layout = nullptr, double *lop3_per_pass = nullptr,
                            uint32_t *built = nullptr, bool *grouped = nullptr) {
@@ -1351,11 +1362,12 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
   if (!grouped) grouped = &grouped_sink;
   *grouped = false;
   double per_sink = 0;
-  uint32_t built_sink[3];
+  uint32_t built_sink[4];
   if (!lop3_per_pass) lop3_per_pass = &per_sink;
   if (!built) built = built_sink;
   *lop3_per_pass = 0;
   built[2] = 0;  // copies cap (0: the default rule)
+  built[3] = 0;  // shared-memory slots per thread
   // LEC_ES_JIT_NVRTC=1 compiles the table form from CUDA C++ through NVRTC
   // instead (same tables, for comparing the two compilation paths)
   static const bool via_nvrtc = getenv("LEC_ES_JIT_NVRTC") != nullptr;
@@ -1401,6 +1413,7 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
                                                layout->groups, &split, lop3_per_pass),
                                    major, minor, cubin, lg);
         *grouped = split.grouped;
+        built[3] = split.in_shared;
         if (rc != LEC_ES_OK || !spilled(lg) || plan == 0) {
           log += lg;
           return rc;
@@ -1410,7 +1423,7 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
       struct Cand {
         std::string ptx;
         double per = 0;
-        uint32_t regs = 0, plan = 0, cap = 0;
+        uint32_t regs = 0, plan = 0, cap = 0, shared = 0;
         bool grouped = false;
       };
       std::vector<Cand> cands;
@@ -1420,6 +1433,7 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
         cd.ptx = gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis, layout->groups, &split, &cd.per);
         cd.regs = regs;
         cd.plan = plan;
+        cd.shared = split.in_shared;
         cd.grouped = split.grouped;
         cands.push_back(std::move(cd));
         if (plan == 0) break;
@@ -1438,6 +1452,7 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
           cd.regs = r2;
           cd.plan = p2;
           cd.cap = 2;
+          cd.shared = split.in_shared;
           cd.grouped = split.grouped;
           cands.push_back(std::move(cd));
           if (p2 == 0) break;
@@ -1491,6 +1506,7 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
         built[0] = cd.regs;
         built[1] = cd.plan;
         built[2] = cd.cap;
+        built[3] = cd.shared;
         return rcs[i];
       };
       for (size_t i = 0; i < n && done[i]; i++)
@@ -1514,6 +1530,7 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
                                              layout->groups, &split, lop3_per_pass),
                                  major, minor, cubin, lg);
       *grouped = split.grouped;
+      built[3] = split.in_shared;
       if (rc != LEC_ES_OK || !spilled(lg) || plan == 0) {
         log += lg;
         return rc;
@@ -1648,7 +1665,8 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
   }
   double nvrtc_ms = 0;
   double lop3_per_pass = 0;  // of the PTX form's kernel (a sidecar file next to a cached cubin)
-  uint32_t budgets[3] = {lay.regs, lay.plan, 0};  // register, plan and copies budgets it was generated with
+  uint32_t budgets[4] = {lay.regs, lay.plan, 0, 0};  // register, plan and copies budgets it was generated with,
+                                                     // and its shared-memory slots per thread
   bool grouped = false;                         // its passes run in straight-line groups
   if (path.empty() || !read_file(path, cubin)) {
     std::string log;
@@ -1664,7 +1682,7 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
       write_file(path, cubin);
       const std::string txt =
           std::to_string(lop3_per_pass) + " " + std::to_string(budgets[0]) + " " + std::to_string(budgets[1]) + " " +
-          std::to_string(grouped ? 1 : 0) + " " + std::to_string(budgets[2]);
+          std::to_string(grouped ? 1 : 0) + " " + std::to_string(budgets[2]) + " " + std::to_string(budgets[3]);
       write_file(path + ".lop3", std::vector<char>(txt.begin(), txt.end()));
     }
   } else {
@@ -1672,11 +1690,12 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
     if (read_file(path + ".lop3", txt)) {
       const std::string t(txt.begin(), txt.end());
       double per = 0;
-      unsigned r = budgets[0], pl = budgets[1], gr = 0, cp = 0;
-      if (sscanf(t.c_str(), "%lf %u %u %u %u", &per, &r, &pl, &gr, &cp) >= 1) lop3_per_pass = per;
+      unsigned r = budgets[0], pl = budgets[1], gr = 0, cp = 0, sh = 0;
+      if (sscanf(t.c_str(), "%lf %u %u %u %u %u", &per, &r, &pl, &gr, &cp, &sh) >= 1) lop3_per_pass = per;
       budgets[0] = r;
       budgets[1] = pl;
       budgets[2] = cp;
+      budgets[3] = sh;
       grouped = gr != 0;
     }
   }
@@ -1689,13 +1708,21 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
     delete k;
     return LEC_ES_EJIT;
   }
+  // slots beyond a static array's: dynamic shared memory, allowed once here
+  k->dyn_smem = jit_dyn_smem(budgets[3]);
+  if (k->dyn_smem && cudaKernelSetAttributeForDevice(k->kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)k->dyn_smem, c->device) != cudaSuccess) {
+    cudaLibraryUnload(k->lib);
+    delete k;
+    return LEC_ES_EJIT;
+  }
   cudaFuncAttributes attr;
   if (cudaFuncGetAttributes(&attr, (const void *)k->kern) == cudaSuccess) {
     k->regs = attr.numRegs;
     k->local_bytes = attr.localSizeBytes;
   }
   int bps = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void *)k->kern, kJitBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void *)k->kern, kJitBlock, k->dyn_smem);
   k->blocks_per_sm = std::max(1, bps);
   k->block = kJitBlock;
   k->num_luts = g.lut.count;
@@ -2003,7 +2030,8 @@ int jit_launch(lec_es_ctx *c, lec_es_plan *p, uint64_t chunk_begin, uint64_t chu
   uint64_t q0 = 0, qend = 0;
   jit_grab_range(p->jit, rep, chunk_begin, chunk_end, &q0, &qend);
   void *args[] = {&chunk_begin, &chunk_end, &cex, &evaluated, &next, &max_grabs, &rep, &q0, &qend};
-  cudaError_t e = cudaLaunchKernel((const void *)p->jit->kern, dim3(g), dim3(p->jit_block), args, 0, p->stream);
+  cudaError_t e =
+      cudaLaunchKernel((const void *)p->jit->kern, dim3(g), dim3(p->jit_block), args, p->jit->dyn_smem, p->stream);
   return e == cudaSuccess ? 0 : (int)e;
 }
 
@@ -2057,17 +2085,21 @@ int jit_dump_tables(lec_es_ctx *c, const Program &g, uint64_t wb, uint64_t we, u
     uint64_t cb = std::min<uint64_t>(2 * wb, NCH), ce = std::min<uint64_t>(2 * we, NCH);
     uint64_t rep = lay.rep, q0 = 0, qend = 0, maxg = ~0ull;
     jit_grab_range(k, rep, cb, ce, &q0, &qend);
+    cudaError_t e = cudaSuccess;
+    if (k->dyn_smem)
+      e = cudaKernelSetAttributeForDevice(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k->dyn_smem,
+                                          c->device);
     int bps = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void *)kern, kJitBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void *)kern, kJitBlock, k->dyn_smem);
     const unsigned grid = (unsigned)std::max(1, c->sm_count * std::max(1, bps));
     unsigned long long *cex = d_res, *ev = d_res + 1, *next = d_res + 3;  // a counter: no static stride
     void *tt = d_tt;
     void *args[] = {&cb, &ce, &cex, &ev, &next, &maxg, &rep, &q0, &qend, &tt};
     h.resize(NT * stride);
-    cudaError_t e = cudaMemsetAsync(d_tt, 0, bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_tt, 0, bytes, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(d_res, c->h_init, kResWords * 8, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaLaunchKernel((const void *)kern, dim3(grid), dim3(kJitBlock), args, 0, st);
+    if (e == cudaSuccess) e = cudaLaunchKernel((const void *)kern, dim3(grid), dim3(kJitBlock), args, k->dyn_smem, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d_tt, bytes, cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess || e != cudaSuccess) err = LEC_ES_ECUDA;
   }

@@ -247,7 +247,7 @@ int launch(Server *s, Request *r) {
     void *args[] = {&cb, &ce, &cex, &ev, &next, &grabs, &rep, &q0, &qend};
     const uint64_t per_block = (uint64_t)(k->block / 32) * 32 * grabs * rep;
     const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>((C + per_block - 1) / per_block, 1u << 30));
-    err = cudaLaunchKernel((const void *)k->kern, dim3((unsigned)grid), dim3(k->block), args, 0, st) ==
+    err = cudaLaunchKernel((const void *)k->kern, dim3((unsigned)grid), dim3(k->block), args, k->dyn_smem, st) ==
                   cudaSuccess
               ? 0
               : 1;
