@@ -36,7 +36,7 @@ WORKLOAD = "16x16 array vs radix-4 Booth/Dadda multiplier miter, 32 PIs, 2^32 pa
 # the generated kernel are the ones that were captured.
 NCU_TRAFFIC = {("jit", 0xdfdebdb6dd06a0a8, 1714, 21): 57600, ("jit", 0xdfdebdb6dd06a0a8, 1714, 22): 56832,
                ("jit", 0xdfdebdb6dd06a0a8, 1714, 23): 56832, ("jit", 0xdfdebdb6dd06a0a8, 1714, 24): 57344,
-               ("jit", 0xdfdebdb6dd06a0a8, 1714, 25): 57088}
+               ("jit", 0xdfdebdb6dd06a0a8, 1714, 25): 57088, ("jit", 0xdfdebdb6dd06a0a8, 1714, 26): 57088}
 
 
 CASES = ["mult16-jit", "mult16-interp", "mult12-interp", "pairs-light", "pairs-all", "pair-jit", "sweep-32x32",
