@@ -1399,10 +1399,12 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
     // comes from the unrolled copies' working set, which moving values to
     // shared memory or shrinking the plan does not lower predictably, so a
     // second chain halves the copies (from four to two, starting from the
-    // search's budgets).  Candidates are tried in order of the lop3 per pass
-    // they execute (chain order among equals); the first without spills is
-    // kept.  (17x17 multiplier miter: the four-copy chain ended at 726 lop3
-    // per pass and still spilled.)
+    // search's budgets), at most kMaxChain steps each.  Candidates are tried
+    // in order of the lop3 per pass they execute (chain order among equals);
+    // the first without spills is kept.  If all spill, the build goes on
+    // from the four-copy chain's end, one layout at a time.  (17x17
+    // multiplier miter with 96 shared slots: the four-copy chain ended at
+    // 726 lop3 per pass and still spilled, the two-copy one reached 631.)
     if (g.lut.count >= kParallelChainTables && !getenv("LEC_ES_JIT_SERIAL_BUILD")) {
       if (!t_single_build) {
         std::string lg;
@@ -1426,44 +1428,42 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
         uint32_t regs = 0, plan = 0, cap = 0, shared = 0;
         bool grouped = false;
       };
-      std::vector<Cand> cands;
-      for (uint32_t i = 0; i < 2 * kMaxChain; i++) {  // to its end (plan 0), the fallback when all spill
-        SlotSplit split;
-        Cand cd;
-        cd.ptx = gen_ptx_lut(g, major, minor, layout->rep, regs, plan, layout->pass_pis, layout->groups, &split, &cd.per);
-        cd.regs = regs;
-        cd.plan = plan;
-        cd.shared = split.in_shared;
-        cd.grouped = split.grouped;
-        cands.push_back(std::move(cd));
-        if (plan == 0) break;
-        next_layout(split);
-      }
-      const size_t chain_a = cands.size();
-      const bool a_ends_at_zero = plan == 0;
-      const uint32_t copies = unroll_copies(g.lut);
-      if (copies > 2 && copies <= 4) {
-        uint32_t r2 = layout->regs, p2 = layout->plan;
-        for (uint32_t i = 0; i < 2 * kMaxChain; i++) {  // its clean layout can be many steps down
+      // the two chains are generated on two host threads (each step of a
+      // chain depends on the previous step's slot split)
+      auto gen_chain = [&](uint32_t cap, uint32_t r, uint32_t pl, std::vector<Cand> &out) {
+        for (uint32_t i = 0; i < kMaxChain; i++) {
           SlotSplit split;
           Cand cd;
-          cd.ptx = gen_ptx_lut(g, major, minor, layout->rep, r2, p2, layout->pass_pis, layout->groups, &split, &cd.per,
-                               nullptr, 2);
-          cd.regs = r2;
-          cd.plan = p2;
-          cd.cap = 2;
+          cd.ptx = gen_ptx_lut(g, major, minor, layout->rep, r, pl, layout->pass_pis, layout->groups, &split, &cd.per,
+                               nullptr, cap);
+          cd.regs = r;
+          cd.plan = pl;
+          cd.cap = cap;
           cd.shared = split.in_shared;
           cd.grouped = split.grouped;
-          cands.push_back(std::move(cd));
-          if (p2 == 0) break;
+          out.push_back(std::move(cd));
+          if (pl == 0) break;
           if (split.inner_in_regs > 0 && split.in_shared < shared_slots()) {
-            r2 = split.inner_in_regs - std::min<uint32_t>(16, split.inner_in_regs);
+            r = split.inner_in_regs - std::min<uint32_t>(16, split.inner_in_regs);
           } else {
-            p2 -= std::min<uint32_t>(16, p2);
-            r2 = std::min(r2, p2);
+            pl -= std::min<uint32_t>(16, pl);
+            r = std::min(r, pl);
           }
         }
-      }
+        return std::make_pair(r, pl);
+      };
+      std::vector<Cand> cands, chain_b;
+      const uint32_t copies = unroll_copies(g.lut);
+      std::thread tb;
+      if (copies > 2 && copies <= 4)
+        tb = std::thread([&]() { gen_chain(2, layout->regs, layout->plan, chain_b); });
+      const auto a_end = gen_chain(0, regs, plan, cands);
+      if (tb.joinable()) tb.join();
+      const size_t chain_a = cands.size();
+      const bool a_ends_at_zero = cands.back().plan == 0;
+      regs = a_end.first;  // where the serial continuation goes on from
+      plan = a_end.second;
+      for (Cand &cd : chain_b) cands.push_back(std::move(cd));
       std::vector<size_t> order(cands.size());
       for (size_t i = 0; i < order.size(); i++) order[i] = i;
       std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cands[x].per < cands[y].per; });
