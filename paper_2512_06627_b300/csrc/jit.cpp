@@ -1452,71 +1452,106 @@ int compile_program_kernel(const Program &g, bool lut_form, int major, int minor
         }
         return std::make_pair(r, pl);
       };
-      std::vector<Cand> cands, chain_b;
+      // Waves: the first holds kMaxChain steps of each chain; while the
+      // four-copy chain has steps left and its last step's lop3 per pass is
+      // still below the best clean candidate's, the next wave continues it
+      // (more values in shared memory, then a smaller plan).
       const uint32_t copies = unroll_copies(g.lut);
-      std::thread tb;
-      if (copies > 2 && copies <= 4)
-        tb = std::thread([&]() { gen_chain(2, layout->regs, layout->plan, chain_b); });
-      const auto a_end = gen_chain(0, regs, plan, cands);
-      if (tb.joinable()) tb.join();
-      const size_t chain_a = cands.size();
-      const bool a_ends_at_zero = cands.back().plan == 0;
-      regs = a_end.first;  // where the serial continuation goes on from
-      plan = a_end.second;
-      for (Cand &cd : chain_b) cands.push_back(std::move(cd));
-      std::vector<size_t> order(cands.size());
-      for (size_t i = 0; i < order.size(); i++) order[i] = i;
-      std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cands[x].per < cands[y].per; });
-      const size_t n = order.size();
-      std::vector<int> rcs(n, LEC_ES_EJIT);
-      std::vector<std::string> logs(n);
-      std::vector<std::vector<char>> bins(n);
-      std::vector<uint8_t> done(n, 0);
-      std::mutex mu;
-      size_t next_i = 0, first_ok = n;
-      auto work = [&]() {
-        for (;;) {
-          size_t i;
-          {
+      std::vector<char> best_bin;
+      std::string best_log;
+      Cand best;
+      bool have_best = false;
+      int rc_fail = LEC_ES_OK;
+      const double t0 = now_ms();
+      for (uint32_t wave = 0; wave < 4; wave++) {
+        std::vector<Cand> cands, chain_b;
+        std::thread tb;
+        if (wave == 0 && copies > 2 && copies <= 4)
+          tb = std::thread([&]() { gen_chain(2, layout->regs, layout->plan, chain_b); });
+        const auto a_end = gen_chain(0, regs, plan, cands);
+        if (tb.joinable()) tb.join();
+        const size_t chain_a = cands.size();
+        const Cand a_last = cands.back();
+        regs = a_end.first;
+        plan = a_end.second;
+        for (Cand &cd : chain_b) cands.push_back(std::move(cd));
+        std::vector<size_t> order(cands.size());
+        for (size_t i = 0; i < order.size(); i++) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cands[x].per < cands[y].per; });
+        const size_t n = order.size();
+        std::vector<int> rcs(n, LEC_ES_EJIT);
+        std::vector<std::string> logs(n);
+        std::vector<std::vector<char>> bins(n);
+        std::vector<uint8_t> done(n, 0);
+        std::mutex mu;
+        size_t next_i = 0, first_ok = n;
+        auto work = [&]() {
+          for (;;) {
+            size_t i;
+            {
+              std::lock_guard<std::mutex> lk(mu);
+              if (next_i >= n || next_i > first_ok) return;  // a candidate earlier in the order already built clean
+              if (have_best && cands[order[next_i]].per >= best.per) return;  // no better than the kept one
+              i = next_i++;
+            }
+            const int rc = compile_ptx(cands[order[i]].ptx, major, minor, bins[i], logs[i]);
             std::lock_guard<std::mutex> lk(mu);
-            if (next_i >= n || next_i > first_ok) return;  // a candidate earlier in the order already built clean
-            i = next_i++;
+            rcs[i] = rc;
+            done[i] = 1;
+            if (rc == LEC_ES_OK && !spilled(logs[i])) first_ok = std::min(first_ok, i);
           }
-          const int rc = compile_ptx(cands[order[i]].ptx, major, minor, bins[i], logs[i]);
-          std::lock_guard<std::mutex> lk(mu);
-          rcs[i] = rc;
-          done[i] = 1;
-          if (rc == LEC_ES_OK && !spilled(logs[i])) first_ok = std::min(first_ok, i);
+        };
+        const unsigned nt = (unsigned)std::min<size_t>(n, std::max(1u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> pool;
+        for (unsigned t = 1; t < nt; t++) pool.emplace_back(work);
+        work();
+        for (auto &t : pool) t.join();
+        for (size_t i = 0; i < n && done[i]; i++) {
+          if (rcs[i] != LEC_ES_OK) {
+            rc_fail = rcs[i];
+            break;
+          }
+          if (spilled(logs[i])) continue;
+          if (!have_best || cands[order[i]].per < best.per) {
+            best = cands[order[i]];
+            best_bin = std::move(bins[i]);
+            best_log = logs[i];
+            have_best = true;
+          }
+          break;
         }
-      };
-      const unsigned nt = (unsigned)std::min<size_t>(n, std::max(1u, std::thread::hardware_concurrency()));
-      std::vector<std::thread> pool;
-      for (unsigned t = 1; t < nt; t++) pool.emplace_back(work);
-      work();
-      for (auto &t : pool) t.join();
-      auto take = [&](size_t i) {
-        const Cand &cd = cands[order[i]];
+        if (rc_fail) break;
+        const bool a_done = a_last.plan == 0;
+        if (!have_best && a_done) {  // every candidate spilled and the four-copy chain has no plan left: its last
+          for (size_t i = 0; i < n; i++)
+            if (order[i] == chain_a - 1) {
+              if (!done[i]) rcs[i] = compile_ptx(cands[order[i]].ptx, major, minor, bins[i], logs[i]);
+              if (rcs[i] != LEC_ES_OK) return rcs[i];
+              best = cands[order[i]];
+              best_bin = std::move(bins[i]);
+              best_log = logs[i];
+              have_best = true;
+            }
+          break;
+        }
+        if (a_done || (have_best && a_last.per >= best.per)) break;
+      }
+      if (rc_fail) return rc_fail;
+      if (have_best) {
         if (getenv("LEC_ES_JIT_LOG"))
-          fprintf(stderr, "lec_es JIT %016llx: kept %.1f lop3 per pass (copies cap %u, %s), candidate %zu of %zu in order\n",
-                  (unsigned long long)g.hash, cd.per, cd.cap, spilled(logs[i]) ? "spills" : "no spills", i + 1, n);
-        log += logs[i];
-        cubin = std::move(bins[i]);
-        *lop3_per_pass = cd.per;
-        *grouped = cd.grouped;
-        built[0] = cd.regs;
-        built[1] = cd.plan;
-        built[2] = cd.cap;
-        built[3] = cd.shared;
-        return rcs[i];
-      };
-      for (size_t i = 0; i < n && done[i]; i++)
-        if (rcs[i] != LEC_ES_OK || !spilled(logs[i])) return take(i);
-      if (a_ends_at_zero) {  // every candidate spilled and the four-copy chain has no plan left: its last
-        for (size_t i = 0; i < n; i++)
-          if (order[i] == chain_a - 1) {
-            if (!done[i]) rcs[i] = compile_ptx(cands[order[i]].ptx, major, minor, bins[i], logs[i]);
-            return take(i);
-          }
+          fprintf(stderr,
+                  "lec_es JIT %016llx: kept %.1f lop3 per pass (copies cap %u, %u shared slots, %s) in %.0f ms\n",
+                  (unsigned long long)g.hash, best.per, best.cap, best.shared,
+                  spilled(best_log) ? "spills" : "no spills", now_ms() - t0);
+        log += best_log;
+        cubin = std::move(best_bin);
+        *lop3_per_pass = best.per;
+        *grouped = best.grouped;
+        built[0] = best.regs;
+        built[1] = best.plan;
+        built[2] = best.cap;
+        built[3] = best.shared;
+        return LEC_ES_OK;
       }
       // every candidate spilled: go on from the four-copy chain's end
     }
