@@ -40,7 +40,7 @@ NCU_TRAFFIC = {("jit", 0xdfdebdb6dd06a0a8, 1714, 21): 57600, ("jit", 0xdfdebdb6d
 
 
 CASES = ["mult16-jit", "mult16-interp", "mult12-interp", "pairs-light", "pairs-all", "pair-jit", "sweep-32x32",
-         "mult16-planted-jit"]
+         "mult16-planted-jit", "mult17-jit"]
 
 
 def parse():
@@ -1063,7 +1063,9 @@ def run_case(args):
       pairs-all          all 4,096 node-pair miters, one prepared batch
       pair-jit           one node-pair miter of support --n on the specialised kernel
       sweep-32x32        random-simulation signatures of the 32x32 four-multiplier graph
-      mult16-planted-jit the 16x16 miter with a minterm planted at 2^31 + 12,345 (early exit)"""
+      mult16-planted-jit the 16x16 miter with a minterm planted at 2^31 + 12,345 (early exit)
+      mult17-jit         the 17x17 array vs Booth/Dadda miter on the specialised kernel (values kept
+                         across loops in dynamic shared memory)"""
     from paper_2512_06627_b300 import build as B
     from paper_2512_06627_b300 import circuits as C
     from paper_2512_06627_b300 import lec_es as L
@@ -1079,6 +1081,8 @@ def run_case(args):
     elif a.case.startswith("mult"):
         if a.case == "mult16-planted-jit":
             aig = C.config3_mult16(minterm=(1 << 31) + 12345)
+        elif a.case == "mult17-jit":
+            aig = C.build_multiplier_pair(17, tree="dadda")
         else:
             aig = C.config3_mult16() if a.case.startswith("mult16") else C.config2_mult12()
         tier = L.TIER_JIT if a.case.endswith("jit") else L.TIER_INTERP
