@@ -325,6 +325,20 @@ def test_jit_compiles_for_sm103a_without_spills():
         assert "0 bytes spill stores" in log, log
 
 
+def test_jit_keeps_values_in_dynamic_shared_memory_for_17x17():
+    """The 17x17 miter's kernel keeps more values across its pass loops than
+    a static shared array may hold (96 slots per thread): the generated PTX
+    declares them as dynamic shared memory, ptxas accepts it, and the kept
+    layout compiles with no spills (its four-copy layouts with at most 96
+    slots all spilled)."""
+    import re as _re
+    log, nbytes = L.lec_es_jit_compile(L.miter_of(C.build_multiplier_pair(17, tree="dadda")), 10, 3)
+    assert nbytes > 0
+    assert int(_re.search(r"Used (\d+) registers", log).group(1)) <= 255
+    assert "0 bytes spill stores" in log, log
+    assert "bytes smem" not in log  # no static shared array: its slots are dynamic
+
+
 @pytest.mark.parametrize("rep,hoist,nest", [("4", "0", "2"), ("16", "0", "1"), ("16", "64", "2"), ("32", "128", "1"),
                                             ("16", "128", "0"), ("32", "128", "3")])
 def test_jit_grab_shapes_and_hoisting_compile_without_spills(rep, hoist, nest, monkeypatch):
