@@ -52,7 +52,7 @@ namespace {
 // 0.03 / 0.025 / 0.02 / 0.0125 / 0.005 ms -> 25.3 / 10.5 / 5.39 / 4.09 /
 // 3.89 / 3.84 / 4.05 / 5.12 ms per batch.
 constexpr double kBatchJitMs = 0.02;
-constexpr uint32_t kBatchJitLive = 230;  // table live set that still fits the register file
+constexpr uint32_t kBatchJitLive = 288;  // table live set given an own kernel (as a single check's)
 constexpr int kMaxBranches = 64;         // parallel graph branches (at most)
 constexpr int kDefaultBranches = 8;  // 4 / 8 / 16 branches: 3.85 / 3.80 / 3.78 ms on the 4,096-pair batch
 

@@ -109,7 +109,11 @@ constexpr uint32_t kDryPlan = 160;  // plan of the layout search's dry runs (see
 // otherwise idle): a large cone's first layout and the rest of its chain then
 // build at once, instead of the rest only after the first spills.
 thread_local bool t_single_build = false;
-constexpr uint32_t kMaxJitLive = 230;        // table live set that still fits the register file
+// Largest table live set given a specialised kernel: values kept across pass
+// loops go to registers and up to kHoistShared shared slots, and a layout
+// that still spills is kept only if every candidate does (whole multiplier
+// miters: 16x16 198 live, 18x18 237, 20x20 265, all built without spills).
+constexpr uint32_t kMaxJitLive = 288;
 // A cone whose tables keep at most kFewLive values live is not register-bound:
 // its innermost pass levels unroll into up to 64 copies, and the passes run
 // in straight-line groups of up to kGroupPasses passes and kGroupEvals table

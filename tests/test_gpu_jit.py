@@ -496,3 +496,28 @@ def test_19x19_planted_minterms_past_2_to_32_chunks(ctx):
         assert r.verdict == L.NONEQUIVALENT and r.cex == p, (hex(p), hex(r.cex))
         lo = max(0, (p >> 6) - 32)
         assert oracle_cex(mm, mm.outputs[0], lo, lo + 64) == p
+
+
+def test_wide_live_sets_in_batch_server_and_auto(ctx):
+    """Cones whose tables keep more values live than a static shared array
+    holds run as specialised kernels with dynamic shared memory on every
+    path: a 17x17 miter with one planted minterm (235 live tables) as a
+    batch's own kernel and as a served request with the kernel held, and an
+    18x18 one (about 250 live) through a default AUTO check, which starts on
+    the interpreter and hands the rest of the range to the kernel when its
+    build lands.  Each returns the planted pattern, the only
+    counterexample."""
+    p17 = (1 << 33) + 4321
+    m17 = L.miter_of(C.build_multiplier_pair(17, tree="dadda", planted_minterm=p17))
+    small = [L.miter_of(C.config1_adders(s)) for s in (None, 1, 2)]
+    got = L.lec_es_batch(ctx, small + [m17])
+    assert got[3].cex == p17 and got[3].tier == L.TIER_JIT
+    assert [r.cex_or_none for r in got[:3]] == [L.lec_es_check(ctx, m).cex_or_none for m in small]
+    r = L.lec_es_wait(ctx, L.lec_es_submit(ctx, m17), 600.0)
+    assert r.cex == p17 and r.tier == L.TIER_JIT
+    p18 = (1 << 35) + (1 << 20) + 99
+    aig18 = C.build_multiplier_pair(18, tree="dadda", planted_minterm=p18)
+    r = L.lec_es_check(ctx, L.miter_of(aig18))
+    assert r.cex == p18 and r.support_n == 36
+    lo = (p18 >> 6) - 32
+    assert oracle_cex(aig18, aig18.outputs[0], lo, lo + 64) == p18
