@@ -662,7 +662,9 @@ namespace lec {
 // A check the AUTO tier sends to the interpreter while its cone could run
 // as a specialised kernel that the context does not hold yet: the kernel's
 // build is scheduled in the background at once, and the interpreter runs
-// the word range in ascending slices of about kRaceSliceMs each.  A slice
+// the word range in ascending slices, the first of about kRaceSliceMs, each
+// next twice as long up to kRaceSliceMaxMs (fewer slice boundaries, where the
+// GPU waits for the host; a landed kernel waits at most that long).  A slice
 // that fails ends the check (its counterexample is the lowest: every lower
 // word has passed); once the kernel lands, the rest of the range goes to it.
 // So a cold check takes about the lesser of the interpreter's time and the
@@ -670,6 +672,7 @@ namespace lec {
 // finds the kernel built.  Worth it only where a build can pay off.
 constexpr double kRaceMinMs = 20.0;     // predicted interpreter time below this: no race
 constexpr double kRaceSliceMs = 20.0;
+constexpr double kRaceSliceMaxMs = 80.0;  // 16x16 miter: 6 slices instead of 17 (cold check 345 -> 339 ms)
 
 bool race_wanted(lec_es_ctx *c, const lec_es_plan *p, const lec_es_options *opt) {
   if (opt && (opt->tier != LEC_ES_TIER_AUTO || opt->grid_blocks || opt->block_threads || opt->flags)) return false;
@@ -688,7 +691,8 @@ int check_race(lec_es_ctx *c, lec_es_plan *p, const lec_es_miter *m, const lec_e
   const uint64_t W = num_words(g.n);
   const uint64_t wb = opt ? opt->word_begin : 0, we = opt ? std::min<uint64_t>(opt->word_end, W) : W;
   const double t_int = std::max(1e-3, cost_run_ms(c, LEC_ES_TIER_INTERP, g.cone_ands, g.n));
-  const uint64_t slice = std::max<uint64_t>(1u << 16, (uint64_t)((double)W * kRaceSliceMs / t_int));
+  uint64_t slice = std::max<uint64_t>(1u << 16, (uint64_t)((double)W * kRaceSliceMs / t_int));
+  const uint64_t slice_max = std::max<uint64_t>(slice, (uint64_t)((double)W * kRaceSliceMaxMs / t_int));
   std::shared_ptr<CompactMiter> cone;
   if (g.lut.deferred) {  // the build makes the table cover from its own copy of the cone
     cone = std::make_shared<CompactMiter>();
@@ -723,6 +727,7 @@ int check_race(lec_es_ctx *c, lec_es_plan *p, const lec_es_miter *m, const lec_e
     }
     o.word_begin = w;
     o.word_end = std::min(we, w + slice);
+    slice = std::min(slice_max, 2 * slice);
     rc = plan_run_async(c, p, &o);
     if (!rc) rc = plan_result(c, p, &r);
     if (rc) return rc;

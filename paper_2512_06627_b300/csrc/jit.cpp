@@ -37,7 +37,10 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#include <sys/resource.h>
 #include <sys/stat.h>
+#include <sys/syscall.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <condition_variable>
@@ -104,6 +107,7 @@ constexpr uint64_t kStrideMaxGrabs = 2 * 148 * 64;
 // parallel (see compile_program_kernel), at most kMaxChain layouts at once.
 constexpr uint32_t kParallelChainTables = 1000;
 constexpr uint32_t kMaxChain = 12;
+constexpr int kBuildNice = 10;  // nice value of background build threads
 constexpr uint32_t kDryPlan = 160;  // plan of the layout search's dry runs (see jit_layout)
 // Set while a single plan's kernel builds on the calling thread (the host is
 // otherwise idle): a large cone's first layout and the rest of its chain then
@@ -1794,6 +1798,12 @@ int build_kernel(lec_es_ctx *c, const Program &g, bool lut_form, JitKernel **out
 }
 
 void worker_loop(lec_es_ctx *c) {
+  // Background builds yield the host to the threads that launch kernels and
+  // wait for them: this thread, and the threads it starts for layout dry
+  // runs and compiles (they inherit its nice value), run at a lower
+  // priority.  (A cold 16x16 check ran its interpreter slices 12 ms slower
+  // than one interpreter launch while the build held every host thread.)
+  setpriority(PRIO_PROCESS, (id_t)syscall(SYS_gettid), kBuildNice);
   JitState *js = c->jit;
   for (;;) {
     Program g;

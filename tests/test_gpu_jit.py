@@ -70,7 +70,10 @@ def test_config3_full_and_closed_form_cex(ctx):
 
 
 def test_auto_picks_jit_for_big_work(ctx):
+    # with the kernel held (a cold check races the interpreter against the
+    # build instead: test_cold_check_races_interpreter_against_kernel_build)
     m = C.config3_mult16()
+    L.lec_es_check_ex(ctx, L.miter_of(m), L.options(tier=L.TIER_JIT))
     r = L.lec_es_check(ctx, L.miter_of(m))
     assert r.tier == L.TIER_JIT and r.verdict == L.EQUIVALENT
 
